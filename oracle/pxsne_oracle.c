@@ -1,0 +1,647 @@
+/*
+ * PixelSNE CPU oracle (FP64, plain C).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * statement of what the CUDA path computes.  Only the test-suite, the smoke
+ * check and the bench's CPU-baseline leg load it.  It shares no code, header,
+ * table or constant with the CUDA library, and it includes none of it.
+ *
+ * Every function follows the paper (Kim et al., "PixelSNE: Visualizing Fast
+ * with Just Enough Precision via Pixel-Aligned Stochastic Neighbor
+ * Embedding", arXiv 1611.02568) and cites the passage it follows.
+ *
+ * Conventions (the readings of the paper that this oracle implements):
+ *  - Screen r x r with r = 2^L.  Positions are fixed point: z_d is a u32 in
+ *    [0, 2^32) ulps; the pixel is z_d >> F with F = 32 - L (Eq. z1/z2).
+ *  - y-space (t-SNE's own coordinates) is y_d = s_d * z_d (+ an offset that no
+ *    quantity depends on).  s_d is the product of the per-iteration rescale
+ *    factors, i.e. sqrt(beta_d) of Eq. beta_scaling, carried directly.
+ *  - Morton index of a cell: x bits at even positions, y bits at odd ones.
+ *    Cell (l, m) at level l covers the pixels whose top l bits of x and y
+ *    give m; level offsets in a flattened pyramid are (4^l - 1) / 3.
+ *  - Barnes-Hut criterion (Eq. bh_criteria) read as r_c / ||y_i - y_c|| < theta
+ *    with r_c the cell's diagonal in y-units (the printed squared distance is
+ *    kept as crit_mode 1).
+ *  - The cell that contains point i is always opened; at a leaf, i is removed
+ *    from its own cell's count and sums (Sec. 4.1 "leaf termination").
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_R 4294967296.0 /* 2^32 ulps per axis */
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_num_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.3 (sparse P, exact neighbour sets as the vantage-point tree gives):
+ * the k nearest neighbours of x_i by squared Euclidean distance, self
+ * excluded by index, ties broken towards the lower index.  Brute force over
+ * all j in FP64 from the FP32 inputs.  rows == NULL means all n rows;
+ * otherwise the m query rows listed.  Output rows are ascending. */
+static int knn_before(double da, int32_t ja, double db, int32_t jb)
+{
+    return da < db || (da == db && ja < jb);
+}
+
+int orc_knn(const float *X, int64_t n, int32_t D, int32_t k,
+            const int64_t *rows, int64_t m, int32_t *idx, double *d2)
+{
+    if (k < 1 || (int64_t)k >= n) return -1;
+    int64_t err = 0;
+#pragma omp parallel for schedule(dynamic, 4) reduction(| : err)
+    for (int64_t q = 0; q < m; q++) {
+        int64_t i = rows ? rows[q] : q;
+        if (i < 0 || i >= n) { err |= 1; continue; }
+        int32_t *I = idx + q * k;
+        double *Dd = d2 + q * k;
+        int32_t cnt = 0;
+        const float *xi = X + i * (int64_t)D;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            const float *xj = X + j * (int64_t)D;
+            double s = 0.0;
+            for (int32_t d = 0; d < D; d++) {
+                double t = (double)xi[d] - (double)xj[d];
+                s += t * t;
+            }
+            int32_t p;
+            if (cnt < k) {
+                p = cnt++;
+            } else if (knn_before(s, (int32_t)j, Dd[k - 1], I[k - 1])) {
+                p = k - 1;
+            } else {
+                continue;
+            }
+            while (p > 0 && knn_before(s, (int32_t)j, Dd[p - 1], I[p - 1])) {
+                Dd[p] = Dd[p - 1];
+                I[p] = I[p - 1];
+                p--;
+            }
+            Dd[p] = s;
+            I[p] = (int32_t)j;
+        }
+    }
+    return err ? -2 : 0;
+}
+
+/* Sec. 3.2: the conditional p_{j|i} = exp(-beta_i d2_ij) / sum_j' exp(-beta_i d2_ij')
+ * over the k neighbours, with beta_i found by bisection so that the entropy
+ * H_i = -sum_j p_{j|i} ln p_{j|i} equals ln(perplexity).  Exponents are shifted
+ * by the row's minimum distance (p is unchanged).  Start beta = 1; double or
+ * halve until the target is bracketed, then bisect; stop when
+ * |H - ln u| < tol or after max_iter evaluations.  Returns the number of
+ * rows that did not converge. */
+int64_t orc_perplexity(const double *d2, int64_t n, int32_t k, double perplexity,
+                       double tol, int32_t max_iter, double *pcond,
+                       double *beta_out, double *H_out)
+{
+    const double target = log(perplexity);
+    int64_t bad = 0;
+#pragma omp parallel for schedule(static) reduction(+ : bad)
+    for (int64_t i = 0; i < n; i++) {
+        const double *d = d2 + i * k;
+        double *p = pcond + i * k;
+        double dmin = d[0];
+        for (int32_t j = 1; j < k; j++)
+            if (d[j] < dmin) dmin = d[j];
+        double beta = 1.0, lo = 0.0, hi = 0.0;
+        int has_lo = 0, has_hi = 0, ok = 0;
+        double H = 0.0;
+        for (int32_t it = 0; it < max_iter; it++) {
+            double sum = 0.0, hs = 0.0;
+            for (int32_t j = 0; j < k; j++) {
+                double e = exp(-beta * (d[j] - dmin));
+                sum += e;
+                hs += (d[j] - dmin) * e;
+            }
+            H = log(sum) + beta * hs / sum;
+            if (fabs(H - target) < tol) { ok = 1; break; }
+            if (H > target) { /* too flat: sharpen */
+                lo = beta; has_lo = 1;
+                beta = has_hi ? 0.5 * (beta + hi) : 2.0 * beta;
+            } else {
+                hi = beta; has_hi = 1;
+                beta = has_lo ? 0.5 * (beta + lo) : 0.5 * beta;
+            }
+        }
+        double sum = 0.0, hs = 0.0;
+        for (int32_t j = 0; j < k; j++) {
+            p[j] = exp(-beta * (d[j] - dmin));
+            sum += p[j];
+            hs += (d[j] - dmin) * p[j];
+        }
+        for (int32_t j = 0; j < k; j++) p[j] /= sum;
+        if (beta_out) beta_out[i] = beta;
+        if (H_out) H_out[i] = log(sum) + beta * hs / sum;
+        if (!ok) bad++;
+    }
+    return bad;
+}
+
+/* Sec. 3.3: the symmetric joint p_ij = (p_{j|i} + p_{i|j}) / (2n) on the union
+ * of the kNN patterns, as CSR with columns ascending in each row.
+ * Call with col == NULL to get nnz (row_ptr is then also filled). */
+typedef struct { int64_t r; int32_t c; double v; } orc_trip;
+
+static int trip_cmp(const void *a, const void *b)
+{
+    const orc_trip *x = (const orc_trip *)a, *y = (const orc_trip *)b;
+    if (x->r != y->r) return x->r < y->r ? -1 : 1;
+    if (x->c != y->c) return x->c < y->c ? -1 : 1;
+    return 0;
+}
+
+int64_t orc_symmetrize(const int32_t *idx, const double *pcond, int64_t n, int32_t k,
+                       int64_t *row_ptr, int32_t *col, double *val)
+{
+    int64_t m = 2 * n * (int64_t)k;
+    orc_trip *t = (orc_trip *)malloc((size_t)m * sizeof(orc_trip));
+    if (!t) return -1;
+    int64_t o = 0;
+    for (int64_t i = 0; i < n; i++)
+        for (int32_t a = 0; a < k; a++) {
+            int32_t j = idx[i * k + a];
+            double v = pcond[i * k + a];
+            t[o].r = i; t[o].c = j; t[o].v = v; o++;          /* p_{j|i} into (i,j) */
+            t[o].r = j; t[o].c = (int32_t)i; t[o].v = v; o++; /* p_{j|i} into (j,i) */
+        }
+    qsort(t, (size_t)m, sizeof(orc_trip), trip_cmp);
+    int64_t nnz = 0;
+    for (int64_t i = 0; i <= n; i++) row_ptr[i] = 0;
+    for (int64_t a = 0; a < m;) {
+        int64_t b = a;
+        double v = 0.0;
+        while (b < m && t[b].r == t[a].r && t[b].c == t[a].c) v += t[b++].v;
+        if (col) {
+            col[nnz] = t[a].c;
+            val[nnz] = v / (2.0 * (double)n);
+        }
+        row_ptr[t[a].r + 1]++;
+        nnz++;
+        a = b;
+    }
+    for (int64_t i = 0; i < n; i++) row_ptr[i + 1] += row_ptr[i];
+    free(t);
+    return nnz;
+}
+
+/* Eq. z1/z2: map an initial embedding Y0 (n x 2, y-units) onto the fixed-point
+ * screen: z_d = min(R-1, floor((y_d - min_d) * R / (max_d - min_d))),
+ * s_d = (max_d - min_d) / R, with R = 2^32.  An axis with zero extent maps to
+ * z_d = 0 and s_d = 1/R. */
+void orc_init_fx(const double *Y0, int64_t n, uint32_t *z, double *s)
+{
+    for (int d = 0; d < 2; d++) {
+        double mn = Y0[d], mx = Y0[d];
+        for (int64_t i = 1; i < n; i++) {
+            double v = Y0[2 * i + d];
+            if (v < mn) mn = v;
+            if (v > mx) mx = v;
+        }
+        double range = mx - mn;
+        if (!(range > 0.0)) {
+            for (int64_t i = 0; i < n; i++) z[2 * i + d] = 0u;
+            s[d] = 1.0 / ORC_R;
+            continue;
+        }
+        for (int64_t i = 0; i < n; i++) {
+            double q = floor((Y0[2 * i + d] - mn) * ORC_R / range);
+            z[2 * i + d] = q >= ORC_R - 1.0 ? 0xFFFFFFFFu : (uint32_t)q;
+        }
+        s[d] = range / ORC_R;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 4.1 P-Quadtree.  Morton index of pixel (px, py), bit by bit. */
+uint32_t orc_morton(uint32_t px, uint32_t py)
+{
+    uint32_t m = 0;
+    for (int b = 0; b < 16; b++) {
+        m |= ((px >> b) & 1u) << (2 * b);
+        m |= ((py >> b) & 1u) << (2 * b + 1);
+    }
+    return m;
+}
+
+int64_t orc_level_offset(int32_t l)
+{
+    return (((int64_t)1 << (2 * l)) - 1) / 3;
+}
+
+/* Pixel of each point (Eq. z1: floor of the screen coordinate) and the Morton
+ * index of its leaf cell. */
+void orc_leaf_keys(const uint32_t *z, int64_t n, int32_t L, uint32_t *px,
+                   uint32_t *py, uint32_t *morton)
+{
+    int F = 32 - L;
+    for (int64_t i = 0; i < n; i++) {
+        uint32_t x = z[2 * i] >> F, y = z[2 * i + 1] >> F;
+        if (px) px[i] = x;
+        if (py) py[i] = y;
+        morton[i] = orc_morton(x, y);
+    }
+}
+
+/* Eq. ycell / ctrofmass on the fixed tree: for every cell of every level
+ * l = 0..L, N_c = number of points whose pixel lies in the cell and the exact
+ * integer sums of their z (the centre of mass is sum / N_c).  Each point is
+ * added directly to the cell that contains it at every level. */
+void orc_pyramid(const uint32_t *z, int64_t n, int32_t L, uint32_t *cnt,
+                 uint64_t *sx, uint64_t *sy)
+{
+    int64_t cells = orc_level_offset(L + 1);
+    memset(cnt, 0, (size_t)cells * sizeof(uint32_t));
+    memset(sx, 0, (size_t)cells * sizeof(uint64_t));
+    memset(sy, 0, (size_t)cells * sizeof(uint64_t));
+    int F = 32 - L;
+    for (int64_t i = 0; i < n; i++) {
+        uint32_t m = orc_morton(z[2 * i] >> F, z[2 * i + 1] >> F);
+        for (int32_t l = 0; l <= L; l++) {
+            int64_t c = orc_level_offset(l) + (m >> (2 * (L - l)));
+            cnt[c] += 1u;
+            sx[c] += z[2 * i];
+            sy[c] += z[2 * i + 1];
+        }
+    }
+}
+
+/* Offset, in ulps, of a point from a centre of mass S / N: z - S/N computed as
+ * (z - floor(S/N)) - (S mod N)/N so that no precision is lost for large S. */
+static double com_offset(uint32_t zi, uint64_t S, uint64_t N)
+{
+    uint64_t q = S / N, r = S % N;
+    return (double)((int64_t)zi - (int64_t)q) - (double)r / (double)N;
+}
+
+/* Eq. grad second term with Eq. bh_criteria on the pixel-aligned tree
+ * (Sec. 3.3, Sec. 4.1).  For each point i (rows == NULL: all; else the m
+ * listed ones), depth-first over the cells with N_c > 0, starting at the root:
+ *   - the cell containing i's pixel is opened; at a leaf, i is taken out
+ *     (N' = N_c - 1, S' = S - z_i) and the rest is used if N' > 0;
+ *   - another cell is accepted if it is a leaf (bounded depth, Sec. 4.1) or if
+ *     r_c / ||y_i - y_c|| < theta (crit_mode 0; crit_mode 1 is the printed
+ *     r_c / ||y_i - y_c||^2 < theta), else its four children are visited;
+ *   - an accepted cell adds N w to Z_i and N w^2 (y_i - y_c) to Frep_i with
+ *     w = 1 / (1 + ||y_i - y_c||^2).
+ * y_c is the centre of mass (centre_mode 0) or the cell's geometric centre
+ * (centre_mode 1, the approximation printed in Sec. 4.1).
+ * Frep is the un-normalised sum (the gradient divides it by Z = sum_i Z_i).
+ * n_inter (optional) gets the number of accepted cells per listed row. */
+void orc_bh_repulsion(const uint32_t *z, const double *s, int64_t n, int32_t L,
+                      double theta, int32_t crit_mode, int32_t centre_mode,
+                      const uint32_t *cnt, const uint64_t *sx, const uint64_t *sy,
+                      const int64_t *rows, int64_t m, double *Frep, double *Zi,
+                      int64_t *n_inter)
+{
+    const int F = 32 - L;
+    const double th2 = theta * theta;
+    const double s0 = s[0], s1 = s[1];
+    (void)n;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < m; q++) {
+        int64_t i = rows ? rows[q] : q;
+        const uint32_t zx = z[2 * i], zy = z[2 * i + 1];
+        const uint32_t mi = orc_morton(zx >> F, zy >> F);
+        int32_t stk_l[64 * 4];
+        uint32_t stk_m[64 * 4];
+        int sp = 0;
+        double fx = 0.0, fy = 0.0, zsum = 0.0;
+        int64_t acc = 0;
+        stk_l[sp] = 0; stk_m[sp] = 0; sp++;
+        while (sp > 0) {
+            sp--;
+            int32_t l = stk_l[sp];
+            uint32_t mc = stk_m[sp];
+            int64_t c = orc_level_offset(l) + mc;
+            uint64_t N = cnt[c];
+            if (N == 0) continue;
+            int leaf = (l == L);
+            int contains = ((mi >> (2 * (L - l))) == mc);
+            uint64_t Sx = sx[c], Sy = sy[c];
+            if (contains) {
+                if (!leaf) {
+                    for (uint32_t ch = 0; ch < 4; ch++) {
+                        stk_l[sp] = l + 1; stk_m[sp] = 4 * mc + ch; sp++;
+                    }
+                    continue;
+                }
+                N -= 1;
+                if (N == 0) continue;
+                Sx -= zx;
+                Sy -= zy;
+            }
+            double dx, dy;
+            if (centre_mode == 0) {
+                dx = s0 * com_offset(zx, Sx, N);
+                dy = s1 * com_offset(zy, Sy, N);
+            } else {
+                /* geometric centre of cell (l, mc): origin + W/2 */
+                uint32_t cx = 0, cy = 0;
+                for (int b = 0; b < l; b++) {
+                    cx |= ((mc >> (2 * b)) & 1u) << b;
+                    cy |= ((mc >> (2 * b + 1)) & 1u) << b;
+                }
+                double W = ldexp(1.0, 32 - l);
+                dx = s0 * ((double)zx - ((double)cx * W + 0.5 * W));
+                dy = s1 * ((double)zy - ((double)cy * W + 0.5 * W));
+            }
+            double dd = dx * dx + dy * dy;
+            if (!leaf && !contains) {
+                double W = ldexp(1.0, 32 - l);
+                double rc2 = (s0 * W) * (s0 * W) + (s1 * W) * (s1 * W);
+                int accept = crit_mode == 0 ? (rc2 < th2 * dd) : (rc2 < th2 * dd * dd);
+                if (!accept) {
+                    for (uint32_t ch = 0; ch < 4; ch++) {
+                        stk_l[sp] = l + 1; stk_m[sp] = 4 * mc + ch; sp++;
+                    }
+                    continue;
+                }
+            }
+            double w = 1.0 / (1.0 + dd);
+            double Nw = (double)N * w;
+            zsum += Nw;
+            fx += Nw * w * dx;
+            fy += Nw * w * dy;
+            acc++;
+        }
+        Frep[2 * q] = fx;
+        Frep[2 * q + 1] = fy;
+        Zi[q] = zsum;
+        if (n_inter) n_inter[q] = acc;
+    }
+}
+
+/* Eq. q and Eq. grad second term without any approximation: for each listed
+ * i, sum over all j != i of w_ij and w_ij^2 (y_i - y_j), w_ij = 1/(1+||y_i-y_j||^2).
+ * Differences of fixed-point positions are exact integers before scaling. */
+void orc_exact_repulsion(const uint32_t *z, const double *s, int64_t n,
+                         const int64_t *rows, int64_t m, double *Frep, double *Zi)
+{
+    const double s0 = s[0], s1 = s[1];
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < m; q++) {
+        int64_t i = rows ? rows[q] : q;
+        double fx = 0.0, fy = 0.0, zs = 0.0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double dx = s0 * (double)((int64_t)z[2 * i] - (int64_t)z[2 * j]);
+            double dy = s1 * (double)((int64_t)z[2 * i + 1] - (int64_t)z[2 * j + 1]);
+            double w = 1.0 / (1.0 + dx * dx + dy * dy);
+            zs += w;
+            fx += w * w * dx;
+            fy += w * w * dy;
+        }
+        Frep[2 * q] = fx;
+        Frep[2 * q + 1] = fy;
+        Zi[q] = zs;
+    }
+}
+
+/* Eq. grad first term over the sparse P (Sec. 3.3):
+ * Fattr_i = sum_j p_ij w_ij (y_i - y_j), un-exaggerated. */
+void orc_attraction(const int64_t *row_ptr, const int32_t *col, const double *val,
+                    const uint32_t *z, const double *s, const int64_t *rows,
+                    int64_t m, double *Fattr)
+{
+    const double s0 = s[0], s1 = s[1];
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < m; q++) {
+        int64_t i = rows ? rows[q] : q;
+        double fx = 0.0, fy = 0.0;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; e++) {
+            int64_t j = col[e];
+            double dx = s0 * (double)((int64_t)z[2 * i] - (int64_t)z[2 * j]);
+            double dy = s1 * (double)((int64_t)z[2 * i + 1] - (int64_t)z[2 * j + 1]);
+            double w = 1.0 / (1.0 + dx * dx + dy * dy);
+            fx += val[e] * w * dx;
+            fy += val[e] * w * dy;
+        }
+        Fattr[2 * q] = fx;
+        Fattr[2 * q + 1] = fy;
+    }
+}
+
+/* Eq. grad assembled, then one gradient-descent step with momentum and
+ * per-coordinate gains (the BH-SNE optimiser the paper keeps):
+ *   g = 4 (alpha Fattr - Frep / Z)
+ *   gain = (sign(g) != sign(u)) ? gain + 0.2 : gain * 0.8, at least min_gain,
+ *          with sign(0) = 0 (so the first step, u = 0, always gains 0.2)
+ *   u = mu u - eta gain g                       (y-units)
+ *   zhat = z + rint(u / s)                      (ulps, int64)
+ * zhat is the un-normalised update of Sec. 4.2, before screen rescaling. */
+static int sgn(double x) { return x > 0.0 ? 1 : (x < 0.0 ? -1 : 0); }
+
+void orc_update(int64_t n, const uint32_t *z, const double *s, const double *Fattr,
+                const double *Frep, double Z, double alpha, double mu, double eta,
+                double min_gain, double *u, double *gains, double *grad, int64_t *zhat)
+{
+    for (int64_t i = 0; i < n; i++)
+        for (int d = 0; d < 2; d++) {
+            int64_t k = 2 * i + d;
+            double g = 4.0 * (alpha * Fattr[k] - Frep[k] / Z);
+            if (grad) grad[k] = g;
+            double gn = (sgn(g) != sgn(u[k])) ? gains[k] + 0.2 : gains[k] * 0.8;
+            if (gn < min_gain) gn = min_gain;
+            gains[k] = gn;
+            u[k] = mu * u[k] - eta * gn * g;
+            zhat[k] = (int64_t)z[k] + llrint(u[k] / s[d]);
+        }
+}
+
+/* Sec. 4.2 screen-driven scaling, in exact integer arithmetic:
+ *   z_d = floor((zhat_d - min_d) * R / gamma_d),  gamma_d = (max_d - min_d) + 1
+ * (the "+ epsilon" of gamma is one ulp), and the compensation of Eq.
+ * beta_scaling carried as s_d <- s_d * gamma_d / R. */
+void orc_rescale(int64_t n, const int64_t *zhat, uint32_t *z, double *s)
+{
+    for (int d = 0; d < 2; d++) {
+        int64_t mn = zhat[d], mx = zhat[d];
+        for (int64_t i = 1; i < n; i++) {
+            int64_t v = zhat[2 * i + d];
+            if (v < mn) mn = v;
+            if (v > mx) mx = v;
+        }
+        uint64_t gamma = (uint64_t)(mx - mn) + 1u;
+        for (int64_t i = 0; i < n; i++) {
+            unsigned __int128 num = (unsigned __int128)(uint64_t)(zhat[2 * i + d] - mn) << 32;
+            z[2 * i + d] = (uint32_t)(num / gamma);
+        }
+        s[d] = s[d] * ldexp((double)gamma, -32);
+    }
+}
+
+/* Eq. cost_func: C = sum_ij p_ij ln(p_ij / q_ij) with q_ij = w_ij / Z, over the
+ * non-zeros of P (zero entries contribute nothing). */
+double orc_kl(const int64_t *row_ptr, const int32_t *col, const double *val,
+              int64_t n, const uint32_t *z, const double *s, double Z)
+{
+    const double s0 = s[0], s1 = s[1];
+    double C = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : C)
+    for (int64_t i = 0; i < n; i++) {
+        double c = 0.0;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; e++) {
+            double p = val[e];
+            if (p <= 0.0) continue;
+            int64_t j = col[e];
+            double dx = s0 * (double)((int64_t)z[2 * i] - (int64_t)z[2 * j]);
+            double dy = s1 * (double)((int64_t)z[2 * i + 1] - (int64_t)z[2 * j + 1]);
+            double q = 1.0 / ((1.0 + dx * dx + dy * dy) * Z);
+            c += p * log(p / q);
+        }
+        C += c;
+    }
+    return C;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One full PixelSNE run (Fig. 1(c), Sec. 4): for t = t0 .. t0+iters-1
+ *   P-Quadtree assignment, BH repulsion, attraction, Z, gradient step,
+ *   screen rescale.
+ * Schedule: alpha = exag for t < exag_iters else 1; mu = mom0 for
+ * t < mom_switch else mom1.  exact != 0 replaces the tree by the O(n^2)
+ * repulsion.  Z_trace (optional, length iters) gets the Z used at each step. */
+typedef struct {
+    int32_t L;
+    double theta;
+    double eta;
+    double exag;
+    int32_t exag_iters;
+    double mom0, mom1;
+    int32_t mom_switch;
+    double min_gain;
+    int32_t crit_mode;
+    int32_t centre_mode;
+    int32_t exact;
+} orc_params;
+
+int orc_run(const orc_params *p, const int64_t *row_ptr, const int32_t *col,
+            const double *val, int64_t n, uint32_t *z, double *s, double *u,
+            double *gains, int32_t t0, int32_t iters, double *Z_trace)
+{
+    int64_t cells = orc_level_offset(p->L + 1);
+    uint32_t *cnt = NULL;
+    uint64_t *sx = NULL, *sy = NULL;
+    if (!p->exact) {
+        cnt = (uint32_t *)malloc((size_t)cells * sizeof(uint32_t));
+        sx = (uint64_t *)malloc((size_t)cells * sizeof(uint64_t));
+        sy = (uint64_t *)malloc((size_t)cells * sizeof(uint64_t));
+    }
+    double *Frep = (double *)malloc((size_t)n * 2 * sizeof(double));
+    double *Fattr = (double *)malloc((size_t)n * 2 * sizeof(double));
+    double *Zi = (double *)malloc((size_t)n * sizeof(double));
+    int64_t *zhat = (int64_t *)malloc((size_t)n * 2 * sizeof(int64_t));
+    if ((!p->exact && (!cnt || !sx || !sy)) || !Frep || !Fattr || !Zi || !zhat) {
+        free(cnt); free(sx); free(sy); free(Frep); free(Fattr); free(Zi); free(zhat);
+        return -1;
+    }
+    for (int32_t t = t0; t < t0 + iters; t++) {
+        if (p->exact) {
+            orc_exact_repulsion(z, s, n, NULL, n, Frep, Zi);
+        } else {
+            orc_pyramid(z, n, p->L, cnt, sx, sy);
+            orc_bh_repulsion(z, s, n, p->L, p->theta, p->crit_mode, p->centre_mode,
+                             cnt, sx, sy, NULL, n, Frep, Zi, NULL);
+        }
+        double Z = 0.0;
+        for (int64_t i = 0; i < n; i++) Z += Zi[i];
+        if (Z_trace) Z_trace[t - t0] = Z;
+        orc_attraction(row_ptr, col, val, z, s, NULL, n, Fattr);
+        double alpha = t < p->exag_iters ? p->exag : 1.0;
+        double mu = t < p->mom_switch ? p->mom0 : p->mom1;
+        orc_update(n, z, s, Fattr, Frep, Z, alpha, mu, p->eta, p->min_gain, u, gains,
+                   NULL, zhat);
+        orc_rescale(n, zhat, z, s);
+    }
+    free(cnt); free(sx); free(sy); free(Frep); free(Fattr); free(Zi); free(zhat);
+    return 0;
+}
+
+/* Z of the current state (BH with the run's theta, or exact), for the KL. */
+double orc_Z(const orc_params *p, int64_t n, const uint32_t *z, const double *s)
+{
+    double *Zi = (double *)malloc((size_t)n * sizeof(double));
+    double *Frep = (double *)malloc((size_t)n * 2 * sizeof(double));
+    double Z = -1.0;
+    if (!Zi || !Frep) goto out;
+    if (p->exact) {
+        orc_exact_repulsion(z, s, n, NULL, n, Frep, Zi);
+    } else {
+        int64_t cells = orc_level_offset(p->L + 1);
+        uint32_t *cnt = (uint32_t *)malloc((size_t)cells * sizeof(uint32_t));
+        uint64_t *sx = (uint64_t *)malloc((size_t)cells * sizeof(uint64_t));
+        uint64_t *sy = (uint64_t *)malloc((size_t)cells * sizeof(uint64_t));
+        if (!cnt || !sx || !sy) { free(cnt); free(sx); free(sy); goto out; }
+        orc_pyramid(z, n, p->L, cnt, sx, sy);
+        orc_bh_repulsion(z, s, n, p->L, p->theta, p->crit_mode, p->centre_mode, cnt, sx,
+                         sy, NULL, n, Frep, Zi, NULL);
+        free(cnt); free(sx); free(sy);
+    }
+    Z = 0.0;
+    for (int64_t i = 0; i < n; i++) Z += Zi[i];
+out:
+    free(Zi);
+    free(Frep);
+    return Z;
+}
+
+/* Eq. nei_prec: (1/(k m)) sum_i |N_D^k(i) intersect N_d^k(i)| over the listed
+ * rows, with N_d^k(i) the k nearest neighbours of y_i in the 2-D embedding
+ * (brute force, FP64, ties to the lower index) and N_D^k(i) given (knn_hd,
+ * row q holds the neighbours of rows[q], at least k per row, stride kh). */
+double orc_nbr_precision(const int32_t *knn_hd, int32_t kh, int32_t k, int64_t n,
+                         const uint32_t *z, const double *s, const int64_t *rows,
+                         int64_t m)
+{
+    const double s0 = s[0], s1 = s[1];
+    int64_t hits = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : hits)
+    for (int64_t q = 0; q < m; q++) {
+        int64_t i = rows ? rows[q] : q;
+        int32_t *I = (int32_t *)malloc((size_t)k * sizeof(int32_t));
+        double *Dd = (double *)malloc((size_t)k * sizeof(double));
+        int32_t cnt = 0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double dx = s0 * (double)((int64_t)z[2 * i] - (int64_t)z[2 * j]);
+            double dy = s1 * (double)((int64_t)z[2 * i + 1] - (int64_t)z[2 * j + 1]);
+            double dd = dx * dx + dy * dy;
+            int32_t p;
+            if (cnt < k) p = cnt++;
+            else if (knn_before(dd, (int32_t)j, Dd[k - 1], I[k - 1])) p = k - 1;
+            else continue;
+            while (p > 0 && knn_before(dd, (int32_t)j, Dd[p - 1], I[p - 1])) {
+                Dd[p] = Dd[p - 1]; I[p] = I[p - 1]; p--;
+            }
+            Dd[p] = dd; I[p] = (int32_t)j;
+        }
+        for (int32_t a = 0; a < k; a++)
+            for (int32_t b = 0; b < k; b++)
+                if (knn_hd[q * (int64_t)kh + b] == I[a]) { hits++; break; }
+        free(I);
+        free(Dd);
+    }
+    return (double)hits / ((double)k * (double)m);
+}

@@ -1,0 +1,494 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each oracle function is checked against what the paper and the mathematics
+fix, so that a dropped term, a wrong sign or index, or a transposed operand
+fails at least one test:
+
+  knn            brute force by a full stable argsort of the FP64 distance matrix
+  perplexity     definitional invariants of the output (entropy of the returned
+                 row = ln u, p proportional to exp(-beta d2), rows sum to 1),
+                 closed form for equal distances, scale invariance
+  symmetrize     dense (P_cond + P_cond^T) / 2n construction, sum 1, symmetry
+  init_fx        extremes map to 0 and R-1, affine within one ulp
+  morton         recursive quadtree child numbering (child = 2*ybit + xbit)
+  pyramid        per-level bincount of the shifted pixel pairs; sums
+  exact forces   scikit-learn's exact t-SNE KL and gradient; hand-derived
+                 closed forms (tests/golden/kl_closed_forms.txt); finite
+                 differences of the KL; net force zero
+  bh_repulsion   theta = 0 with <= 1 point per pixel equals the exact sum;
+                 theta = 0 in general equals a tree-free brute force over pixels
+  rescale        Python big-integer arithmetic; pixel range exactly 0..r-1
+  run            the fixed-point + rescale + beta run equals plain y-space
+                 t-SNE (scikit-learn gradient) up to translation (Sec. 4.2's
+                 claimed equivalence)
+  kl             scikit-learn, closed forms, KL >= 0
+  nbr_precision  identity cases (precision 1 for the same geometry, ~k/n for
+                 an unrelated one)
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+R = 2 ** 32
+
+
+# ------------------------------------------------------------------ kNN
+def test_knn_matches_full_sort():
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((257, 7)).astype(np.float32)
+    X[10] = X[3]           # duplicate points: distance 0, tie on index
+    X[200] = X[3]
+    X[50] = X[51]
+    k = 12
+    idx, d2 = oracle.knn(X, k)
+    Xd = X.astype(np.float64)
+    Dm = ((Xd[:, None, :] - Xd[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(Dm, np.inf)
+    ref = np.argsort(Dm, axis=1, kind="stable")[:, :k]
+    assert np.array_equal(idx, ref)
+    np.testing.assert_allclose(d2, np.take_along_axis(Dm, ref, 1), rtol=1e-12, atol=0)
+    # sampled rows give the same answer as the full run
+    rows = np.array([0, 3, 256, 10])
+    idx2, d22 = oracle.knn(X, k, rows=rows)
+    assert np.array_equal(idx2, idx[rows])
+    assert idx[3][0] in (10, 200) and idx[3][0] == 10  # lower index wins the tie
+
+
+def test_knn_rejects_k_ge_n():
+    X = np.zeros((5, 3), np.float32)
+    with pytest.raises(ValueError):
+        oracle.knn(X, 5)
+
+
+# ------------------------------------------------------------------ perplexity
+def test_perplexity_invariants():
+    rng = np.random.default_rng(2)
+    d2 = np.sort(rng.gamma(3.0, 20.0, (300, 90)), axis=1)
+    u = 30.0
+    p, beta, H, bad = oracle.perplexity(d2, u)
+    assert bad == 0
+    assert np.all(beta > 0)
+    np.testing.assert_allclose(p.sum(1), 1.0, rtol=0, atol=1e-12)
+    Hdef = -(p * np.log(p)).sum(1)            # entropy of the returned rows
+    assert np.max(np.abs(Hdef - math.log(u))) < 1e-5
+    np.testing.assert_allclose(Hdef, H, rtol=0, atol=1e-10)
+    # Gaussian kernel: p_j / p_0 = exp(-beta (d_j - d_0))
+    ratio = p / p[:, :1]
+    np.testing.assert_allclose(ratio, np.exp(-beta[:, None] * (d2 - d2[:, :1])),
+                               rtol=1e-10, atol=1e-300)
+    # ascending distances give non-increasing p
+    assert np.all(np.diff(p, axis=1) <= 1e-15)
+
+
+def test_perplexity_equal_distances_closed_form():
+    # all k distances equal: p = 1/k for every beta and H = ln k
+    d2 = np.full((4, 30), 7.25)
+    p, beta, H, bad = oracle.perplexity(d2, 30.0)
+    assert bad == 0
+    np.testing.assert_allclose(p, 1.0 / 30, rtol=1e-14)
+    np.testing.assert_allclose(H, math.log(30), rtol=1e-14)
+
+
+def test_perplexity_scale_invariance():
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((400, 10)).astype(np.float32)
+    idx1, d1 = oracle.knn(X, 30)
+    idx2, d2 = oracle.knn(X * np.float32(4.0), 30)
+    assert np.array_equal(idx1, idx2)
+    p1, b1, _, _ = oracle.perplexity(d1, 10.0)
+    p2, b2, _, _ = oracle.perplexity(d2, 10.0)
+    # beta absorbs the scale (c^2 = 16) up to the bisection tolerance
+    np.testing.assert_allclose(p1, p2, rtol=2e-3, atol=1e-6)
+
+
+# ------------------------------------------------------------------ symmetrize
+def test_symmetrize_dense():
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((150, 5)).astype(np.float32)
+    k = 9
+    idx, d2 = oracle.knn(X, k)
+    p, _, _, _ = oracle.perplexity(d2, 3.0)
+    P = oracle.symmetrize(idx, p)
+    n = X.shape[0]
+    C = np.zeros((n, n))
+    for i in range(n):
+        C[i, idx[i]] = p[i]
+    ref = (C + C.T) / (2 * n)
+    D = P.dense()
+    np.testing.assert_allclose(D, ref, rtol=1e-14, atol=0)
+    assert abs(D.sum() - 1.0) < 1e-12
+    assert np.array_equal(D != 0, ref != 0)
+    for i in range(n):  # columns strictly ascending in each row, no self
+        c = P.col[P.row_ptr[i]:P.row_ptr[i + 1]]
+        assert np.all(np.diff(c) > 0) and i not in c
+
+
+# ------------------------------------------------------------------ fixed point
+def test_init_fx_extremes_and_affine():
+    rng = np.random.default_rng(5)
+    Y = rng.standard_normal((500, 2)) * 1e-4
+    z, s = oracle.init_fx(Y)
+    for d in range(2):
+        assert z[:, d].min() == 0 and z[:, d].max() == R - 1
+        mn, mx = Y[:, d].min(), Y[:, d].max()
+        assert s[d] == (mx - mn) / R
+        back = z[:, d].astype(np.float64) * s[d] + mn
+        assert np.max(np.abs(back - Y[:, d])) <= s[d] * 1.0000001
+    # degenerate axis
+    Y2 = np.stack([np.arange(4.0), np.full(4, 3.0)], 1)
+    z2, s2 = oracle.init_fx(Y2)
+    assert np.all(z2[:, 1] == 0) and s2[1] == 1.0 / R
+
+
+def _morton_rec(px, py):
+    if px == 0 and py == 0:
+        return 0
+    return 4 * _morton_rec(px >> 1, py >> 1) + ((py & 1) << 1 | (px & 1))
+
+
+def test_morton_recursive_child_numbering():
+    rng = np.random.default_rng(6)
+    for px, py in rng.integers(0, 2 ** 15, (300, 2)):
+        assert oracle.morton(px, py) == _morton_rec(int(px), int(py))
+    assert [oracle.morton(x, y) for (x, y) in [(0, 0), (1, 0), (0, 1), (1, 1)]] == [0, 1, 2, 3]
+    # an aligned 2^k x 2^k block is a contiguous Morton range
+    k = 3
+    block = sorted(oracle.morton(8 + x, 16 + y) for x in range(8) for y in range(8))
+    assert block == list(range(block[0], block[0] + 64))
+
+
+def test_pyramid_counts_and_sums():
+    rng = np.random.default_rng(7)
+    L = 5
+    n = 3000
+    z = rng.integers(0, R, (n, 2), dtype=np.uint64)
+    z[:500] = z[0]          # a hot pixel
+    z = z.astype(np.uint32)
+    cnt, sx, sy = oracle.pyramid(z, L)
+    assert cnt.shape[0] == (4 ** (L + 1) - 1) // 3
+    F = 32 - L
+    px = (z[:, 0] >> F).astype(np.int64)
+    py = (z[:, 1] >> F).astype(np.int64)
+    for l in range(L + 1):
+        off = (4 ** l - 1) // 3
+        cx, cy = px >> (L - l), py >> (L - l)
+        m = np.array([_morton_rec(int(a), int(b)) for a, b in zip(cx, cy)])
+        ref_cnt = np.bincount(m, minlength=4 ** l)
+        assert np.array_equal(cnt[off:off + 4 ** l], ref_cnt)
+        ref_sx = np.zeros(4 ** l, dtype=object)
+        ref_sy = np.zeros(4 ** l, dtype=object)
+        for i in range(n):
+            ref_sx[m[i]] += int(z[i, 0])
+            ref_sy[m[i]] += int(z[i, 1])
+        assert [int(v) for v in sx[off:off + 4 ** l]] == list(ref_sx)
+        assert [int(v) for v in sy[off:off + 4 ** l]] == list(ref_sy)
+        assert int(cnt[off:off + 4 ** l].sum()) == n
+    _, _, mk = oracle.leaf_keys(z, L)
+    assert np.array_equal(mk, [_morton_rec(int(a), int(b)) for a, b in zip(px, py)])
+
+
+# ------------------------------------------------------------------ forces / KL
+def _dense_csr(Pd):
+    n = Pd.shape[0]
+    rows, cols = np.nonzero(Pd)
+    rp = np.zeros(n + 1, np.int64)
+    np.add.at(rp, rows + 1, 1)
+    rp = np.cumsum(rp)
+    return oracle.CSR(rp, cols.astype(np.int32), Pd[rows, cols].astype(np.float64))
+
+
+def _random_state(n, seed, sigma=3.0):
+    rng = np.random.default_rng(seed)
+    Y = rng.standard_normal((n, 2)) * sigma
+    return oracle.init_fx(Y)
+
+
+def _oracle_grad(P, z, s, alpha=1.0):
+    Frep, Zi = oracle.exact_repulsion(z, s)
+    Fattr = oracle.attraction(P, z, s)
+    Z = Zi.sum()
+    return 4.0 * (alpha * Fattr - Frep / Z), Z, Fattr, Frep
+
+
+def test_exact_gradient_and_kl_match_sklearn():
+    tsne = pytest.importorskip("sklearn.manifold._t_sne")
+    from scipy.spatial.distance import squareform
+    n = 40
+    rng = np.random.default_rng(8)
+    A = rng.random((n, n))
+    A = A + A.T
+    np.fill_diagonal(A, 0)
+    Pd = A / A.sum()
+    P = _dense_csr(Pd)
+    z, s = _random_state(n, 9)
+    y = z.astype(np.float64) * s
+    g, Z, _, _ = _oracle_grad(P, z, s)
+    kl_ref, g_ref = tsne._kl_divergence(y.ravel(), squareform(Pd, checks=False), 1, n, 2)
+    np.testing.assert_allclose(g.ravel(), g_ref, rtol=1e-9, atol=1e-12 * np.abs(g_ref).max())
+    assert abs(oracle.kl(P, z, s, Z) - kl_ref) < 1e-10 * max(1.0, kl_ref)
+    # exaggerated gradient = gradient of the KL with alpha * P in the first term
+    g4, _, _, _ = _oracle_grad(P, z, s, alpha=4.0)
+    _, g4_ref = tsne._kl_divergence(y.ravel(), 4.0 * squareform(Pd, checks=False), 1, n, 2)
+    np.testing.assert_allclose(g4.ravel(), g4_ref, rtol=1e-9,
+                               atol=1e-12 * np.abs(g4_ref).max())
+
+
+def test_gradient_finite_differences():
+    n = 25
+    rng = np.random.default_rng(10)
+    A = rng.random((n, n)) ** 3
+    A = A + A.T
+    np.fill_diagonal(A, 0)
+    P = _dense_csr(A / A.sum())
+    z, s = _random_state(n, 11)
+    g, _, _, _ = _oracle_grad(P, z, s)
+
+    def C(zz):
+        _, Zi = oracle.exact_repulsion(zz, s)
+        return oracle.kl(P, zz, s, Zi.sum())
+
+    h = 2 ** 18  # ulps
+    for i, d in [(0, 0), (3, 1), (17, 0), (24, 1)]:
+        zp = z.astype(np.int64).copy()
+        zm = z.astype(np.int64).copy()
+        zp[i, d] += h
+        zm[i, d] -= h
+        fd = (C(zp.astype(np.uint32)) - C(zm.astype(np.uint32))) / (2 * h * s[d])
+        assert abs(fd - g[i, d]) < 1e-6 * np.abs(g).max()
+
+
+def _golden_cases():
+    out = []
+    with open(os.path.join(GOLDEN, "kl_closed_forms.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            t = line.split()
+            n = int(t[1])
+            xs = [float(v) for v in t[2:2 + n]]
+            kl = float(t[2 + n])
+            gx = [float(v) for v in t[3 + n:3 + 2 * n]]
+            out.append((t[0], n, xs, kl, gx))
+    return out
+
+
+@pytest.mark.parametrize("case", _golden_cases(), ids=lambda c: c[0])
+def test_closed_form_kl_and_gradient(case):
+    name, n, xs, kl_ref, gx_ref = case
+    # y_x = s_x * z_x exactly with s_x = 2^-20; y_y = 0
+    s = np.array([2.0 ** -20, 1.0])
+    z = np.zeros((n, 2), np.uint32)
+    z[:, 0] = [int(round(x * 2 ** 20)) for x in xs]
+    Pd = np.zeros((n, n))
+    Pd[0, 1] = Pd[1, 0] = 0.5
+    P = _dense_csr(Pd)
+    g, Z, _, _ = _oracle_grad(P, z, s)
+    assert abs(oracle.kl(P, z, s, Z) - kl_ref) < 1e-14
+    np.testing.assert_allclose(g[:, 0], gx_ref, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(g[:, 1], 0.0, atol=0)
+
+
+def test_net_forces_vanish():
+    n = 120
+    rng = np.random.default_rng(12)
+    A = (rng.random((n, n)) < 0.1) * rng.random((n, n))
+    A = A + A.T
+    np.fill_diagonal(A, 0)
+    P = _dense_csr(A / A.sum())
+    z, s = _random_state(n, 13)
+    Frep, Zi = oracle.exact_repulsion(z, s)
+    Fattr = oracle.attraction(P, z, s)
+    assert np.abs(Fattr.sum(0)).max() < 1e-12 * np.abs(Fattr).sum()
+    assert np.abs(Frep.sum(0)).max() < 1e-12 * np.abs(Frep).sum()
+
+
+def _unique_pixel_state(n, L, seed):
+    rng = np.random.default_rng(seed)
+    F = 32 - L
+    pix = rng.choice(4 ** L, size=n, replace=False)
+    px, py = pix % (2 ** L), pix // (2 ** L)
+    z = np.stack([(px << F) | rng.integers(0, 2 ** F, n),
+                  (py << F) | rng.integers(0, 2 ** F, n)], 1).astype(np.uint32)
+    s = np.array([3e-9, 2e-9])
+    return z, s
+
+
+def test_bh_theta0_one_point_per_pixel_is_exact():
+    L = 9
+    z, s = _unique_pixel_state(180, L, 14)
+    Fb, Zb, acc = oracle.bh_repulsion(z, s, L, 0.0)
+    Fe, Ze = oracle.exact_repulsion(z, s)
+    np.testing.assert_allclose(Fb, Fe, rtol=1e-12, atol=1e-14 * np.abs(Fe).max())
+    np.testing.assert_allclose(Zb, Ze, rtol=1e-12)
+    assert np.all(acc == 179)   # every other point is its own leaf
+
+
+def test_bh_theta0_equals_pixel_bruteforce():
+    L = 4
+    F = 32 - L
+    rng = np.random.default_rng(15)
+    n = 240
+    centres = rng.integers(2, 14, (12, 2))
+    pix = centres[rng.integers(0, 12, n)] + rng.integers(-2, 3, (n, 2))
+    z = ((pix.astype(np.int64) << F) + rng.integers(0, 2 ** F, (n, 2))).astype(np.uint32)
+    z[5] = z[6]               # an exact duplicate
+    s = np.array([1.1e-9, 0.7e-9])
+    Fb, Zb, _ = oracle.bh_repulsion(z, s, L, 0.0)
+    # tree-free brute force: every other pixel's centre of mass with weight N,
+    # the own pixel without i
+    key = (z[:, 0] >> F).astype(np.int64) * 4096 + (z[:, 1] >> F)
+    groups = {}
+    for i, kk in enumerate(key):
+        groups.setdefault(int(kk), []).append(i)
+    Fr = np.zeros((n, 2))
+    Zr = np.zeros(n)
+    for i in range(n):
+        for kk, members in groups.items():
+            mem = [j for j in members if j != i]
+            if not mem:
+                continue
+            N = len(mem)
+            cx = sum(int(z[j, 0]) for j in mem) / N
+            cy = sum(int(z[j, 1]) for j in mem) / N
+            dx = s[0] * (int(z[i, 0]) - cx)
+            dy = s[1] * (int(z[i, 1]) - cy)
+            w = 1.0 / (1.0 + dx * dx + dy * dy)
+            Zr[i] += N * w
+            Fr[i] += N * w * w * np.array([dx, dy])
+    np.testing.assert_allclose(Fb, Fr, rtol=1e-9, atol=1e-12 * np.abs(Fr).max())
+    np.testing.assert_allclose(Zb, Zr, rtol=1e-12)
+
+
+def test_bh_theta_half_close_to_exact():
+    rng = np.random.default_rng(16)
+    L = 9
+    Y = np.concatenate([rng.standard_normal((400, 2)) * 2 + c for c in ([0, 0], [15, 3], [-6, 12])])
+    z, s = oracle.init_fx(Y)
+    Fe, Ze = oracle.exact_repulsion(z, s)
+    errs = []
+    for th in (0.8, 0.5, 0.25):
+        Fb, Zb, acc = oracle.bh_repulsion(z, s, L, th)
+        errs.append(np.linalg.norm(Fb - Fe) / np.linalg.norm(Fe))
+        assert abs(Zb.sum() - Ze.sum()) / Ze.sum() < 0.02
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[1] < 0.05
+    # the geometric-centre variant (Sec. 4.1's printed approximation) is coarser
+    Fg, _, _ = oracle.bh_repulsion(z, s, L, 0.5, centre_mode=1)
+    assert np.linalg.norm(Fg - Fe) / np.linalg.norm(Fe) < 0.5
+
+
+# ------------------------------------------------------------------ update / rescale
+def test_rescale_big_integer_arithmetic():
+    rng = np.random.default_rng(17)
+    n = 500
+    zhat = np.stack([rng.integers(-2 ** 34, 2 ** 35, n), rng.integers(-7, 2 ** 20, n)], 1)
+    s = np.array([1e-9, 3e-8])
+    z, s2 = oracle.rescale(zhat, s)
+    for d in range(2):
+        mn, mx = int(zhat[:, d].min()), int(zhat[:, d].max())
+        gamma = mx - mn + 1
+        ref = [((int(v) - mn) << 32) // gamma for v in zhat[:, d]]
+        assert [int(v) for v in z[:, d]] == ref
+        assert s2[d] == s[d] * (gamma / 2 ** 32)
+    for L in (9, 11):  # Sec. 4.2: pixel coordinates span exactly 0 .. r-1
+        F = 32 - L
+        for d in range(2):
+            assert (z[:, d] >> F).min() == 0 and (z[:, d] >> F).max() == 2 ** L - 1
+
+
+def test_update_rule_cases():
+    # g = 4 (alpha Fattr - Frep / Z); gains compare sign(g) with sign(u), sign(0) = 0
+    z = np.array([[1000, 1000]] * 4, np.uint32)
+    s = np.array([0.5, 0.25])
+    Fattr = np.array([[1.0, -1.0], [1.0, -1.0], [0.0, 0.0], [1.0, 1.0]])
+    Frep = np.zeros((4, 2))
+    u = np.array([[0.0, 0.0], [2.0, 2.0], [1.0, -1.0], [-3.0, 5.0]])
+    gains = np.array([[1.0, 1.0], [1.0, 1.0], [0.011, 1.0], [1.0, 1.0]])
+    zhat, g = oracle.update(z, s, Fattr, Frep, 1.0, 2.0, 0.5, 10.0, u, gains)
+    np.testing.assert_array_equal(g, [[8, -8], [8, -8], [0, 0], [8, 8]])
+    # u = 0: always different sign -> +0.2; same sign -> *0.8; g = 0 vs u != 0 -> +0.2
+    np.testing.assert_allclose(gains, [[1.2, 1.2], [0.8, 1.2], [0.211, 1.2], [1.2, 0.8]])
+    np.testing.assert_allclose(u[0], [-96.0, 96.0])
+    assert zhat[0, 0] == 1000 + round(-96.0 / 0.5) and zhat[0, 1] == 1000 + round(96 / 0.25)
+    # min gain clamp
+    gains2 = np.array([[0.01, 0.01]])
+    u2 = np.array([[1.0, 1.0]])
+    oracle.update(z[:1], s, np.array([[1.0, 1.0]]), np.zeros((1, 2)), 1.0, 1.0, 0.5, 1.0,
+                  u2, gains2, min_gain=0.01)
+    np.testing.assert_allclose(gains2, [[0.01, 0.01]])
+
+
+def test_fixed_point_run_equals_y_space_tsne():
+    """Sec. 4.2: with the rescale compensated (Eq. q_wrt_z, Eq. beta_scaling), each
+    PixelSNE step is a plain t-SNE step in y-space (scikit-learn's exact
+    gradient) up to translation and the 2^-32 quantisation of the screen.
+    Checked step by step along a 20-step trajectory; the free-running
+    trajectories separate only at the chaotic rate of the dynamics."""
+    tsne = pytest.importorskip("sklearn.manifold._t_sne")
+    from scipy.spatial.distance import squareform
+    n = 50
+    rng = np.random.default_rng(18)
+    X = np.concatenate([rng.standard_normal((25, 4)), rng.standard_normal((25, 4)) + 4])
+    idx, d2 = oracle.knn(X.astype(np.float32), 15)
+    p, _, _, _ = oracle.perplexity(d2, 5.0)
+    P = oracle.symmetrize(idx, p)
+    Pc = squareform(P.dense(), checks=False)
+    Y0 = rng.standard_normal((n, 2)) * 1e-2
+    params = oracle.Params(L=9, exact=1, exag=4.0, exag_iters=10, mom_switch=10,
+                           eta=50.0)
+    st = oracle.State.from_y0(Y0)
+    for t in range(20):
+        y, u, gains = st.y(), st.u.copy(), st.gains.copy()
+        alpha = params.exag if t < params.exag_iters else 1.0
+        mu = params.mom0 if t < params.mom_switch else params.mom1
+        _, g = tsne._kl_divergence(y.ravel(), alpha * Pc, 1, n, 2)
+        g = g.reshape(n, 2)
+        gains = np.where(np.sign(g) != np.sign(u), gains + 0.2, gains * 0.8)
+        gains = np.maximum(gains, params.min_gain)
+        u = mu * u - params.eta * gains * g
+        y = y + u
+        s_old = st.s.copy()
+        oracle.run(P, st, params, 1)
+        np.testing.assert_allclose(st.u, u, rtol=1e-9, atol=1e-12 * np.abs(u).max())
+        np.testing.assert_array_equal(st.gains, gains)
+        a = st.y() - st.y().mean(0)
+        b = y - y.mean(0)
+        # half an old ulp from rint(u/s) plus one new ulp from the floor
+        tol = 0.5 * s_old + st.s + 1e-12 * np.abs(b).max()
+        assert np.all(np.abs(a - b).max(0) <= 2 * tol)
+
+
+def test_run_lowers_kl_and_keeps_screen():
+    import datagen
+    X, _ = datagen.gauss10(0, n=600)
+    P, _, _, bad = oracle.affinities(X, 30, 90)
+    assert bad == 0
+    st = oracle.State.from_y0(datagen.init_y0(0, 600))
+    params = oracle.Params(L=9)
+    kl0 = oracle.kl_of(P, st, params)
+    oracle.run(P, st, params, 300)
+    kl1 = oracle.kl_of(P, st, params)
+    assert 0 < kl1 < kl0
+    F = 32 - 9
+    for d in range(2):
+        assert (st.z[:, d] >> F).min() == 0 and (st.z[:, d] >> F).max() == 511
+
+
+# ------------------------------------------------------------------ quality metric
+def test_nbr_precision_identity_cases():
+    rng = np.random.default_rng(19)
+    n, k = 300, 10
+    Y = rng.standard_normal((n, 2))
+    z, s = oracle.init_fx(Y)
+    idx, _ = oracle.knn((z.astype(np.float64) * s).astype(np.float32), k)
+    # high-D neighbours computed on the same geometry: precision ~ 1 (ties and
+    # the fp32 copy may swap a few boundary neighbours)
+    assert oracle.nbr_precision(idx, k, z, s) > 0.97
+    # unrelated geometry: precision ~ k / n
+    z2, s2 = oracle.init_fx(rng.standard_normal((n, 2)))
+    assert oracle.nbr_precision(idx, k, z2, s2) < 0.15
