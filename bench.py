@@ -1,0 +1,387 @@
+"""PixelSNE iterations/s on one GB300 (n = 1,000,000, D = 128, 2048^2 screen).
+
+Workload ``gmm128``: 100-component anisotropic Gaussian mixture with Zipf(1.1)
+sizes, k = 90 neighbours, perplexity 30, theta 0.5, 2^11 x 2^11 screen.
+A step is one gradient iteration of the method (tree, Barnes-Hut repulsion,
+attraction, Z, update with screen rescale).  P is built once before timing
+(its time is reported separately, like the paper's P / Coord split).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Timed region: K iterations from t = 0 of the schedule
+(exaggeration 12 for 250 iterations), CUDA events on the library's stream,
+barrier + synchronize on both sides, max over ranks.  Every iteration streams
+P (about 1 GB), so the inputs exceed the 129 MB L2.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="gmm128", n=1_000_000, D=128, k=90, perplexity=30.0, log2_r=11,
+                theta=0.5, iterations=1000)
+METRIC = "t-SNE iterations/sec at n=1M, 2048^2 screen"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="points (debug only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=40000,
+                    help="rows of the oracle sample (CPU baseline)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- workload
+def make_inputs(n, seed=0):
+    import datagen
+    X, _ = datagen.gmm128(seed=seed, n=n)
+    Y0 = datagen.init_y0(seed, n)
+    return X, Y0
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# Algorithmic bytes (HBM) per launch of each kernel group, and FLOPs of the
+# traversal per tested / accepted (point, cell) pair.
+def group_bytes(n, nnz, L):
+    leaves = 4 ** L
+    cells = (4 ** (L + 1) - 1) // 3
+    return {
+        "k_update": n * (8 + 8 + 8 + 8 + 8 + 8 + 8 + 16),      # z,Frep,Fattr,u,gains r; u,gains w; zhat w
+        "k_snap_hist": leaves * 20 + n * (4 + 16 + 8 + 4),     # memset; perm,zhat r; z,rank w
+        "k_pyr_pass": leaves * (20 + 4) + cells * 16,          # leaf sums r, leaf_start w, records w
+        "k_perm_scatter": n * (8 + 4 + 4 + 4),
+        "k_bh_traverse": n * (4 + 8 + 8 + 4) + cells * 16,
+        "k_attract": nnz * 8 + (n + 1) * 8 + n * (8 + 8),
+        "k_zsum": n * 4,
+    }
+
+
+FLOP_TEST = 10    # offset, d^2 and criterion of one tested cell
+FLOP_ACCEPT = 10  # kernel value, N w, N w^2 and the three accumulations
+
+
+def oracle_sample(_unused, Y0, rows, L, theta, seed=0):
+    """Time the oracle's iteration on a bounded sample: the full tree, the BH
+    repulsion and attraction of `rows` sampled points, the full update and
+    rescale; scaled to one full iteration.  Returns (it/s, details)."""
+    import oracle
+    n = Y0.shape[0]
+    rng = np.random.default_rng(seed + 99)
+    st = oracle.State.from_y0(Y0)
+    sample = np.sort(rng.choice(n, size=min(rows, n), replace=False)).astype(np.int64)
+    m = sample.shape[0]
+    # a P of the workload's shape for the sampled rows only: 90 neighbours + 45
+    # reverse edges per row, uniform columns, values 1/(2 n 90)
+    per = 135
+    rp = np.zeros(n + 1, np.int64)
+    cnt = np.zeros(n, np.int64)
+    cnt[sample] = per
+    rp[1:] = np.cumsum(cnt)
+    col = rng.integers(0, n, size=m * per).astype(np.int32)
+    val = np.full(m * per, 1.0 / (2 * n * 90))
+    P = oracle.CSR(rp, col, val)
+    t0 = time.perf_counter()
+    tree = oracle.pyramid(st.z, L)
+    t1 = time.perf_counter()
+    Frep, Zi, _ = oracle.bh_repulsion(st.z, st.s, L, theta, rows=sample, tree=tree)
+    t2 = time.perf_counter()
+    Fattr = oracle.attraction(P, st.z, st.s, rows=sample)
+    t3 = time.perf_counter()
+    Fr = np.zeros((n, 2))
+    Fa = np.zeros((n, 2))
+    Fr[sample] = Frep
+    Fa[sample] = Fattr
+    zhat, _ = oracle.update(st.z, st.s, Fa, Fr, max(Zi.sum() * n / m, 1.0), 12.0, 0.5, 200.0,
+                            st.u, st.gains)
+    oracle.rescale(zhat, st.s)
+    t4 = time.perf_counter()
+    scale = n / m
+    per_iter = (t1 - t0) + (t2 - t1) * scale + (t3 - t2) * scale + (t4 - t3)
+    det = {"tree_s": t1 - t0, "bh_sample_s": t2 - t1, "attr_sample_s": t3 - t2,
+           "update_rescale_s": t4 - t3, "rows": m, "scale": scale}
+    return 1.0 / per_iter, det, (t4 - t0)
+
+
+def run_reference(args):
+    """The oracle (plain FP64 C, OpenMP) as the reference arm."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    import datagen
+    n = args.n
+    Y0 = datagen.init_y0(0, n)
+    L = WORKLOAD["log2_r"]
+    vals = []
+    for _ in range(max(args.warmup, 0)):
+        oracle_sample(None, Y0, max(1000, args.cpu_rows // 8), L, WORKLOAD["theta"])
+    wall = 0.0
+    for k in range(max(args.steps, 1)):
+        v, det, w = oracle_sample(None, Y0, max(1000, args.cpu_rows // 8), L,
+                                  WORKLOAD["theta"], seed=k)
+        vals.append(v)
+        wall += w
+        if wall > 120.0:
+            break
+    value = float(np.mean(vals))
+    cores = oracle.num_threads()
+    sample = (f"first iteration from Y0 at n={n}: full tree + BH/attraction of "
+              f"{det['rows']} sampled rows scaled by {det['scale']:.1f} + full update/rescale, "
+              f"{len(vals)} repetitions")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "it/s",
+            "n_gpus": args.gpus, "steps": len(vals), "warmup": args.warmup,
+            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {k: WORKLOAD[k] for k in WORKLOAD} | {"n": n},
+            "cpu_baseline": {"value": value, "unit": "it/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "it/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1611_02568_gb300 as px
+    from paper_1611_02568_gb300 import build as pxbuild
+    if rank == 0 or ws == 1:
+        pxbuild.build()
+    if dist:
+        dist.barrier()
+
+    n = args.n
+    W = WORKLOAD
+    X, Y0 = make_inputs(n, seed=rank)
+    stream = torch.cuda.Stream()
+    params = px.Params(log2_r=W["log2_r"], theta=W["theta"], k=W["k"],
+                       perplexity=W["perplexity"])
+    ctx = px.Context(params, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.affinities(X)
+    p_seconds = time.perf_counter() - t0
+    n_, nnz = ctx.sizes()
+    ctx.init(Y0)
+    ctx.step(max(args.warmup, 3) if args.warmup >= 0 else 3)  # graph capture + warm-up
+    ctx.sync()
+    ctx.init(Y0)                                              # timed run starts at t = 0
+    ctx.sync()
+
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ctx.sync()
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * args.steps / (ms / 1000.0)
+    kl_after = ctx.kl()
+
+    # per-kernel breakdown: the same K iterations again from t = 0, with CUDA
+    # events around each kernel group on the library's stream
+    ctx.init(Y0)
+    groups, prof_total = ctx.step_profiled(args.steps)
+    acc, tst = ctx.counters()
+    peaks, peak_kind = measured_peaks()
+    gb = group_bytes(n, nnz, W["log2_r"])
+    top = max(groups, key=groups.get)
+    avg_ms = {g: v / args.steps for g, v in groups.items()}
+    sm_mhz = ck["sm_mhz"] if ck else 1477.0
+    alu_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    if top == "k_bh_traverse":
+        # work of the last traversal (final state) as the per-launch estimate
+        flops = FLOP_TEST * tst + FLOP_ACCEPT * acc
+        achieved = flops / (avg_ms[top] / 1e3) / 1e12
+        roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": alu_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak_tflops, "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median "
+                               "SM clock of this run)"}
+    else:
+        achieved = gb[top] / (avg_ms[top] / 1e3) / 1e9
+        roof = {"kernel": top, "bound": "hbm", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_kind})"}
+    kernels = {g: {"ms_per_launch": avg_ms[g], "share": groups[g] / sum(groups.values()),
+                   "alg_GBps": gb[g] / (avg_ms[g] / 1e3) / 1e9 if avg_ms[g] > 0 else None}
+               for g in groups}
+
+    # end to end through the public API with host buffers: P from pinned host
+    # X, init from host Y0, then every iteration pxsne_step(1) + pxsne_get_Y to
+    # pinned host memory (the frame a screen would draw)
+    e2e = None
+    if not args.no_e2e:
+        Xp = torch.from_numpy(X).pin_memory()
+        Y0p = torch.from_numpy(Y0).pin_memory()
+        Yh = torch.empty((n, 2), dtype=torch.float32).pin_memory()
+        Ph = torch.empty((n, 2), dtype=torch.int32).pin_memory()
+        ctx2 = px.Context(params, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        ctx2.affinities(Xp)
+        ctx2.init(Y0p)
+        for _ in range(args.steps):
+            ctx2.step(1)
+            ctx2.get_Y(Yh, Ph)
+        t1 = time.perf_counter()
+        el = t1 - t0
+        if dist:
+            t = torch.tensor([el], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        ctx2.close()
+        e2e = {"value": ws * args.steps / el, "unit": "it/s",
+               "h2d_bytes_per_step": int((X.nbytes + Y0.nbytes) / args.steps),
+               "d2h_bytes_per_step": int(Yh.numel() * 4 + Ph.numel() * 4),
+               "wall_s": el, "includes": "P construction + init + K x (step + get_Y)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        v, det, w = oracle_sample(X.shape, Y0, args.cpu_rows, W["log2_r"], W["theta"])
+        cpu = {"value": v, "unit": "it/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": (f"first iteration from Y0: full tree + BH/attraction of "
+                          f"{det['rows']} of {n} rows scaled by {det['scale']:.1f} + full "
+                          f"update/rescale ({w:.1f} s of CPU work)")}
+
+    ctx.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {k: W[k] for k in W} | {"n": n, "nnz": nnz,
+                                              "parallelism": "replicas" if ws > 1 else "single",
+                                              "l2": "inputs larger than L2 (P ~1 GB/iter)",
+                                              "timed_iterations": f"t = 0..{args.steps - 1}"},
+            "roofline": roof, "kernels": kernels,
+            "traversal": {"accepted_pairs": acc, "tested_pairs": tst,
+                          "accepted_per_point": acc / n, "tested_per_point": tst / n},
+            "profiled_total_ms": prof_total, "p_construction_s": p_seconds,
+            "kl_after_timed": kl_after,
+            "clocks": ck, "e2e": e2e, "cpu_baseline": cpu,
+            # per iteration: update, snap_hist, ceil(L/5) pyramid passes, scan,
+            # perm_scatter, traverse, attract, zsum
+            "gpu_launches": args.steps * (7 + (W["log2_r"] + 4) // 5),
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

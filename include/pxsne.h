@@ -1,0 +1,213 @@
+/*
+ * pxsne.h - C ABI of the GB300 (sm_103a) PixelSNE library.
+ *
+ * PixelSNE (Kim et al., arXiv 1611.02568) is t-SNE whose 2-D output lives on a
+ * screen of r x r pixels (Sec. 3.1, Eq. z1/z2).  Each gradient iteration
+ * assigns the points to a fixed pixel-aligned quadtree (Sec. 4.1), takes the
+ * Barnes-Hut repulsion against it (Sec. 3.3, Eq. bh_criteria), the attraction
+ * over the sparse affinity matrix P (Sec. 3.3, Eq. grad) and a gradient step
+ * followed by the screen-driven rescale (Sec. 4.2).  This library runs all of
+ * it in hand-written CUDA kernels on one GPU.
+ *
+ * Conventions shared by every call:
+ *  - Return value: PXSNE_OK (0) or a negative PXSNE_E_* code; the message of the
+ *    last failure is available from pxsne_last_error().  No C++ exception
+ *    crosses this boundary.
+ *  - Device work is enqueued on the context's CUDA stream.  Calls that return
+ *    data to the host synchronise that stream; errors raised on the device
+ *    (non-finite gradient, traversal stack overflow) are reported by the next
+ *    synchronising call as PXSNE_E_DEVICE.
+ *  - Pointers marked "host or device" are read as device pointers when the
+ *    matching *_on_device flag is non-zero (they must then be device memory of
+ *    the context's device, ordered before the call on the context's stream or
+ *    already complete); otherwise as host memory.
+ *  - The caller owns every buffer it passes; the library copies what it needs
+ *    and keeps no pointer to caller memory after a call returns.  The library
+ *    owns, and frees in pxsne_destroy(), all device memory it allocates.
+ *  - One context may be used by one host thread at a time.
+ *
+ * Positions.  The state holds each point as unsigned 32-bit fixed point per
+ * axis: z_d in [0, 2^32) ulps, pixel = z_d >> (32 - L) for a 2^L x 2^L screen.
+ * t-SNE's own coordinates are y_d = s_d * z_d (+ an arbitrary offset), where the
+ * per-axis scale s_d (y-units per ulp) carries the compensation of
+ * Eq. beta_scaling (s_d^2 = beta_d).
+ */
+#ifndef PXSNE_H
+#define PXSNE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PXSNE_OK 0
+#define PXSNE_E_ARG (-1)         /* invalid argument */
+#define PXSNE_E_OOM (-2)         /* device or host allocation failed */
+#define PXSNE_E_CUDA (-3)        /* a CUDA runtime call failed */
+#define PXSNE_E_STATE (-4)       /* call out of order (e.g. step before init) */
+#define PXSNE_E_DEVICE (-5)      /* error flagged by a kernel */
+#define PXSNE_E_UNSUPPORTED (-6) /* valid request this build does not support */
+
+/* Device error flags (pxsne_device_errors). */
+#define PXSNE_DEVERR_NONFINITE 1u   /* non-finite gradient or step */
+#define PXSNE_DEVERR_STACK 2u       /* BH traversal stack overflow */
+#define PXSNE_DEVERR_BISECT 4u      /* a perplexity row did not converge */
+#define PXSNE_DEVERR_RANGE 8u       /* step clamped: |u / s| beyond 2^60 ulps */
+
+typedef struct pxsne_ctx pxsne_ctx;
+
+/* Parameters of one embedding.  Defaults (pxsne_default_params): L = 11,
+ * theta = 0.5, eta = 200, exaggeration 12 for 250 iterations, momentum 0.5
+ * then 0.8 from iteration 250, min_gain 0.01, k = 90, perplexity 30,
+ * init_sigma 1e-4, centre of mass. */
+typedef struct pxsne_params {
+    int32_t log2_r;          /* L: screen is 2^L x 2^L pixels, 1 <= L <= 14 (Sec. 4.1 depth) */
+    float theta;             /* Barnes-Hut threshold, >= 0 (Eq. bh_criteria) */
+    float eta;               /* learning rate (y-units) */
+    float exaggeration;      /* factor on P in the attraction while t < exag_iters */
+    int32_t exag_iters;
+    float momentum0;         /* momentum while t < momentum_switch */
+    float momentum1;         /* momentum from then on */
+    int32_t momentum_switch;
+    float min_gain;          /* lower bound of the per-coordinate gains */
+    int32_t k;               /* neighbours per row of P; >= 1 and < n */
+    float perplexity;        /* target perplexity u of each row, 0 < u <= k */
+    float init_sigma;        /* std-dev of the random initial embedding */
+    int32_t centre_mode;     /* 0: cell centre of mass; 1: geometric cell centre (Sec. 4.1) */
+} pxsne_params;
+
+void pxsne_default_params(pxsne_params *p);
+
+/* Create a context on the current CUDA device.  p is copied.  stream: a
+ * cudaStream_t to enqueue on, or NULL to let the library create its own
+ * non-blocking stream.  Fails with PXSNE_E_ARG on out-of-range parameters. */
+int pxsne_create(pxsne_ctx **out, const pxsne_params *p, void *stream);
+
+/* Free all device memory and the context.  NULL is ignored. */
+void pxsne_destroy(pxsne_ctx *ctx);
+
+/* Message of the last failure on ctx (or of the last failed pxsne_create when
+ * ctx is NULL).  Valid until the next call on the same context. */
+const char *pxsne_last_error(const pxsne_ctx *ctx);
+
+/* Build the sparse affinity matrix P (Sec. 3.2-3.3; Sec. 4.3 replaces the
+ * neighbour search, here done exactly by brute force):
+ *   - the k nearest neighbours of each row of X by squared Euclidean
+ *     distance, self excluded, ties to the lower index;
+ *   - p_{j|i} proportional to exp(-beta_i d2_ij) with beta_i set by bisection
+ *     so that each row's entropy is ln(perplexity);
+ *   - p_ij = (p_{j|i} + p_{i|j}) / (2n) on the union pattern, stored as CSR.
+ * X: host or device, row-major n x D float32.  perplexity <= 0 uses the
+ * context's parameter.  Replaces any previous P and clears the embedding
+ * state.  Synchronises.  Row convergence failures set PXSNE_DEVERR_BISECT and
+ * return PXSNE_E_DEVICE (P is still built from the last bracket). */
+int pxsne_affinities(pxsne_ctx *ctx, const float *X, int64_t n, int32_t D,
+                     float perplexity, int x_on_device);
+
+/* Start an embedding (Sec. 3.1, Eq. z1/z2): Y0 (host or device, n x 2 float32,
+ * y-units) is mapped per axis onto the fixed-point screen,
+ *   z_d = min(2^32 - 1, floor((y_d - min_d) * 2^32 / (max_d - min_d))),
+ *   s_d = (max_d - min_d) / 2^32,
+ * in FP64 (an axis with zero extent maps to z_d = 0, s_d = 2^-32).  Y0 == NULL
+ * draws Y0 ~ N(0, init_sigma^2 I) from `seed` with Philox4x32-10 (Salmon et al.
+ * 2011) and the Box-Muller transform.  Velocities are zeroed, gains set to 1,
+ * the iteration counter to 0, and the forces of the initial state computed.
+ * Requires P (pxsne_affinities or pxsne_set_P). */
+int pxsne_init(pxsne_ctx *ctx, const float *Y0, int y_on_device, uint64_t seed);
+
+/* Run `iters` >= 0 gradient iterations, asynchronously on the context's
+ * stream.  Iteration t: g = 4 (alpha_t Fattr - Frep / Z) (Eq. grad), the
+ * gains/momentum step u = mu_t u - eta gain g, zhat = z + rint(u / s), then the
+ * screen-driven rescale z_d = floor((zhat_d - min_d) 2^32 / (max_d - min_d + 1)),
+ * s_d <- s_d (max_d - min_d + 1) / 2^32 (Sec. 4.2), then the pixel-aligned tree
+ * and forces of the new state (Sec. 4.1, Eq. bh_criteria, Eq. grad).
+ * Returns enqueue errors only. */
+int pxsne_step(pxsne_ctx *ctx, int32_t iters);
+
+/* KL divergence of the current state (Eq. cost_func) in FP64, with Z the
+ * Barnes-Hut normalisation of the current tree and the un-exaggerated P.
+ * Synchronises. */
+int pxsne_kl(pxsne_ctx *ctx, double *out);
+
+/* Current embedding.  Y (host or device, n x 2 float32, may be NULL) gets
+ * y = s * z minus the per-axis mean (t-SNE coordinates, centred); pix (host or
+ * device, n x 2 int32, may be NULL) gets the pixel coordinates z >> (32 - L).
+ * Synchronises. */
+int pxsne_get_Y(pxsne_ctx *ctx, float *Y, int32_t *pix, int on_device);
+
+/* Wait for the context's stream; returns PXSNE_E_DEVICE if a kernel flagged
+ * an error since the last check (flags in *dev_errors when non-NULL). */
+int pxsne_sync(pxsne_ctx *ctx, uint32_t *dev_errors);
+
+/* ------------------------------------------------------------------------
+ * Inspection and injection (host buffers; all synchronise).  They expose the
+ * internal state at the boundary so that each step can be compared with an
+ * independent implementation.
+ * ------------------------------------------------------------------------ */
+
+/* Number of points and non-zeros of P (0 before affinities). */
+int pxsne_get_sizes(pxsne_ctx *ctx, int64_t *n, int64_t *nnz);
+
+/* P as CSR with columns ascending per row: row_ptr[n+1] int64, col[nnz]
+ * int32, val[nnz] float32.  Any pointer may be NULL. */
+int pxsne_get_P(pxsne_ctx *ctx, int64_t *row_ptr, int32_t *col, float *val);
+
+/* Replace P by a caller CSR (row_ptr[n+1] int64, col int32 in [0, n), no
+ * self entries; val float32 >= 0).  Clears the embedding state. */
+int pxsne_set_P(pxsne_ctx *ctx, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                const float *val);
+
+/* The neighbour lists of the last pxsne_affinities: idx[n*k] int32 and
+ * d2[n*k] float32 (FP32 squared distances), ascending per row; beta[n]
+ * float32 (the bisection result).  Any pointer may be NULL. */
+int pxsne_get_knn(pxsne_ctx *ctx, int32_t *idx, float *d2, float *beta);
+
+/* Overwrite the embedding state: z[n*2] u32 fixed point, s[2] y-units per
+ * ulp, u[n*2] velocities (y-units, NULL = 0), gains[n*2] (NULL = 1), and the
+ * iteration counter t; then build the tree and forces of that state. */
+int pxsne_set_state(pxsne_ctx *ctx, const uint32_t *z, const double *s, const float *u,
+                    const float *gains, int32_t t);
+
+/* Read the embedding state (any pointer may be NULL). */
+int pxsne_get_state(pxsne_ctx *ctx, uint32_t *z, double *s, float *u, float *gains,
+                    int32_t *t);
+
+/* The tree of the current state at one level l (0 = root .. L = pixels), in
+ * Morton order (x bits at even positions): cnt[4^l] u32 cell counts N_c and,
+ * for l = L only, sx/sy[4^l] u64 exact sums of the fixed-point coordinates of
+ * the points in each pixel (NULL to skip).  Pixel Morton keys per point go to
+ * morton[n] when non-NULL. */
+int pxsne_get_tree(pxsne_ctx *ctx, int32_t level, uint32_t *cnt, uint64_t *sx,
+                   uint64_t *sy, uint32_t *morton);
+
+/* Forces of the current state: Frep[n*2] = sum over accepted cells of
+ * N w^2 (y_i - y_c) (un-normalised), Zi[n] = sum of N w, Fattr[n*2] =
+ * sum_j p_ij w_ij (y_i - y_j) (un-exaggerated), Z = sum_i Zi (FP64).  Any
+ * pointer may be NULL. */
+int pxsne_get_forces(pxsne_ctx *ctx, float *Frep, float *Zi, float *Fattr, double *Z);
+
+/* Tracing: run `iters` >= 1 iterations like pxsne_step, without the CUDA
+ * graph, with CUDA events recorded on the context's stream around each kernel
+ * group of an iteration (no synchronisation between iterations).  group_ms
+ * (n_groups >= 7 slots) receives the summed milliseconds of each group over
+ * all iterations and total_ms (may be NULL) the elapsed time of the whole
+ * run.  Group g is named by pxsne_kernel_group_name(g).  Synchronises. */
+int pxsne_step_profiled(pxsne_ctx *ctx, int32_t iters, double *group_ms, int32_t n_groups,
+                        double *total_ms);
+
+/* Name of kernel group g (0 <= g < 7), or NULL. */
+const char *pxsne_kernel_group_name(int32_t g);
+
+/* Work counters of the last Barnes-Hut traversal: n_accept = accepted
+ * (point, cell) pairs (the interactions of Eq. bh_criteria), n_test = tested
+ * pairs (accepted + opened + own-pixel).  Synchronises. */
+int pxsne_get_counters(pxsne_ctx *ctx, uint64_t *n_accept, uint64_t *n_test);
+
+/* Total bytes of device memory the context holds. */
+int64_t pxsne_device_bytes(const pxsne_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PXSNE_H */

@@ -1,0 +1,311 @@
+"""GB300-native PixelSNE (arXiv 1611.02568): Python binding of ``libpxsne.so``.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+behind the C ABI of ``include/pxsne.h``.  There is no CPU fallback; importing
+works without a GPU, but every call needs the compiled library and a CUDA
+device.
+
+Names follow the C ABI::
+
+    ctx = Context(Params(log2_r=11))
+    ctx.affinities(X)            # pxsne_affinities
+    ctx.init(Y0)                 # pxsne_init (Y0=None draws from the seed)
+    ctx.step(1000)               # pxsne_step
+    ctx.kl()                     # pxsne_kl
+    Y, pix = ctx.get_Y()         # pxsne_get_Y
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, fields
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+_lib = None
+
+PXSNE_OK = 0
+ERRORS = {-1: "E_ARG", -2: "E_OOM", -3: "E_CUDA", -4: "E_STATE", -5: "E_DEVICE",
+          -6: "E_UNSUPPORTED"}
+DEVERR = {1: "NONFINITE", 2: "STACK", 4: "BISECT", 8: "RANGE"}
+
+
+class PxsneError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pxsne {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _CParams(C.Structure):
+    _fields_ = [("log2_r", C.c_int32), ("theta", C.c_float), ("eta", C.c_float),
+                ("exaggeration", C.c_float), ("exag_iters", C.c_int32),
+                ("momentum0", C.c_float), ("momentum1", C.c_float),
+                ("momentum_switch", C.c_int32), ("min_gain", C.c_float), ("k", C.c_int32),
+                ("perplexity", C.c_float), ("init_sigma", C.c_float),
+                ("centre_mode", C.c_int32)]
+
+
+@dataclass
+class Params:
+    """Mirror of ``pxsne_params`` (defaults of ``pxsne_default_params``)."""
+    log2_r: int = 11
+    theta: float = 0.5
+    eta: float = 200.0
+    exaggeration: float = 12.0
+    exag_iters: int = 250
+    momentum0: float = 0.5
+    momentum1: float = 0.8
+    momentum_switch: int = 250
+    min_gain: float = 0.01
+    k: int = 90
+    perplexity: float = 30.0
+    init_sigma: float = 1e-4
+    centre_mode: int = 0
+
+    def c(self):
+        return _CParams(*[getattr(self, f.name) for f in fields(self)])
+
+
+def load(path: str | None = None):
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(p)
+    vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+    L.pxsne_default_params.argtypes = [C.POINTER(_CParams)]
+    L.pxsne_create.argtypes = [C.POINTER(vp), C.POINTER(_CParams), vp]
+    L.pxsne_destroy.argtypes = [vp]
+    L.pxsne_destroy.restype = None
+    L.pxsne_last_error.argtypes = [vp]
+    L.pxsne_last_error.restype = C.c_char_p
+    L.pxsne_affinities.argtypes = [vp, vp, i64, i32, C.c_float, C.c_int]
+    L.pxsne_init.argtypes = [vp, vp, C.c_int, u64]
+    L.pxsne_step.argtypes = [vp, i32]
+    L.pxsne_kl.argtypes = [vp, C.POINTER(C.c_double)]
+    L.pxsne_get_Y.argtypes = [vp, vp, vp, C.c_int]
+    L.pxsne_sync.argtypes = [vp, C.POINTER(C.c_uint32)]
+    L.pxsne_get_sizes.argtypes = [vp, C.POINTER(i64), C.POINTER(i64)]
+    L.pxsne_get_P.argtypes = [vp, vp, vp, vp]
+    L.pxsne_set_P.argtypes = [vp, i64, vp, vp, vp]
+    L.pxsne_get_knn.argtypes = [vp, vp, vp, vp]
+    L.pxsne_set_state.argtypes = [vp, vp, vp, vp, vp, i32]
+    L.pxsne_get_state.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.pxsne_get_tree.argtypes = [vp, i32, vp, vp, vp, vp]
+    L.pxsne_get_forces.argtypes = [vp, vp, vp, vp, vp]
+    L.pxsne_step_profiled.argtypes = [vp, i32, C.POINTER(C.c_double), i32,
+                                      C.POINTER(C.c_double)]
+    L.pxsne_kernel_group_name.argtypes = [i32]
+    L.pxsne_kernel_group_name.restype = C.c_char_p
+    L.pxsne_get_counters.argtypes = [vp, C.POINTER(u64), C.POINTER(u64)]
+    L.pxsne_device_bytes.argtypes = [vp]
+    L.pxsne_device_bytes.restype = i64
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or torch tensor (or None)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data, 0
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            assert a.is_contiguous()
+            if a.is_cuda:
+                torch.cuda.current_stream(a.device).synchronize()
+                return a.data_ptr(), 1
+            return a.data_ptr(), 0
+    except ImportError:
+        pass
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+class Context:
+    """One embedding problem on the current CUDA device (``pxsne_ctx``)."""
+
+    def __init__(self, params: Params | None = None, stream=None):
+        self.L = load()
+        self.params = params or Params()
+        self._p = self.params.c()
+        h = C.c_void_p()
+        rc = self.L.pxsne_create(C.byref(h), C.byref(self._p), stream)
+        if rc != PXSNE_OK:
+            raise PxsneError(rc, self.L.pxsne_last_error(None).decode())
+        self.h = h
+
+    def _ck(self, rc):
+        if rc != PXSNE_OK:
+            raise PxsneError(rc, self.L.pxsne_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.pxsne_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- the method
+    def affinities(self, X, perplexity: float = 0.0):
+        if isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X, dtype=np.float32)
+        n, D = X.shape
+        p, dev = _ptr(X)
+        self._ck(self.L.pxsne_affinities(self.h, p, n, D, float(perplexity), dev))
+
+    def init(self, Y0=None, seed: int = 0):
+        if isinstance(Y0, np.ndarray):
+            Y0 = np.ascontiguousarray(Y0, dtype=np.float32)
+        p, dev = _ptr(Y0)
+        self._ck(self.L.pxsne_init(self.h, p, dev, int(seed)))
+
+    def step(self, iters: int = 1):
+        self._ck(self.L.pxsne_step(self.h, int(iters)))
+
+    def kl(self) -> float:
+        out = C.c_double()
+        self._ck(self.L.pxsne_kl(self.h, C.byref(out)))
+        return out.value
+
+    def get_Y(self, Y=None, pix=None, want_pix=True):
+        """Centred y-space coordinates and pixels; fills Y/pix if given
+        (numpy, or CUDA tensors), else returns new numpy arrays."""
+        n = self.sizes()[0]
+        if Y is None and pix is None:
+            Y = np.empty((n, 2), np.float32)
+            pix = np.empty((n, 2), np.int32) if want_pix else None
+        py, dy = _ptr(Y)
+        pp, dp = _ptr(pix)
+        dev = dy or dp
+        self._ck(self.L.pxsne_get_Y(self.h, py, pp, dev))
+        return Y, pix
+
+    def sync(self):
+        f = C.c_uint32()
+        rc = self.L.pxsne_sync(self.h, C.byref(f))
+        self._ck(rc)
+        return f.value
+
+    # ---------------------------------------------------------------- inspection
+    def sizes(self):
+        n, nnz = C.c_int64(), C.c_int64()
+        self._ck(self.L.pxsne_get_sizes(self.h, C.byref(n), C.byref(nnz)))
+        return n.value, nnz.value
+
+    def get_P(self):
+        n, nnz = self.sizes()
+        rp = np.empty(n + 1, np.int64)
+        col = np.empty(nnz, np.int32)
+        val = np.empty(nnz, np.float32)
+        self._ck(self.L.pxsne_get_P(self.h, rp.ctypes.data, col.ctypes.data, val.ctypes.data))
+        return rp, col, val
+
+    def set_P(self, row_ptr, col, val):
+        row_ptr = np.ascontiguousarray(row_ptr, np.int64)
+        col = np.ascontiguousarray(col, np.int32)
+        val = np.ascontiguousarray(val, np.float32)
+        self._ck(self.L.pxsne_set_P(self.h, row_ptr.shape[0] - 1, row_ptr.ctypes.data,
+                                    col.ctypes.data, val.ctypes.data))
+
+    def get_knn(self):
+        n, _ = self.sizes()
+        k = self.params.k
+        idx = np.empty((n, k), np.int32)
+        d2 = np.empty((n, k), np.float32)
+        beta = np.empty(n, np.float32)
+        self._ck(self.L.pxsne_get_knn(self.h, idx.ctypes.data, d2.ctypes.data, beta.ctypes.data))
+        return idx, d2, beta
+
+    def set_state(self, z, s, u=None, gains=None, t=0):
+        z = np.ascontiguousarray(z, np.uint32)
+        s = np.ascontiguousarray(s, np.float64)
+        u = None if u is None else np.ascontiguousarray(u, np.float32)
+        gains = None if gains is None else np.ascontiguousarray(gains, np.float32)
+        self._ck(self.L.pxsne_set_state(self.h, z.ctypes.data, s.ctypes.data,
+                                        None if u is None else u.ctypes.data,
+                                        None if gains is None else gains.ctypes.data, int(t)))
+
+    def get_state(self):
+        n, _ = self.sizes()
+        z = np.empty((n, 2), np.uint32)
+        s = np.empty(2, np.float64)
+        u = np.empty((n, 2), np.float32)
+        g = np.empty((n, 2), np.float32)
+        t = C.c_int32()
+        self._ck(self.L.pxsne_get_state(self.h, z.ctypes.data, s.ctypes.data, u.ctypes.data,
+                                        g.ctypes.data, C.byref(t)))
+        return z, s, u, g, t.value
+
+    def get_tree(self, level, sums=False, morton=False):
+        n, _ = self.sizes()
+        cells = 4 ** level
+        cnt = np.empty(cells, np.uint32)
+        sx = np.empty(cells, np.uint64) if sums else None
+        sy = np.empty(cells, np.uint64) if sums else None
+        mk = np.empty(n, np.uint32) if morton else None
+        self._ck(self.L.pxsne_get_tree(self.h, int(level), cnt.ctypes.data,
+                                       None if sx is None else sx.ctypes.data,
+                                       None if sy is None else sy.ctypes.data,
+                                       None if mk is None else mk.ctypes.data))
+        return cnt, sx, sy, mk
+
+    def get_forces(self):
+        n, _ = self.sizes()
+        Frep = np.empty((n, 2), np.float32)
+        Zi = np.empty(n, np.float32)
+        Fattr = np.empty((n, 2), np.float32)
+        Z = C.c_double()
+        self._ck(self.L.pxsne_get_forces(self.h, Frep.ctypes.data, Zi.ctypes.data,
+                                         Fattr.ctypes.data, C.byref(Z)))
+        return Frep, Zi, Fattr, Z.value
+
+    def step_profiled(self, iters: int):
+        """Run iterations with CUDA events around each kernel group; returns
+        ({group name: summed ms}, total ms)."""
+        g = (C.c_double * 16)()
+        tot = C.c_double()
+        self._ck(self.L.pxsne_step_profiled(self.h, int(iters), g, 16, C.byref(tot)))
+        out = {}
+        for k in range(16):
+            name = self.L.pxsne_kernel_group_name(k)
+            if name is None:
+                break
+            out[name.decode()] = g[k]
+        return out, tot.value
+
+    def counters(self):
+        """(accepted, tested) (point, cell) pairs of the last traversal."""
+        a, t = C.c_uint64(), C.c_uint64()
+        self._ck(self.L.pxsne_get_counters(self.h, C.byref(a), C.byref(t)))
+        return a.value, t.value
+
+    def device_bytes(self):
+        return int(self.L.pxsne_device_bytes(self.h))
+
+
+EXPORTED = ["pxsne_default_params", "pxsne_create", "pxsne_destroy", "pxsne_last_error",
+            "pxsne_affinities", "pxsne_init", "pxsne_step", "pxsne_kl", "pxsne_get_Y",
+            "pxsne_sync", "pxsne_get_sizes", "pxsne_get_P", "pxsne_set_P", "pxsne_get_knn",
+            "pxsne_set_state", "pxsne_get_state", "pxsne_get_tree", "pxsne_get_forces",
+            "pxsne_device_bytes", "pxsne_step_profiled", "pxsne_kernel_group_name",
+            "pxsne_get_counters"]

@@ -1,0 +1,526 @@
+// Affinity matrix P of t-SNE (Sec. 3.2) on the sparse kNN pattern of Sec. 3.3.
+//
+//   k_knn_tile     brute-force k nearest neighbours: a 64 x 128 tile of
+//                  approximate squared distances |q|^2 + |c|^2 - 2 q.c (FP32
+//                  dot products) filters candidates against each row's current
+//                  k-th distance plus an error slack; survivors get their exact
+//                  FP32 sum of squared differences and enter a sorted list
+//                  (ties to the lower index)
+//   k_perplexity   per-row bisection on beta so that the entropy of
+//                  p_{j|i} ~ exp(-beta d2) is ln(perplexity), one warp per row
+//   symmetrize     p_ij = (p_{j|i} + p_{i|j}) / 2n on the union pattern, CSR
+#include <cmath>
+#include <cstdio>
+#include <string>
+
+#include "common.cuh"
+
+namespace pxsne {
+
+constexpr int kQR = 64;    // query rows per CTA
+constexpr int kCT = 128;   // candidates per tile
+constexpr int kKnnThreads = 256;
+
+__global__ void k_row_norms(int64_t n, int D, const float *__restrict__ X, float *__restrict__ nrm) {
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    float s = 0.f;
+    for (int d = lane; d < D; d += 32) {
+        const float v = X[row * D + d];
+        s = fmaf(v, v, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) nrm[row] = s;
+}
+
+// Exact FP32 squared distance between rows a and b, one warp, fixed order.
+__device__ __forceinline__ float warp_exact_d2(const float *__restrict__ X, int D, int64_t a,
+                                               int64_t b, int lane) {
+    float s = 0.f;
+    for (int d = lane; d < D; d += 32) {
+        const float t = X[a * D + d] - X[b * D + d];
+        s = fmaf(t, t, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Insert (d, j) into the ascending list (ld, lj) of length k held in shared
+// memory (entries with d = +inf are empty).  Whole warp.
+__device__ __forceinline__ void warp_list_insert(float *ld, int32_t *lj, int k, float d,
+                                                 int32_t j, int lane) {
+    // position = number of entries ordered before (d, j)
+    int pos = 0;
+    for (int b = 0; b < k; b += 32) {
+        const int e = b + lane;
+        bool before = false;
+        if (e < k) {
+            const float de = ld[e];
+            before = de < d || (de == d && lj[e] < j);
+        }
+        pos += __popc(__ballot_sync(0xffffffffu, before));
+    }
+    if (pos >= k) return;
+    // shift [pos, k-1) up by one, highest chunk first
+    for (int b = ((k - 1) / 32) * 32; b >= 0; b -= 32) {
+        const int e = b + lane;
+        float dv = 0.f;
+        int32_t jv = 0;
+        const bool mv = (e >= pos && e < k - 1);
+        if (mv) {
+            dv = ld[e];
+            jv = lj[e];
+        }
+        __syncwarp();
+        if (mv) {
+            ld[e + 1] = dv;
+            lj[e + 1] = jv;
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        ld[pos] = d;
+        lj[pos] = j;
+    }
+    __syncwarp();
+}
+
+// One CTA: kQR query rows against all n candidates, in tiles of kCT.
+// Dynamic shared memory: qs[D][kQR], cs[D][kCT] (transposed tiles), the
+// lists ld/lj[kQR][k], qn[kQR], the approximate distances ds[kQR][kCT] and
+// the candidate norms of each warp's tile [8][kCT].
+__global__ void __launch_bounds__(kKnnThreads)
+    k_knn_tile(int64_t n, int D, int k, const float *__restrict__ X,
+               const float *__restrict__ nrm, int32_t *__restrict__ out_idx,
+               float *__restrict__ out_d2) {
+    extern __shared__ float smem[];
+    float *qs = smem;                       // D * kQR
+    float *cs = qs + (size_t)D * kQR;       // D * kCT
+    float *ld = cs + (size_t)D * kCT;       // kQR * k
+    int32_t *lj = reinterpret_cast<int32_t *>(ld + (size_t)kQR * k);
+    float *qn = reinterpret_cast<float *>(lj + (size_t)kQR * k);
+    float *ds = qn + kQR;                   // kQR * kCT approximate distances
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int64_t q0 = (int64_t)blockIdx.x * kQR;
+    for (int e = tid; e < kQR * k; e += kKnnThreads) {
+        ld[e] = INFINITY;
+        lj[e] = 0x7fffffff;
+    }
+    for (int e = tid; e < D * kQR; e += kKnnThreads) {
+        const int d = e / kQR, q = e % kQR;
+        qs[e] = (q0 + q < n) ? X[(q0 + q) * D + d] : 0.f;
+    }
+    if (tid < kQR) qn[tid] = (q0 + tid < n) ? nrm[q0 + tid] : 0.f;
+    // approximate-distance error bound: rounding of a length-D dot product
+    const float slack_rel = 4.0f * (float)(D + 4) * 5.9604645e-8f;
+    for (int64_t c0 = 0; c0 < n; c0 += kCT) {
+        __syncthreads();
+        if ((D & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+            // 16-byte loads along a row; consecutive threads take consecutive
+            // rows so the transposed shared-memory writes do not conflict
+            for (int e = tid; e < (D >> 2) * kCT; e += kKnnThreads) {
+                const int c = e % kCT, d4 = e / kCT;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (c0 + c < n) v = *reinterpret_cast<const float4 *>(X + (c0 + c) * D + 4 * d4);
+                cs[(4 * d4 + 0) * kCT + c] = v.x;
+                cs[(4 * d4 + 1) * kCT + c] = v.y;
+                cs[(4 * d4 + 2) * kCT + c] = v.z;
+                cs[(4 * d4 + 3) * kCT + c] = v.w;
+            }
+        } else {
+            for (int e = tid; e < D * kCT; e += kKnnThreads) {
+                const int c = e % kCT, d = e / kCT;
+                cs[e] = (c0 + c < n) ? X[(c0 + c) * D + d] : 0.f;
+            }
+        }
+        __syncthreads();
+        // 8 queries (warp w) x 4 candidates (4 * lane .. +3) per thread
+        float acc[8][4];
+#pragma unroll
+        for (int a = 0; a < 8; a++)
+#pragma unroll
+            for (int b = 0; b < 4; b++) acc[a][b] = 0.f;
+        for (int d = 0; d < D; d++) {
+            const float4 qa = *reinterpret_cast<const float4 *>(qs + d * kQR + 8 * w);
+            const float4 qb = *reinterpret_cast<const float4 *>(qs + d * kQR + 8 * w + 4);
+            const float4 cv = *reinterpret_cast<const float4 *>(cs + d * kCT + 4 * lane);
+            const float qv[8] = {qa.x, qa.y, qa.z, qa.w, qb.x, qb.y, qb.z, qb.w};
+            const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+            for (int a = 0; a < 8; a++)
+#pragma unroll
+                for (int b = 0; b < 4; b++) acc[a][b] = fmaf(qv[a], cc[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const int64_t j = c0 + 4 * lane + b;
+            const float cn = j < n ? nrm[j] : 0.f;
+#pragma unroll
+            for (int a = 0; a < 8; a++) {
+                const int q = 8 * w + a;
+                // approximate d2 and its error bound, packed for the selection
+                ds[q * kCT + 4 * lane + b] = qn[q] + cn - 2.0f * acc[a][b];
+            }
+            ds[kQR * kCT + w * kCT + 4 * lane + b] = cn;
+        }
+        __syncwarp();
+        // selection: the warp owns its 8 query rows, so no other warp touches
+        // their lists
+#pragma unroll 1
+        for (int a = 0; a < 8; a++) {
+            const int q = 8 * w + a;
+            const int64_t qi = q0 + q;
+            if (qi >= n) break;
+            float *qld = ld + (size_t)q * k;
+            int32_t *qlj = lj + (size_t)q * k;
+            const float qnv = qn[q];
+#pragma unroll 1
+            for (int b = 0; b < 4; b++) {
+                const int64_t j = c0 + 4 * lane + b;
+                const float approx = ds[q * kCT + 4 * lane + b];
+                const float cn = ds[kQR * kCT + w * kCT + 4 * lane + b];
+                const float tau = qld[k - 1];
+                const bool cand = (j < n) && (j != qi) &&
+                                  (approx <= tau + slack_rel * (qnv + cn) || !(tau < INFINITY));
+                unsigned m = __ballot_sync(0xffffffffu, cand);
+                while (m) {
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1u;
+                    const int64_t jj = __shfl_sync(0xffffffffu, j, src);
+                    const float dex = warp_exact_d2(X, D, qi, jj, lane);
+                    const float t2 = qld[k - 1];
+                    if (dex < t2 || (dex == t2 && (int32_t)jj < qlj[k - 1]))
+                        warp_list_insert(qld, qlj, k, dex, (int32_t)jj, lane);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < kQR * k; e += kKnnThreads) {
+        const int q = e / k;
+        if (q0 + q < n) {
+            out_idx[(q0 + q) * k + (e % k)] = lj[e];
+            out_d2[(q0 + q) * k + (e % k)] = ld[e];
+        }
+    }
+}
+
+cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, int32_t k,
+                       int32_t *idx, float *d2) {
+    cudaStream_t st = c->stream;
+    cudaError_t e;
+    float *nrm = nullptr;
+    if ((e = cudaMallocAsync(&nrm, n * sizeof(float), st))) return e;
+    k_row_norms<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(n, D, Xdev, nrm);
+    if ((e = cudaGetLastError())) return e;
+    const size_t smem = (size_t)D * (kQR + kCT) * 4 + (size_t)kQR * k * 8 + kQR * 4 +
+                        (size_t)(kQR + kKnnThreads / 32) * kCT * 4;
+    if ((e = cudaFuncSetAttribute(k_knn_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)))
+        return e;
+    k_knn_tile<<<(unsigned)((n + kQR - 1) / kQR), kKnnThreads, smem, st>>>(n, D, k, Xdev, nrm,
+                                                                          idx, d2);
+    if ((e = cudaGetLastError())) return e;
+    return cudaFreeAsync(nrm, st);
+}
+
+// ---------------------------------------------------------------- perplexity
+// Sec. 3.2: bisection on beta_i (start 1; double or halve until bracketed,
+// then halve the bracket) until |H_i - ln u| < 1e-5 or 200 steps, with the
+// exponents shifted by the row's smallest distance.
+__global__ void __launch_bounds__(256)
+    k_perplexity(int64_t n, int k, float target, const float *__restrict__ d2,
+                 float *__restrict__ pcond, float *__restrict__ beta_out, DevScalars *sc) {
+    constexpr int VPL = 8;  // values per lane, k <= 256
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    float d[VPL];
+    float dmin = INFINITY;
+#pragma unroll
+    for (int v = 0; v < VPL; v++) {
+        const int e = lane + 32 * v;
+        d[v] = e < k ? d2[row * k + e] : INFINITY;
+        dmin = fminf(dmin, d[v]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dmin = fminf(dmin, __shfl_xor_sync(0xffffffffu, dmin, o));
+#pragma unroll
+    for (int v = 0; v < VPL; v++) d[v] = (lane + 32 * v < k) ? d[v] - dmin : 0.f;
+    float beta = 1.f, lo = 0.f, hi = 0.f;
+    bool has_lo = false, has_hi = false, ok = false;
+    float sum = 0.f, hs = 0.f;
+    for (int it = 0; it < 200; it++) {
+        sum = 0.f;
+        hs = 0.f;
+#pragma unroll
+        for (int v = 0; v < VPL; v++) {
+            if (lane + 32 * v < k) {
+                const float ev = expf(-beta * d[v]);
+                sum += ev;
+                hs = fmaf(d[v], ev, hs);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            hs += __shfl_xor_sync(0xffffffffu, hs, o);
+        }
+        const float H = logf(sum) + beta * hs / sum;
+        if (fabsf(H - target) < 1e-5f) {
+            ok = true;
+            break;
+        }
+        if (H > target) {
+            lo = beta;
+            has_lo = true;
+            beta = has_hi ? 0.5f * (beta + hi) : 2.f * beta;
+        } else {
+            hi = beta;
+            has_hi = true;
+            beta = has_lo ? 0.5f * (beta + lo) : 0.5f * beta;
+        }
+    }
+    sum = 0.f;
+    float ev[VPL];
+#pragma unroll
+    for (int v = 0; v < VPL; v++) {
+        ev[v] = (lane + 32 * v < k) ? expf(-beta * d[v]) : 0.f;
+        sum += ev[v];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    const float inv = 1.f / sum;
+#pragma unroll
+    for (int v = 0; v < VPL; v++) {
+        const int e = lane + 32 * v;
+        if (e < k) pcond[row * k + e] = ev[v] * inv;
+    }
+    if (lane == 0) {
+        beta_out[row] = beta;
+        if (!ok) atomicOr(&sc->err, (unsigned)PXSNE_DEVERR_BISECT);
+    }
+}
+
+cudaError_t launch_perplexity(pxsne_ctx *c, const float *d2, int64_t n, int32_t k,
+                              float perplexity, float *pcond, float *beta) {
+    k_perplexity<<<(unsigned)((n * 32 + 255) / 256), 256, 0, c->stream>>>(
+        n, k, logf(perplexity), d2, pcond, beta, c->sc);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- symmetrize
+__global__ void k_indeg(int64_t nk, const int32_t *__restrict__ idx, uint32_t *deg) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < nk) atomicAdd(&deg[idx[e]], 1u);
+}
+
+// Exclusive scan of 32-bit counts into int64 offsets: per-block scan, then a
+// single-block scan of the block totals, then the add.
+constexpr int kScanB = 1024;
+__global__ void __launch_bounds__(kScanB)
+    k_scan_blocks(int64_t m, const uint32_t *__restrict__ in, int64_t *__restrict__ out,
+                  int64_t *__restrict__ bsum) {
+    __shared__ int64_t s[kScanB];
+    const int64_t i = blockIdx.x * (int64_t)kScanB + threadIdx.x;
+    const int64_t v = i < m ? (int64_t)in[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < kScanB; o <<= 1) {
+        const int64_t t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+        __syncthreads();
+        s[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (i < m) out[i] = s[threadIdx.x] - v;
+    if (threadIdx.x == kScanB - 1) bsum[blockIdx.x] = s[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kScanB) k_scan_bsum(int64_t nb, int64_t *bsum, int64_t *total) {
+    __shared__ int64_t s[kScanB];
+    __shared__ int64_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += kScanB) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t v = i < nb ? bsum[i] : 0;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < kScanB; o <<= 1) {
+            const int64_t t = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+            __syncthreads();
+            s[threadIdx.x] += t;
+            __syncthreads();
+        }
+        const int64_t cy = carry;
+        if (i < nb) bsum[i] = cy + s[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == kScanB - 1) carry = cy + s[threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_scan_add(int64_t m, int64_t *out, const int64_t *__restrict__ bsum,
+                           const int64_t *__restrict__ total) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < m) out[i] += bsum[i / kScanB];
+    if (i == m) out[m] = *total;
+}
+
+// out[0..m] = exclusive scan of in[0..m) with out[m] = total (int64).
+static cudaError_t scan_u32_to_i64(const uint32_t *in, int64_t m, int64_t *out,
+                                   cudaStream_t st) {
+    const int64_t nb = (m + kScanB - 1) / kScanB;
+    int64_t *bsum = nullptr;
+    cudaError_t e;
+    if ((e = cudaMallocAsync(&bsum, (nb + 1) * sizeof(int64_t), st))) return e;
+    k_scan_blocks<<<(unsigned)(nb > 0 ? nb : 1), kScanB, 0, st>>>(m, in, out, bsum);
+    k_scan_bsum<<<1, kScanB, 0, st>>>(nb, bsum, bsum + nb);
+    k_scan_add<<<(unsigned)((m + 1 + 255) / 256), 256, 0, st>>>(m, out, bsum, bsum + nb);
+    if ((e = cudaGetLastError())) return e;
+    return cudaFreeAsync(bsum, st);
+}
+
+// Row i of the union pattern: its own k entries (j, p_{j|i}) first, then the
+// incoming ones (j, p_{i|j}) for every j that lists i.
+__global__ void k_fill(int64_t n, int k, const int32_t *__restrict__ idx,
+                       const float *__restrict__ pcond, const int64_t *__restrict__ tptr,
+                       uint32_t *__restrict__ cursor, int32_t *__restrict__ tcol,
+                       float *__restrict__ tval) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n * k) return;
+    const int64_t i = e / k;
+    const int a = (int)(e % k);
+    const int32_t j = idx[e];
+    const float p = pcond[e];
+    tcol[tptr[i] + a] = j;
+    tval[tptr[i] + a] = p;
+    const uint32_t slot = (uint32_t)k + atomicAdd(&cursor[j], 1u);
+    tcol[tptr[j] + slot] = (int32_t)i;
+    tval[tptr[j] + slot] = p;
+}
+
+// Sort each temporary row by (col, position) (rank sort, one warp per row),
+// then merge equal columns; count = number of distinct columns.  With
+// write == 1 the merged row goes to (col, val / 2n) at rp[i].
+__global__ void __launch_bounds__(256)
+    k_sort_merge(int64_t n, int write, const int64_t *__restrict__ tptr,
+                 const int32_t *__restrict__ tcol, const float *__restrict__ tval,
+                 int32_t *__restrict__ scol, float *__restrict__ sval,
+                 uint32_t *__restrict__ cnt, const int64_t *__restrict__ rp,
+                 int32_t *__restrict__ col, float *__restrict__ val) {
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const int64_t a = tptr[row], b = tptr[row + 1];
+    const int len = (int)(b - a);
+    if (!write) {
+        for (int e = lane; e < len; e += 32) {
+            const int32_t ce = tcol[a + e];
+            int r = 0;
+            for (int f = 0; f < len; f++) {
+                const int32_t cf = tcol[a + f];
+                r += (cf < ce) || (cf == ce && f < e);
+            }
+            scol[a + r] = ce;
+            sval[a + r] = tval[a + e];
+        }
+        __syncwarp();
+        if (lane == 0) {
+            uint32_t u = 0;
+            for (int e = 0; e < len; e++) u += (e == 0 || scol[a + e] != scol[a + e - 1]);
+            cnt[row] = u;
+        }
+    } else if (lane == 0) {
+        const float inv2n = (float)(0.5 / (double)n);
+        int64_t o = rp[row] - 1;
+        for (int e = 0; e < len; e++) {
+            const int32_t ce = scol[a + e];
+            const float ve = sval[a + e];
+            if (e == 0 || ce != scol[a + e - 1]) {
+                o++;
+                col[o] = ce;
+                val[o] = ve;
+            } else {
+                val[o] += ve;
+            }
+        }
+        for (int64_t q = rp[row]; q <= o; q++) val[q] *= inv2n;
+    }
+}
+
+__global__ void k_add_const(int64_t n, const uint32_t *in, uint32_t *out, uint32_t a) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i] + a;
+}
+
+cudaError_t build_symmetric_csr(pxsne_ctx *c, const int32_t *idx, const float *pcond,
+                                int64_t n, int32_t k, std::string &err) {
+    cudaStream_t st = c->stream;
+    cudaError_t e;
+    const int64_t nk = n * k;
+    uint32_t *deg = nullptr, *cursor = nullptr;
+    int64_t *tptr = nullptr;
+    int32_t *tcol = nullptr, *scol = nullptr;
+    float *tval = nullptr, *sval = nullptr;
+#define TRY(x)                 \
+    do {                       \
+        if ((e = (x))) {       \
+            err = #x;          \
+            return e;          \
+        }                      \
+    } while (0)
+    TRY(cudaMallocAsync(&deg, n * sizeof(uint32_t), st));
+    TRY(cudaMallocAsync(&cursor, n * sizeof(uint32_t), st));
+    TRY(cudaMallocAsync(&tptr, (n + 1) * sizeof(int64_t), st));
+    TRY(cudaMemsetAsync(deg, 0, n * sizeof(uint32_t), st));
+    TRY(cudaMemsetAsync(cursor, 0, n * sizeof(uint32_t), st));
+    k_indeg<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(nk, idx, deg);
+    TRY(cudaGetLastError());
+    // temporary rows of length k + indeg(i); 2 n k entries in total
+    uint32_t *len = cursor;
+    k_add_const<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, deg, len, (uint32_t)k);
+    TRY(cudaGetLastError());
+    TRY(scan_u32_to_i64(len, n, tptr, st));
+    TRY(cudaMemsetAsync(cursor, 0, n * sizeof(uint32_t), st));
+    TRY(cudaMallocAsync(&tcol, 2 * nk * sizeof(int32_t), st));
+    TRY(cudaMallocAsync(&tval, 2 * nk * sizeof(float), st));
+    TRY(cudaMallocAsync(&scol, 2 * nk * sizeof(int32_t), st));
+    TRY(cudaMallocAsync(&sval, 2 * nk * sizeof(float), st));
+    k_fill<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(n, k, idx, pcond, tptr, cursor, tcol,
+                                                        tval);
+    TRY(cudaGetLastError());
+    uint32_t *ucnt = deg;  // reuse
+    k_sort_merge<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(
+        n, 0, tptr, tcol, tval, scol, sval, ucnt, nullptr, nullptr, nullptr);
+    TRY(cudaGetLastError());
+    if (c->rp) { cudaFreeAsync(c->rp, st); c->rp = nullptr; }
+    if (c->col) { cudaFreeAsync(c->col, st); c->col = nullptr; }
+    if (c->val) { cudaFreeAsync(c->val, st); c->val = nullptr; }
+    TRY(cudaMallocAsync(&c->rp, (n + 1) * sizeof(int64_t), st));
+    TRY(scan_u32_to_i64(ucnt, n, c->rp, st));
+    int64_t nnz = 0;
+    TRY(cudaMemcpyAsync(&nnz, c->rp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    TRY(cudaMallocAsync(&c->col, (nnz > 0 ? nnz : 1) * sizeof(int32_t), st));
+    TRY(cudaMallocAsync(&c->val, (nnz > 0 ? nnz : 1) * sizeof(float), st));
+    k_sort_merge<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(
+        n, 1, tptr, tcol, tval, scol, sval, ucnt, c->rp, c->col, c->val);
+    TRY(cudaGetLastError());
+    c->nnz = nnz;
+    cudaFreeAsync(deg, st);
+    cudaFreeAsync(cursor, st);
+    cudaFreeAsync(tptr, st);
+    cudaFreeAsync(tcol, st);
+    cudaFreeAsync(tval, st);
+    cudaFreeAsync(scol, st);
+    cudaFreeAsync(sval, st);
+#undef TRY
+    return cudaGetLastError();
+}
+
+}  // namespace pxsne

@@ -1,0 +1,646 @@
+// C ABI of the PixelSNE library (include/pxsne.h): context, buffers, the
+// per-iteration schedule (captured once as a CUDA graph) and the inspection
+// hooks.  All compute is in the kernels of tree.cu, forces.cu, update.cu and
+// affinity.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace pxsne;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int fail(pxsne_ctx *c, int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    else g_create_err = buf;
+    return code;
+}
+
+int cuda_fail(pxsne_ctx *c, cudaError_t e, const char *what) {
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? PXSNE_E_OOM : PXSNE_E_CUDA, "%s: %s (%s)",
+                what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define CK(c, x)                                              \
+    do {                                                      \
+        cudaError_t e_ = (x);                                 \
+        if (e_ != cudaSuccess) return cuda_fail((c), e_, #x); \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(pxsne_ctx *c, T **p, size_t count) {
+    if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    (void)c;
+    return cudaMalloc(reinterpret_cast<void **>(p), bytes);
+}
+
+template <class T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+void drop_graph(pxsne_ctx *c) {
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+}
+
+void free_state(pxsne_ctx *c) {
+    drop_graph(c);
+    dfree(c->z); dfree(c->zhat); dfree(c->u); dfree(c->gains);
+    dfree(c->Frep); dfree(c->Zi); dfree(c->Fattr); dfree(c->perm); dfree(c->rank);
+    dfree(c->leaf_cnt); dfree(c->leaf_sx); dfree(c->leaf_sy); dfree(c->rec);
+    for (int k = 0; k < 2; k++) { dfree(c->lvl_cnt[k]); dfree(c->lvl_sx[k]); dfree(c->lvl_sy[k]); }
+    dfree(c->leaf_start); dfree(c->blk_off); dfree(c->zpart); dfree(c->klpart);
+    c->state_ready = false;
+}
+
+int check_params(const pxsne_params *p) {
+    if (!p) return fail(nullptr, PXSNE_E_ARG, "params is NULL");
+    if (p->log2_r < 1 || p->log2_r > kMaxL)
+        return fail(nullptr, PXSNE_E_ARG, "log2_r = %d outside [1, %d]", p->log2_r, kMaxL);
+    if (!(p->theta >= 0.f)) return fail(nullptr, PXSNE_E_ARG, "theta must be >= 0");
+    if (!(p->eta > 0.f)) return fail(nullptr, PXSNE_E_ARG, "eta must be > 0");
+    if (!(p->exaggeration > 0.f)) return fail(nullptr, PXSNE_E_ARG, "exaggeration must be > 0");
+    if (!(p->momentum0 >= 0.f) || !(p->momentum1 >= 0.f) || p->momentum0 >= 1.f ||
+        p->momentum1 >= 1.f)
+        return fail(nullptr, PXSNE_E_ARG, "momentum must be in [0, 1)");
+    if (!(p->min_gain > 0.f)) return fail(nullptr, PXSNE_E_ARG, "min_gain must be > 0");
+    if (p->k < 1 || p->k > 256) return fail(nullptr, PXSNE_E_ARG, "k = %d outside [1, 256]", p->k);
+    if (!(p->perplexity > 0.f) || p->perplexity > (float)p->k)
+        return fail(nullptr, PXSNE_E_ARG, "perplexity must be in (0, k]");
+    if (!(p->init_sigma > 0.f)) return fail(nullptr, PXSNE_E_ARG, "init_sigma must be > 0");
+    if (p->centre_mode != 0 && p->centre_mode != 1)
+        return fail(nullptr, PXSNE_E_ARG, "centre_mode must be 0 or 1");
+    return PXSNE_OK;
+}
+
+// Allocate the per-point and tree buffers for the current n and L.
+int ensure_state(pxsne_ctx *c) {
+    if (c->z && c->L == c->p.log2_r) return PXSNE_OK;
+    free_state(c);
+    const int64_t n = c->n;
+    c->L = c->p.log2_r;
+    const int L = c->L;
+    const int64_t leaves = int64_t(1) << (2 * L);
+    const int64_t cells = level_offset(L + 1);
+    const int K1 = L < kPyrK ? L : kPyrK;
+    const int64_t lvl = int64_t(1) << (2 * (L - K1));
+    CK(c, dalloc(c, &c->z, n));
+    CK(c, dalloc(c, &c->zhat, n));
+    CK(c, dalloc(c, &c->u, n));
+    CK(c, dalloc(c, &c->gains, n));
+    CK(c, dalloc(c, &c->Frep, n));
+    CK(c, dalloc(c, &c->Zi, n));
+    CK(c, dalloc(c, &c->Fattr, n));
+    CK(c, dalloc(c, &c->perm, n));
+    CK(c, dalloc(c, &c->rank, n));
+    CK(c, dalloc(c, &c->leaf_cnt, leaves));
+    CK(c, dalloc(c, &c->leaf_sx, leaves));
+    CK(c, dalloc(c, &c->leaf_sy, leaves));
+    CK(c, dalloc(c, &c->rec, cells));
+    CK(c, dalloc(c, &c->leaf_start, leaves));
+    CK(c, dalloc(c, &c->blk_off, lvl));
+    for (int k = 0; k < 2; k++) {
+        CK(c, dalloc(c, &c->lvl_cnt[k], lvl + 4));
+        CK(c, dalloc(c, &c->lvl_sx[k], lvl + 4));
+        CK(c, dalloc(c, &c->lvl_sy[k], lvl + 4));
+    }
+    c->zblocks = (int)((n + 4095) / 4096);
+    if (c->zblocks > 1024) c->zblocks = 1024;
+    if (c->zblocks < 1) c->zblocks = 1;
+    CK(c, dalloc(c, &c->zpart, c->zblocks));
+    c->klblocks = 304;
+    CK(c, dalloc(c, &c->klpart, 2 * c->klblocks));
+    return PXSNE_OK;
+}
+
+__global__ void k_iota(int n, uint32_t *p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = (uint32_t)i;
+}
+
+__global__ void k_set_scalars(DevScalars *sc, double s0, double s1, int t, float theta, int L) {
+    sc->s[0] = s0;
+    sc->s[1] = s1;
+    sc->t = t;
+    sc->Z = 0.0;
+    for (int p = 0; p < 2; p++) {
+        sc->mm[p][0] = 0x7fffffffffffffffll;
+        sc->mm[p][1] = 0x7fffffffffffffffll;
+        sc->mm[p][2] = (long long)0x8000000000000000ull;
+        sc->mm[p][3] = (long long)0x8000000000000000ull;
+    }
+    derive_scalars(sc, theta, L);
+}
+
+__global__ void k_fill_f2(int n, float2 *p, float v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = make_float2(v, v);
+}
+
+// Tree and forces of the state just written (no rescale).
+int prime(pxsne_ctx *c) {
+    const int n = (int)c->n;
+    k_iota<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->perm);
+    CK(c, cudaGetLastError());
+    CK(c, launch_tree(c, false));
+    CK(c, launch_forces(c));
+    c->state_ready = true;
+    return PXSNE_OK;
+}
+
+int one_iteration(pxsne_ctx *c, cudaEvent_t *marks = nullptr) {
+    CK(c, launch_update(c, marks));
+    CK(c, launch_tree(c, true, marks));
+    CK(c, launch_forces(c, marks));
+    return PXSNE_OK;
+}
+
+const char *kGroupNames[KG_COUNT] = {"k_update", "k_snap_hist", "k_pyr_pass",
+                                     "k_perm_scatter", "k_bh_traverse", "k_attract",
+                                     "k_zsum"};
+
+int check_device(pxsne_ctx *c, uint32_t *flags_out) {
+    CK(c, cudaStreamSynchronize(c->stream));
+    unsigned err = 0;
+    CK(c, cudaMemcpy(&err, &c->sc->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (flags_out) *flags_out = err;
+    if (err) {
+        const unsigned zero = 0;
+        CK(c, cudaMemcpy(&c->sc->err, &zero, sizeof(unsigned), cudaMemcpyHostToDevice));
+        return fail(c, PXSNE_E_DEVICE, "device error flags 0x%x%s%s%s%s", err,
+                    (err & PXSNE_DEVERR_NONFINITE) ? " non-finite" : "",
+                    (err & PXSNE_DEVERR_STACK) ? " stack-overflow" : "",
+                    (err & PXSNE_DEVERR_BISECT) ? " bisection" : "",
+                    (err & PXSNE_DEVERR_RANGE) ? " step-range" : "");
+    }
+    return PXSNE_OK;
+}
+
+int need_state(pxsne_ctx *c) {
+    if (!c) return PXSNE_E_ARG;
+    if (!c->state_ready) return fail(c, PXSNE_E_STATE, "no embedding state (call pxsne_init)");
+    return PXSNE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pxsne_default_params(pxsne_params *p) {
+    if (!p) return;
+    p->log2_r = 11;
+    p->theta = 0.5f;
+    p->eta = 200.f;
+    p->exaggeration = 12.f;
+    p->exag_iters = 250;
+    p->momentum0 = 0.5f;
+    p->momentum1 = 0.8f;
+    p->momentum_switch = 250;
+    p->min_gain = 0.01f;
+    p->k = 90;
+    p->perplexity = 30.f;
+    p->init_sigma = 1e-4f;
+    p->centre_mode = 0;
+}
+
+int pxsne_create(pxsne_ctx **out, const pxsne_params *p, void *stream) {
+    if (!out) return fail(nullptr, PXSNE_E_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_params(p);
+    if (rc) return rc;
+    pxsne_ctx *c = new (std::nothrow) pxsne_ctx();
+    if (!c) return fail(nullptr, PXSNE_E_OOM, "host allocation");
+    c->p = *p;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) {
+        if (stream) {
+            c->stream = (cudaStream_t)stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            c->own_stream = (e == cudaSuccess);
+        }
+    }
+    if (e == cudaSuccess) e = dalloc(c, &c->sc, 1);
+    if (e == cudaSuccess) e = cudaMemset(c->sc, 0, sizeof(DevScalars));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail(nullptr, e == cudaErrorMemoryAllocation ? PXSNE_E_OOM : PXSNE_E_CUDA,
+             "pxsne_create: %s", cudaGetErrorString(e));
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return e == cudaErrorMemoryAllocation ? PXSNE_E_OOM : PXSNE_E_CUDA;
+    }
+    *out = c;
+    return PXSNE_OK;
+}
+
+void pxsne_destroy(pxsne_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_state(c);
+    dfree(c->rp); dfree(c->col); dfree(c->val);
+    dfree(c->knn_idx); dfree(c->knn_d2); dfree(c->beta);
+    dfree(c->sc);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char *pxsne_last_error(const pxsne_ctx *c) {
+    return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+int pxsne_affinities(pxsne_ctx *c, const float *X, int64_t n, int32_t D, float perplexity,
+                     int x_on_device) {
+    if (!c) return PXSNE_E_ARG;
+    if (!X) return fail(c, PXSNE_E_ARG, "X is NULL");
+    const int k = c->p.k;
+    if (n < 2 || n > 0x7fffffff) return fail(c, PXSNE_E_ARG, "n = %lld out of range", (long long)n);
+    if ((int64_t)k >= n) return fail(c, PXSNE_E_ARG, "k = %d must be < n = %lld", k, (long long)n);
+    if (D < 1 || D > 256) return fail(c, PXSNE_E_UNSUPPORTED, "D = %d outside [1, 256]", D);
+    if (perplexity <= 0.f) perplexity = c->p.perplexity;
+    if (perplexity > (float)k) return fail(c, PXSNE_E_ARG, "perplexity > k");
+    if (!x_on_device) {
+        for (int64_t q = 0; q < n * D; q++)
+            if (!std::isfinite(X[q])) return fail(c, PXSNE_E_ARG, "X has a non-finite entry");
+    }
+    cudaStream_t st = c->stream;
+    free_state(c);
+    dfree(c->rp); dfree(c->col); dfree(c->val);
+    dfree(c->knn_idx); dfree(c->knn_d2); dfree(c->beta);
+    c->n = n;
+    c->D = D;
+    c->nnz = 0;
+    float *Xd = nullptr;
+    const float *Xuse = X;
+    if (!x_on_device) {
+        CK(c, cudaMallocAsync(&Xd, (size_t)n * D * sizeof(float), st));
+        CK(c, cudaMemcpyAsync(Xd, X, (size_t)n * D * sizeof(float), cudaMemcpyHostToDevice, st));
+        Xuse = Xd;
+    }
+    CK(c, dalloc(c, &c->knn_idx, (size_t)n * k));
+    CK(c, dalloc(c, &c->knn_d2, (size_t)n * k));
+    CK(c, dalloc(c, &c->beta, (size_t)n));
+    c->knn_k = k;
+    CK(c, launch_knn(c, Xuse, n, D, k, c->knn_idx, c->knn_d2));
+    if (Xd) CK(c, cudaFreeAsync(Xd, st));
+    float *pcond = nullptr;
+    CK(c, cudaMallocAsync(&pcond, (size_t)n * k * sizeof(float), st));
+    CK(c, launch_perplexity(c, c->knn_d2, n, k, perplexity, pcond, c->beta));
+    std::string where;
+    cudaError_t e = build_symmetric_csr(c, c->knn_idx, pcond, n, k, where);
+    if (e != cudaSuccess) return cuda_fail(c, e, where.c_str());
+    CK(c, cudaFreeAsync(pcond, st));
+    return check_device(c, nullptr);
+}
+
+int pxsne_set_P(pxsne_ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *col,
+                const float *val) {
+    if (!c) return PXSNE_E_ARG;
+    if (n < 2 || n > 0x7fffffff || !row_ptr) return fail(c, PXSNE_E_ARG, "bad n or row_ptr");
+    if (row_ptr[0] != 0) return fail(c, PXSNE_E_ARG, "row_ptr[0] != 0");
+    for (int64_t i = 0; i < n; i++)
+        if (row_ptr[i + 1] < row_ptr[i]) return fail(c, PXSNE_E_ARG, "row_ptr not monotone");
+    const int64_t nnz = row_ptr[n];
+    if (nnz > 0 && (!col || !val)) return fail(c, PXSNE_E_ARG, "col/val NULL");
+    for (int64_t i = 0; i < n; i++)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; e++) {
+            if (col[e] < 0 || col[e] >= n || col[e] == i)
+                return fail(c, PXSNE_E_ARG, "bad column %d in row %lld", col[e], (long long)i);
+            if (!(val[e] >= 0.f) || !std::isfinite(val[e]))
+                return fail(c, PXSNE_E_ARG, "bad value in row %lld", (long long)i);
+        }
+    free_state(c);
+    dfree(c->rp); dfree(c->col); dfree(c->val);
+    dfree(c->knn_idx); dfree(c->knn_d2); dfree(c->beta);
+    c->knn_k = 0;
+    c->n = n;
+    c->nnz = nnz;
+    CK(c, dalloc(c, &c->rp, n + 1));
+    CK(c, dalloc(c, &c->col, nnz > 0 ? nnz : 1));
+    CK(c, dalloc(c, &c->val, nnz > 0 ? nnz : 1));
+    CK(c, cudaMemcpyAsync(c->rp, row_ptr, (n + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+    if (nnz > 0) {
+        CK(c, cudaMemcpyAsync(c->col, col, nnz * 4, cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(c->val, val, nnz * 4, cudaMemcpyHostToDevice, c->stream));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    return PXSNE_OK;
+}
+
+int pxsne_init(pxsne_ctx *c, const float *Y0, int y_on_device, uint64_t seed) {
+    if (!c) return PXSNE_E_ARG;
+    if (c->n < 2 || !c->rp) return fail(c, PXSNE_E_STATE, "no affinities (call pxsne_affinities)");
+    int rc = ensure_state(c);
+    if (rc) return rc;
+    cudaStream_t st = c->stream;
+    const int64_t n = c->n;
+    float *Yd = nullptr;
+    uint32_t *mm = nullptr;
+    CK(c, cudaMallocAsync(&mm, 4 * sizeof(uint32_t), st));
+    const float *Yuse = Y0;
+    if (!Y0 || !y_on_device) {
+        CK(c, cudaMallocAsync(&Yd, (size_t)n * 2 * sizeof(float), st));
+        if (Y0) {
+            CK(c, cudaMemcpyAsync(Yd, Y0, (size_t)n * 8, cudaMemcpyHostToDevice, st));
+        } else {
+            CK(c, launch_philox_y0(c, Yd, seed, c->p.init_sigma));
+        }
+        Yuse = Yd;
+    }
+    const unsigned zero = 0;
+    CK(c, cudaMemcpyAsync(&c->sc->err, &zero, sizeof(unsigned), cudaMemcpyHostToDevice, st));
+    CK(c, launch_init_map(c, Yuse, mm));
+    rc = prime(c);
+    if (rc) return rc;
+    if (Yd) CK(c, cudaFreeAsync(Yd, st));
+    CK(c, cudaFreeAsync(mm, st));
+    rc = check_device(c, nullptr);
+    if (rc) {
+        c->state_ready = false;
+        return rc;
+    }
+    return PXSNE_OK;
+}
+
+int pxsne_set_state(pxsne_ctx *c, const uint32_t *z, const double *s, const float *u,
+                    const float *gains, int32_t t) {
+    if (!c) return PXSNE_E_ARG;
+    if (c->n < 2 || !c->rp) return fail(c, PXSNE_E_STATE, "no affinities");
+    if (!z || !s || !(s[0] > 0.0) || !(s[1] > 0.0) || t < 0)
+        return fail(c, PXSNE_E_ARG, "bad z, s or t");
+    int rc = ensure_state(c);
+    if (rc) return rc;
+    const int n = (int)c->n;
+    cudaStream_t st = c->stream;
+    CK(c, cudaMemcpyAsync(c->z, z, (size_t)n * 8, cudaMemcpyHostToDevice, st));
+    if (u) CK(c, cudaMemcpyAsync(c->u, u, (size_t)n * 8, cudaMemcpyHostToDevice, st));
+    else k_fill_f2<<<(n + 255) / 256, 256, 0, st>>>(n, c->u, 0.f);
+    if (gains) CK(c, cudaMemcpyAsync(c->gains, gains, (size_t)n * 8, cudaMemcpyHostToDevice, st));
+    else k_fill_f2<<<(n + 255) / 256, 256, 0, st>>>(n, c->gains, 1.f);
+    k_set_scalars<<<1, 1, 0, st>>>(c->sc, s[0], s[1], t, c->p.theta, c->L);
+    CK(c, cudaGetLastError());
+    rc = prime(c);
+    if (rc) return rc;
+    return check_device(c, nullptr);
+}
+
+int pxsne_step(pxsne_ctx *c, int32_t iters) {
+    int rc = need_state(c);
+    if (rc) return rc;
+    if (iters < 0) return fail(c, PXSNE_E_ARG, "iters < 0");
+    if (iters == 0) return PXSNE_OK;
+    if (!c->graph && c->stream != nullptr && c->stream != cudaStreamLegacy &&
+        c->stream != cudaStreamPerThread) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            int r = one_iteration(c);
+            cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+            if (r == PXSNE_OK && e2 == cudaSuccess && g) {
+                if (cudaGraphInstantiate(&c->graph, g, 0) != cudaSuccess) c->graph = nullptr;
+            }
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();
+    }
+    for (int32_t k = 0; k < iters; k++) {
+        if (c->graph) {
+            CK(c, cudaGraphLaunch(c->graph, c->stream));
+        } else {
+            rc = one_iteration(c);
+            if (rc) return rc;
+        }
+    }
+    return PXSNE_OK;
+}
+
+int pxsne_step_profiled(pxsne_ctx *c, int32_t iters, double *group_ms, int32_t n_groups,
+                        double *total_ms) {
+    int rc = need_state(c);
+    if (rc) return rc;
+    if (iters < 1 || !group_ms || n_groups < KG_COUNT)
+        return fail(c, PXSNE_E_ARG, "need iters >= 1 and %d group slots", (int)KG_COUNT);
+    std::vector<cudaEvent_t> ev((size_t)iters * (KG_COUNT + 1) + 2, nullptr);
+    for (auto &e : ev) CK(c, cudaEventCreate(&e));
+    cudaEvent_t *t0 = &ev[ev.size() - 2], *t1 = &ev[ev.size() - 1];
+    CK(c, cudaEventRecord(*t0, c->stream));
+    for (int32_t k = 0; k < iters; k++) {
+        rc = one_iteration(c, &ev[(size_t)k * (KG_COUNT + 1)]);
+        if (rc) break;
+    }
+    if (!rc) {
+        CK(c, cudaEventRecord(*t1, c->stream));
+        CK(c, cudaEventSynchronize(*t1));
+        for (int g = 0; g < KG_COUNT; g++) group_ms[g] = 0.0;
+        for (int32_t k = 0; k < iters; k++) {
+            cudaEvent_t *m = &ev[(size_t)k * (KG_COUNT + 1)];
+            for (int g = 0; g < KG_COUNT; g++) {
+                float ms = 0.f;
+                CK(c, cudaEventElapsedTime(&ms, m[g], m[g + 1]));
+                group_ms[g] += ms;
+            }
+        }
+        if (total_ms) {
+            float ms = 0.f;
+            CK(c, cudaEventElapsedTime(&ms, *t0, *t1));
+            *total_ms = ms;
+        }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (rc) return rc;
+    return check_device(c, nullptr);
+}
+
+const char *pxsne_kernel_group_name(int32_t g) {
+    return (g >= 0 && g < KG_COUNT) ? kGroupNames[g] : nullptr;
+}
+
+int pxsne_kl(pxsne_ctx *c, double *out) {
+    int rc = need_state(c);
+    if (rc) return rc;
+    if (!out) return fail(c, PXSNE_E_ARG, "out is NULL");
+    double *d = nullptr;
+    CK(c, cudaMallocAsync(&d, sizeof(double), c->stream));
+    CK(c, launch_kl(c, d));
+    CK(c, cudaMemcpyAsync(out, d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaFreeAsync(d, c->stream));
+    return check_device(c, nullptr);
+}
+
+int pxsne_get_Y(pxsne_ctx *c, float *Y, int32_t *pix, int on_device) {
+    int rc = need_state(c);
+    if (rc) return rc;
+    cudaStream_t st = c->stream;
+    const int64_t n = c->n;
+    float *scratch = nullptr;
+    CK(c, cudaMallocAsync(&scratch, 16, st));
+    float *Yd = Y;
+    int32_t *Pd = pix;
+    if (!on_device) {
+        Yd = nullptr;
+        Pd = nullptr;
+        if (Y) CK(c, cudaMallocAsync(&Yd, (size_t)n * 8, st));
+        if (pix) CK(c, cudaMallocAsync(&Pd, (size_t)n * 8, st));
+    }
+    CK(c, launch_centre_y(c, Yd, Pd, scratch));
+    if (!on_device) {
+        if (Y) {
+            CK(c, cudaMemcpyAsync(Y, Yd, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+            CK(c, cudaFreeAsync(Yd, st));
+        }
+        if (pix) {
+            CK(c, cudaMemcpyAsync(pix, Pd, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+            CK(c, cudaFreeAsync(Pd, st));
+        }
+    }
+    CK(c, cudaFreeAsync(scratch, st));
+    return check_device(c, nullptr);
+}
+
+int pxsne_sync(pxsne_ctx *c, uint32_t *dev_errors) {
+    if (!c) return PXSNE_E_ARG;
+    return check_device(c, dev_errors);
+}
+
+int pxsne_get_sizes(pxsne_ctx *c, int64_t *n, int64_t *nnz) {
+    if (!c) return PXSNE_E_ARG;
+    if (n) *n = c->n;
+    if (nnz) *nnz = c->nnz;
+    return PXSNE_OK;
+}
+
+int pxsne_get_P(pxsne_ctx *c, int64_t *row_ptr, int32_t *col, float *val) {
+    if (!c) return PXSNE_E_ARG;
+    if (!c->rp) return fail(c, PXSNE_E_STATE, "no affinities");
+    cudaStream_t st = c->stream;
+    if (row_ptr) CK(c, cudaMemcpyAsync(row_ptr, c->rp, (c->n + 1) * 8, cudaMemcpyDeviceToHost, st));
+    if (col && c->nnz) CK(c, cudaMemcpyAsync(col, c->col, c->nnz * 4, cudaMemcpyDeviceToHost, st));
+    if (val && c->nnz) CK(c, cudaMemcpyAsync(val, c->val, c->nnz * 4, cudaMemcpyDeviceToHost, st));
+    return check_device(c, nullptr);
+}
+
+int pxsne_get_knn(pxsne_ctx *c, int32_t *idx, float *d2, float *beta) {
+    if (!c) return PXSNE_E_ARG;
+    if (!c->knn_idx) return fail(c, PXSNE_E_STATE, "no neighbour lists (P was injected?)");
+    cudaStream_t st = c->stream;
+    const size_t nk = (size_t)c->n * c->knn_k;
+    if (idx) CK(c, cudaMemcpyAsync(idx, c->knn_idx, nk * 4, cudaMemcpyDeviceToHost, st));
+    if (d2) CK(c, cudaMemcpyAsync(d2, c->knn_d2, nk * 4, cudaMemcpyDeviceToHost, st));
+    if (beta) CK(c, cudaMemcpyAsync(beta, c->beta, c->n * 4, cudaMemcpyDeviceToHost, st));
+    return check_device(c, nullptr);
+}
+
+int pxsne_get_state(pxsne_ctx *c, uint32_t *z, double *s, float *u, float *gains, int32_t *t) {
+    int rc = need_state(c);
+    if (rc) return rc;
+    cudaStream_t st = c->stream;
+    const size_t n = (size_t)c->n;
+    if (z) CK(c, cudaMemcpyAsync(z, c->z, n * 8, cudaMemcpyDeviceToHost, st));
+    if (u) CK(c, cudaMemcpyAsync(u, c->u, n * 8, cudaMemcpyDeviceToHost, st));
+    if (gains) CK(c, cudaMemcpyAsync(gains, c->gains, n * 8, cudaMemcpyDeviceToHost, st));
+    DevScalars h;
+    CK(c, cudaMemcpyAsync(&h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+    rc = check_device(c, nullptr);
+    if (rc) return rc;
+    if (s) {
+        s[0] = h.s[0];
+        s[1] = h.s[1];
+    }
+    if (t) *t = h.t;
+    return PXSNE_OK;
+}
+
+int pxsne_get_tree(pxsne_ctx *c, int32_t level, uint32_t *cnt, uint64_t *sx, uint64_t *sy,
+                   uint32_t *morton) {
+    int rc = need_state(c);
+    if (rc) return rc;
+    if (level < 0 || level > c->L) return fail(c, PXSNE_E_ARG, "level out of range");
+    cudaStream_t st = c->stream;
+    const size_t cells = size_t(1) << (2 * level);
+    if (cnt) {
+        uint32_t *d = nullptr;
+        CK(c, cudaMallocAsync(&d, cells * 4, st));
+        CK(c, launch_level_counts(c, level, d));
+        CK(c, cudaMemcpyAsync(cnt, d, cells * 4, cudaMemcpyDeviceToHost, st));
+        CK(c, cudaFreeAsync(d, st));
+    }
+    if (level == c->L) {
+        if (sx) CK(c, cudaMemcpyAsync(sx, c->leaf_sx, cells * 8, cudaMemcpyDeviceToHost, st));
+        if (sy) CK(c, cudaMemcpyAsync(sy, c->leaf_sy, cells * 8, cudaMemcpyDeviceToHost, st));
+    }
+    if (morton) {
+        uint32_t *d = nullptr;
+        CK(c, cudaMallocAsync(&d, (size_t)c->n * 4, st));
+        CK(c, launch_morton_keys(c, d));
+        CK(c, cudaMemcpyAsync(morton, d, (size_t)c->n * 4, cudaMemcpyDeviceToHost, st));
+        CK(c, cudaFreeAsync(d, st));
+    }
+    return check_device(c, nullptr);
+}
+
+int pxsne_get_forces(pxsne_ctx *c, float *Frep, float *Zi, float *Fattr, double *Z) {
+    int rc = need_state(c);
+    if (rc) return rc;
+    cudaStream_t st = c->stream;
+    const size_t n = (size_t)c->n;
+    if (Frep) CK(c, cudaMemcpyAsync(Frep, c->Frep, n * 8, cudaMemcpyDeviceToHost, st));
+    if (Zi) CK(c, cudaMemcpyAsync(Zi, c->Zi, n * 4, cudaMemcpyDeviceToHost, st));
+    if (Fattr) CK(c, cudaMemcpyAsync(Fattr, c->Fattr, n * 8, cudaMemcpyDeviceToHost, st));
+    if (Z) CK(c, cudaMemcpyAsync(Z, &c->sc->Z, sizeof(double), cudaMemcpyDeviceToHost, st));
+    return check_device(c, nullptr);
+}
+
+int pxsne_get_counters(pxsne_ctx *c, uint64_t *n_accept, uint64_t *n_test) {
+    int rc = need_state(c);
+    if (rc) return rc;
+    DevScalars h;
+    CK(c, cudaMemcpyAsync(&h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    rc = check_device(c, nullptr);
+    if (rc) return rc;
+    if (n_accept) *n_accept = h.n_accept;
+    if (n_test) *n_test = h.n_test;
+    return PXSNE_OK;
+}
+
+int64_t pxsne_device_bytes(const pxsne_ctx *c) {
+    if (!c) return 0;
+    int64_t b = sizeof(DevScalars);
+    const int64_t n = c->n;
+    if (c->rp) b += (n + 1) * 8 + c->nnz * 8;
+    if (c->knn_idx) b += n * c->knn_k * 8 + n * 4;
+    if (c->z) {
+        const int L = c->L;
+        const int64_t leaves = int64_t(1) << (2 * L);
+        const int K1 = L < kPyrK ? L : kPyrK;
+        const int64_t lvl = int64_t(1) << (2 * (L - K1));
+        b += n * (8 + 16 + 8 + 8 + 8 + 4 + 8 + 4 + 4);
+        b += leaves * (4 + 8 + 8 + 4) + level_offset(L + 1) * 16 + lvl * 4 + 2 * (lvl + 4) * 20;
+        b += (int64_t)c->zblocks * 8 + (int64_t)c->klblocks * 16;
+    }
+    return b;
+}
+
+}  // extern "C"

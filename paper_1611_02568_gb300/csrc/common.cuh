@@ -1,0 +1,183 @@
+// Internal declarations shared by the CUDA translation units of the PixelSNE
+// library (sm_103a).  Nothing here is part of the public ABI (include/pxsne.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "pxsne.h"
+
+namespace pxsne {
+
+typedef unsigned long long u64;
+typedef long long i64;
+
+constexpr int kMaxL = 14;           // screen up to 2^14 x 2^14 (Morton keys < 2^28)
+constexpr int kTravWarps = 8;       // warps per CTA in the traversal
+constexpr int kTravStack = 64;      // entries per warp; depth needs <= 3L + 1
+constexpr int kPyrK = 5;            // pyramid levels reduced per CTA pass
+constexpr double kR = 4294967296.0; // 2^32 ulps per axis
+
+// Scalars of the iteration that live on the device so that a captured graph
+// can replay iterations without host involvement.
+struct DevScalars {
+    double s[2];         // y-units per ulp (s_d^2 = beta_d of Eq. beta_scaling)
+    double inv_s[2];     // 1 / s_d
+    float sf[2];         // s_d rounded to float
+    float T[kMaxL + 2];  // BH acceptance: accept cell of level l iff d^2 > T[l]
+    i64 mm[2][4];        // [t & 1] = {min_x, min_y, max_x, max_y} of zhat
+    double Z;            // sum_i Z_i of the current state
+    double kl_acc[2];    // KL partial results {sum p ln(p/w), sum p}
+    int t;               // iteration counter
+    unsigned err;        // PXSNE_DEVERR_* flags
+    unsigned ticket;     // last-block-done counter of the Z reduction
+    unsigned ticket2;    // same for the KL reduction
+    u64 n_accept;        // accepted (point, cell) pairs of the last traversal
+    u64 n_test;          // (point, cell) pairs tested by the last traversal
+};
+
+// Record of one cell of the pyramid, 16 bytes:
+//   x = hi_x | hi_y << 16   (integer part of the centre of mass >> 16)
+//   y = lo_x (float bits)   (centre of mass - hi_x * 65536, in ulps)
+//   z = lo_y (float bits)
+//   w = N_c
+// The centre of mass of cell c is S_c / N_c in ulps; splitting it at bit 16
+// lets a point compute z_i - com exactly in float (see bh.cu).
+
+__host__ __device__ inline int64_t level_offset(int l) {
+    return ((int64_t(1) << (2 * l)) - 1) / 3;
+}
+
+__device__ __forceinline__ uint32_t spread_bits16(uint32_t x) {
+    x &= 0x0000ffffu;
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+__device__ __forceinline__ uint32_t gather_bits16(uint32_t x) {
+    x &= 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0f0f0f0fu;
+    x = (x | (x >> 4)) & 0x00ff00ffu;
+    x = (x | (x >> 8)) & 0x0000ffffu;
+    return x;
+}
+
+// Morton key of pixel (px, py): x bits at even positions, y bits at odd ones.
+__device__ __forceinline__ uint32_t morton2(uint32_t px, uint32_t py) {
+    return spread_bits16(px) | (spread_bits16(py) << 1);
+}
+
+// Derived per-iteration scalars from s (called by one thread).
+__device__ inline void derive_scalars(DevScalars *sc, float theta, int L) {
+    const double s0 = sc->s[0], s1 = sc->s[1];
+    sc->inv_s[0] = 1.0 / s0;
+    sc->inv_s[1] = 1.0 / s1;
+    sc->sf[0] = (float)s0;
+    sc->sf[1] = (float)s1;
+    const double th2 = (double)theta * (double)theta;
+    for (int l = 0; l <= kMaxL + 1; l++) {
+        if (l > L) { sc->T[l] = INFINITY; continue; }
+        // diagonal of a level-l cell in y-units, squared: W^2 (s0^2 + s1^2),
+        // W = 2^(32-l) ulps; Eq. bh_criteria accepts when r_c^2 < theta^2 d^2
+        double W2 = ldexp(1.0, 64 - 2 * l);
+        double rc2 = W2 * (s0 * s0 + s1 * s1);
+        sc->T[l] = th2 > 0.0 ? (float)(rc2 / th2) : INFINITY;
+    }
+}
+
+
+}  // namespace pxsne
+
+// Host-side context.
+struct pxsne_ctx {
+    pxsne_params p;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    std::string err;
+
+    int64_t n = 0;
+    int32_t D = 0;
+    int64_t nnz = 0;
+
+    // P as CSR
+    int64_t *rp = nullptr;
+    int32_t *col = nullptr;
+    float *val = nullptr;
+
+    // neighbour lists of the last affinities call
+    int32_t *knn_idx = nullptr;
+    float *knn_d2 = nullptr;
+    float *beta = nullptr;
+    int32_t knn_k = 0;
+
+    // embedding state (data order)
+    uint2 *z = nullptr;
+    longlong2 *zhat = nullptr;
+    float2 *u = nullptr;
+    float2 *gains = nullptr;
+    float2 *Frep = nullptr;
+    float *Zi = nullptr;
+    float2 *Fattr = nullptr;
+    uint32_t *perm = nullptr;  // traversal order (Morton order of a recent state)
+    uint32_t *rank = nullptr;  // rank of each point inside its pixel
+
+    // tree
+    int L = 0;
+    uint32_t *leaf_cnt = nullptr;
+    unsigned long long *leaf_sx = nullptr, *leaf_sy = nullptr;
+    uint4 *rec = nullptr;
+    uint32_t *lvl_cnt[2] = {nullptr, nullptr};
+    unsigned long long *lvl_sx[2] = {nullptr, nullptr}, *lvl_sy[2] = {nullptr, nullptr};
+    uint32_t *leaf_start = nullptr;
+    uint32_t *blk_off = nullptr;
+
+    double *zpart = nullptr;
+    int zblocks = 0;
+    double *klpart = nullptr;
+    int klblocks = 0;
+
+    pxsne::DevScalars *sc = nullptr;
+    bool state_ready = false;
+    cudaGraphExec_t graph = nullptr;
+    int64_t dev_bytes = 0;
+};
+
+// Launchers implemented in the .cu files (all enqueue on ctx->stream).
+namespace pxsne {
+cudaError_t launch_init_map(pxsne_ctx *c, const float *Y0dev, uint32_t *mm_scratch);
+// Kernel groups of one iteration, in launch order (timing marks).
+enum KernelGroup {
+    KG_UPDATE = 0,   // k_update
+    KG_SNAP,         // leaf memsets + k_snap_hist
+    KG_PYRAMID,      // k_pyr_pass x passes + k_scan1
+    KG_PERM,         // k_perm_scatter
+    KG_TRAVERSE,     // k_bh_traverse
+    KG_ATTRACT,      // k_attract
+    KG_ZSUM,         // k_zsum
+    KG_COUNT
+};
+// marks (optional): an event is recorded on the stream before each group g
+// (marks[g]) and after the last one (marks[KG_COUNT]).
+cudaError_t launch_tree(pxsne_ctx *c, bool rescale, cudaEvent_t *marks = nullptr);
+cudaError_t launch_forces(pxsne_ctx *c, cudaEvent_t *marks = nullptr);
+cudaError_t launch_update(pxsne_ctx *c, cudaEvent_t *marks = nullptr);
+cudaError_t launch_kl(pxsne_ctx *c, double *out_dev);
+cudaError_t launch_centre_y(pxsne_ctx *c, float *Ydev, int32_t *pixdev, float *scratch);
+cudaError_t launch_philox_y0(pxsne_ctx *c, float *Y0dev, uint64_t seed, float sigma);
+cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, int32_t k,
+                       int32_t *idx, float *d2);
+cudaError_t launch_perplexity(pxsne_ctx *c, const float *d2, int64_t n, int32_t k,
+                              float perplexity, float *pcond, float *beta);
+cudaError_t build_symmetric_csr(pxsne_ctx *c, const int32_t *idx, const float *pcond,
+                                int64_t n, int32_t k, std::string &err);
+cudaError_t launch_level_counts(pxsne_ctx *c, int level, uint32_t *cnt);
+cudaError_t launch_morton_keys(pxsne_ctx *c, uint32_t *keys);
+}  // namespace pxsne

@@ -1,0 +1,316 @@
+// Forces of the PixelSNE gradient (Eq. grad) on the pixel-aligned tree.
+//
+//   k_bh_traverse  repulsion by Barnes-Hut (Sec. 3.3, Eq. bh_criteria) on the
+//                  dense pyramid, one warp per 32 points of the Morton order;
+//                  each lane keeps its own accept/open decisions (a lane mask
+//                  per stack entry), so every point sees exactly the cells its
+//                  own depth-first search would accept
+//   k_attract      attraction over the CSR of P, one warp per row
+//   k_zsum         Z = sum_i Z_i in FP64, fixed summation order
+//   k_kl           Eq. cost_func in FP64 accumulation
+#include <cmath>
+
+#include "common.cuh"
+
+namespace pxsne {
+
+// z_i - com along one axis, in ulps.  hi is the com's integer part >> 16,
+// lo the rest (float, < 65536); zh = z >> 16, zl = z & 0xffff as float.  The
+// difference of the high parts is an exact integer below 2^16 in magnitude,
+// so the only rounding is the final fma.
+__device__ __forceinline__ float com_delta(int zh, float zl, uint32_t hi, float lo) {
+    const float dh = (float)(zh - (int)hi);
+    return fmaf(dh, 65536.0f, zl - lo);
+}
+
+__global__ void __launch_bounds__(kTravWarps * 32)
+    k_bh_traverse(int n, int L, int centre_mode, const uint2 *__restrict__ z,
+                  const uint32_t *__restrict__ perm, const uint4 *__restrict__ rec,
+                  DevScalars *sc, float2 *__restrict__ Frep, float *__restrict__ Zi) {
+    __shared__ uint32_t s_node[kTravWarps][kTravStack];
+    __shared__ uint32_t s_mask[kTravWarps][kTravStack];
+    __shared__ float s_T[kMaxL + 2];
+    __shared__ int64_t s_off[kMaxL + 2];
+    if (threadIdx.x < kMaxL + 2) {
+        s_T[threadIdx.x] = sc->T[threadIdx.x];
+        s_off[threadIdx.x] = threadIdx.x <= L ? level_offset(threadIdx.x) : 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int idx = (blockIdx.x * kTravWarps + w) * 32 + lane;
+    const bool valid = idx < n;
+    const unsigned active = __ballot_sync(0xffffffffu, valid);
+    if (active == 0u) return;
+    const uint32_t i = valid ? perm[idx] : 0u;
+    const uint2 zi = z[i];
+    const int F = 32 - L;
+    const uint32_t mi = morton2(zi.x >> F, zi.y >> F);
+    const int zhx = (int)(zi.x >> 16), zhy = (int)(zi.y >> 16);
+    const float zlx = (float)(zi.x & 0xffffu), zly = (float)(zi.y & 0xffffu);
+    const float sf0 = sc->sf[0], sf1 = sc->sf[1];
+    float fx = 0.f, fy = 0.f, zs = 0.f;
+    uint32_t n_acc = 0u, n_tst = 0u;
+
+    uint32_t *stn = s_node[w];
+    uint32_t *stm = s_mask[w];
+    int sp = 0;
+    // The root contains every point: start with its four children.
+    if (lane == 0) {
+        stn[0] = 0u;  // (level 0 << 28) | morton 0
+        stm[0] = active;
+    }
+    sp = 1;
+    __syncwarp();
+    bool overflow = false;
+    while (sp > 0) {
+        sp--;
+        const uint32_t node = stn[sp];
+        const uint32_t mask = stm[sp];
+        __syncwarp();
+        const int lc = (int)(node >> 28) + 1;  // level of the children
+        const uint32_t m0 = (node & 0x0fffffffu) << 2;
+        const uint4 *rc = rec + s_off[lc] + m0;
+        const bool me = (mask >> lane) & 1u;
+        const bool leaf = (lc == L);
+        const float Tl = s_T[lc];
+        const uint32_t mine = mi >> (2 * (L - lc));
+#pragma unroll
+        for (int ch = 0; ch < 4; ch++) {
+            const uint4 r = __ldg(rc + ch);
+            if (r.w == 0u) continue;
+            const uint32_t mc = m0 + ch;
+            bool want_open = false;
+            if (me) {
+                n_tst++;
+                const bool contains = (mine == mc);
+                if (contains && !leaf) {
+                    want_open = true;
+                } else {
+                    float dx, dy, Nf;
+                    if (centre_mode == 0) {
+                        dx = com_delta(zhx, zlx, r.x & 0xffffu, __uint_as_float(r.y));
+                        dy = com_delta(zhy, zly, r.x >> 16, __uint_as_float(r.z));
+                    } else {
+                        // geometric centre of the cell: origin + W / 2
+                        const uint32_t cx = gather_bits16(mc), cy = gather_bits16(mc >> 1);
+                        const int64_t half = int64_t(1) << (31 - lc);
+                        dx = (float)((int64_t)zi.x - (((int64_t)cx << (32 - lc)) + half));
+                        dy = (float)((int64_t)zi.y - (((int64_t)cy << (32 - lc)) + half));
+                    }
+                    Nf = (float)r.w;
+                    bool skip = false;
+                    if (contains) {  // own pixel: take point i out of the cell
+                        if (r.w == 1u) {
+                            skip = true;
+                        } else if (centre_mode == 0) {
+                            const float sc2 = Nf / (Nf - 1.0f);
+                            dx *= sc2;
+                            dy *= sc2;
+                        }
+                        Nf -= 1.0f;
+                    }
+                    dx *= sf0;
+                    dy *= sf1;
+                    const float d2 = fmaf(dx, dx, dy * dy);
+                    if (!skip) {
+                        if (!leaf && !contains && !(d2 > Tl)) {
+                            want_open = true;
+                        } else {
+                            n_acc++;
+                            const float q = 1.0f / (1.0f + d2);
+                            const float Nq = Nf * q;
+                            zs += Nq;
+                            const float Nq2 = Nq * q;
+                            fx = fmaf(Nq2, dx, fx);
+                            fy = fmaf(Nq2, dy, fy);
+                        }
+                    }
+                }
+            }
+            const unsigned ob = __ballot_sync(0xffffffffu, want_open);
+            if (ob) {
+                if (sp >= kTravStack) {
+                    overflow = true;
+                } else {
+                    if (lane == 0) {
+                        stn[sp] = ((uint32_t)lc << 28) | mc;
+                        stm[sp] = ob;
+                    }
+                    sp++;
+                }
+            }
+        }
+        __syncwarp();
+        if (overflow) break;
+    }
+    if (overflow && lane == 0) atomicOr(&sc->err, (unsigned)PXSNE_DEVERR_STACK);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n_acc += __shfl_xor_sync(0xffffffffu, n_acc, o);
+        n_tst += __shfl_xor_sync(0xffffffffu, n_tst, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&sc->n_accept, (u64)n_acc);
+        atomicAdd(&sc->n_test, (u64)n_tst);
+    }
+    if (valid) {
+        Frep[i] = make_float2(fx, fy);
+        Zi[i] = zs;
+    }
+}
+
+// Eq. grad, first term: Fattr_i = sum_j p_ij w_ij (y_i - y_j), one warp per row.
+__global__ void __launch_bounds__(256)
+    k_attract(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+              const float *__restrict__ val, const uint2 *__restrict__ z,
+              const DevScalars *__restrict__ sc, float2 *__restrict__ Fattr) {
+    const int lane = threadIdx.x & 31;
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= n) return;
+    const float sf0 = sc->sf[0], sf1 = sc->sf[1];
+    const uint2 zi = z[row];
+    const int64_t e0 = rp[row], e1 = rp[row + 1];
+    float fx = 0.f, fy = 0.f;
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+        const int32_t j = __ldg(col + e);
+        const float p = __ldg(val + e);
+        const uint2 zj = z[j];
+        const float dx = (float)((int64_t)zi.x - (int64_t)zj.x) * sf0;
+        const float dy = (float)((int64_t)zi.y - (int64_t)zj.y) * sf1;
+        const float q = 1.0f / (1.0f + fmaf(dx, dx, dy * dy));
+        const float pq = p * q;
+        fx = fmaf(pq, dx, fx);
+        fy = fmaf(pq, dy, fy);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+    }
+    if (lane == 0) Fattr[row] = make_float2(fx, fy);
+}
+
+// Deterministic FP64 block sum (fixed tree order) of blockDim.x values.
+__device__ double block_sum_f64(double v, double *s_red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int k = 0; k < nw; k++) t += s_red[k];
+    }
+    __syncthreads();
+    return t;
+}
+
+// Z = sum_i Z_i: each block sums a fixed contiguous chunk, the last block to
+// finish adds the partials in index order.
+__global__ void __launch_bounds__(512)
+    k_zsum(int n, const float *__restrict__ Zi, double *__restrict__ part, DevScalars *sc) {
+    __shared__ double s_red[16];
+    __shared__ bool s_last;
+    const int chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int a = blockIdx.x * chunk, b = min(n, a + chunk);
+    double v = 0.0;
+    for (int k = a + threadIdx.x; k < b; k += blockDim.x) v += (double)Zi[k];
+    const double t = block_sum_f64(v, s_red);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = t;
+        __threadfence();
+        const unsigned tk = atomicAdd(&sc->ticket, 1u);
+        s_last = (tk == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double w = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x)
+        w += reinterpret_cast<volatile double *>(part)[k];
+    const double Z = block_sum_f64(w, s_red);
+    if (threadIdx.x == 0) {
+        sc->Z = Z;
+        sc->ticket = 0u;
+    }
+}
+
+cudaError_t launch_forces(pxsne_ctx *c, cudaEvent_t *marks) {
+    cudaStream_t st = c->stream;
+    const int n = (int)c->n;
+    cudaError_t e;
+    if (marks && (e = cudaEventRecord(marks[KG_TRAVERSE], st))) return e;
+    const int trav_blocks = (n + kTravWarps * 32 - 1) / (kTravWarps * 32);
+    k_bh_traverse<<<trav_blocks, kTravWarps * 32, 0, st>>>(n, c->L, c->p.centre_mode, c->z,
+                                                           c->perm, c->rec, c->sc, c->Frep,
+                                                           c->Zi);
+    if ((e = cudaGetLastError())) return e;
+    if (marks && (e = cudaEventRecord(marks[KG_ATTRACT], st))) return e;
+    const int att_blocks = (int)((int64_t(n) * 32 + 255) / 256);
+    k_attract<<<att_blocks, 256, 0, st>>>(n, c->rp, c->col, c->val, c->z, c->sc, c->Fattr);
+    if ((e = cudaGetLastError())) return e;
+    if (marks && (e = cudaEventRecord(marks[KG_ZSUM], st))) return e;
+    k_zsum<<<c->zblocks, 512, 0, st>>>(n, c->Zi, c->zpart, c->sc);
+    if ((e = cudaGetLastError())) return e;
+    if (marks && (e = cudaEventRecord(marks[KG_COUNT], st))) return e;
+    return cudaSuccess;
+}
+
+// Eq. cost_func: C = sum_ij p_ij ln(p_ij Z / w_ij)
+//                  = sum p (ln p - ln w) + (sum p) ln Z,
+// one warp per row, FP32 terms accumulated in FP64, fixed order.
+__global__ void __launch_bounds__(256)
+    k_kl(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+         const float *__restrict__ val, const uint2 *__restrict__ z, DevScalars *sc,
+         double *__restrict__ part, double *out) {
+    __shared__ double s_red[8];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31;
+    const int warps_total = gridDim.x * (blockDim.x >> 5);
+    const float sf0 = sc->sf[0], sf1 = sc->sf[1];
+    double acc = 0.0, psum = 0.0;
+    for (int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < n;
+         row += warps_total) {
+        const uint2 zi = z[row];
+        for (int64_t e = rp[row] + lane; e < rp[row + 1]; e += 32) {
+            const float p = val[e];
+            if (!(p > 0.f)) continue;
+            const uint2 zj = z[col[e]];
+            const float dx = (float)((int64_t)zi.x - (int64_t)zj.x) * sf0;
+            const float dy = (float)((int64_t)zi.y - (int64_t)zj.y) * sf1;
+            acc += (double)(p * (logf(p) + log1pf(fmaf(dx, dx, dy * dy))));
+            psum += (double)p;
+        }
+    }
+    const double a = block_sum_f64(acc, s_red);
+    const double ps = block_sum_f64(psum, s_red);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = ps;
+        __threadfence();
+        const unsigned tk = atomicAdd(&sc->ticket2, 1u);
+        s_last = (tk == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        double A = 0.0, S = 0.0;
+        volatile double *vp = part;
+        for (int k = 0; k < (int)gridDim.x; k++) {
+            A += vp[2 * k];
+            S += vp[2 * k + 1];
+        }
+        *out = A + S * log(sc->Z);
+        sc->ticket2 = 0u;
+    }
+}
+
+cudaError_t launch_kl(pxsne_ctx *c, double *out_dev) {
+    k_kl<<<c->klblocks, 256, 0, c->stream>>>((int)c->n, c->rp, c->col, c->val, c->z, c->sc,
+                                             c->klpart, out_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace pxsne

@@ -1,0 +1,459 @@
+// Pixel-aligned quadtree of PixelSNE (Sec. 4.1) and the screen-driven rescale
+// (Sec. 4.2), built every iteration as a dense Morton-ordered pyramid.
+//
+//   k_snap_hist   rescale zhat -> z (exact integer, Sec. 4.2), pixel snap
+//                 (Eq. z1), leaf histogram of counts and exact coordinate sums
+//   k_pyr_pass    bottom-up reduction, 5 levels per CTA pass, writing the
+//                 16-byte cell records the traversal reads
+//   k_scan1 / k_perm_scatter   counting sort of the points by pixel Morton key
+//                 (the traversal order of the next kernels)
+#include <cmath>
+#include <cstdio>
+
+#include "common.cuh"
+
+namespace pxsne {
+
+// floor(a * 2^32 / gamma) for 0 <= a < gamma < 2^61, exactly: a double
+// estimate within one of the quotient, then a remainder correction in
+// wrapping 64-bit arithmetic (the true remainder is within +-3 gamma).
+__device__ __forceinline__ uint32_t rescale_exact(u64 a, u64 gamma, double q) {
+    u64 q0 = (u64)((double)a * q);
+    if (q0 > 0xffffffffull) q0 = 0xffffffffull;
+    i64 r = (i64)((a << 32) - q0 * gamma);
+#pragma unroll 1
+    for (int k = 0; k < 4 && r < 0; k++) { q0--; r += (i64)gamma; }
+#pragma unroll 1
+    for (int k = 0; k < 4 && (u64)r >= gamma; k++) { q0++; r -= (i64)gamma; }
+    return (uint32_t)q0;
+}
+
+__global__ void k_snap_hist(int n, int L, int rescale, float theta,
+                            const longlong2 *__restrict__ zhat, uint2 *__restrict__ z,
+                            const uint32_t *__restrict__ perm, uint32_t *__restrict__ rank,
+                            uint32_t *__restrict__ cnt, u64 *__restrict__ sx,
+                            u64 *__restrict__ sy, DevScalars *sc) {
+    const int F = 32 - L;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int par = sc->t & 1;
+    i64 mnx = 0, mny = 0;
+    u64 gx = 1, gy = 1;
+    double qx = 0.0, qy = 0.0;
+    if (rescale) {
+        mnx = sc->mm[par][0];
+        mny = sc->mm[par][1];
+        gx = (u64)(sc->mm[par][2] - mnx) + 1ull;
+        gy = (u64)(sc->mm[par][3] - mny) + 1ull;
+        qx = kR / (double)gx;
+        qy = kR / (double)gy;
+        if (tid == 0) {
+            sc->n_accept = 0ull;
+            sc->n_test = 0ull;
+            // Eq. beta_scaling carried as s_d <- s_d * gamma_d / 2^32
+            sc->s[0] = sc->s[0] * ldexp((double)gx, -32);
+            sc->s[1] = sc->s[1] * ldexp((double)gy, -32);
+            derive_scalars(sc, theta, L);
+            sc->mm[par ^ 1][0] = 0x7fffffffffffffffll;
+            sc->mm[par ^ 1][1] = 0x7fffffffffffffffll;
+            sc->mm[par ^ 1][2] = (i64)0x8000000000000000ull;
+            sc->mm[par ^ 1][3] = (i64)0x8000000000000000ull;
+        }
+    }
+    if (!rescale && tid == 0) {
+        sc->n_accept = 0ull;
+        sc->n_test = 0ull;
+    }
+    if (tid >= n) return;
+    const uint32_t i = perm[tid];
+    uint32_t zx, zy;
+    if (rescale) {
+        longlong2 h = zhat[i];
+        zx = rescale_exact((u64)(h.x - mnx), gx, qx);
+        zy = rescale_exact((u64)(h.y - mny), gy, qy);
+        z[i] = make_uint2(zx, zy);
+    } else {
+        uint2 v = z[i];
+        zx = v.x;
+        zy = v.y;
+    }
+    const uint32_t m = morton2(zx >> F, zy >> F);
+    rank[i] = atomicAdd(&cnt[m], 1u);
+    atomicAdd(&sx[m], (u64)zx);
+    atomicAdd(&sy[m], (u64)zy);
+}
+
+// Centre-of-mass record of a cell (layout in common.cuh).
+__device__ __forceinline__ uint4 make_record(uint32_t N, u64 Sx, u64 Sy) {
+    if (N == 0) return make_uint4(0u, 0u, 0u, 0u);
+    const u64 qx = Sx / N, qy = Sy / N;
+    const uint32_t rx = (uint32_t)(Sx - qx * N), ry = (uint32_t)(Sy - qy * N);
+    const float fN = (float)N;
+    const float lox = (float)(uint32_t)(qx & 0xffffu) + (float)rx / fN;
+    const float loy = (float)(uint32_t)(qy & 0xffffu) + (float)ry / fN;
+    const uint32_t hi = (uint32_t)(qx >> 16) | ((uint32_t)(qy >> 16) << 16);
+    return make_uint4(hi, __float_as_uint(lox), __float_as_uint(loy), N);
+}
+
+// Block-wide exclusive scan of one value per thread (nt threads, nt <= 1024).
+__device__ uint32_t block_excl_scan(uint32_t v, int nt, uint32_t *s_warp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned mask = nt >= 32 ? 0xffffffffu : ((1u << nt) - 1u);
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(mask, x, o);
+        if (lane >= o) x += y;
+    }
+    if (nt <= 32) return x - v;
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = nt >> 5;
+        uint32_t w = lane < nw ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < nw) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t before = warp > 0 ? s_warp[warp - 1] : 0u;
+    __syncthreads();
+    return before + x - v;
+}
+
+// One bottom-up pass: reads the sums of level h for 4^K consecutive cells per
+// CTA (an aligned 2^K x 2^K block), writes the records of levels h .. h-K+1
+// (and of level h-K when `top`), and the sums of level h-K (one cell per CTA).
+// With leaf_start != NULL it also writes the exclusive scan of the counts of
+// level h within each CTA (the local start of each pixel in Morton order).
+template <int K>
+__global__ void __launch_bounds__(1 << (2 * (K - 1)))
+    k_pyr_pass(int h, int top, const uint32_t *__restrict__ in_cnt,
+               const u64 *__restrict__ in_sx, const u64 *__restrict__ in_sy,
+               uint4 *__restrict__ rec, uint32_t *__restrict__ out_cnt,
+               u64 *__restrict__ out_sx, u64 *__restrict__ out_sy,
+               uint32_t *__restrict__ leaf_start, DevScalars *sc, int bump_t) {
+    constexpr int NT = 1 << (2 * (K - 1));
+    __shared__ uint32_t s_c[NT];
+    __shared__ u64 s_x[NT], s_y[NT];
+    __shared__ uint32_t s_warp[32];
+    const int tid = threadIdx.x;
+    const int64_t b = blockIdx.x;
+    const int64_t cell0 = b * (NT * 4) + 4 * tid;
+    const uint4 c4 = reinterpret_cast<const uint4 *>(in_cnt)[cell0 >> 2];
+    const ulonglong2 x01 = reinterpret_cast<const ulonglong2 *>(in_sx)[cell0 >> 1];
+    const ulonglong2 x23 = reinterpret_cast<const ulonglong2 *>(in_sx)[(cell0 >> 1) + 1];
+    const ulonglong2 y01 = reinterpret_cast<const ulonglong2 *>(in_sy)[cell0 >> 1];
+    const ulonglong2 y23 = reinterpret_cast<const ulonglong2 *>(in_sy)[(cell0 >> 1) + 1];
+    uint4 *rl = rec + level_offset(h) + cell0;
+    rl[0] = make_record(c4.x, x01.x, y01.x);
+    rl[1] = make_record(c4.y, x01.y, y01.y);
+    rl[2] = make_record(c4.z, x23.x, y23.x);
+    rl[3] = make_record(c4.w, x23.y, y23.y);
+    uint32_t N = c4.x + c4.y + c4.z + c4.w;
+    u64 X = x01.x + x01.y + x23.x + x23.y;
+    u64 Y = y01.x + y01.y + y23.x + y23.y;
+    if (leaf_start != nullptr) {
+        const uint32_t e = block_excl_scan(N, NT, s_warp);
+        uint4 st;
+        st.x = e;
+        st.y = e + c4.x;
+        st.z = st.y + c4.y;
+        st.w = st.z + c4.z;
+        reinterpret_cast<uint4 *>(leaf_start)[cell0 >> 2] = st;
+    }
+    int lvl = h - 1;
+    int64_t idx = b * NT + tid;
+#pragma unroll
+    for (int j = K - 1; j >= 0; j--) {
+        const int cells = 1 << (2 * j);
+        if (tid < cells) {
+            if (j > 0 || top) rec[level_offset(lvl) + idx] = make_record(N, X, Y);
+            if (j == 0) {
+                out_cnt[b] = N;
+                out_sx[b] = X;
+                out_sy[b] = Y;
+            }
+        }
+        if (j == 0) break;
+        __syncthreads();
+        if (tid < cells) {
+            s_c[tid] = N;
+            s_x[tid] = X;
+            s_y[tid] = Y;
+        }
+        __syncthreads();
+        if (tid < (cells >> 2)) {
+            const int a = 4 * tid;
+            N = s_c[a] + s_c[a + 1] + s_c[a + 2] + s_c[a + 3];
+            X = s_x[a] + s_x[a + 1] + s_x[a + 2] + s_x[a + 3];
+            Y = s_y[a] + s_y[a + 1] + s_y[a + 2] + s_y[a + 3];
+        }
+        lvl--;
+        idx = b * (cells >> 2) + tid;
+    }
+    if (bump_t && b == 0 && tid == 0) sc->t += 1;
+}
+
+// Exclusive scan of m values in one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan1(const uint32_t *__restrict__ in,
+                                                uint32_t *__restrict__ out, int64_t m) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < m; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        const uint32_t v = i < m ? in[i] : 0u;
+        const uint32_t e = block_excl_scan(v, 1024, s_warp);
+        const uint32_t carry = s_carry;
+        if (i < m) out[i] = carry + e;
+        __syncthreads();
+        if (threadIdx.x == 1023) s_carry = carry + e + v;
+        __syncthreads();
+    }
+}
+
+__global__ void k_perm_scatter(int n, int L, int K1, const uint2 *__restrict__ z,
+                               const uint32_t *__restrict__ rank,
+                               const uint32_t *__restrict__ leaf_start,
+                               const uint32_t *__restrict__ blk_off,
+                               uint32_t *__restrict__ perm, DevScalars *sc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int F = 32 - L;
+    const uint2 v = z[i];
+    const uint32_t m = morton2(v.x >> F, v.y >> F);
+    const uint32_t pos = blk_off[m >> (2 * K1)] + leaf_start[m] + rank[i];
+    if (pos < (uint32_t)n) perm[pos] = (uint32_t)i;
+    else atomicOr(&sc->err, (unsigned)PXSNE_DEVERR_STACK);
+}
+
+static cudaError_t pyr_pass(int K, int64_t blocks, cudaStream_t st, int h, int top,
+                            const uint32_t *ic, const u64 *ix, const u64 *iy, uint4 *rec,
+                            uint32_t *oc, u64 *ox, u64 *oy, uint32_t *ls, DevScalars *sc,
+                            int bump) {
+    const dim3 g((unsigned)blocks);
+    switch (K) {
+    case 1: k_pyr_pass<1><<<g, 1, 0, st>>>(h, top, ic, ix, iy, rec, oc, ox, oy, ls, sc, bump); break;
+    case 2: k_pyr_pass<2><<<g, 4, 0, st>>>(h, top, ic, ix, iy, rec, oc, ox, oy, ls, sc, bump); break;
+    case 3: k_pyr_pass<3><<<g, 16, 0, st>>>(h, top, ic, ix, iy, rec, oc, ox, oy, ls, sc, bump); break;
+    case 4: k_pyr_pass<4><<<g, 64, 0, st>>>(h, top, ic, ix, iy, rec, oc, ox, oy, ls, sc, bump); break;
+    default: k_pyr_pass<5><<<g, 256, 0, st>>>(h, top, ic, ix, iy, rec, oc, ox, oy, ls, sc, bump); break;
+    }
+    return cudaGetLastError();
+}
+
+// Tree of the current state.  rescale != 0: zhat -> z first (an iteration);
+// otherwise z is taken as it is (initial state).  Also rebuilds the traversal
+// order and, for an iteration, advances the iteration counter.
+cudaError_t launch_tree(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
+    cudaStream_t st = c->stream;
+    const int L = c->L;
+    const int64_t leaves = int64_t(1) << (2 * L);
+    cudaError_t e;
+    if (marks && (e = cudaEventRecord(marks[KG_SNAP], st))) return e;
+    if ((e = cudaMemsetAsync(c->leaf_cnt, 0, leaves * sizeof(uint32_t), st))) return e;
+    if ((e = cudaMemsetAsync(c->leaf_sx, 0, leaves * sizeof(u64), st))) return e;
+    if ((e = cudaMemsetAsync(c->leaf_sy, 0, leaves * sizeof(u64), st))) return e;
+    const int n = (int)c->n;
+    k_snap_hist<<<(n + 255) / 256, 256, 0, st>>>(n, L, rescale ? 1 : 0, c->p.theta, c->zhat,
+                                                 c->z, c->perm, c->rank, c->leaf_cnt,
+                                                 c->leaf_sx, c->leaf_sy, c->sc);
+    if ((e = cudaGetLastError())) return e;
+    if (marks && (e = cudaEventRecord(marks[KG_PYRAMID], st))) return e;
+    // bottom-up passes
+    int h = L;
+    const int K1 = L < kPyrK ? L : kPyrK;
+    int cur = 0;
+    {
+        const int64_t blocks = leaves >> (2 * K1);
+        const int top = (h - K1 == 0);
+        if ((e = pyr_pass(K1, blocks, st, h, top, c->leaf_cnt, c->leaf_sx, c->leaf_sy, c->rec,
+                          c->lvl_cnt[0], c->lvl_sx[0], c->lvl_sy[0], c->leaf_start, c->sc,
+                          (rescale && top) ? 1 : 0)))
+            return e;
+        h -= K1;
+    }
+    // traversal order: scan of the per-CTA pixel totals of the first pass
+    k_scan1<<<1, 1024, 0, st>>>(c->lvl_cnt[0], c->blk_off, int64_t(1) << (2 * h));
+    if ((e = cudaGetLastError())) return e;
+    while (h > 0) {
+        const int K = h < kPyrK ? h : kPyrK;
+        const int64_t blocks = (int64_t(1) << (2 * h)) >> (2 * K);
+        const int top = (h - K == 0);
+        if ((e = pyr_pass(K, blocks, st, h, top, c->lvl_cnt[cur], c->lvl_sx[cur],
+                          c->lvl_sy[cur], c->rec, c->lvl_cnt[cur ^ 1], c->lvl_sx[cur ^ 1],
+                          c->lvl_sy[cur ^ 1], nullptr, c->sc, (rescale && top) ? 1 : 0)))
+            return e;
+        cur ^= 1;
+        h -= K;
+    }
+    if (marks && (e = cudaEventRecord(marks[KG_PERM], st))) return e;
+    k_perm_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, L, K1, c->z, c->rank, c->leaf_start,
+                                                    c->blk_off, c->perm, c->sc);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- init / output
+__device__ __forceinline__ uint32_t f2key(float f) {
+    uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key2f(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+__global__ void k_minmax_y0(int n, const float2 *__restrict__ Y, uint32_t *mm,
+                            DevScalars *sc) {
+    uint32_t mnx = 0xffffffffu, mny = 0xffffffffu, mxx = 0u, mxy = 0u;
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float2 y = Y[i];
+        bad |= !isfinite(y.x) || !isfinite(y.y);
+        const uint32_t kx = f2key(y.x), ky = f2key(y.y);
+        mnx = min(mnx, kx); mxx = max(mxx, kx);
+        mny = min(mny, ky); mxy = max(mxy, ky);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mnx = min(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+        mny = min(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+        mxx = max(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+        mxy = max(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&mm[0], mnx); atomicMin(&mm[1], mny);
+        atomicMax(&mm[2], mxx); atomicMax(&mm[3], mxy);
+    }
+    if (bad) atomicOr(&sc->err, (unsigned)PXSNE_DEVERR_NONFINITE);
+}
+
+// Eq. z1/z2 mapping of the initial embedding onto the fixed-point screen (FP64).
+__global__ void k_map_y0(int n, int L, float theta, const float2 *__restrict__ Y,
+                         const uint32_t *__restrict__ mm, uint2 *__restrict__ z,
+                         float2 *__restrict__ u, float2 *__restrict__ gains, DevScalars *sc) {
+    const double mnx = (double)key2f(mm[0]), mny = (double)key2f(mm[1]);
+    const double rx = (double)key2f(mm[2]) - mnx, ry = (double)key2f(mm[3]) - mny;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) {
+        sc->s[0] = rx > 0.0 ? rx / kR : 1.0 / kR;
+        sc->s[1] = ry > 0.0 ? ry / kR : 1.0 / kR;
+        derive_scalars(sc, theta, L);
+        sc->t = 0;
+        sc->Z = 0.0;
+        for (int p = 0; p < 2; p++) {
+            sc->mm[p][0] = 0x7fffffffffffffffll;
+            sc->mm[p][1] = 0x7fffffffffffffffll;
+            sc->mm[p][2] = (i64)0x8000000000000000ull;
+            sc->mm[p][3] = (i64)0x8000000000000000ull;
+        }
+    }
+    if (i >= n) return;
+    const float2 y = Y[i];
+    uint32_t zx = 0u, zy = 0u;
+    if (rx > 0.0) {
+        const double q = floor(((double)y.x - mnx) * kR / rx);
+        zx = q >= kR - 1.0 ? 0xffffffffu : (uint32_t)q;
+    }
+    if (ry > 0.0) {
+        const double q = floor(((double)y.y - mny) * kR / ry);
+        zy = q >= kR - 1.0 ? 0xffffffffu : (uint32_t)q;
+    }
+    z[i] = make_uint2(zx, zy);
+    u[i] = make_float2(0.f, 0.f);
+    gains[i] = make_float2(1.f, 1.f);
+}
+
+cudaError_t launch_init_map(pxsne_ctx *c, const float *Y0dev, uint32_t *mm_scratch) {
+    cudaStream_t st = c->stream;
+    const int n = (int)c->n;
+    const uint32_t init[4] = {0xffffffffu, 0xffffffffu, 0u, 0u};
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(mm_scratch, init, sizeof(init), cudaMemcpyHostToDevice, st)))
+        return e;
+    const int blocks = (n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184;
+    k_minmax_y0<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(
+        n, reinterpret_cast<const float2 *>(Y0dev), mm_scratch, c->sc);
+    if ((e = cudaGetLastError())) return e;
+    k_map_y0<<<(n + 255) / 256, 256, 0, st>>>(n, c->L, c->p.theta,
+                                              reinterpret_cast<const float2 *>(Y0dev),
+                                              mm_scratch, c->z, c->u, c->gains, c->sc);
+    return cudaGetLastError();
+}
+
+__global__ void k_sum_z(int n, const uint2 *__restrict__ z, u64 *sums) {
+    u64 ax = 0, ay = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint2 v = z[i];
+        ax += v.x;
+        ay += v.y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&sums[0], ax);
+        atomicAdd(&sums[1], ay);
+    }
+}
+
+__global__ void k_write_y(int n, int L, const uint2 *__restrict__ z, const u64 *__restrict__ sums,
+                          const DevScalars *__restrict__ sc, float2 *__restrict__ Y,
+                          int2 *__restrict__ pix) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint2 v = z[i];
+    if (Y) {
+        const double mx = (double)sums[0] / (double)n, my = (double)sums[1] / (double)n;
+        Y[i] = make_float2((float)(sc->s[0] * ((double)v.x - mx)),
+                           (float)(sc->s[1] * ((double)v.y - my)));
+    }
+    if (pix) pix[i] = make_int2((int)(v.x >> (32 - L)), (int)(v.y >> (32 - L)));
+}
+
+cudaError_t launch_centre_y(pxsne_ctx *c, float *Ydev, int32_t *pixdev, float *scratch) {
+    cudaStream_t st = c->stream;
+    const int n = (int)c->n;
+    u64 *sums = reinterpret_cast<u64 *>(scratch);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(sums, 0, 2 * sizeof(u64), st))) return e;
+    const int blocks = (n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184;
+    k_sum_z<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(n, c->z, sums);
+    if ((e = cudaGetLastError())) return e;
+    k_write_y<<<(n + 255) / 256, 256, 0, st>>>(n, c->L, c->z, sums, c->sc,
+                                               reinterpret_cast<float2 *>(Ydev),
+                                               reinterpret_cast<int2 *>(pixdev));
+    return cudaGetLastError();
+}
+
+__global__ void k_level_counts(int64_t cells, const uint4 *__restrict__ rec, uint32_t *cnt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < cells) cnt[i] = rec[i].w;
+}
+
+cudaError_t launch_level_counts(pxsne_ctx *c, int level, uint32_t *cnt) {
+    const int64_t cells = int64_t(1) << (2 * level);
+    k_level_counts<<<(unsigned)((cells + 255) / 256), 256, 0, c->stream>>>(
+        cells, c->rec + level_offset(level), cnt);
+    return cudaGetLastError();
+}
+
+__global__ void k_morton_keys(int n, int L, const uint2 *__restrict__ z, uint32_t *keys) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint2 v = z[i];
+    keys[i] = morton2(v.x >> (32 - L), v.y >> (32 - L));
+}
+
+cudaError_t launch_morton_keys(pxsne_ctx *c, uint32_t *keys) {
+    const int n = (int)c->n;
+    k_morton_keys<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->L, c->z, keys);
+    return cudaGetLastError();
+}
+
+}  // namespace pxsne

@@ -1,0 +1,265 @@
+"""GPU path vs the CPU oracle, through the C ABI, on the same seeded inputs.
+
+Bars (written in each test):
+  tree (pixels, Morton keys, counts, exact coordinate sums)  bit-exact
+  forces Frep, Zi, Fattr, Z                                  <= 1e-4 relative L2
+  final KL of a full run                                     <= 1 % of the oracle's
+  fixed-point init / rescale                                  bit-exact
+"""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+FORCE_TOL = 1e-4
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def px():
+    import paper_1611_02568_gb300 as m
+    from paper_1611_02568_gb300 import build
+    build.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def gauss():
+    """Config-1 workload: oracle P and an oracle state after 60 iterations
+    (clustered under exaggeration)."""
+    X, lab = datagen.gauss10(0)
+    P, idx, d2, bad = oracle.affinities(X, 30.0, 90)
+    assert bad == 0
+    Y0 = datagen.init_y0(0, X.shape[0])
+    st = oracle.State.from_y0(Y0)
+    oracle.run(P, st, oracle.Params(L=9), 60)
+    return X, P, Y0, st
+
+
+def make_ctx(px, L=9, **kw):
+    return px.Context(px.Params(log2_r=L, **kw))
+
+
+def inject(ctx, P, st):
+    ctx.set_P(P.row_ptr, P.col, P.val.astype(np.float32))
+    ctx.set_state(st.z, st.s, st.u.astype(np.float32), st.gains.astype(np.float32), st.t)
+
+
+def check_tree(ctx, z, L):
+    cnt_o, sx_o, sy_o = oracle.pyramid(z, L)
+    for l in range(L + 1):
+        cnt, sx, sy, _ = ctx.get_tree(l, sums=(l == L))
+        off = oracle.level_offset(l)
+        assert np.array_equal(cnt, cnt_o[off:off + 4 ** l]), f"level {l} counts"
+        if l == L:
+            assert np.array_equal(sx, sx_o[off:off + 4 ** l])
+            assert np.array_equal(sy, sy_o[off:off + 4 ** l])
+    _, _, _, mk = ctx.get_tree(0, morton=True)
+    _, _, mo = oracle.leaf_keys(z, L)
+    assert np.array_equal(mk, mo)
+
+
+def test_init_maps_y0_bit_exact(px):
+    n = 1537
+    Y0 = datagen.init_y0(3, n)
+    X = np.random.default_rng(0).standard_normal((n, 4)).astype(np.float32)
+    with make_ctx(px, L=10, k=5, perplexity=3.0) as ctx:
+        ctx.affinities(X)
+        ctx.init(Y0)
+        z, s, u, g, t = ctx.get_state()
+        zo, so = oracle.init_fx(Y0.astype(np.float64))
+        assert np.array_equal(z, zo) and np.array_equal(s, so)
+        assert t == 0 and np.all(u == 0) and np.all(g == 1)
+        check_tree(ctx, z, 10)
+
+
+@pytest.mark.parametrize("L", [1, 4, 5, 6, 9, 11])
+def test_tree_bit_exact(px, gauss, L):
+    X, P, Y0, st = gauss
+    rng = np.random.default_rng(L)
+    n = P.n
+    z = st.z.copy()
+    z[:300] = z[0]                      # one very hot pixel
+    z[300:310] = rng.integers(0, 2 ** 32, (10, 2), dtype=np.uint64).astype(np.uint32)
+    z[310, :] = 0
+    z[311, :] = 0xFFFFFFFF             # screen corners
+    with make_ctx(px, L=L) as ctx:
+        ctx.set_P(P.row_ptr, P.col, P.val.astype(np.float32))
+        ctx.set_state(z, st.s)
+        check_tree(ctx, z, L)
+
+
+@pytest.mark.parametrize("theta", [0.5, 0.0, 0.25, 1.0])
+def test_forces_match_oracle(px, gauss, theta):
+    X, P, Y0, st = gauss
+    L = 9
+    with make_ctx(px, L=L, theta=theta) as ctx:
+        inject(ctx, P, st)
+        Frep, Zi, Fattr, Z = ctx.get_forces()
+    oF, oZi, _ = oracle.bh_repulsion(st.z, st.s, L, theta)
+    oA = oracle.attraction(P, st.z, st.s)
+    assert rel(Frep, oF) <= FORCE_TOL
+    assert rel(Zi, oZi) <= FORCE_TOL
+    assert rel(Fattr, oA) <= FORCE_TOL
+    assert abs(Z - oZi.sum()) / oZi.sum() <= FORCE_TOL
+
+
+def test_forces_geometric_centre_mode(px, gauss):
+    X, P, Y0, st = gauss
+    with make_ctx(px, L=9, centre_mode=1) as ctx:
+        inject(ctx, P, st)
+        Frep, Zi, _, _ = ctx.get_forces()
+    oF, oZi, _ = oracle.bh_repulsion(st.z, st.s, 9, 0.5, centre_mode=1)
+    assert rel(Frep, oF) <= FORCE_TOL
+    assert rel(Zi, oZi) <= FORCE_TOL
+
+
+def test_one_step_matches_oracle(px, gauss):
+    X, P, Y0, st = gauss
+    L = 9
+    params = oracle.Params(L=L)
+    with make_ctx(px, L=L) as ctx:
+        inject(ctx, P, st)
+        ctx.step(1)
+        z, s, u, g, t = ctx.get_state()
+    so = st.copy()
+    oracle.run(P, so, params, 1)
+    assert t == so.t
+    assert np.allclose(s, so.s, rtol=1e-6)
+    # positions after one step: the FP32 forces move points by < 1e-4 of a step
+    y, yo = z * s, so.z * so.s
+    step = np.abs(so.u).max()
+    assert np.abs((y - y.mean(0)) - (yo - yo.mean(0))).max() <= 1e-3 * step + 4 * so.s.max()
+    assert rel(u, so.u) <= 1e-3
+
+
+def test_full_run_kl_within_one_percent(px, gauss):
+    """Config 1 (n=2000, 512^2, 500 iterations): injected oracle P, same Y0."""
+    X, P, Y0, _ = gauss
+    params = oracle.Params(L=9)
+    st = oracle.State.from_y0(Y0)
+    oracle.run(P, st, params, 500)
+    kl_o = oracle.kl_of(P, st, params)
+    with make_ctx(px, L=9) as ctx:
+        ctx.set_P(P.row_ptr, P.col, P.val.astype(np.float32))
+        ctx.init(Y0)
+        ctx.step(500)
+        kl_g = ctx.kl()
+        z, s, _, _, t = ctx.get_state()
+    assert t == 500
+    # the GPU's own KL evaluation against the oracle's on the GPU's final state
+    kl_o_on_g = oracle.kl_of(P, oracle.State(z, s, None, None), params)
+    assert abs(kl_g - kl_o_on_g) <= 1e-4 * kl_o_on_g
+    assert abs(kl_g - kl_o) <= 0.01 * kl_o, (kl_g, kl_o)
+
+
+def test_affinities_match_oracle(px):
+    X, _ = datagen.gauss10(1, n=1500)
+    k, u = 90, 30.0
+    P, idx_o, d2_o, bad = oracle.affinities(X, u, k)
+    with make_ctx(px, L=9, k=k, perplexity=u) as ctx:
+        ctx.affinities(X)
+        idx, d2, beta = ctx.get_knn()
+        rp, col, val = ctx.get_P()
+    n = X.shape[0]
+    # neighbour sets: what is unique must match; ties within FP32 error are valid
+    tol = 2e-5
+    for i in range(n):
+        dk = d2_o[i, -1]
+        must = set(idx_o[i][d2_o[i] < dk * (1 - tol)])
+        got = set(idx[i])
+        assert must <= got, i
+        # every returned neighbour is within tolerance of the true k-th distance
+        dd = ((X[idx[i]].astype(np.float64) - X[i].astype(np.float64)) ** 2).sum(1)
+        assert np.all(dd <= dk * (1 + tol)), i
+        np.testing.assert_allclose(d2[i], np.sort(dd), rtol=1e-5)
+    # perplexity of each GPU row, evaluated in FP64 from its own d2 and beta
+    e = np.exp(-beta[:, None].astype(np.float64) * (d2 - d2[:, :1]))
+    p = e / e.sum(1, keepdims=True)
+    H = -(p * np.log(p)).sum(1)
+    assert np.abs(H - np.log(u)).max() < 1e-4
+    # symmetric P: same pattern, values within the bisection tolerance
+    assert np.array_equal(rp, P.row_ptr) and np.array_equal(col, P.col)
+    np.testing.assert_allclose(val, P.val, rtol=2e-3, atol=1e-9)
+    assert abs(val.astype(np.float64).sum() - 1.0) < 1e-5
+
+
+def test_full_gpu_path_kl(px):
+    """Whole GPU path (P built on the GPU) vs the oracle's whole path."""
+    X, _ = datagen.gauss10(0)
+    Y0 = datagen.init_y0(0, X.shape[0])
+    params = oracle.Params(L=9)
+    P, _, _, _ = oracle.affinities(X, 30.0, 90)
+    st = oracle.State.from_y0(Y0)
+    oracle.run(P, st, params, 500)
+    kl_o = oracle.kl_of(P, st, params)
+    with make_ctx(px, L=9) as ctx:
+        ctx.affinities(X)
+        ctx.init(Y0)
+        ctx.step(500)
+        kl_g = ctx.kl()
+    assert abs(kl_g - kl_o) <= 0.01 * kl_o, (kl_g, kl_o)
+
+
+def test_get_Y_and_pixels(px, gauss):
+    X, P, Y0, st = gauss
+    with make_ctx(px, L=9) as ctx:
+        inject(ctx, P, st)
+        Y, pix = ctx.get_Y()
+    assert np.array_equal(pix, (st.z >> (32 - 9)).astype(np.int32))
+    y = st.y()
+    np.testing.assert_allclose(Y, y - y.mean(0), rtol=0, atol=1e-6 * np.abs(y).max())
+
+
+def test_edge_cases(px):
+    # two points (k = 1), both in one pixel, then apart
+    P = oracle.CSR(np.array([0, 1, 2]), np.array([1, 0], np.int32), np.array([0.5, 0.5]))
+    with make_ctx(px, L=3, k=1, perplexity=1.0) as ctx:
+        ctx.set_P(P.row_ptr, P.col, P.val.astype(np.float32))
+        for z in (np.array([[5, 5], [5, 5]], np.uint32),
+                  np.array([[0, 0], [2 ** 32 - 1, 2 ** 32 - 1]], np.uint32)):
+            s = np.array([1e-9, 2e-9])
+            ctx.set_state(z, s)
+            Frep, Zi, Fattr, Z = ctx.get_forces()
+            oF, oZi, _ = oracle.bh_repulsion(z, s, 3, 0.5)
+            np.testing.assert_allclose(Frep, oF, rtol=1e-5, atol=1e-30)
+            np.testing.assert_allclose(Zi, oZi, rtol=1e-6)
+            ctx.step(3)
+            assert np.isfinite(ctx.kl())
+    # ragged n (not a multiple of the warp or CTA), all points in one pixel
+    n = 1001
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((n, 3)).astype(np.float32)
+    Po, _, _, _ = oracle.affinities(X, 5.0, 15)
+    z = np.full((n, 2), 123456789, np.uint32)
+    z[:, 0] += np.arange(n, dtype=np.uint32)
+    s = np.array([1e-6, 1e-6])
+    with make_ctx(px, L=11, k=15, perplexity=5.0) as ctx:
+        ctx.set_P(Po.row_ptr, Po.col, Po.val.astype(np.float32))
+        ctx.set_state(z, s)
+        check_tree(ctx, z, 11)
+        Frep, Zi, Fattr, Z = ctx.get_forces()
+        oF, oZi, _ = oracle.bh_repulsion(z, s, 11, 0.5)
+        assert rel(Frep, oF) <= FORCE_TOL and rel(Zi, oZi) <= FORCE_TOL
+        ctx.step(5)
+        assert ctx.sync() == 0
+
+
+def test_invalid_calls(px):
+    with make_ctx(px, L=9) as ctx:
+        with pytest.raises(px.PxsneError):
+            ctx.step(1)                     # no state
+        with pytest.raises(px.PxsneError):
+            ctx.init(np.zeros((10, 2), np.float32))   # no P
+        X = np.zeros((50, 3), np.float32)
+        X[3, 1] = np.nan
+        with pytest.raises(px.PxsneError):
+            ctx.affinities(X)
+        with pytest.raises(px.PxsneError):
+            ctx.affinities(np.zeros((50, 300), np.float32))   # D > 256
