@@ -207,6 +207,38 @@ int pxsne_get_counters(pxsne_ctx *ctx, uint64_t *n_accept, uint64_t *n_test);
 /* Total bytes of device memory the context holds. */
 int64_t pxsne_device_bytes(const pxsne_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free KL.  The paper has no counterpart: this is a service for
+ * callers that cannot call cudaMalloc/cudaFree, e.g. code running while a
+ * framework's caching allocator owns the device memory, or a loop that must not
+ * take the implicit device synchronisation those calls imply.
+ *
+ * Computes the same value as pxsne_kl for the embedding given by the caller:
+ * C = sum_ij p_ij ln(p_ij Z / w_ij), w_ij = 1 / (1 + s0^2 dz_x^2 + s1^2 dz_y^2),
+ * enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream) of
+ * the current device.  All pointers are device pointers owned by the caller:
+ * row_ptr[n+1] int64 and col[nnz] int32 (values in [0, n)) and val[nnz]
+ * float32 of P, z[n*2] u32 fixed-point positions; s0, s1 > 0 are the y-units
+ * per ulp and Z > 0 the normalisation (e.g. from pxsne_get_forces).  The result
+ * is written to out[0] (device) when the stream reaches it.
+ *
+ * No memory is allocated: the reduction's scratch is one file-scope device
+ * array of 128 KiB (8192 block partials) that every GPU which loads the
+ * library holds until the process exits, so n is limited to
+ * pxsne_kl_noalloc_max_rows() = 16,777,216 rows (larger n returns
+ * PXSNE_E_ARG).  The first call on a device looks the array's address up on
+ * that device (make that first call before any stream capture).  All calls
+ * share the array: calls whose executions overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  Returns
+ * PXSNE_E_ARG for bad arguments and PXSNE_E_CUDA if the launch fails; there is
+ * no context, so no message is kept. */
+int pxsne_kl_noalloc(const int64_t *row_ptr, const int32_t *col, const float *val, int64_t n,
+                     const uint32_t *z, double s0, double s1, double Z, double *out,
+                     void *stream);
+
+/* Largest n that pxsne_kl_noalloc accepts. */
+int64_t pxsne_kl_noalloc_max_rows(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -308,4 +308,4 @@ EXPORTED = ["pxsne_default_params", "pxsne_create", "pxsne_destroy", "pxsne_last
             "pxsne_sync", "pxsne_get_sizes", "pxsne_get_P", "pxsne_set_P", "pxsne_get_knn",
             "pxsne_set_state", "pxsne_get_state", "pxsne_get_tree", "pxsne_get_forces",
             "pxsne_device_bytes", "pxsne_step_profiled", "pxsne_kernel_group_name",
-            "pxsne_get_counters"]
+            "pxsne_get_counters", "pxsne_kl_noalloc", "pxsne_kl_noalloc_max_rows"]
