@@ -159,11 +159,15 @@ __global__ void __launch_bounds__(kTravWarps * 32)
     }
 }
 
-// Eq. grad, first term: Fattr_i = sum_j p_ij w_ij (y_i - y_j), one warp per row.
+// Eq. grad, first term: Fattr_i = sum_j p_ij w_ij (y_i - y_j), one warp per
+// row.  Each lane keeps four entries in flight (P is streamed with evict-first
+// loads; the positions z_j are gathered from L2), so that enough bytes are
+// outstanding to cover HBM latency.
 __global__ void __launch_bounds__(256)
     k_attract(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
               const float *__restrict__ val, const uint2 *__restrict__ z,
               const DevScalars *__restrict__ sc, float2 *__restrict__ Fattr) {
+    constexpr int U = 4;
     const int lane = threadIdx.x & 31;
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row >= n) return;
@@ -171,16 +175,27 @@ __global__ void __launch_bounds__(256)
     const uint2 zi = z[row];
     const int64_t e0 = rp[row], e1 = rp[row + 1];
     float fx = 0.f, fy = 0.f;
-    for (int64_t e = e0 + lane; e < e1; e += 32) {
-        const int32_t j = __ldg(col + e);
-        const float p = __ldg(val + e);
-        const uint2 zj = z[j];
-        const float dx = (float)((int64_t)zi.x - (int64_t)zj.x) * sf0;
-        const float dy = (float)((int64_t)zi.y - (int64_t)zj.y) * sf1;
-        const float q = 1.0f / (1.0f + fmaf(dx, dx, dy * dy));
-        const float pq = p * q;
-        fx = fmaf(pq, dx, fx);
-        fy = fmaf(pq, dy, fy);
+    for (int64_t e = e0 + lane; e < e1; e += 32 * U) {
+        int32_t j[U];
+        float p[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t q = e + 32 * u;
+            j[u] = q < e1 ? __ldcs(col + q) : row;
+            p[u] = q < e1 ? __ldcs(val + q) : 0.f;
+        }
+        uint2 zj[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) zj[u] = z[j[u]];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const float dx = (float)((int64_t)zi.x - (int64_t)zj[u].x) * sf0;
+            const float dy = (float)((int64_t)zi.y - (int64_t)zj[u].y) * sf1;
+            const float q = 1.0f / (1.0f + fmaf(dx, dx, dy * dy));
+            const float pq = p[u] * q;
+            fx = fmaf(pq, dx, fx);
+            fy = fmaf(pq, dy, fy);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
