@@ -98,7 +98,9 @@ const char *pxsne_last_error(const pxsne_ctx *ctx);
  *   - p_{j|i} proportional to exp(-beta_i d2_ij) with beta_i set by bisection
  *     so that each row's entropy is ln(perplexity);
  *   - p_ij = (p_{j|i} + p_{i|j}) / (2n) on the union pattern, stored as CSR.
- * X: host or device, row-major n x D float32.  perplexity <= 0 uses the
+ * X: host or device, row-major n x D float32, 2 <= n <= 2^24, 1 <= D <= 256
+ * (the shared-memory tiles of the search bound D further for large k; an
+ * unsupported size returns an error).  perplexity <= 0 uses the
  * context's parameter.  Replaces any previous P and clears the embedding
  * state.  Synchronises.  Row convergence failures set PXSNE_DEVERR_BISECT and
  * return PXSNE_E_DEVICE (P is still built from the last bracket). */
@@ -153,8 +155,8 @@ int pxsne_get_sizes(pxsne_ctx *ctx, int64_t *n, int64_t *nnz);
  * int32, val[nnz] float32.  Any pointer may be NULL. */
 int pxsne_get_P(pxsne_ctx *ctx, int64_t *row_ptr, int32_t *col, float *val);
 
-/* Replace P by a caller CSR (row_ptr[n+1] int64, col int32 in [0, n), no
- * self entries; val float32 >= 0).  Clears the embedding state. */
+/* Replace P by a caller CSR (2 <= n <= 2^24; row_ptr[n+1] int64, col int32 in
+ * [0, n), no self entries; val float32 >= 0).  Clears the embedding state. */
 int pxsne_set_P(pxsne_ctx *ctx, int64_t n, const int64_t *row_ptr, const int32_t *col,
                 const float *val);
 

@@ -450,7 +450,16 @@ __global__ void __launch_bounds__(256)
             }
         }
         for (int64_t q = rp[row]; q <= o; q++) val[q] *= inv2n;
+        for (int64_t q = o + 1; q < rp[row + 1]; q++) {  // padding to a multiple of 4
+            col[q] = (int32_t)row;
+            val[q] = 0.f;
+        }
     }
+}
+
+__global__ void k_round4(int64_t n, const uint32_t *in, uint32_t *out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (in[i] + 3u) & ~3u;
 }
 
 __global__ void k_add_const(int64_t n, const uint32_t *in, uint32_t *out, uint32_t a) {
@@ -501,20 +510,33 @@ cudaError_t build_symmetric_csr(pxsne_ctx *c, const int32_t *idx, const float *p
     if (c->rp) { cudaFreeAsync(c->rp, st); c->rp = nullptr; }
     if (c->col) { cudaFreeAsync(c->col, st); c->col = nullptr; }
     if (c->val) { cudaFreeAsync(c->val, st); c->val = nullptr; }
+    if (c->rowlen) { cudaFreeAsync(c->rowlen, st); c->rowlen = nullptr; }
+    // true row lengths and nnz
+    TRY(cudaMallocAsync(&c->rowlen, n * sizeof(int32_t), st));
+    TRY(cudaMemcpyAsync(c->rowlen, ucnt, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    int64_t *uscan = nullptr;
+    TRY(cudaMallocAsync(&uscan, (n + 1) * sizeof(int64_t), st));
+    TRY(scan_u32_to_i64(ucnt, n, uscan, st));
+    int64_t nnz = 0, nnz_pad = 0;
+    TRY(cudaMemcpyAsync(&nnz, uscan + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    // padded offsets
+    k_round4<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ucnt, cursor);
+    TRY(cudaGetLastError());
     TRY(cudaMallocAsync(&c->rp, (n + 1) * sizeof(int64_t), st));
-    TRY(scan_u32_to_i64(ucnt, n, c->rp, st));
-    int64_t nnz = 0;
-    TRY(cudaMemcpyAsync(&nnz, c->rp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    TRY(scan_u32_to_i64(cursor, n, c->rp, st));
+    TRY(cudaMemcpyAsync(&nnz_pad, c->rp + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
-    TRY(cudaMallocAsync(&c->col, (nnz > 0 ? nnz : 1) * sizeof(int32_t), st));
-    TRY(cudaMallocAsync(&c->val, (nnz > 0 ? nnz : 1) * sizeof(float), st));
+    TRY(cudaMallocAsync(&c->col, (nnz_pad > 0 ? nnz_pad : 4) * sizeof(int32_t), st));
+    TRY(cudaMallocAsync(&c->val, (nnz_pad > 0 ? nnz_pad : 4) * sizeof(float), st));
     k_sort_merge<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(
         n, 1, tptr, tcol, tval, scol, sval, ucnt, c->rp, c->col, c->val);
     TRY(cudaGetLastError());
+    c->nnz_pad = nnz_pad;
     c->nnz = nnz;
     cudaFreeAsync(deg, st);
     cudaFreeAsync(cursor, st);
     cudaFreeAsync(tptr, st);
+    cudaFreeAsync(uscan, st);
     cudaFreeAsync(tcol, st);
     cudaFreeAsync(tval, st);
     cudaFreeAsync(scol, st);

@@ -70,7 +70,7 @@ void free_state(pxsne_ctx *c) {
     drop_graph(c);
     dfree(c->z); dfree(c->zhat); dfree(c->u); dfree(c->gains);
     dfree(c->Frep); dfree(c->Zi); dfree(c->Fattr); dfree(c->perm); dfree(c->rank);
-    dfree(c->leaf_cnt); dfree(c->leaf_sx); dfree(c->leaf_sy); dfree(c->rec);
+    dfree(c->leaf_cnt); dfree(c->leaf_sx); dfree(c->leaf_sy); dfree(c->rec); dfree(c->recn);
     for (int k = 0; k < 2; k++) { dfree(c->lvl_cnt[k]); dfree(c->lvl_sx[k]); dfree(c->lvl_sy[k]); }
     dfree(c->leaf_start); dfree(c->blk_off); dfree(c->zpart); dfree(c->klpart);
     c->state_ready = false;
@@ -104,7 +104,7 @@ int ensure_state(pxsne_ctx *c) {
     c->L = c->p.log2_r;
     const int L = c->L;
     const int64_t leaves = int64_t(1) << (2 * L);
-    const int64_t cells = level_offset(L + 1);
+    const int64_t cells = rec_offset(L + 1);
     const int K1 = L < kPyrK ? L : kPyrK;
     const int64_t lvl = int64_t(1) << (2 * (L - K1));
     CK(c, dalloc(c, &c->z, n));
@@ -120,6 +120,7 @@ int ensure_state(pxsne_ctx *c) {
     CK(c, dalloc(c, &c->leaf_sx, leaves));
     CK(c, dalloc(c, &c->leaf_sy, leaves));
     CK(c, dalloc(c, &c->rec, cells));
+    CK(c, dalloc(c, &c->recn, cells));
     CK(c, dalloc(c, &c->leaf_start, leaves));
     CK(c, dalloc(c, &c->blk_off, lvl));
     for (int k = 0; k < 2; k++) {
@@ -171,10 +172,25 @@ int prime(pxsne_ctx *c) {
     return PXSNE_OK;
 }
 
+// One iteration.  With timing marks every kernel runs in order on the main
+// stream.  Without, the attraction (which needs only the rescaled z and P)
+// runs on the high-priority side stream concurrently with the pyramid and the
+// traversal, and joins before the next update.
 int one_iteration(pxsne_ctx *c, cudaEvent_t *marks = nullptr) {
     CK(c, launch_update(c, marks));
-    CK(c, launch_tree(c, true, marks));
-    CK(c, launch_forces(c, marks));
+    if (marks || !c->side) {
+        CK(c, launch_tree(c, true, marks));
+        CK(c, launch_forces(c, marks));
+        return PXSNE_OK;
+    }
+    CK(c, launch_snap(c, true));
+    CK(c, cudaEventRecord(c->ev_fork, c->stream));
+    CK(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    CK(c, launch_attract(c, c->side));
+    CK(c, cudaEventRecord(c->ev_join, c->side));
+    CK(c, launch_pyramid(c, true));
+    CK(c, launch_traverse_zsum(c));
+    CK(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     return PXSNE_OK;
 }
 
@@ -243,6 +259,13 @@ int pxsne_create(pxsne_ctx **out, const pxsne_params *p, void *stream) {
             c->own_stream = (e == cudaSuccess);
         }
     }
+    if (e == cudaSuccess) {
+        int lo = 0, hi = 0;
+        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = dalloc(c, &c->sc, 1);
     if (e == cudaSuccess) e = cudaMemset(c->sc, 0, sizeof(DevScalars));
     if (e != cudaSuccess) {
@@ -261,9 +284,12 @@ void pxsne_destroy(pxsne_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     free_state(c);
-    dfree(c->rp); dfree(c->col); dfree(c->val);
+    dfree(c->rp); dfree(c->col); dfree(c->val); dfree(c->rowlen);
     dfree(c->knn_idx); dfree(c->knn_d2); dfree(c->beta);
     dfree(c->sc);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->side) cudaStreamDestroy(c->side);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -277,7 +303,7 @@ int pxsne_affinities(pxsne_ctx *c, const float *X, int64_t n, int32_t D, float p
     if (!c) return PXSNE_E_ARG;
     if (!X) return fail(c, PXSNE_E_ARG, "X is NULL");
     const int k = c->p.k;
-    if (n < 2 || n > 0x7fffffff) return fail(c, PXSNE_E_ARG, "n = %lld out of range", (long long)n);
+    if (n < 2 || n > kMaxN) return fail(c, PXSNE_E_ARG, "n = %lld outside [2, 2^24]", (long long)n);
     if ((int64_t)k >= n) return fail(c, PXSNE_E_ARG, "k = %d must be < n = %lld", k, (long long)n);
     if (D < 1 || D > 256) return fail(c, PXSNE_E_UNSUPPORTED, "D = %d outside [1, 256]", D);
     if (perplexity <= 0.f) perplexity = c->p.perplexity;
@@ -288,7 +314,7 @@ int pxsne_affinities(pxsne_ctx *c, const float *X, int64_t n, int32_t D, float p
     }
     cudaStream_t st = c->stream;
     free_state(c);
-    dfree(c->rp); dfree(c->col); dfree(c->val);
+    dfree(c->rp); dfree(c->col); dfree(c->val); dfree(c->rowlen);
     dfree(c->knn_idx); dfree(c->knn_d2); dfree(c->beta);
     c->n = n;
     c->D = D;
@@ -319,7 +345,7 @@ int pxsne_affinities(pxsne_ctx *c, const float *X, int64_t n, int32_t D, float p
 int pxsne_set_P(pxsne_ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *col,
                 const float *val) {
     if (!c) return PXSNE_E_ARG;
-    if (n < 2 || n > 0x7fffffff || !row_ptr) return fail(c, PXSNE_E_ARG, "bad n or row_ptr");
+    if (n < 2 || n > kMaxN || !row_ptr) return fail(c, PXSNE_E_ARG, "bad n or row_ptr");
     if (row_ptr[0] != 0) return fail(c, PXSNE_E_ARG, "row_ptr[0] != 0");
     for (int64_t i = 0; i < n; i++)
         if (row_ptr[i + 1] < row_ptr[i]) return fail(c, PXSNE_E_ARG, "row_ptr not monotone");
@@ -332,20 +358,43 @@ int pxsne_set_P(pxsne_ctx *c, int64_t n, const int64_t *row_ptr, const int32_t *
             if (!(val[e] >= 0.f) || !std::isfinite(val[e]))
                 return fail(c, PXSNE_E_ARG, "bad value in row %lld", (long long)i);
         }
+    // rows padded to multiples of 4 (padding: column = row, value 0)
+    std::vector<int64_t> rp(n + 1);
+    std::vector<int32_t> len(n);
+    rp[0] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        len[i] = (int32_t)(row_ptr[i + 1] - row_ptr[i]);
+        rp[i + 1] = rp[i] + ((len[i] + 3) & ~3);
+    }
+    const int64_t nnz_pad = rp[n];
+    std::vector<int32_t> pc(nnz_pad > 0 ? nnz_pad : 4);
+    std::vector<float> pv(nnz_pad > 0 ? nnz_pad : 4);
+    for (int64_t i = 0; i < n; i++) {
+        int64_t o = rp[i];
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; e++, o++) {
+            pc[o] = col[e];
+            pv[o] = val[e];
+        }
+        for (; o < rp[i + 1]; o++) {
+            pc[o] = (int32_t)i;
+            pv[o] = 0.f;
+        }
+    }
     free_state(c);
-    dfree(c->rp); dfree(c->col); dfree(c->val);
+    dfree(c->rp); dfree(c->col); dfree(c->val); dfree(c->rowlen);
     dfree(c->knn_idx); dfree(c->knn_d2); dfree(c->beta);
     c->knn_k = 0;
     c->n = n;
     c->nnz = nnz;
+    c->nnz_pad = nnz_pad;
     CK(c, dalloc(c, &c->rp, n + 1));
-    CK(c, dalloc(c, &c->col, nnz > 0 ? nnz : 1));
-    CK(c, dalloc(c, &c->val, nnz > 0 ? nnz : 1));
-    CK(c, cudaMemcpyAsync(c->rp, row_ptr, (n + 1) * 8, cudaMemcpyHostToDevice, c->stream));
-    if (nnz > 0) {
-        CK(c, cudaMemcpyAsync(c->col, col, nnz * 4, cudaMemcpyHostToDevice, c->stream));
-        CK(c, cudaMemcpyAsync(c->val, val, nnz * 4, cudaMemcpyHostToDevice, c->stream));
-    }
+    CK(c, dalloc(c, &c->rowlen, n));
+    CK(c, dalloc(c, &c->col, pc.size()));
+    CK(c, dalloc(c, &c->val, pv.size()));
+    CK(c, cudaMemcpyAsync(c->rp, rp.data(), (n + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->rowlen, len.data(), n * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->col, pc.data(), pc.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->val, pv.data(), pv.size() * 4, cudaMemcpyHostToDevice, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return PXSNE_OK;
 }
@@ -536,10 +585,31 @@ int pxsne_get_P(pxsne_ctx *c, int64_t *row_ptr, int32_t *col, float *val) {
     if (!c) return PXSNE_E_ARG;
     if (!c->rp) return fail(c, PXSNE_E_STATE, "no affinities");
     cudaStream_t st = c->stream;
-    if (row_ptr) CK(c, cudaMemcpyAsync(row_ptr, c->rp, (c->n + 1) * 8, cudaMemcpyDeviceToHost, st));
-    if (col && c->nnz) CK(c, cudaMemcpyAsync(col, c->col, c->nnz * 4, cudaMemcpyDeviceToHost, st));
-    if (val && c->nnz) CK(c, cudaMemcpyAsync(val, c->val, c->nnz * 4, cudaMemcpyDeviceToHost, st));
-    return check_device(c, nullptr);
+    const int64_t n = c->n;
+    std::vector<int64_t> rp(n + 1);
+    std::vector<int32_t> len(n);
+    CK(c, cudaMemcpyAsync(rp.data(), c->rp, (n + 1) * 8, cudaMemcpyDeviceToHost, st));
+    CK(c, cudaMemcpyAsync(len.data(), c->rowlen, n * 4, cudaMemcpyDeviceToHost, st));
+    std::vector<int32_t> pc;
+    std::vector<float> pv;
+    if (col) pc.resize(c->nnz_pad);
+    if (val) pv.resize(c->nnz_pad);
+    if (col && c->nnz_pad)
+        CK(c, cudaMemcpyAsync(pc.data(), c->col, c->nnz_pad * 4, cudaMemcpyDeviceToHost, st));
+    if (val && c->nnz_pad)
+        CK(c, cudaMemcpyAsync(pv.data(), c->val, c->nnz_pad * 4, cudaMemcpyDeviceToHost, st));
+    int rc = check_device(c, nullptr);
+    if (rc) return rc;
+    int64_t o = 0;
+    if (row_ptr) row_ptr[0] = 0;
+    for (int64_t i = 0; i < n; i++) {
+        for (int32_t a = 0; a < len[i]; a++, o++) {
+            if (col) col[o] = pc[rp[i] + a];
+            if (val) val[o] = pv[rp[i] + a];
+        }
+        if (row_ptr) row_ptr[i + 1] = o;
+    }
+    return PXSNE_OK;
 }
 
 int pxsne_get_knn(pxsne_ctx *c, int32_t *idx, float *d2, float *beta) {
@@ -629,7 +699,7 @@ int64_t pxsne_device_bytes(const pxsne_ctx *c) {
     if (!c) return 0;
     int64_t b = sizeof(DevScalars);
     const int64_t n = c->n;
-    if (c->rp) b += (n + 1) * 8 + c->nnz * 8;
+    if (c->rp) b += (n + 1) * 8 + n * 4 + c->nnz_pad * 8;
     if (c->knn_idx) b += n * c->knn_k * 8 + n * 4;
     if (c->z) {
         const int L = c->L;
@@ -637,7 +707,7 @@ int64_t pxsne_device_bytes(const pxsne_ctx *c) {
         const int K1 = L < kPyrK ? L : kPyrK;
         const int64_t lvl = int64_t(1) << (2 * (L - K1));
         b += n * (8 + 16 + 8 + 8 + 8 + 4 + 8 + 4 + 4);
-        b += leaves * (4 + 8 + 8 + 4) + level_offset(L + 1) * 16 + lvl * 4 + 2 * (lvl + 4) * 20;
+        b += leaves * (4 + 8 + 8 + 4) + rec_offset(L + 1) * 20 + lvl * 4 + 2 * (lvl + 4) * 20;
         b += (int64_t)c->zblocks * 8 + (int64_t)c->klblocks * 16;
     }
     return b;

@@ -16,6 +16,7 @@ typedef unsigned long long u64;
 typedef long long i64;
 
 constexpr int kMaxL = 14;           // screen up to 2^14 x 2^14 (Morton keys < 2^28)
+constexpr int64_t kMaxN = 1 << 24;  // cell counts are exact floats below 2^24
 constexpr int kTravWarps = 8;       // warps per CTA in the traversal
 constexpr int kTravStack = 64;      // entries per warp; depth needs <= 3L + 1
 constexpr int kPyrK = 5;            // pyramid levels reduced per CTA pass
@@ -39,13 +40,18 @@ struct DevScalars {
     u64 n_test;          // (point, cell) pairs tested by the last traversal
 };
 
-// Record of one cell of the pyramid, 16 bytes:
-//   x = hi_x | hi_y << 16   (integer part of the centre of mass >> 16)
-//   y = lo_x (float bits)   (centre of mass - hi_x * 65536, in ulps)
-//   z = lo_y (float bits)
-//   w = N_c
-// The centre of mass of cell c is S_c / N_c in ulps; splitting it at bit 16
-// lets a point compute z_i - com exactly in float (see bh.cu).
+// The pyramid of cell records.  Cell (l, m) (level l, Morton index m) is at
+// rec_offset(l) + m of two arrays:
+//   rec  float4 {c_hi_x, c_lo_x, c_hi_y, c_lo_y}: the centre of mass S_c / N_c in
+//        ulps, split at bit 16 (c_hi = floor(com) with the low 16 bits cleared,
+//        exact in float; c_lo = the rest, in [0, 65536)), so that a point's
+//        offset z - com is (z_hi - c_hi) + (z_lo - c_lo) with one rounding;
+//   recn float N_c (exact below 2^24).
+// rec_offset pads level 0 to four slots so that every group of four siblings
+// starts on a 16-byte boundary.
+__host__ __device__ inline int64_t rec_offset(int l) {
+    return l == 0 ? 0 : ((int64_t(1) << (2 * l)) + 8) / 3;
+}
 
 __host__ __device__ inline int64_t level_offset(int l) {
     return ((int64_t(1) << (2 * l)) - 1) / 3;
@@ -100,6 +106,8 @@ struct pxsne_ctx {
     pxsne_params p;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t side = nullptr;          // high-priority stream for the attraction
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     std::string err;
 
@@ -108,9 +116,14 @@ struct pxsne_ctx {
     int64_t nnz = 0;
 
     // P as CSR
+    // P as CSR with every row padded to a multiple of 4 entries (padding:
+    // column = the row itself, value 0); rp holds the padded offsets and
+    // rowlen the true row lengths
     int64_t *rp = nullptr;
     int32_t *col = nullptr;
     float *val = nullptr;
+    int32_t *rowlen = nullptr;
+    int64_t nnz_pad = 0;
 
     // neighbour lists of the last affinities call
     int32_t *knn_idx = nullptr;
@@ -133,7 +146,8 @@ struct pxsne_ctx {
     int L = 0;
     uint32_t *leaf_cnt = nullptr;
     unsigned long long *leaf_sx = nullptr, *leaf_sy = nullptr;
-    uint4 *rec = nullptr;
+    float4 *rec = nullptr;
+    float *recn = nullptr;
     uint32_t *lvl_cnt[2] = {nullptr, nullptr};
     unsigned long long *lvl_sx[2] = {nullptr, nullptr}, *lvl_sy[2] = {nullptr, nullptr};
     uint32_t *leaf_start = nullptr;
@@ -168,6 +182,13 @@ enum KernelGroup {
 // (marks[g]) and after the last one (marks[KG_COUNT]).
 cudaError_t launch_tree(pxsne_ctx *c, bool rescale, cudaEvent_t *marks = nullptr);
 cudaError_t launch_forces(pxsne_ctx *c, cudaEvent_t *marks = nullptr);
+// The two halves of launch_tree and of launch_forces, for the overlapped
+// schedule: snap (memsets + histogram) then pyramid (passes, scan, scatter);
+// attraction alone on stream `st`, then traversal + Z.
+cudaError_t launch_snap(pxsne_ctx *c, bool rescale, cudaEvent_t *marks = nullptr);
+cudaError_t launch_pyramid(pxsne_ctx *c, bool rescale, cudaEvent_t *marks = nullptr);
+cudaError_t launch_attract(pxsne_ctx *c, cudaStream_t st);
+cudaError_t launch_traverse_zsum(pxsne_ctx *c);
 cudaError_t launch_update(pxsne_ctx *c, cudaEvent_t *marks = nullptr);
 cudaError_t launch_kl(pxsne_ctx *c, double *out_dev);
 cudaError_t launch_centre_y(pxsne_ctx *c, float *Ydev, int32_t *pixdev, float *scratch);

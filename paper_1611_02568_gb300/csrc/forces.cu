@@ -14,18 +14,36 @@
 
 namespace pxsne {
 
-// z_i - com along one axis, in ulps.  hi is the com's integer part >> 16,
-// lo the rest (float, < 65536); zh = z >> 16, zl = z & 0xffff as float.  The
-// difference of the high parts is an exact integer below 2^16 in magnitude,
-// so the only rounding is the final fma.
-__device__ __forceinline__ float com_delta(int zh, float zl, uint32_t hi, float lo) {
-    const float dh = (float)(zh - (int)hi);
-    return fmaf(dh, 65536.0f, zl - lo);
+// One warp = 32 points consecutive in Morton order.  Each stack entry is a
+// node whose four children are to be tested, with the mask of the lanes that
+// opened it.  The per-child step is branch-free within a level: every lane
+// computes its offset, distance and kernel value, and the accept/open
+// decisions only gate the accumulation and the push.  Children at the leaf
+// level are always accepted (bounded depth, Sec. 4.1) except for a lane's own
+// pixel, which is used without the point itself; children above it follow
+// Eq. bh_criteria, and the cell holding a lane's own pixel is opened.
+// CENTRE = 0: centre of mass; 1: geometric cell centre.  COUNT = 1 also
+// counts tested and accepted (point, cell) pairs.
+template <int CENTRE>
+__device__ __forceinline__ void cell_offset(int lc, uint32_t mc, const float4 *rec, int64_t at,
+                                            uint2 zi, float zhx, float zlx, float zhy,
+                                            float zly, float &dx, float &dy) {
+    if (CENTRE == 0) {
+        const float4 r = __ldg(rec + at);
+        dx = (zhx - r.x) + (zlx - r.y);
+        dy = (zhy - r.z) + (zly - r.w);
+    } else {
+        const uint32_t cx = gather_bits16(mc), cy = gather_bits16(mc >> 1);
+        const int64_t half = int64_t(1) << (31 - lc);
+        dx = (float)((int64_t)zi.x - (((int64_t)cx << (32 - lc)) + half));
+        dy = (float)((int64_t)zi.y - (((int64_t)cy << (32 - lc)) + half));
+    }
 }
 
-__global__ void __launch_bounds__(kTravWarps * 32)
-    k_bh_traverse(int n, int L, int centre_mode, const uint2 *__restrict__ z,
-                  const uint32_t *__restrict__ perm, const uint4 *__restrict__ rec,
+template <int CENTRE, int COUNT>
+__global__ void __launch_bounds__(kTravWarps * 32, 5)
+    k_bh_traverse(int n, int L, const uint2 *__restrict__ z, const uint32_t *__restrict__ perm,
+                  const float4 *__restrict__ rec, const float *__restrict__ recn,
                   DevScalars *sc, float2 *__restrict__ Frep, float *__restrict__ Zi) {
     __shared__ uint32_t s_node[kTravWarps][kTravStack];
     __shared__ uint32_t s_mask[kTravWarps][kTravStack];
@@ -33,7 +51,7 @@ __global__ void __launch_bounds__(kTravWarps * 32)
     __shared__ int64_t s_off[kMaxL + 2];
     if (threadIdx.x < kMaxL + 2) {
         s_T[threadIdx.x] = sc->T[threadIdx.x];
-        s_off[threadIdx.x] = threadIdx.x <= L ? level_offset(threadIdx.x) : 0;
+        s_off[threadIdx.x] = threadIdx.x <= L ? rec_offset(threadIdx.x) : 0;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -45,21 +63,21 @@ __global__ void __launch_bounds__(kTravWarps * 32)
     const uint2 zi = z[i];
     const int F = 32 - L;
     const uint32_t mi = morton2(zi.x >> F, zi.y >> F);
-    const int zhx = (int)(zi.x >> 16), zhy = (int)(zi.y >> 16);
-    const float zlx = (float)(zi.x & 0xffffu), zly = (float)(zi.y & 0xffffu);
+    // z split at bit 16, both halves exact in float (see rec in common.cuh)
+    const float zhx = (float)(zi.x & 0xffff0000u), zlx = (float)(zi.x & 0xffffu);
+    const float zhy = (float)(zi.y & 0xffff0000u), zly = (float)(zi.y & 0xffffu);
     const float sf0 = sc->sf[0], sf1 = sc->sf[1];
     float fx = 0.f, fy = 0.f, zs = 0.f;
     uint32_t n_acc = 0u, n_tst = 0u;
 
     uint32_t *stn = s_node[w];
     uint32_t *stm = s_mask[w];
-    int sp = 0;
     // The root contains every point: start with its four children.
     if (lane == 0) {
         stn[0] = 0u;  // (level 0 << 28) | morton 0
         stm[0] = active;
     }
-    sp = 1;
+    int sp = 1;
     __syncwarp();
     bool overflow = false;
     while (sp > 0) {
@@ -69,74 +87,82 @@ __global__ void __launch_bounds__(kTravWarps * 32)
         __syncwarp();
         const int lc = (int)(node >> 28) + 1;  // level of the children
         const uint32_t m0 = (node & 0x0fffffffu) << 2;
-        const uint4 *rc = rec + s_off[lc] + m0;
+        const int64_t base = s_off[lc] + m0;
+        const float4 nv = __ldg(reinterpret_cast<const float4 *>(recn + base));
         const bool me = (mask >> lane) & 1u;
-        const bool leaf = (lc == L);
-        const float Tl = s_T[lc];
-        const uint32_t mine = mi >> (2 * (L - lc));
+        const uint32_t mine = mi >> (2 * (L - lc));  // own cell at level lc
+        const float Nc[4] = {nv.x, nv.y, nv.z, nv.w};
+        if (lc == L) {
 #pragma unroll
-        for (int ch = 0; ch < 4; ch++) {
-            const uint4 r = __ldg(rc + ch);
-            if (r.w == 0u) continue;
-            const uint32_t mc = m0 + ch;
-            bool want_open = false;
-            if (me) {
-                n_tst++;
-                const bool contains = (mine == mc);
-                if (contains && !leaf) {
-                    want_open = true;
-                } else {
-                    float dx, dy, Nf;
-                    if (centre_mode == 0) {
-                        dx = com_delta(zhx, zlx, r.x & 0xffffu, __uint_as_float(r.y));
-                        dy = com_delta(zhy, zly, r.x >> 16, __uint_as_float(r.z));
-                    } else {
-                        // geometric centre of the cell: origin + W / 2
-                        const uint32_t cx = gather_bits16(mc), cy = gather_bits16(mc >> 1);
-                        const int64_t half = int64_t(1) << (31 - lc);
-                        dx = (float)((int64_t)zi.x - (((int64_t)cx << (32 - lc)) + half));
-                        dy = (float)((int64_t)zi.y - (((int64_t)cy << (32 - lc)) + half));
-                    }
-                    Nf = (float)r.w;
-                    bool skip = false;
-                    if (contains) {  // own pixel: take point i out of the cell
-                        if (r.w == 1u) {
-                            skip = true;
-                        } else if (centre_mode == 0) {
-                            const float sc2 = Nf / (Nf - 1.0f);
-                            dx *= sc2;
-                            dy *= sc2;
-                        }
-                        Nf -= 1.0f;
-                    }
-                    dx *= sf0;
-                    dy *= sf1;
-                    const float d2 = fmaf(dx, dx, dy * dy);
-                    if (!skip) {
-                        if (!leaf && !contains && !(d2 > Tl)) {
-                            want_open = true;
-                        } else {
-                            n_acc++;
-                            const float q = 1.0f / (1.0f + d2);
-                            const float Nq = Nf * q;
-                            zs += Nq;
-                            const float Nq2 = Nq * q;
-                            fx = fmaf(Nq2, dx, fx);
-                            fy = fmaf(Nq2, dy, fy);
+            for (int ch = 0; ch < 4; ch++) {
+                const float N = Nc[ch];
+                if (N == 0.f) continue;
+                const uint32_t mc = m0 + ch;
+                float dx, dy;
+                cell_offset<CENTRE>(lc, mc, rec, base + ch, zi, zhx, zlx, zhy, zly, dx, dy);
+                const bool own = me && (mine == mc);
+                float Nf = N;
+                if (__any_sync(0xffffffffu, own)) {  // own pixel: take point i out
+                    if (own) {
+                        Nf = N - 1.0f;
+                        if (CENTRE == 0 && N > 1.0f) {
+                            const float k = N / Nf;
+                            dx *= k;
+                            dy *= k;
                         }
                     }
                 }
+                dx *= sf0;
+                dy *= sf1;
+                const float d2 = fmaf(dx, dx, dy * dy);
+                const bool acc = me && (Nf > 0.f);
+                if (COUNT) {
+                    n_tst += me ? 1u : 0u;
+                    n_acc += acc ? 1u : 0u;
+                }
+                const float q = __fdividef(1.0f, 1.0f + d2);
+                const float Nq = acc ? Nf * q : 0.0f;
+                zs += Nq;
+                const float Nq2 = Nq * q;
+                fx = fmaf(Nq2, dx, fx);
+                fy = fmaf(Nq2, dy, fy);
             }
-            const unsigned ob = __ballot_sync(0xffffffffu, want_open);
-            if (ob) {
-                if (sp >= kTravStack) {
-                    overflow = true;
-                } else {
-                    if (lane == 0) {
-                        stn[sp] = ((uint32_t)lc << 28) | mc;
-                        stm[sp] = ob;
+        } else {
+            const float Tl = s_T[lc];
+#pragma unroll
+            for (int ch = 0; ch < 4; ch++) {
+                const float N = Nc[ch];
+                if (N == 0.f) continue;
+                const uint32_t mc = m0 + ch;
+                float dx, dy;
+                cell_offset<CENTRE>(lc, mc, rec, base + ch, zi, zhx, zlx, zhy, zly, dx, dy);
+                dx *= sf0;
+                dy *= sf1;
+                const float d2 = fmaf(dx, dx, dy * dy);
+                const bool contains = (mine == mc);
+                const bool far = (d2 > Tl) && !contains;
+                const bool acc = me && far;
+                if (COUNT) {
+                    n_tst += me ? 1u : 0u;
+                    n_acc += acc ? 1u : 0u;
+                }
+                const float q = __fdividef(1.0f, 1.0f + d2);
+                const float Nq = acc ? N * q : 0.0f;
+                zs += Nq;
+                const float Nq2 = Nq * q;
+                fx = fmaf(Nq2, dx, fx);
+                fy = fmaf(Nq2, dy, fy);
+                const unsigned ob = __ballot_sync(0xffffffffu, me && !far);
+                if (ob) {
+                    if (sp >= kTravStack) {
+                        overflow = true;
+                    } else {
+                        if (lane == 0) {
+                            stn[sp] = ((uint32_t)lc << 28) | mc;
+                            stm[sp] = ob;
+                        }
+                        sp++;
                     }
-                    sp++;
                 }
             }
         }
@@ -144,14 +170,16 @@ __global__ void __launch_bounds__(kTravWarps * 32)
         if (overflow) break;
     }
     if (overflow && lane == 0) atomicOr(&sc->err, (unsigned)PXSNE_DEVERR_STACK);
+    if (COUNT) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        n_acc += __shfl_xor_sync(0xffffffffu, n_acc, o);
-        n_tst += __shfl_xor_sync(0xffffffffu, n_tst, o);
-    }
-    if (lane == 0) {
-        atomicAdd(&sc->n_accept, (u64)n_acc);
-        atomicAdd(&sc->n_test, (u64)n_tst);
+        for (int o = 16; o > 0; o >>= 1) {
+            n_acc += __shfl_xor_sync(0xffffffffu, n_acc, o);
+            n_tst += __shfl_xor_sync(0xffffffffu, n_tst, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&sc->n_accept, (u64)n_acc);
+            atomicAdd(&sc->n_test, (u64)n_tst);
+        }
     }
     if (valid) {
         Frep[i] = make_float2(fx, fy);
@@ -160,41 +188,61 @@ __global__ void __launch_bounds__(kTravWarps * 32)
 }
 
 // Eq. grad, first term: Fattr_i = sum_j p_ij w_ij (y_i - y_j), one warp per
-// row.  Each lane keeps four entries in flight (P is streamed with evict-first
-// loads; the positions z_j are gathered from L2), so that enough bytes are
-// outstanding to cover HBM latency.
+// row (row lengths vary with the in-degree of the kNN graph; a warp per row
+// keeps long rows from stalling short ones).  Each lane keeps two entries in
+// flight; P is streamed with evict-first loads so that the positions z_j stay
+// in L2.  z_i - z_j is formed exactly in float from the 16-bit halves of the
+// fixed-point coordinates (both differences are exact; one final rounding).
 __global__ void __launch_bounds__(256)
     k_attract(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
               const float *__restrict__ val, const uint2 *__restrict__ z,
               const DevScalars *__restrict__ sc, float2 *__restrict__ Fattr) {
-    constexpr int U = 4;
+    constexpr int U = 2;
     const int lane = threadIdx.x & 31;
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row >= n) return;
     const float sf0 = sc->sf[0], sf1 = sc->sf[1];
     const uint2 zi = z[row];
+    const float xh = (float)(zi.x & 0xffff0000u), xl = (float)(zi.x & 0xffffu);
+    const float yh = (float)(zi.y & 0xffff0000u), yl = (float)(zi.y & 0xffffu);
     const int64_t e0 = rp[row], e1 = rp[row + 1];
     float fx = 0.f, fy = 0.f;
+    // software pipeline: the next batch of P is requested while the current
+    // batch's positions are being gathered
+    int32_t jn[U];
+    float pn[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int64_t q = e0 + lane + 32 * u;
+        jn[u] = q < e1 ? __ldcs(col + q) : row;
+        pn[u] = q < e1 ? __ldcs(val + q) : 0.f;
+    }
     for (int64_t e = e0 + lane; e < e1; e += 32 * U) {
         int32_t j[U];
         float p[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int64_t q = e + 32 * u;
-            j[u] = q < e1 ? __ldcs(col + q) : row;
-            p[u] = q < e1 ? __ldcs(val + q) : 0.f;
-        }
         uint2 zj[U];
 #pragma unroll
-        for (int u = 0; u < U; u++) zj[u] = z[j[u]];
+        for (int u = 0; u < U; u++) {
+            j[u] = jn[u];
+            p[u] = pn[u];
+            zj[u] = z[j[u]];
+        }
 #pragma unroll
         for (int u = 0; u < U; u++) {
-            const float dx = (float)((int64_t)zi.x - (int64_t)zj[u].x) * sf0;
-            const float dy = (float)((int64_t)zi.y - (int64_t)zj[u].y) * sf1;
-            const float q = 1.0f / (1.0f + fmaf(dx, dx, dy * dy));
-            const float pq = p[u] * q;
-            fx = fmaf(pq, dx, fx);
-            fy = fmaf(pq, dy, fy);
+            const int64_t q = e + 32 * (U + u);
+            jn[u] = q < e1 ? __ldcs(col + q) : row;
+            pn[u] = q < e1 ? __ldcs(val + q) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const float dx =
+                ((xh - (float)(zj[u].x & 0xffff0000u)) + (xl - (float)(zj[u].x & 0xffffu))) * sf0;
+            const float dy =
+                ((yh - (float)(zj[u].y & 0xffff0000u)) + (yl - (float)(zj[u].y & 0xffffu))) * sf1;
+            const float w = __fdividef(1.0f, 1.0f + fmaf(dx, dx, dy * dy));
+            const float pw = p[u] * w;
+            fx = fmaf(pw, dx, fx);
+            fy = fmaf(pw, dy, fy);
         }
     }
 #pragma unroll
@@ -251,23 +299,58 @@ __global__ void __launch_bounds__(512)
     }
 }
 
-cudaError_t launch_forces(pxsne_ctx *c, cudaEvent_t *marks) {
-    cudaStream_t st = c->stream;
+static cudaError_t traverse(pxsne_ctx *c, cudaStream_t st, bool count) {
     const int n = (int)c->n;
-    cudaError_t e;
-    if (marks && (e = cudaEventRecord(marks[KG_TRAVERSE], st))) return e;
     const int trav_blocks = (n + kTravWarps * 32 - 1) / (kTravWarps * 32);
-    k_bh_traverse<<<trav_blocks, kTravWarps * 32, 0, st>>>(n, c->L, c->p.centre_mode, c->z,
-                                                           c->perm, c->rec, c->sc, c->Frep,
-                                                           c->Zi);
-    if ((e = cudaGetLastError())) return e;
-    if (marks && (e = cudaEventRecord(marks[KG_ATTRACT], st))) return e;
+    const dim3 g(trav_blocks), b(kTravWarps * 32);
+    if (c->p.centre_mode == 0) {
+        if (count)
+            k_bh_traverse<0, 1><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
+                                                 c->Frep, c->Zi);
+        else
+            k_bh_traverse<0, 0><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
+                                                 c->Frep, c->Zi);
+    } else {
+        if (count)
+            k_bh_traverse<1, 1><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
+                                                 c->Frep, c->Zi);
+        else
+            k_bh_traverse<1, 0><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
+                                                 c->Frep, c->Zi);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_attract(pxsne_ctx *c, cudaStream_t st) {
+    const int n = (int)c->n;
     const int att_blocks = (int)((int64_t(n) * 32 + 255) / 256);
     k_attract<<<att_blocks, 256, 0, st>>>(n, c->rp, c->col, c->val, c->z, c->sc, c->Fattr);
-    if ((e = cudaGetLastError())) return e;
+    return cudaGetLastError();
+}
+
+static cudaError_t zsum(pxsne_ctx *c, cudaStream_t st) {
+    k_zsum<<<c->zblocks, 512, 0, st>>>((int)c->n, c->Zi, c->zpart, c->sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_traverse_zsum(pxsne_ctx *c) {
+    cudaError_t e = traverse(c, c->stream, false);
+    if (e) return e;
+    return zsum(c, c->stream);
+}
+
+// Sequential forces (traversal, attraction, Z) with optional timing marks.
+cudaError_t launch_forces(pxsne_ctx *c, cudaEvent_t *marks) {
+    cudaStream_t st = c->stream;
+    cudaError_t e;
+    if (marks && (e = cudaEventRecord(marks[KG_TRAVERSE], st))) return e;
+    // the work counters are kept by the sequential (initial-state and
+    // profiled) schedule only
+    if ((e = traverse(c, st, true))) return e;
+    if (marks && (e = cudaEventRecord(marks[KG_ATTRACT], st))) return e;
+    if ((e = launch_attract(c, st))) return e;
     if (marks && (e = cudaEventRecord(marks[KG_ZSUM], st))) return e;
-    k_zsum<<<c->zblocks, 512, 0, st>>>(n, c->Zi, c->zpart, c->sc);
-    if ((e = cudaGetLastError())) return e;
+    if ((e = zsum(c, st))) return e;
     if (marks && (e = cudaEventRecord(marks[KG_COUNT], st))) return e;
     return cudaSuccess;
 }

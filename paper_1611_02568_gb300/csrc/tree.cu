@@ -63,35 +63,64 @@ __global__ void k_snap_hist(int n, int L, int rescale, float theta,
         sc->n_accept = 0ull;
         sc->n_test = 0ull;
     }
-    if (tid >= n) return;
-    const uint32_t i = perm[tid];
-    uint32_t zx, zy;
-    if (rescale) {
-        longlong2 h = zhat[i];
-        zx = rescale_exact((u64)(h.x - mnx), gx, qx);
-        zy = rescale_exact((u64)(h.y - mny), gy, qy);
-        z[i] = make_uint2(zx, zy);
-    } else {
-        uint2 v = z[i];
-        zx = v.x;
-        zy = v.y;
+    // Points arrive in the Morton order of a recent state, so lanes with equal
+    // leaf keys mostly form runs: each run adds its count and sums with one
+    // set of atomics (segmented shuffle scan), and each lane's rank inside its
+    // pixel is the run's base plus its position in the run.
+    const bool valid = tid < n;
+    const int lane = threadIdx.x & 31;
+    uint32_t i = 0u, zx = 0u, zy = 0u, m = 0xffffffffu;
+    if (valid) {
+        i = perm[tid];
+        if (rescale) {
+            const longlong2 h = zhat[i];
+            zx = rescale_exact((u64)(h.x - mnx), gx, qx);
+            zy = rescale_exact((u64)(h.y - mny), gy, qy);
+            z[i] = make_uint2(zx, zy);
+        } else {
+            const uint2 v = z[i];
+            zx = v.x;
+            zy = v.y;
+        }
+        m = morton2(zx >> F, zy >> F);
     }
-    const uint32_t m = morton2(zx >> F, zy >> F);
-    rank[i] = atomicAdd(&cnt[m], 1u);
-    atomicAdd(&sx[m], (u64)zx);
-    atomicAdd(&sy[m], (u64)zy);
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, m, 1);
+    const bool head = (lane == 0) || (prev != m);
+    const unsigned heads = __ballot_sync(0xffffffffu, head);
+    const unsigned upto = (lane == 31) ? 0xffffffffu : ((2u << lane) - 1u);
+    const int start = 31 - __clz(heads & upto);
+    const unsigned later = heads & ~upto;
+    const int end = later ? __ffs(later) - 2 : 31;
+    u64 vx = zx, vy = zy;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u64 tx = __shfl_up_sync(0xffffffffu, vx, o);
+        const u64 ty = __shfl_up_sync(0xffffffffu, vy, o);
+        if (lane - o >= start) {
+            vx += tx;
+            vy += ty;
+        }
+    }
+    uint32_t base = 0u;
+    if (lane == end && valid) {
+        base = atomicAdd(&cnt[m], (uint32_t)(end - start + 1));
+        atomicAdd(&sx[m], vx);
+        atomicAdd(&sy[m], vy);
+    }
+    base = __shfl_sync(0xffffffffu, base, end);
+    if (valid) rank[i] = base + (uint32_t)(lane - start);
 }
 
 // Centre-of-mass record of a cell (layout in common.cuh).
-__device__ __forceinline__ uint4 make_record(uint32_t N, u64 Sx, u64 Sy) {
-    if (N == 0) return make_uint4(0u, 0u, 0u, 0u);
+__device__ __forceinline__ float4 make_record(uint32_t N, u64 Sx, u64 Sy) {
+    if (N == 0) return make_float4(0.f, 0.f, 0.f, 0.f);
     const u64 qx = Sx / N, qy = Sy / N;
     const uint32_t rx = (uint32_t)(Sx - qx * N), ry = (uint32_t)(Sy - qy * N);
     const float fN = (float)N;
-    const float lox = (float)(uint32_t)(qx & 0xffffu) + (float)rx / fN;
-    const float loy = (float)(uint32_t)(qy & 0xffffu) + (float)ry / fN;
-    const uint32_t hi = (uint32_t)(qx >> 16) | ((uint32_t)(qy >> 16) << 16);
-    return make_uint4(hi, __float_as_uint(lox), __float_as_uint(loy), N);
+    return make_float4((float)(uint32_t)(qx & 0xffff0000u),
+                       (float)(uint32_t)(qx & 0xffffu) + (float)rx / fN,
+                       (float)(uint32_t)(qy & 0xffff0000u),
+                       (float)(uint32_t)(qy & 0xffffu) + (float)ry / fN);
 }
 
 // Block-wide exclusive scan of one value per thread (nt threads, nt <= 1024).
@@ -132,7 +161,8 @@ template <int K>
 __global__ void __launch_bounds__(1 << (2 * (K - 1)))
     k_pyr_pass(int h, int top, const uint32_t *__restrict__ in_cnt,
                const u64 *__restrict__ in_sx, const u64 *__restrict__ in_sy,
-               uint4 *__restrict__ rec, uint32_t *__restrict__ out_cnt,
+               float4 *__restrict__ rec, float *__restrict__ recn,
+               uint32_t *__restrict__ out_cnt,
                u64 *__restrict__ out_sx, u64 *__restrict__ out_sy,
                uint32_t *__restrict__ leaf_start, DevScalars *sc, int bump_t) {
     constexpr int NT = 1 << (2 * (K - 1));
@@ -147,11 +177,13 @@ __global__ void __launch_bounds__(1 << (2 * (K - 1)))
     const ulonglong2 x23 = reinterpret_cast<const ulonglong2 *>(in_sx)[(cell0 >> 1) + 1];
     const ulonglong2 y01 = reinterpret_cast<const ulonglong2 *>(in_sy)[cell0 >> 1];
     const ulonglong2 y23 = reinterpret_cast<const ulonglong2 *>(in_sy)[(cell0 >> 1) + 1];
-    uint4 *rl = rec + level_offset(h) + cell0;
+    float4 *rl = rec + rec_offset(h) + cell0;
     rl[0] = make_record(c4.x, x01.x, y01.x);
     rl[1] = make_record(c4.y, x01.y, y01.y);
     rl[2] = make_record(c4.z, x23.x, y23.x);
     rl[3] = make_record(c4.w, x23.y, y23.y);
+    reinterpret_cast<float4 *>(recn + rec_offset(h))[cell0 >> 2] =
+        make_float4((float)c4.x, (float)c4.y, (float)c4.z, (float)c4.w);
     uint32_t N = c4.x + c4.y + c4.z + c4.w;
     u64 X = x01.x + x01.y + x23.x + x23.y;
     u64 Y = y01.x + y01.y + y23.x + y23.y;
@@ -170,7 +202,10 @@ __global__ void __launch_bounds__(1 << (2 * (K - 1)))
     for (int j = K - 1; j >= 0; j--) {
         const int cells = 1 << (2 * j);
         if (tid < cells) {
-            if (j > 0 || top) rec[level_offset(lvl) + idx] = make_record(N, X, Y);
+            if (j > 0 || top) {
+                rec[rec_offset(lvl) + idx] = make_record(N, X, Y);
+                recn[rec_offset(lvl) + idx] = (float)N;
+            }
             if (j == 0) {
                 out_cnt[b] = N;
                 out_sx[b] = X;
@@ -232,16 +267,17 @@ __global__ void k_perm_scatter(int n, int L, int K1, const uint2 *__restrict__ z
 }
 
 static cudaError_t pyr_pass(int K, int64_t blocks, cudaStream_t st, int h, int top,
-                            const uint32_t *ic, const u64 *ix, const u64 *iy, uint4 *rec,
+                            const uint32_t *ic, const u64 *ix, const u64 *iy, float4 *rec,
+                            float *recn,
                             uint32_t *oc, u64 *ox, u64 *oy, uint32_t *ls, DevScalars *sc,
                             int bump) {
     const dim3 g((unsigned)blocks);
     switch (K) {
-    case 1: k_pyr_pass<1><<<g, 1, 0, st>>>(h, top, ic, ix, iy, rec, oc, ox, oy, ls, sc, bump); break;
-    case 2: k_pyr_pass<2><<<g, 4, 0, st>>>(h, top, ic, ix, iy, rec, oc, ox, oy, ls, sc, bump); break;
-    case 3: k_pyr_pass<3><<<g, 16, 0, st>>>(h, top, ic, ix, iy, rec, oc, ox, oy, ls, sc, bump); break;
-    case 4: k_pyr_pass<4><<<g, 64, 0, st>>>(h, top, ic, ix, iy, rec, oc, ox, oy, ls, sc, bump); break;
-    default: k_pyr_pass<5><<<g, 256, 0, st>>>(h, top, ic, ix, iy, rec, oc, ox, oy, ls, sc, bump); break;
+    case 1: k_pyr_pass<1><<<g, 1, 0, st>>>(h, top, ic, ix, iy, rec, recn, oc, ox, oy, ls, sc, bump); break;
+    case 2: k_pyr_pass<2><<<g, 4, 0, st>>>(h, top, ic, ix, iy, rec, recn, oc, ox, oy, ls, sc, bump); break;
+    case 3: k_pyr_pass<3><<<g, 16, 0, st>>>(h, top, ic, ix, iy, rec, recn, oc, ox, oy, ls, sc, bump); break;
+    case 4: k_pyr_pass<4><<<g, 64, 0, st>>>(h, top, ic, ix, iy, rec, recn, oc, ox, oy, ls, sc, bump); break;
+    default: k_pyr_pass<5><<<g, 256, 0, st>>>(h, top, ic, ix, iy, rec, recn, oc, ox, oy, ls, sc, bump); break;
     }
     return cudaGetLastError();
 }
@@ -249,7 +285,7 @@ static cudaError_t pyr_pass(int K, int64_t blocks, cudaStream_t st, int h, int t
 // Tree of the current state.  rescale != 0: zhat -> z first (an iteration);
 // otherwise z is taken as it is (initial state).  Also rebuilds the traversal
 // order and, for an iteration, advances the iteration counter.
-cudaError_t launch_tree(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
+cudaError_t launch_snap(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
     cudaStream_t st = c->stream;
     const int L = c->L;
     const int64_t leaves = int64_t(1) << (2 * L);
@@ -262,7 +298,15 @@ cudaError_t launch_tree(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
     k_snap_hist<<<(n + 255) / 256, 256, 0, st>>>(n, L, rescale ? 1 : 0, c->p.theta, c->zhat,
                                                  c->z, c->perm, c->rank, c->leaf_cnt,
                                                  c->leaf_sx, c->leaf_sy, c->sc);
-    if ((e = cudaGetLastError())) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pyramid(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
+    cudaStream_t st = c->stream;
+    const int L = c->L;
+    const int64_t leaves = int64_t(1) << (2 * L);
+    const int n = (int)c->n;
+    cudaError_t e;
     if (marks && (e = cudaEventRecord(marks[KG_PYRAMID], st))) return e;
     // bottom-up passes
     int h = L;
@@ -272,8 +316,8 @@ cudaError_t launch_tree(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
         const int64_t blocks = leaves >> (2 * K1);
         const int top = (h - K1 == 0);
         if ((e = pyr_pass(K1, blocks, st, h, top, c->leaf_cnt, c->leaf_sx, c->leaf_sy, c->rec,
-                          c->lvl_cnt[0], c->lvl_sx[0], c->lvl_sy[0], c->leaf_start, c->sc,
-                          (rescale && top) ? 1 : 0)))
+                          c->recn, c->lvl_cnt[0], c->lvl_sx[0], c->lvl_sy[0], c->leaf_start,
+                          c->sc, (rescale && top) ? 1 : 0)))
             return e;
         h -= K1;
     }
@@ -285,8 +329,9 @@ cudaError_t launch_tree(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
         const int64_t blocks = (int64_t(1) << (2 * h)) >> (2 * K);
         const int top = (h - K == 0);
         if ((e = pyr_pass(K, blocks, st, h, top, c->lvl_cnt[cur], c->lvl_sx[cur],
-                          c->lvl_sy[cur], c->rec, c->lvl_cnt[cur ^ 1], c->lvl_sx[cur ^ 1],
-                          c->lvl_sy[cur ^ 1], nullptr, c->sc, (rescale && top) ? 1 : 0)))
+                          c->lvl_sy[cur], c->rec, c->recn, c->lvl_cnt[cur ^ 1],
+                          c->lvl_sx[cur ^ 1], c->lvl_sy[cur ^ 1], nullptr, c->sc,
+                          (rescale && top) ? 1 : 0)))
             return e;
         cur ^= 1;
         h -= K;
@@ -295,6 +340,15 @@ cudaError_t launch_tree(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
     k_perm_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, L, K1, c->z, c->rank, c->leaf_start,
                                                     c->blk_off, c->perm, c->sc);
     return cudaGetLastError();
+}
+
+// Tree of the current state.  rescale != 0: zhat -> z first (an iteration);
+// otherwise z is taken as it is (initial state).  Also rebuilds the traversal
+// order and, for an iteration, advances the iteration counter.
+cudaError_t launch_tree(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
+    cudaError_t e = launch_snap(c, rescale, marks);
+    if (e) return e;
+    return launch_pyramid(c, rescale, marks);
 }
 
 // ---------------------------------------------------------------- init / output
@@ -431,15 +485,15 @@ cudaError_t launch_centre_y(pxsne_ctx *c, float *Ydev, int32_t *pixdev, float *s
     return cudaGetLastError();
 }
 
-__global__ void k_level_counts(int64_t cells, const uint4 *__restrict__ rec, uint32_t *cnt) {
+__global__ void k_level_counts(int64_t cells, const float *__restrict__ recn, uint32_t *cnt) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < cells) cnt[i] = rec[i].w;
+    if (i < cells) cnt[i] = (uint32_t)recn[i];
 }
 
 cudaError_t launch_level_counts(pxsne_ctx *c, int level, uint32_t *cnt) {
     const int64_t cells = int64_t(1) << (2 * level);
     k_level_counts<<<(unsigned)((cells + 255) / 256), 256, 0, c->stream>>>(
-        cells, c->rec + level_offset(level), cnt);
+        cells, c->recn + rec_offset(level), cnt);
     return cudaGetLastError();
 }
 
