@@ -206,6 +206,12 @@ const char *pxsne_kernel_group_name(int32_t g);
  * pairs (accepted + opened + own-pixel).  Synchronises. */
 int pxsne_get_counters(pxsne_ctx *ctx, uint64_t *n_accept, uint64_t *n_test);
 
+/* Work counters of the last neighbour search: exact FP32 distances computed
+ * and list insertions over all rows (tensor-core search only; 0 otherwise),
+ * and the search used (1 tensor cores, 0 FP32 CUDA cores, -1 none).
+ * Synchronises. */
+int pxsne_get_knn_counters(pxsne_ctx *ctx, uint64_t *exact, uint64_t *inserted, int32_t *path);
+
 /* Total bytes of device memory the context holds. */
 int64_t pxsne_device_bytes(const pxsne_ctx *ctx);
 

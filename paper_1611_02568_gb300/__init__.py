@@ -105,6 +105,7 @@ def load(path: str | None = None):
     L.pxsne_kernel_group_name.argtypes = [i32]
     L.pxsne_kernel_group_name.restype = C.c_char_p
     L.pxsne_get_counters.argtypes = [vp, C.POINTER(u64), C.POINTER(u64)]
+    L.pxsne_get_knn_counters.argtypes = [vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(i32)]
     L.pxsne_device_bytes.argtypes = [vp]
     L.pxsne_device_bytes.restype = i64
     _lib = L
@@ -299,6 +300,12 @@ class Context:
         self._ck(self.L.pxsne_get_counters(self.h, C.byref(a), C.byref(t)))
         return a.value, t.value
 
+    def knn_counters(self):
+        """(exact distances, insertions, path) of the last neighbour search."""
+        a, b, p = C.c_uint64(), C.c_uint64(), C.c_int32()
+        self._ck(self.L.pxsne_get_knn_counters(self.h, C.byref(a), C.byref(b), C.byref(p)))
+        return a.value, b.value, p.value
+
     def device_bytes(self):
         return int(self.L.pxsne_device_bytes(self.h))
 
@@ -308,4 +315,5 @@ EXPORTED = ["pxsne_default_params", "pxsne_create", "pxsne_destroy", "pxsne_last
             "pxsne_sync", "pxsne_get_sizes", "pxsne_get_P", "pxsne_set_P", "pxsne_get_knn",
             "pxsne_set_state", "pxsne_get_state", "pxsne_get_tree", "pxsne_get_forces",
             "pxsne_device_bytes", "pxsne_step_profiled", "pxsne_kernel_group_name",
-            "pxsne_get_counters", "pxsne_kl_noalloc", "pxsne_kl_noalloc_max_rows"]
+            "pxsne_get_counters", "pxsne_kl_noalloc", "pxsne_kl_noalloc_max_rows",
+            "pxsne_get_knn_counters"]

@@ -11,11 +11,22 @@
 //   symmetrize     p_ij = (p_{j|i} + p_{i|j}) / 2n on the union pattern, CSR
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <string>
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
+#include "tc.cuh"
 
 namespace pxsne {
+
+static inline float __uint_as_float_host(unsigned u) {
+    float f;
+    memcpy(&f, &u, sizeof f);
+    return f;
+}
 
 constexpr int kQR = 64;    // query rows per CTA
 constexpr int kCT = 128;   // candidates per tile
@@ -208,6 +219,290 @@ __global__ void __launch_bounds__(kKnnThreads)
     }
 }
 
+// ---------------------------------------------------------------- tensor-core kNN
+// The same search on the tensor cores: the dot products q.c of a 128 x 128
+// tile come from tcgen05 MMAs on FP16 copies of X scaled by 2^e, accumulated
+// in FP32 in TMEM.  An FP16 operand carries a relative rounding error of at
+// most u = 2^-11, so |q~.c~ - 2^2e q.c| <= 2^2e |q||c| (2u + u^2 + D 2^-24) and
+// the approximate d2 = |q|^2 + |c|^2 - 2 q.c is within kappa |q||c| (plus
+// FP32 rounding of the norms) of the exact one.  A candidate can only belong
+// to the k nearest if its approximate d2 is below the row's current k-th exact
+// distance plus that bound; only those get their exact FP32 distance
+// (sum of squared differences) and enter the row's sorted list.
+constexpr int kTcRows = 128;     // query rows per CTA (MMA M)
+constexpr int kTcCols = 128;     // candidates per tile (MMA N)
+constexpr int kTcThreads = 256;  // warps 0-3: one query row per thread; 4-7 load tiles
+constexpr int kTcPolls = 1 << 24;
+
+__global__ void k_absmax(int64_t m, const float *__restrict__ X, unsigned *out) {
+    unsigned v = 0u;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v = max(v, __float_as_uint(fabsf(X[i])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, v);
+}
+
+__global__ void k_to_half(int64_t n, int D, int Dp, float scale, const float *__restrict__ X,
+                          __half *__restrict__ Xh) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n * Dp) return;
+    const int64_t row = i / Dp;
+    const int d = (int)(i % Dp);
+    Xh[i] = __float2half_rn(d < D ? X[row * D + d] * scale : 0.0f);
+}
+
+// Exact FP32 squared distance between rows a and b by one thread, summed in
+// index order (16-byte loads when rows are 16-byte aligned).
+__device__ __forceinline__ float thread_exact_d2(const float *__restrict__ X, int D, int64_t a,
+                                                 int64_t b, bool vec4) {
+    const float *xa = X + a * D, *xb = X + b * D;
+    float s = 0.f;
+    if (vec4) {
+        const float4 *pa = reinterpret_cast<const float4 *>(xa);
+        const float4 *pb = reinterpret_cast<const float4 *>(xb);
+#pragma unroll 8
+        for (int d = 0; d < (D >> 2); d++) {
+            const float4 u = __ldg(pa + d), v = __ldg(pb + d);
+            float t = u.x - v.x;
+            s = fmaf(t, t, s);
+            t = u.y - v.y;
+            s = fmaf(t, t, s);
+            t = u.z - v.z;
+            s = fmaf(t, t, s);
+            t = u.w - v.w;
+            s = fmaf(t, t, s);
+        }
+        return s;
+    }
+    for (int d = 0; d < D; d++) {
+        const float t = xa[d] - xb[d];
+        s = fmaf(t, t, s);
+    }
+    return s;
+}
+
+// Copy rows [r0, r0 + 128) of Xh (Dp halves each, zero rows past n) into the
+// 128-byte swizzled K-major layout at `dst`; `nt` threads starting at `t0`.
+__device__ __forceinline__ void load_tile_sw128(uint8_t *dst, const __half *__restrict__ Xh,
+                                                int64_t n, int Dp, int64_t r0, int t0, int nt) {
+    const int chunks = Dp >> 3;  // 16-byte chunks per row
+    for (int q = t0; q < kTcRows * chunks; q += nt) {
+        const int r = q / chunks, c8 = q % chunks;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (r0 + r < n) v = *reinterpret_cast<const uint4 *>(Xh + (r0 + r) * Dp + 8 * c8);
+        *reinterpret_cast<uint4 *>(dst + tc::sw128_offset(r, 8 * c8, kTcRows)) = v;
+    }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_knn_tc(int64_t n, int D, int Dp, int k, float inv_s2, float kappa, float eps_abs,
+             const float *__restrict__ X, const __half *__restrict__ Xh,
+             const float *__restrict__ nrm, int32_t *__restrict__ out_idx,
+             float *__restrict__ out_d2, unsigned *err, u64 *stats) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t mbar[2];
+    __shared__ uint32_t tslot;
+    __shared__ int s_abort;
+    // 1024-byte aligned base for the swizzled operand tiles
+    uint8_t *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+    const uint32_t tile_bytes = (uint32_t)kTcRows * Dp * 2;
+    uint8_t *sA = smem;
+    uint8_t *sB0 = smem + tile_bytes;
+    float *ld = reinterpret_cast<float *>(smem + 3 * tile_bytes);
+    int32_t *lj = reinterpret_cast<int32_t *>(ld + kTcRows * k);
+    float *cn2 = reinterpret_cast<float *>(lj + kTcRows * k);  // [2][128] (1-eps)|c|^2
+    float *cn1 = cn2 + 2 * kTcCols;                           // [2][128] |c|
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t q0 = (int64_t)blockIdx.x * kTcRows;
+    const int64_t T = (n + kTcCols - 1) / kTcCols;
+    // per epilogue warp: a queue of up to 32 x 32 survivors (row << 8 | column)
+    // and their exact distances
+    uint16_t *wq = reinterpret_cast<uint16_t *>(cn1 + 2 * kTcCols) + (warp & 3) * 1024;
+    float *wd = reinterpret_cast<float *>(reinterpret_cast<uint16_t *>(cn1 + 2 * kTcCols) + 4 * 1024) +
+                (warp & 3) * 1024;
+    const bool vec4 = ((D & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+
+    load_tile_sw128(sA, Xh, n, Dp, q0, tid, kTcThreads);
+    load_tile_sw128(sB0, Xh, n, Dp, 0, tid, kTcThreads);
+    if (tid < kTcCols) {
+        const float c2 = tid < n ? nrm[tid] : 0.f;
+        cn2[tid] = tid < n ? (1.0f - eps_abs) * c2 : INFINITY;
+        cn1[tid] = sqrtf(c2);
+    }
+    for (int e = tid; e < kTcRows * k; e += kTcThreads) {
+        ld[e] = INFINITY;
+        lj[e] = 0x7fffffff;
+    }
+    if (warp == 0) tc::tmem_alloc(&tslot, 2 * kTcCols);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+        s_abort = 0;
+    }
+    tc::fence_proxy_async();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tbase = tslot;
+    const uint32_t idesc = tc::idesc_f16(kTcRows, kTcCols, 0);
+    auto issue = [&](int buf) {
+        const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB0 + buf * tile_bytes);
+        for (int kk = 0; kk < Dp / 16; kk++) {
+            const uint32_t off = (uint32_t)(kk >> 2) * (kTcRows * 128) + (uint32_t)(kk & 3) * 32;
+            tc::mma_f16(tbase + (uint32_t)(buf * kTcCols), tc::sdesc_sw128(a0 + off),
+                        tc::sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
+        }
+        tc::commit(&mbar[buf]);
+    };
+    if (tid == 0) issue(0);
+
+    // epilogue state: thread tid < 128 owns query row q0 + tid
+    const int64_t qi = q0 + tid;
+    const bool qvalid = tid < kTcRows && qi < n;
+    const float qn2 = qvalid ? nrm[qi] : 0.f, qn1 = sqrtf(qn2);
+    float *myd = ld + (size_t)(tid < kTcRows ? tid : 0) * k;
+    int32_t *myj = lj + (size_t)(tid < kTcRows ? tid : 0) * k;
+    float tau = INFINITY;
+    int32_t jlast = 0x7fffffff;
+    uint32_t n_exact = 0u, n_ins = 0u;
+    const float Bq = kappa * qn1;
+    const float onem = 1.0f - eps_abs;
+    // tau - (1 - eps)|q|^2; finite while the list fills so that padding
+    // candidates (+inf) never pass
+    float tauA = 3.402823466e38f;
+
+    for (int64_t t = 0; t < T; t++) {
+        const int buf = (int)(t & 1);
+        const int64_t c0 = t * kTcCols;
+        if (warp >= 4) {
+            // producers: next candidate tile into the other buffer
+            if (t + 1 < T) {
+                load_tile_sw128(sB0 + (buf ^ 1) * tile_bytes, Xh, n, Dp, c0 + kTcCols, tid - 128,
+                                kTcThreads - 128);
+                const int j = tid - 128;
+                const int64_t cj = c0 + kTcCols + j;
+                const float c2 = cj < n ? nrm[cj] : 0.f;
+                cn2[(buf ^ 1) * kTcCols + j] = cj < n ? (1.0f - eps_abs) * c2 : INFINITY;
+                cn1[(buf ^ 1) * kTcCols + j] = sqrtf(c2);
+            }
+            tc::fence_proxy_async();
+        } else {
+            // warp-uniform: every lane must take the same path into the
+            // aligned TMEM loads and the warp-synchronous queue below
+            const bool got = __all_sync(
+                0xffffffffu, tc::mbar_wait(&mbar[buf], (uint32_t)((t >> 1) & 1), kTcPolls));
+            if (!got) {
+                s_abort = 1;
+                atomicOr(err, (unsigned)PXSNE_DEVERR_STACK);
+            }
+            tc::fence_after();
+            if (got) {
+#pragma unroll 1
+                for (int cb = 0; cb < kTcCols; cb += 32) {
+                    float v[32];
+                    tc::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * kTcCols + cb), v);
+                    // survivors of the filter (tau can only fall during the
+                    // chunk, so this is a superset; each is re-checked exactly).
+                    // approx <= tau + slack rearranged as
+                    //   (1-eps)|c|^2 - kappa|q||c| - 2 q.c <= tau - (1-eps)|q|^2,
+                    // with |c|^2 = +inf for rows past n
+                    uint32_t sm = 0u;
+                    const float *hp = cn2 + buf * kTcCols + cb;
+                    const float *gp = cn1 + buf * kTcCols + cb;
+#pragma unroll
+                    for (int j4 = 0; j4 < 8; j4++) {
+                        const float4 h4 = *reinterpret_cast<const float4 *>(hp + 4 * j4);
+                        const float4 g4 = *reinterpret_cast<const float4 *>(gp + 4 * j4);
+                        const float hh[4] = {h4.x, h4.y, h4.z, h4.w};
+                        const float gg[4] = {g4.x, g4.y, g4.z, g4.w};
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const int j = 4 * j4 + u;
+                            const float lhs = fmaf(-Bq, gg[u], fmaf(-2.0f * inv_s2, v[j], hh[u]));
+                            sm |= (lhs <= tauA) ? (1u << j) : 0u;
+                        }
+                    }
+                    if (!qvalid) sm = 0u;
+                    if (qi >= c0 + cb && qi < c0 + cb + 32) sm &= ~(1u << (int)(qi - c0 - cb));
+                    // compact the warp's survivors (row, column) into its queue
+                    const uint32_t cnt = (uint32_t)__popc(sm);
+                    uint32_t incl = cnt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const uint32_t excl = incl - cnt;
+                    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                    uint32_t mm = sm;
+                    for (uint32_t q = excl; mm; q++) {
+                        const int j = __ffs(mm) - 1;
+                        mm &= mm - 1u;
+                        wq[q] = (uint16_t)((lane << 8) | j);
+                    }
+                    __syncwarp();
+                    // every lane computes queued exact distances
+                    for (uint32_t q = lane; q < total; q += 32) {
+                        const uint32_t e = wq[q];
+                        const int64_t row = q0 + 32 * warp + (e >> 8);
+                        wd[q] = thread_exact_d2(X, D, row, c0 + cb + (e & 255u), vec4);
+                    }
+                    __syncwarp();
+                    // the row's owner inserts its results
+                    for (uint32_t q = excl; q < incl; q++) {
+                        const float dex = wd[q];
+                        const int64_t cand = c0 + cb + (wq[q] & 255u);
+                        if (!(dex < tau || (dex == tau && (int32_t)cand < jlast))) continue;
+                        n_ins++;
+                        int p = k - 1;
+                        while (p > 0 && (myd[p - 1] > dex ||
+                                         (myd[p - 1] == dex && myj[p - 1] > (int32_t)cand))) {
+                            myd[p] = myd[p - 1];
+                            myj[p] = myj[p - 1];
+                            p--;
+                        }
+                        myd[p] = dex;
+                        myj[p] = (int32_t)cand;
+                        tau = myd[k - 1];
+                        jlast = myj[k - 1];
+                        tauA = fminf(tau - onem * qn2, 3.402823466e38f);
+                    }
+                    n_exact += cnt;
+                    __syncwarp();
+                }
+            }
+            tc::fence_before();
+        }
+        __syncthreads();
+        tc::fence_after();
+        if (s_abort) break;
+        if (tid == 0 && t + 1 < T) issue(buf ^ 1);
+    }
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    if (warp == 0) tc::tmem_dealloc(tbase, 2 * kTcCols);
+    if (tid < kTcRows) {
+        atomicAdd(&stats[0], (u64)n_exact);
+        atomicAdd(&stats[1], (u64)n_ins);
+    }
+    for (int e = tid; e < kTcRows * k; e += kTcThreads) {
+        const int64_t row = q0 + e / k;
+        if (row < n) {
+            out_idx[row * k + (e % k)] = lj[e];
+            out_d2[row * k + (e % k)] = ld[e];
+        }
+    }
+}
+
+static size_t knn_tc_smem(int Dp, int k) {
+    return (size_t)3 * kTcRows * Dp * 2 + (size_t)kTcRows * k * 8 + 4 * kTcCols * 4 +
+           4 * 1024 * (2 + 4) + 1024;
+}
+
 cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, int32_t k,
                        int32_t *idx, float *d2) {
     cudaStream_t st = c->stream;
@@ -216,6 +511,51 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
     if ((e = cudaMallocAsync(&nrm, n * sizeof(float), st))) return e;
     k_row_norms<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(n, D, Xdev, nrm);
     if ((e = cudaGetLastError())) return e;
+    const int Dp = (D + 63) / 64 * 64;
+    const char *force = getenv("PXSNE_KNN");
+    const bool want_fp32 = force && force[0] == 'f';
+    int dev = 0, smem_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t smem_tc = knn_tc_smem(Dp, k);
+    if (!want_fp32 && Dp <= 128 && smem_tc <= (size_t)smem_max) {
+        c->knn_path = 1;
+        unsigned *amax = nullptr;
+        __half *Xh = nullptr;
+        unsigned *err = &c->sc->err;
+        if ((e = cudaMemsetAsync(&c->sc->knn_exact, 0, 2 * sizeof(u64), st))) return e;
+        if ((e = cudaMallocAsync(&amax, sizeof(unsigned), st))) return e;
+        if ((e = cudaMemsetAsync(amax, 0, sizeof(unsigned), st))) return e;
+        k_absmax<<<1184, 256, 0, st>>>(n * D, Xdev, amax);
+        unsigned hmax = 0;
+        if ((e = cudaMemcpyAsync(&hmax, amax, sizeof(unsigned), cudaMemcpyDeviceToHost, st)))
+            return e;
+        if ((e = cudaStreamSynchronize(st))) return e;
+        const float mx = __uint_as_float_host(hmax);
+        // scale the largest |x| into [2^14, 2^15): FP16 stays far from overflow
+        int ex = 0;
+        if (mx > 0.f) ex = 14 - (int)floorf(log2f(mx));
+        if (ex > 100) ex = 100;
+        if (ex < -100) ex = -100;
+        const float scale = ldexpf(1.0f, ex);
+        const float inv_s2 = ldexpf(1.0f, -2 * ex);
+        const float u = 1.0f / 2048.0f;
+        const float kappa = 1.25f * 2.0f * (2.0f * u + u * u + (float)Dp * 5.9604645e-8f * 1.01f);
+        const float eps_abs = (float)(2 * D + 8) * 5.9604645e-8f;
+        if ((e = cudaMallocAsync(&Xh, (size_t)n * Dp * sizeof(__half), st))) return e;
+        k_to_half<<<(unsigned)((n * Dp + 255) / 256), 256, 0, st>>>(n, D, Dp, scale, Xdev, Xh);
+        if ((e = cudaGetLastError())) return e;
+        if ((e = cudaFuncSetAttribute(k_knn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem_tc)))
+            return e;
+        k_knn_tc<<<(unsigned)((n + kTcRows - 1) / kTcRows), kTcThreads, smem_tc, st>>>(
+            n, D, Dp, k, inv_s2, kappa, eps_abs, Xdev, Xh, nrm, idx, d2, err, &c->sc->knn_exact);
+        if ((e = cudaGetLastError())) return e;
+        cudaFreeAsync(Xh, st);
+        cudaFreeAsync(amax, st);
+        return cudaFreeAsync(nrm, st);
+    }
+    c->knn_path = 0;
     const size_t smem = (size_t)D * (kQR + kCT) * 4 + (size_t)kQR * k * 8 + kQR * 4 +
                         (size_t)(kQR + kKnnThreads / 32) * kCT * 4;
     if ((e = cudaFuncSetAttribute(k_knn_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -695,6 +695,18 @@ int pxsne_get_counters(pxsne_ctx *c, uint64_t *n_accept, uint64_t *n_test) {
     return PXSNE_OK;
 }
 
+int pxsne_get_knn_counters(pxsne_ctx *c, uint64_t *exact, uint64_t *inserted, int32_t *path) {
+    if (!c) return PXSNE_E_ARG;
+    DevScalars h;
+    CK(c, cudaMemcpyAsync(&h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    int rc = check_device(c, nullptr);
+    if (rc) return rc;
+    if (exact) *exact = h.knn_exact;
+    if (inserted) *inserted = h.knn_insert;
+    if (path) *path = c->knn_path;
+    return PXSNE_OK;
+}
+
 int64_t pxsne_device_bytes(const pxsne_ctx *c) {
     if (!c) return 0;
     int64_t b = sizeof(DevScalars);

@@ -38,6 +38,8 @@ struct DevScalars {
     unsigned ticket2;    // same for the KL reduction
     u64 n_accept;        // accepted (point, cell) pairs of the last traversal
     u64 n_test;          // (point, cell) pairs tested by the last traversal
+    u64 knn_exact;       // exact distances computed by the last neighbour search
+    u64 knn_insert;      // list insertions of the last neighbour search
 };
 
 // The pyramid of cell records.  Cell (l, m) (level l, Morton index m) is at
@@ -130,6 +132,7 @@ struct pxsne_ctx {
     float *knn_d2 = nullptr;
     float *beta = nullptr;
     int32_t knn_k = 0;
+    int knn_path = -1;  // 1: tensor-core kNN, 0: FP32 CUDA-core kNN
 
     // embedding state (data order)
     uint2 *z = nullptr;

@@ -159,8 +159,35 @@ def test_full_run_kl_within_one_percent(px, gauss):
     assert abs(kl_g - kl_o) <= 0.01 * kl_o, (kl_g, kl_o)
 
 
-def test_affinities_match_oracle(px):
+def check_knn_rows(X, rows, idx_o, d2_o, idx, d2, tol=2e-5):
+    """What is unique must match (neighbours closer than the true k-th distance
+    by more than the FP32 error); every returned neighbour must be within the
+    tolerance of the true k-th distance."""
+    for q, i in enumerate(rows):
+        dk = d2_o[q, -1]
+        must = set(idx_o[q][d2_o[q] < dk * (1 - tol)])
+        got = set(idx[i])
+        assert must <= got, i
+        dd = ((X[idx[i]].astype(np.float64) - X[i].astype(np.float64)) ** 2).sum(1)
+        assert np.all(dd <= dk * (1 + tol)), i
+        assert i not in got
+        np.testing.assert_allclose(d2[i], np.sort(dd), rtol=1e-5)
+
+
+@pytest.fixture(params=["tc", "fp32"])
+def knn_path(request, monkeypatch):
+    """Run the neighbour search on the tensor cores (default) or the FP32 path."""
+    if request.param == "fp32":
+        monkeypatch.setenv("PXSNE_KNN", "fp32")
+    else:
+        monkeypatch.delenv("PXSNE_KNN", raising=False)
+    return request.param
+
+
+def test_affinities_match_oracle(px, knn_path):
     X, _ = datagen.gauss10(1, n=1500)
+    X[7] = X[3]                       # duplicate rows: distance 0, tie on index
+    X[900] = X[3]
     k, u = 90, 30.0
     P, idx_o, d2_o, bad = oracle.affinities(X, u, k)
     with make_ctx(px, L=9, k=k, perplexity=u) as ctx:
@@ -168,17 +195,8 @@ def test_affinities_match_oracle(px):
         idx, d2, beta = ctx.get_knn()
         rp, col, val = ctx.get_P()
     n = X.shape[0]
-    # neighbour sets: what is unique must match; ties within FP32 error are valid
-    tol = 2e-5
-    for i in range(n):
-        dk = d2_o[i, -1]
-        must = set(idx_o[i][d2_o[i] < dk * (1 - tol)])
-        got = set(idx[i])
-        assert must <= got, i
-        # every returned neighbour is within tolerance of the true k-th distance
-        dd = ((X[idx[i]].astype(np.float64) - X[i].astype(np.float64)) ** 2).sum(1)
-        assert np.all(dd <= dk * (1 + tol)), i
-        np.testing.assert_allclose(d2[i], np.sort(dd), rtol=1e-5)
+    check_knn_rows(X, np.arange(n), idx_o, d2_o, idx, d2)
+    assert idx[3][0] == 7 and idx[3][1] == 900
     # perplexity of each GPU row, evaluated in FP64 from its own d2 and beta
     e = np.exp(-beta[:, None].astype(np.float64) * (d2 - d2[:, :1]))
     p = e / e.sum(1, keepdims=True)
@@ -188,6 +206,20 @@ def test_affinities_match_oracle(px):
     assert np.array_equal(rp, P.row_ptr) and np.array_equal(col, P.col)
     np.testing.assert_allclose(val, P.val, rtol=2e-3, atol=1e-9)
     assert abs(val.astype(np.float64).sum() - 1.0) < 1e-5
+
+
+def test_knn_d128_sampled_rows(px, knn_path):
+    """The bench's data shape (D = 128 anisotropic mixture) at n = 20,000 with a
+    ragged last tile; exact FP64 neighbours of 300 sampled rows."""
+    n, k = 20011, 90
+    X, _ = datagen.gmm128(seed=3, n=n)
+    rows = np.random.default_rng(0).choice(n, 300, replace=False)
+    rows = np.concatenate([rows, [0, n - 1]])
+    idx_o, d2_o = oracle.knn(X, k, rows=rows)
+    with make_ctx(px, L=11, k=k, perplexity=30.0) as ctx:
+        ctx.affinities(X)
+        idx, d2, _ = ctx.get_knn()
+    check_knn_rows(X, rows, idx_o, d2_o, idx, d2)
 
 
 def test_full_gpu_path_kl(px):
