@@ -53,7 +53,8 @@ extern "C" {
 #define PXSNE_DEVERR_NONFINITE 1u   /* non-finite gradient or step */
 #define PXSNE_DEVERR_STACK 2u       /* BH traversal stack overflow */
 #define PXSNE_DEVERR_BISECT 4u      /* a perplexity row did not converge */
-#define PXSNE_DEVERR_RANGE 8u       /* step clamped: |u / s| beyond 2^60 ulps */
+#define PXSNE_DEVERR_RANGE 8u       /* step clamped: |u / s| beyond 2^58 ulps */
+#define PXSNE_DEVERR_TIMEOUT 16u    /* a bounded wait on the tensor cores gave up */
 
 typedef struct pxsne_ctx pxsne_ctx;
 
@@ -126,6 +127,12 @@ int pxsne_init(pxsne_ctx *ctx, const float *Y0, int y_on_device, uint64_t seed);
  * and forces of the new state (Sec. 4.1, Eq. bh_criteria, Eq. grad).
  * Returns enqueue errors only. */
 int pxsne_step(pxsne_ctx *ctx, int32_t iters);
+
+/* Change the optimiser schedule of an existing context (learning rate,
+ * exaggeration and its length, momenta and switch, minimum gain) without
+ * rebuilding P; e.g. refining a warm start without exaggeration.  Takes effect
+ * at the next pxsne_step.  Other fields of p are ignored. */
+int pxsne_set_schedule(pxsne_ctx *ctx, const pxsne_params *p);
 
 /* KL divergence of the current state (Eq. cost_func) in FP64, with Z the
  * Barnes-Hut normalisation of the current tree and the un-exaggerated P.
@@ -214,6 +221,54 @@ int pxsne_get_knn_counters(pxsne_ctx *ctx, uint64_t *exact, uint64_t *inserted, 
 
 /* Total bytes of device memory the context holds. */
 int64_t pxsne_device_bytes(const pxsne_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start (not in the paper): an MLP d -> 256 -> 256 -> 2 with the
+ * exact GELU g(z) = z Phi(z), BF16 weights and activations as tensor-core
+ * operands, FP32 accumulation, FP32 master weights and Adam (beta 0.9 / 0.999,
+ * eps 1e-8).  It is trained with the mean squared error
+ * L = (1/m) sum_r ||y_r - t_r||^2 on 2-D embeddings the method produced, and
+ * its output initialises pxsne_init.  Parameters are one flat FP32 vector,
+ * row-major: W1[256 x d], b1[256], W2[256 x 256], b2[256], W3[2 x 256], b3[2].
+ * All calls synchronise the model's stream; X (n x d) and T / Y (n x 2) are
+ * float32, host or device per on_device.
+ * ------------------------------------------------------------------------ */
+typedef struct pxsne_mlp pxsne_mlp;
+
+/* d in [1, 1024]; He-normal weights drawn from `seed`, zero biases.  stream:
+ * a cudaStream_t or NULL for a private one.  Returns PXSNE_E_ARG, _OOM or
+ * _CUDA on failure (*out stays NULL). */
+int pxsne_mlp_create(pxsne_mlp **out, int32_t d, uint64_t seed, void *stream);
+void pxsne_mlp_destroy(pxsne_mlp *m);
+const char *pxsne_mlp_last_error(const pxsne_mlp *m);
+int64_t pxsne_mlp_num_params(const pxsne_mlp *m);
+/* Set / read the flat FP32 parameters (host).  Setting resets Adam. */
+int pxsne_mlp_set_params(pxsne_mlp *m, const float *params);
+int pxsne_mlp_get_params(pxsne_mlp *m, float *params);
+
+/* Loss and its gradient with respect to the flat parameters on one batch of
+ * 1 <= n <= 8192 rows (no update).  grad (host, num_params floats) may be
+ * NULL. */
+int pxsne_mlp_loss_grad(pxsne_mlp *m, const float *X, const float *T, int64_t n, float *grad,
+                        double *loss, int on_device);
+
+/* `epochs` passes of Adam (learning rate lr) over the n rows in minibatches of
+ * `batch` <= 8192 rows, shuffled with `shuffle_seed`; final_loss (may be NULL)
+ * gets the mean batch loss of the last epoch. */
+int pxsne_mlp_train(pxsne_mlp *m, const float *X, const float *T, int64_t n, int32_t epochs,
+                    int32_t batch, float lr, uint64_t shuffle_seed, double *final_loss,
+                    int on_device);
+
+/* Y = MLP(X) for n rows. */
+int pxsne_mlp_predict(pxsne_mlp *m, const float *X, int64_t n, float *Y, int on_device);
+
+/* Normalise an embedding Y (n x 2) to zero mean and unit RMS per coordinate
+ * (isotropic scale) and, when Yref is non-NULL, apply the orthogonal map
+ * (rotation or reflection) that best aligns it with the normalised Yref in the
+ * least-squares sense (2 x 2 orthogonal Procrustes, closed form).  Used to put
+ * target embeddings of different random seeds in one frame before training the
+ * warm start.  Yout may alias Y.  Host or device buffers per on_device. */
+int pxsne_embed_align(const float *Y, const float *Yref, int64_t n, float *Yout, int on_device);
 
 /* ------------------------------------------------------------------------
  * Allocation-free KL.  The paper has no counterpart: this is a service for

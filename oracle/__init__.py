@@ -86,6 +86,12 @@ def lib():
         L.orc_Z.restype = dbl
         L.orc_nbr_precision.argtypes = [pi32, i32, i32, i64, pu32, pd, pi64, i64]
         L.orc_nbr_precision.restype = dbl
+        L.orc_mlp.argtypes = [C.c_int32, C.c_int32, pd, pd, pd, pd, pd, pd, pf, pf, i64, pd, pd]
+        L.orc_mlp.restype = dbl
+        L.orc_gelu.argtypes = [dbl]
+        L.orc_gelu.restype = dbl
+        L.orc_gelu_d.argtypes = [dbl]
+        L.orc_gelu_d.restype = dbl
         L.orc_num_threads.restype = C.c_int
         L.orc_set_num_threads.argtypes = [C.c_int]
         _lib = L
@@ -389,3 +395,57 @@ def nbr_precision(knn_hd, k, z, s, rows=None):
     return float(lib().orc_nbr_precision(_P(knn_hd, C.c_int32), knn_hd.shape[1], k, n,
                                          _P(z, C.c_uint32), _P(s, C.c_double),
                                          _ptr_or_null(r, C.c_int64), m))
+
+
+# ---------------------------------------------------------------- MLP warm start
+@dataclass
+class MLP:
+    """Weights of d -> H -> H -> 2 (row-major, FP64)."""
+    W1: np.ndarray
+    b1: np.ndarray
+    W2: np.ndarray
+    b2: np.ndarray
+    W3: np.ndarray
+    b3: np.ndarray
+
+    @property
+    def d(self):
+        return self.W1.shape[1]
+
+    @property
+    def H(self):
+        return self.W1.shape[0]
+
+    def flat(self):
+        return np.concatenate([a.ravel() for a in (self.W1, self.b1, self.W2, self.b2,
+                                                    self.W3, self.b3)])
+
+    @classmethod
+    def from_flat(cls, v, d, H):
+        sizes = [H * d, H, H * H, H, 2 * H, 2]
+        parts = np.split(np.asarray(v, dtype=np.float64), np.cumsum(sizes)[:-1])
+        return cls(parts[0].reshape(H, d), parts[1], parts[2].reshape(H, H), parts[3],
+                   parts[4].reshape(2, H), parts[5])
+
+
+def gelu(z):
+    return float(lib().orc_gelu(float(z)))
+
+
+def gelu_d(z):
+    return float(lib().orc_gelu_d(float(z)))
+
+
+def mlp(net: MLP, X, T=None, grad=False):
+    """(loss, Y [m,2], flat gradient or None) of the MLP on rows X with targets T."""
+    X = np.ascontiguousarray(X, dtype=np.float32)
+    m = X.shape[0]
+    w = [np.ascontiguousarray(a, dtype=np.float64) for a in (net.W1, net.b1, net.W2, net.b2,
+                                                            net.W3, net.b3)]
+    Tc = None if T is None else np.ascontiguousarray(T, dtype=np.float32)
+    Y = np.empty((m, 2))
+    g = np.empty(net.flat().size) if grad else None
+    L = lib().orc_mlp(net.d, net.H, *[_P(a, C.c_double) for a in w], _P(X, C.c_float),
+                      None if Tc is None else _P(Tc, C.c_float), m, _P(Y, C.c_double),
+                      None if g is None else _P(g, C.c_double))
+    return float(L), Y, g

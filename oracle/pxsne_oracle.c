@@ -25,6 +25,7 @@
  *  - The cell that contains point i is always opened; at a leaf, i is removed
  *    from its own cell's count and sums (Sec. 4.1 "leaf termination").
  */
+#define _GNU_SOURCE
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -645,3 +646,86 @@ double orc_nbr_precision(const int32_t *knn_hd, int32_t kh, int32_t k, int64_t n
     }
     return (double)hits / ((double)k * (double)m);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Learned warm start (not in the paper; the initialiser of the north-star
+ * "learned part"): y = W3 g(W2 g(W1 x + b1) + b2) + b3 with g the exact GELU
+ * g(z) = z Phi(z) = 0.5 z (1 + erf(z / sqrt 2)), dimensions d -> H -> H -> 2.
+ * Weights row-major: W1[H x d], W2[H x H], W3[2 x H].  Loss over a batch of m
+ * rows: L = (1/m) sum_r ||y_r - t_r||^2.  Returns L; when grad != NULL writes
+ * dL/d(W1, b1, W2, b2, W3, b3) in that order (same layout as the weights), and
+ * Y (m x 2) when non-NULL. */
+static double gelu(double z) { return 0.5 * z * (1.0 + erf(z / sqrt(2.0))); }
+static double gelu_d(double z)
+{
+    return 0.5 * (1.0 + erf(z / sqrt(2.0))) + z * exp(-0.5 * z * z) / sqrt(2.0 * M_PI);
+}
+
+double orc_mlp(int32_t d, int32_t H, const double *W1, const double *b1, const double *W2,
+               const double *b2, const double *W3, const double *b3, const float *X,
+               const float *T, int64_t m, double *Y, double *grad)
+{
+    double *z1 = (double *)malloc((size_t)H * sizeof(double));
+    double *h1 = (double *)malloc((size_t)H * sizeof(double));
+    double *z2 = (double *)malloc((size_t)H * sizeof(double));
+    double *h2 = (double *)malloc((size_t)H * sizeof(double));
+    double *dz2 = (double *)malloc((size_t)H * sizeof(double));
+    double *dz1 = (double *)malloc((size_t)H * sizeof(double));
+    double *gW1 = grad, *gb1 = grad ? grad + (size_t)H * d : NULL;
+    double *gW2 = grad ? gb1 + H : NULL, *gb2 = grad ? gW2 + (size_t)H * H : NULL;
+    double *gW3 = grad ? gb2 + H : NULL, *gb3 = grad ? gW3 + 2 * (size_t)H : NULL;
+    if (grad) memset(grad, 0, ((size_t)H * d + H + (size_t)H * H + H + 2 * (size_t)H + 2) * sizeof(double));
+    double L = 0.0;
+    for (int64_t r = 0; r < m; r++) {
+        const float *x = X + r * d;
+        for (int32_t a = 0; a < H; a++) {
+            double s = b1[a];
+            for (int32_t c = 0; c < d; c++) s += W1[(size_t)a * d + c] * (double)x[c];
+            z1[a] = s;
+            h1[a] = gelu(s);
+        }
+        for (int32_t a = 0; a < H; a++) {
+            double s = b2[a];
+            for (int32_t c = 0; c < H; c++) s += W2[(size_t)a * H + c] * h1[c];
+            z2[a] = s;
+            h2[a] = gelu(s);
+        }
+        double y[2], dy[2];
+        for (int o = 0; o < 2; o++) {
+            double s = b3[o];
+            for (int32_t c = 0; c < H; c++) s += W3[(size_t)o * H + c] * h2[c];
+            y[o] = s;
+            if (Y) Y[2 * r + o] = s;
+            double e = T ? s - (double)T[2 * r + o] : 0.0;
+            L += e * e;
+            dy[o] = 2.0 * e / (double)m;
+        }
+        if (!grad) continue;
+        for (int o = 0; o < 2; o++) {
+            gb3[o] += dy[o];
+            for (int32_t c = 0; c < H; c++) gW3[(size_t)o * H + c] += dy[o] * h2[c];
+        }
+        for (int32_t a = 0; a < H; a++) {
+            double dh = dy[0] * W3[a] + dy[1] * W3[(size_t)H + a];
+            dz2[a] = dh * gelu_d(z2[a]);
+        }
+        for (int32_t a = 0; a < H; a++) {
+            gb2[a] += dz2[a];
+            for (int32_t c = 0; c < H; c++) gW2[(size_t)a * H + c] += dz2[a] * h1[c];
+        }
+        for (int32_t c = 0; c < H; c++) {
+            double dh = 0.0;
+            for (int32_t a = 0; a < H; a++) dh += dz2[a] * W2[(size_t)a * H + c];
+            dz1[c] = dh * gelu_d(z1[c]);
+        }
+        for (int32_t a = 0; a < H; a++) {
+            gb1[a] += dz1[a];
+            for (int32_t c = 0; c < d; c++) gW1[(size_t)a * d + c] += dz1[a] * (double)x[c];
+        }
+    }
+    free(z1); free(h1); free(z2); free(h2); free(dz2); free(dz1);
+    return L / (double)m;
+}
+
+double orc_gelu(double z) { return gelu(z); }
+double orc_gelu_d(double z) { return gelu_d(z); }

@@ -106,6 +106,21 @@ def load(path: str | None = None):
     L.pxsne_kernel_group_name.restype = C.c_char_p
     L.pxsne_get_counters.argtypes = [vp, C.POINTER(u64), C.POINTER(u64)]
     L.pxsne_get_knn_counters.argtypes = [vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(i32)]
+    L.pxsne_set_schedule.argtypes = [vp, C.POINTER(_CParams)]
+    L.pxsne_mlp_create.argtypes = [C.POINTER(vp), i32, u64, vp]
+    L.pxsne_mlp_destroy.argtypes = [vp]
+    L.pxsne_mlp_destroy.restype = None
+    L.pxsne_mlp_last_error.argtypes = [vp]
+    L.pxsne_mlp_last_error.restype = C.c_char_p
+    L.pxsne_mlp_num_params.argtypes = [vp]
+    L.pxsne_mlp_num_params.restype = i64
+    L.pxsne_mlp_set_params.argtypes = [vp, vp]
+    L.pxsne_mlp_get_params.argtypes = [vp, vp]
+    L.pxsne_mlp_loss_grad.argtypes = [vp, vp, vp, i64, vp, C.POINTER(C.c_double), C.c_int]
+    L.pxsne_mlp_train.argtypes = [vp, vp, vp, i64, i32, i32, C.c_float, u64,
+                                  C.POINTER(C.c_double), C.c_int]
+    L.pxsne_mlp_predict.argtypes = [vp, vp, i64, vp, C.c_int]
+    L.pxsne_embed_align.argtypes = [vp, vp, i64, vp, C.c_int]
     L.pxsne_device_bytes.argtypes = [vp]
     L.pxsne_device_bytes.restype = i64
     _lib = L
@@ -300,6 +315,14 @@ class Context:
         self._ck(self.L.pxsne_get_counters(self.h, C.byref(a), C.byref(t)))
         return a.value, t.value
 
+    def set_schedule(self, **kw):
+        """Change optimiser fields (eta, exaggeration, exag_iters, momentum0,
+        momentum1, momentum_switch, min_gain) of this context."""
+        for k, v in kw.items():
+            setattr(self.params, k, v)
+        self._p = self.params.c()
+        self._ck(self.L.pxsne_set_schedule(self.h, C.byref(self._p)))
+
     def knn_counters(self):
         """(exact distances, insertions, path) of the last neighbour search."""
         a, b, p = C.c_uint64(), C.c_uint64(), C.c_int32()
@@ -310,10 +333,102 @@ class Context:
         return int(self.L.pxsne_device_bytes(self.h))
 
 
+class MLP:
+    """The learned warm start (``pxsne_mlp``): d -> 256 -> 256 -> 2, GELU."""
+
+    def __init__(self, d: int, seed: int = 0, stream=None):
+        self.L = load()
+        h = C.c_void_p()
+        rc = self.L.pxsne_mlp_create(C.byref(h), int(d), int(seed), stream)
+        if rc != PXSNE_OK:
+            raise PxsneError(rc, "pxsne_mlp_create")
+        self.h = h
+        self.d = d
+        self.np = int(self.L.pxsne_mlp_num_params(h))
+
+    def _ck(self, rc):
+        if rc != PXSNE_OK:
+            raise PxsneError(rc, self.L.pxsne_mlp_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.pxsne_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def get_params(self):
+        w = np.empty(self.np, np.float32)
+        self._ck(self.L.pxsne_mlp_get_params(self.h, w.ctypes.data))
+        return w
+
+    def set_params(self, w):
+        w = np.ascontiguousarray(w, np.float32)
+        assert w.size == self.np
+        self._ck(self.L.pxsne_mlp_set_params(self.h, w.ctypes.data))
+
+    def loss_grad(self, X, T):
+        X = np.ascontiguousarray(X, np.float32)
+        T = np.ascontiguousarray(T, np.float32)
+        g = np.empty(self.np, np.float32)
+        loss = C.c_double()
+        self._ck(self.L.pxsne_mlp_loss_grad(self.h, X.ctypes.data, T.ctypes.data, X.shape[0],
+                                            g.ctypes.data, C.byref(loss), 0))
+        return loss.value, g
+
+    def train(self, X, T, epochs=10, batch=4096, lr=1e-3, seed=0):
+        Xp, dx = _ptr(np.ascontiguousarray(X, np.float32) if isinstance(X, np.ndarray) else X)
+        Tp, dt = _ptr(np.ascontiguousarray(T, np.float32) if isinstance(T, np.ndarray) else T)
+        assert dx == dt
+        n = X.shape[0]
+        loss = C.c_double()
+        self._ck(self.L.pxsne_mlp_train(self.h, Xp, Tp, n, int(epochs), int(batch), float(lr),
+                                        int(seed), C.byref(loss), dx))
+        return loss.value
+
+    def predict(self, X, Y=None):
+        if isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X, np.float32)
+        n = X.shape[0]
+        if Y is None:
+            Y = np.empty((n, 2), np.float32)
+        Xp, dx = _ptr(X)
+        Yp, dy = _ptr(Y)
+        assert dx == dy
+        self._ck(self.L.pxsne_mlp_predict(self.h, Xp, n, Yp, dx))
+        return Y
+
+
+def embed_align(Y, Yref=None):
+    """Centre, scale to unit RMS and (with Yref) orthogonally align Y (numpy)."""
+    L = load()
+    Y = np.ascontiguousarray(Y, np.float32)
+    out = np.empty_like(Y)
+    R = None if Yref is None else np.ascontiguousarray(Yref, np.float32)
+    rc = L.pxsne_embed_align(Y.ctypes.data, None if R is None else R.ctypes.data, Y.shape[0],
+                             out.ctypes.data, 0)
+    if rc != PXSNE_OK:
+        raise PxsneError(rc, "pxsne_embed_align")
+    return out
+
+
 EXPORTED = ["pxsne_default_params", "pxsne_create", "pxsne_destroy", "pxsne_last_error",
             "pxsne_affinities", "pxsne_init", "pxsne_step", "pxsne_kl", "pxsne_get_Y",
             "pxsne_sync", "pxsne_get_sizes", "pxsne_get_P", "pxsne_set_P", "pxsne_get_knn",
             "pxsne_set_state", "pxsne_get_state", "pxsne_get_tree", "pxsne_get_forces",
             "pxsne_device_bytes", "pxsne_step_profiled", "pxsne_kernel_group_name",
             "pxsne_get_counters", "pxsne_kl_noalloc", "pxsne_kl_noalloc_max_rows",
-            "pxsne_get_knn_counters"]
+            "pxsne_get_knn_counters", "pxsne_set_schedule", "pxsne_mlp_create",
+            "pxsne_mlp_destroy", "pxsne_mlp_last_error", "pxsne_mlp_num_params",
+            "pxsne_mlp_set_params", "pxsne_mlp_get_params", "pxsne_mlp_loss_grad",
+            "pxsne_mlp_train", "pxsne_mlp_predict", "pxsne_embed_align"]

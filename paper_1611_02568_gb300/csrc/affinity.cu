@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 0xffffffffu, tc::mbar_wait(&mbar[buf], (uint32_t)((t >> 1) & 1), kTcPolls));
             if (!got) {
                 s_abort = 1;
-                atomicOr(err, (unsigned)PXSNE_DEVERR_STACK);
+                atomicOr(err, (unsigned)PXSNE_DEVERR_TIMEOUT);
             }
             tc::fence_after();
             if (got) {

@@ -206,11 +206,12 @@ int check_device(pxsne_ctx *c, uint32_t *flags_out) {
     if (err) {
         const unsigned zero = 0;
         CK(c, cudaMemcpy(&c->sc->err, &zero, sizeof(unsigned), cudaMemcpyHostToDevice));
-        return fail(c, PXSNE_E_DEVICE, "device error flags 0x%x%s%s%s%s", err,
+        return fail(c, PXSNE_E_DEVICE, "device error flags 0x%x%s%s%s%s%s", err,
                     (err & PXSNE_DEVERR_NONFINITE) ? " non-finite" : "",
                     (err & PXSNE_DEVERR_STACK) ? " stack-overflow" : "",
                     (err & PXSNE_DEVERR_BISECT) ? " bisection" : "",
-                    (err & PXSNE_DEVERR_RANGE) ? " step-range" : "");
+                    (err & PXSNE_DEVERR_RANGE) ? " step-range" : "",
+                    (err & PXSNE_DEVERR_TIMEOUT) ? " tensor-core-timeout" : "");
     }
     return PXSNE_OK;
 }
@@ -525,6 +526,23 @@ int pxsne_step_profiled(pxsne_ctx *c, int32_t iters, double *group_ms, int32_t n
 
 const char *pxsne_kernel_group_name(int32_t g) {
     return (g >= 0 && g < KG_COUNT) ? kGroupNames[g] : nullptr;
+}
+
+int pxsne_set_schedule(pxsne_ctx *c, const pxsne_params *p) {
+    if (!c || !p) return PXSNE_E_ARG;
+    pxsne_params q = c->p;
+    q.eta = p->eta;
+    q.exaggeration = p->exaggeration;
+    q.exag_iters = p->exag_iters;
+    q.momentum0 = p->momentum0;
+    q.momentum1 = p->momentum1;
+    q.momentum_switch = p->momentum_switch;
+    q.min_gain = p->min_gain;
+    int rc = check_params(&q);
+    if (rc) return fail(c, rc, "%s", g_create_err.c_str());
+    c->p = q;
+    drop_graph(c);  // the update kernel's arguments are part of the graph
+    return PXSNE_OK;
 }
 
 int pxsne_kl(pxsne_ctx *c, double *out) {

@@ -1,0 +1,154 @@
+"""Learned warm start on the GPU vs the FP64 oracle MLP, through the C ABI.
+
+The GPU uses BF16 weights and activations as tensor-core operands with FP32
+accumulation; the oracle runs the same network in FP64 on the same (BF16-
+representable) weights and inputs.  Bars: loss within 1 %, each gradient
+tensor within 3 % relative L2, outputs within 1 % relative L2."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+H = 256
+
+
+@pytest.fixture(scope="module")
+def px():
+    import paper_1611_02568_gb300 as m
+    from paper_1611_02568_gb300 import build
+    build.build()
+    return m
+
+
+def bf16(a):
+    """Round float32 values to the nearest BF16 (ties to even), as float32."""
+    a = np.ascontiguousarray(a, np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32)
+
+
+def split(v, d):
+    net = oracle.MLP.from_flat(v.astype(np.float64), d, H)
+    return net
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def test_mlp_loss_and_gradient_match_oracle(px):
+    d, n = 128, 1000
+    X, _ = datagen.gmm128(seed=5, n=n)
+    X = bf16(X * np.float32(0.25))
+    T = np.random.default_rng(1).standard_normal((n, 2)).astype(np.float32)
+    with px.MLP(d, seed=3) as net:
+        w = bf16(net.get_params())
+        net.set_params(w)
+        loss, g = net.loss_grad(X, T)
+    ref = split(w, d)
+    loss_o, _, g_o = oracle.mlp(ref, X, T, grad=True)
+    assert abs(loss - loss_o) <= 1e-2 * loss_o
+    go = oracle.MLP.from_flat(g_o, d, H)
+    gg = oracle.MLP.from_flat(g.astype(np.float64), d, H)
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        assert rel(getattr(gg, name), getattr(go, name)) <= 3e-2, name
+
+
+def test_mlp_predict_multibatch_and_padded_width(px):
+    d, n = 50, 10000                         # 2 batches of 8192; d padded to 64
+    X, _ = datagen.gauss10(2, n=n, D=d)
+    X = bf16(X * np.float32(0.3))
+    with px.MLP(d, seed=4) as net:
+        w = bf16(net.get_params())
+        net.set_params(w)
+        Y = net.predict(X)
+    _, Yo, _ = oracle.mlp(split(w, d), X)
+    assert rel(Y, Yo) <= 1e-2
+
+
+def test_mlp_training_fits_a_teacher(px):
+    d, n = 128, 20000
+    rng = np.random.default_rng(6)
+    X, _ = datagen.gmm128(seed=6, n=n)
+    X = (X * np.float32(0.25)).astype(np.float32)
+    A = rng.standard_normal((d, 2)) / np.sqrt(d)
+    T = np.tanh(X.astype(np.float64) @ A).astype(np.float32) * 3.0
+    with px.MLP(d, seed=7) as net:
+        l0 = float(((net.predict(X) - T) ** 2).sum(1).mean())
+        last = net.train(X, T, epochs=15, batch=1024, lr=1e-3, seed=1)
+        l1 = float(((net.predict(X) - T) ** 2).sum(1).mean())
+    assert np.isfinite(last)
+    assert l1 < 0.1 * l0, (l0, l1)
+
+
+def test_embed_align_recovers_orthogonal_transforms(px):
+    rng = np.random.default_rng(8)
+    ref = rng.standard_normal((5000, 2)).astype(np.float32) * np.array([3.0, 1.0], np.float32)
+    ref_n = px.embed_align(ref)
+    np.testing.assert_allclose(ref_n.mean(0), 0, atol=1e-5)
+    assert abs((ref_n.astype(np.float64) ** 2).sum() / (2 * 5000) - 1) < 1e-5
+    for refl in (False, True):
+        phi = 0.7
+        R = np.array([[np.cos(phi), -np.sin(phi)], [np.sin(phi), np.cos(phi)]])
+        if refl:
+            R = R @ np.diag([1.0, -1.0])
+        Y = (ref.astype(np.float64) @ R * 17.0 + np.array([5.0, -9.0])).astype(np.float32)
+        out = px.embed_align(Y, ref)
+        np.testing.assert_allclose(out, ref_n, atol=2e-4)
+
+
+def _embedding(px, X, seed, iters, L):
+    with px.Context(px.Params(log2_r=L)) as ctx:
+        ctx.affinities(X)
+        ctx.init(datagen.init_y0(seed, X.shape[0]))
+        ctx.step(iters)
+        Y, _ = ctx.get_Y(want_pix=False)
+    return Y
+
+
+@pytest.mark.slow
+def test_warm_start_beats_random_init_early(px):
+    """The network trained on embeddings of independent draws of the same
+    mixture places a fresh draw so that refinement (no exaggeration) is ahead
+    of the plain method from a random start at equal iteration counts."""
+    n, L = 20000, 10
+    Xs = [datagen.gmm128(seed=s, n=n)[0] for s in (11, 12, 13)]
+    Ys = [_embedding(px, X, s, 1000, L) for s, X in zip((11, 12, 13), Xs)]
+    ref = px.embed_align(Ys[0])
+    Ts = [ref] + [px.embed_align(Y, ref) for Y in Ys[1:]]
+    Xtr = np.concatenate(Xs) * np.float32(0.1)
+    Ttr = np.concatenate(Ts)
+    Xf, _ = datagen.gmm128(seed=21, n=n)
+    with px.MLP(128, seed=1) as net:
+        net.train(Xtr, Ttr, epochs=20, batch=2048, lr=1e-3, seed=2)
+        Y0w = net.predict(Xf * np.float32(0.1))
+    with px.Context(px.Params(log2_r=L)) as ctx:
+        ctx.affinities(Xf)
+        ctx.init(datagen.init_y0(21, n))
+        ctx.step(300)
+        kl_plain_300 = ctx.kl()
+        ctx.step(700)
+        kl_plain = ctx.kl()
+        Yp, _ = ctx.get_Y(want_pix=False)
+        rms = float(np.sqrt((Yp.astype(np.float64) ** 2).sum() / (2 * n)))
+        ctx.set_schedule(exag_iters=0, momentum_switch=0)
+        ctx.init((Y0w * rms).astype(np.float32))
+        kl_warm_0 = ctx.kl()
+        ctx.step(300)
+        kl_warm_300 = ctx.kl()
+        # iterations of the warm start to reach the plain run's final KL
+        it = 300
+        kl = kl_warm_300
+        while kl > kl_plain and it < 1000:
+            ctx.step(50)
+            it += 50
+            kl = ctx.kl()
+    print(f"plain: KL(300) {kl_plain_300:.4f} KL(1000) {kl_plain:.4f}; warm: KL(0) "
+          f"{kl_warm_0:.4f} KL(300) {kl_warm_300:.4f}, reaches {kl:.4f} at {it}")
+    assert kl_warm_300 < kl_plain_300, (kl_warm_300, kl_plain_300)
+    assert kl_warm_0 > kl_warm_300
+    assert kl <= kl_plain and it < 1000, (it, kl, kl_plain)

@@ -492,3 +492,51 @@ def test_nbr_precision_identity_cases():
     # unrelated geometry: precision ~ k / n
     z2, s2 = oracle.init_fx(rng.standard_normal((n, 2)))
     assert oracle.nbr_precision(idx, k, z2, s2) < 0.15
+
+
+# ------------------------------------------------------------------ MLP warm start
+def _gelu_ref(z):
+    return 0.5 * z * (1.0 + math.erf(z / math.sqrt(2.0)))
+
+
+def test_gelu_against_erf_definition():
+    for z in (-6.0, -1.3, -0.2, 0.0, 0.7, 2.5, 8.0):
+        assert abs(oracle.gelu(z) - _gelu_ref(z)) < 1e-15
+        h = 1e-6
+        fd = (_gelu_ref(z + h) - _gelu_ref(z - h)) / (2 * h)
+        assert abs(oracle.gelu_d(z) - fd) < 1e-8
+
+
+def test_mlp_forward_closed_form():
+    # identity weights, zero biases: y = g(g(x)) component-wise (d = H = 2)
+    I = np.eye(2)
+    net = oracle.MLP(I.copy(), np.zeros(2), I.copy(), np.zeros(2), I.copy(), np.array([0.5, -1.0]))
+    X = np.array([[0.3, -1.7], [2.0, 0.0]], np.float32)
+    _, Y, _ = oracle.mlp(net, X)
+    for r in range(2):
+        for o in range(2):
+            ref = _gelu_ref(_gelu_ref(float(X[r, o]))) + net.b3[o]
+            assert abs(Y[r, o] - ref) < 1e-14
+
+
+def test_mlp_gradient_finite_differences():
+    rng = np.random.default_rng(21)
+    d, H, m = 5, 7, 9
+    net = oracle.MLP(rng.standard_normal((H, d)) * 0.5, rng.standard_normal(H) * 0.1,
+                     rng.standard_normal((H, H)) * 0.4, rng.standard_normal(H) * 0.1,
+                     rng.standard_normal((2, H)) * 0.5, rng.standard_normal(2) * 0.1)
+    X = rng.standard_normal((m, d)).astype(np.float32)
+    T = rng.standard_normal((m, 2)).astype(np.float32)
+    L, _, g = oracle.mlp(net, X, T, grad=True)
+    v = net.flat()
+    h = 1e-6
+    for q in rng.choice(v.size, 40, replace=False):
+        vp, vm = v.copy(), v.copy()
+        vp[q] += h
+        vm[q] -= h
+        Lp, _, _ = oracle.mlp(oracle.MLP.from_flat(vp, d, H), X, T)
+        Lm, _, _ = oracle.mlp(oracle.MLP.from_flat(vm, d, H), X, T)
+        assert abs((Lp - Lm) / (2 * h) - g[q]) < 1e-7 * max(1.0, abs(g[q]))
+    # the loss is the mean squared error of the outputs
+    _, Y, _ = oracle.mlp(net, X)
+    assert abs(L - ((Y - T) ** 2).sum() / m) < 1e-12
