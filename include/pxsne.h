@@ -145,6 +145,17 @@ int pxsne_kl(pxsne_ctx *ctx, double *out);
  * Synchronises. */
 int pxsne_get_Y(pxsne_ctx *ctx, float *Y, int32_t *pix, int on_device);
 
+/* Neighbourhood precision of the current embedding (Eq. nei_prec):
+ * (1/(k n)) sum_i |N_D^k(i) ∩ N_d^k(i)|.  N_D^k(i) = the first k entries of row
+ * i of knn_hd (n x kh int32, host or device per on_device, neighbours in
+ * ascending distance; NULL = the lists of the last pxsne_affinities).
+ * N_d^k(i) = the exact k nearest points of i in the 2-D embedding by squared
+ * y-space distance (FP64), ties to the lower index.  1 <= k <= min(32, kh).
+ * hits (host, n int32, may be NULL) gets |N_D^k(i) ∩ N_d^k(i)| per point.
+ * Synchronises. */
+int pxsne_nbr_precision(pxsne_ctx *ctx, int32_t k, const int32_t *knn_hd, int32_t kh,
+                        int on_device, double *precision, int32_t *hits);
+
 /* Wait for the context's stream; returns PXSNE_E_DEVICE if a kernel flagged
  * an error since the last check (flags in *dev_errors when non-NULL). */
 int pxsne_sync(pxsne_ctx *ctx, uint32_t *dev_errors);
@@ -261,6 +272,17 @@ int pxsne_mlp_train(pxsne_mlp *m, const float *X, const float *T, int64_t n, int
 
 /* Y = MLP(X) for n rows. */
 int pxsne_mlp_predict(pxsne_mlp *m, const float *X, int64_t n, float *Y, int on_device);
+
+/* PCA pre-processing (Sec. 5.1.1 reduces every dataset to 50 dimensions
+ * before P): Xout (n x dout) = (X - mean) V with V the dout leading
+ * eigenvectors of the sample covariance (X - mean)^T (X - mean) / (n - 1).
+ * Mean and covariance are formed on the GPU (FP32 tiles, FP64 sums); V comes
+ * from block subspace iteration with a Rayleigh-Ritz step on the host in FP64
+ * (start drawn from `seed`); each eigenvector's largest component is positive.
+ * components (host, D x dout row-major) and eigenvalues (host, dout,
+ * descending) may be NULL.  X / Xout host or device per on_device. */
+int pxsne_pca(const float *X, int64_t n, int32_t D, int32_t dout, float *Xout,
+              float *components, float *eigenvalues, int on_device, uint64_t seed);
 
 /* Normalise an embedding Y (n x 2) to zero mean and unit RMS per coordinate
  * (isotropic scale) and, when Yref is non-NULL, apply the orthogonal map

@@ -84,7 +84,7 @@ def lib():
         L.orc_run.restype = C.c_int
         L.orc_Z.argtypes = [C.c_void_p, i64, pu32, pd]
         L.orc_Z.restype = dbl
-        L.orc_nbr_precision.argtypes = [pi32, i32, i32, i64, pu32, pd, pi64, i64]
+        L.orc_nbr_precision.argtypes = [pi32, i32, i32, i64, pu32, pd, pi64, i64, pi32]
         L.orc_nbr_precision.restype = dbl
         L.orc_mlp.argtypes = [C.c_int32, C.c_int32, pd, pd, pd, pd, pd, pd, pf, pf, i64, pd, pd]
         L.orc_mlp.restype = dbl
@@ -385,16 +385,19 @@ def kl_of(P: CSR, state: State, params: Params):
     return kl(P, state.z, state.s, Z_of(state, params))
 
 
-def nbr_precision(knn_hd, k, z, s, rows=None):
+def nbr_precision(knn_hd, k, z, s, rows=None, per_row=False):
+    """Eq. nei_prec over the listed rows; with per_row also the hit counts."""
     knn_hd = np.ascontiguousarray(knn_hd, dtype=np.int32)
     z = np.ascontiguousarray(z, dtype=np.uint32)
     s = np.ascontiguousarray(s, dtype=np.float64)
     n = z.shape[0]
     r, m = _rows(rows, n)
     assert knn_hd.shape[0] == m and knn_hd.shape[1] >= k
-    return float(lib().orc_nbr_precision(_P(knn_hd, C.c_int32), knn_hd.shape[1], k, n,
-                                         _P(z, C.c_uint32), _P(s, C.c_double),
-                                         _ptr_or_null(r, C.c_int64), m))
+    hits = np.empty(m, dtype=np.int32)
+    v = float(lib().orc_nbr_precision(_P(knn_hd, C.c_int32), knn_hd.shape[1], k, n,
+                                      _P(z, C.c_uint32), _P(s, C.c_double),
+                                      _ptr_or_null(r, C.c_int64), m, _P(hits, C.c_int32)))
+    return (v, hits) if per_row else v
 
 
 # ---------------------------------------------------------------- MLP warm start
@@ -449,3 +452,20 @@ def mlp(net: MLP, X, T=None, grad=False):
                       None if Tc is None else _P(Tc, C.c_float), m, _P(Y, C.c_double),
                       None if g is None else _P(g, C.c_double))
     return float(L), Y, g
+
+
+# ---------------------------------------------------------------- PCA (Sec. 5.1.1)
+def pca(X, dout):
+    """(projection, components [D, dout], eigenvalues) from the FP64 sample
+    covariance and numpy's symmetric eigensolver; each component's largest
+    entry is positive."""
+    Xd = np.asarray(X, dtype=np.float64)
+    mu = Xd.mean(0)
+    Xc = Xd - mu
+    Cv = Xc.T @ Xc / (Xd.shape[0] - 1)
+    lam, V = np.linalg.eigh(Cv)
+    order = np.argsort(-lam, kind="stable")[:dout]
+    lam, V = lam[order], V[:, order]
+    sg = np.sign(V[np.argmax(np.abs(V), axis=0), np.arange(dout)])
+    V = V * sg
+    return Xc @ V, V, lam

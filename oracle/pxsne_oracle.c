@@ -614,7 +614,7 @@ out:
  * row q holds the neighbours of rows[q], at least k per row, stride kh). */
 double orc_nbr_precision(const int32_t *knn_hd, int32_t kh, int32_t k, int64_t n,
                          const uint32_t *z, const double *s, const int64_t *rows,
-                         int64_t m)
+                         int64_t m, int32_t *hits_out)
 {
     const double s0 = s[0], s1 = s[1];
     int64_t hits = 0;
@@ -638,9 +638,12 @@ double orc_nbr_precision(const int32_t *knn_hd, int32_t kh, int32_t k, int64_t n
             }
             Dd[p] = dd; I[p] = (int32_t)j;
         }
+        int32_t h = 0;
         for (int32_t a = 0; a < k; a++)
             for (int32_t b = 0; b < k; b++)
-                if (knn_hd[q * (int64_t)kh + b] == I[a]) { hits++; break; }
+                if (knn_hd[q * (int64_t)kh + b] == I[a]) { h++; break; }
+        hits += h;
+        if (hits_out) hits_out[q] = h;
         free(I);
         free(Dd);
     }

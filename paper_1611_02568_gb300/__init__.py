@@ -107,6 +107,7 @@ def load(path: str | None = None):
     L.pxsne_get_counters.argtypes = [vp, C.POINTER(u64), C.POINTER(u64)]
     L.pxsne_get_knn_counters.argtypes = [vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(i32)]
     L.pxsne_set_schedule.argtypes = [vp, C.POINTER(_CParams)]
+    L.pxsne_nbr_precision.argtypes = [vp, i32, vp, i32, C.c_int, C.POINTER(C.c_double), vp]
     L.pxsne_mlp_create.argtypes = [C.POINTER(vp), i32, u64, vp]
     L.pxsne_mlp_destroy.argtypes = [vp]
     L.pxsne_mlp_destroy.restype = None
@@ -121,6 +122,7 @@ def load(path: str | None = None):
                                   C.POINTER(C.c_double), C.c_int]
     L.pxsne_mlp_predict.argtypes = [vp, vp, i64, vp, C.c_int]
     L.pxsne_embed_align.argtypes = [vp, vp, i64, vp, C.c_int]
+    L.pxsne_pca.argtypes = [vp, i64, i32, i32, vp, vp, vp, C.c_int, u64]
     L.pxsne_device_bytes.argtypes = [vp]
     L.pxsne_device_bytes.restype = i64
     _lib = L
@@ -315,6 +317,23 @@ class Context:
         self._ck(self.L.pxsne_get_counters(self.h, C.byref(a), C.byref(t)))
         return a.value, t.value
 
+    def nbr_precision(self, k=10, knn_hd=None, per_point=False):
+        """Eq. nei_prec of the current embedding (high-D lists from the last
+        affinities call unless knn_hd [n x kh] is given)."""
+        n = self.sizes()[0]
+        prec = C.c_double()
+        hits = np.empty(n, np.int32) if per_point else None
+        if knn_hd is None:
+            rc = self.L.pxsne_nbr_precision(self.h, int(k), None, 0, 0, C.byref(prec),
+                                            None if hits is None else hits.ctypes.data)
+        else:
+            kd = np.ascontiguousarray(knn_hd, np.int32)
+            rc = self.L.pxsne_nbr_precision(self.h, int(k), kd.ctypes.data, kd.shape[1], 0,
+                                            C.byref(prec),
+                                            None if hits is None else hits.ctypes.data)
+        self._ck(rc)
+        return (prec.value, hits) if per_point else prec.value
+
     def set_schedule(self, **kw):
         """Change optimiser fields (eta, exaggeration, exag_iters, momentum0,
         momentum1, momentum_switch, min_gain) of this context."""
@@ -422,6 +441,21 @@ def embed_align(Y, Yref=None):
     return out
 
 
+def pca(X, dout=50, seed=0):
+    """(projection [n, dout], components [D, dout], eigenvalues [dout])."""
+    L = load()
+    X = np.ascontiguousarray(X, np.float32)
+    n, D = X.shape
+    out = np.empty((n, dout), np.float32)
+    V = np.empty((D, dout), np.float32)
+    lam = np.empty(dout, np.float32)
+    rc = L.pxsne_pca(X.ctypes.data, n, D, int(dout), out.ctypes.data, V.ctypes.data,
+                     lam.ctypes.data, 0, int(seed))
+    if rc != PXSNE_OK:
+        raise PxsneError(rc, "pxsne_pca")
+    return out, V, lam
+
+
 EXPORTED = ["pxsne_default_params", "pxsne_create", "pxsne_destroy", "pxsne_last_error",
             "pxsne_affinities", "pxsne_init", "pxsne_step", "pxsne_kl", "pxsne_get_Y",
             "pxsne_sync", "pxsne_get_sizes", "pxsne_get_P", "pxsne_set_P", "pxsne_get_knn",
@@ -431,4 +465,5 @@ EXPORTED = ["pxsne_default_params", "pxsne_create", "pxsne_destroy", "pxsne_last
             "pxsne_get_knn_counters", "pxsne_set_schedule", "pxsne_mlp_create",
             "pxsne_mlp_destroy", "pxsne_mlp_last_error", "pxsne_mlp_num_params",
             "pxsne_mlp_set_params", "pxsne_mlp_get_params", "pxsne_mlp_loss_grad",
-            "pxsne_mlp_train", "pxsne_mlp_predict", "pxsne_embed_align"]
+            "pxsne_mlp_train", "pxsne_mlp_predict", "pxsne_embed_align",
+            "pxsne_nbr_precision", "pxsne_pca"]

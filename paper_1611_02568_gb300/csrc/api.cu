@@ -587,6 +587,44 @@ int pxsne_get_Y(pxsne_ctx *c, float *Y, int32_t *pix, int on_device) {
     return check_device(c, nullptr);
 }
 
+int pxsne_nbr_precision(pxsne_ctx *c, int32_t k, const int32_t *knn_hd, int32_t kh,
+                        int on_device, double *precision, int32_t *hits) {
+    int rc = need_state(c);
+    if (rc) return rc;
+    if (!knn_hd) {
+        if (!c->knn_idx) return fail(c, PXSNE_E_STATE, "no neighbour lists: pass knn_hd");
+        knn_hd = c->knn_idx;
+        kh = c->knn_k;
+        on_device = 1;
+    }
+    if (k < 1 || k > 32 || k > kh || (int64_t)k >= c->n)
+        return fail(c, PXSNE_E_ARG, "need 1 <= k <= min(32, kh) and k < n");
+    cudaStream_t st = c->stream;
+    const int64_t n = c->n;
+    int32_t *dh = nullptr, *dk = nullptr;
+    unsigned long long *dt = nullptr;
+    CK(c, cudaMallocAsync(&dh, (size_t)n * 4, st));
+    CK(c, cudaMallocAsync(&dt, 8, st));
+    CK(c, cudaMemsetAsync(dt, 0, 8, st));
+    const int32_t *kd = knn_hd;
+    if (!on_device) {
+        CK(c, cudaMallocAsync(&dk, (size_t)n * kh * 4, st));
+        CK(c, cudaMemcpyAsync(dk, knn_hd, (size_t)n * kh * 4, cudaMemcpyHostToDevice, st));
+        kd = dk;
+    }
+    CK(c, launch_nbr_precision(c, k, kd, kh, dh, dt));
+    unsigned long long tot = 0;
+    CK(c, cudaMemcpyAsync(&tot, dt, 8, cudaMemcpyDeviceToHost, st));
+    if (hits) CK(c, cudaMemcpyAsync(hits, dh, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+    CK(c, cudaFreeAsync(dh, st));
+    CK(c, cudaFreeAsync(dt, st));
+    if (dk) CK(c, cudaFreeAsync(dk, st));
+    rc = check_device(c, nullptr);
+    if (rc) return rc;
+    if (precision) *precision = (double)tot / ((double)k * (double)n);
+    return PXSNE_OK;
+}
+
 int pxsne_sync(pxsne_ctx *c, uint32_t *dev_errors) {
     if (!c) return PXSNE_E_ARG;
     return check_device(c, dev_errors);

@@ -204,4 +204,6 @@ cudaError_t build_symmetric_csr(pxsne_ctx *c, const int32_t *idx, const float *p
                                 int64_t n, int32_t k, std::string &err);
 cudaError_t launch_level_counts(pxsne_ctx *c, int level, uint32_t *cnt);
 cudaError_t launch_morton_keys(pxsne_ctx *c, uint32_t *keys);
+cudaError_t launch_nbr_precision(pxsne_ctx *c, int k, const int32_t *knn_hd, int kh,
+                                 int32_t *hits, unsigned long long *total);
 }  // namespace pxsne

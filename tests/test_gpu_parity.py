@@ -295,3 +295,38 @@ def test_invalid_calls(px):
             ctx.affinities(X)
         with pytest.raises(px.PxsneError):
             ctx.affinities(np.zeros((50, 300), np.float32))   # D > 256
+
+
+@pytest.mark.parametrize("k", [1, 10, 32])
+def test_nbr_precision_matches_oracle(px, gauss, k):
+    X, P, Y0, st = gauss
+    kh = 90
+    idx, _ = oracle.knn(X, kh)
+    z = st.z.copy()
+    z[10] = z[11]                 # coinciding points: ties to the lower index
+    z[12] = z[11]
+    with make_ctx(px, L=9) as ctx:
+        ctx.set_P(P.row_ptr, P.col, P.val.astype(np.float32))
+        ctx.set_state(z, st.s)
+        prec, hits = ctx.nbr_precision(k=k, knn_hd=idx, per_point=True)
+    prec_o, hits_o = oracle.nbr_precision(idx, k, z, st.s, per_row=True)
+    assert np.array_equal(hits, hits_o)
+    assert prec == pytest.approx(prec_o, abs=1e-15)
+
+
+def test_pca_matches_oracle(px):
+    """MNIST-shaped workload (784-D, 10 classes) at 8,000 rows, 50 components."""
+    X, _ = datagen.protos784(seed=4, n=8000)
+    Z, V, lam = px.pca(X, 50, seed=1)
+    Zo, Vo, lamo = oracle.pca(X, 50)
+    # the leading, well separated eigenpairs agree; the 50-dim subspace keeps the
+    # same variance
+    np.testing.assert_allclose(lam[:10], lamo[:10], rtol=1e-4)
+    P10 = V[:, :10].astype(np.float64) @ V[:, :10].T
+    Po10 = Vo[:, :10] @ Vo[:, :10].T
+    assert np.linalg.norm(P10 - Po10) < 1e-3
+    assert abs(lam.sum() - lamo.sum()) <= 2e-3 * lamo.sum()
+    np.testing.assert_allclose(V.T.astype(np.float64) @ V, np.eye(50), atol=1e-4)
+    # projections agree up to the (fixed) signs of the leading components
+    rel = np.linalg.norm(Z[:, :10] - Zo[:, :10]) / np.linalg.norm(Zo[:, :10])
+    assert rel < 1e-3

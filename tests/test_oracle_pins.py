@@ -540,3 +540,34 @@ def test_mlp_gradient_finite_differences():
     # the loss is the mean squared error of the outputs
     _, Y, _ = oracle.mlp(net, X)
     assert abs(L - ((Y - T) ** 2).sum() / m) < 1e-12
+
+
+def test_nbr_precision_bruteforce_per_row():
+    rng = np.random.default_rng(22)
+    n, k, kh = 400, 10, 15
+    z = rng.integers(0, 2 ** 20, (n, 2)).astype(np.uint32)
+    z[5] = z[6]                 # duplicate positions: ties go to the lower index
+    z[100] = z[6]
+    s = np.array([2e-6, 3e-6])
+    knn_hd = np.stack([rng.choice(n, kh, replace=False) for _ in range(n)]).astype(np.int32)
+    prec, hits = oracle.nbr_precision(knn_hd, k, z, s, per_row=True)
+    y = z.astype(np.float64) * s
+    dd = ((y[:, None, :] - y[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(dd, np.inf)
+    nn2 = np.argsort(dd, axis=1, kind="stable")[:, :k]
+    ref = np.array([len(set(nn2[i]) & set(knn_hd[i, :k])) for i in range(n)])
+    assert np.array_equal(hits, ref)
+    assert abs(prec - ref.sum() / (k * n)) < 1e-15
+
+
+def test_pca_against_svd():
+    rng = np.random.default_rng(23)
+    X = rng.standard_normal((500, 12)) @ rng.standard_normal((12, 12)) + 3.0
+    Z, V, lam = oracle.pca(X, 5)
+    Xc = X - X.mean(0)
+    U, S, Vt = np.linalg.svd(Xc, full_matrices=False)       # a different routine
+    np.testing.assert_allclose(lam, S[:5] ** 2 / (X.shape[0] - 1), rtol=1e-10)
+    for c in range(5):
+        assert abs(abs(V[:, c] @ Vt[c]) - 1.0) < 1e-8
+    np.testing.assert_allclose(V.T @ V, np.eye(5), atol=1e-12)
+    np.testing.assert_allclose(Z.var(0, ddof=1), lam, rtol=1e-10)
