@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=40000,
                     help="rows of the oracle sample (CPU baseline)")
+    ap.add_argument("--no-warmstart", action="store_true",
+                    help="skip the learned warm-start experiment")
+    ap.add_argument("--warm-seeds", type=int, default=20)
+    ap.add_argument("--warm-n", type=int, default=50000)
     return ap.parse_args()
 
 
@@ -180,6 +184,79 @@ def oracle_sample(_unused, Y0, rows, L, theta, seed=0):
     return 1.0 / per_iter, det, (t4 - t0)
 
 
+def warmstart_experiment(px, ctx, X, Y0, args, torch):
+    """Learned warm start (survey config 4): an MLP trained on embeddings the
+    method produced for independent draws of the same mixture, applied to this
+    draw, refined without exaggeration; iterations and wall time to the plain
+    run's final KL.  Reuses ctx's P (the bench workload)."""
+    import datagen
+    W = WORKLOAD
+    n = X.shape[0]
+    xs = np.float32(0.1)  # input scale of the network
+    # plain run: 1,000 iterations of the full schedule from Y0
+    ctx.set_schedule(exaggeration=12.0, exag_iters=250, momentum0=0.5, momentum1=0.8,
+                     momentum_switch=250)
+    ctx.init(Y0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.step(1000)
+    kl_plain = ctx.kl()
+    t_plain = time.perf_counter() - t0
+    Yp, _ = ctx.get_Y(want_pix=False)
+    rms = float(np.sqrt((Yp.astype(np.float64) ** 2).sum() / (2 * n)))
+    prec_plain = ctx.nbr_precision(10)
+    # training embeddings
+    t0 = time.perf_counter()
+    Xs, Ts = [], []
+    ref = None
+    for k in range(args.warm_seeds):
+        sd = 1000 + k
+        Xk, _ = datagen.gmm128(seed=sd, n=args.warm_n)
+        with px.Context(px.Params(log2_r=W["log2_r"], theta=W["theta"], k=W["k"],
+                                  perplexity=W["perplexity"])) as c2:
+            c2.affinities(Xk)
+            c2.init(datagen.init_y0(sd, args.warm_n))
+            c2.step(1000)
+            Yk, _ = c2.get_Y(want_pix=False)
+        Yk = px.embed_align(Yk, ref)
+        if ref is None:
+            ref = Yk
+        Xs.append(Xk * xs)
+        Ts.append(Yk)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    with px.MLP(X.shape[1], seed=1) as net:
+        train_loss = net.train(np.concatenate(Xs), np.concatenate(Ts), epochs=10, batch=4096,
+                               lr=1e-3, seed=2)
+        t_train = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        # warm start: inference + refinement until the plain run's final KL
+        t0 = time.perf_counter()
+        Yw = net.predict(X * xs) * np.float32(rms)
+    ctx.set_schedule(exag_iters=0, momentum_switch=0)
+    ctx.init(Yw.astype(np.float32))
+    kl0 = ctx.kl()
+    it, kl = 0, kl0
+    trace = [(0, kl0)]
+    while kl > kl_plain and it < 1000:
+        ctx.step(25)
+        it += 25
+        kl = ctx.kl()
+        trace.append((it, kl))
+    t_warm = time.perf_counter() - t0
+    prec_warm = ctx.nbr_precision(10)
+    reached = kl <= kl_plain
+    return {"plain": {"iterations": 1000, "kl": kl_plain, "wall_s": t_plain,
+                      "precision_k10": prec_plain},
+            "warm": {"iterations_to_plain_kl": it if reached else None, "reached": reached,
+                     "kl": kl, "kl_at_start": kl0, "wall_s_to_plain_kl": t_warm,
+                     "precision_k10": prec_warm, "trace": trace[:: max(1, len(trace) // 12)]},
+            "training": {"embeddings": args.warm_seeds, "rows_each": args.warm_n,
+                         "data_s": t_data, "train_s": t_train, "final_mse": train_loss},
+            "schedule": "warm: no exaggeration, momentum 0.8, eta 200, gains reset; "
+                        "start scaled to the plain run's final RMS"}
+
+
 def run_reference(args):
     """The oracle (plain FP64 C, OpenMP) as the reference arm."""
     ws, rank, _ = dist_env()
@@ -283,7 +360,7 @@ def run_gpu(args):
     # events around each kernel group on the library's stream
     ctx.init(Y0)
     groups, prof_total = ctx.step_profiled(args.steps)
-    acc, tst = ctx.counters()
+    acc, tst, wsteps, nodes = ctx.counters()
     peaks, peak_kind = measured_peaks()
     gb = group_bytes(n, nnz, W["log2_r"])
     top = max(groups, key=groups.get)
@@ -349,6 +426,13 @@ def run_gpu(args):
                           f"{det['rows']} of {n} rows scaled by {det['scale']:.1f} + full "
                           f"update/rescale ({w:.1f} s of CPU work)")}
 
+    warm = None
+    if rank == 0 and not args.no_warmstart:
+        try:
+            warm = warmstart_experiment(px, ctx, X, Y0, args, torch)
+        except Exception as ex:  # the experiment must not take the bench line down
+            warm = {"error": repr(ex)}
+
     ctx.close()
     if rank == 0:
         line = {
@@ -362,10 +446,12 @@ def run_gpu(args):
                                               "timed_iterations": f"t = 0..{args.steps - 1}"},
             "roofline": roof, "kernels": kernels,
             "traversal": {"accepted_pairs": acc, "tested_pairs": tst,
-                          "accepted_per_point": acc / n, "tested_per_point": tst / n},
+                          "accepted_per_point": acc / n, "tested_per_point": tst / n,
+                          "warp_steps": wsteps, "nodes": nodes,
+                          "lanes_per_step": tst / wsteps if wsteps else None},
             "profiled_total_ms": prof_total, "p_construction_s": p_seconds,
             "kl_after_timed": kl_after,
-            "clocks": ck, "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": ck, "e2e": e2e, "cpu_baseline": cpu, "warmstart": warm,
             # per iteration: update, snap_hist, ceil(L/5) pyramid passes, scan,
             # perm_scatter, traverse, attract, zsum
             "gpu_launches": args.steps * (7 + (W["log2_r"] + 4) // 5),

@@ -219,10 +219,14 @@ int pxsne_step_profiled(pxsne_ctx *ctx, int32_t iters, double *group_ms, int32_t
 /* Name of kernel group g (0 <= g < 7), or NULL. */
 const char *pxsne_kernel_group_name(int32_t g);
 
-/* Work counters of the last Barnes-Hut traversal: n_accept = accepted
- * (point, cell) pairs (the interactions of Eq. bh_criteria), n_test = tested
- * pairs (accepted + opened + own-pixel).  Synchronises. */
-int pxsne_get_counters(pxsne_ctx *ctx, uint64_t *n_accept, uint64_t *n_test);
+/* Work counters of the last Barnes-Hut traversal run by the sequential
+ * schedule (pxsne_init, pxsne_set_state, pxsne_step_profiled): n_accept =
+ * accepted (point, cell) pairs (the interactions of Eq. bh_criteria), n_test =
+ * tested pairs (accepted + opened + own-pixel), n_warp_steps = warp-level
+ * (node, non-empty child) steps, n_nodes = stack entries popped.  Any pointer
+ * may be NULL.  Synchronises. */
+int pxsne_get_counters(pxsne_ctx *ctx, uint64_t *n_accept, uint64_t *n_test,
+                       uint64_t *n_warp_steps, uint64_t *n_nodes);
 
 /* Work counters of the last neighbour search: exact FP32 distances computed
  * and list insertions over all rows (tensor-core search only; 0 otherwise),

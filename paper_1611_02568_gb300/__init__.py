@@ -104,7 +104,8 @@ def load(path: str | None = None):
                                       C.POINTER(C.c_double)]
     L.pxsne_kernel_group_name.argtypes = [i32]
     L.pxsne_kernel_group_name.restype = C.c_char_p
-    L.pxsne_get_counters.argtypes = [vp, C.POINTER(u64), C.POINTER(u64)]
+    L.pxsne_get_counters.argtypes = [vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(u64),
+                                     C.POINTER(u64)]
     L.pxsne_get_knn_counters.argtypes = [vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(i32)]
     L.pxsne_set_schedule.argtypes = [vp, C.POINTER(_CParams)]
     L.pxsne_nbr_precision.argtypes = [vp, i32, vp, i32, C.c_int, C.POINTER(C.c_double), vp]
@@ -312,10 +313,12 @@ class Context:
         return out, tot.value
 
     def counters(self):
-        """(accepted, tested) (point, cell) pairs of the last traversal."""
-        a, t = C.c_uint64(), C.c_uint64()
-        self._ck(self.L.pxsne_get_counters(self.h, C.byref(a), C.byref(t)))
-        return a.value, t.value
+        """(accepted pairs, tested pairs, warp steps, nodes) of the last
+        counted traversal."""
+        a, t, w, nd = C.c_uint64(), C.c_uint64(), C.c_uint64(), C.c_uint64()
+        self._ck(self.L.pxsne_get_counters(self.h, C.byref(a), C.byref(t), C.byref(w),
+                                           C.byref(nd)))
+        return a.value, t.value, w.value, nd.value
 
     def nbr_precision(self, k=10, knn_hd=None, per_point=False):
         """Eq. nei_prec of the current embedding (high-D lists from the last

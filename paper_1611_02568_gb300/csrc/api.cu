@@ -739,7 +739,8 @@ int pxsne_get_forces(pxsne_ctx *c, float *Frep, float *Zi, float *Fattr, double 
     return check_device(c, nullptr);
 }
 
-int pxsne_get_counters(pxsne_ctx *c, uint64_t *n_accept, uint64_t *n_test) {
+int pxsne_get_counters(pxsne_ctx *c, uint64_t *n_accept, uint64_t *n_test,
+                       uint64_t *n_warp_steps, uint64_t *n_nodes) {
     int rc = need_state(c);
     if (rc) return rc;
     DevScalars h;
@@ -748,6 +749,8 @@ int pxsne_get_counters(pxsne_ctx *c, uint64_t *n_accept, uint64_t *n_test) {
     if (rc) return rc;
     if (n_accept) *n_accept = h.n_accept;
     if (n_test) *n_test = h.n_test;
+    if (n_warp_steps) *n_warp_steps = h.n_steps;
+    if (n_nodes) *n_nodes = h.n_nodes;
     return PXSNE_OK;
 }
 

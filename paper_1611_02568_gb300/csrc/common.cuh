@@ -38,6 +38,8 @@ struct DevScalars {
     unsigned ticket2;    // same for the KL reduction
     u64 n_accept;        // accepted (point, cell) pairs of the last traversal
     u64 n_test;          // (point, cell) pairs tested by the last traversal
+    u64 n_steps;         // warp-level (node, non-empty child) steps of the last traversal
+    u64 n_nodes;         // stack entries popped by the last traversal
     u64 knn_exact;       // exact distances computed by the last neighbour search
     u64 knn_insert;      // list insertions of the last neighbour search
 };

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kTravWarps * 32, 5)
     const float zhy = (float)(zi.y & 0xffff0000u), zly = (float)(zi.y & 0xffffu);
     const float sf0 = sc->sf[0], sf1 = sc->sf[1];
     float fx = 0.f, fy = 0.f, zs = 0.f;
-    uint32_t n_acc = 0u, n_tst = 0u;
+    uint32_t n_acc = 0u, n_tst = 0u, n_stp = 0u, n_nod = 0u;
 
     uint32_t *stn = s_node[w];
     uint32_t *stm = s_mask[w];
@@ -92,6 +92,10 @@ __global__ void __launch_bounds__(kTravWarps * 32, 5)
         const bool me = (mask >> lane) & 1u;
         const uint32_t mine = mi >> (2 * (L - lc));  // own cell at level lc
         const float Nc[4] = {nv.x, nv.y, nv.z, nv.w};
+        if (COUNT) {
+            n_nod++;
+            n_stp += (nv.x != 0.f) + (nv.y != 0.f) + (nv.z != 0.f) + (nv.w != 0.f);
+        }
         if (lc == L) {
 #pragma unroll
             for (int ch = 0; ch < 4; ch++) {
@@ -169,6 +173,10 @@ __global__ void __launch_bounds__(kTravWarps * 32, 5)
         __syncwarp();
         if (overflow) break;
     }
+    if (valid) {
+        Frep[i] = make_float2(fx, fy);
+        Zi[i] = zs;
+    }
     if (overflow && lane == 0) atomicOr(&sc->err, (unsigned)PXSNE_DEVERR_STACK);
     if (COUNT) {
 #pragma unroll
@@ -179,11 +187,9 @@ __global__ void __launch_bounds__(kTravWarps * 32, 5)
         if (lane == 0) {
             atomicAdd(&sc->n_accept, (u64)n_acc);
             atomicAdd(&sc->n_test, (u64)n_tst);
+            atomicAdd(&sc->n_steps, (u64)n_stp);
+            atomicAdd(&sc->n_nodes, (u64)n_nod);
         }
-    }
-    if (valid) {
-        Frep[i] = make_float2(fx, fy);
-        Zi[i] = zs;
     }
 }
 

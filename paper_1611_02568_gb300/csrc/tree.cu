@@ -49,6 +49,8 @@ __global__ void k_snap_hist(int n, int L, int rescale, float theta,
         if (tid == 0) {
             sc->n_accept = 0ull;
             sc->n_test = 0ull;
+            sc->n_steps = 0ull;
+            sc->n_nodes = 0ull;
             // Eq. beta_scaling carried as s_d <- s_d * gamma_d / 2^32
             sc->s[0] = sc->s[0] * ldexp((double)gx, -32);
             sc->s[1] = sc->s[1] * ldexp((double)gy, -32);
@@ -62,6 +64,8 @@ __global__ void k_snap_hist(int n, int L, int rescale, float theta,
     if (!rescale && tid == 0) {
         sc->n_accept = 0ull;
         sc->n_test = 0ull;
+        sc->n_steps = 0ull;
+        sc->n_nodes = 0ull;
     }
     // Points arrive in the Morton order of a recent state, so lanes with equal
     // leaf keys mostly form runs: each run adds its count and sums with one
