@@ -1,6 +1,10 @@
 // Affinity matrix P of t-SNE (Sec. 3.2) on the sparse kNN pattern of Sec. 3.3.
 //
-//   k_knn_tile     brute-force k nearest neighbours: a 64 x 128 tile of
+//   k_knn_tc       brute-force k nearest neighbours on the tensor cores: FP16
+//                  dot-product tiles (tcgen05, FP32 accumulator in TMEM) filter
+//                  candidates with a rigorous error bound; survivors are
+//                  re-ranked with exact FP32 distances (the default path)
+//   k_knn_tile     the same search on FP32 CUDA cores (check path): a 64 x 128 tile of
 //                  approximate squared distances |q|^2 + |c|^2 - 2 q.c (FP32
 //                  dot products) filters candidates against each row's current
 //                  k-th distance plus an error slack; survivors get their exact
