@@ -124,16 +124,22 @@ def measured_peaks():
 
 # Algorithmic bytes (HBM) per launch of each kernel group, and FLOPs of the
 # traversal per tested / accepted (point, cell) pair.
+RELABEL_EVERY = 25  # the library refreshes the attraction's relabelled P this often
+
+
 def group_bytes(n, nnz, L):
     leaves = 4 ** L
     cells = (4 ** (L + 1) - 1) // 3
     return {
+        # per iteration on average: P read and written once per relabel, plus
+        # the maps, row lengths, scan and positions
+        "k_relabel": (nnz * 16 + n * (4 + 8 + 4 + 4 + 4 + 8 + 8 + 8 + 8)) / RELABEL_EVERY,
         "k_update": n * (8 + 8 + 8 + 8 + 8 + 8 + 8 + 16),      # z,Frep,Fattr,u,gains r; u,gains w; zhat w
-        "k_snap_hist": leaves * 20 + n * (4 + 16 + 8 + 4),     # memset; perm,zhat r; z,rank w
+        "k_snap_hist": leaves * 20 + n * (4 + 16 + 8 + 4 + 4 + 8),  # memset; perm,zhat,ainv r; z,rank,zp w
         "k_pyr_pass": leaves * (20 + 4) + cells * 16,          # leaf sums r, leaf_start w, records w
         "k_perm_scatter": n * (8 + 4 + 4 + 4),
         "k_bh_traverse": n * (4 + 8 + 8 + 4) + cells * 16,
-        "k_attract": nnz * 8 + (n + 1) * 8 + n * (8 + 8),
+        "k_attract": nnz * 8 + (n + 1) * 8 + n * (8 + 4 + 8),
         "k_zsum": n * 4,
     }
 
@@ -453,8 +459,10 @@ def run_gpu(args):
             "kl_after_timed": kl_after,
             "clocks": ck, "e2e": e2e, "cpu_baseline": cpu, "warmstart": warm,
             # per iteration: update, snap_hist, ceil(L/5) pyramid passes, scan,
-            # perm_scatter, traverse, attract, zsum
-            "gpu_launches": args.steps * (7 + (W["log2_r"] + 4) // 5),
+            # perm_scatter, traverse, attract, zsum; per relabel (before every
+            # RELABEL_EVERY-th iteration): maps, three scan kernels, rows
+            "gpu_launches": args.steps * (7 + (W["log2_r"] + 4) // 5)
+                            + 5 * ((args.steps - 1) // RELABEL_EVERY),
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -716,8 +716,7 @@ __global__ void k_scan_add(int64_t m, int64_t *out, const int64_t *__restrict__ 
 }
 
 // out[0..m] = exclusive scan of in[0..m) with out[m] = total (int64).
-static cudaError_t scan_u32_to_i64(const uint32_t *in, int64_t m, int64_t *out,
-                                   cudaStream_t st) {
+cudaError_t scan_u32_to_i64(const uint32_t *in, int64_t m, int64_t *out, cudaStream_t st) {
     const int64_t nb = (m + kScanB - 1) / kScanB;
     int64_t *bsum = nullptr;
     cudaError_t e;

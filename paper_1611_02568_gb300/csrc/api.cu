@@ -73,6 +73,8 @@ void free_state(pxsne_ctx *c) {
     dfree(c->leaf_cnt); dfree(c->leaf_sx); dfree(c->leaf_sy); dfree(c->rec); dfree(c->recn);
     for (int k = 0; k < 2; k++) { dfree(c->lvl_cnt[k]); dfree(c->lvl_sx[k]); dfree(c->lvl_sy[k]); }
     dfree(c->leaf_start); dfree(c->blk_off); dfree(c->zpart); dfree(c->klpart);
+    dfree(c->rp2); dfree(c->col2); dfree(c->val2);
+    dfree(c->aperm); dfree(c->ainv); dfree(c->rl2); dfree(c->zp);
     c->state_ready = false;
 }
 
@@ -116,6 +118,13 @@ int ensure_state(pxsne_ctx *c) {
     CK(c, dalloc(c, &c->Fattr, n));
     CK(c, dalloc(c, &c->perm, n));
     CK(c, dalloc(c, &c->rank, n));
+    CK(c, dalloc(c, &c->rp2, n + 1));
+    CK(c, dalloc(c, &c->col2, (size_t)(c->nnz_pad > 0 ? c->nnz_pad : 4)));
+    CK(c, dalloc(c, &c->val2, (size_t)(c->nnz_pad > 0 ? c->nnz_pad : 4)));
+    CK(c, dalloc(c, &c->aperm, n));
+    CK(c, dalloc(c, &c->ainv, n));
+    CK(c, dalloc(c, &c->rl2, n));
+    CK(c, dalloc(c, &c->zp, n));
     CK(c, dalloc(c, &c->leaf_cnt, leaves));
     CK(c, dalloc(c, &c->leaf_sx, leaves));
     CK(c, dalloc(c, &c->leaf_sy, leaves));
@@ -167,9 +176,21 @@ int prime(pxsne_ctx *c) {
     k_iota<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->perm);
     CK(c, cudaGetLastError());
     CK(c, launch_tree(c, false));
+    // a state set from outside: P relabelled for its Morton order before the
+    // first attraction
+    CK(c, launch_relabel(c, c->stream));
+    c->since_relabel = 0;
     CK(c, launch_forces(c));
     c->state_ready = true;
     return PXSNE_OK;
+}
+
+// The attraction's relabelled copy of P follows the Morton order of the last
+// tree; it is refreshed every kRelabelEvery iterations (before the update).
+cudaError_t relabel_if_due(pxsne_ctx *c) {
+    if (c->since_relabel < kRelabelEvery) return cudaSuccess;
+    c->since_relabel = 0;
+    return launch_relabel(c, c->stream);
 }
 
 // One iteration.  With timing marks every kernel runs in order on the main
@@ -194,7 +215,7 @@ int one_iteration(pxsne_ctx *c, cudaEvent_t *marks = nullptr) {
     return PXSNE_OK;
 }
 
-const char *kGroupNames[KG_COUNT] = {"k_update", "k_snap_hist", "k_pyr_pass",
+const char *kGroupNames[KG_COUNT] = {"k_relabel", "k_update", "k_snap_hist", "k_pyr_pass",
                                      "k_perm_scatter", "k_bh_traverse", "k_attract",
                                      "k_zsum"};
 
@@ -477,12 +498,14 @@ int pxsne_step(pxsne_ctx *c, int32_t iters) {
         cudaGetLastError();
     }
     for (int32_t k = 0; k < iters; k++) {
+        CK(c, relabel_if_due(c));
         if (c->graph) {
             CK(c, cudaGraphLaunch(c->graph, c->stream));
         } else {
             rc = one_iteration(c);
             if (rc) return rc;
         }
+        c->since_relabel++;
     }
     return PXSNE_OK;
 }
@@ -498,8 +521,12 @@ int pxsne_step_profiled(pxsne_ctx *c, int32_t iters, double *group_ms, int32_t n
     cudaEvent_t *t0 = &ev[ev.size() - 2], *t1 = &ev[ev.size() - 1];
     CK(c, cudaEventRecord(*t0, c->stream));
     for (int32_t k = 0; k < iters; k++) {
-        rc = one_iteration(c, &ev[(size_t)k * (KG_COUNT + 1)]);
+        cudaEvent_t *m = &ev[(size_t)k * (KG_COUNT + 1)];
+        CK(c, cudaEventRecord(m[KG_RELABEL], c->stream));
+        CK(c, relabel_if_due(c));
+        rc = one_iteration(c, m);
         if (rc) break;
+        c->since_relabel++;
     }
     if (!rc) {
         CK(c, cudaEventRecord(*t1, c->stream));
@@ -780,6 +807,7 @@ int64_t pxsne_device_bytes(const pxsne_ctx *c) {
         b += n * (8 + 16 + 8 + 8 + 8 + 4 + 8 + 4 + 4);
         b += leaves * (4 + 8 + 8 + 4) + rec_offset(L + 1) * 20 + lvl * 4 + 2 * (lvl + 4) * 20;
         b += (int64_t)c->zblocks * 8 + (int64_t)c->klblocks * 16;
+        b += (n + 1) * 8 + c->nnz_pad * 8 + n * (4 + 4 + 4 + 8);  // relabelled P, maps, zp
     }
     return b;
 }

@@ -147,6 +147,17 @@ struct pxsne_ctx {
     uint32_t *perm = nullptr;  // traversal order (Morton order of a recent state)
     uint32_t *rank = nullptr;  // rank of each point inside its pixel
 
+    // P relabelled for the attraction: rows and columns renumbered in the
+    // Morton order of a recent state (aperm: new label -> point, ainv: point
+    // -> new label), refreshed every kRelabelEvery iterations; zp holds the
+    // positions under the new labels (written by the snap kernel)
+    int64_t *rp2 = nullptr;
+    int32_t *col2 = nullptr;
+    float *val2 = nullptr;
+    uint32_t *aperm = nullptr, *ainv = nullptr, *rl2 = nullptr;
+    uint2 *zp = nullptr;
+    int since_relabel = 0;
+
     // tree
     int L = 0;
     uint32_t *leaf_cnt = nullptr;
@@ -174,7 +185,8 @@ namespace pxsne {
 cudaError_t launch_init_map(pxsne_ctx *c, const float *Y0dev, uint32_t *mm_scratch);
 // Kernel groups of one iteration, in launch order (timing marks).
 enum KernelGroup {
-    KG_UPDATE = 0,   // k_update
+    KG_RELABEL = 0,  // k_relabel_maps + scan + k_relabel_rows (every kRelabelEvery iterations)
+    KG_UPDATE,       // k_update
     KG_SNAP,         // leaf memsets + k_snap_hist
     KG_PYRAMID,      // k_pyr_pass x passes + k_scan1
     KG_PERM,         // k_perm_scatter
@@ -193,6 +205,12 @@ cudaError_t launch_forces(pxsne_ctx *c, cudaEvent_t *marks = nullptr);
 cudaError_t launch_snap(pxsne_ctx *c, bool rescale, cudaEvent_t *marks = nullptr);
 cudaError_t launch_pyramid(pxsne_ctx *c, bool rescale, cudaEvent_t *marks = nullptr);
 cudaError_t launch_attract(pxsne_ctx *c, cudaStream_t st);
+// Renumber P's rows and columns in the Morton order of the last tree (perm)
+// into rp2/col2/val2 and refresh aperm, ainv and zp.
+constexpr int kRelabelEvery = 25;
+cudaError_t launch_relabel(pxsne_ctx *c, cudaStream_t st);
+// out[0..m] = exclusive scan of in[0..m) with out[m] = the total
+cudaError_t scan_u32_to_i64(const uint32_t *in, int64_t m, int64_t *out, cudaStream_t st);
 cudaError_t launch_traverse_zsum(pxsne_ctx *c);
 cudaError_t launch_update(pxsne_ctx *c, cudaEvent_t *marks = nullptr);
 cudaError_t launch_kl(pxsne_ctx *c, double *out_dev);

@@ -195,14 +195,19 @@ __global__ void __launch_bounds__(kTravWarps * 32, 5)
 
 // Eq. grad, first term: Fattr_i = sum_j p_ij w_ij (y_i - y_j), one warp per
 // row (row lengths vary with the in-degree of the kNN graph; a warp per row
-// keeps long rows from stalling short ones).  Each lane keeps two entries in
-// flight; P is streamed with evict-first loads so that the positions z_j stay
-// in L2.  z_i - z_j is formed exactly in float from the 16-bit halves of the
+// keeps long rows from stalling short ones).  It runs over the relabelled copy
+// of P (rows and columns in the Morton order of a recent state), so a row's
+// gathered positions zp[j] lie close together in memory, and writes each row's
+// force back under the point's own index.  Each lane keeps two entries in
+// flight; P is streamed with evict-first loads so that the positions stay in
+// L2.  z_i - z_j is formed exactly in float from the 16-bit halves of the
 // fixed-point coordinates (both differences are exact; one final rounding).
+// Entry order within a row is that of P, so the sums equal those over P.
 __global__ void __launch_bounds__(256)
     k_attract(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
               const float *__restrict__ val, const uint2 *__restrict__ z,
-              const DevScalars *__restrict__ sc, float2 *__restrict__ Fattr) {
+              const uint32_t *__restrict__ aperm, const DevScalars *__restrict__ sc,
+              float2 *__restrict__ Fattr) {
     constexpr int U = 2;
     const int lane = threadIdx.x & 31;
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -256,7 +261,44 @@ __global__ void __launch_bounds__(256)
         fx += __shfl_xor_sync(0xffffffffu, fx, o);
         fy += __shfl_xor_sync(0xffffffffu, fy, o);
     }
-    if (lane == 0) Fattr[row] = make_float2(fx, fy);
+    if (lane == 0) Fattr[aperm[row]] = make_float2(fx, fy);
+}
+
+// Relabelling: new label r is the point perm[r] (Morton order of the last
+// tree).  Maps, padded row lengths under the new labels, and the positions.
+__global__ void k_relabel_maps(int n, const uint32_t *__restrict__ perm,
+                               const int64_t *__restrict__ rp, const uint2 *__restrict__ z,
+                               uint32_t *__restrict__ aperm, uint32_t *__restrict__ ainv,
+                               uint32_t *__restrict__ len2, uint2 *__restrict__ zp) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const uint32_t i = perm[r];
+    aperm[r] = i;
+    ainv[i] = (uint32_t)r;
+    len2[r] = (uint32_t)(rp[i + 1] - rp[i]);
+    zp[r] = z[i];
+}
+
+// Row r of the relabelled P is row aperm[r] of P with every column j replaced
+// by ainv[j], entries in the same order; one warp per row, 16-byte quads (rows
+// are padded to multiples of four on both sides).
+__global__ void __launch_bounds__(256)
+    k_relabel_rows(int n, const uint32_t *__restrict__ aperm, const uint32_t *__restrict__ ainv,
+                   const int64_t *__restrict__ rp, const int4 *__restrict__ col4,
+                   const float4 *__restrict__ val4, const int64_t *__restrict__ rp2,
+                   int4 *__restrict__ col2, float4 *__restrict__ val2) {
+    const int lane = threadIdx.x & 31;
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (r >= n) return;
+    const uint32_t i = aperm[r];
+    const int64_t q0 = rp[i] >> 2, q1 = rp[i + 1] >> 2, d0 = rp2[r] >> 2;
+    for (int64_t q = q0 + lane; q < q1; q += 32) {
+        const int4 c = __ldcs(col4 + q);
+        const float4 v = __ldcs(val4 + q);
+        col2[d0 + (q - q0)] = make_int4((int)ainv[c.x], (int)ainv[c.y], (int)ainv[c.z],
+                                        (int)ainv[c.w]);
+        val2[d0 + (q - q0)] = v;
+    }
 }
 
 // Deterministic FP64 block sum (fixed tree order) of blockDim.x values.
@@ -330,12 +372,29 @@ static cudaError_t traverse(pxsne_ctx *c, cudaStream_t st, bool count) {
 cudaError_t launch_attract(pxsne_ctx *c, cudaStream_t st) {
     const int n = (int)c->n;
     const int att_blocks = (int)((int64_t(n) * 32 + 255) / 256);
-    k_attract<<<att_blocks, 256, 0, st>>>(n, c->rp, c->col, c->val, c->z, c->sc, c->Fattr);
+    k_attract<<<att_blocks, 256, 0, st>>>(n, c->rp2, c->col2, c->val2, c->zp, c->aperm, c->sc,
+                                          c->Fattr);
     return cudaGetLastError();
 }
 
 static cudaError_t zsum(pxsne_ctx *c, cudaStream_t st) {
     k_zsum<<<c->zblocks, 512, 0, st>>>((int)c->n, c->Zi, c->zpart, c->sc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relabel(pxsne_ctx *c, cudaStream_t st) {
+    const int n = (int)c->n;
+    k_relabel_maps<<<(n + 255) / 256, 256, 0, st>>>(n, c->perm, c->rp, c->z, c->aperm, c->ainv,
+                                                     c->rl2, c->zp);
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    if ((e = scan_u32_to_i64(c->rl2, n, c->rp2, st))) return e;
+    const unsigned blocks = (unsigned)(((int64_t)n * 32 + 255) / 256);
+    k_relabel_rows<<<blocks, 256, 0, st>>>(n, c->aperm, c->ainv, c->rp,
+                                           reinterpret_cast<const int4 *>(c->col),
+                                           reinterpret_cast<const float4 *>(c->val), c->rp2,
+                                           reinterpret_cast<int4 *>(c->col2),
+                                           reinterpret_cast<float4 *>(c->val2));
     return cudaGetLastError();
 }
 

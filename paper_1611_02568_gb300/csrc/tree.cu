@@ -32,7 +32,8 @@ __global__ void k_snap_hist(int n, int L, int rescale, float theta,
                             const longlong2 *__restrict__ zhat, uint2 *__restrict__ z,
                             const uint32_t *__restrict__ perm, uint32_t *__restrict__ rank,
                             uint32_t *__restrict__ cnt, u64 *__restrict__ sx,
-                            u64 *__restrict__ sy, DevScalars *sc) {
+                            u64 *__restrict__ sy, DevScalars *sc,
+                            const uint32_t *__restrict__ ainv, uint2 *__restrict__ zp) {
     const int F = 32 - L;
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int par = sc->t & 1;
@@ -81,6 +82,7 @@ __global__ void k_snap_hist(int n, int L, int rescale, float theta,
             zx = rescale_exact((u64)(h.x - mnx), gx, qx);
             zy = rescale_exact((u64)(h.y - mny), gy, qy);
             z[i] = make_uint2(zx, zy);
+            zp[ainv[i]] = make_uint2(zx, zy);  // the attraction's copy
         } else {
             const uint2 v = z[i];
             zx = v.x;
@@ -301,7 +303,8 @@ cudaError_t launch_snap(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
     const int n = (int)c->n;
     k_snap_hist<<<(n + 255) / 256, 256, 0, st>>>(n, L, rescale ? 1 : 0, c->p.theta, c->zhat,
                                                  c->z, c->perm, c->rank, c->leaf_cnt,
-                                                 c->leaf_sx, c->leaf_sy, c->sc);
+                                                 c->leaf_sx, c->leaf_sy, c->sc, c->ainv,
+                                                 c->zp);
     return cudaGetLastError();
 }
 
