@@ -194,9 +194,11 @@ cudaError_t relabel_if_due(pxsne_ctx *c) {
 }
 
 // One iteration.  With timing marks every kernel runs in order on the main
-// stream.  Without, the attraction (which needs only the rescaled z and P)
-// runs on the high-priority side stream concurrently with the pyramid and the
-// traversal, and joins before the next update.
+// stream.  Without, the attraction (which needs only the rescaled positions
+// and P) runs on the side stream concurrently with the traversal: the
+// traversal is enqueued first so that its blocks are dispatched first, and
+// the attraction's blocks fill the SMs as the traversal's drain.  The two
+// join before the next update.
 int one_iteration(pxsne_ctx *c, cudaEvent_t *marks = nullptr) {
     CK(c, launch_update(c, marks));
     if (marks || !c->side) {
@@ -204,13 +206,12 @@ int one_iteration(pxsne_ctx *c, cudaEvent_t *marks = nullptr) {
         CK(c, launch_forces(c, marks));
         return PXSNE_OK;
     }
-    CK(c, launch_snap(c, true));
+    CK(c, launch_tree(c, true));
     CK(c, cudaEventRecord(c->ev_fork, c->stream));
+    CK(c, launch_traverse_zsum(c));
     CK(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     CK(c, launch_attract(c, c->side));
     CK(c, cudaEventRecord(c->ev_join, c->side));
-    CK(c, launch_pyramid(c, true));
-    CK(c, launch_traverse_zsum(c));
     CK(c, cudaStreamWaitEvent(c->stream, c->ev_join, 0));
     return PXSNE_OK;
 }
@@ -282,9 +283,11 @@ int pxsne_create(pxsne_ctx **out, const pxsne_params *p, void *stream) {
         }
     }
     if (e == cudaSuccess) {
+        // the attraction's stream at the least priority: the traversal's
+        // blocks, enqueued before it, are dispatched first
         int lo = 0, hi = 0;
         e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
-        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, lo);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     }

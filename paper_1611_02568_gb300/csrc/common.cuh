@@ -110,7 +110,7 @@ struct pxsne_ctx {
     pxsne_params p;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    cudaStream_t side = nullptr;          // high-priority stream for the attraction
+    cudaStream_t side = nullptr;          // stream of the attraction (overlaps the traversal)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     std::string err;
