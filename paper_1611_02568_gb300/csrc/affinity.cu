@@ -233,10 +233,25 @@ __global__ void __launch_bounds__(kKnnThreads)
 // to the k nearest if its approximate d2 is below the row's current k-th exact
 // distance plus that bound; only those get their exact FP32 distance
 // (sum of squared differences) and enter the row's sorted list.
+//
+// One CTA owns 128 query rows and sweeps every candidate tile (all CTAs in the
+// same order, so that concurrent CTAs share each tile through L2).  Warp roles: warp 4 streams candidate tiles (pre-swizzled FP16
+// images, one bulk copy each) into a ring of shared-memory stages; warp 5
+// issues the MMAs into four TMEM accumulators; warps 0-3 (one query row per
+// thread, TMEM lanes 32w..32w+31) filter.  The filter's fast path needs two
+// instructions per (row, candidate): with h_j = (1-eps)|c_j|^2 and the tile's
+// largest |c|, a 32-column chunk is skipped when
+//   min_j (h_j - 2 q.c_j) > tau - (1-eps)|q|^2 + kappa |q| max|c|.
+// Otherwise the exact per-column bound picks the survivors.  A warp queues the
+// survivors of its 32 rows over a whole tile, then computes their exact
+// distances 32 at a time and lets each row's owner insert its own.
 constexpr int kTcRows = 128;     // query rows per CTA (MMA M)
 constexpr int kTcCols = 128;     // candidates per tile (MMA N)
-constexpr int kTcThreads = 256;  // warps 0-3: one query row per thread; 4-7 load tiles
-constexpr int kTcPolls = 1 << 24;
+constexpr int kTcStages = 2;     // candidate-tile stages in shared memory
+constexpr int kTcQueue = 1024;   // survivor queue per filter warp (entries)
+constexpr int kTcAcc = 4;        // TMEM accumulators (4 x 128 columns)
+constexpr int kTcThreads = 192;  // warps 0-3 filter, 4 loads, 5 issues MMAs
+constexpr int kTcPolls = 1 << 22;
 
 __global__ void k_absmax(int64_t m, const float *__restrict__ X, unsigned *out) {
     unsigned v = 0u;
@@ -248,13 +263,48 @@ __global__ void k_absmax(int64_t m, const float *__restrict__ X, unsigned *out) 
     if ((threadIdx.x & 31) == 0) atomicMax(out, v);
 }
 
-__global__ void k_to_half(int64_t n, int D, int Dp, float scale, const float *__restrict__ X,
-                          __half *__restrict__ Xh) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n * Dp) return;
-    const int64_t row = i / Dp;
-    const int d = (int)(i % Dp);
-    Xh[i] = __float2half_rn(d < D ? X[row * D + d] * scale : 0.0f);
+// FP16 copy of X * scale as ready-made shared-memory images: tile t (rows
+// 128t .. 128t + 127, zero rows past n and zero columns past D) in the 128-byte
+// swizzled K-major layout of the MMA operands, so that one bulk copy loads it.
+__global__ void k_to_half_img(int64_t n, int D, int Dp, int64_t T, float scale,
+                              const float *__restrict__ X, uint8_t *__restrict__ img) {
+    const int chunks = Dp >> 3;  // 16-byte chunks per row
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= T * kTcRows * chunks) return;
+    const int64_t row = q / chunks;
+    const int c8 = (int)(q % chunks);
+    const int64_t t = row / kTcRows;
+    const int r = (int)(row % kTcRows);
+    __align__(16) __half h[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+        const int d = 8 * c8 + u;
+        h[u] = __float2half_rn(row < n && d < D ? X[row * D + d] * scale : 0.0f);
+    }
+    *reinterpret_cast<uint4 *>(img + t * (int64_t)kTcRows * Dp * 2 +
+                               tc::sw128_offset(r, 8 * c8, kTcRows)) =
+        *reinterpret_cast<const uint4 *>(h);
+}
+
+// Per candidate: h = (1-eps)|c|^2 (+inf past n) and |c|; per tile: max |c|.
+__global__ void k_tile_norms(int64_t n, int64_t T, float eps_abs, const float *__restrict__ nrm,
+                             float *__restrict__ H, float *__restrict__ G,
+                             float *__restrict__ Gmax) {
+    const int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (t >= T) return;
+    float m = 0.f;
+    for (int j = lane; j < kTcCols; j += 32) {
+        const int64_t c = t * kTcCols + j;
+        const float c2 = c < n ? nrm[c] : 0.f;
+        const float g = sqrtf(c2);
+        H[c] = c < n ? (1.0f - eps_abs) * c2 : INFINITY;
+        G[c] = g;
+        m = fmaxf(m, g);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) Gmax[t] = m;
 }
 
 // Exact FP32 squared distance between rows a and b by one thread, summed in
@@ -287,151 +337,246 @@ __device__ __forceinline__ float thread_exact_d2(const float *__restrict__ X, in
     return s;
 }
 
-// Copy rows [r0, r0 + 128) of Xh (Dp halves each, zero rows past n) into the
-// 128-byte swizzled K-major layout at `dst`; `nt` threads starting at `t0`.
-__device__ __forceinline__ void load_tile_sw128(uint8_t *dst, const __half *__restrict__ Xh,
-                                                int64_t n, int Dp, int64_t r0, int t0, int nt) {
-    const int chunks = Dp >> 3;  // 16-byte chunks per row
-    for (int q = t0; q < kTcRows * chunks; q += nt) {
-        const int r = q / chunks, c8 = q % chunks;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (r0 + r < n) v = *reinterpret_cast<const uint4 *>(Xh + (r0 + r) * Dp + 8 * c8);
-        *reinterpret_cast<uint4 *>(dst + tc::sw128_offset(r, 8 * c8, kTcRows)) = v;
-    }
-}
+struct KnnTcArgs {
+    int64_t n, T;
+    int D, Dp, k;
+    float inv_s2, kappa, eps_abs;
+    const float *X;       // FP32 rows (exact distances)
+    const uint8_t *img;   // FP16 tile images
+    const float *nrm;     // |x|^2
+    const float *H, *G, *Gmax;
+    int32_t *out_idx;
+    float *out_d2;
+    unsigned *err;
+    u64 *stats;
+};
 
-__global__ void __launch_bounds__(kTcThreads, 1)
-    k_knn_tc(int64_t n, int D, int Dp, int k, float inv_s2, float kappa, float eps_abs,
-             const float *__restrict__ X, const __half *__restrict__ Xh,
-             const float *__restrict__ nrm, int32_t *__restrict__ out_idx,
-             float *__restrict__ out_d2, unsigned *err, u64 *stats) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t mbar[2];
+    __shared__ uint64_t bar_a, bar_sf[kTcStages], bar_se[kTcStages], bar_tf[kTcAcc],
+        bar_te[kTcAcc], bar_hf[kTcAcc];
     __shared__ uint32_t tslot;
-    __shared__ int s_abort;
+    __shared__ volatile int s_abort;
     // 1024-byte aligned base for the swizzled operand tiles
     uint8_t *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
-    const uint32_t tile_bytes = (uint32_t)kTcRows * Dp * 2;
+    const int64_t n = a.n, T = a.T;
+    const int k = a.k;
+    const uint32_t tile_bytes = (uint32_t)kTcRows * a.Dp * 2;
     uint8_t *sA = smem;
-    uint8_t *sB0 = smem + tile_bytes;
-    float *ld = reinterpret_cast<float *>(smem + 3 * tile_bytes);
-    int32_t *lj = reinterpret_cast<int32_t *>(ld + kTcRows * k);
-    float *cn2 = reinterpret_cast<float *>(lj + kTcRows * k);  // [2][128] (1-eps)|c|^2
-    float *cn1 = cn2 + 2 * kTcCols;                           // [2][128] |c|
+    uint8_t *sB = smem + tile_bytes;
+    float *hbuf = reinterpret_cast<float *>(sB + (size_t)kTcStages * tile_bytes);  // [4][128]
+    // row lists with an odd stride (no bank conflicts between the rows)
+    const int ks = k | 1;
+    float *ld = hbuf + kTcAcc * kTcCols;
+    int32_t *lj = reinterpret_cast<int32_t *>(ld + kTcRows * ks);
+    // per filter warp: survivors as (row lane << 8 | column) and their exact d2
+    float *qd_all = reinterpret_cast<float *>(lj + kTcRows * ks);
+    uint16_t *qe_all = reinterpret_cast<uint16_t *>(qd_all + 4 * kTcQueue);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t q0 = (int64_t)blockIdx.x * kTcRows;
-    const int64_t T = (n + kTcCols - 1) / kTcCols;
-    // per epilogue warp: a queue of up to 32 x 32 survivors (row << 8 | column)
-    // and their exact distances
-    uint16_t *wq = reinterpret_cast<uint16_t *>(cn1 + 2 * kTcCols) + (warp & 3) * 1024;
-    float *wd = reinterpret_cast<float *>(reinterpret_cast<uint16_t *>(cn1 + 2 * kTcCols) + 4 * 1024) +
-                (warp & 3) * 1024;
-    const bool vec4 = ((D & 3) == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    const int64_t qt = blockIdx.x;  // query tile
+    const int64_t q0 = qt * kTcRows;
 
-    load_tile_sw128(sA, Xh, n, Dp, q0, tid, kTcThreads);
-    load_tile_sw128(sB0, Xh, n, Dp, 0, tid, kTcThreads);
-    if (tid < kTcCols) {
-        const float c2 = tid < n ? nrm[tid] : 0.f;
-        cn2[tid] = tid < n ? (1.0f - eps_abs) * c2 : INFINITY;
-        cn1[tid] = sqrtf(c2);
-    }
-    for (int e = tid; e < kTcRows * k; e += kTcThreads) {
+    for (int e = tid; e < kTcRows * ks; e += kTcThreads) {
         ld[e] = INFINITY;
         lj[e] = 0x7fffffff;
     }
-    if (warp == 0) tc::tmem_alloc(&tslot, 2 * kTcCols);
+    if (warp == 5) tc::tmem_alloc(&tslot, kTcAcc * kTcCols);
     if (tid == 0) {
-        tc::mbar_init(&mbar[0], 1);
-        tc::mbar_init(&mbar[1], 1);
+        tc::mbar_init(&bar_a, 1);
+        for (int s = 0; s < kTcStages; s++) {
+            tc::mbar_init(&bar_sf[s], 1);
+            tc::mbar_init(&bar_se[s], 1);
+        }
+        for (int b = 0; b < kTcAcc; b++) {
+            tc::mbar_init(&bar_tf[b], 1);
+            tc::mbar_init(&bar_te[b], 4);
+            tc::mbar_init(&bar_hf[b], 1);
+        }
         s_abort = 0;
     }
-    tc::fence_proxy_async();
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tbase = tslot;
-    const uint32_t idesc = tc::idesc_f16(kTcRows, kTcCols, 0);
-    auto issue = [&](int buf) {
-        const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB0 + buf * tile_bytes);
-        for (int kk = 0; kk < Dp / 16; kk++) {
-            const uint32_t off = (uint32_t)(kk >> 2) * (kTcRows * 128) + (uint32_t)(kk & 3) * 32;
-            tc::mma_f16(tbase + (uint32_t)(buf * kTcCols), tc::sdesc_sw128(a0 + off),
-                        tc::sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
-        }
-        tc::commit(&mbar[buf]);
-    };
-    if (tid == 0) issue(0);
 
-    // epilogue state: thread tid < 128 owns query row q0 + tid
-    const int64_t qi = q0 + tid;
-    const bool qvalid = tid < kTcRows && qi < n;
-    const float qn2 = qvalid ? nrm[qi] : 0.f, qn1 = sqrtf(qn2);
-    float *myd = ld + (size_t)(tid < kTcRows ? tid : 0) * k;
-    int32_t *myj = lj + (size_t)(tid < kTcRows ? tid : 0) * k;
-    float tau = INFINITY;
-    int32_t jlast = 0x7fffffff;
-    uint32_t n_exact = 0u, n_ins = 0u;
-    const float Bq = kappa * qn1;
-    const float onem = 1.0f - eps_abs;
-    // tau - (1 - eps)|q|^2; finite while the list fills so that padding
-    // candidates (+inf) never pass
-    float tauA = 3.402823466e38f;
-
-    for (int64_t t = 0; t < T; t++) {
-        const int buf = (int)(t & 1);
-        const int64_t c0 = t * kTcCols;
-        if (warp >= 4) {
-            // producers: next candidate tile into the other buffer
-            if (t + 1 < T) {
-                load_tile_sw128(sB0 + (buf ^ 1) * tile_bytes, Xh, n, Dp, c0 + kTcCols, tid - 128,
-                                kTcThreads - 128);
-                const int j = tid - 128;
-                const int64_t cj = c0 + kTcCols + j;
-                const float c2 = cj < n ? nrm[cj] : 0.f;
-                cn2[(buf ^ 1) * kTcCols + j] = cj < n ? (1.0f - eps_abs) * c2 : INFINITY;
-                cn1[(buf ^ 1) * kTcCols + j] = sqrtf(c2);
+    if (warp == 4) {
+        // ---- producer: candidate tiles and their h values
+        if (lane == 0) {
+            tc::mbar_expect_tx(&bar_a, tile_bytes);
+            tc::bulk_g2s(sA, a.img + qt * tile_bytes, tile_bytes, &bar_a);
+            int64_t i = 0;
+            for (; i < T && !s_abort; i++) {
+                const int64_t t = i;
+                const int s = (int)(i % kTcStages), b = (int)(i % kTcAcc);
+                if (i >= kTcStages &&
+                    !tc::mbar_wait(&bar_se[s], (uint32_t)((i / kTcStages - 1) & 1), kTcPolls)) {
+                    s_abort = 1;
+                    atomicOr(a.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
+                    break;
+                }
+                tc::mbar_expect_tx(&bar_sf[s], tile_bytes);
+                tc::bulk_g2s(sB + (size_t)s * tile_bytes, a.img + t * tile_bytes, tile_bytes,
+                             &bar_sf[s]);
+                if (i >= kTcAcc &&
+                    !tc::mbar_wait(&bar_te[b], (uint32_t)((i / kTcAcc - 1) & 1), kTcPolls)) {
+                    s_abort = 1;
+                    atomicOr(a.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
+                    i++;  // the stage copy above is in flight
+                    break;
+                }
+                tc::mbar_expect_tx(&bar_hf[b], kTcCols * 4);
+                tc::bulk_g2s(hbuf + b * kTcCols, a.H + t * kTcCols, kTcCols * 4, &bar_hf[b]);
             }
-            tc::fence_proxy_async();
-        } else {
-            // warp-uniform: every lane must take the same path into the
-            // aligned TMEM loads and the warp-synchronous queue below
-            const bool got = __all_sync(
-                0xffffffffu, tc::mbar_wait(&mbar[buf], (uint32_t)((t >> 1) & 1), kTcPolls));
-            if (!got) {
+            // copies still in flight complete before the CTA exits
+            tc::mbar_wait(&bar_a, 0u, kTcPolls);
+            for (int64_t j = (i > kTcStages ? i - kTcStages : 0); j < i; j++)
+                tc::mbar_wait(&bar_sf[j % kTcStages], (uint32_t)((j / kTcStages) & 1), kTcPolls);
+            for (int64_t j = (i > kTcAcc ? i - kTcAcc : 0); j < i; j++)
+                tc::mbar_wait(&bar_hf[j % kTcAcc], (uint32_t)((j / kTcAcc) & 1), kTcPolls);
+        }
+    } else if (warp == 5) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_f16(kTcRows, kTcCols, 0);
+            const uint32_t a0 = tc::smem_u32(sA);
+            bool ok = tc::mbar_wait(&bar_a, 0u, kTcPolls);
+            int64_t i = 0;
+            for (; ok && i < T && !s_abort; i++) {
+                const int s = (int)(i % kTcStages), b = (int)(i % kTcAcc);
+                ok = tc::mbar_wait(&bar_sf[s], (uint32_t)((i / kTcStages) & 1), kTcPolls);
+                if (ok && i >= kTcAcc)
+                    ok = tc::mbar_wait(&bar_te[b], (uint32_t)((i / kTcAcc - 1) & 1), kTcPolls);
+                if (!ok) break;
+                tc::fence_after();
+                const uint32_t b0 = tc::smem_u32(sB + (size_t)s * tile_bytes);
+                for (int kk = 0; kk < a.Dp / 16; kk++) {
+                    const uint32_t off =
+                        (uint32_t)(kk >> 2) * (kTcRows * 128) + (uint32_t)(kk & 3) * 32;
+                    tc::mma_f16(tbase + (uint32_t)(b * kTcCols), tc::sdesc_sw128(a0 + off),
+                                tc::sdesc_sw128(b0 + off), idesc, kk > 0 ? 1u : 0u);
+                }
+                tc::commit(&bar_se[s]);
+                tc::commit(&bar_tf[b]);
+            }
+            if (!ok) {
                 s_abort = 1;
-                atomicOr(err, (unsigned)PXSNE_DEVERR_TIMEOUT);
+                atomicOr(a.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
+            }
+            // MMAs still in flight finish before TMEM is freed
+            for (int64_t j = (i > kTcAcc ? i - kTcAcc : 0); j < i; j++)
+                tc::mbar_wait(&bar_tf[j % kTcAcc], (uint32_t)((j / kTcAcc) & 1), kTcPolls);
+        }
+    } else {
+        // ---- filter: thread tid owns query row q0 + tid
+        const int64_t qi = q0 + tid;
+        const bool qvalid = qi < n;
+        const float qn2 = qvalid ? a.nrm[qi] : 0.f, qn1 = sqrtf(qn2);
+        float *myd = ld + (size_t)tid * ks;
+        int32_t *myj = lj + (size_t)tid * ks;
+        float tau = INFINITY;
+        int32_t jlast = 0x7fffffff;
+        uint32_t n_exact = 0u, n_ins = 0u;
+        const float Bq = a.kappa * qn1;
+        const float onem = 1.0f - a.eps_abs;
+        const float cneg = -2.0f * a.inv_s2;
+        const bool vec4 = ((a.D & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
+        // tau - (1 - eps)|q|^2; finite while the list fills so that padding
+        // candidates (+inf) never pass
+        float tauA = 3.402823466e38f;
+        float *wd = qd_all + warp * kTcQueue;
+        uint16_t *wq = qe_all + warp * kTcQueue;
+        uint32_t qn = 0u;  // entries in the warp's queue (warp-uniform)
+        // this lane's entries: chunk c of the current tile put them at
+        // [rs[c], rs[c] + rc[c]) of the queue
+        uint32_t rs[4] = {0u, 0u, 0u, 0u}, rc[4] = {0u, 0u, 0u, 0u};
+        int64_t c0 = 0;
+        // exact distances of the queued survivors, 32 at a time, then every
+        // lane inserts its own row's survivors (all lanes at once)
+        auto flush = [&]() {
+            for (uint32_t q = lane; q < qn; q += 32) {
+                const uint32_t e = wq[q];
+                wd[q] = thread_exact_d2(a.X, a.D, q0 + 32 * warp + (e >> 8), c0 + (e & 255u), vec4);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                for (uint32_t q = rs[c]; q < rs[c] + rc[c]; q++) {
+                    n_exact++;
+                    const float d = wd[q];
+                    const int32_t cand = (int32_t)(c0 + (wq[q] & 255u));
+                    if (!(d < tau || (d == tau && cand < jlast))) continue;
+                    n_ins++;
+                    int p = k - 1;
+                    while (p > 0 && (myd[p - 1] > d || (myd[p - 1] == d && myj[p - 1] > cand))) {
+                        myd[p] = myd[p - 1];
+                        myj[p] = myj[p - 1];
+                        p--;
+                    }
+                    myd[p] = d;
+                    myj[p] = cand;
+                    tau = myd[k - 1];
+                    jlast = myj[k - 1];
+                    tauA = fminf(tau - onem * qn2, 3.402823466e38f);
+                }
+                rc[c] = 0u;
+            }
+            __syncwarp();
+            qn = 0u;
+        };
+        for (int64_t i = 0; i < T; i++) {
+            const int64_t t = i;
+            const int b = (int)(i % kTcAcc);
+            const uint32_t par = (uint32_t)((i / kTcAcc) & 1);
+            // warp-uniform: every lane takes the same path into the aligned
+            // TMEM loads and the warp-synchronous queue below
+            const bool got = __all_sync(0xffffffffu, tc::mbar_wait(&bar_tf[b], par, kTcPolls) &&
+                                                         tc::mbar_wait(&bar_hf[b], par, kTcPolls));
+            if (!got || s_abort) {
+                s_abort = 1;
+                if (!got && lane == 0) atomicOr(a.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
+                break;
             }
             tc::fence_after();
-            if (got) {
-#pragma unroll 1
-                for (int cb = 0; cb < kTcCols; cb += 32) {
-                    float v[32];
-                    tc::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(buf * kTcCols + cb), v);
-                    // survivors of the filter (tau can only fall during the
-                    // chunk, so this is a superset; each is re-checked exactly).
-                    // approx <= tau + slack rearranged as
-                    //   (1-eps)|c|^2 - kappa|q||c| - 2 q.c <= tau - (1-eps)|q|^2,
-                    // with |c|^2 = +inf for rows past n
-                    uint32_t sm = 0u;
-                    const float *hp = cn2 + buf * kTcCols + cb;
-                    const float *gp = cn1 + buf * kTcCols + cb;
+            c0 = t * kTcCols;
+            const float gmax = __ldg(a.Gmax + t);
+            const float *hb = hbuf + b * kTcCols;
 #pragma unroll
-                    for (int j4 = 0; j4 < 8; j4++) {
-                        const float4 h4 = *reinterpret_cast<const float4 *>(hp + 4 * j4);
-                        const float4 g4 = *reinterpret_cast<const float4 *>(gp + 4 * j4);
-                        const float hh[4] = {h4.x, h4.y, h4.z, h4.w};
-                        const float gg[4] = {g4.x, g4.y, g4.z, g4.w};
+            for (int ci = 0; ci < 4; ci++) {
+                const int cb = 32 * ci;
+                float v[32];
+                tc::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * kTcCols + cb),
+                              v);
+                // fast path: the chunk's smallest h_j - 2 q.c_j against the
+                // loosest bound of the tile
+                float mn[8];
 #pragma unroll
-                        for (int u = 0; u < 4; u++) {
-                            const int j = 4 * j4 + u;
-                            const float lhs = fmaf(-Bq, gg[u], fmaf(-2.0f * inv_s2, v[j], hh[u]));
-                            sm |= (lhs <= tauA) ? (1u << j) : 0u;
-                        }
+                for (int j4 = 0; j4 < 8; j4++) {
+                    const float4 h4 = *reinterpret_cast<const float4 *>(hb + cb + 4 * j4);
+                    const float e0 = fmaf(cneg, v[4 * j4], h4.x);
+                    const float e1 = fmaf(cneg, v[4 * j4 + 1], h4.y);
+                    const float e2 = fmaf(cneg, v[4 * j4 + 2], h4.z);
+                    const float e3 = fmaf(cneg, v[4 * j4 + 3], h4.w);
+                    mn[j4] = fminf(fminf(e0, e1), fminf(e2, e3));
+                }
+                const float m = fminf(fminf(fminf(mn[0], mn[1]), fminf(mn[2], mn[3])),
+                                      fminf(fminf(mn[4], mn[5]), fminf(mn[6], mn[7])));
+                const float thr = fminf(tauA + Bq * gmax, 3.402823466e38f);
+                uint32_t sm = 0u;
+                if (qvalid && m <= thr) {
+                    // exact per-column bound:
+                    //   (1-eps)|c|^2 - kappa|q||c| - 2 q.c <= tau - (1-eps)|q|^2
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        const float lhs =
+                            fmaf(-Bq, __ldg(a.G + c0 + cb + j), fmaf(cneg, v[j], hb[cb + j]));
+                        sm |= (lhs <= tauA) ? (1u << j) : 0u;
                     }
-                    if (!qvalid) sm = 0u;
                     if (qi >= c0 + cb && qi < c0 + cb + 32) sm &= ~(1u << (int)(qi - c0 - cb));
-                    // compact the warp's survivors (row, column) into its queue
+                }
+                if (__any_sync(0xffffffffu, sm != 0u)) {
+                    // append the chunk's survivors to the queue (flush first
+                    // if they might not fit)
                     const uint32_t cnt = (uint32_t)__popc(sm);
                     uint32_t incl = cnt;
 #pragma unroll
@@ -439,72 +584,46 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
                         if (lane >= o) incl += y;
                     }
-                    const uint32_t excl = incl - cnt;
                     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                    if (qn + total > (uint32_t)kTcQueue) flush();
+                    rs[ci] = qn + incl - cnt;
+                    rc[ci] = cnt;
                     uint32_t mm = sm;
-                    for (uint32_t q = excl; mm; q++) {
+                    for (uint32_t q = rs[ci]; mm; q++) {
                         const int j = __ffs(mm) - 1;
                         mm &= mm - 1u;
-                        wq[q] = (uint16_t)((lane << 8) | j);
+                        wq[q] = (uint16_t)((lane << 8) | (cb + j));
                     }
-                    __syncwarp();
-                    // every lane computes queued exact distances
-                    for (uint32_t q = lane; q < total; q += 32) {
-                        const uint32_t e = wq[q];
-                        const int64_t row = q0 + 32 * warp + (e >> 8);
-                        wd[q] = thread_exact_d2(X, D, row, c0 + cb + (e & 255u), vec4);
-                    }
-                    __syncwarp();
-                    // the row's owner inserts its results
-                    for (uint32_t q = excl; q < incl; q++) {
-                        const float dex = wd[q];
-                        const int64_t cand = c0 + cb + (wq[q] & 255u);
-                        if (!(dex < tau || (dex == tau && (int32_t)cand < jlast))) continue;
-                        n_ins++;
-                        int p = k - 1;
-                        while (p > 0 && (myd[p - 1] > dex ||
-                                         (myd[p - 1] == dex && myj[p - 1] > (int32_t)cand))) {
-                            myd[p] = myd[p - 1];
-                            myj[p] = myj[p - 1];
-                            p--;
-                        }
-                        myd[p] = dex;
-                        myj[p] = (int32_t)cand;
-                        tau = myd[k - 1];
-                        jlast = myj[k - 1];
-                        tauA = fminf(tau - onem * qn2, 3.402823466e38f);
-                    }
-                    n_exact += cnt;
+                    qn += total;
                     __syncwarp();
                 }
             }
+            // the accumulator is free once read; the queue is then flushed
             tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&bar_te[b]);
+            if (qn) flush();
         }
-        __syncthreads();
-        tc::fence_after();
-        if (s_abort) break;
-        if (tid == 0 && t + 1 < T) issue(buf ^ 1);
+        atomicAdd(&a.stats[0], (u64)n_exact);
+        atomicAdd(&a.stats[1], (u64)n_ins);
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_dealloc(tbase, 2 * kTcCols);
-    if (tid < kTcRows) {
-        atomicAdd(&stats[0], (u64)n_exact);
-        atomicAdd(&stats[1], (u64)n_ins);
-    }
+    if (warp == 5) tc::tmem_dealloc(tbase, kTcAcc * kTcCols);
     for (int e = tid; e < kTcRows * k; e += kTcThreads) {
-        const int64_t row = q0 + e / k;
+        const int r = e / k, j = e % k;
+        const int64_t row = q0 + r;
         if (row < n) {
-            out_idx[row * k + (e % k)] = lj[e];
-            out_d2[row * k + (e % k)] = ld[e];
+            a.out_idx[row * k + j] = lj[r * ks + j];
+            a.out_d2[row * k + j] = ld[r * ks + j];
         }
     }
 }
 
 static size_t knn_tc_smem(int Dp, int k) {
-    return (size_t)3 * kTcRows * Dp * 2 + (size_t)kTcRows * k * 8 + 4 * kTcCols * 4 +
-           4 * 1024 * (2 + 4) + 1024;
+    return (size_t)(1 + kTcStages) * kTcRows * Dp * 2 + (size_t)kTcAcc * kTcCols * 4 +
+           (size_t)kTcRows * (k | 1) * 8 + (size_t)4 * kTcQueue * (4 + 2) + 1024;
 }
 
 cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, int32_t k,
@@ -525,7 +644,6 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
     if (!want_fp32 && Dp <= 128 && smem_tc <= (size_t)smem_max) {
         c->knn_path = 1;
         unsigned *amax = nullptr;
-        __half *Xh = nullptr;
         unsigned *err = &c->sc->err;
         if ((e = cudaMemsetAsync(&c->sc->knn_exact, 0, 2 * sizeof(u64), st))) return e;
         if ((e = cudaMallocAsync(&amax, sizeof(unsigned), st))) return e;
@@ -546,16 +664,45 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         const float u = 1.0f / 2048.0f;
         const float kappa = 1.25f * 2.0f * (2.0f * u + u * u + (float)Dp * 5.9604645e-8f * 1.01f);
         const float eps_abs = (float)(2 * D + 8) * 5.9604645e-8f;
-        if ((e = cudaMallocAsync(&Xh, (size_t)n * Dp * sizeof(__half), st))) return e;
-        k_to_half<<<(unsigned)((n * Dp + 255) / 256), 256, 0, st>>>(n, D, Dp, scale, Xdev, Xh);
+        const int64_t T = (n + kTcCols - 1) / kTcCols;
+        const size_t img_bytes = (size_t)T * kTcRows * Dp * 2;
+        uint8_t *img = nullptr;
+        float *HG = nullptr;
+        if ((e = cudaMallocAsync(&img, img_bytes, st))) return e;
+        if ((e = cudaMallocAsync(&HG, (size_t)T * (2 * kTcCols + 1) * sizeof(float), st)))
+            return e;
+        float *H = HG, *G = HG + T * kTcCols, *Gmax = HG + 2 * T * kTcCols;
+        const int64_t nchunks = T * kTcRows * (Dp / 8);
+        k_to_half_img<<<(unsigned)((nchunks + 255) / 256), 256, 0, st>>>(n, D, Dp, T, scale, Xdev,
+                                                                          img);
+        k_tile_norms<<<(unsigned)((T + 7) / 8), 256, 0, st>>>(n, T, eps_abs, nrm, H, G, Gmax);
         if ((e = cudaGetLastError())) return e;
         if ((e = cudaFuncSetAttribute(k_knn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem_tc)))
             return e;
-        k_knn_tc<<<(unsigned)((n + kTcRows - 1) / kTcRows), kTcThreads, smem_tc, st>>>(
-            n, D, Dp, k, inv_s2, kappa, eps_abs, Xdev, Xh, nrm, idx, d2, err, &c->sc->knn_exact);
+        KnnTcArgs ka;
+        ka.n = n;
+        ka.T = T;
+        ka.D = D;
+        ka.Dp = Dp;
+        ka.k = k;
+        ka.inv_s2 = inv_s2;
+        ka.kappa = kappa;
+        ka.eps_abs = eps_abs;
+        ka.X = Xdev;
+        ka.img = img;
+        ka.nrm = nrm;
+        ka.H = H;
+        ka.G = G;
+        ka.Gmax = Gmax;
+        ka.out_idx = idx;
+        ka.out_d2 = d2;
+        ka.err = err;
+        ka.stats = &c->sc->knn_exact;
+        k_knn_tc<<<(unsigned)T, kTcThreads, smem_tc, st>>>(ka);
         if ((e = cudaGetLastError())) return e;
-        cudaFreeAsync(Xh, st);
+        cudaFreeAsync(img, st);
+        cudaFreeAsync(HG, st);
         cudaFreeAsync(amax, st);
         return cudaFreeAsync(nrm, st);
     }
