@@ -243,8 +243,9 @@ __global__ void __launch_bounds__(kKnnThreads)
 // largest |c|, a 32-column chunk is skipped when
 //   min_j (h_j - 2 q.c_j) > tau - (1-eps)|q|^2 + kappa |q| max|c|.
 // Otherwise the exact per-column bound picks the survivors.  A warp queues the
-// survivors of its 32 rows over a whole tile, then computes their exact
-// distances 32 at a time and lets each row's owner insert its own.
+// survivors of its 32 rows (a chain per row through the queue) over as many
+// tiles as it takes to gather about 32; then every lane walks its own chain,
+// computing exact distances and inserting, all lanes at once.
 constexpr int kTcRows = 128;     // query rows per CTA (MMA M)
 constexpr int kTcCols = 128;     // candidates per tile (MMA N)
 constexpr int kTcStages = 2;     // candidate-tile stages in shared memory
@@ -369,9 +370,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
     const int ks = k | 1;
     float *ld = hbuf + kTcAcc * kTcCols;
     int32_t *lj = reinterpret_cast<int32_t *>(ld + kTcRows * ks);
-    // per filter warp: survivors as (row lane << 8 | column) and their exact d2
-    float *qd_all = reinterpret_cast<float *>(lj + kTcRows * ks);
-    uint16_t *qe_all = reinterpret_cast<uint16_t *>(qd_all + 4 * kTcQueue);
+    // per filter warp: queued survivors (candidate index) and, per entry, the
+    // previous entry of the same row
+    int32_t *qc_all = lj + kTcRows * ks;
+    uint16_t *qp_all = reinterpret_cast<uint16_t *>(qc_all + 4 * kTcQueue);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t qt = blockIdx.x;  // query tile
@@ -410,7 +412,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                 const int64_t t = i;
                 const int s = (int)(i % kTcStages), b = (int)(i % kTcAcc);
                 if (i >= kTcStages &&
-                    !tc::mbar_wait(&bar_se[s], (uint32_t)((i / kTcStages - 1) & 1), kTcPolls)) {
+                    !tc::mbar_wait_sleep(&bar_se[s], (uint32_t)((i / kTcStages - 1) & 1), kTcPolls, 2000u)) {
                     s_abort = 1;
                     atomicOr(a.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
                     break;
@@ -419,7 +421,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                 tc::bulk_g2s(sB + (size_t)s * tile_bytes, a.img + t * tile_bytes, tile_bytes,
                              &bar_sf[s]);
                 if (i >= kTcAcc &&
-                    !tc::mbar_wait(&bar_te[b], (uint32_t)((i / kTcAcc - 1) & 1), kTcPolls)) {
+                    !tc::mbar_wait_sleep(&bar_te[b], (uint32_t)((i / kTcAcc - 1) & 1), kTcPolls, 2000u)) {
                     s_abort = 1;
                     atomicOr(a.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
                     i++;  // the stage copy above is in flight
@@ -444,9 +446,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             int64_t i = 0;
             for (; ok && i < T && !s_abort; i++) {
                 const int s = (int)(i % kTcStages), b = (int)(i % kTcAcc);
-                ok = tc::mbar_wait(&bar_sf[s], (uint32_t)((i / kTcStages) & 1), kTcPolls);
+                ok = tc::mbar_wait_sleep(&bar_sf[s], (uint32_t)((i / kTcStages) & 1), kTcPolls, 2000u);
                 if (ok && i >= kTcAcc)
-                    ok = tc::mbar_wait(&bar_te[b], (uint32_t)((i / kTcAcc - 1) & 1), kTcPolls);
+                    ok = tc::mbar_wait_sleep(&bar_te[b], (uint32_t)((i / kTcAcc - 1) & 1), kTcPolls, 2000u);
                 if (!ok) break;
                 tc::fence_after();
                 const uint32_t b0 = tc::smem_u32(sB + (size_t)s * tile_bytes);
@@ -484,44 +486,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
         // tau - (1 - eps)|q|^2; finite while the list fills so that padding
         // candidates (+inf) never pass
         float tauA = 3.402823466e38f;
-        float *wd = qd_all + warp * kTcQueue;
-        uint16_t *wq = qe_all + warp * kTcQueue;
-        uint32_t qn = 0u;  // entries in the warp's queue (warp-uniform)
-        // this lane's entries: chunk c of the current tile put them at
-        // [rs[c], rs[c] + rc[c]) of the queue
-        uint32_t rs[4] = {0u, 0u, 0u, 0u}, rc[4] = {0u, 0u, 0u, 0u};
-        int64_t c0 = 0;
-        // exact distances of the queued survivors, 32 at a time, then every
-        // lane inserts its own row's survivors (all lanes at once)
+        int32_t *wq = qc_all + warp * kTcQueue;
+        uint16_t *wp = qp_all + warp * kTcQueue;
+        constexpr uint32_t kNil = 0xffffu;
+        uint32_t qn = 0u;       // entries in the warp's queue (warp-uniform)
+        uint32_t head = kNil;   // this row's last queued entry
+        // every lane walks its own row's chain: exact distance, then insertion
         auto flush = [&]() {
-            for (uint32_t q = lane; q < qn; q += 32) {
-                const uint32_t e = wq[q];
-                wd[q] = thread_exact_d2(a.X, a.D, q0 + 32 * warp + (e >> 8), c0 + (e & 255u), vec4);
-            }
             __syncwarp();
-#pragma unroll
-            for (int c = 0; c < 4; c++) {
-                for (uint32_t q = rs[c]; q < rs[c] + rc[c]; q++) {
-                    n_exact++;
-                    const float d = wd[q];
-                    const int32_t cand = (int32_t)(c0 + (wq[q] & 255u));
-                    if (!(d < tau || (d == tau && cand < jlast))) continue;
-                    n_ins++;
-                    int p = k - 1;
-                    while (p > 0 && (myd[p - 1] > d || (myd[p - 1] == d && myj[p - 1] > cand))) {
-                        myd[p] = myd[p - 1];
-                        myj[p] = myj[p - 1];
-                        p--;
-                    }
-                    myd[p] = d;
-                    myj[p] = cand;
-                    tau = myd[k - 1];
-                    jlast = myj[k - 1];
-                    tauA = fminf(tau - onem * qn2, 3.402823466e38f);
+            for (uint32_t q = head; q != kNil; q = wp[q]) {
+                const int32_t cand = wq[q];
+                const float d = thread_exact_d2(a.X, a.D, qi, cand, vec4);
+                n_exact++;
+                if (!(d < tau || (d == tau && cand < jlast))) continue;
+                n_ins++;
+                int p = k - 1;
+                while (p > 0 && (myd[p - 1] > d || (myd[p - 1] == d && myj[p - 1] > cand))) {
+                    myd[p] = myd[p - 1];
+                    myj[p] = myj[p - 1];
+                    p--;
                 }
-                rc[c] = 0u;
+                myd[p] = d;
+                myj[p] = cand;
+                tau = myd[k - 1];
+                jlast = myj[k - 1];
+                tauA = fminf(tau - onem * qn2, 3.402823466e38f);
             }
             __syncwarp();
+            head = kNil;
             qn = 0u;
         };
         for (int64_t i = 0; i < T; i++) {
@@ -530,15 +522,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             const uint32_t par = (uint32_t)((i / kTcAcc) & 1);
             // warp-uniform: every lane takes the same path into the aligned
             // TMEM loads and the warp-synchronous queue below
-            const bool got = __all_sync(0xffffffffu, tc::mbar_wait(&bar_tf[b], par, kTcPolls) &&
-                                                         tc::mbar_wait(&bar_hf[b], par, kTcPolls));
+            const bool got =
+                __all_sync(0xffffffffu, tc::mbar_wait_sleep(&bar_tf[b], par, kTcPolls, 2000u) &&
+                                            tc::mbar_wait_sleep(&bar_hf[b], par, kTcPolls, 2000u));
             if (!got || s_abort) {
                 s_abort = 1;
                 if (!got && lane == 0) atomicOr(a.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
                 break;
             }
             tc::fence_after();
-            c0 = t * kTcCols;
+            const int64_t c0 = t * kTcCols;
             const float gmax = __ldg(a.Gmax + t);
             const float *hb = hbuf + b * kTcCols;
 #pragma unroll
@@ -586,24 +579,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                     }
                     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
                     if (qn + total > (uint32_t)kTcQueue) flush();
-                    rs[ci] = qn + incl - cnt;
-                    rc[ci] = cnt;
                     uint32_t mm = sm;
-                    for (uint32_t q = rs[ci]; mm; q++) {
+                    for (uint32_t q = qn + incl - cnt; mm; q++) {
                         const int j = __ffs(mm) - 1;
                         mm &= mm - 1u;
-                        wq[q] = (uint16_t)((lane << 8) | (cb + j));
+                        wq[q] = (int32_t)(c0 + cb + j);
+                        wp[q] = (uint16_t)head;
+                        head = q;
                     }
                     qn += total;
                     __syncwarp();
                 }
             }
-            // the accumulator is free once read; the queue is then flushed
+            // the accumulator is free once read; the queue is flushed once it
+            // holds a batch
             tc::fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&bar_te[b]);
-            if (qn) flush();
+            if (qn >= 32u) flush();
         }
+        if (qn) flush();
         atomicAdd(&a.stats[0], (u64)n_exact);
         atomicAdd(&a.stats[1], (u64)n_ins);
     }

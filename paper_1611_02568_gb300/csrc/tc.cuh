@@ -130,6 +130,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, uint32_t parity, int m
     return done != 0;
 }
 
+// As mbar_wait, but each poll may suspend the thread for up to `hint_ns`
+// nanoseconds until the phase completes (frees issue slots while waiting).
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t *mbar, uint32_t parity, int max_polls,
+                                                uint32_t hint_ns) {
+    uint32_t done = 0;
+    for (int it = 0; it < max_polls && !done; it++) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            "selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_u32(mbar)), "r"(parity), "r"(hint_ns)
+            : "memory");
+    }
+    return done != 0;
+}
+
 // 32 consecutive FP32 columns of this warp's 32 TMEM lanes (lane = thread).
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     uint32_t r[32];
