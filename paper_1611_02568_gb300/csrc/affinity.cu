@@ -338,6 +338,15 @@ __device__ __forceinline__ float thread_exact_d2(const float *__restrict__ X, in
     return s;
 }
 
+// A neighbour-list entry; (d, j) orders by distance, then by index.
+struct __align__(8) KnnEntry {
+    float d;
+    int32_t j;
+};
+__device__ __forceinline__ bool knn_worse(KnnEntry a, KnnEntry b) {
+    return a.d > b.d || (a.d == b.d && a.j > b.j);
+}
+
 struct KnnTcArgs {
     int64_t n, T;
     int D, Dp, k;
@@ -366,23 +375,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
     uint8_t *sA = smem;
     uint8_t *sB = smem + tile_bytes;
     float *hbuf = reinterpret_cast<float *>(sB + (size_t)kTcStages * tile_bytes);  // [4][128]
-    // row lists with an odd stride (no bank conflicts between the rows)
+    // per row: its k best (d2, index) so far as a max-heap on (d2, index),
+    // rows at an odd stride (no bank conflicts between the rows)
     const int ks = k | 1;
-    float *ld = hbuf + kTcAcc * kTcCols;
-    int32_t *lj = reinterpret_cast<int32_t *>(ld + kTcRows * ks);
+    KnnEntry *lst = reinterpret_cast<KnnEntry *>(hbuf + kTcAcc * kTcCols);
     // per filter warp: queued survivors (candidate index) and, per entry, the
     // previous entry of the same row
-    int32_t *qc_all = lj + kTcRows * ks;
+    int32_t *qc_all = reinterpret_cast<int32_t *>(lst + kTcRows * ks);
     uint16_t *qp_all = reinterpret_cast<uint16_t *>(qc_all + 4 * kTcQueue);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t qt = blockIdx.x;  // query tile
     const int64_t q0 = qt * kTcRows;
 
-    for (int e = tid; e < kTcRows * ks; e += kTcThreads) {
-        ld[e] = INFINITY;
-        lj[e] = 0x7fffffff;
-    }
+    for (int e = tid; e < kTcRows * ks; e += kTcThreads) lst[e] = KnnEntry{INFINITY, 0x7fffffff};
     if (warp == 5) tc::tmem_alloc(&tslot, kTcAcc * kTcCols);
     if (tid == 0) {
         tc::mbar_init(&bar_a, 1);
@@ -474,8 +480,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
         const int64_t qi = q0 + tid;
         const bool qvalid = qi < n;
         const float qn2 = qvalid ? a.nrm[qi] : 0.f, qn1 = sqrtf(qn2);
-        float *myd = ld + (size_t)tid * ks;
-        int32_t *myj = lj + (size_t)tid * ks;
+        KnnEntry *heap = lst + (size_t)tid * ks;
         float tau = INFINITY;
         int32_t jlast = 0x7fffffff;
         uint32_t n_exact = 0u, n_ins = 0u;
@@ -500,16 +505,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                 n_exact++;
                 if (!(d < tau || (d == tau && cand < jlast))) continue;
                 n_ins++;
-                int p = k - 1;
-                while (p > 0 && (myd[p - 1] > d || (myd[p - 1] == d && myj[p - 1] > cand))) {
-                    myd[p] = myd[p - 1];
-                    myj[p] = myj[p - 1];
-                    p--;
+                // the new entry replaces the worst (the root) and sinks
+                const KnnEntry ne{d, cand};
+                int p = 0;
+                for (;;) {
+                    int m = 2 * p + 1;
+                    if (m >= k) break;
+                    KnnEntry cm = heap[m];
+                    if (m + 1 < k) {
+                        const KnnEntry cr = heap[m + 1];
+                        if (knn_worse(cr, cm)) {
+                            cm = cr;
+                            m++;
+                        }
+                    }
+                    if (!knn_worse(cm, ne)) break;
+                    heap[p] = cm;
+                    p = m;
                 }
-                myd[p] = d;
-                myj[p] = cand;
-                tau = myd[k - 1];
-                jlast = myj[k - 1];
+                heap[p] = ne;
+                const KnnEntry rt = heap[0];
+                tau = rt.d;
+                jlast = rt.j;
                 tauA = fminf(tau - onem * qn2, 3.402823466e38f);
             }
             __syncwarp();
@@ -606,12 +623,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
     __syncthreads();
     tc::fence_after();
     if (warp == 5) tc::tmem_dealloc(tbase, kTcAcc * kTcCols);
+    // heap sort of each row's list (ascending), then out
+    if (tid < kTcRows) {
+        KnnEntry *heap = lst + (size_t)tid * ks;
+        for (int last = k - 1; last > 0; last--) {
+            const KnnEntry top = heap[0], ne = heap[last];
+            heap[last] = top;
+            int p = 0;
+            for (;;) {
+                int m = 2 * p + 1;
+                if (m >= last) break;
+                KnnEntry cm = heap[m];
+                if (m + 1 < last) {
+                    const KnnEntry cr = heap[m + 1];
+                    if (knn_worse(cr, cm)) {
+                        cm = cr;
+                        m++;
+                    }
+                }
+                if (!knn_worse(cm, ne)) break;
+                heap[p] = cm;
+                p = m;
+            }
+            heap[p] = ne;
+        }
+    }
+    __syncthreads();
     for (int e = tid; e < kTcRows * k; e += kTcThreads) {
         const int r = e / k, j = e % k;
         const int64_t row = q0 + r;
         if (row < n) {
-            a.out_idx[row * k + j] = lj[r * ks + j];
-            a.out_d2[row * k + j] = ld[r * ks + j];
+            const KnnEntry v = lst[r * ks + j];
+            a.out_idx[row * k + j] = v.j;
+            a.out_d2[row * k + j] = v.d;
         }
     }
 }
