@@ -238,18 +238,20 @@ __global__ void __launch_bounds__(kKnnThreads)
 // same order, so that concurrent CTAs share each tile through L2).  Warp roles: warp 4 streams candidate tiles (pre-swizzled FP16
 // images, one bulk copy each) into a ring of shared-memory stages; warp 5
 // issues the MMAs into four TMEM accumulators; warps 0-3 (one query row per
-// thread, TMEM lanes 32w..32w+31) filter.  The filter's fast path needs two
-// instructions per (row, candidate): with h_j = (1-eps)|c_j|^2 and the tile's
-// largest |c|, a 32-column chunk is skipped when
-//   min_j (h_j - 2 q.c_j) > tau - (1-eps)|q|^2 + kappa |q| max|c|.
-// Otherwise the exact per-column bound picks the survivors.  A warp queues the
+// thread, TMEM lanes 32w..32w+31) filter.  With h_j = (1-eps)|c_j|^2 and
+// g_j = |c_j| (staged with the tile), each (row, candidate) costs two FMAs and
+// a min: a 32-column chunk is skipped when
+//   min_j (h_j - kappa |q| g_j - 2 q.c_j) > tau - (1-eps)|q|^2,
+// and otherwise the same per-column values pick the survivors.  A warp queues the
 // survivors of its 32 rows (a chain per row through the queue) over as many
-// tiles as it takes to gather about 32; then every lane walks its own chain,
-// computing exact distances and inserting, all lanes at once.
+// tiles as it takes to gather a batch; then the warp computes their exact
+// distances, one survivor per lane, and every lane walks its own row's chain
+// inserting them, all lanes at once.
 constexpr int kTcRows = 128;     // query rows per CTA (MMA M)
 constexpr int kTcCols = 128;     // candidates per tile (MMA N)
 constexpr int kTcStages = 2;     // candidate-tile stages in shared memory
-constexpr int kTcQueue = 1024;   // survivor queue per filter warp (entries)
+constexpr int kTcQueue = 768;    // survivor queue per filter warp (entries)
+constexpr uint32_t kTcFlushAt = 128u;  // queued survivors that trigger a flush
 constexpr int kTcAcc = 4;        // TMEM accumulators (4 x 128 columns)
 constexpr int kTcThreads = 192;  // warps 0-3 filter, 4 loads, 5 issues MMAs
 constexpr int kTcPolls = 1 << 22;
@@ -287,25 +289,17 @@ __global__ void k_to_half_img(int64_t n, int D, int Dp, int64_t T, float scale,
         *reinterpret_cast<const uint4 *>(h);
 }
 
-// Per candidate: h = (1-eps)|c|^2 (+inf past n) and |c|; per tile: max |c|.
+// Per candidate tile t: h_j = (1-eps)|c_j|^2 (+inf past n) at HG[256 t + j]
+// and |c_j| at HG[256 t + 128 + j].
 __global__ void k_tile_norms(int64_t n, int64_t T, float eps_abs, const float *__restrict__ nrm,
-                             float *__restrict__ H, float *__restrict__ G,
-                             float *__restrict__ Gmax) {
-    const int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (t >= T) return;
-    float m = 0.f;
-    for (int j = lane; j < kTcCols; j += 32) {
-        const int64_t c = t * kTcCols + j;
-        const float c2 = c < n ? nrm[c] : 0.f;
-        const float g = sqrtf(c2);
-        H[c] = c < n ? (1.0f - eps_abs) * c2 : INFINITY;
-        G[c] = g;
-        m = fmaxf(m, g);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) Gmax[t] = m;
+                             float *__restrict__ HG) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= T * kTcCols) return;
+    const int64_t t = i / kTcCols;
+    const int j = (int)(i % kTcCols);
+    const float c2 = i < n ? nrm[i] : 0.f;
+    HG[t * 2 * kTcCols + j] = i < n ? (1.0f - eps_abs) * c2 : INFINITY;
+    HG[t * 2 * kTcCols + kTcCols + j] = sqrtf(c2);
 }
 
 // Exact FP32 squared distance between rows a and b by one thread, summed in
@@ -354,7 +348,7 @@ struct KnnTcArgs {
     const float *X;       // FP32 rows (exact distances)
     const uint8_t *img;   // FP16 tile images
     const float *nrm;     // |x|^2
-    const float *H, *G, *Gmax;
+    const float *HG;      // per tile: h_j then |c_j|
     int32_t *out_idx;
     float *out_d2;
     unsigned *err;
@@ -374,15 +368,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
     const uint32_t tile_bytes = (uint32_t)kTcRows * a.Dp * 2;
     uint8_t *sA = smem;
     uint8_t *sB = smem + tile_bytes;
-    float *hbuf = reinterpret_cast<float *>(sB + (size_t)kTcStages * tile_bytes);  // [4][128]
+    // per accumulator: h_j (128) then g_j (128) of its tile
+    float *hbuf = reinterpret_cast<float *>(sB + (size_t)kTcStages * tile_bytes);  // [4][256]
     // per row: its k best (d2, index) so far as a max-heap on (d2, index),
     // rows at an odd stride (no bank conflicts between the rows)
     const int ks = k | 1;
-    KnnEntry *lst = reinterpret_cast<KnnEntry *>(hbuf + kTcAcc * kTcCols);
-    // per filter warp: queued survivors (candidate index) and, per entry, the
-    // previous entry of the same row
-    int32_t *qc_all = reinterpret_cast<int32_t *>(lst + kTcRows * ks);
-    uint16_t *qp_all = reinterpret_cast<uint16_t *>(qc_all + 4 * kTcQueue);
+    KnnEntry *lst = reinterpret_cast<KnnEntry *>(hbuf + kTcAcc * 2 * kTcCols);
+    // per filter warp: queued survivors (row lane << 24 | candidate index),
+    // their exact d2 and, per entry, the previous entry of the same row
+    uint32_t *qc_all = reinterpret_cast<uint32_t *>(lst + kTcRows * ks);
+    float *qd_all = reinterpret_cast<float *>(qc_all + 4 * kTcQueue);
+    uint16_t *qp_all = reinterpret_cast<uint16_t *>(qd_all + 4 * kTcQueue);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t qt = blockIdx.x;  // query tile
@@ -433,8 +429,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                     i++;  // the stage copy above is in flight
                     break;
                 }
-                tc::mbar_expect_tx(&bar_hf[b], kTcCols * 4);
-                tc::bulk_g2s(hbuf + b * kTcCols, a.H + t * kTcCols, kTcCols * 4, &bar_hf[b]);
+                tc::mbar_expect_tx(&bar_hf[b], 2 * kTcCols * 4);
+                tc::bulk_g2s(hbuf + b * 2 * kTcCols, a.HG + t * 2 * kTcCols, 2 * kTcCols * 4,
+                             &bar_hf[b]);
             }
             // copies still in flight complete before the CTA exits
             tc::mbar_wait(&bar_a, 0u, kTcPolls);
@@ -491,17 +488,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
         // tau - (1 - eps)|q|^2; finite while the list fills so that padding
         // candidates (+inf) never pass
         float tauA = 3.402823466e38f;
-        int32_t *wq = qc_all + warp * kTcQueue;
+        uint32_t *wq = qc_all + warp * kTcQueue;
+        float *wd = qd_all + warp * kTcQueue;
         uint16_t *wp = qp_all + warp * kTcQueue;
         constexpr uint32_t kNil = 0xffffu;
         uint32_t qn = 0u;       // entries in the warp's queue (warp-uniform)
         uint32_t head = kNil;   // this row's last queued entry
-        // every lane walks its own row's chain: exact distance, then insertion
+        // exact distances of the queued survivors, one per lane, then every
+        // lane walks its own row's chain and inserts
         auto flush = [&]() {
             __syncwarp();
+            for (uint32_t q = lane; q < qn; q += 32) {
+                const uint32_t e = wq[q];
+                wd[q] = thread_exact_d2(a.X, a.D, q0 + 32 * warp + (e >> 24), e & 0xffffffu, vec4);
+            }
+            __syncwarp();
             for (uint32_t q = head; q != kNil; q = wp[q]) {
-                const int32_t cand = wq[q];
-                const float d = thread_exact_d2(a.X, a.D, qi, cand, vec4);
+                const int32_t cand = (int32_t)(wq[q] & 0xffffffu);
+                const float d = wd[q];
                 n_exact++;
                 if (!(d < tau || (d == tau && cand < jlast))) continue;
                 n_ins++;
@@ -549,63 +553,63 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             }
             tc::fence_after();
             const int64_t c0 = t * kTcCols;
-            const float gmax = __ldg(a.Gmax + t);
-            const float *hb = hbuf + b * kTcCols;
+            const float *hb = hbuf + b * 2 * kTcCols;
 #pragma unroll
             for (int ci = 0; ci < 4; ci++) {
                 const int cb = 32 * ci;
                 float v[32];
                 tc::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * kTcCols + cb),
                               v);
-                // fast path: the chunk's smallest h_j - 2 q.c_j against the
-                // loosest bound of the tile
+                // e_j = (1-eps)|c|^2 - kappa|q||c| - 2 q.c (in place of v)
                 float mn[8];
 #pragma unroll
                 for (int j4 = 0; j4 < 8; j4++) {
                     const float4 h4 = *reinterpret_cast<const float4 *>(hb + cb + 4 * j4);
-                    const float e0 = fmaf(cneg, v[4 * j4], h4.x);
-                    const float e1 = fmaf(cneg, v[4 * j4 + 1], h4.y);
-                    const float e2 = fmaf(cneg, v[4 * j4 + 2], h4.z);
-                    const float e3 = fmaf(cneg, v[4 * j4 + 3], h4.w);
-                    mn[j4] = fminf(fminf(e0, e1), fminf(e2, e3));
+                    const float4 g4 = *reinterpret_cast<const float4 *>(hb + kTcCols + cb + 4 * j4);
+                    v[4 * j4] = fmaf(-Bq, g4.x, fmaf(cneg, v[4 * j4], h4.x));
+                    v[4 * j4 + 1] = fmaf(-Bq, g4.y, fmaf(cneg, v[4 * j4 + 1], h4.y));
+                    v[4 * j4 + 2] = fmaf(-Bq, g4.z, fmaf(cneg, v[4 * j4 + 2], h4.z));
+                    v[4 * j4 + 3] = fmaf(-Bq, g4.w, fmaf(cneg, v[4 * j4 + 3], h4.w));
+                    mn[j4] = fminf(fminf(v[4 * j4], v[4 * j4 + 1]), fminf(v[4 * j4 + 2], v[4 * j4 + 3]));
                 }
                 const float m = fminf(fminf(fminf(mn[0], mn[1]), fminf(mn[2], mn[3])),
                                       fminf(fminf(mn[4], mn[5]), fminf(mn[6], mn[7])));
-                const float thr = fminf(tauA + Bq * gmax, 3.402823466e38f);
                 uint32_t sm = 0u;
-                if (qvalid && m <= thr) {
-                    // exact per-column bound:
+                if (qvalid && m <= tauA) {
+                    // survivors:
                     //   (1-eps)|c|^2 - kappa|q||c| - 2 q.c <= tau - (1-eps)|q|^2
 #pragma unroll
-                    for (int j = 0; j < 32; j++) {
-                        const float lhs =
-                            fmaf(-Bq, __ldg(a.G + c0 + cb + j), fmaf(cneg, v[j], hb[cb + j]));
-                        sm |= (lhs <= tauA) ? (1u << j) : 0u;
-                    }
+                    for (int j = 0; j < 32; j++) sm |= (v[j] <= tauA) ? (1u << j) : 0u;
                     if (qi >= c0 + cb && qi < c0 + cb + 32) sm &= ~(1u << (int)(qi - c0 - cb));
                 }
                 if (__any_sync(0xffffffffu, sm != 0u)) {
-                    // append the chunk's survivors to the queue (flush first
-                    // if they might not fit)
-                    const uint32_t cnt = (uint32_t)__popc(sm);
-                    uint32_t incl = cnt;
+                    // append the chunk's survivors to the queue, 16 columns at
+                    // a time (at most 512 entries; flush first if they might
+                    // not fit)
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += y;
+                    for (int hf = 0; hf < 2; hf++) {
+                        const uint32_t hm = hf ? (sm & 0xffff0000u) : (sm & 0x0000ffffu);
+                        const uint32_t cnt = (uint32_t)__popc(hm);
+                        uint32_t incl = cnt;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl += y;
+                        }
+                        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                        if (total == 0u) continue;
+                        if (qn + total > (uint32_t)kTcQueue) flush();
+                        uint32_t mm = hm;
+                        for (uint32_t q = qn + incl - cnt; mm; q++) {
+                            const int j = __ffs(mm) - 1;
+                            mm &= mm - 1u;
+                            wq[q] = ((uint32_t)lane << 24) | (uint32_t)(c0 + cb + j);
+                            wp[q] = (uint16_t)head;
+                            head = q;
+                        }
+                        qn += total;
+                        __syncwarp();
                     }
-                    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-                    if (qn + total > (uint32_t)kTcQueue) flush();
-                    uint32_t mm = sm;
-                    for (uint32_t q = qn + incl - cnt; mm; q++) {
-                        const int j = __ffs(mm) - 1;
-                        mm &= mm - 1u;
-                        wq[q] = (int32_t)(c0 + cb + j);
-                        wp[q] = (uint16_t)head;
-                        head = q;
-                    }
-                    qn += total;
-                    __syncwarp();
                 }
             }
             // the accumulator is free once read; the queue is flushed once it
@@ -613,7 +617,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             tc::fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&bar_te[b]);
-            if (qn >= 32u) flush();
+            if (qn >= kTcFlushAt) flush();
         }
         if (qn) flush();
         atomicAdd(&a.stats[0], (u64)n_exact);
@@ -661,8 +665,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
 }
 
 static size_t knn_tc_smem(int Dp, int k) {
-    return (size_t)(1 + kTcStages) * kTcRows * Dp * 2 + (size_t)kTcAcc * kTcCols * 4 +
-           (size_t)kTcRows * (k | 1) * 8 + (size_t)4 * kTcQueue * (4 + 2) + 1024;
+    return (size_t)(1 + kTcStages) * kTcRows * Dp * 2 + (size_t)kTcAcc * 2 * kTcCols * 4 +
+           (size_t)kTcRows * (k | 1) * 8 + (size_t)4 * kTcQueue * (4 + 4 + 2) + 1024;
 }
 
 cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, int32_t k,
@@ -708,13 +712,11 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         uint8_t *img = nullptr;
         float *HG = nullptr;
         if ((e = cudaMallocAsync(&img, img_bytes, st))) return e;
-        if ((e = cudaMallocAsync(&HG, (size_t)T * (2 * kTcCols + 1) * sizeof(float), st)))
-            return e;
-        float *H = HG, *G = HG + T * kTcCols, *Gmax = HG + 2 * T * kTcCols;
+        if ((e = cudaMallocAsync(&HG, (size_t)T * 2 * kTcCols * sizeof(float), st))) return e;
         const int64_t nchunks = T * kTcRows * (Dp / 8);
         k_to_half_img<<<(unsigned)((nchunks + 255) / 256), 256, 0, st>>>(n, D, Dp, T, scale, Xdev,
                                                                           img);
-        k_tile_norms<<<(unsigned)((T + 7) / 8), 256, 0, st>>>(n, T, eps_abs, nrm, H, G, Gmax);
+        k_tile_norms<<<(unsigned)((T * kTcCols + 255) / 256), 256, 0, st>>>(n, T, eps_abs, nrm, HG);
         if ((e = cudaGetLastError())) return e;
         if ((e = cudaFuncSetAttribute(k_knn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem_tc)))
@@ -731,9 +733,7 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         ka.X = Xdev;
         ka.img = img;
         ka.nrm = nrm;
-        ka.H = H;
-        ka.G = G;
-        ka.Gmax = Gmax;
+        ka.HG = HG;
         ka.out_idx = idx;
         ka.out_d2 = d2;
         ka.err = err;
