@@ -255,6 +255,7 @@ constexpr uint32_t kTcFlushAt = 128u;  // queued survivors that trigger a flush
 constexpr int kTcAcc = 4;        // TMEM accumulators (4 x 128 columns)
 constexpr int kTcThreads = 192;  // warps 0-3 filter, 4 loads, 5 issues MMAs
 constexpr int kTcPolls = 1 << 22;
+constexpr uint32_t kTcSleepNs = 2000u;  // suspend hint of the pipeline waits
 
 __global__ void k_absmax(int64_t m, const float *__restrict__ X, unsigned *out) {
     unsigned v = 0u;
@@ -358,7 +359,7 @@ struct KnnTcArgs {
 __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bar_a, bar_sf[kTcStages], bar_se[kTcStages], bar_tf[kTcAcc],
-        bar_te[kTcAcc], bar_hf[kTcAcc];
+        bar_te[kTcAcc], bar_hf[kTcAcc], bar_he[kTcAcc];
     __shared__ uint32_t tslot;
     __shared__ volatile int s_abort;
     // 1024-byte aligned base for the swizzled operand tiles
@@ -396,6 +397,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             tc::mbar_init(&bar_tf[b], 1);
             tc::mbar_init(&bar_te[b], 4);
             tc::mbar_init(&bar_hf[b], 1);
+            tc::mbar_init(&bar_he[b], 4);
         }
         s_abort = 0;
     }
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                 const int64_t t = i;
                 const int s = (int)(i % kTcStages), b = (int)(i % kTcAcc);
                 if (i >= kTcStages &&
-                    !tc::mbar_wait_sleep(&bar_se[s], (uint32_t)((i / kTcStages - 1) & 1), kTcPolls, 2000u)) {
+                    !tc::mbar_wait_sleep(&bar_se[s], (uint32_t)((i / kTcStages - 1) & 1), kTcPolls, kTcSleepNs)) {
                     s_abort = 1;
                     atomicOr(a.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
                     break;
@@ -423,7 +425,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                 tc::bulk_g2s(sB + (size_t)s * tile_bytes, a.img + t * tile_bytes, tile_bytes,
                              &bar_sf[s]);
                 if (i >= kTcAcc &&
-                    !tc::mbar_wait_sleep(&bar_te[b], (uint32_t)((i / kTcAcc - 1) & 1), kTcPolls, 2000u)) {
+                    !tc::mbar_wait_sleep(&bar_he[b], (uint32_t)((i / kTcAcc - 1) & 1), kTcPolls, kTcSleepNs)) {
                     s_abort = 1;
                     atomicOr(a.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
                     i++;  // the stage copy above is in flight
@@ -449,9 +451,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             int64_t i = 0;
             for (; ok && i < T && !s_abort; i++) {
                 const int s = (int)(i % kTcStages), b = (int)(i % kTcAcc);
-                ok = tc::mbar_wait_sleep(&bar_sf[s], (uint32_t)((i / kTcStages) & 1), kTcPolls, 2000u);
+                ok = tc::mbar_wait_sleep(&bar_sf[s], (uint32_t)((i / kTcStages) & 1), kTcPolls, kTcSleepNs);
                 if (ok && i >= kTcAcc)
-                    ok = tc::mbar_wait_sleep(&bar_te[b], (uint32_t)((i / kTcAcc - 1) & 1), kTcPolls, 2000u);
+                    ok = tc::mbar_wait_sleep(&bar_te[b], (uint32_t)((i / kTcAcc - 1) & 1), kTcPolls, kTcSleepNs);
                 if (!ok) break;
                 tc::fence_after();
                 const uint32_t b0 = tc::smem_u32(sB + (size_t)s * tile_bytes);
@@ -544,8 +546,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             // warp-uniform: every lane takes the same path into the aligned
             // TMEM loads and the warp-synchronous queue below
             const bool got =
-                __all_sync(0xffffffffu, tc::mbar_wait_sleep(&bar_tf[b], par, kTcPolls, 2000u) &&
-                                            tc::mbar_wait_sleep(&bar_hf[b], par, kTcPolls, 2000u));
+                __all_sync(0xffffffffu, tc::mbar_wait_sleep(&bar_tf[b], par, kTcPolls, kTcSleepNs) &&
+                                            tc::mbar_wait_sleep(&bar_hf[b], par, kTcPolls, kTcSleepNs));
             if (!got || s_abort) {
                 s_abort = 1;
                 if (!got && lane == 0) atomicOr(a.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
@@ -554,12 +556,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             tc::fence_after();
             const int64_t c0 = t * kTcCols;
             const float *hb = hbuf + b * 2 * kTcCols;
+            // all 128 columns of the warp's rows in one round trip; the
+            // accumulator is released right after, h and g after the filter
+            uint32_t raw[4][32];
+#pragma unroll
+            for (int ci = 0; ci < 4; ci++)
+                tc::tmem_ld32_async(
+                    tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * kTcCols + 32 * ci),
+                    raw[ci]);
+            tc::tmem_wait_ld();
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&bar_te[b]);
 #pragma unroll
             for (int ci = 0; ci < 4; ci++) {
                 const int cb = 32 * ci;
                 float v[32];
-                tc::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * kTcCols + cb),
-                              v);
+#pragma unroll
+                for (int j = 0; j < 32; j++) v[j] = __uint_as_float(raw[ci][j]);
                 // e_j = (1-eps)|c|^2 - kappa|q||c| - 2 q.c (in place of v)
                 float mn[8];
 #pragma unroll
@@ -612,11 +626,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                     }
                 }
             }
-            // the accumulator is free once read; the queue is flushed once it
-            // holds a batch
-            tc::fence_before();
+            // the tile's h and g are no longer needed
             __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&bar_te[b]);
+            if (lane == 0) tc::mbar_arrive(&bar_he[b]);
+            // the queue is flushed once it holds a batch
             if (qn >= kTcFlushAt) flush();
         }
         if (qn) flush();
