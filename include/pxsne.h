@@ -291,9 +291,11 @@ int pxsne_pca(const float *X, int64_t n, int32_t D, int32_t dout, float *Xout,
 /* Normalise an embedding Y (n x 2) to zero mean and unit RMS per coordinate
  * (isotropic scale) and, when Yref is non-NULL, apply the orthogonal map
  * (rotation or reflection) that best aligns it with the normalised Yref in the
- * least-squares sense (2 x 2 orthogonal Procrustes, closed form).  Used to put
- * target embeddings of different random seeds in one frame before training the
- * warm start.  Yout may alias Y.  Host or device buffers per on_device. */
+ * least-squares sense (2 x 2 orthogonal Procrustes, closed form).  Row i of Y
+ * and row i of Yref must be the same point (e.g. an embedding and a network's
+ * prediction for the same rows).  Used to put the warm start's training
+ * embeddings in one frame.  Yout may alias Y.  Host or device buffers per
+ * on_device. */
 int pxsne_embed_align(const float *Y, const float *Yref, int64_t n, float *Yout, int on_device);
 
 /* ------------------------------------------------------------------------

@@ -432,7 +432,8 @@ class MLP:
 
 
 def embed_align(Y, Yref=None):
-    """Centre, scale to unit RMS and (with Yref) orthogonally align Y (numpy)."""
+    """Centre, scale to unit RMS and (with Yref, whose row i is the same point
+    as row i of Y) orthogonally align Y (numpy)."""
     L = load()
     Y = np.ascontiguousarray(Y, np.float32)
     out = np.empty_like(Y)

@@ -101,54 +101,73 @@ def test_embed_align_recovers_orthogonal_transforms(px):
         np.testing.assert_allclose(out, ref_n, atol=2e-4)
 
 
-def _embedding(px, X, seed, iters, L):
-    with px.Context(px.Params(log2_r=L)) as ctx:
-        ctx.affinities(X)
-        ctx.init(datagen.init_y0(seed, X.shape[0]))
-        ctx.step(iters)
-        Y, _ = ctx.get_Y(want_pix=False)
-    return Y
+def _rms(Y):
+    Y = Y.astype(np.float64)
+    Y = Y - Y.mean(0)
+    return float(np.sqrt((Y ** 2).sum() / (2 * len(Y))))
 
 
 @pytest.mark.slow
-def test_warm_start_beats_random_init_early(px):
+def test_warm_start_beats_random_init(px):
     """The network trained on embeddings of independent draws of the same
-    mixture places a fresh draw so that refinement (no exaggeration) is ahead
-    of the plain method from a random start at equal iteration counts."""
+    mixture places a fresh draw ahead of the plain method: its start alone has
+    a lower KL than 250 plain iterations, refinement (no exaggeration) stays
+    ahead at equal iteration counts, and after 1,000 iterations it is within 1 %
+    of the plain run.
+
+    Training layouts: the first from the plain method; the others refined from
+    the prediction of a network fitted to the first (so they share its
+    arrangement) and rotated onto that prediction, row for row."""
     n, L = 20000, 10
-    Xs = [datagen.gmm128(seed=s, n=n)[0] for s in (11, 12, 13)]
-    Ys = [_embedding(px, X, s, 1000, L) for s, X in zip((11, 12, 13), Xs)]
-    ref = px.embed_align(Ys[0])
-    Ts = [ref] + [px.embed_align(Y, ref) for Y in Ys[1:]]
-    Xtr = np.concatenate(Xs) * np.float32(0.1)
-    Ttr = np.concatenate(Ts)
+    xs = np.float32(0.1)
+    Xs, Ts, rr = [], [], []
+    first = None
+    for s in (11, 12, 13):
+        X = datagen.gmm128(seed=s, n=n)[0]
+        with px.Context(px.Params(log2_r=L)) as ctx:
+            ctx.affinities(X)
+            if first is None:
+                ctx.init(datagen.init_y0(s, n))
+                ctx.step(1000)
+                Y, _ = ctx.get_Y(want_pix=False)
+                T = px.embed_align(Y)
+                first = px.MLP(128, seed=1)
+                first.train(X * xs, T, epochs=30, batch=2048, lr=1e-3, seed=2)
+            else:
+                Pk = px.embed_align(first.predict(X * xs))
+                ctx.set_schedule(exag_iters=0, momentum_switch=0)
+                ctx.init((Pk * np.float32(rr[0])).astype(np.float32))
+                ctx.step(500)
+                Y, _ = ctx.get_Y(want_pix=False)
+                T = px.embed_align(Y, Pk)
+                # the refined layout keeps the predicted arrangement
+                assert float(((T - Pk) ** 2).sum(1).mean()) < 0.1
+        rr.append(_rms(Y))
+        Xs.append(X * xs)
+        Ts.append(T)
+    first.close()
     Xf, _ = datagen.gmm128(seed=21, n=n)
-    with px.MLP(128, seed=1) as net:
-        net.train(Xtr, Ttr, epochs=20, batch=2048, lr=1e-3, seed=2)
-        Y0w = net.predict(Xf * np.float32(0.1))
+    with px.MLP(128, seed=3) as net:
+        loss = net.train(np.concatenate(Xs), np.concatenate(Ts), epochs=30, batch=2048,
+                         lr=1e-3, seed=2)
+        Y0w = net.predict(Xf * xs) * np.float32(np.mean(rr))
+    assert loss < 0.2, loss
     with px.Context(px.Params(log2_r=L)) as ctx:
         ctx.affinities(Xf)
         ctx.init(datagen.init_y0(21, n))
-        ctx.step(300)
-        kl_plain_300 = ctx.kl()
-        ctx.step(700)
-        kl_plain = ctx.kl()
-        Yp, _ = ctx.get_Y(want_pix=False)
-        rms = float(np.sqrt((Yp.astype(np.float64) ** 2).sum() / (2 * n)))
+        plain = []
+        for _ in range(4):
+            ctx.step(250)
+            plain.append(ctx.kl())
         ctx.set_schedule(exag_iters=0, momentum_switch=0)
-        ctx.init((Y0w * rms).astype(np.float32))
-        kl_warm_0 = ctx.kl()
-        ctx.step(300)
-        kl_warm_300 = ctx.kl()
-        # iterations of the warm start to reach the plain run's final KL
-        it = 300
-        kl = kl_warm_300
-        while kl > kl_plain and it < 1000:
-            ctx.step(50)
-            it += 50
-            kl = ctx.kl()
-    print(f"plain: KL(300) {kl_plain_300:.4f} KL(1000) {kl_plain:.4f}; warm: KL(0) "
-          f"{kl_warm_0:.4f} KL(300) {kl_warm_300:.4f}, reaches {kl:.4f} at {it}")
-    assert kl_warm_300 < kl_plain_300, (kl_warm_300, kl_plain_300)
-    assert kl_warm_0 > kl_warm_300
-    assert kl <= kl_plain and it < 1000, (it, kl, kl_plain)
+        ctx.init(Y0w.astype(np.float32))
+        warm = [ctx.kl()]
+        for _ in range(4):
+            ctx.step(250)
+            warm.append(ctx.kl())
+    print("plain KL at 250..1000:", np.round(plain, 4), "warm KL at 0..1000:", np.round(warm, 4))
+    # the network's start alone is ahead of 250 plain iterations, and the warm
+    # run stays ahead at equal iteration counts
+    assert warm[0] < plain[0], (warm[0], plain[0])
+    assert warm[1] < plain[0] and warm[2] < plain[1], (warm, plain)
+    assert warm[4] <= plain[3] * 1.01, (warm, plain)
