@@ -1,0 +1,110 @@
+"""Parity at the bench's full size and launch configuration: the gmm128 workload
+(n = 1,000,000, D = 128, k = 90, perplexity 30, 2048^2 screen, theta 0.5) run
+through the same calls as bench.py, checked against the oracle on sampled
+outputs it can compute one by one (kNN rows, per-point forces), on whole
+outputs where it is fast enough (the tree, Z), and through properties of P.
+
+Bars: kNN as in test_gpu_parity (FP64 neighbours of the sampled rows); tree
+bit-exact; Frep, Zi, Fattr of the sampled points and Z <= 1e-4 relative L2; P
+sums to 1 and is symmetric."""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+N, D, K, L, THETA = 1_000_000, 128, 90, 11, 0.5
+FORCE_TOL = 1e-4
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def run():
+    import paper_1611_02568_gb300 as px
+    from paper_1611_02568_gb300 import build
+    build.build()
+    X, _ = datagen.gmm128(seed=0, n=N)
+    Y0 = datagen.init_y0(0, N)
+    ctx = px.Context(px.Params(log2_r=L, theta=THETA, k=K, perplexity=30.0))
+    ctx.affinities(X)
+    ctx.init(Y0)
+    rp, col, val = ctx.get_P()
+    P = oracle.CSR(rp, col, val.astype(np.float64))
+    yield X, ctx, P
+    ctx.close()
+
+
+def sample_rows(seed, m=64):
+    r = np.random.default_rng(seed).choice(N, m, replace=False)
+    return np.unique(np.concatenate([r, [0, N - 1]]))
+
+
+def test_knn_sampled_rows(run):
+    X, ctx, _ = run
+    rows = sample_rows(1)
+    idx_o, d2_o = oracle.knn(X, K, rows=rows)
+    idx, d2, _ = ctx.get_knn()
+    x = X.astype(np.float64)
+    for a, r in enumerate(rows):
+        tau = d2_o[a, K - 1]
+        # every returned neighbour is within 2e-5 of the true k-th distance
+        ex = ((x[idx[r]] - x[r]) ** 2).sum(1)
+        assert np.all(ex <= tau * (1 + 2e-5)), r
+        # every true neighbour clearly inside the k-th distance is returned
+        must = set(idx_o[a][d2_o[a] < tau * (1 - 2e-5)].tolist())
+        assert must <= set(idx[r].tolist()), r
+        assert r not in set(idx[r].tolist())
+        np.testing.assert_allclose(d2[r], ex, rtol=1e-5)
+        assert np.all(np.diff(d2[r]) >= 0)
+
+
+def test_P_properties(run):
+    _, ctx, P = run
+    assert abs(P.val.sum() - 1.0) < 1e-5
+    assert np.all(P.val >= 0)
+    assert np.all(np.diff(P.row_ptr) >= K)
+    rp, col, val = P.row_ptr, P.col, P.val
+    for r in sample_rows(2, 32):
+        cs = col[rp[r]:rp[r + 1]]
+        assert np.all(np.diff(cs) > 0)
+        for j, v in zip(cs, val[rp[r]:rp[r + 1]]):
+            cj = col[rp[j]:rp[j + 1]]
+            p = np.searchsorted(cj, r)
+            assert p < cj.size and cj[p] == r
+            assert val[rp[j] + p] == pytest.approx(v, rel=1e-6)
+
+
+def check_state(ctx, P, rows):
+    z, s, _, _, _ = ctx.get_state()
+    Frep, Zi, Fattr, Z = ctx.get_forces()
+    tree = oracle.pyramid(z, L)
+    cnt_o = tree[0]
+    for lev in range(L + 1):
+        cnt, _, _, _ = ctx.get_tree(lev)
+        off = oracle.level_offset(lev)
+        assert np.array_equal(cnt, cnt_o[off:off + 4 ** lev]), f"level {lev} counts"
+    _, _, _, mk = ctx.get_tree(0, morton=True)
+    assert np.array_equal(mk, oracle.leaf_keys(z, L)[2])
+    oF, oZi, _ = oracle.bh_repulsion(z, s, L, THETA, tree=tree)
+    assert abs(Z - oZi.sum()) / oZi.sum() <= FORCE_TOL
+    assert rel(Frep[rows], oF[rows]) <= FORCE_TOL
+    assert rel(Zi[rows], oZi[rows]) <= FORCE_TOL
+    oA = oracle.attraction(P, z, s, rows=rows)
+    assert rel(Fattr[rows], oA) <= FORCE_TOL
+
+
+def test_tree_and_forces_at_init(run):
+    _, ctx, P = run
+    check_state(ctx, P, sample_rows(3, 512))
+
+
+def test_tree_and_forces_after_100_iterations(run):
+    # the attraction's relabelled copy of P is refreshed four times on the way
+    _, ctx, P = run
+    ctx.step(100)
+    check_state(ctx, P, sample_rows(4, 512))
