@@ -144,6 +144,11 @@ def group_bytes(n, nnz, L):
     }
 
 
+# DRAM bytes per launch from one ncu capture of the current kernels at full size
+# (dram__bytes_read.sum + dram__bytes_write.sum, profiles/traffic_gmm128_n1M.md);
+# to be set to None whenever the kernel changes
+TRAFFIC_BYTES = {"k_bh_traverse": 47.65e6, "k_attract": 1.293e9}
+
 FLOP_TEST = 10    # offset, d^2 and criterion of one tested cell
 FLOP_ACCEPT = 10  # kernel value, N w, N w^2 and the three accumulations
 
@@ -363,6 +368,19 @@ def run_gpu(args):
     ctx.affinities(X)
     p_seconds = time.perf_counter() - t0
     n_, nnz = ctx.sizes()
+    # the one dense contraction: q.c for every (query, candidate) pair on the
+    # tensor cores, 2 n^2 D FLOP, against the measured dense bf16 peak (FP16 and
+    # bf16 share the tensor rate)
+    knn_ms = ctx.knn_time_ms()
+    kx, ki, kpath = ctx.knn_counters()
+    knn_flop = 2.0 * n * n * X.shape[1]
+    pk, pk_kind = measured_peaks()
+    knn = {"kernel": "k_knn_tc" if kpath == 1 else "k_knn_tile", "ms": knn_ms,
+           "bound": "tensor", "achieved": knn_flop / (knn_ms / 1e3) / 1e12,
+           "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+           "frac": knn_flop / (knn_ms / 1e3) / 1e12 / pk["bf16_tflops"],
+           "peak_source": f"bf16_tflops of MEASURED_PEAKS.json ({pk_kind})",
+           "exact_rerank_per_row": kx / n, "insertions_per_row": ki / n}
     ctx.init(Y0)
     ctx.step(max(args.warmup, 3) if args.warmup >= 0 else 3)  # graph capture + warm-up
     ctx.sync()
@@ -409,14 +427,15 @@ def run_gpu(args):
         flops = FLOP_TEST * tst + FLOP_ACCEPT * acc
         achieved = flops / (avg_ms[top] / 1e3) / 1e12
         roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": alu_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / alu_peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak_tflops,
+                "traffic": TRAFFIC_BYTES.get(top),
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median "
                                "SM clock of this run)"}
     else:
         achieved = gb[top] / (avg_ms[top] / 1e3) / 1e9
         roof = {"kernel": top, "bound": "hbm", "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "frac": achieved / peaks["hbm_gbs"], "traffic": TRAFFIC_BYTES.get(top),
                 "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_kind})"}
     kernels = {g: {"ms_per_launch": avg_ms[g], "share": groups[g] / sum(groups.values()),
                    "alg_GBps": gb[g] / (avg_ms[g] / 1e3) / 1e9 if avg_ms[g] > 0 else None}
@@ -486,7 +505,7 @@ def run_gpu(args):
                           "accepted_per_point": acc / n, "tested_per_point": tst / n,
                           "warp_steps": wsteps, "nodes": nodes,
                           "lanes_per_step": tst / wsteps if wsteps else None},
-            "profiled_total_ms": prof_total, "p_construction_s": p_seconds,
+            "profiled_total_ms": prof_total, "p_construction_s": p_seconds, "knn": knn,
             "kl_after_timed": kl_after,
             "clocks": ck, "e2e": e2e, "cpu_baseline": cpu, "warmstart": warm,
             # per iteration: update, snap_hist, ceil(L/5) pyramid passes, scan,

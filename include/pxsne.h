@@ -234,6 +234,11 @@ int pxsne_get_counters(pxsne_ctx *ctx, uint64_t *n_accept, uint64_t *n_test,
  * Synchronises. */
 int pxsne_get_knn_counters(pxsne_ctx *ctx, uint64_t *exact, uint64_t *inserted, int32_t *path);
 
+/* Device time in milliseconds of the last neighbour-search kernel (the brute
+ * force of Sec. 3.3's kNN pattern; CUDA events around its launch on the
+ * context's stream).  PXSNE_E_STATE if no search has run.  Synchronises. */
+int pxsne_get_knn_time(pxsne_ctx *ctx, double *search_ms);
+
 /* Total bytes of device memory the context holds. */
 int64_t pxsne_device_bytes(const pxsne_ctx *ctx);
 

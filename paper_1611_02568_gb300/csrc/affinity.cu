@@ -682,6 +682,14 @@ static size_t knn_tc_smem(int Dp, int k) {
            (size_t)kTcRows * (k | 1) * 8 + (size_t)4 * kTcQueue * (4 + 4 + 2) + 1024;
 }
 
+// Timing events around the search kernel (created on first use).
+static cudaError_t knn_mark(pxsne_ctx *c, int which, cudaStream_t st) {
+    cudaError_t e;
+    if (!c->knn_ev[which] && (e = cudaEventCreate(&c->knn_ev[which]))) return e;
+    c->knn_timed = (which == 1);
+    return cudaEventRecord(c->knn_ev[which], st);
+}
+
 cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, int32_t k,
                        int32_t *idx, float *d2) {
     cudaStream_t st = c->stream;
@@ -751,8 +759,10 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         ka.out_d2 = d2;
         ka.err = err;
         ka.stats = &c->sc->knn_exact;
+        if ((e = knn_mark(c, 0, st))) return e;
         k_knn_tc<<<(unsigned)T, kTcThreads, smem_tc, st>>>(ka);
         if ((e = cudaGetLastError())) return e;
+        if ((e = knn_mark(c, 1, st))) return e;
         cudaFreeAsync(img, st);
         cudaFreeAsync(HG, st);
         cudaFreeAsync(amax, st);
@@ -764,9 +774,11 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
     if ((e = cudaFuncSetAttribute(k_knn_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)))
         return e;
+    if ((e = knn_mark(c, 0, st))) return e;
     k_knn_tile<<<(unsigned)((n + kQR - 1) / kQR), kKnnThreads, smem, st>>>(n, D, k, Xdev, nrm,
                                                                           idx, d2);
     if ((e = cudaGetLastError())) return e;
+    if ((e = knn_mark(c, 1, st))) return e;
     return cudaFreeAsync(nrm, st);
 }
 

@@ -312,6 +312,8 @@ void pxsne_destroy(pxsne_ctx *c) {
     dfree(c->rp); dfree(c->col); dfree(c->val); dfree(c->rowlen);
     dfree(c->knn_idx); dfree(c->knn_d2); dfree(c->beta);
     dfree(c->sc);
+    for (auto &ev : c->knn_ev)
+        if (ev) cudaEventDestroy(ev);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->side) cudaStreamDestroy(c->side);
@@ -793,6 +795,16 @@ int pxsne_get_knn_counters(pxsne_ctx *c, uint64_t *exact, uint64_t *inserted, in
     if (exact) *exact = h.knn_exact;
     if (inserted) *inserted = h.knn_insert;
     if (path) *path = c->knn_path;
+    return PXSNE_OK;
+}
+
+int pxsne_get_knn_time(pxsne_ctx *c, double *search_ms) {
+    if (!c || !search_ms) return PXSNE_E_ARG;
+    if (!c->knn_timed) return fail(c, PXSNE_E_STATE, "no neighbour search has run");
+    CK(c, cudaEventSynchronize(c->knn_ev[1]));
+    float ms = 0.f;
+    CK(c, cudaEventElapsedTime(&ms, c->knn_ev[0], c->knn_ev[1]));
+    *search_ms = ms;
     return PXSNE_OK;
 }
 

@@ -135,6 +135,8 @@ struct pxsne_ctx {
     float *beta = nullptr;
     int32_t knn_k = 0;
     int knn_path = -1;  // 1: tensor-core kNN, 0: FP32 CUDA-core kNN
+    cudaEvent_t knn_ev[2] = {nullptr, nullptr};  // around the last search kernel
+    bool knn_timed = false;
 
     // embedding state (data order)
     uint2 *z = nullptr;
