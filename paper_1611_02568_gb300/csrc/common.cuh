@@ -36,6 +36,7 @@ struct DevScalars {
     unsigned err;        // PXSNE_DEVERR_* flags
     unsigned ticket;     // last-block-done counter of the Z reduction
     unsigned ticket2;    // same for the KL reduction
+    unsigned pyr_ticket; // last-block-done counter of the pyramid's first pass
     u64 n_accept;        // accepted (point, cell) pairs of the last traversal
     u64 n_test;          // (point, cell) pairs tested by the last traversal
     u64 n_steps;         // warp-level (node, non-empty child) steps of the last traversal
@@ -48,8 +49,10 @@ struct DevScalars {
 // rec_offset(l) + m of two arrays:
 //   rec  float4 {c_hi_x, c_lo_x, c_hi_y, c_lo_y}: the centre of mass S_c / N_c in
 //        ulps, split at bit 16 (c_hi = floor(com) with the low 16 bits cleared,
-//        exact in float; c_lo = the rest, in [0, 65536)), so that a point's
-//        offset z - com is (z_hi - c_hi) + (z_lo - c_lo) with one rounding;
+//        exact in float; c_lo = the rest, in [0, 65536]; the centre's offset in
+//        its cell is one FP32 quotient, good to about 2^-23 of the cell width),
+//        so that a point's offset z - com is (z_hi - c_hi) + (z_lo - c_lo)
+//        with one rounding;
 //   recn float N_c (exact below 2^24).
 // rec_offset pads level 0 to four slots so that every group of four siblings
 // starts on a 16-byte boundary.

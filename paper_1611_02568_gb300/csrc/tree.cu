@@ -117,16 +117,37 @@ __global__ void k_snap_hist(int n, int L, int rescale, float theta,
     if (valid) rank[i] = base + (uint32_t)(lane - start);
 }
 
-// Centre-of-mass record of a cell (layout in common.cuh).
-__device__ __forceinline__ float4 make_record(uint32_t N, u64 Sx, u64 Sy) {
+// One axis of a centre-of-mass record: the centre base + S_off / N of a cell
+// whose lower corner is `base` (S_off = S - N base, the sum of the points'
+// offsets in the cell, exact), split at bit 16 as the layout in common.cuh
+// asks.  The offset is one FP32 quotient (relative error about 2^-23 of the
+// cell width, a fraction of an ulp at the leaves).
+__device__ __forceinline__ void record_axis(uint32_t N, u64 S, uint32_t base, int sh,
+                                            float &hi, float &lo) {
+    const u64 soff = S - (u64)N * base;
+    float c = (float)soff / (float)N;  // in [0, 2^sh]
+    c = fminf(c, 4294967040.0f);
+    uint32_t q = (uint32_t)c;
+    float fr = c - (float)q;
+    const uint32_t wmax = sh >= 32 ? 0xffffffffu : ((1u << sh) - 1u);
+    if (q > wmax) {  // rounding at the cell's far edge
+        q = wmax;
+        fr = 1.0f;
+    }
+    hi = (float)(base + (q & 0xffff0000u));
+    lo = (float)(q & 0xffffu) + fr;
+}
+
+// Centre-of-mass record of cell m of level l (layout in common.cuh).
+__device__ __forceinline__ float4 make_record(uint32_t N, u64 Sx, u64 Sy, int l, uint32_t m) {
     if (N == 0) return make_float4(0.f, 0.f, 0.f, 0.f);
-    const u64 qx = Sx / N, qy = Sy / N;
-    const uint32_t rx = (uint32_t)(Sx - qx * N), ry = (uint32_t)(Sy - qy * N);
-    const float fN = (float)N;
-    return make_float4((float)(uint32_t)(qx & 0xffff0000u),
-                       (float)(uint32_t)(qx & 0xffffu) + (float)rx / fN,
-                       (float)(uint32_t)(qy & 0xffff0000u),
-                       (float)(uint32_t)(qy & 0xffffu) + (float)ry / fN);
+    const int sh = 32 - l;
+    const uint32_t bx = l > 0 ? gather_bits16(m) << sh : 0u;
+    const uint32_t by = l > 0 ? gather_bits16(m >> 1) << sh : 0u;
+    float4 r;
+    record_axis(N, Sx, bx, sh, r.x, r.y);
+    record_axis(N, Sy, by, sh, r.z, r.w);
+    return r;
 }
 
 // Block-wide exclusive scan of one value per thread (nt threads, nt <= 1024).
@@ -184,10 +205,10 @@ __global__ void __launch_bounds__(1 << (2 * (K - 1)))
     const ulonglong2 y01 = reinterpret_cast<const ulonglong2 *>(in_sy)[cell0 >> 1];
     const ulonglong2 y23 = reinterpret_cast<const ulonglong2 *>(in_sy)[(cell0 >> 1) + 1];
     float4 *rl = rec + rec_offset(h) + cell0;
-    rl[0] = make_record(c4.x, x01.x, y01.x);
-    rl[1] = make_record(c4.y, x01.y, y01.y);
-    rl[2] = make_record(c4.z, x23.x, y23.x);
-    rl[3] = make_record(c4.w, x23.y, y23.y);
+    rl[0] = make_record(c4.x, x01.x, y01.x, h, (uint32_t)cell0);
+    rl[1] = make_record(c4.y, x01.y, y01.y, h, (uint32_t)cell0 + 1u);
+    rl[2] = make_record(c4.z, x23.x, y23.x, h, (uint32_t)cell0 + 2u);
+    rl[3] = make_record(c4.w, x23.y, y23.y, h, (uint32_t)cell0 + 3u);
     reinterpret_cast<float4 *>(recn + rec_offset(h))[cell0 >> 2] =
         make_float4((float)c4.x, (float)c4.y, (float)c4.z, (float)c4.w);
     uint32_t N = c4.x + c4.y + c4.z + c4.w;
@@ -209,7 +230,7 @@ __global__ void __launch_bounds__(1 << (2 * (K - 1)))
         const int cells = 1 << (2 * j);
         if (tid < cells) {
             if (j > 0 || top) {
-                rec[rec_offset(lvl) + idx] = make_record(N, X, Y);
+                rec[rec_offset(lvl) + idx] = make_record(N, X, Y, lvl, (uint32_t)idx);
                 recn[rec_offset(lvl) + idx] = (float)N;
             }
             if (j == 0) {
@@ -236,6 +257,197 @@ __global__ void __launch_bounds__(1 << (2 * (K - 1)))
         idx = b * (cells >> 2) + tid;
     }
     if (bump_t && b == 0 && tid == 0) sc->t += 1;
+}
+
+// The first pass with K = 5 levels over the leaves, by warp shuffles: a
+// thread owns 4 leaves (one level-(h-1) cell); lanes 4k..4k+3 make a level-(h-2)
+// cell, 16 lanes a level-(h-3) cell, two warps a level-(h-4) cell and the CTA
+// one level-(h-5) cell.  It writes the records of levels h .. h-4, the sums of
+// level h-5 and, per CTA, the exclusive scan of the leaf counts (local start of
+// each pixel in Morton order).  With fuse_top the last CTA to finish also does
+// the rest of the pyramid (pyr_top).
+__device__ __forceinline__ u64 shfl_xor_u64(u64 v, int o) {
+    return __shfl_xor_sync(0xffffffffu, v, o);
+}
+
+__device__ __forceinline__ void put_record(float4 *rec, float *recn, int l, uint32_t m,
+                                           uint32_t N, u64 X, u64 Y) {
+    rec[rec_offset(l) + m] = make_record(N, X, Y, l, m);
+    recn[rec_offset(l) + m] = (float)N;
+}
+
+// Levels h0-1 .. 0 from the sums of level h0 (4^h0 cells in c0/x0/y0, whose
+// records are written), by one CTA of 256 threads, ping-ponging through
+// c1/x1/y1; also blk_off = the exclusive scan of the level-h0 counts (each the
+// pixel total of one first-pass CTA).
+__device__ void pyr_top(int h0, uint32_t *c0, u64 *x0, u64 *y0, uint32_t *c1, u64 *x1, u64 *y1,
+                        float4 *rec, float *recn, uint32_t *blk_off, uint32_t *s_warp) {
+    const int tid = threadIdx.x;
+    const int nb = 1 << (2 * h0);
+    // blk_off: each thread scans a contiguous segment (16-byte loads when the
+    // segments are multiples of four)
+    const int seg = (nb + 255) / 256;
+    const int a = tid * seg, e = min(nb, a + seg);
+    uint32_t v = 0u;
+    if ((seg & 3) == 0) {
+        for (int i = a; i < e; i += 4) {
+            const uint4 q = __ldcg(reinterpret_cast<const uint4 *>(c0 + i));
+            v += q.x + q.y + q.z + q.w;
+        }
+    } else {
+        for (int i = a; i < e; i++) v += __ldcg(c0 + i);
+    }
+    uint32_t run = block_excl_scan(v, 256, s_warp);
+    if ((seg & 3) == 0) {
+        for (int i = a; i < e; i += 4) {
+            const uint4 q = __ldcg(reinterpret_cast<const uint4 *>(c0 + i));
+            uint4 o;
+            o.x = run;
+            o.y = o.x + q.x;
+            o.z = o.y + q.y;
+            o.w = o.z + q.z;
+            run = o.w + q.w;
+            *reinterpret_cast<uint4 *>(blk_off + i) = o;
+        }
+    } else {
+        for (int i = a; i < e; i++) {
+            const uint32_t ci = __ldcg(c0 + i);
+            blk_off[i] = run;
+            run += ci;
+        }
+    }
+    uint32_t *cc = c0, *cn = c1;
+    u64 *xc = x0, *xn = x1, *yc = y0, *yn = y1;
+    for (int l = h0;; l--) {
+        const int cells = 1 << (2 * l);
+        if (l < h0)
+            for (int c = tid; c < cells; c += 256)
+                put_record(rec, recn, l, (uint32_t)c, __ldcg(cc + c), __ldcg(xc + c),
+                           __ldcg(yc + c));
+        if (l == 0) break;
+        for (int p = tid; p < (cells >> 2); p += 256) {
+            const uint4 q4 = __ldcg(reinterpret_cast<const uint4 *>(cc) + p);
+            const ulonglong2 xa = __ldcg(reinterpret_cast<const ulonglong2 *>(xc) + 2 * p);
+            const ulonglong2 xb = __ldcg(reinterpret_cast<const ulonglong2 *>(xc) + 2 * p + 1);
+            const ulonglong2 ya = __ldcg(reinterpret_cast<const ulonglong2 *>(yc) + 2 * p);
+            const ulonglong2 yb = __ldcg(reinterpret_cast<const ulonglong2 *>(yc) + 2 * p + 1);
+            cn[p] = q4.x + q4.y + q4.z + q4.w;
+            xn[p] = xa.x + xa.y + xb.x + xb.y;
+            yn[p] = ya.x + ya.y + yb.x + yb.y;
+        }
+        __threadfence_block();
+        __syncthreads();
+        uint32_t *tc = cc;
+        cc = cn;
+        cn = tc;
+        u64 *tx = xc;
+        xc = xn;
+        xn = tx;
+        u64 *ty = yc;
+        yc = yn;
+        yn = ty;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+    k_pyr_bottom(int h, const uint32_t *__restrict__ in_cnt, const u64 *__restrict__ in_sx,
+                 const u64 *__restrict__ in_sy, float4 *__restrict__ rec, float *__restrict__ recn,
+                 uint32_t *out_cnt, u64 *out_sx, u64 *out_sy, uint32_t *scr_cnt, u64 *scr_sx,
+                 u64 *scr_sy, uint32_t *__restrict__ leaf_start, uint32_t *blk_off,
+                 DevScalars *sc, int bump_t) {
+    __shared__ uint32_t s_n[8];
+    __shared__ u64 s_x[8], s_y[8];
+    __shared__ uint32_t s_warp[32];
+    __shared__ bool s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t b = blockIdx.x;
+    const uint32_t cell0 = b * 1024u + 4u * (uint32_t)tid;
+    const uint4 c4 = reinterpret_cast<const uint4 *>(in_cnt)[cell0 >> 2];
+    const ulonglong2 x01 = reinterpret_cast<const ulonglong2 *>(in_sx)[cell0 >> 1];
+    const ulonglong2 x23 = reinterpret_cast<const ulonglong2 *>(in_sx)[(cell0 >> 1) + 1];
+    const ulonglong2 y01 = reinterpret_cast<const ulonglong2 *>(in_sy)[cell0 >> 1];
+    const ulonglong2 y23 = reinterpret_cast<const ulonglong2 *>(in_sy)[(cell0 >> 1) + 1];
+    float4 *rl = rec + rec_offset(h) + cell0;
+    rl[0] = make_record(c4.x, x01.x, y01.x, h, cell0);
+    rl[1] = make_record(c4.y, x01.y, y01.y, h, cell0 + 1u);
+    rl[2] = make_record(c4.z, x23.x, y23.x, h, cell0 + 2u);
+    rl[3] = make_record(c4.w, x23.y, y23.y, h, cell0 + 3u);
+    reinterpret_cast<float4 *>(recn + rec_offset(h))[cell0 >> 2] =
+        make_float4((float)c4.x, (float)c4.y, (float)c4.z, (float)c4.w);
+    uint32_t N = c4.x + c4.y + c4.z + c4.w;
+    u64 X = x01.x + x01.y + x23.x + x23.y;
+    u64 Y = y01.x + y01.y + y23.x + y23.y;
+    // inclusive warp scan of the level-(h-1) counts (for the pixel starts)
+    uint32_t inc = N;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    put_record(rec, recn, h - 1, b * 256u + (uint32_t)tid, N, X, Y);
+    // levels h-2 (4 lanes) and h-3 (16 lanes)
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+        N += __shfl_xor_sync(0xffffffffu, N, o);
+        X += shfl_xor_u64(X, o);
+        Y += shfl_xor_u64(Y, o);
+    }
+    if ((lane & 3) == 0) put_record(rec, recn, h - 2, b * 64u + (uint32_t)(tid >> 2), N, X, Y);
+#pragma unroll
+    for (int o = 4; o <= 8; o <<= 1) {
+        N += __shfl_xor_sync(0xffffffffu, N, o);
+        X += shfl_xor_u64(X, o);
+        Y += shfl_xor_u64(Y, o);
+    }
+    if ((lane & 15) == 0) put_record(rec, recn, h - 3, b * 16u + (uint32_t)(tid >> 4), N, X, Y);
+    N += __shfl_xor_sync(0xffffffffu, N, 16);
+    X += shfl_xor_u64(X, 16);
+    Y += shfl_xor_u64(Y, 16);
+    if (lane == 0) {
+        s_n[warp] = N;
+        s_x[warp] = X;
+        s_y[warp] = Y;
+    }
+    __syncthreads();
+    // pixel starts within the CTA
+    uint32_t before = 0u;
+    for (int w = 0; w < warp; w++) before += s_n[w];
+    const uint32_t e0 = before + inc - (c4.x + c4.y + c4.z + c4.w);
+    uint4 st;
+    st.x = e0;
+    st.y = e0 + c4.x;
+    st.z = st.y + c4.y;
+    st.w = st.z + c4.z;
+    reinterpret_cast<uint4 *>(leaf_start)[cell0 >> 2] = st;
+    // level h-4: pairs of warps; level h-5: the CTA
+    if (tid < 4)
+        put_record(rec, recn, h - 4, b * 4u + (uint32_t)tid, s_n[2 * tid] + s_n[2 * tid + 1],
+                   s_x[2 * tid] + s_x[2 * tid + 1], s_y[2 * tid] + s_y[2 * tid + 1]);
+    if (tid == 0) {
+        uint32_t n5 = 0u;
+        u64 x5 = 0ull, y5 = 0ull;
+        for (int w = 0; w < 8; w++) {
+            n5 += s_n[w];
+            x5 += s_x[w];
+            y5 += s_y[w];
+        }
+        out_cnt[b] = n5;
+        out_sx[b] = x5;
+        out_sy[b] = y5;
+        put_record(rec, recn, h - 5, b, n5, x5, y5);
+        // the last CTA to finish builds the top of the pyramid
+        __threadfence();
+        const unsigned tk = atomicAdd(&sc->pyr_ticket, 1u);
+        s_last = (tk == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    pyr_top(h - 5, out_cnt, out_sx, out_sy, scr_cnt, scr_sx, scr_sy, rec, recn, blk_off, s_warp);
+    if (tid == 0) {
+        sc->pyr_ticket = 0u;
+        if (bump_t) sc->t += 1;
+    }
 }
 
 // Exclusive scan of m values in one CTA of 1024 threads.
@@ -315,33 +527,42 @@ cudaError_t launch_pyramid(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
     const int n = (int)c->n;
     cudaError_t e;
     if (marks && (e = cudaEventRecord(marks[KG_PYRAMID], st))) return e;
-    // bottom-up passes
-    int h = L;
     const int K1 = L < kPyrK ? L : kPyrK;
-    int cur = 0;
-    {
-        const int64_t blocks = leaves >> (2 * K1);
-        const int top = (h - K1 == 0);
-        if ((e = pyr_pass(K1, blocks, st, h, top, c->leaf_cnt, c->leaf_sx, c->leaf_sy, c->rec,
-                          c->recn, c->lvl_cnt[0], c->lvl_sx[0], c->lvl_sy[0], c->leaf_start,
-                          c->sc, (rescale && top) ? 1 : 0)))
-            return e;
-        h -= K1;
-    }
-    // traversal order: scan of the per-CTA pixel totals of the first pass
-    k_scan1<<<1, 1024, 0, st>>>(c->lvl_cnt[0], c->blk_off, int64_t(1) << (2 * h));
-    if ((e = cudaGetLastError())) return e;
-    while (h > 0) {
-        const int K = h < kPyrK ? h : kPyrK;
-        const int64_t blocks = (int64_t(1) << (2 * h)) >> (2 * K);
-        const int top = (h - K == 0);
-        if ((e = pyr_pass(K, blocks, st, h, top, c->lvl_cnt[cur], c->lvl_sx[cur],
-                          c->lvl_sy[cur], c->rec, c->recn, c->lvl_cnt[cur ^ 1],
-                          c->lvl_sx[cur ^ 1], c->lvl_sy[cur ^ 1], nullptr, c->sc,
-                          (rescale && top) ? 1 : 0)))
-            return e;
-        cur ^= 1;
-        h -= K;
+    if (L >= kPyrK && L - kPyrK <= 7) {
+        // one pass: shuffle-reduced bottom levels, the top by the last CTA
+        k_pyr_bottom<<<(unsigned)(leaves >> 10), 256, 0, st>>>(
+            L, c->leaf_cnt, c->leaf_sx, c->leaf_sy, c->rec, c->recn, c->lvl_cnt[0],
+            c->lvl_sx[0], c->lvl_sy[0], c->lvl_cnt[1], c->lvl_sx[1], c->lvl_sy[1],
+            c->leaf_start, c->blk_off, c->sc, rescale ? 1 : 0);
+        if ((e = cudaGetLastError())) return e;
+    } else {
+        // bottom-up passes
+        int h = L;
+        int cur = 0;
+        {
+            const int64_t blocks = leaves >> (2 * K1);
+            const int top = (h - K1 == 0);
+            if ((e = pyr_pass(K1, blocks, st, h, top, c->leaf_cnt, c->leaf_sx, c->leaf_sy,
+                              c->rec, c->recn, c->lvl_cnt[0], c->lvl_sx[0], c->lvl_sy[0],
+                              c->leaf_start, c->sc, (rescale && top) ? 1 : 0)))
+                return e;
+            h -= K1;
+        }
+        // traversal order: scan of the per-CTA pixel totals of the first pass
+        k_scan1<<<1, 1024, 0, st>>>(c->lvl_cnt[0], c->blk_off, int64_t(1) << (2 * h));
+        if ((e = cudaGetLastError())) return e;
+        while (h > 0) {
+            const int K = h < kPyrK ? h : kPyrK;
+            const int64_t blocks = (int64_t(1) << (2 * h)) >> (2 * K);
+            const int top = (h - K == 0);
+            if ((e = pyr_pass(K, blocks, st, h, top, c->lvl_cnt[cur], c->lvl_sx[cur],
+                              c->lvl_sy[cur], c->rec, c->recn, c->lvl_cnt[cur ^ 1],
+                              c->lvl_sx[cur ^ 1], c->lvl_sy[cur ^ 1], nullptr, c->sc,
+                              (rescale && top) ? 1 : 0)))
+                return e;
+            cur ^= 1;
+            h -= K;
+        }
     }
     if (marks && (e = cudaEventRecord(marks[KG_PERM], st))) return e;
     k_perm_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, L, K1, c->z, c->rank, c->leaf_start,

@@ -79,7 +79,7 @@ def test_init_maps_y0_bit_exact(px):
         check_tree(ctx, z, 10)
 
 
-@pytest.mark.parametrize("L", [1, 4, 5, 6, 9, 11])
+@pytest.mark.parametrize("L", [1, 4, 5, 6, 9, 11, 12, 13])
 def test_tree_bit_exact(px, gauss, L):
     X, P, Y0, st = gauss
     rng = np.random.default_rng(L)
