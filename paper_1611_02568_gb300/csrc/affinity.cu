@@ -13,11 +13,13 @@
 //   k_perplexity   per-row bisection on beta so that the entropy of
 //                  p_{j|i} ~ exp(-beta d2) is ln(perplexity), one warp per row
 //   symmetrize     p_ij = (p_{j|i} + p_{i|j}) / 2n on the union pattern, CSR
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include <cuda_fp16.h>
 
@@ -333,6 +335,75 @@ __device__ __forceinline__ float thread_exact_d2(const float *__restrict__ X, in
     return s;
 }
 
+// ---- locality order for the search (rows grouped by their nearest pivot)
+constexpr int kCells = 128;  // pivots (cells) of the locality order
+
+// cell[i] = the pivot nearest to row i (squared Euclidean, |p|^2 - 2 x.p in
+// FP32), pivots staged in shared memory; DP = D rounded up to 64.
+template <int DP>
+__global__ void __launch_bounds__(256)
+    k_assign_cells(int64_t n, int D, int m, const float *__restrict__ X,
+                   const float *__restrict__ piv, const float *__restrict__ pn,
+                   uint32_t *__restrict__ cell) {
+    extern __shared__ float s_piv[];  // m x DP
+    for (int q = threadIdx.x; q < m * DP; q += blockDim.x) {
+        const int pi = q / DP, d = q % DP;
+        s_piv[q] = d < D ? piv[(int64_t)pi * D + d] : 0.f;
+    }
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float xr[DP];
+#pragma unroll
+    for (int d = 0; d < DP; d++) xr[d] = d < D ? X[i * D + d] : 0.f;
+    float best = INFINITY;
+    uint32_t bi = 0u;
+    for (int pi = 0; pi < m; pi++) {
+        const float4 *pr = reinterpret_cast<const float4 *>(s_piv + pi * DP);
+        float dot = 0.f;
+#pragma unroll
+        for (int d4 = 0; d4 < DP / 4; d4++) {
+            const float4 pv = pr[d4];
+            dot = fmaf(xr[4 * d4], pv.x, dot);
+            dot = fmaf(xr[4 * d4 + 1], pv.y, dot);
+            dot = fmaf(xr[4 * d4 + 2], pv.z, dot);
+            dot = fmaf(xr[4 * d4 + 3], pv.w, dot);
+        }
+        const float v = fmaf(-2.0f, dot, pn[pi]);
+        if (v < best) {
+            best = v;
+            bi = (uint32_t)pi;
+        }
+    }
+    cell[i] = bi;
+}
+
+__global__ void k_cell_count(int64_t n, const uint32_t *__restrict__ cell, uint32_t *cnt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[cell[i]], 1u);
+}
+
+// order[r]: the row at sorted position r (rows of one cell contiguous, cells
+// in chain order; the order inside a cell is immaterial to the result)
+__global__ void k_cell_scatter(int64_t n, const uint32_t *__restrict__ cell, uint32_t *cursor,
+                               uint32_t *__restrict__ order) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) order[atomicAdd(&cursor[cell[i]], 1u)] = (uint32_t)i;
+}
+
+// Xs[r] = X[order[r]], ns[r] = nrm[order[r]]
+__global__ void k_gather_rows(int64_t n, int D, const uint32_t *__restrict__ order,
+                              const float *__restrict__ X, const float *__restrict__ nrm,
+                              float *__restrict__ Xs, float *__restrict__ ns) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n * D) return;
+    const int64_t r = q / D;
+    const int d = (int)(q % D);
+    const uint32_t i = order[r];
+    Xs[q] = X[(int64_t)i * D + d];
+    if (d == 0) ns[r] = nrm[i];
+}
+
 // A neighbour-list entry; (d, j) orders by distance, then by index.
 struct __align__(8) KnnEntry {
     float d;
@@ -350,11 +421,20 @@ struct KnnTcArgs {
     const uint8_t *img;   // FP16 tile images
     const float *nrm;     // |x|^2
     const float *HG;      // per tile: h_j then |c_j|
+    const uint32_t *order;  // sorted position -> row of X (the locality order)
     int32_t *out_idx;
     float *out_d2;
     unsigned *err;
     u64 *stats;
 };
+
+// The i-th candidate tile a CTA visits: its own, then alternately the next
+// and the previous ones (mod T), so that the rows nearby in the locality order
+// come first.
+__device__ __forceinline__ int64_t knn_tile_at(int64_t qt, int64_t i, int64_t T) {
+    const int64_t off = (i & 1) ? (i + 1) / 2 : -(i / 2);
+    return ((qt + off) % T + T) % T;
+}
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
     extern __shared__ uint8_t smem_raw[];
@@ -413,7 +493,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             tc::bulk_g2s(sA, a.img + qt * tile_bytes, tile_bytes, &bar_a);
             int64_t i = 0;
             for (; i < T && !s_abort; i++) {
-                const int64_t t = i;
+                const int64_t t = knn_tile_at(qt, i, T);
                 const int s = (int)(i % kTcStages), b = (int)(i % kTcAcc);
                 if (i >= kTcStages &&
                     !tc::mbar_wait_sleep(&bar_se[s], (uint32_t)((i / kTcStages - 1) & 1), kTcPolls, kTcSleepNs)) {
@@ -506,7 +586,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             }
             __syncwarp();
             for (uint32_t q = head; q != kNil; q = wp[q]) {
-                const int32_t cand = (int32_t)(wq[q] & 0xffffffu);
+                const int32_t cand = (int32_t)__ldg(a.order + (wq[q] & 0xffffffu));
                 const float d = wd[q];
                 n_exact++;
                 if (!(d < tau || (d == tau && cand < jlast))) continue;
@@ -540,7 +620,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             qn = 0u;
         };
         for (int64_t i = 0; i < T; i++) {
-            const int64_t t = i;
+            const int64_t t = knn_tile_at(qt, i, T);
             const int b = (int)(i % kTcAcc);
             const uint32_t par = (uint32_t)((i / kTcAcc) & 1);
             // warp-uniform: every lane takes the same path into the aligned
@@ -671,8 +751,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
         const int64_t row = q0 + r;
         if (row < n) {
             const KnnEntry v = lst[r * ks + j];
-            a.out_idx[row * k + j] = v.j;
-            a.out_d2[row * k + j] = v.d;
+            const int64_t orow = a.order[row];
+            a.out_idx[orow * k + j] = v.j;
+            a.out_d2[orow * k + j] = v.d;
         }
     }
 }
@@ -728,6 +809,95 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         const float u = 1.0f / 2048.0f;
         const float kappa = 1.25f * 2.0f * (2.0f * u + u * u + (float)Dp * 5.9604645e-8f * 1.01f);
         const float eps_abs = (float)(2 * D + 8) * 5.9604645e-8f;
+        // locality order: rows grouped by their nearest of m pivots (rows
+        // i n / m), the pivots chained greedily by nearest neighbour on the host
+        const int m = (int)std::min<int64_t>(kCells, std::max<int64_t>(1, n / 256));
+        std::vector<float> hp((size_t)m * D), hq((size_t)m * D), hn((size_t)m);
+        for (int q = 0; q < m; q++)
+            if ((e = cudaMemcpyAsync(hp.data() + (size_t)q * D, Xdev + (q * n / m) * D,
+                                     (size_t)D * sizeof(float), cudaMemcpyDeviceToHost, st)))
+                return e;
+        if ((e = cudaStreamSynchronize(st))) return e;
+        {
+            std::vector<char> used((size_t)m, 0);
+            int cur = 0;
+            for (int q = 0; q < m; q++) {
+                used[(size_t)cur] = 1;
+                double pn2 = 0.0;
+                for (int d = 0; d < D; d++) {
+                    const float v = hp[(size_t)cur * D + d];
+                    hq[(size_t)q * D + d] = v;
+                    pn2 += (double)v * v;
+                }
+                hn[(size_t)q] = (float)pn2;
+                int nxt = -1;
+                double bd = 0.0;
+                for (int r = 0; r < m; r++) {
+                    if (used[(size_t)r]) continue;
+                    double dd = 0.0;
+                    for (int d = 0; d < D; d++) {
+                        const double t = (double)hp[(size_t)cur * D + d] - hp[(size_t)r * D + d];
+                        dd += t * t;
+                    }
+                    if (nxt < 0 || dd < bd) {
+                        nxt = r;
+                        bd = dd;
+                    }
+                }
+                if (nxt < 0) break;
+                cur = nxt;
+            }
+        }
+        float *piv = nullptr, *Xs = nullptr, *ns = nullptr;
+        uint32_t *cell = nullptr, *order = nullptr, *ccnt = nullptr;
+        if ((e = cudaMallocAsync(&piv, (size_t)m * (D + 1) * sizeof(float), st))) return e;
+        if ((e = cudaMallocAsync(&cell, (size_t)n * sizeof(uint32_t), st))) return e;
+        if ((e = cudaMallocAsync(&order, (size_t)n * sizeof(uint32_t), st))) return e;
+        if ((e = cudaMallocAsync(&ccnt, (size_t)m * sizeof(uint32_t), st))) return e;
+        if ((e = cudaMallocAsync(&Xs, (size_t)n * D * sizeof(float), st))) return e;
+        if ((e = cudaMallocAsync(&ns, (size_t)n * sizeof(float), st))) return e;
+        float *pn = piv + (size_t)m * D;
+        if ((e = cudaMemcpyAsync(piv, hq.data(), (size_t)m * D * sizeof(float),
+                                 cudaMemcpyHostToDevice, st)))
+            return e;
+        if ((e = cudaMemcpyAsync(pn, hn.data(), (size_t)m * sizeof(float), cudaMemcpyHostToDevice,
+                                 st)))
+            return e;
+        const size_t smem_a = (size_t)m * Dp * sizeof(float);
+        const unsigned ablocks = (unsigned)((n + 255) / 256);
+        if (Dp == 64) {
+            if ((e = cudaFuncSetAttribute(k_assign_cells<64>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a)))
+                return e;
+            k_assign_cells<64><<<ablocks, 256, smem_a, st>>>(n, D, m, Xdev, piv, pn, cell);
+        } else {
+            if ((e = cudaFuncSetAttribute(k_assign_cells<128>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a)))
+                return e;
+            k_assign_cells<128><<<ablocks, 256, smem_a, st>>>(n, D, m, Xdev, piv, pn, cell);
+        }
+        if ((e = cudaMemsetAsync(ccnt, 0, (size_t)m * sizeof(uint32_t), st))) return e;
+        k_cell_count<<<ablocks, 256, 0, st>>>(n, cell, ccnt);
+        std::vector<uint32_t> hc((size_t)m);
+        if ((e = cudaMemcpyAsync(hc.data(), ccnt, (size_t)m * sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, st)))
+            return e;
+        if ((e = cudaStreamSynchronize(st))) return e;
+        uint32_t run = 0u;
+        for (int q = 0; q < m; q++) {
+            const uint32_t v = hc[(size_t)q];
+            hc[(size_t)q] = run;
+            run += v;
+        }
+        if ((e = cudaMemcpyAsync(ccnt, hc.data(), (size_t)m * sizeof(uint32_t),
+                                 cudaMemcpyHostToDevice, st)))
+            return e;
+        k_cell_scatter<<<ablocks, 256, 0, st>>>(n, cell, ccnt, order);
+        k_gather_rows<<<(unsigned)((n * D + 255) / 256), 256, 0, st>>>(n, D, order, Xdev, nrm, Xs,
+                                                                       ns);
+        if ((e = cudaGetLastError())) return e;
+        // the search runs on the ordered rows
+        const float *Xo = Xs;
         const int64_t T = (n + kTcCols - 1) / kTcCols;
         const size_t img_bytes = (size_t)T * kTcRows * Dp * 2;
         uint8_t *img = nullptr;
@@ -735,9 +905,9 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         if ((e = cudaMallocAsync(&img, img_bytes, st))) return e;
         if ((e = cudaMallocAsync(&HG, (size_t)T * 2 * kTcCols * sizeof(float), st))) return e;
         const int64_t nchunks = T * kTcRows * (Dp / 8);
-        k_to_half_img<<<(unsigned)((nchunks + 255) / 256), 256, 0, st>>>(n, D, Dp, T, scale, Xdev,
+        k_to_half_img<<<(unsigned)((nchunks + 255) / 256), 256, 0, st>>>(n, D, Dp, T, scale, Xo,
                                                                           img);
-        k_tile_norms<<<(unsigned)((T * kTcCols + 255) / 256), 256, 0, st>>>(n, T, eps_abs, nrm, HG);
+        k_tile_norms<<<(unsigned)((T * kTcCols + 255) / 256), 256, 0, st>>>(n, T, eps_abs, ns, HG);
         if ((e = cudaGetLastError())) return e;
         if ((e = cudaFuncSetAttribute(k_knn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem_tc)))
@@ -751,10 +921,11 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         ka.inv_s2 = inv_s2;
         ka.kappa = kappa;
         ka.eps_abs = eps_abs;
-        ka.X = Xdev;
+        ka.X = Xo;
         ka.img = img;
-        ka.nrm = nrm;
+        ka.nrm = ns;
         ka.HG = HG;
+        ka.order = order;
         ka.out_idx = idx;
         ka.out_d2 = d2;
         ka.err = err;
@@ -766,6 +937,12 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         cudaFreeAsync(img, st);
         cudaFreeAsync(HG, st);
         cudaFreeAsync(amax, st);
+        cudaFreeAsync(piv, st);
+        cudaFreeAsync(cell, st);
+        cudaFreeAsync(order, st);
+        cudaFreeAsync(ccnt, st);
+        cudaFreeAsync(Xs, st);
+        cudaFreeAsync(ns, st);
         return cudaFreeAsync(nrm, st);
     }
     c->knn_path = 0;
