@@ -336,7 +336,8 @@ __device__ __forceinline__ float thread_exact_d2(const float *__restrict__ X, in
 }
 
 // ---- locality order for the search (rows grouped by their nearest pivot)
-constexpr int kCells = 128;  // pivots (cells) of the locality order
+constexpr int kCells = 512;     // pivots (cells) of the locality order
+constexpr int kPivChunk = 128;  // pivots staged in shared memory at a time
 
 // cell[i] = the pivot nearest to row i (squared Euclidean, |p|^2 - 2 x.p in
 // FP32), pivots staged in shared memory; DP = D rounded up to 64.
@@ -345,37 +346,40 @@ __global__ void __launch_bounds__(256)
     k_assign_cells(int64_t n, int D, int m, const float *__restrict__ X,
                    const float *__restrict__ piv, const float *__restrict__ pn,
                    uint32_t *__restrict__ cell) {
-    extern __shared__ float s_piv[];  // m x DP
-    for (int q = threadIdx.x; q < m * DP; q += blockDim.x) {
-        const int pi = q / DP, d = q % DP;
-        s_piv[q] = d < D ? piv[(int64_t)pi * D + d] : 0.f;
-    }
-    __syncthreads();
+    extern __shared__ float s_piv[];  // kPivChunk x DP
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
     float xr[DP];
 #pragma unroll
-    for (int d = 0; d < DP; d++) xr[d] = d < D ? X[i * D + d] : 0.f;
+    for (int d = 0; d < DP; d++) xr[d] = (i < n && d < D) ? X[i * D + d] : 0.f;
     float best = INFINITY;
     uint32_t bi = 0u;
-    for (int pi = 0; pi < m; pi++) {
-        const float4 *pr = reinterpret_cast<const float4 *>(s_piv + pi * DP);
-        float dot = 0.f;
-#pragma unroll
-        for (int d4 = 0; d4 < DP / 4; d4++) {
-            const float4 pv = pr[d4];
-            dot = fmaf(xr[4 * d4], pv.x, dot);
-            dot = fmaf(xr[4 * d4 + 1], pv.y, dot);
-            dot = fmaf(xr[4 * d4 + 2], pv.z, dot);
-            dot = fmaf(xr[4 * d4 + 3], pv.w, dot);
+    for (int p0 = 0; p0 < m; p0 += kPivChunk) {
+        const int pc = min(kPivChunk, m - p0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < pc * DP; q += blockDim.x) {
+            const int pi = q / DP, d = q % DP;
+            s_piv[q] = d < D ? piv[(int64_t)(p0 + pi) * D + d] : 0.f;
         }
-        const float v = fmaf(-2.0f, dot, pn[pi]);
-        if (v < best) {
-            best = v;
-            bi = (uint32_t)pi;
+        __syncthreads();
+        for (int pi = 0; pi < pc; pi++) {
+            const float4 *pr = reinterpret_cast<const float4 *>(s_piv + pi * DP);
+            float dot = 0.f;
+#pragma unroll
+            for (int d4 = 0; d4 < DP / 4; d4++) {
+                const float4 pv = pr[d4];
+                dot = fmaf(xr[4 * d4], pv.x, dot);
+                dot = fmaf(xr[4 * d4 + 1], pv.y, dot);
+                dot = fmaf(xr[4 * d4 + 2], pv.z, dot);
+                dot = fmaf(xr[4 * d4 + 3], pv.w, dot);
+            }
+            const float v = fmaf(-2.0f, dot, pn[p0 + pi]);
+            if (v < best) {
+                best = v;
+                bi = (uint32_t)(p0 + pi);
+            }
         }
     }
-    cell[i] = bi;
+    if (i < n) cell[i] = bi;
 }
 
 __global__ void k_cell_count(int64_t n, const uint32_t *__restrict__ cell, uint32_t *cnt) {
@@ -863,7 +867,7 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         if ((e = cudaMemcpyAsync(pn, hn.data(), (size_t)m * sizeof(float), cudaMemcpyHostToDevice,
                                  st)))
             return e;
-        const size_t smem_a = (size_t)m * Dp * sizeof(float);
+        const size_t smem_a = (size_t)std::min(m, kPivChunk) * Dp * sizeof(float);
         const unsigned ablocks = (unsigned)((n + 255) / 256);
         if (Dp == 64) {
             if ((e = cudaFuncSetAttribute(k_assign_cells<64>,
