@@ -1139,56 +1139,173 @@ __global__ void k_fill(int64_t n, int k, const int32_t *__restrict__ idx,
     tval[tptr[j] + slot] = p;
 }
 
-// Sort each temporary row by (col, position) (rank sort, one warp per row),
-// then merge equal columns; count = number of distinct columns.  With
-// write == 1 the merged row goes to (col, val / 2n) at rp[i].
+// Sort each temporary row by (col, position) (rank sort, one warp per row,
+// the row's columns staged in shared memory when it has at most kSmRow
+// entries), then merge equal columns (a column appears at most twice: once
+// from the row's own list, once from the other row's); count = number of
+// distinct columns.  With write == 1 the merged row goes to (col, val / 2n) at
+// rp[i], padded with (i, 0) to rp[i + 1].
+constexpr int kSmRow = 1024;
 __global__ void __launch_bounds__(256)
     k_sort_merge(int64_t n, int write, const int64_t *__restrict__ tptr,
                  const int32_t *__restrict__ tcol, const float *__restrict__ tval,
                  int32_t *__restrict__ scol, float *__restrict__ sval,
                  uint32_t *__restrict__ cnt, const int64_t *__restrict__ rp,
                  int32_t *__restrict__ col, float *__restrict__ val) {
+    __shared__ int32_t s_c[8][kSmRow];
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) & 7;
     if (row >= n) return;
     const int64_t a = tptr[row], b = tptr[row + 1];
     const int len = (int)(b - a);
     if (!write) {
-        for (int e = lane; e < len; e += 32) {
-            const int32_t ce = tcol[a + e];
-            int r = 0;
-            for (int f = 0; f < len; f++) {
-                const int32_t cf = tcol[a + f];
-                r += (cf < ce) || (cf == ce && f < e);
+        if (len <= kSmRow) {
+            // columns in shared memory, padded to a multiple of 4 with a value
+            // above every column; each pass ranks up to 8 elements per lane
+            // against all columns, read 16 bytes at a time
+            int32_t *sc = s_c[w];
+            const int len4 = (len + 3) & ~3;
+            for (int e = lane; e < len4; e += 32) sc[e] = e < len ? tcol[a + e] : 0x7fffffff;
+            __syncwarp();
+            const int4 *sc4 = reinterpret_cast<const int4 *>(sc);
+            for (int e0 = 0; e0 < len; e0 += 256) {
+                int32_t ce[8];
+                int r[8];
+#pragma unroll
+                for (int m = 0; m < 8; m++) {
+                    const int e = e0 + 32 * m + lane;
+                    ce[m] = e < len ? sc[e] : 0x7fffffff;
+                    r[m] = 0;
+                }
+                for (int f4 = 0; f4 < (len4 >> 2); f4++) {
+                    const int4 c4 = sc4[f4];
+                    const int f = 4 * f4;
+#pragma unroll
+                    for (int m = 0; m < 8; m++) {
+                        const int e = e0 + 32 * m + lane;
+                        r[m] += (c4.x < ce[m]) || (c4.x == ce[m] && f < e);
+                        r[m] += (c4.y < ce[m]) || (c4.y == ce[m] && f + 1 < e);
+                        r[m] += (c4.z < ce[m]) || (c4.z == ce[m] && f + 2 < e);
+                        r[m] += (c4.w < ce[m]) || (c4.w == ce[m] && f + 3 < e);
+                    }
+                }
+#pragma unroll
+                for (int m = 0; m < 8; m++) {
+                    const int e = e0 + 32 * m + lane;
+                    if (e < len) {
+                        scol[a + r[m]] = ce[m];
+                        sval[a + r[m]] = tval[a + e];
+                    }
+                }
             }
-            scol[a + r] = ce;
-            sval[a + r] = tval[a + e];
+        } else {
+            return;  // a long row: k_sort_long
         }
         __syncwarp();
-        if (lane == 0) {
-            uint32_t u = 0;
-            for (int e = 0; e < len; e++) u += (e == 0 || scol[a + e] != scol[a + e - 1]);
-            cnt[row] = u;
+        uint32_t u = 0;
+        for (int e0 = 0; e0 < len; e0 += 32) {
+            const int e = e0 + lane;
+            const bool head = e < len && (e == 0 || scol[a + e] != scol[a + e - 1]);
+            u += (uint32_t)__popc(__ballot_sync(0xffffffffu, head));
         }
-    } else if (lane == 0) {
+        if (lane == 0) cnt[row] = u;
+    } else {
         const float inv2n = (float)(0.5 / (double)n);
-        int64_t o = rp[row] - 1;
-        for (int e = 0; e < len; e++) {
-            const int32_t ce = scol[a + e];
-            const float ve = sval[a + e];
-            if (e == 0 || ce != scol[a + e - 1]) {
-                o++;
-                col[o] = ce;
-                val[o] = ve;
-            } else {
-                val[o] += ve;
+        const int64_t o0 = rp[row];
+        uint32_t done = 0;  // distinct columns written so far
+        for (int e0 = 0; e0 < len; e0 += 32) {
+            const int e = e0 + lane;
+            int32_t ce = 0;
+            bool head = false;
+            if (e < len) {
+                ce = scol[a + e];
+                head = (e == 0 || ce != scol[a + e - 1]);
             }
+            const unsigned hm = __ballot_sync(0xffffffffu, head);
+            if (head) {
+                float v = sval[a + e];
+                if (e + 1 < len && scol[a + e + 1] == ce) v += sval[a + e + 1];
+                const int64_t o = o0 + done + __popc(hm & ((1u << lane) - 1u));
+                col[o] = ce;
+                val[o] = v * inv2n;
+            }
+            done += (uint32_t)__popc(hm);
         }
-        for (int64_t q = rp[row]; q <= o; q++) val[q] *= inv2n;
-        for (int64_t q = o + 1; q < rp[row + 1]; q++) {  // padding to a multiple of 4
+        for (int64_t q = o0 + done + lane; q < rp[row + 1]; q += 32) {  // padding
             col[q] = (int32_t)row;
             val[q] = 0.f;
         }
+    }
+}
+
+// Rows longer than kSmRow (the hubs of the kNN graph, with thousands of
+// incoming entries): one CTA per row sorts the keys (col << 32 | position) by a
+// bitonic network in global scratch padded to a power of two, then writes the
+// sorted row and its count of distinct columns.
+__global__ void k_long_rows(int64_t n, const int64_t *__restrict__ tptr, uint32_t *list,
+                            uint32_t *nlong, uint32_t *plen) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t len = tptr[i + 1] - tptr[i];
+    if (len > kSmRow) {
+        const uint32_t q = atomicAdd(nlong, 1u);
+        uint32_t p2 = 1u;
+        while (p2 < (uint64_t)len) p2 <<= 1;
+        list[q] = (uint32_t)i;
+        plen[q] = p2;
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+    k_sort_long(const uint32_t *__restrict__ list, const uint32_t *__restrict__ plen,
+                const int64_t *__restrict__ soff, const int64_t *__restrict__ tptr,
+                const int32_t *__restrict__ tcol, const float *__restrict__ tval,
+                unsigned long long *scratch, int32_t *__restrict__ scol,
+                float *__restrict__ sval, uint32_t *__restrict__ cnt) {
+    __shared__ uint32_t s_w[32];
+    const uint32_t row = list[blockIdx.x];
+    const int64_t a = tptr[row];
+    const int len = (int)(tptr[row + 1] - a);
+    const int P = (int)plen[blockIdx.x];
+    unsigned long long *key = scratch + soff[blockIdx.x];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < P; i += blockDim.x)
+        key[i] = i < len ? (((unsigned long long)(uint32_t)tcol[a + i]) << 32) | (uint32_t)i
+                         : ~0ull;
+    __syncthreads();
+    for (int k2 = 2; k2 <= P; k2 <<= 1) {
+        for (int j = k2 >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < P; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const unsigned long long x = key[i], y = key[l];
+                    const bool asc = (i & k2) == 0;
+                    if ((x > y) == asc) {
+                        key[i] = y;
+                        key[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < len; i += blockDim.x) {
+        const unsigned long long u = key[i];
+        scol[a + i] = (int32_t)(u >> 32);
+        sval[a + i] = tval[a + (uint32_t)(u & 0xffffffffull)];
+    }
+    __syncthreads();
+    uint32_t u = 0u;
+    for (int i = tid; i < len; i += blockDim.x)
+        u += (i == 0 || scol[a + i] != scol[a + i - 1]) ? 1u : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+    if ((tid & 31) == 0) s_w[tid >> 5] = u;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t t = 0u;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_w[w];
+        cnt[row] = t;
     }
 }
 
@@ -1242,6 +1359,44 @@ cudaError_t build_symmetric_csr(pxsne_ctx *c, const int32_t *idx, const float *p
     k_sort_merge<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(
         n, 0, tptr, tcol, tval, scol, sval, ucnt, nullptr, nullptr, nullptr);
     TRY(cudaGetLastError());
+    {
+        // long rows
+        uint32_t *list = nullptr, *nlong = nullptr, *plen = nullptr;
+        TRY(cudaMallocAsync(&list, (size_t)n * sizeof(uint32_t), st));
+        TRY(cudaMallocAsync(&plen, (size_t)n * sizeof(uint32_t), st));
+        TRY(cudaMallocAsync(&nlong, sizeof(uint32_t), st));
+        TRY(cudaMemsetAsync(nlong, 0, sizeof(uint32_t), st));
+        k_long_rows<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, tptr, list, nlong, plen);
+        TRY(cudaGetLastError());
+        uint32_t hl = 0;
+        TRY(cudaMemcpyAsync(&hl, nlong, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        if (hl > 0) {
+            std::vector<uint32_t> hp(hl);
+            TRY(cudaMemcpyAsync(hp.data(), plen, hl * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                st));
+            TRY(cudaStreamSynchronize(st));
+            std::vector<int64_t> ho(hl);
+            int64_t tot = 0;
+            for (uint32_t q = 0; q < hl; q++) {
+                ho[q] = tot;
+                tot += hp[q];
+            }
+            int64_t *soff = nullptr;
+            unsigned long long *scr = nullptr;
+            TRY(cudaMallocAsync(&soff, hl * sizeof(int64_t), st));
+            TRY(cudaMallocAsync(&scr, (size_t)tot * sizeof(unsigned long long), st));
+            TRY(cudaMemcpyAsync(soff, ho.data(), hl * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+            k_sort_long<<<hl, 1024, 0, st>>>(list, plen, soff, tptr, tcol, tval, scr, scol, sval,
+                                             ucnt);
+            TRY(cudaGetLastError());
+            cudaFreeAsync(soff, st);
+            cudaFreeAsync(scr, st);
+        }
+        cudaFreeAsync(list, st);
+        cudaFreeAsync(plen, st);
+        cudaFreeAsync(nlong, st);
+    }
     if (c->rp) { cudaFreeAsync(c->rp, st); c->rp = nullptr; }
     if (c->col) { cudaFreeAsync(c->col, st); c->col = nullptr; }
     if (c->val) { cudaFreeAsync(c->val, st); c->val = nullptr; }

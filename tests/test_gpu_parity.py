@@ -208,6 +208,26 @@ def test_affinities_match_oracle(px, knn_path):
     assert abs(val.astype(np.float64).sum() - 1.0) < 1e-5
 
 
+def test_affinities_with_hub_rows(px):
+    """Rows of the symmetric P longer than a warp's staging buffer (1,024
+    entries): points spread over a shell (radii 8 to 12) around two central
+    points, which are in nearly every other point's neighbour list."""
+    rng = np.random.default_rng(5)
+    n, D, k, u = 2500, 50, 90, 30.0
+    X = rng.standard_normal((n, D))
+    X *= rng.uniform(8.0, 12.0, (n, 1)) / np.linalg.norm(X, axis=1, keepdims=True)
+    X = X.astype(np.float32)
+    X[0] = 0.0
+    X[1] = 0.05
+    P, idx_o, d2_o, bad = oracle.affinities(X, u, k)
+    assert np.diff(P.row_ptr)[:2].min() > 1024
+    with make_ctx(px, L=9, k=k, perplexity=u) as ctx:
+        ctx.affinities(X)
+        rp, col, val = ctx.get_P()
+    assert np.array_equal(rp, P.row_ptr) and np.array_equal(col, P.col)
+    np.testing.assert_allclose(val, P.val, rtol=2e-3, atol=1e-9)
+
+
 def test_knn_d128_sampled_rows(px, knn_path):
     """The bench's data shape (D = 128 anisotropic mixture) at n = 20,000 with a
     ragged last tile; exact FP64 neighbours of 300 sampled rows."""
