@@ -14,22 +14,24 @@
 
 namespace pxsne {
 
-// One warp = 32 points consecutive in Morton order.  Each stack entry is a
-// node whose four children are to be tested, with the mask of the lanes that
-// opened it.  The per-child step is branch-free within a level: every lane
-// computes its offset, distance and kernel value, and the accept/open
-// decisions only gate the accumulation and the push.  Children at the leaf
-// level are always accepted (bounded depth, Sec. 4.1) except for a lane's own
-// pixel, which is used without the point itself; children above it follow
-// Eq. bh_criteria, and the cell holding a lane's own pixel is opened.
+// One warp = 32 x PPL points consecutive in Morton order (PPL per lane: lane
+// l holds points l, l + 32, ...).  Each stack entry is a node whose four
+// children are to be tested, with one mask per lane slot of the points that
+// opened it; every point sees exactly the cells its own depth-first search
+// would.  A child's record is loaded once for all the warp's points.  The
+// per-child step is branch-free within a level: every lane computes its
+// points' offsets, distances and kernel values, and the accept/open decisions
+// only gate the accumulation and the push.  Children at the leaf level are
+// always accepted (bounded depth, Sec. 4.1) except for a point's own pixel,
+// which is used without the point itself; children above it follow Eq.
+// bh_criteria, and the cell holding a point's own pixel is opened.
 // CENTRE = 0: centre of mass; 1: geometric cell centre.  COUNT = 1 also
 // counts tested and accepted (point, cell) pairs.
 template <int CENTRE>
-__device__ __forceinline__ void cell_offset(int lc, uint32_t mc, const float4 *rec, int64_t at,
-                                            uint2 zi, float zhx, float zlx, float zhy,
-                                            float zly, float &dx, float &dy) {
+__device__ __forceinline__ void cell_offset(int lc, uint32_t mc, float4 r, uint2 zi, float zhx,
+                                            float zlx, float zhy, float zly, float &dx,
+                                            float &dy) {
     if (CENTRE == 0) {
-        const float4 r = __ldg(rec + at);
         dx = (zhx - r.x) + (zlx - r.y);
         dy = (zhy - r.z) + (zly - r.w);
     } else {
@@ -40,57 +42,89 @@ __device__ __forceinline__ void cell_offset(int lc, uint32_t mc, const float4 *r
     }
 }
 
-template <int CENTRE, int COUNT>
-__global__ void __launch_bounds__(kTravWarps * 32, 5)
+template <int PPL>
+struct TravEntry;
+template <>
+struct __align__(8) TravEntry<1> {
+    uint32_t node, m[1];
+};
+template <>
+struct __align__(16) TravEntry<2> {
+    uint32_t node, m[2], pad;
+};
+
+template <int CENTRE, int COUNT, int PPL>
+__global__ void __launch_bounds__(kTravWarps * 32, PPL == 1 ? 5 : 4)
     k_bh_traverse(int n, int L, const uint2 *__restrict__ z, const uint32_t *__restrict__ perm,
                   const float4 *__restrict__ rec, const float *__restrict__ recn,
                   DevScalars *sc, float2 *__restrict__ Frep, float *__restrict__ Zi) {
-    __shared__ uint32_t s_node[kTravWarps][kTravStack];
-    __shared__ uint32_t s_mask[kTravWarps][kTravStack];
+    // stack entry: (level << 28) | Morton index of a node, and per lane slot
+    // the mask of the lanes whose point opens it
+    __shared__ TravEntry<PPL> s_stk[kTravWarps][kTravStack];
     __shared__ float s_T[kMaxL + 2];
-    __shared__ int64_t s_off[kMaxL + 2];
+    __shared__ int s_off[kMaxL + 2];
     if (threadIdx.x < kMaxL + 2) {
         s_T[threadIdx.x] = sc->T[threadIdx.x];
-        s_off[threadIdx.x] = threadIdx.x <= L ? rec_offset(threadIdx.x) : 0;
+        s_off[threadIdx.x] = threadIdx.x <= L ? (int)rec_offset(threadIdx.x) : 0;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int idx = (blockIdx.x * kTravWarps + w) * 32 + lane;
-    const bool valid = idx < n;
-    const unsigned active = __ballot_sync(0xffffffffu, valid);
-    if (active == 0u) return;
-    const uint32_t i = valid ? perm[idx] : 0u;
-    const uint2 zi = z[i];
+    const int base = (blockIdx.x * kTravWarps + w) * 32 * PPL;
     const int F = 32 - L;
-    const uint32_t mi = morton2(zi.x >> F, zi.y >> F);
-    // z split at bit 16, both halves exact in float (see rec in common.cuh)
-    const float zhx = (float)(zi.x & 0xffff0000u), zlx = (float)(zi.x & 0xffffu);
-    const float zhy = (float)(zi.y & 0xffff0000u), zly = (float)(zi.y & 0xffffu);
+    bool valid[PPL];
+    unsigned act[PPL];
+    uint32_t ip[PPL], mi[PPL];
+    uint2 zi[PPL];
+    float zhx[PPL], zlx[PPL], zhy[PPL], zly[PPL], fx[PPL], fy[PPL], zs[PPL];
+#pragma unroll
+    for (int p = 0; p < PPL; p++) {
+        const int idx = base + 32 * p + lane;
+        valid[p] = idx < n;
+        act[p] = __ballot_sync(0xffffffffu, valid[p]);
+        ip[p] = valid[p] ? perm[idx] : 0u;
+        zi[p] = z[ip[p]];
+        mi[p] = morton2(zi[p].x >> F, zi[p].y >> F);
+        // z split at bit 16, both halves exact in float (see rec in common.cuh)
+        zhx[p] = (float)(zi[p].x & 0xffff0000u);
+        zlx[p] = (float)(zi[p].x & 0xffffu);
+        zhy[p] = (float)(zi[p].y & 0xffff0000u);
+        zly[p] = (float)(zi[p].y & 0xffffu);
+        fx[p] = 0.f;
+        fy[p] = 0.f;
+        zs[p] = 0.f;
+    }
+    if (act[0] == 0u) return;
     const float sf0 = sc->sf[0], sf1 = sc->sf[1];
-    float fx = 0.f, fy = 0.f, zs = 0.f;
     uint32_t n_acc = 0u, n_tst = 0u, n_stp = 0u, n_nod = 0u;
 
-    uint32_t *stn = s_node[w];
-    uint32_t *stm = s_mask[w];
+    TravEntry<PPL> *stk = s_stk[w];
     // The root contains every point: start with its four children.
     if (lane == 0) {
-        stn[0] = 0u;  // (level 0 << 28) | morton 0
-        stm[0] = active;
+        TravEntry<PPL> e0;
+        e0.node = 0u;  // (level 0 << 28) | morton 0
+#pragma unroll
+        for (int p = 0; p < PPL; p++) e0.m[p] = act[p];
+        stk[0] = e0;
     }
     int sp = 1;
     __syncwarp();
     bool overflow = false;
     while (sp > 0) {
         sp--;
-        const uint32_t node = stn[sp];
-        const uint32_t mask = stm[sp];
+        const TravEntry<PPL> top = stk[sp];
         __syncwarp();
+        const uint32_t node = top.node;
         const int lc = (int)(node >> 28) + 1;  // level of the children
         const uint32_t m0 = (node & 0x0fffffffu) << 2;
-        const int64_t base = s_off[lc] + m0;
-        const float4 nv = __ldg(reinterpret_cast<const float4 *>(recn + base));
-        const bool me = (mask >> lane) & 1u;
-        const uint32_t mine = mi >> (2 * (L - lc));  // own cell at level lc
+        const int at = s_off[lc] + (int)m0;
+        const float4 nv = __ldg(reinterpret_cast<const float4 *>(recn + at));
+        bool me[PPL];
+        uint32_t mine[PPL];
+#pragma unroll
+        for (int p = 0; p < PPL; p++) {
+            me[p] = (top.m[p] >> lane) & 1u;
+            mine[p] = mi[p] >> (2 * (L - lc));  // own cell at level lc
+        }
         const float Nc[4] = {nv.x, nv.y, nv.z, nv.w};
         if (COUNT) {
             n_nod++;
@@ -102,34 +136,46 @@ __global__ void __launch_bounds__(kTravWarps * 32, 5)
                 const float N = Nc[ch];
                 if (N == 0.f) continue;
                 const uint32_t mc = m0 + ch;
-                float dx, dy;
-                cell_offset<CENTRE>(lc, mc, rec, base + ch, zi, zhx, zlx, zhy, zly, dx, dy);
-                const bool own = me && (mine == mc);
-                float Nf = N;
-                if (__any_sync(0xffffffffu, own)) {  // own pixel: take point i out
-                    if (own) {
-                        Nf = N - 1.0f;
-                        if (CENTRE == 0 && N > 1.0f) {
-                            const float k = N / Nf;
-                            dx *= k;
-                            dy *= k;
+                float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (CENTRE == 0) r = __ldg(rec + at + ch);
+                bool own[PPL];
+                bool any = false;
+#pragma unroll
+                for (int p = 0; p < PPL; p++) {
+                    own[p] = me[p] && (mine[p] == mc);
+                    any = any || own[p];
+                }
+                const bool any_own = __any_sync(0xffffffffu, any);
+#pragma unroll
+                for (int p = 0; p < PPL; p++) {
+                    float dx, dy;
+                    cell_offset<CENTRE>(lc, mc, r, zi[p], zhx[p], zlx[p], zhy[p], zly[p], dx, dy);
+                    float Nf = N;
+                    if (any_own) {  // own pixel: take point i out
+                        if (own[p]) {
+                            Nf = N - 1.0f;
+                            if (CENTRE == 0 && N > 1.0f) {
+                                const float k = N / Nf;
+                                dx *= k;
+                                dy *= k;
+                            }
                         }
                     }
+                    dx *= sf0;
+                    dy *= sf1;
+                    const float d2 = fmaf(dx, dx, dy * dy);
+                    const bool acc = me[p] && (Nf > 0.f);
+                    if (COUNT) {
+                        n_tst += me[p] ? 1u : 0u;
+                        n_acc += acc ? 1u : 0u;
+                    }
+                    const float q = __fdividef(1.0f, 1.0f + d2);
+                    const float Nq = acc ? Nf * q : 0.0f;
+                    zs[p] += Nq;
+                    const float Nq2 = Nq * q;
+                    fx[p] = fmaf(Nq2, dx, fx[p]);
+                    fy[p] = fmaf(Nq2, dy, fy[p]);
                 }
-                dx *= sf0;
-                dy *= sf1;
-                const float d2 = fmaf(dx, dx, dy * dy);
-                const bool acc = me && (Nf > 0.f);
-                if (COUNT) {
-                    n_tst += me ? 1u : 0u;
-                    n_acc += acc ? 1u : 0u;
-                }
-                const float q = __fdividef(1.0f, 1.0f + d2);
-                const float Nq = acc ? Nf * q : 0.0f;
-                zs += Nq;
-                const float Nq2 = Nq * q;
-                fx = fmaf(Nq2, dx, fx);
-                fy = fmaf(Nq2, dy, fy);
             }
         } else {
             const float Tl = s_T[lc];
@@ -138,32 +184,43 @@ __global__ void __launch_bounds__(kTravWarps * 32, 5)
                 const float N = Nc[ch];
                 if (N == 0.f) continue;
                 const uint32_t mc = m0 + ch;
-                float dx, dy;
-                cell_offset<CENTRE>(lc, mc, rec, base + ch, zi, zhx, zlx, zhy, zly, dx, dy);
-                dx *= sf0;
-                dy *= sf1;
-                const float d2 = fmaf(dx, dx, dy * dy);
-                const bool contains = (mine == mc);
-                const bool far = (d2 > Tl) && !contains;
-                const bool acc = me && far;
-                if (COUNT) {
-                    n_tst += me ? 1u : 0u;
-                    n_acc += acc ? 1u : 0u;
+                float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (CENTRE == 0) r = __ldg(rec + at + ch);
+                unsigned ob[PPL];
+                unsigned oball = 0u;
+#pragma unroll
+                for (int p = 0; p < PPL; p++) {
+                    float dx, dy;
+                    cell_offset<CENTRE>(lc, mc, r, zi[p], zhx[p], zlx[p], zhy[p], zly[p], dx, dy);
+                    dx *= sf0;
+                    dy *= sf1;
+                    const float d2 = fmaf(dx, dx, dy * dy);
+                    const bool contains = (mine[p] == mc);
+                    const bool far = (d2 > Tl) && !contains;
+                    const bool acc = me[p] && far;
+                    if (COUNT) {
+                        n_tst += me[p] ? 1u : 0u;
+                        n_acc += acc ? 1u : 0u;
+                    }
+                    const float q = __fdividef(1.0f, 1.0f + d2);
+                    const float Nq = acc ? N * q : 0.0f;
+                    zs[p] += Nq;
+                    const float Nq2 = Nq * q;
+                    fx[p] = fmaf(Nq2, dx, fx[p]);
+                    fy[p] = fmaf(Nq2, dy, fy[p]);
+                    ob[p] = __ballot_sync(0xffffffffu, me[p] && !far);
+                    oball |= ob[p];
                 }
-                const float q = __fdividef(1.0f, 1.0f + d2);
-                const float Nq = acc ? N * q : 0.0f;
-                zs += Nq;
-                const float Nq2 = Nq * q;
-                fx = fmaf(Nq2, dx, fx);
-                fy = fmaf(Nq2, dy, fy);
-                const unsigned ob = __ballot_sync(0xffffffffu, me && !far);
-                if (ob) {
+                if (oball) {
                     if (sp >= kTravStack) {
                         overflow = true;
                     } else {
                         if (lane == 0) {
-                            stn[sp] = ((uint32_t)lc << 28) | mc;
-                            stm[sp] = ob;
+                            TravEntry<PPL> e;
+                            e.node = ((uint32_t)lc << 28) | mc;
+#pragma unroll
+                            for (int p = 0; p < PPL; p++) e.m[p] = ob[p];
+                            stk[sp] = e;
                         }
                         sp++;
                     }
@@ -173,10 +230,12 @@ __global__ void __launch_bounds__(kTravWarps * 32, 5)
         __syncwarp();
         if (overflow) break;
     }
-    if (valid) {
-        Frep[i] = make_float2(fx, fy);
-        Zi[i] = zs;
-    }
+#pragma unroll
+    for (int p = 0; p < PPL; p++)
+        if (valid[p]) {
+            Frep[ip[p]] = make_float2(fx[p], fy[p]);
+            Zi[ip[p]] = zs[p];
+        }
     if (overflow && lane == 0) atomicOr(&sc->err, (unsigned)PXSNE_DEVERR_STACK);
     if (COUNT) {
 #pragma unroll
@@ -349,22 +408,23 @@ __global__ void __launch_bounds__(512)
 
 static cudaError_t traverse(pxsne_ctx *c, cudaStream_t st, bool count) {
     const int n = (int)c->n;
-    const int trav_blocks = (n + kTravWarps * 32 - 1) / (kTravWarps * 32);
-    const dim3 g(trav_blocks), b(kTravWarps * 32);
+    constexpr int P = kTravPPL;
+    const int per_block = kTravWarps * 32 * P;
+    const dim3 g((n + per_block - 1) / per_block), b(kTravWarps * 32);
     if (c->p.centre_mode == 0) {
         if (count)
-            k_bh_traverse<0, 1><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
-                                                 c->Frep, c->Zi);
+            k_bh_traverse<0, 1, P><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn,
+                                                    c->sc, c->Frep, c->Zi);
         else
-            k_bh_traverse<0, 0><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
-                                                 c->Frep, c->Zi);
+            k_bh_traverse<0, 0, P><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn,
+                                                    c->sc, c->Frep, c->Zi);
     } else {
         if (count)
-            k_bh_traverse<1, 1><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
-                                                 c->Frep, c->Zi);
+            k_bh_traverse<1, 1, P><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn,
+                                                    c->sc, c->Frep, c->Zi);
         else
-            k_bh_traverse<1, 0><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
-                                                 c->Frep, c->Zi);
+            k_bh_traverse<1, 0, P><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn,
+                                                    c->sc, c->Frep, c->Zi);
     }
     return cudaGetLastError();
 }
