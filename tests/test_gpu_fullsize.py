@@ -3,6 +3,8 @@
 through the same calls as bench.py, checked against the oracle on sampled
 outputs it can compute one by one (kNN rows, per-point forces), on whole
 outputs where it is fast enough (the tree, Z), and through properties of P.
+The scale workload's shape (gmm64out: D = 64, 1 % uniform outliers, 4096^2
+screen) is checked the same way at n = 2,000,000.
 
 Bars: kNN as in test_gpu_parity (FP64 neighbours of the sampled rows); tree
 bit-exact; Frep, Zi, Fattr of the sampled points and Z <= 1e-4 relative L2; P
@@ -79,7 +81,7 @@ def test_P_properties(run):
             assert val[rp[j] + p] == pytest.approx(v, rel=1e-6)
 
 
-def check_state(ctx, P, rows):
+def check_state(ctx, P, rows, L=L, theta=THETA):
     z, s, _, _, _ = ctx.get_state()
     Frep, Zi, Fattr, Z = ctx.get_forces()
     tree = oracle.pyramid(z, L)
@@ -90,7 +92,7 @@ def check_state(ctx, P, rows):
         assert np.array_equal(cnt, cnt_o[off:off + 4 ** lev]), f"level {lev} counts"
     _, _, _, mk = ctx.get_tree(0, morton=True)
     assert np.array_equal(mk, oracle.leaf_keys(z, L)[2])
-    oF, oZi, _ = oracle.bh_repulsion(z, s, L, THETA, tree=tree)
+    oF, oZi, _ = oracle.bh_repulsion(z, s, L, theta, tree=tree)
     assert abs(Z - oZi.sum()) / oZi.sum() <= FORCE_TOL
     assert rel(Frep[rows], oF[rows]) <= FORCE_TOL
     assert rel(Zi[rows], oZi[rows]) <= FORCE_TOL
@@ -108,3 +110,30 @@ def test_tree_and_forces_after_100_iterations(run):
     _, ctx, P = run
     ctx.step(100)
     check_state(ctx, P, sample_rows(4, 512))
+
+
+def test_scale_workload_shape_at_2M():
+    """gmm64out (D = 64, 256 components, 1 % outliers in [-50, 50]^64) at
+    n = 2,000,000 on a 4096^2 screen (L = 12): sampled kNN rows, the tree, and
+    sampled forces after 60 iterations."""
+    import paper_1611_02568_gb300 as px
+    n, Ls = 2_000_000, 12
+    X, _ = datagen.gmm64out(seed=0, n=n)
+    with px.Context(px.Params(log2_r=Ls, theta=THETA, k=K, perplexity=30.0)) as ctx:
+        ctx.affinities(X)
+        rows = np.unique(np.concatenate([np.random.default_rng(7).choice(n, 48, replace=False),
+                                         [0, n - 1]]))
+        idx_o, d2_o = oracle.knn(X, K, rows=rows)
+        idx, d2, _ = ctx.get_knn()
+        x = X.astype(np.float64)
+        for a, r in enumerate(rows):
+            tau = d2_o[a, K - 1]
+            ex = ((x[idx[r]] - x[r]) ** 2).sum(1)
+            assert np.all(ex <= tau * (1 + 2e-5)), r
+            must = set(idx_o[a][d2_o[a] < tau * (1 - 2e-5)].tolist())
+            assert must <= set(idx[r].tolist()), r
+        ctx.init(datagen.init_y0(0, n))
+        ctx.step(60)
+        rp, col, val = ctx.get_P()
+        P = oracle.CSR(rp, col, val.astype(np.float64))
+        check_state(ctx, P, np.random.default_rng(8).choice(n, 512, replace=False), L=Ls)
