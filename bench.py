@@ -28,9 +28,18 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(workload="gmm128", n=1_000_000, D=128, k=90, perplexity=30.0, log2_r=11,
-                theta=0.5, iterations=1000)
-METRIC = "t-SNE iterations/sec at n=1M, 2048^2 screen"
+# The headline workload (the default) and the scale workload (100-component
+# 128-D mixture at n = 1M on 2048^2; 256-component 64-D mixture with 1 %
+# outliers at n = 10M on 4096^2).
+WORKLOADS = {
+    "gmm128": (dict(workload="gmm128", n=1_000_000, D=128, k=90, perplexity=30.0, log2_r=11,
+                    theta=0.5, iterations=1000),
+               "t-SNE iterations/sec at n=1M, 2048^2 screen"),
+    "gmm64out": (dict(workload="gmm64out", n=10_000_000, D=64, k=90, perplexity=30.0,
+                      log2_r=12, theta=0.5, iterations=1000),
+                 "t-SNE iterations/sec at n=10M, 4096^2 screen (scale workload)"),
+}
+WORKLOAD, METRIC = WORKLOADS["gmm128"]
 
 
 def parse():
@@ -39,7 +48,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--n", type=int, default=WORKLOAD["n"], help="points (debug only)")
+    ap.add_argument("--workload", default="gmm128", choices=sorted(WORKLOADS))
+    ap.add_argument("--n", type=int, default=None, help="points (debug only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=40000,
@@ -107,11 +117,14 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- workload
+def draw(seed, n):
+    import datagen
+    return getattr(datagen, WORKLOAD["workload"])(seed=seed, n=n)[0]
+
+
 def make_inputs(n, seed=0):
     import datagen
-    X, _ = datagen.gmm128(seed=seed, n=n)
-    Y0 = datagen.init_y0(seed, n)
-    return X, Y0
+    return draw(seed, n), datagen.init_y0(seed, n)
 
 
 def measured_peaks():
@@ -239,7 +252,7 @@ def warmstart_experiment(px, ctx, X, Y0, args, torch):
     first = None
     for k in range(args.warm_seeds):
         sd = 1000 + k
-        Xk, _ = datagen.gmm128(seed=sd, n=args.warm_n)
+        Xk = draw(sd, args.warm_n)
         with px.Context(params) as c2:
             c2.affinities(Xk)
             if first is None:
@@ -419,6 +432,8 @@ def run_gpu(args):
     acc, tst, wsteps, nodes = ctx.counters()
     peaks, peak_kind = measured_peaks()
     gb = group_bytes(n, nnz, W["log2_r"])
+    # the recorded DRAM traffic holds for the headline workload at full size only
+    traffic = TRAFFIC_BYTES if (W["workload"] == "gmm128" and n == 1_000_000) else {}
     top = max(groups, key=groups.get)
     avg_ms = {g: v / args.steps for g, v in groups.items()}
     sm_mhz = ck["sm_mhz"] if ck else 1477.0
@@ -429,14 +444,14 @@ def run_gpu(args):
         achieved = flops / (avg_ms[top] / 1e3) / 1e12
         roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": alu_peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / alu_peak_tflops,
-                "traffic": TRAFFIC_BYTES.get(top),
+                "traffic": traffic.get(top),
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median "
                                "SM clock of this run)"}
     else:
         achieved = gb[top] / (avg_ms[top] / 1e3) / 1e9
         roof = {"kernel": top, "bound": "hbm", "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": TRAFFIC_BYTES.get(top),
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic.get(top),
                 "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_kind})"}
     kernels = {g: {"ms_per_launch": avg_ms[g], "share": groups[g] / sum(groups.values()),
                    "alg_GBps": gb[g] / (avg_ms[g] / 1e3) / 1e9 if avg_ms[g] > 0 else None}
@@ -499,7 +514,8 @@ def run_gpu(args):
             "dtype": "f32", "data": "synthetic",
             "config": {k: W[k] for k in W} | {"n": n, "nnz": nnz,
                                               "parallelism": "replicas" if ws > 1 else "single",
-                                              "l2": "inputs larger than L2 (P ~1 GB/iter)",
+                                              "l2": f"inputs larger than L2 (P "
+                                                    f"{nnz * 8 / 1e9:.1f} GB read per iteration)",
                                               "timed_iterations": f"t = 0..{args.steps - 1}"},
             "roofline": roof, "kernels": kernels,
             "traversal": {"accepted_pairs": acc, "tested_pairs": tst,
@@ -509,11 +525,11 @@ def run_gpu(args):
             "profiled_total_ms": prof_total, "p_construction_s": p_seconds, "knn": knn,
             "kl_after_timed": kl_after,
             "clocks": ck, "e2e": e2e, "cpu_baseline": cpu, "warmstart": warm,
-            # per iteration: update, snap_hist, ceil(L/5) pyramid passes, scan,
-            # perm_scatter, traverse, attract, zsum; per relabel (before every
-            # RELABEL_EVERY-th iteration): maps, three scan kernels, rows
-            "gpu_launches": args.steps * (7 + (W["log2_r"] + 4) // 5)
-                            + 5 * ((args.steps - 1) // RELABEL_EVERY),
+            # per iteration: update, snap_hist, the pyramid (one launch for
+            # 5 <= L <= 12), perm_scatter, traverse, attract, zsum; per relabel
+            # (before every RELABEL_EVERY-th iteration): maps, three scan
+            # kernels, rows
+            "gpu_launches": args.steps * 7 + 5 * ((args.steps - 1) // RELABEL_EVERY),
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -522,7 +538,11 @@ def run_gpu(args):
 
 
 def main():
+    global WORKLOAD, METRIC
     args = parse()
+    WORKLOAD, METRIC = WORKLOADS[args.workload]
+    if args.n is None:
+        args.n = WORKLOAD["n"]
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
