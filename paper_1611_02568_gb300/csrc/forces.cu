@@ -42,6 +42,16 @@ __device__ __forceinline__ void cell_offset(int lc, uint32_t mc, float4 r, uint2
     }
 }
 
+// Packed FP32 pairs (one per point of a lane): each component is rounded to
+// nearest exactly as the scalar operation, so the packed step gives the same
+// values as two scalar ones.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    return __ffma2_rn(a, b, c);
+}
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+
 template <int PPL>
 struct TravEntry;
 template <>
@@ -146,35 +156,85 @@ __global__ void __launch_bounds__(kTravWarps * 32, PPL == 1 ? 5 : 4)
                     any = any || own[p];
                 }
                 const bool any_own = __any_sync(0xffffffffu, any);
-#pragma unroll
-                for (int p = 0; p < PPL; p++) {
-                    float dx, dy;
-                    cell_offset<CENTRE>(lc, mc, r, zi[p], zhx[p], zlx[p], zhy[p], zly[p], dx, dy);
-                    float Nf = N;
-                    if (any_own) {  // own pixel: take point i out
-                        if (own[p]) {
-                            Nf = N - 1.0f;
-                            if (CENTRE == 0 && N > 1.0f) {
-                                const float k = N / Nf;
-                                dx *= k;
-                                dy *= k;
+                if constexpr (PPL == 2 && CENTRE == 0) {
+                    // both points at once
+                    float2 dx = add2(add2(make_float2(zhx[0], zhx[1]), bc2(-r.x)),
+                                     add2(make_float2(zlx[0], zlx[1]), bc2(-r.y)));
+                    float2 dy = add2(add2(make_float2(zhy[0], zhy[1]), bc2(-r.z)),
+                                     add2(make_float2(zly[0], zly[1]), bc2(-r.w)));
+                    float2 Nf = bc2(N);
+                    if (any_own) {  // own pixel: take the point out
+                        if (own[0]) {
+                            Nf.x = N - 1.0f;
+                            if (N > 1.0f) {
+                                const float k = N / Nf.x;
+                                dx.x *= k;
+                                dy.x *= k;
+                            }
+                        }
+                        if (own[1]) {
+                            Nf.y = N - 1.0f;
+                            if (N > 1.0f) {
+                                const float k = N / Nf.y;
+                                dx.y *= k;
+                                dy.y *= k;
                             }
                         }
                     }
-                    dx *= sf0;
-                    dy *= sf1;
-                    const float d2 = fmaf(dx, dx, dy * dy);
-                    const bool acc = me[p] && (Nf > 0.f);
+                    dx = mul2(dx, bc2(sf0));
+                    dy = mul2(dy, bc2(sf1));
+                    const float2 d2 = fma2(dx, dx, mul2(dy, dy));
+                    const bool acc0 = me[0] && (Nf.x > 0.f), acc1 = me[1] && (Nf.y > 0.f);
                     if (COUNT) {
-                        n_tst += me[p] ? 1u : 0u;
-                        n_acc += acc ? 1u : 0u;
+                        n_tst += (me[0] ? 1u : 0u) + (me[1] ? 1u : 0u);
+                        n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
                     }
-                    const float q = __fdividef(1.0f, 1.0f + d2);
-                    const float Nq = acc ? Nf * q : 0.0f;
-                    zs[p] += Nq;
-                    const float Nq2 = Nq * q;
-                    fx[p] = fmaf(Nq2, dx, fx[p]);
-                    fy[p] = fmaf(Nq2, dy, fy[p]);
+                    const float2 w1 = add2(bc2(1.0f), d2);
+                    const float2 q = make_float2(__fdividef(1.0f, w1.x), __fdividef(1.0f, w1.y));
+                    const float2 Nq0 = mul2(Nf, q);
+                    const float2 Nq = make_float2(acc0 ? Nq0.x : 0.0f, acc1 ? Nq0.y : 0.0f);
+                    const float2 zs2 = add2(make_float2(zs[0], zs[1]), Nq);
+                    const float2 Nq2 = mul2(Nq, q);
+                    const float2 fx2 = fma2(Nq2, dx, make_float2(fx[0], fx[1]));
+                    const float2 fy2 = fma2(Nq2, dy, make_float2(fy[0], fy[1]));
+                    zs[0] = zs2.x;
+                    zs[1] = zs2.y;
+                    fx[0] = fx2.x;
+                    fx[1] = fx2.y;
+                    fy[0] = fy2.x;
+                    fy[1] = fy2.y;
+                } else {
+    #pragma unroll
+                    for (int p = 0; p < PPL; p++) {
+                        float dx, dy;
+                        cell_offset<CENTRE>(lc, mc, r, zi[p], zhx[p], zlx[p], zhy[p], zly[p], dx, dy);
+                        float Nf = N;
+                        if (any_own) {  // own pixel: take point i out
+                            if (own[p]) {
+                                Nf = N - 1.0f;
+                                if (CENTRE == 0 && N > 1.0f) {
+                                    const float k = N / Nf;
+                                    dx *= k;
+                                    dy *= k;
+                                }
+                            }
+                        }
+                        dx *= sf0;
+                        dy *= sf1;
+                        const float d2 = fmaf(dx, dx, dy * dy);
+                        const bool acc = me[p] && (Nf > 0.f);
+                        if (COUNT) {
+                            n_tst += me[p] ? 1u : 0u;
+                            n_acc += acc ? 1u : 0u;
+                        }
+                        const float q = __fdividef(1.0f, 1.0f + d2);
+                        const float Nq = acc ? Nf * q : 0.0f;
+                        zs[p] += Nq;
+                        const float Nq2 = Nq * q;
+                        fx[p] = fmaf(Nq2, dx, fx[p]);
+                        fy[p] = fmaf(Nq2, dy, fy[p]);
+                    }
+
                 }
             }
         } else {
@@ -188,28 +248,63 @@ __global__ void __launch_bounds__(kTravWarps * 32, PPL == 1 ? 5 : 4)
                 if (CENTRE == 0) r = __ldg(rec + at + ch);
                 unsigned ob[PPL];
                 unsigned oball = 0u;
-#pragma unroll
-                for (int p = 0; p < PPL; p++) {
-                    float dx, dy;
-                    cell_offset<CENTRE>(lc, mc, r, zi[p], zhx[p], zlx[p], zhy[p], zly[p], dx, dy);
-                    dx *= sf0;
-                    dy *= sf1;
-                    const float d2 = fmaf(dx, dx, dy * dy);
-                    const bool contains = (mine[p] == mc);
-                    const bool far = (d2 > Tl) && !contains;
-                    const bool acc = me[p] && far;
+                if constexpr (PPL == 2 && CENTRE == 0) {
+                    // both points at once
+                    float2 dx = add2(add2(make_float2(zhx[0], zhx[1]), bc2(-r.x)),
+                                     add2(make_float2(zlx[0], zlx[1]), bc2(-r.y)));
+                    float2 dy = add2(add2(make_float2(zhy[0], zhy[1]), bc2(-r.z)),
+                                     add2(make_float2(zly[0], zly[1]), bc2(-r.w)));
+                    dx = mul2(dx, bc2(sf0));
+                    dy = mul2(dy, bc2(sf1));
+                    const float2 d2 = fma2(dx, dx, mul2(dy, dy));
+                    const bool far0 = (d2.x > Tl) && (mine[0] != mc);
+                    const bool far1 = (d2.y > Tl) && (mine[1] != mc);
+                    const bool acc0 = me[0] && far0, acc1 = me[1] && far1;
                     if (COUNT) {
-                        n_tst += me[p] ? 1u : 0u;
-                        n_acc += acc ? 1u : 0u;
+                        n_tst += (me[0] ? 1u : 0u) + (me[1] ? 1u : 0u);
+                        n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
                     }
-                    const float q = __fdividef(1.0f, 1.0f + d2);
-                    const float Nq = acc ? N * q : 0.0f;
-                    zs[p] += Nq;
-                    const float Nq2 = Nq * q;
-                    fx[p] = fmaf(Nq2, dx, fx[p]);
-                    fy[p] = fmaf(Nq2, dy, fy[p]);
-                    ob[p] = __ballot_sync(0xffffffffu, me[p] && !far);
-                    oball |= ob[p];
+                    const float2 w1 = add2(bc2(1.0f), d2);
+                    const float2 q = make_float2(__fdividef(1.0f, w1.x), __fdividef(1.0f, w1.y));
+                    const float2 Nq0 = mul2(bc2(N), q);
+                    const float2 Nq = make_float2(acc0 ? Nq0.x : 0.0f, acc1 ? Nq0.y : 0.0f);
+                    const float2 zs2 = add2(make_float2(zs[0], zs[1]), Nq);
+                    const float2 Nq2 = mul2(Nq, q);
+                    const float2 fx2 = fma2(Nq2, dx, make_float2(fx[0], fx[1]));
+                    const float2 fy2 = fma2(Nq2, dy, make_float2(fy[0], fy[1]));
+                    zs[0] = zs2.x;
+                    zs[1] = zs2.y;
+                    fx[0] = fx2.x;
+                    fx[1] = fx2.y;
+                    fy[0] = fy2.x;
+                    fy[1] = fy2.y;
+                    ob[0] = __ballot_sync(0xffffffffu, me[0] && !far0);
+                    ob[1] = __ballot_sync(0xffffffffu, me[1] && !far1);
+                    oball = ob[0] | ob[1];
+                } else {
+    #pragma unroll
+                    for (int p = 0; p < PPL; p++) {
+                        float dx, dy;
+                        cell_offset<CENTRE>(lc, mc, r, zi[p], zhx[p], zlx[p], zhy[p], zly[p], dx, dy);
+                        dx *= sf0;
+                        dy *= sf1;
+                        const float d2 = fmaf(dx, dx, dy * dy);
+                        const bool contains = (mine[p] == mc);
+                        const bool far = (d2 > Tl) && !contains;
+                        const bool acc = me[p] && far;
+                        if (COUNT) {
+                            n_tst += me[p] ? 1u : 0u;
+                            n_acc += acc ? 1u : 0u;
+                        }
+                        const float q = __fdividef(1.0f, 1.0f + d2);
+                        const float Nq = acc ? N * q : 0.0f;
+                        zs[p] += Nq;
+                        const float Nq2 = Nq * q;
+                        fx[p] = fmaf(Nq2, dx, fx[p]);
+                        fy[p] = fmaf(Nq2, dy, fy[p]);
+                        ob[p] = __ballot_sync(0xffffffffu, me[p] && !far);
+                        oball |= ob[p];
+                    }
                 }
                 if (oball) {
                     if (sp >= kTravStack) {
