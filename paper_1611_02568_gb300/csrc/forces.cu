@@ -62,9 +62,13 @@ template <>
 struct __align__(16) TravEntry<2> {
     uint32_t node, m[2], pad;
 };
+template <>
+struct __align__(16) TravEntry<4> {
+    uint32_t node, m[4], pad[3];
+};
 
 template <int CENTRE, int COUNT, int PPL>
-__global__ void __launch_bounds__(kTravWarps * 32, PPL == 1 ? 5 : 4)
+__global__ void __launch_bounds__(kTravWarps * 32, PPL == 1 ? 5 : (PPL == 2 ? 4 : 3))
     k_bh_traverse(int n, int L, const uint2 *__restrict__ z, const uint32_t *__restrict__ perm,
                   const float4 *__restrict__ rec, const float *__restrict__ recn,
                   DevScalars *sc, float2 *__restrict__ Frep, float *__restrict__ Zi) {
@@ -156,53 +160,57 @@ __global__ void __launch_bounds__(kTravWarps * 32, PPL == 1 ? 5 : 4)
                     any = any || own[p];
                 }
                 const bool any_own = __any_sync(0xffffffffu, any);
-                if constexpr (PPL == 2 && CENTRE == 0) {
-                    // both points at once
-                    float2 dx = add2(add2(make_float2(zhx[0], zhx[1]), bc2(-r.x)),
-                                     add2(make_float2(zlx[0], zlx[1]), bc2(-r.y)));
-                    float2 dy = add2(add2(make_float2(zhy[0], zhy[1]), bc2(-r.z)),
-                                     add2(make_float2(zly[0], zly[1]), bc2(-r.w)));
-                    float2 Nf = bc2(N);
-                    if (any_own) {  // own pixel: take the point out
-                        if (own[0]) {
-                            Nf.x = N - 1.0f;
-                            if (N > 1.0f) {
-                                const float k = N / Nf.x;
-                                dx.x *= k;
-                                dy.x *= k;
+                if constexpr (PPL % 2 == 0 && CENTRE == 0) {
+                    // the lane's points in pairs
+#pragma unroll
+                    for (int h = 0; h < PPL; h += 2) {
+                        float2 dx = add2(add2(make_float2(zhx[h], zhx[h + 1]), bc2(-r.x)),
+                                         add2(make_float2(zlx[h], zlx[h + 1]), bc2(-r.y)));
+                        float2 dy = add2(add2(make_float2(zhy[h], zhy[h + 1]), bc2(-r.z)),
+                                         add2(make_float2(zly[h], zly[h + 1]), bc2(-r.w)));
+                        float2 Nf = bc2(N);
+                        if (any_own) {  // own pixel: take the point out
+                            if (own[h]) {
+                                Nf.x = N - 1.0f;
+                                if (N > 1.0f) {
+                                    const float k = N / Nf.x;
+                                    dx.x *= k;
+                                    dy.x *= k;
+                                }
+                            }
+                            if (own[h + 1]) {
+                                Nf.y = N - 1.0f;
+                                if (N > 1.0f) {
+                                    const float k = N / Nf.y;
+                                    dx.y *= k;
+                                    dy.y *= k;
+                                }
                             }
                         }
-                        if (own[1]) {
-                            Nf.y = N - 1.0f;
-                            if (N > 1.0f) {
-                                const float k = N / Nf.y;
-                                dx.y *= k;
-                                dy.y *= k;
-                            }
+                        dx = mul2(dx, bc2(sf0));
+                        dy = mul2(dy, bc2(sf1));
+                        const float2 d2 = fma2(dx, dx, mul2(dy, dy));
+                        const bool acc0 = me[h] && (Nf.x > 0.f), acc1 = me[h + 1] && (Nf.y > 0.f);
+                        if (COUNT) {
+                            n_tst += (me[h] ? 1u : 0u) + (me[h + 1] ? 1u : 0u);
+                            n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
                         }
+                        const float2 w1 = add2(bc2(1.0f), d2);
+                        const float2 q =
+                            make_float2(__fdividef(1.0f, w1.x), __fdividef(1.0f, w1.y));
+                        const float2 Nq0 = mul2(Nf, q);
+                        const float2 Nq = make_float2(acc0 ? Nq0.x : 0.0f, acc1 ? Nq0.y : 0.0f);
+                        const float2 zs2 = add2(make_float2(zs[h], zs[h + 1]), Nq);
+                        const float2 Nq2 = mul2(Nq, q);
+                        const float2 fx2 = fma2(Nq2, dx, make_float2(fx[h], fx[h + 1]));
+                        const float2 fy2 = fma2(Nq2, dy, make_float2(fy[h], fy[h + 1]));
+                        zs[h] = zs2.x;
+                        zs[h + 1] = zs2.y;
+                        fx[h] = fx2.x;
+                        fx[h + 1] = fx2.y;
+                        fy[h] = fy2.x;
+                        fy[h + 1] = fy2.y;
                     }
-                    dx = mul2(dx, bc2(sf0));
-                    dy = mul2(dy, bc2(sf1));
-                    const float2 d2 = fma2(dx, dx, mul2(dy, dy));
-                    const bool acc0 = me[0] && (Nf.x > 0.f), acc1 = me[1] && (Nf.y > 0.f);
-                    if (COUNT) {
-                        n_tst += (me[0] ? 1u : 0u) + (me[1] ? 1u : 0u);
-                        n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
-                    }
-                    const float2 w1 = add2(bc2(1.0f), d2);
-                    const float2 q = make_float2(__fdividef(1.0f, w1.x), __fdividef(1.0f, w1.y));
-                    const float2 Nq0 = mul2(Nf, q);
-                    const float2 Nq = make_float2(acc0 ? Nq0.x : 0.0f, acc1 ? Nq0.y : 0.0f);
-                    const float2 zs2 = add2(make_float2(zs[0], zs[1]), Nq);
-                    const float2 Nq2 = mul2(Nq, q);
-                    const float2 fx2 = fma2(Nq2, dx, make_float2(fx[0], fx[1]));
-                    const float2 fy2 = fma2(Nq2, dy, make_float2(fy[0], fy[1]));
-                    zs[0] = zs2.x;
-                    zs[1] = zs2.y;
-                    fx[0] = fx2.x;
-                    fx[1] = fx2.y;
-                    fy[0] = fy2.x;
-                    fy[1] = fy2.y;
                 } else {
     #pragma unroll
                     for (int p = 0; p < PPL; p++) {
@@ -248,39 +256,43 @@ __global__ void __launch_bounds__(kTravWarps * 32, PPL == 1 ? 5 : 4)
                 if (CENTRE == 0) r = __ldg(rec + at + ch);
                 unsigned ob[PPL];
                 unsigned oball = 0u;
-                if constexpr (PPL == 2 && CENTRE == 0) {
-                    // both points at once
-                    float2 dx = add2(add2(make_float2(zhx[0], zhx[1]), bc2(-r.x)),
-                                     add2(make_float2(zlx[0], zlx[1]), bc2(-r.y)));
-                    float2 dy = add2(add2(make_float2(zhy[0], zhy[1]), bc2(-r.z)),
-                                     add2(make_float2(zly[0], zly[1]), bc2(-r.w)));
-                    dx = mul2(dx, bc2(sf0));
-                    dy = mul2(dy, bc2(sf1));
-                    const float2 d2 = fma2(dx, dx, mul2(dy, dy));
-                    const bool far0 = (d2.x > Tl) && (mine[0] != mc);
-                    const bool far1 = (d2.y > Tl) && (mine[1] != mc);
-                    const bool acc0 = me[0] && far0, acc1 = me[1] && far1;
-                    if (COUNT) {
-                        n_tst += (me[0] ? 1u : 0u) + (me[1] ? 1u : 0u);
-                        n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
+                if constexpr (PPL % 2 == 0 && CENTRE == 0) {
+                    // the lane's points in pairs
+#pragma unroll
+                    for (int h = 0; h < PPL; h += 2) {
+                        float2 dx = add2(add2(make_float2(zhx[h], zhx[h + 1]), bc2(-r.x)),
+                                         add2(make_float2(zlx[h], zlx[h + 1]), bc2(-r.y)));
+                        float2 dy = add2(add2(make_float2(zhy[h], zhy[h + 1]), bc2(-r.z)),
+                                         add2(make_float2(zly[h], zly[h + 1]), bc2(-r.w)));
+                        dx = mul2(dx, bc2(sf0));
+                        dy = mul2(dy, bc2(sf1));
+                        const float2 d2 = fma2(dx, dx, mul2(dy, dy));
+                        const bool far0 = (d2.x > Tl) && (mine[h] != mc);
+                        const bool far1 = (d2.y > Tl) && (mine[h + 1] != mc);
+                        const bool acc0 = me[h] && far0, acc1 = me[h + 1] && far1;
+                        if (COUNT) {
+                            n_tst += (me[h] ? 1u : 0u) + (me[h + 1] ? 1u : 0u);
+                            n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
+                        }
+                        const float2 w1 = add2(bc2(1.0f), d2);
+                        const float2 q =
+                            make_float2(__fdividef(1.0f, w1.x), __fdividef(1.0f, w1.y));
+                        const float2 Nq0 = mul2(bc2(N), q);
+                        const float2 Nq = make_float2(acc0 ? Nq0.x : 0.0f, acc1 ? Nq0.y : 0.0f);
+                        const float2 zs2 = add2(make_float2(zs[h], zs[h + 1]), Nq);
+                        const float2 Nq2 = mul2(Nq, q);
+                        const float2 fx2 = fma2(Nq2, dx, make_float2(fx[h], fx[h + 1]));
+                        const float2 fy2 = fma2(Nq2, dy, make_float2(fy[h], fy[h + 1]));
+                        zs[h] = zs2.x;
+                        zs[h + 1] = zs2.y;
+                        fx[h] = fx2.x;
+                        fx[h + 1] = fx2.y;
+                        fy[h] = fy2.x;
+                        fy[h + 1] = fy2.y;
+                        ob[h] = __ballot_sync(0xffffffffu, me[h] && !far0);
+                        ob[h + 1] = __ballot_sync(0xffffffffu, me[h + 1] && !far1);
+                        oball |= ob[h] | ob[h + 1];
                     }
-                    const float2 w1 = add2(bc2(1.0f), d2);
-                    const float2 q = make_float2(__fdividef(1.0f, w1.x), __fdividef(1.0f, w1.y));
-                    const float2 Nq0 = mul2(bc2(N), q);
-                    const float2 Nq = make_float2(acc0 ? Nq0.x : 0.0f, acc1 ? Nq0.y : 0.0f);
-                    const float2 zs2 = add2(make_float2(zs[0], zs[1]), Nq);
-                    const float2 Nq2 = mul2(Nq, q);
-                    const float2 fx2 = fma2(Nq2, dx, make_float2(fx[0], fx[1]));
-                    const float2 fy2 = fma2(Nq2, dy, make_float2(fy[0], fy[1]));
-                    zs[0] = zs2.x;
-                    zs[1] = zs2.y;
-                    fx[0] = fx2.x;
-                    fx[1] = fx2.y;
-                    fy[0] = fy2.x;
-                    fy[1] = fy2.y;
-                    ob[0] = __ballot_sync(0xffffffffu, me[0] && !far0);
-                    ob[1] = __ballot_sync(0xffffffffu, me[1] && !far1);
-                    oball = ob[0] | ob[1];
                 } else {
     #pragma unroll
                     for (int p = 0; p < PPL; p++) {
