@@ -1,10 +1,10 @@
 // Forces of the PixelSNE gradient (Eq. grad) on the pixel-aligned tree.
 //
 //   k_bh_traverse  repulsion by Barnes-Hut (Sec. 3.3, Eq. bh_criteria) on the
-//                  dense pyramid, one warp per 32 points of the Morton order;
-//                  each lane keeps its own accept/open decisions (a lane mask
-//                  per stack entry), so every point sees exactly the cells its
-//                  own depth-first search would accept
+//                  dense pyramid, one warp per 64 points of the Morton order
+//                  (two per lane, as packed FP32 pairs); each point keeps its
+//                  own accept/open decisions (lane masks per stack entry), so
+//                  it sees exactly the cells its own depth-first search would
 //   k_attract      attraction over the CSR of P, one warp per row
 //   k_zsum         Z = sum_i Z_i in FP64, fixed summation order
 //   k_kl           Eq. cost_func in FP64 accumulation
@@ -14,37 +14,22 @@
 
 namespace pxsne {
 
-// One warp = 32 x PPL points consecutive in Morton order (PPL per lane: lane
-// l holds points l, l + 32, ...).  Each stack entry is a node whose four
-// children are to be tested, with one mask per lane slot of the points that
-// opened it; every point sees exactly the cells its own depth-first search
-// would.  A child's record is loaded once for all the warp's points.  The
-// per-child step is branch-free within a level: every lane computes its
-// points' offsets, distances and kernel values, and the accept/open decisions
-// only gate the accumulation and the push.  Children at the leaf level are
-// always accepted (bounded depth, Sec. 4.1) except for a point's own pixel,
-// which is used without the point itself; children above it follow Eq.
-// bh_criteria, and the cell holding a point's own pixel is opened.
+// One warp = 64 points consecutive in Morton order, two per lane (lane l holds
+// points l and l + 32); the two are held and computed as packed FP32 pairs
+// (each component rounded to nearest exactly as the scalar operation).  Each
+// stack entry is a node whose four children are to be tested, with one mask per
+// half of the warp's points marking the points that opened it, so every point
+// sees exactly the cells its own depth-first search would.  A child's record is
+// loaded once for all the warp's points.  The per-child step is branch-free
+// within a level: every lane computes its points' offsets, distances and kernel
+// values, and the accept/open decisions only gate the accumulation and the
+// push.  Children at the leaf level are always accepted (bounded depth, Sec.
+// 4.1) except for a point's own pixel, which is used without the point itself;
+// children above it follow Eq. bh_criteria, and the cell holding a point's own
+// pixel is opened.  A point accumulates its cells in the fixed depth-first order
+// of the tree, so its result does not depend on the warp it shares.
 // CENTRE = 0: centre of mass; 1: geometric cell centre.  COUNT = 1 also
 // counts tested and accepted (point, cell) pairs.
-template <int CENTRE>
-__device__ __forceinline__ void cell_offset(int lc, uint32_t mc, float4 r, uint2 zi, float zhx,
-                                            float zlx, float zhy, float zly, float &dx,
-                                            float &dy) {
-    if (CENTRE == 0) {
-        dx = (zhx - r.x) + (zlx - r.y);
-        dy = (zhy - r.z) + (zly - r.w);
-    } else {
-        const uint32_t cx = gather_bits16(mc), cy = gather_bits16(mc >> 1);
-        const int64_t half = int64_t(1) << (31 - lc);
-        dx = (float)((int64_t)zi.x - (((int64_t)cx << (32 - lc)) + half));
-        dy = (float)((int64_t)zi.y - (((int64_t)cy << (32 - lc)) + half));
-    }
-}
-
-// Packed FP32 pairs (one per point of a lane): each component is rounded to
-// nearest exactly as the scalar operation, so the packed step gives the same
-// values as two scalar ones.
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
@@ -52,29 +37,36 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 }
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 
-template <int PPL>
-struct TravEntry;
-template <>
-struct __align__(8) TravEntry<1> {
-    uint32_t node, m[1];
-};
-template <>
-struct __align__(16) TravEntry<2> {
-    uint32_t node, m[2], pad;
-};
-template <>
-struct __align__(16) TravEntry<4> {
-    uint32_t node, m[4], pad[3];
+// Offset z - c of a lane's two points from the cell's centre: of mass (the
+// split record r), or the geometric centre of cell mc of level lc.
+template <int CENTRE>
+__device__ __forceinline__ void cell_offset2(int lc, uint32_t mc, float4 r, uint2 z0, uint2 z1,
+                                             float2 zhx, float2 zlx, float2 zhy, float2 zly,
+                                             float2 &dx, float2 &dy) {
+    if (CENTRE == 0) {
+        dx = add2(add2(zhx, bc2(-r.x)), add2(zlx, bc2(-r.y)));
+        dy = add2(add2(zhy, bc2(-r.z)), add2(zly, bc2(-r.w)));
+    } else {
+        const uint32_t cx = gather_bits16(mc), cy = gather_bits16(mc >> 1);
+        const int64_t half = int64_t(1) << (31 - lc);
+        const int64_t bx = ((int64_t)cx << (32 - lc)) + half, by = ((int64_t)cy << (32 - lc)) + half;
+        dx = make_float2((float)((int64_t)z0.x - bx), (float)((int64_t)z1.x - bx));
+        dy = make_float2((float)((int64_t)z0.y - by), (float)((int64_t)z1.y - by));
+    }
+}
+
+struct __align__(16) TravEntry {
+    uint32_t node, m0, m1, pad;
 };
 
-template <int CENTRE, int COUNT, int PPL>
-__global__ void __launch_bounds__(kTravWarps * 32, PPL == 1 ? 5 : (PPL == 2 ? 4 : 3))
+template <int CENTRE, int COUNT>
+__global__ void __launch_bounds__(kTravWarps * 32, 4)
     k_bh_traverse(int n, int L, const uint2 *__restrict__ z, const uint32_t *__restrict__ perm,
                   const float4 *__restrict__ rec, const float *__restrict__ recn,
                   DevScalars *sc, float2 *__restrict__ Frep, float *__restrict__ Zi) {
-    // stack entry: (level << 28) | Morton index of a node, and per lane slot
-    // the mask of the lanes whose point opens it
-    __shared__ TravEntry<PPL> s_stk[kTravWarps][kTravStack];
+    // stack entry: (level << 28) | Morton index of a node, and for each half of
+    // the warp's points the mask of the lanes whose point opens it
+    __shared__ TravEntry s_stk[kTravWarps][kTravStack];
     __shared__ float s_T[kMaxL + 2];
     __shared__ int s_off[kMaxL + 2];
     if (threadIdx.x < kMaxL + 2) {
@@ -83,62 +75,43 @@ __global__ void __launch_bounds__(kTravWarps * 32, PPL == 1 ? 5 : (PPL == 2 ? 4 
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int base = (blockIdx.x * kTravWarps + w) * 32 * PPL;
+    const int base = (blockIdx.x * kTravWarps + w) * 64;
     const int F = 32 - L;
-    bool valid[PPL];
-    unsigned act[PPL];
-    uint32_t ip[PPL], mi[PPL];
-    uint2 zi[PPL];
-    float zhx[PPL], zlx[PPL], zhy[PPL], zly[PPL], fx[PPL], fy[PPL], zs[PPL];
-#pragma unroll
-    for (int p = 0; p < PPL; p++) {
-        const int idx = base + 32 * p + lane;
-        valid[p] = idx < n;
-        act[p] = __ballot_sync(0xffffffffu, valid[p]);
-        ip[p] = valid[p] ? perm[idx] : 0u;
-        zi[p] = z[ip[p]];
-        mi[p] = morton2(zi[p].x >> F, zi[p].y >> F);
-        // z split at bit 16, both halves exact in float (see rec in common.cuh)
-        zhx[p] = (float)(zi[p].x & 0xffff0000u);
-        zlx[p] = (float)(zi[p].x & 0xffffu);
-        zhy[p] = (float)(zi[p].y & 0xffff0000u);
-        zly[p] = (float)(zi[p].y & 0xffffu);
-        fx[p] = 0.f;
-        fy[p] = 0.f;
-        zs[p] = 0.f;
-    }
-    if (act[0] == 0u) return;
-    const float sf0 = sc->sf[0], sf1 = sc->sf[1];
+    const int idx0 = base + lane, idx1 = base + 32 + lane;
+    const bool valid0 = idx0 < n, valid1 = idx1 < n;
+    const unsigned act0 = __ballot_sync(0xffffffffu, valid0);
+    const unsigned act1 = __ballot_sync(0xffffffffu, valid1);
+    if (act0 == 0u) return;
+    const uint32_t i0 = valid0 ? perm[idx0] : 0u, i1 = valid1 ? perm[idx1] : 0u;
+    const uint2 z0 = z[i0], z1 = z[i1];
+    const uint32_t mi0 = morton2(z0.x >> F, z0.y >> F), mi1 = morton2(z1.x >> F, z1.y >> F);
+    // z split at bit 16, both halves exact in float (see rec in common.cuh)
+    const float2 zhx = make_float2((float)(z0.x & 0xffff0000u), (float)(z1.x & 0xffff0000u));
+    const float2 zlx = make_float2((float)(z0.x & 0xffffu), (float)(z1.x & 0xffffu));
+    const float2 zhy = make_float2((float)(z0.y & 0xffff0000u), (float)(z1.y & 0xffff0000u));
+    const float2 zly = make_float2((float)(z0.y & 0xffffu), (float)(z1.y & 0xffffu));
+    const float2 sf0 = bc2(sc->sf[0]), sf1 = bc2(sc->sf[1]);
+    float2 fx = bc2(0.f), fy = bc2(0.f), zs = bc2(0.f);
     uint32_t n_acc = 0u, n_tst = 0u, n_stp = 0u, n_nod = 0u;
 
-    TravEntry<PPL> *stk = s_stk[w];
+    TravEntry *stk = s_stk[w];
     // The root contains every point: start with its four children.
-    if (lane == 0) {
-        TravEntry<PPL> e0;
-        e0.node = 0u;  // (level 0 << 28) | morton 0
-#pragma unroll
-        for (int p = 0; p < PPL; p++) e0.m[p] = act[p];
-        stk[0] = e0;
-    }
+    if (lane == 0) stk[0] = TravEntry{0u, act0, act1, 0u};  // (level 0 << 28) | morton 0
     int sp = 1;
     __syncwarp();
     bool overflow = false;
     while (sp > 0) {
         sp--;
-        const TravEntry<PPL> top = stk[sp];
+        const TravEntry top = stk[sp];
         __syncwarp();
         const uint32_t node = top.node;
         const int lc = (int)(node >> 28) + 1;  // level of the children
         const uint32_t m0 = (node & 0x0fffffffu) << 2;
         const int at = s_off[lc] + (int)m0;
         const float4 nv = __ldg(reinterpret_cast<const float4 *>(recn + at));
-        bool me[PPL];
-        uint32_t mine[PPL];
-#pragma unroll
-        for (int p = 0; p < PPL; p++) {
-            me[p] = (top.m[p] >> lane) & 1u;
-            mine[p] = mi[p] >> (2 * (L - lc));  // own cell at level lc
-        }
+        const bool me0 = (top.m0 >> lane) & 1u, me1 = (top.m1 >> lane) & 1u;
+        const int sh = 2 * (L - lc);
+        const uint32_t mine0 = mi0 >> sh, mine1 = mi1 >> sh;  // own cells at level lc
         const float Nc[4] = {nv.x, nv.y, nv.z, nv.w};
         if (COUNT) {
             n_nod++;
@@ -152,98 +125,44 @@ __global__ void __launch_bounds__(kTravWarps * 32, PPL == 1 ? 5 : (PPL == 2 ? 4 
                 const uint32_t mc = m0 + ch;
                 float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (CENTRE == 0) r = __ldg(rec + at + ch);
-                bool own[PPL];
-                bool any = false;
-#pragma unroll
-                for (int p = 0; p < PPL; p++) {
-                    own[p] = me[p] && (mine[p] == mc);
-                    any = any || own[p];
-                }
-                const bool any_own = __any_sync(0xffffffffu, any);
-                if constexpr (PPL % 2 == 0 && CENTRE == 0) {
-                    // the lane's points in pairs
-#pragma unroll
-                    for (int h = 0; h < PPL; h += 2) {
-                        float2 dx = add2(add2(make_float2(zhx[h], zhx[h + 1]), bc2(-r.x)),
-                                         add2(make_float2(zlx[h], zlx[h + 1]), bc2(-r.y)));
-                        float2 dy = add2(add2(make_float2(zhy[h], zhy[h + 1]), bc2(-r.z)),
-                                         add2(make_float2(zly[h], zly[h + 1]), bc2(-r.w)));
-                        float2 Nf = bc2(N);
-                        if (any_own) {  // own pixel: take the point out
-                            if (own[h]) {
-                                Nf.x = N - 1.0f;
-                                if (N > 1.0f) {
-                                    const float k = N / Nf.x;
-                                    dx.x *= k;
-                                    dy.x *= k;
-                                }
-                            }
-                            if (own[h + 1]) {
-                                Nf.y = N - 1.0f;
-                                if (N > 1.0f) {
-                                    const float k = N / Nf.y;
-                                    dx.y *= k;
-                                    dy.y *= k;
-                                }
-                            }
+                float2 dx, dy;
+                cell_offset2<CENTRE>(lc, mc, r, z0, z1, zhx, zlx, zhy, zly, dx, dy);
+                const bool own0 = me0 && (mine0 == mc), own1 = me1 && (mine1 == mc);
+                float2 Nf = bc2(N);
+                if (__any_sync(0xffffffffu, own0 || own1)) {  // own pixel: take the point out
+                    if (own0) {
+                        Nf.x = N - 1.0f;
+                        if (CENTRE == 0 && N > 1.0f) {
+                            const float k = N / Nf.x;
+                            dx.x *= k;
+                            dy.x *= k;
                         }
-                        dx = mul2(dx, bc2(sf0));
-                        dy = mul2(dy, bc2(sf1));
-                        const float2 d2 = fma2(dx, dx, mul2(dy, dy));
-                        const bool acc0 = me[h] && (Nf.x > 0.f), acc1 = me[h + 1] && (Nf.y > 0.f);
-                        if (COUNT) {
-                            n_tst += (me[h] ? 1u : 0u) + (me[h + 1] ? 1u : 0u);
-                            n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
-                        }
-                        const float2 w1 = add2(bc2(1.0f), d2);
-                        const float2 q =
-                            make_float2(__fdividef(1.0f, w1.x), __fdividef(1.0f, w1.y));
-                        const float2 Nq0 = mul2(Nf, q);
-                        const float2 Nq = make_float2(acc0 ? Nq0.x : 0.0f, acc1 ? Nq0.y : 0.0f);
-                        const float2 zs2 = add2(make_float2(zs[h], zs[h + 1]), Nq);
-                        const float2 Nq2 = mul2(Nq, q);
-                        const float2 fx2 = fma2(Nq2, dx, make_float2(fx[h], fx[h + 1]));
-                        const float2 fy2 = fma2(Nq2, dy, make_float2(fy[h], fy[h + 1]));
-                        zs[h] = zs2.x;
-                        zs[h + 1] = zs2.y;
-                        fx[h] = fx2.x;
-                        fx[h + 1] = fx2.y;
-                        fy[h] = fy2.x;
-                        fy[h + 1] = fy2.y;
                     }
-                } else {
-    #pragma unroll
-                    for (int p = 0; p < PPL; p++) {
-                        float dx, dy;
-                        cell_offset<CENTRE>(lc, mc, r, zi[p], zhx[p], zlx[p], zhy[p], zly[p], dx, dy);
-                        float Nf = N;
-                        if (any_own) {  // own pixel: take point i out
-                            if (own[p]) {
-                                Nf = N - 1.0f;
-                                if (CENTRE == 0 && N > 1.0f) {
-                                    const float k = N / Nf;
-                                    dx *= k;
-                                    dy *= k;
-                                }
-                            }
+                    if (own1) {
+                        Nf.y = N - 1.0f;
+                        if (CENTRE == 0 && N > 1.0f) {
+                            const float k = N / Nf.y;
+                            dx.y *= k;
+                            dy.y *= k;
                         }
-                        dx *= sf0;
-                        dy *= sf1;
-                        const float d2 = fmaf(dx, dx, dy * dy);
-                        const bool acc = me[p] && (Nf > 0.f);
-                        if (COUNT) {
-                            n_tst += me[p] ? 1u : 0u;
-                            n_acc += acc ? 1u : 0u;
-                        }
-                        const float q = __fdividef(1.0f, 1.0f + d2);
-                        const float Nq = acc ? Nf * q : 0.0f;
-                        zs[p] += Nq;
-                        const float Nq2 = Nq * q;
-                        fx[p] = fmaf(Nq2, dx, fx[p]);
-                        fy[p] = fmaf(Nq2, dy, fy[p]);
                     }
-
                 }
+                dx = mul2(dx, sf0);
+                dy = mul2(dy, sf1);
+                const float2 d2 = fma2(dx, dx, mul2(dy, dy));
+                const bool acc0 = me0 && (Nf.x > 0.f), acc1 = me1 && (Nf.y > 0.f);
+                if (COUNT) {
+                    n_tst += (me0 ? 1u : 0u) + (me1 ? 1u : 0u);
+                    n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
+                }
+                const float2 w1 = add2(bc2(1.0f), d2);
+                const float2 q = make_float2(__fdividef(1.0f, w1.x), __fdividef(1.0f, w1.y));
+                const float2 Nq0 = mul2(Nf, q);
+                const float2 Nq = make_float2(acc0 ? Nq0.x : 0.0f, acc1 ? Nq0.y : 0.0f);
+                zs = add2(zs, Nq);
+                const float2 Nq2 = mul2(Nq, q);
+                fx = fma2(Nq2, dx, fx);
+                fy = fma2(Nq2, dy, fy);
             }
         } else {
             const float Tl = s_T[lc];
@@ -254,81 +173,33 @@ __global__ void __launch_bounds__(kTravWarps * 32, PPL == 1 ? 5 : (PPL == 2 ? 4 
                 const uint32_t mc = m0 + ch;
                 float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (CENTRE == 0) r = __ldg(rec + at + ch);
-                unsigned ob[PPL];
-                unsigned oball = 0u;
-                if constexpr (PPL % 2 == 0 && CENTRE == 0) {
-                    // the lane's points in pairs
-#pragma unroll
-                    for (int h = 0; h < PPL; h += 2) {
-                        float2 dx = add2(add2(make_float2(zhx[h], zhx[h + 1]), bc2(-r.x)),
-                                         add2(make_float2(zlx[h], zlx[h + 1]), bc2(-r.y)));
-                        float2 dy = add2(add2(make_float2(zhy[h], zhy[h + 1]), bc2(-r.z)),
-                                         add2(make_float2(zly[h], zly[h + 1]), bc2(-r.w)));
-                        dx = mul2(dx, bc2(sf0));
-                        dy = mul2(dy, bc2(sf1));
-                        const float2 d2 = fma2(dx, dx, mul2(dy, dy));
-                        const bool far0 = (d2.x > Tl) && (mine[h] != mc);
-                        const bool far1 = (d2.y > Tl) && (mine[h + 1] != mc);
-                        const bool acc0 = me[h] && far0, acc1 = me[h + 1] && far1;
-                        if (COUNT) {
-                            n_tst += (me[h] ? 1u : 0u) + (me[h + 1] ? 1u : 0u);
-                            n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
-                        }
-                        const float2 w1 = add2(bc2(1.0f), d2);
-                        const float2 q =
-                            make_float2(__fdividef(1.0f, w1.x), __fdividef(1.0f, w1.y));
-                        const float2 Nq0 = mul2(bc2(N), q);
-                        const float2 Nq = make_float2(acc0 ? Nq0.x : 0.0f, acc1 ? Nq0.y : 0.0f);
-                        const float2 zs2 = add2(make_float2(zs[h], zs[h + 1]), Nq);
-                        const float2 Nq2 = mul2(Nq, q);
-                        const float2 fx2 = fma2(Nq2, dx, make_float2(fx[h], fx[h + 1]));
-                        const float2 fy2 = fma2(Nq2, dy, make_float2(fy[h], fy[h + 1]));
-                        zs[h] = zs2.x;
-                        zs[h + 1] = zs2.y;
-                        fx[h] = fx2.x;
-                        fx[h + 1] = fx2.y;
-                        fy[h] = fy2.x;
-                        fy[h + 1] = fy2.y;
-                        ob[h] = __ballot_sync(0xffffffffu, me[h] && !far0);
-                        ob[h + 1] = __ballot_sync(0xffffffffu, me[h + 1] && !far1);
-                        oball |= ob[h] | ob[h + 1];
-                    }
-                } else {
-    #pragma unroll
-                    for (int p = 0; p < PPL; p++) {
-                        float dx, dy;
-                        cell_offset<CENTRE>(lc, mc, r, zi[p], zhx[p], zlx[p], zhy[p], zly[p], dx, dy);
-                        dx *= sf0;
-                        dy *= sf1;
-                        const float d2 = fmaf(dx, dx, dy * dy);
-                        const bool contains = (mine[p] == mc);
-                        const bool far = (d2 > Tl) && !contains;
-                        const bool acc = me[p] && far;
-                        if (COUNT) {
-                            n_tst += me[p] ? 1u : 0u;
-                            n_acc += acc ? 1u : 0u;
-                        }
-                        const float q = __fdividef(1.0f, 1.0f + d2);
-                        const float Nq = acc ? N * q : 0.0f;
-                        zs[p] += Nq;
-                        const float Nq2 = Nq * q;
-                        fx[p] = fmaf(Nq2, dx, fx[p]);
-                        fy[p] = fmaf(Nq2, dy, fy[p]);
-                        ob[p] = __ballot_sync(0xffffffffu, me[p] && !far);
-                        oball |= ob[p];
-                    }
+                float2 dx, dy;
+                cell_offset2<CENTRE>(lc, mc, r, z0, z1, zhx, zlx, zhy, zly, dx, dy);
+                dx = mul2(dx, sf0);
+                dy = mul2(dy, sf1);
+                const float2 d2 = fma2(dx, dx, mul2(dy, dy));
+                const bool far0 = (d2.x > Tl) && (mine0 != mc);
+                const bool far1 = (d2.y > Tl) && (mine1 != mc);
+                const bool acc0 = me0 && far0, acc1 = me1 && far1;
+                if (COUNT) {
+                    n_tst += (me0 ? 1u : 0u) + (me1 ? 1u : 0u);
+                    n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
                 }
-                if (oball) {
+                const float2 w1 = add2(bc2(1.0f), d2);
+                const float2 q = make_float2(__fdividef(1.0f, w1.x), __fdividef(1.0f, w1.y));
+                const float2 Nq0 = mul2(bc2(N), q);
+                const float2 Nq = make_float2(acc0 ? Nq0.x : 0.0f, acc1 ? Nq0.y : 0.0f);
+                zs = add2(zs, Nq);
+                const float2 Nq2 = mul2(Nq, q);
+                fx = fma2(Nq2, dx, fx);
+                fy = fma2(Nq2, dy, fy);
+                const unsigned ob0 = __ballot_sync(0xffffffffu, me0 && !far0);
+                const unsigned ob1 = __ballot_sync(0xffffffffu, me1 && !far1);
+                if (ob0 | ob1) {
                     if (sp >= kTravStack) {
                         overflow = true;
                     } else {
-                        if (lane == 0) {
-                            TravEntry<PPL> e;
-                            e.node = ((uint32_t)lc << 28) | mc;
-#pragma unroll
-                            for (int p = 0; p < PPL; p++) e.m[p] = ob[p];
-                            stk[sp] = e;
-                        }
+                        if (lane == 0) stk[sp] = TravEntry{((uint32_t)lc << 28) | mc, ob0, ob1, 0u};
                         sp++;
                     }
                 }
@@ -337,12 +208,14 @@ __global__ void __launch_bounds__(kTravWarps * 32, PPL == 1 ? 5 : (PPL == 2 ? 4 
         __syncwarp();
         if (overflow) break;
     }
-#pragma unroll
-    for (int p = 0; p < PPL; p++)
-        if (valid[p]) {
-            Frep[ip[p]] = make_float2(fx[p], fy[p]);
-            Zi[ip[p]] = zs[p];
-        }
+    if (valid0) {
+        Frep[i0] = make_float2(fx.x, fy.x);
+        Zi[i0] = zs.x;
+    }
+    if (valid1) {
+        Frep[i1] = make_float2(fx.y, fy.y);
+        Zi[i1] = zs.y;
+    }
     if (overflow && lane == 0) atomicOr(&sc->err, (unsigned)PXSNE_DEVERR_STACK);
     if (COUNT) {
 #pragma unroll
@@ -515,23 +388,22 @@ __global__ void __launch_bounds__(512)
 
 static cudaError_t traverse(pxsne_ctx *c, cudaStream_t st, bool count) {
     const int n = (int)c->n;
-    constexpr int P = kTravPPL;
-    const int per_block = kTravWarps * 32 * P;
+    const int per_block = kTravWarps * 64;
     const dim3 g((n + per_block - 1) / per_block), b(kTravWarps * 32);
     if (c->p.centre_mode == 0) {
         if (count)
-            k_bh_traverse<0, 1, P><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn,
-                                                    c->sc, c->Frep, c->Zi);
+            k_bh_traverse<0, 1><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
+                                                 c->Frep, c->Zi);
         else
-            k_bh_traverse<0, 0, P><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn,
-                                                    c->sc, c->Frep, c->Zi);
+            k_bh_traverse<0, 0><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
+                                                 c->Frep, c->Zi);
     } else {
         if (count)
-            k_bh_traverse<1, 1, P><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn,
-                                                    c->sc, c->Frep, c->Zi);
+            k_bh_traverse<1, 1><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
+                                                 c->Frep, c->Zi);
         else
-            k_bh_traverse<1, 0, P><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn,
-                                                    c->sc, c->Frep, c->Zi);
+            k_bh_traverse<1, 0><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
+                                                 c->Frep, c->Zi);
     }
     return cudaGetLastError();
 }
