@@ -49,11 +49,12 @@ __global__ void __launch_bounds__(256)
     const double Z = sc->Z;
     const float invZ = Z > 0.0 ? (float)(1.0 / Z) : 0.0f;
     const double is0 = sc->inv_s[0], is1 = sc->inv_s[1];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     i64 mnx = 0x7fffffffffffffffll, mny = 0x7fffffffffffffffll;
     i64 mxx = (i64)0x8000000000000000ull, mxy = (i64)0x8000000000000000ull;
     unsigned err = 0u;
-    if (i < n) {
+    // a fixed grid strides over the points, so that few CTAs meet in the
+    // min/max atomics below
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float2 fr = Frep[i], fa = Fattr[i];
         float2 uu = u[i], gg = gains[i];
         const uint2 zz = z[i];
@@ -63,8 +64,10 @@ __global__ void __launch_bounds__(256)
         u[i] = uu;
         gains[i] = gg;
         zhat[i] = zh;
-        mnx = mxx = zh.x;
-        mny = mxy = zh.y;
+        mnx = min(mnx, zh.x);
+        mxx = max(mxx, zh.x);
+        mny = min(mny, zh.y);
+        mxy = max(mxy, zh.y);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -104,8 +107,12 @@ cudaError_t launch_update(pxsne_ctx *c, cudaEvent_t *marks) {
         cudaError_t e = cudaEventRecord(marks[KG_UPDATE], c->stream);
         if (e) return e;
     }
-    k_update<<<(n + 255) / 256, 256, 0, c->stream>>>(n, p, c->z, c->Frep, c->Fattr, c->u,
-                                                     c->gains, c->zhat, c->sc);
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int need = (n + 255) / 256, cap = 8 * (sms > 0 ? sms : 152);
+    k_update<<<need < cap ? need : cap, 256, 0, c->stream>>>(n, p, c->z, c->Frep, c->Fattr, c->u,
+                                                             c->gains, c->zhat, c->sc);
     return cudaGetLastError();
 }
 
