@@ -68,6 +68,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of the ranks' values of x (x itself without a process
+    group): the job's time is its slowest replica's."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, seconds, ws):
+    """Whole-job throughput of ws replicas that each processed units_per_rank
+    units, timed as the slowest replica's seconds."""
+    return ws * units_per_rank / seconds
+
+
 # ---------------------------------------------------------------- clocks
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -418,11 +435,8 @@ def run_gpu(args):
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
     ctx.sync()
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * args.steps / (ms / 1000.0)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = job_rate(args.steps, ms / 1000.0, ws)
     kl_after = ctx.kl()
 
     # per-kernel breakdown: the same K iterations again from t = 0, with CUDA
@@ -477,13 +491,9 @@ def run_gpu(args):
             ctx2.step(1)
             ctx2.get_Y(Yh, Ph)
         t1 = time.perf_counter()
-        el = t1 - t0
-        if dist:
-            t = torch.tensor([el], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            el = float(t.item())
+        el = max_over_ranks(t1 - t0, dist, "cuda")
         ctx2.close()
-        e2e = {"value": ws * args.steps / el, "unit": "it/s",
+        e2e = {"value": job_rate(args.steps, el, ws), "unit": "it/s",
                "h2d_bytes_per_step": int((X.nbytes + Y0.nbytes) / args.steps),
                "d2h_bytes_per_step": int(Yh.numel() * 4 + Ph.numel() * 4),
                "wall_s": el, "includes": "P construction + init + K x (step + get_Y)"}
