@@ -239,6 +239,16 @@ int pxsne_get_knn_counters(pxsne_ctx *ctx, uint64_t *exact, uint64_t *inserted, 
  * context's stream).  PXSNE_E_STATE if no search has run.  Synchronises. */
 int pxsne_get_knn_time(pxsne_ctx *ctx, double *search_ms);
 
+/* Test hook of the bounded waits (no counterpart in the paper): one kernel
+ * waits on an mbarrier that nothing arrives at, for at most `polls` polls of
+ * at most 100 ns each (1 <= polls <= 65536), the way the tensor-core kernels
+ * wait on their pipelines; it then sets PXSNE_DEVERR_TIMEOUT and returns.
+ * flags (may be NULL) receives the device error flags read back.  Returns
+ * PXSNE_E_DEVICE when the wait ran out (the expected outcome), PXSNE_OK if it
+ * did not, PXSNE_E_ARG on a bad polls.  The context stays usable.
+ * Synchronises. */
+int pxsne_test_bounded_wait(pxsne_ctx *ctx, int32_t polls, uint32_t *flags);
+
 /* Total bytes of device memory the context holds. */
 int64_t pxsne_device_bytes(const pxsne_ctx *ctx);
 

@@ -767,6 +767,20 @@ static size_t knn_tc_smem(int Dp, int k) {
            (size_t)kTcRows * (k | 1) * 8 + (size_t)4 * kTcQueue * (4 + 4 + 2) + 1024;
 }
 
+// The bounded wait of the pipelines above, on an mbarrier that nothing
+// arrives at: it must give up after `polls` polls and flag the time-out.
+__global__ void k_wait_probe(int polls, unsigned *err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) tc::mbar_init(&bar, 1);
+    __syncthreads();
+    const bool got = __all_sync(0xffffffffu, tc::mbar_wait_sleep(&bar, 0u, polls, 100u));
+    if (!got && threadIdx.x == 0) atomicOr(err, (unsigned)PXSNE_DEVERR_TIMEOUT);
+}
+
+void launch_wait_probe(pxsne_ctx *c, int polls) {
+    k_wait_probe<<<1, 32, 0, c->stream>>>(polls, &c->sc->err);
+}
+
 // Timing events around the search kernel (created on first use).
 static cudaError_t knn_mark(pxsne_ctx *c, int which, cudaStream_t st) {
     cudaError_t e;
@@ -1013,7 +1027,9 @@ __global__ void __launch_bounds__(256)
         if (H > target) {
             lo = beta;
             has_lo = true;
-            beta = has_hi ? 0.5f * (beta + hi) : 2.f * beta;
+            // capped below FP32 overflow: a row whose target is out of reach
+            // (all distances tied) keeps finite, uniform weights
+            beta = has_hi ? 0.5f * (beta + hi) : fminf(2.f * beta, 1.7014118e38f);
         } else {
             hi = beta;
             has_hi = true;

@@ -798,6 +798,13 @@ int pxsne_get_knn_counters(pxsne_ctx *c, uint64_t *exact, uint64_t *inserted, in
     return PXSNE_OK;
 }
 
+int pxsne_test_bounded_wait(pxsne_ctx *c, int32_t polls, uint32_t *flags) {
+    if (!c || polls < 1 || polls > 65536) return fail(c, PXSNE_E_ARG, "polls outside [1, 65536]");
+    launch_wait_probe(c, polls);
+    CK(c, cudaGetLastError());
+    return check_device(c, flags);
+}
+
 int pxsne_get_knn_time(pxsne_ctx *c, double *search_ms) {
     if (!c || !search_ms) return PXSNE_E_ARG;
     if (!c->knn_timed) return fail(c, PXSNE_E_STATE, "no neighbour search has run");

@@ -229,6 +229,9 @@ cudaError_t build_symmetric_csr(pxsne_ctx *c, const int32_t *idx, const float *p
                                 int64_t n, int32_t k, std::string &err);
 cudaError_t launch_level_counts(pxsne_ctx *c, int level, uint32_t *cnt);
 cudaError_t launch_morton_keys(pxsne_ctx *c, uint32_t *keys);
+// One CTA waiting on an mbarrier that nothing arrives at (bounded; sets
+// PXSNE_DEVERR_TIMEOUT when the polls run out).
+void launch_wait_probe(pxsne_ctx *c, int polls);
 cudaError_t launch_nbr_precision(pxsne_ctx *c, int k, const int32_t *knn_hd, int kh,
                                  int32_t *hits, unsigned long long *total);
 }  // namespace pxsne

@@ -94,6 +94,18 @@ def test_perplexity_equal_distances_closed_form():
     np.testing.assert_allclose(H, math.log(30), rtol=1e-14)
 
 
+def test_perplexity_unreachable_target():
+    # all k distances tied but a perplexity below k: H = ln k whatever beta,
+    # so no beta reaches the target; every row is reported and keeps the
+    # uniform weights 1/k
+    d2 = np.zeros((3, 90))
+    d2[1] = 4.0
+    p, beta, H, bad = oracle.perplexity(d2, 30.0)
+    assert bad == 3
+    np.testing.assert_allclose(p, 1.0 / 90, rtol=1e-14)
+    np.testing.assert_allclose(H, math.log(90), rtol=1e-14)
+
+
 def test_perplexity_scale_invariance():
     rng = np.random.default_rng(3)
     X = rng.standard_normal((400, 10)).astype(np.float32)
