@@ -177,7 +177,7 @@ def group_bytes(n, nnz, L):
 # DRAM bytes per launch from one ncu capture of the current kernels at full size
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/traffic_gmm128_n1M.md);
 # to be set to None whenever the kernel changes
-TRAFFIC_BYTES = {"k_bh_traverse": 46.60e6, "k_attract": 1.293e9, "k_snap_hist": 52.62e6,
+TRAFFIC_BYTES = {"k_bh_traverse": None, "k_attract": None, "k_snap_hist": 52.62e6,
                  "k_pyr_pass": 153.17e6}
 
 FLOP_TEST = 10    # offset, d^2 and criterion of one tested cell

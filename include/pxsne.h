@@ -210,17 +210,18 @@ int pxsne_get_forces(pxsne_ctx *ctx, float *Frep, float *Zi, float *Fattr, doubl
 /* Tracing: run `iters` >= 1 iterations like pxsne_step, without the CUDA
  * graph, with CUDA events recorded on the context's stream around each kernel
  * group of an iteration (no synchronisation between iterations).  group_ms
- * (n_groups >= 7 slots) receives the summed milliseconds of each group over
+ * (n_groups >= 8 slots) receives the summed milliseconds of each group over
  * all iterations and total_ms (may be NULL) the elapsed time of the whole
  * run.  Group g is named by pxsne_kernel_group_name(g).  Synchronises. */
 int pxsne_step_profiled(pxsne_ctx *ctx, int32_t iters, double *group_ms, int32_t n_groups,
                         double *total_ms);
 
-/* Name of kernel group g (0 <= g < 7), or NULL. */
+/* Name of kernel group g (0 <= g < 8), or NULL. */
 const char *pxsne_kernel_group_name(int32_t g);
 
-/* Work counters of the last Barnes-Hut traversal run by the sequential
- * schedule (pxsne_init, pxsne_set_state, pxsne_step_profiled): n_accept =
+/* Work counters of the Barnes-Hut traversal of the state set by pxsne_init or
+ * pxsne_set_state, or of the final state of pxsne_step_profiled (counted by
+ * one extra traversal after its timed groups): n_accept =
  * accepted (point, cell) pairs (the interactions of Eq. bh_criteria), n_test =
  * tested pairs (accepted + opened + own-pixel), n_warp_steps = warp-level
  * (node, non-empty child) steps, n_nodes = stack entries popped.  Any pointer

@@ -535,6 +535,8 @@ int pxsne_step_profiled(pxsne_ctx *c, int32_t iters, double *group_ms, int32_t n
     }
     if (!rc) {
         CK(c, cudaEventRecord(*t1, c->stream));
+        // work counters of the final state, outside the timed groups
+        CK(c, launch_count_traversal(c));
         CK(c, cudaEventSynchronize(*t1));
         for (int g = 0; g < KG_COUNT; g++) group_ms[g] = 0.0;
         for (int32_t k = 0; k < iters; k++) {

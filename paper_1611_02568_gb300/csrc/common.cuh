@@ -210,6 +210,7 @@ cudaError_t launch_forces(pxsne_ctx *c, cudaEvent_t *marks = nullptr);
 cudaError_t launch_snap(pxsne_ctx *c, bool rescale, cudaEvent_t *marks = nullptr);
 cudaError_t launch_pyramid(pxsne_ctx *c, bool rescale, cudaEvent_t *marks = nullptr);
 cudaError_t launch_attract(pxsne_ctx *c, cudaStream_t st);
+cudaError_t launch_count_traversal(pxsne_ctx *c);
 // Renumber P's rows and columns in the Morton order of the last tree (perm)
 // into rp2/col2/val2 and refresh aperm, ainv and zp.
 constexpr int kRelabelEvery = 25;

@@ -109,6 +109,13 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
         const uint32_t m0 = (node & 0x0fffffffu) << 2;
         const int at = s_off[lc] + (int)m0;
         const float4 nv = __ldg(reinterpret_cast<const float4 *>(recn + at));
+        // the four children's records are requested together with their
+        // counts (one latency per node instead of two)
+        float4 rr[4];
+        if (CENTRE == 0) {
+#pragma unroll
+            for (int ch = 0; ch < 4; ch++) rr[ch] = __ldg(rec + at + ch);
+        }
         const bool me0 = (top.m0 >> lane) & 1u, me1 = (top.m1 >> lane) & 1u;
         const int sh = 2 * (L - lc);
         const uint32_t mine0 = mi0 >> sh, mine1 = mi1 >> sh;  // own cells at level lc
@@ -124,7 +131,7 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
                 if (N == 0.f) continue;
                 const uint32_t mc = m0 + ch;
                 float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (CENTRE == 0) r = __ldg(rec + at + ch);
+                if (CENTRE == 0) r = rr[ch];
                 float2 dx, dy;
                 cell_offset2<CENTRE>(lc, mc, r, z0, z1, zhx, zlx, zhy, zly, dx, dy);
                 const bool own0 = me0 && (mine0 == mc), own1 = me1 && (mine1 == mc);
@@ -172,7 +179,7 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
                 if (N == 0.f) continue;
                 const uint32_t mc = m0 + ch;
                 float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (CENTRE == 0) r = __ldg(rec + at + ch);
+                if (CENTRE == 0) r = rr[ch];
                 float2 dx, dy;
                 cell_offset2<CENTRE>(lc, mc, r, z0, z1, zhx, zlx, zhy, zly, dx, dy);
                 dx = mul2(dx, sf0);
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
 // keeps long rows from stalling short ones).  It runs over the relabelled copy
 // of P (rows and columns in the Morton order of a recent state), so a row's
 // gathered positions zp[j] lie close together in memory, and writes each row's
-// force back under the point's own index.  Each lane keeps two entries in
+// force back under the point's own index.  Each lane keeps four entries in
 // flight; P is streamed with evict-first loads so that the positions stay in
 // L2.  z_i - z_j is formed exactly in float from the 16-bit halves of the
 // fixed-point coordinates (both differences are exact; one final rounding).
@@ -247,7 +254,7 @@ __global__ void __launch_bounds__(256)
               const float *__restrict__ val, const uint2 *__restrict__ z,
               const uint32_t *__restrict__ aperm, const DevScalars *__restrict__ sc,
               float2 *__restrict__ Fattr) {
-    constexpr int U = 2;
+    constexpr int U = 4;
     const int lane = threadIdx.x & 31;
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row >= n) return;
@@ -437,6 +444,11 @@ cudaError_t launch_relabel(pxsne_ctx *c, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// The traversal of the current tree again, with the work counters (the
+// tree's snap kernel reset them); Frep and Zi are rewritten with the same
+// values.
+cudaError_t launch_count_traversal(pxsne_ctx *c) { return traverse(c, c->stream, true); }
+
 cudaError_t launch_traverse_zsum(pxsne_ctx *c) {
     cudaError_t e = traverse(c, c->stream, false);
     if (e) return e;
@@ -448,9 +460,9 @@ cudaError_t launch_forces(pxsne_ctx *c, cudaEvent_t *marks) {
     cudaStream_t st = c->stream;
     cudaError_t e;
     if (marks && (e = cudaEventRecord(marks[KG_TRAVERSE], st))) return e;
-    // the work counters are kept by the sequential (initial-state and
-    // profiled) schedule only
-    if ((e = traverse(c, st, true))) return e;
+    // the initial state's traversal keeps the work counters; a timed one is
+    // the kernel of the iteration itself
+    if ((e = traverse(c, st, marks == nullptr))) return e;
     if (marks && (e = cudaEventRecord(marks[KG_ATTRACT], st))) return e;
     if ((e = launch_attract(c, st))) return e;
     if (marks && (e = cudaEventRecord(marks[KG_ZSUM], st))) return e;

@@ -350,3 +350,34 @@ def test_pca_matches_oracle(px):
     # projections agree up to the (fixed) signs of the leading components
     rel = np.linalg.norm(Z[:, :10] - Zo[:, :10]) / np.linalg.norm(Zo[:, :10])
     assert rel < 1e-3
+
+
+def test_profiled_run_and_work_counters(px, gauss):
+    """pxsne_step_profiled times the iteration's own kernels and counts the
+    final state's traversal afterwards: its counters equal those of the same
+    state set again, and the accepted pairs equal the oracle's count."""
+    X, P, Y0, _ = gauss
+    with make_ctx(px, L=9) as ctx:
+        ctx.set_P(P.row_ptr, P.col, P.val.astype(np.float32))
+        ctx.init(Y0)
+        groups, total = ctx.step_profiled(7)
+        assert list(groups) == ["k_relabel", "k_update", "k_snap_hist", "k_pyr_pass",
+                                "k_perm_scatter", "k_bh_traverse", "k_attract", "k_zsum"]
+        assert all(v >= 0.0 for v in groups.values()) and groups["k_bh_traverse"] > 0.0
+        assert sum(groups.values()) <= total * 1.001 + 1e-3
+        c1 = ctx.counters()
+        F1 = ctx.get_forces()
+        z, s, u, g, t = ctx.get_state()
+        ctx.set_state(z, s, u, g, t)
+        c2 = ctx.counters()
+        # per-point counts are the same; warp steps and nodes depend on how
+        # points within a pixel are grouped into warps, which follows the
+        # order of the previous tree (identity order after set_state)
+        assert c2[:2] == c1[:2]
+        assert c2[2] == pytest.approx(c1[2], rel=0.01) and c2[3] == pytest.approx(c1[3], rel=0.01)
+        F2 = ctx.get_forces()
+        for a, b in zip(F1[:3], F2[:3]):
+            assert np.array_equal(a, b)
+    _, _, acc = oracle.bh_repulsion(z, s, 9, 0.5)
+    assert c1[0] == pytest.approx(int(acc.sum()), rel=1e-4)
+    assert c1[1] >= c1[0] and c1[2] > 0 and c1[3] > 0
