@@ -18,7 +18,7 @@ typedef long long i64;
 constexpr int kMaxL = 14;           // screen up to 2^14 x 2^14 (Morton keys < 2^28)
 constexpr int64_t kMaxN = 1 << 24;  // cell counts are exact floats below 2^24
 constexpr int kTravWarps = 8;       // warps per CTA in the traversal
-constexpr int kTravStack = 64;      // entries per warp; depth needs <= 3L + 1
+constexpr int kTravStack = 48;      // entries per warp; depth <= 3L - 2 <= 40
 constexpr int kPyrK = 5;            // pyramid levels reduced per CTA pass
 constexpr double kR = 4294967296.0; // 2^32 ulps per axis
 
