@@ -59,7 +59,7 @@ struct __align__(16) TravEntry {
     uint32_t node, m0, m1, pad;
 };
 
-template <int CENTRE, int COUNT>
+template <int CENTRE, int COUNT, bool OWN>
 __global__ void __launch_bounds__(kTravWarps * 32, 4)
     k_bh_traverse(int n, int L, const uint2 *__restrict__ z, const uint32_t *__restrict__ perm,
                   const float4 *__restrict__ rec, const float *__restrict__ recn,
@@ -117,14 +117,13 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
             for (int ch = 0; ch < 4; ch++) rr[ch] = __ldg(rec + at + ch);
         }
         const bool me0 = (top.m0 >> lane) & 1u, me1 = (top.m1 >> lane) & 1u;
-        const int sh = 2 * (L - lc);
-        const uint32_t mine0 = mi0 >> sh, mine1 = mi1 >> sh;  // own cells at level lc
         const float Nc[4] = {nv.x, nv.y, nv.z, nv.w};
         if (COUNT) {
             n_nod++;
             n_stp += (nv.x != 0.f) + (nv.y != 0.f) + (nv.z != 0.f) + (nv.w != 0.f);
         }
         if (lc == L) {
+            const uint32_t mine0 = mi0, mine1 = mi1;  // own pixels
 #pragma unroll
             for (int ch = 0; ch < 4; ch++) {
                 const float N = Nc[ch];
@@ -173,6 +172,16 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
             }
         } else {
             const float Tl = s_T[lc];
+            // a point's own cell: opened by the criterion itself when theta < 1
+            // (the point and the centre of mass lie in the cell, so d <= r_c <
+            // r_c / theta); tested explicitly otherwise
+            const int sh = 2 * (L - lc);
+            const uint32_t mine0 = OWN ? mi0 >> sh : 0xffffffffu, mine1 = OWN ? mi1 >> sh : 0xffffffffu;
+            // room for the (at most four) entries this node may push
+            if (sp + 4 > kTravStack) {
+                overflow = true;
+                break;
+            }
 #pragma unroll
             for (int ch = 0; ch < 4; ch++) {
                 const float N = Nc[ch];
@@ -185,8 +194,8 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
                 dx = mul2(dx, sf0);
                 dy = mul2(dy, sf1);
                 const float2 d2 = fma2(dx, dx, mul2(dy, dy));
-                const bool far0 = (d2.x > Tl) && (mine0 != mc);
-                const bool far1 = (d2.y > Tl) && (mine1 != mc);
+                const bool far0 = (d2.x > Tl) && (!OWN || mine0 != mc);
+                const bool far1 = (d2.y > Tl) && (!OWN || mine1 != mc);
                 const bool acc0 = me0 && far0, acc1 = me1 && far1;
                 if (COUNT) {
                     n_tst += (me0 ? 1u : 0u) + (me1 ? 1u : 0u);
@@ -202,14 +211,9 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
                 fy = fma2(Nq2, dy, fy);
                 const unsigned ob0 = __ballot_sync(0xffffffffu, me0 && !far0);
                 const unsigned ob1 = __ballot_sync(0xffffffffu, me1 && !far1);
-                if (ob0 | ob1) {
-                    if (sp >= kTravStack) {
-                        overflow = true;
-                    } else {
-                        if (lane == 0) stk[sp] = TravEntry{((uint32_t)lc << 28) | mc, ob0, ob1, 0u};
-                        sp++;
-                    }
-                }
+                // written in any case above the top; kept if some point opens it
+                if (lane == 0) stk[sp] = TravEntry{((uint32_t)lc << 28) | mc, ob0, ob1, 0u};
+                sp += (ob0 | ob1) != 0u;
             }
         }
         __syncwarp();
@@ -393,24 +397,24 @@ __global__ void __launch_bounds__(512)
     }
 }
 
-static cudaError_t traverse(pxsne_ctx *c, cudaStream_t st, bool count) {
+template <int CENTRE, int COUNT, bool OWN>
+static void traverse_as(pxsne_ctx *c, cudaStream_t st) {
     const int n = (int)c->n;
     const int per_block = kTravWarps * 64;
-    const dim3 g((n + per_block - 1) / per_block), b(kTravWarps * 32);
+    k_bh_traverse<CENTRE, COUNT, OWN><<<(n + per_block - 1) / per_block, kTravWarps * 32, 0, st>>>(
+        n, c->L, c->z, c->perm, c->rec, c->recn, c->sc, c->Frep, c->Zi);
+}
+
+static cudaError_t traverse(pxsne_ctx *c, cudaStream_t st, bool count) {
+    // the own-cell test is redundant below theta = 1 (with a margin for the
+    // rounding of d^2)
+    const bool own = c->p.theta >= 0.999f;
     if (c->p.centre_mode == 0) {
-        if (count)
-            k_bh_traverse<0, 1><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
-                                                 c->Frep, c->Zi);
-        else
-            k_bh_traverse<0, 0><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
-                                                 c->Frep, c->Zi);
+        if (count) own ? traverse_as<0, 1, true>(c, st) : traverse_as<0, 1, false>(c, st);
+        else own ? traverse_as<0, 0, true>(c, st) : traverse_as<0, 0, false>(c, st);
     } else {
-        if (count)
-            k_bh_traverse<1, 1><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
-                                                 c->Frep, c->Zi);
-        else
-            k_bh_traverse<1, 0><<<g, b, 0, st>>>(n, c->L, c->z, c->perm, c->rec, c->recn, c->sc,
-                                                 c->Frep, c->Zi);
+        if (count) own ? traverse_as<1, 1, true>(c, st) : traverse_as<1, 1, false>(c, st);
+        else own ? traverse_as<1, 0, true>(c, st) : traverse_as<1, 0, false>(c, st);
     }
     return cudaGetLastError();
 }

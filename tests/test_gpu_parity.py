@@ -102,8 +102,12 @@ def test_forces_match_oracle(px, gauss, theta):
     with make_ctx(px, L=L, theta=theta) as ctx:
         inject(ctx, P, st)
         Frep, Zi, Fattr, Z = ctx.get_forces()
-    oF, oZi, _ = oracle.bh_repulsion(st.z, st.s, L, theta)
+        n_acc = ctx.counters()[0]
+    oF, oZi, oacc = oracle.bh_repulsion(st.z, st.s, L, theta)
     oA = oracle.attraction(P, st.z, st.s)
+    # the same (point, cell) interactions, up to FP32 d^2 at the criterion's
+    # boundary
+    assert n_acc == pytest.approx(int(oacc.sum()), rel=1e-4)
     assert rel(Frep, oF) <= FORCE_TOL
     assert rel(Zi, oZi) <= FORCE_TOL
     assert rel(Fattr, oA) <= FORCE_TOL
