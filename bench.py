@@ -52,8 +52,10 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="points (debug only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-rows", type=int, default=40000,
+    ap.add_argument("--cpu-rows", type=int, default=200000,
                     help="rows of the oracle sample (CPU baseline)")
+    ap.add_argument("--no-studies", action="store_true",
+                    help="skip the time-to-KL-target and screen-size studies")
     ap.add_argument("--no-warmstart", action="store_true",
                     help="skip the learned warm-start experiment")
     ap.add_argument("--warm-seeds", type=int, default=20)
@@ -224,6 +226,84 @@ def oracle_sample(_unused, Y0, rows, L, theta, seed=0):
     det = {"tree_s": t1 - t0, "bh_sample_s": t2 - t1, "attr_sample_s": t3 - t2,
            "update_rescale_s": t4 - t3, "rows": m, "scale": scale}
     return 1.0 / per_iter, det, (t4 - t0)
+
+
+def iterate_to_kl(ctx, target, chunk, max_iters, stream, torch):
+    """Iterations and device seconds of pxsne_step until the KL (evaluated
+    every `chunk` iterations, outside the timed region) is at most `target`."""
+    ms, it, kl = 0.0, 0, float("inf")
+    while it < max_iters:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(chunk)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        it += chunk
+        kl = ctx.kl()
+        if kl <= target:
+            break
+    return {"target": target, "reached": bool(kl <= target), "iterations": it,
+            "seconds": ms / 1e3, "kl": kl, "checked_every": chunk}
+
+
+def kl_target_study(px, ctx, Y0, kl_final, steps, stream, torch):
+    """Wall time to a fixed KL target.
+
+    - gauss10 (n = 2000, 512^2): the target is 1.01 x the oracle's KL after
+      the full 500-iteration schedule, stored in tests/golden by a script that
+      calls only the oracle.
+    - the bench workload: 1.01 x this run's own KL after the timed iterations
+      (the oracle cannot run 1,000 iterations at n = 1M in bounded time).
+    The GPU path runs from the same Y0 through the public calls."""
+    import datagen
+    with open(os.path.join(ROOT, "tests", "golden", "kl_target_gauss10.json")) as f:
+        tgt = json.load(f)
+    Xs, _ = datagen.gauss10(tgt["seed"])
+    Ys = datagen.init_y0(tgt["seed"], Xs.shape[0])
+    p = px.Params(log2_r=tgt["log2_r"], theta=tgt["theta"], k=tgt["k"],
+                  perplexity=tgt["perplexity"])
+    with px.Context(p, stream=stream.cuda_stream) as c:
+        c.affinities(Xs)
+        c.init(Ys)
+        c.step(3)
+        c.sync()
+        c.init(Ys)
+        small = iterate_to_kl(c, 1.01 * tgt["kl"], 10, 2 * tgt["iterations"], stream, torch)
+    small.update({"workload": f"gauss10 n={tgt['n']} {1 << tgt['log2_r']}^2",
+                  "target_from": f"1.01 x oracle KL after {tgt['iterations']} iterations "
+                                 f"({tgt['kl']:.6f}, tests/golden/kl_target_gauss10.json)"})
+    ctx.init(Y0)
+    big = iterate_to_kl(ctx, 1.01 * kl_final, 25, steps, stream, torch)
+    big.update({"workload": WORKLOAD["workload"],
+                "target_from": f"1.01 x this run's KL after {steps} timed iterations "
+                               f"({kl_final:.6f})"})
+    return {"small": small, "bench_workload": big}
+
+
+def screen_sweep(px, X, Y0, params_kw, levels, iters, stream, torch):
+    """Iterations/s of the same data and start on 2^L x 2^L screens (the tree
+    is L levels deep, so a traversal costs O(n L)): t = 0 .. iters-1."""
+    out = {}
+    for L in levels:
+        with px.Context(px.Params(log2_r=L, **params_kw), stream=stream.cuda_stream) as c:
+            c.affinities(X)
+            c.init(Y0)
+            c.step(3)
+            c.sync()
+            c.init(Y0)
+            c.sync()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.step(iters)
+            e1.record(stream)
+            e1.synchronize()
+            c.sync()
+            out[str(L)] = {"screen": f"{1 << L}^2", "it_per_s": iters / (e0.elapsed_time(e1) / 1e3),
+                           "iterations": iters}
+    return out
 
 
 def warmstart_experiment(px, ctx, X, Y0, args, torch):
@@ -502,11 +582,44 @@ def run_gpu(args):
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        v, det, w = oracle_sample(X.shape, Y0, args.cpu_rows, W["log2_r"], W["theta"])
-        cpu = {"value": v, "unit": "it/s", "cores": oracle.num_threads(), "kind": "oracle",
+        cores = oracle.num_threads()
+
+        def repeat(rows, min_s):
+            # the sampled iteration again (other samples) until min_s seconds of
+            # CPU work are done
+            vals, wall, det = [], 0.0, None
+            while wall < min_s and len(vals) < 50:
+                v, det, w = oracle_sample(X.shape, Y0, rows, W["log2_r"], W["theta"],
+                                          seed=len(vals))
+                vals.append(v)
+                wall += w
+            return float(np.mean(vals)), det, wall, len(vals)
+
+        v, det, w, reps = repeat(args.cpu_rows, 10.0)
+        cpu = {"value": v, "unit": "it/s", "cores": cores, "kind": "oracle",
                "sample": (f"first iteration from Y0: full tree + BH/attraction of "
                           f"{det['rows']} of {n} rows scaled by {det['scale']:.1f} + full "
-                          f"update/rescale ({w:.1f} s of CPU work)")}
+                          f"update/rescale, {reps} samples ({w:.1f} s of CPU work)")}
+        # the same on one thread (the paper times its CPU code single-threaded)
+        oracle.set_num_threads(1)
+        try:
+            v1, det1, w1, reps1 = repeat(max(1000, args.cpu_rows // 16), 8.0)
+        finally:
+            oracle.set_num_threads(cores)
+        cpu["one_thread"] = {"value": v1, "unit": "it/s", "cores": 1,
+                             "sample": f"{det1['rows']} of {n} rows scaled by "
+                                       f"{det1['scale']:.1f}, {reps1} samples ({w1:.1f} s of "
+                                       f"CPU work)"}
+
+    studies = None
+    if rank == 0 and not args.no_studies:
+        studies = {
+            "time_to_kl": kl_target_study(px, ctx, Y0, kl_after, args.steps, stream, torch),
+            # (P is rebuilt for every screen: skipped for the 10M scale workload)
+            "screen_sweep": screen_sweep(
+                px, X, Y0, dict(theta=W["theta"], k=W["k"], perplexity=W["perplexity"]),
+                [W["log2_r"] - 2, W["log2_r"] - 1, W["log2_r"], W["log2_r"] + 1,
+                 W["log2_r"] + 2], 300, stream, torch) if n <= 2_000_000 else None}
 
     warm = None
     if rank == 0 and not args.no_warmstart:
@@ -535,6 +648,7 @@ def run_gpu(args):
             "profiled_total_ms": prof_total, "p_construction_s": p_seconds, "knn": knn,
             "kl_after_timed": kl_after,
             "clocks": ck, "e2e": e2e, "cpu_baseline": cpu, "warmstart": warm,
+            "studies": studies,
             # per iteration: update, snap_hist, the pyramid (one launch for
             # 5 <= L <= 12), perm_scatter, traverse, attract, zsum; per relabel
             # (before every RELABEL_EVERY-th iteration): maps, three scan

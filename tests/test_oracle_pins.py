@@ -25,8 +25,10 @@ fails at least one test:
   nbr_precision  identity cases (precision 1 for the same geometry, ~k/n for
                  an unrelated one)
 """
+import json
 import math
 import os
+import sys
 
 import numpy as np
 import pytest
@@ -583,3 +585,15 @@ def test_pca_against_svd():
         assert abs(abs(V[:, c] @ Vt[c]) - 1.0) < 1e-8
     np.testing.assert_allclose(V.T @ V, np.eye(5), atol=1e-12)
     np.testing.assert_allclose(Z.var(0, ddof=1), lam, rtol=1e-10)
+
+
+def test_stored_kl_target_matches_the_oracle():
+    # the time-to-target measurement's stored target is the oracle's own value
+    sys.path.insert(0, GOLDEN)
+    import make_kl_target
+    with open(os.path.join(GOLDEN, "kl_target_gauss10.json")) as f:
+        stored = json.load(f)
+    fresh = make_kl_target.compute()
+    assert stored["kl"] == pytest.approx(fresh["kl"], rel=1e-9)
+    assert {k: v for k, v in stored.items() if k != "kl"} == \
+        {k: v for k, v in fresh.items() if k != "kl"}
