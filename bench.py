@@ -306,6 +306,34 @@ def screen_sweep(px, X, Y0, params_kw, levels, iters, stream, torch):
     return out
 
 
+def geometric_centre_study(px, X, Y0, params_kw, steps, com, stream, torch):
+    """The paper's own approximation of a cell by its geometric centre (Sec.
+    4.1; the tree keeps counts only) on the same data, start and schedule as
+    the timed centre-of-mass run `com` ({it_per_s, kl, precision_k10}): speed,
+    final KL and neighbourhood precision, and the tree kernels' times."""
+    with px.Context(px.Params(centre_mode=1, **params_kw), stream=stream.cuda_stream) as c:
+        c.affinities(X)
+        c.init(Y0)
+        c.step(3)
+        c.sync()
+        c.init(Y0)
+        c.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        c.sync()
+        out = {"it_per_s": steps / (e0.elapsed_time(e1) / 1e3), "kl": c.kl(),
+               "precision_k10": c.nbr_precision(k=10), "iterations": steps}
+        c.init(Y0)
+        groups, _ = c.step_profiled(100)
+        out["tree_ms_per_iteration"] = {g: groups[g] / 100 for g in ("k_snap_hist", "k_pyr_pass")}
+    out["centre_of_mass"] = com
+    return out
+
+
 def warmstart_experiment(px, ctx, X, Y0, args, torch):
     """Learned warm start (survey config 4), on ctx's P (the bench workload).
 
@@ -518,6 +546,7 @@ def run_gpu(args):
     ms = max_over_ranks(ms, dist, "cuda")
     value = job_rate(args.steps, ms / 1000.0, ws)
     kl_after = ctx.kl()
+    prec_after = ctx.nbr_precision(k=10)
 
     # per-kernel breakdown: the same K iterations again from t = 0, with CUDA
     # events around each kernel group on the library's stream
@@ -615,6 +644,12 @@ def run_gpu(args):
     if rank == 0 and not args.no_studies:
         studies = {
             "time_to_kl": kl_target_study(px, ctx, Y0, kl_after, args.steps, stream, torch),
+            "geometric_centre": geometric_centre_study(
+                px, X, Y0, dict(log2_r=W["log2_r"], theta=W["theta"], k=W["k"],
+                                perplexity=W["perplexity"]), args.steps,
+                {"it_per_s": value, "kl": kl_after, "precision_k10": prec_after,
+                 "tree_ms_per_iteration": {g: avg_ms[g] for g in ("k_snap_hist", "k_pyr_pass")}},
+                stream, torch) if n <= 2_000_000 else None,
             # (P is rebuilt for every screen: skipped for the 10M scale workload)
             "screen_sweep": screen_sweep(
                 px, X, Y0, dict(theta=W["theta"], k=W["k"], perplexity=W["perplexity"]),

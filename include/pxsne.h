@@ -197,7 +197,8 @@ int pxsne_get_state(pxsne_ctx *ctx, uint32_t *z, double *s, float *u, float *gai
  * Morton order (x bits at even positions): cnt[4^l] u32 cell counts N_c and,
  * for l = L only, sx/sy[4^l] u64 exact sums of the fixed-point coordinates of
  * the points in each pixel (NULL to skip).  Pixel Morton keys per point go to
- * morton[n] when non-NULL. */
+ * morton[n] when non-NULL.  With centre_mode = 1 the tree keeps counts only:
+ * asking for sx or sy fails with PXSNE_E_UNSUPPORTED. */
 int pxsne_get_tree(pxsne_ctx *ctx, int32_t level, uint32_t *cnt, uint64_t *sx,
                    uint64_t *sy, uint32_t *morton);
 

@@ -738,6 +738,8 @@ int pxsne_get_tree(pxsne_ctx *c, int32_t level, uint32_t *cnt, uint64_t *sx, uin
     int rc = need_state(c);
     if (rc) return rc;
     if (level < 0 || level > c->L) return fail(c, PXSNE_E_ARG, "level out of range");
+    if (level == c->L && (sx || sy) && c->p.centre_mode != 0)
+        return fail(c, PXSNE_E_UNSUPPORTED, "the geometric-centre tree keeps no coordinate sums");
     cudaStream_t st = c->stream;
     const size_t cells = size_t(1) << (2 * level);
     if (cnt) {

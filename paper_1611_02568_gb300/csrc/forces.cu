@@ -38,20 +38,18 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
 
 // Offset z - c of a lane's two points from the cell's centre: of mass (the
-// split record r), or the geometric centre of cell mc of level lc.
+// split record r), or (CENTRE = 1) the geometric centre, passed in r.x / r.z
+// as exact floats (multiples of 2^16 below level 16), so that z - c =
+// (z_hi - c) + z_lo with one rounding, as for a centre of mass.
 template <int CENTRE>
-__device__ __forceinline__ void cell_offset2(int lc, uint32_t mc, float4 r, uint2 z0, uint2 z1,
-                                             float2 zhx, float2 zlx, float2 zhy, float2 zly,
-                                             float2 &dx, float2 &dy) {
+__device__ __forceinline__ void cell_offset2(float4 r, float2 zhx, float2 zlx, float2 zhy,
+                                             float2 zly, float2 &dx, float2 &dy) {
     if (CENTRE == 0) {
         dx = add2(add2(zhx, bc2(-r.x)), add2(zlx, bc2(-r.y)));
         dy = add2(add2(zhy, bc2(-r.z)), add2(zly, bc2(-r.w)));
     } else {
-        const uint32_t cx = gather_bits16(mc), cy = gather_bits16(mc >> 1);
-        const int64_t half = int64_t(1) << (31 - lc);
-        const int64_t bx = ((int64_t)cx << (32 - lc)) + half, by = ((int64_t)cy << (32 - lc)) + half;
-        dx = make_float2((float)((int64_t)z0.x - bx), (float)((int64_t)z1.x - bx));
-        dy = make_float2((float)((int64_t)z0.y - by), (float)((int64_t)z1.y - by));
+        dx = add2(add2(zhx, bc2(-r.x)), zlx);
+        dy = add2(add2(zhy, bc2(-r.z)), zly);
     }
 }
 
@@ -115,6 +113,17 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
         if (CENTRE == 0) {
 #pragma unroll
             for (int ch = 0; ch < 4; ch++) rr[ch] = __ldg(rec + at + ch);
+        } else {
+            // geometric centres: the node's corner (exact floats) and width
+            // 2^(33 - lc); child ch's centre is a quarter or three quarters
+            // across on each axis
+            const uint32_t pm = node & 0x0fffffffu;
+            const float wp = __int_as_float((127 + 33 - lc) << 23);
+            const float px = (float)gather_bits16(pm) * wp, py = (float)gather_bits16(pm >> 1) * wp;
+#pragma unroll
+            for (int ch = 0; ch < 4; ch++)
+                rr[ch] = make_float4(fmaf(wp, (ch & 1) ? 0.75f : 0.25f, px), 0.f,
+                                     fmaf(wp, (ch & 2) ? 0.75f : 0.25f, py), 0.f);
         }
         const bool me0 = (top.m0 >> lane) & 1u, me1 = (top.m1 >> lane) & 1u;
         const float Nc[4] = {nv.x, nv.y, nv.z, nv.w};
@@ -129,10 +138,9 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
                 const float N = Nc[ch];
                 if (N == 0.f) continue;
                 const uint32_t mc = m0 + ch;
-                float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (CENTRE == 0) r = rr[ch];
+                const float4 r = rr[ch];
                 float2 dx, dy;
-                cell_offset2<CENTRE>(lc, mc, r, z0, z1, zhx, zlx, zhy, zly, dx, dy);
+                cell_offset2<CENTRE>(r, zhx, zlx, zhy, zly, dx, dy);
                 const bool own0 = me0 && (mine0 == mc), own1 = me1 && (mine1 == mc);
                 float2 Nf = bc2(N);
                 if (__any_sync(0xffffffffu, own0 || own1)) {  // own pixel: take the point out
@@ -187,10 +195,9 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
                 const float N = Nc[ch];
                 if (N == 0.f) continue;
                 const uint32_t mc = m0 + ch;
-                float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (CENTRE == 0) r = rr[ch];
+                const float4 r = rr[ch];
                 float2 dx, dy;
-                cell_offset2<CENTRE>(lc, mc, r, z0, z1, zhx, zlx, zhy, zly, dx, dy);
+                cell_offset2<CENTRE>(r, zhx, zlx, zhy, zly, dx, dy);
                 dx = mul2(dx, sf0);
                 dy = mul2(dy, sf1);
                 const float2 d2 = fma2(dx, dx, mul2(dy, dy));

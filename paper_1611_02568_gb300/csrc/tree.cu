@@ -97,21 +97,28 @@ __global__ void k_snap_hist(int n, int L, int rescale, float theta,
     const int start = 31 - __clz(heads & upto);
     const unsigned later = heads & ~upto;
     const int end = later ? __ffs(later) - 2 : 31;
+    // the coordinate sums are kept for centres of mass only (sx == NULL: a
+    // count-only tree for geometric centres)
+    const bool sums = sx != nullptr;
     u64 vx = zx, vy = zy;
+    if (sums) {
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const u64 tx = __shfl_up_sync(0xffffffffu, vx, o);
-        const u64 ty = __shfl_up_sync(0xffffffffu, vy, o);
-        if (lane - o >= start) {
-            vx += tx;
-            vy += ty;
+        for (int o = 1; o < 32; o <<= 1) {
+            const u64 tx = __shfl_up_sync(0xffffffffu, vx, o);
+            const u64 ty = __shfl_up_sync(0xffffffffu, vy, o);
+            if (lane - o >= start) {
+                vx += tx;
+                vy += ty;
+            }
         }
     }
     uint32_t base = 0u;
     if (lane == end && valid) {
         base = atomicAdd(&cnt[m], (uint32_t)(end - start + 1));
-        atomicAdd(&sx[m], vx);
-        atomicAdd(&sy[m], vy);
+        if (sums) {
+            atomicAdd(&sx[m], vx);
+            atomicAdd(&sy[m], vy);
+        }
     }
     base = __shfl_sync(0xffffffffu, base, end);
     if (valid) rank[i] = base + (uint32_t)(lane - start);
@@ -199,16 +206,20 @@ __global__ void __launch_bounds__(1 << (2 * (K - 1)))
     const int tid = threadIdx.x;
     const int64_t b = blockIdx.x;
     const int64_t cell0 = b * (NT * 4) + 4 * tid;
+    const bool sums = in_sx != nullptr;  // count-only tree otherwise
     const uint4 c4 = reinterpret_cast<const uint4 *>(in_cnt)[cell0 >> 2];
-    const ulonglong2 x01 = reinterpret_cast<const ulonglong2 *>(in_sx)[cell0 >> 1];
-    const ulonglong2 x23 = reinterpret_cast<const ulonglong2 *>(in_sx)[(cell0 >> 1) + 1];
-    const ulonglong2 y01 = reinterpret_cast<const ulonglong2 *>(in_sy)[cell0 >> 1];
-    const ulonglong2 y23 = reinterpret_cast<const ulonglong2 *>(in_sy)[(cell0 >> 1) + 1];
-    float4 *rl = rec + rec_offset(h) + cell0;
-    rl[0] = make_record(c4.x, x01.x, y01.x, h, (uint32_t)cell0);
-    rl[1] = make_record(c4.y, x01.y, y01.y, h, (uint32_t)cell0 + 1u);
-    rl[2] = make_record(c4.z, x23.x, y23.x, h, (uint32_t)cell0 + 2u);
-    rl[3] = make_record(c4.w, x23.y, y23.y, h, (uint32_t)cell0 + 3u);
+    ulonglong2 x01{0, 0}, x23{0, 0}, y01{0, 0}, y23{0, 0};
+    if (sums) {
+        x01 = reinterpret_cast<const ulonglong2 *>(in_sx)[cell0 >> 1];
+        x23 = reinterpret_cast<const ulonglong2 *>(in_sx)[(cell0 >> 1) + 1];
+        y01 = reinterpret_cast<const ulonglong2 *>(in_sy)[cell0 >> 1];
+        y23 = reinterpret_cast<const ulonglong2 *>(in_sy)[(cell0 >> 1) + 1];
+        float4 *rl = rec + rec_offset(h) + cell0;
+        rl[0] = make_record(c4.x, x01.x, y01.x, h, (uint32_t)cell0);
+        rl[1] = make_record(c4.y, x01.y, y01.y, h, (uint32_t)cell0 + 1u);
+        rl[2] = make_record(c4.z, x23.x, y23.x, h, (uint32_t)cell0 + 2u);
+        rl[3] = make_record(c4.w, x23.y, y23.y, h, (uint32_t)cell0 + 3u);
+    }
     reinterpret_cast<float4 *>(recn + rec_offset(h))[cell0 >> 2] =
         make_float4((float)c4.x, (float)c4.y, (float)c4.z, (float)c4.w);
     uint32_t N = c4.x + c4.y + c4.z + c4.w;
@@ -230,13 +241,15 @@ __global__ void __launch_bounds__(1 << (2 * (K - 1)))
         const int cells = 1 << (2 * j);
         if (tid < cells) {
             if (j > 0 || top) {
-                rec[rec_offset(lvl) + idx] = make_record(N, X, Y, lvl, (uint32_t)idx);
+                if (sums) rec[rec_offset(lvl) + idx] = make_record(N, X, Y, lvl, (uint32_t)idx);
                 recn[rec_offset(lvl) + idx] = (float)N;
             }
             if (j == 0) {
                 out_cnt[b] = N;
-                out_sx[b] = X;
-                out_sy[b] = Y;
+                if (sums) {
+                    out_sx[b] = X;
+                    out_sy[b] = Y;
+                }
             }
         }
         if (j == 0) break;
@@ -272,7 +285,7 @@ __device__ __forceinline__ u64 shfl_xor_u64(u64 v, int o) {
 
 __device__ __forceinline__ void put_record(float4 *rec, float *recn, int l, uint32_t m,
                                            uint32_t N, u64 X, u64 Y) {
-    rec[rec_offset(l) + m] = make_record(N, X, Y, l, m);
+    if (rec != nullptr) rec[rec_offset(l) + m] = make_record(N, X, Y, l, m);  // NULL: counts only
     recn[rec_offset(l) + m] = (float)N;
 }
 
@@ -318,22 +331,25 @@ __device__ void pyr_top(int h0, uint32_t *c0, u64 *x0, u64 *y0, uint32_t *c1, u6
     }
     uint32_t *cc = c0, *cn = c1;
     u64 *xc = x0, *xn = x1, *yc = y0, *yn = y1;
+    const bool sums = rec != nullptr;
     for (int l = h0;; l--) {
         const int cells = 1 << (2 * l);
         if (l < h0)
             for (int c = tid; c < cells; c += 256)
-                put_record(rec, recn, l, (uint32_t)c, __ldcg(cc + c), __ldcg(xc + c),
-                           __ldcg(yc + c));
+                put_record(rec, recn, l, (uint32_t)c, __ldcg(cc + c), sums ? __ldcg(xc + c) : 0ull,
+                           sums ? __ldcg(yc + c) : 0ull);
         if (l == 0) break;
         for (int p = tid; p < (cells >> 2); p += 256) {
             const uint4 q4 = __ldcg(reinterpret_cast<const uint4 *>(cc) + p);
-            const ulonglong2 xa = __ldcg(reinterpret_cast<const ulonglong2 *>(xc) + 2 * p);
-            const ulonglong2 xb = __ldcg(reinterpret_cast<const ulonglong2 *>(xc) + 2 * p + 1);
-            const ulonglong2 ya = __ldcg(reinterpret_cast<const ulonglong2 *>(yc) + 2 * p);
-            const ulonglong2 yb = __ldcg(reinterpret_cast<const ulonglong2 *>(yc) + 2 * p + 1);
             cn[p] = q4.x + q4.y + q4.z + q4.w;
-            xn[p] = xa.x + xa.y + xb.x + xb.y;
-            yn[p] = ya.x + ya.y + yb.x + yb.y;
+            if (sums) {
+                const ulonglong2 xa = __ldcg(reinterpret_cast<const ulonglong2 *>(xc) + 2 * p);
+                const ulonglong2 xb = __ldcg(reinterpret_cast<const ulonglong2 *>(xc) + 2 * p + 1);
+                const ulonglong2 ya = __ldcg(reinterpret_cast<const ulonglong2 *>(yc) + 2 * p);
+                const ulonglong2 yb = __ldcg(reinterpret_cast<const ulonglong2 *>(yc) + 2 * p + 1);
+                xn[p] = xa.x + xa.y + xb.x + xb.y;
+                yn[p] = ya.x + ya.y + yb.x + yb.y;
+            }
         }
         __threadfence_block();
         __syncthreads();
@@ -362,16 +378,21 @@ __global__ void __launch_bounds__(256)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t b = blockIdx.x;
     const uint32_t cell0 = b * 1024u + 4u * (uint32_t)tid;
+    // rec == NULL: a count-only tree (geometric centres), no sums read or kept
+    const bool sums = rec != nullptr;
     const uint4 c4 = reinterpret_cast<const uint4 *>(in_cnt)[cell0 >> 2];
-    const ulonglong2 x01 = reinterpret_cast<const ulonglong2 *>(in_sx)[cell0 >> 1];
-    const ulonglong2 x23 = reinterpret_cast<const ulonglong2 *>(in_sx)[(cell0 >> 1) + 1];
-    const ulonglong2 y01 = reinterpret_cast<const ulonglong2 *>(in_sy)[cell0 >> 1];
-    const ulonglong2 y23 = reinterpret_cast<const ulonglong2 *>(in_sy)[(cell0 >> 1) + 1];
-    float4 *rl = rec + rec_offset(h) + cell0;
-    rl[0] = make_record(c4.x, x01.x, y01.x, h, cell0);
-    rl[1] = make_record(c4.y, x01.y, y01.y, h, cell0 + 1u);
-    rl[2] = make_record(c4.z, x23.x, y23.x, h, cell0 + 2u);
-    rl[3] = make_record(c4.w, x23.y, y23.y, h, cell0 + 3u);
+    ulonglong2 x01{0, 0}, x23{0, 0}, y01{0, 0}, y23{0, 0};
+    if (sums) {
+        x01 = reinterpret_cast<const ulonglong2 *>(in_sx)[cell0 >> 1];
+        x23 = reinterpret_cast<const ulonglong2 *>(in_sx)[(cell0 >> 1) + 1];
+        y01 = reinterpret_cast<const ulonglong2 *>(in_sy)[cell0 >> 1];
+        y23 = reinterpret_cast<const ulonglong2 *>(in_sy)[(cell0 >> 1) + 1];
+        float4 *rl = rec + rec_offset(h) + cell0;
+        rl[0] = make_record(c4.x, x01.x, y01.x, h, cell0);
+        rl[1] = make_record(c4.y, x01.y, y01.y, h, cell0 + 1u);
+        rl[2] = make_record(c4.z, x23.x, y23.x, h, cell0 + 2u);
+        rl[3] = make_record(c4.w, x23.y, y23.y, h, cell0 + 3u);
+    }
     reinterpret_cast<float4 *>(recn + rec_offset(h))[cell0 >> 2] =
         make_float4((float)c4.x, (float)c4.y, (float)c4.z, (float)c4.w);
     uint32_t N = c4.x + c4.y + c4.z + c4.w;
@@ -389,20 +410,26 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int o = 1; o <= 2; o <<= 1) {
         N += __shfl_xor_sync(0xffffffffu, N, o);
-        X += shfl_xor_u64(X, o);
-        Y += shfl_xor_u64(Y, o);
+        if (sums) {
+            X += shfl_xor_u64(X, o);
+            Y += shfl_xor_u64(Y, o);
+        }
     }
     if ((lane & 3) == 0) put_record(rec, recn, h - 2, b * 64u + (uint32_t)(tid >> 2), N, X, Y);
 #pragma unroll
     for (int o = 4; o <= 8; o <<= 1) {
         N += __shfl_xor_sync(0xffffffffu, N, o);
-        X += shfl_xor_u64(X, o);
-        Y += shfl_xor_u64(Y, o);
+        if (sums) {
+            X += shfl_xor_u64(X, o);
+            Y += shfl_xor_u64(Y, o);
+        }
     }
     if ((lane & 15) == 0) put_record(rec, recn, h - 3, b * 16u + (uint32_t)(tid >> 4), N, X, Y);
     N += __shfl_xor_sync(0xffffffffu, N, 16);
-    X += shfl_xor_u64(X, 16);
-    Y += shfl_xor_u64(Y, 16);
+    if (sums) {
+        X += shfl_xor_u64(X, 16);
+        Y += shfl_xor_u64(Y, 16);
+    }
     if (lane == 0) {
         s_n[warp] = N;
         s_x[warp] = X;
@@ -432,8 +459,10 @@ __global__ void __launch_bounds__(256)
             y5 += s_y[w];
         }
         out_cnt[b] = n5;
-        out_sx[b] = x5;
-        out_sy[b] = y5;
+        if (sums) {
+            out_sx[b] = x5;
+            out_sy[b] = y5;
+        }
         put_record(rec, recn, h - 5, b, n5, x5, y5);
         // the last CTA to finish builds the top of the pyramid
         __threadfence();
@@ -509,13 +538,18 @@ cudaError_t launch_snap(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
     const int64_t leaves = int64_t(1) << (2 * L);
     cudaError_t e;
     if (marks && (e = cudaEventRecord(marks[KG_SNAP], st))) return e;
+    // geometric centres (Sec. 4.1's approximation) need the counts only
+    const bool sums = c->p.centre_mode == 0;
     if ((e = cudaMemsetAsync(c->leaf_cnt, 0, leaves * sizeof(uint32_t), st))) return e;
-    if ((e = cudaMemsetAsync(c->leaf_sx, 0, leaves * sizeof(u64), st))) return e;
-    if ((e = cudaMemsetAsync(c->leaf_sy, 0, leaves * sizeof(u64), st))) return e;
+    if (sums) {
+        if ((e = cudaMemsetAsync(c->leaf_sx, 0, leaves * sizeof(u64), st))) return e;
+        if ((e = cudaMemsetAsync(c->leaf_sy, 0, leaves * sizeof(u64), st))) return e;
+    }
     const int n = (int)c->n;
     k_snap_hist<<<(n + 255) / 256, 256, 0, st>>>(n, L, rescale ? 1 : 0, c->p.theta, c->zhat,
                                                  c->z, c->perm, c->rank, c->leaf_cnt,
-                                                 c->leaf_sx, c->leaf_sy, c->sc, c->ainv,
+                                                 sums ? c->leaf_sx : nullptr,
+                                                 sums ? c->leaf_sy : nullptr, c->sc, c->ainv,
                                                  c->zp);
     return cudaGetLastError();
 }
@@ -528,10 +562,11 @@ cudaError_t launch_pyramid(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
     cudaError_t e;
     if (marks && (e = cudaEventRecord(marks[KG_PYRAMID], st))) return e;
     const int K1 = L < kPyrK ? L : kPyrK;
+    const bool sums = c->p.centre_mode == 0;  // count-only tree for geometric centres
     if (L >= kPyrK && L - kPyrK <= 7) {
         // one pass: shuffle-reduced bottom levels, the top by the last CTA
         k_pyr_bottom<<<(unsigned)(leaves >> 10), 256, 0, st>>>(
-            L, c->leaf_cnt, c->leaf_sx, c->leaf_sy, c->rec, c->recn, c->lvl_cnt[0],
+            L, c->leaf_cnt, c->leaf_sx, c->leaf_sy, sums ? c->rec : nullptr, c->recn, c->lvl_cnt[0],
             c->lvl_sx[0], c->lvl_sy[0], c->lvl_cnt[1], c->lvl_sx[1], c->lvl_sy[1],
             c->leaf_start, c->blk_off, c->sc, rescale ? 1 : 0);
         if ((e = cudaGetLastError())) return e;
@@ -542,7 +577,8 @@ cudaError_t launch_pyramid(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
         {
             const int64_t blocks = leaves >> (2 * K1);
             const int top = (h - K1 == 0);
-            if ((e = pyr_pass(K1, blocks, st, h, top, c->leaf_cnt, c->leaf_sx, c->leaf_sy,
+            if ((e = pyr_pass(K1, blocks, st, h, top, c->leaf_cnt, sums ? c->leaf_sx : nullptr,
+                              c->leaf_sy,
                               c->rec, c->recn, c->lvl_cnt[0], c->lvl_sx[0], c->lvl_sy[0],
                               c->leaf_start, c->sc, (rescale && top) ? 1 : 0)))
                 return e;
@@ -555,8 +591,9 @@ cudaError_t launch_pyramid(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
             const int K = h < kPyrK ? h : kPyrK;
             const int64_t blocks = (int64_t(1) << (2 * h)) >> (2 * K);
             const int top = (h - K == 0);
-            if ((e = pyr_pass(K, blocks, st, h, top, c->lvl_cnt[cur], c->lvl_sx[cur],
-                              c->lvl_sy[cur], c->rec, c->recn, c->lvl_cnt[cur ^ 1],
+            if ((e = pyr_pass(K, blocks, st, h, top, c->lvl_cnt[cur],
+                              sums ? c->lvl_sx[cur] : nullptr, c->lvl_sy[cur], c->rec, c->recn,
+                              c->lvl_cnt[cur ^ 1],
                               c->lvl_sx[cur ^ 1], c->lvl_sy[cur ^ 1], nullptr, c->sc,
                               (rescale && top) ? 1 : 0)))
                 return e;

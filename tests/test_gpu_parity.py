@@ -124,6 +124,33 @@ def test_forces_geometric_centre_mode(px, gauss):
     assert rel(Zi, oZi) <= FORCE_TOL
 
 
+@pytest.mark.parametrize("L", [4, 9, 13])
+def test_geometric_centre_mode_keeps_counts_only(px, gauss, L):
+    """The geometric-centre tree (counts only, no coordinate sums): counts
+    bit-exact at every level, through iterations (rescale, relabel) on both
+    pyramid paths; forces still match the oracle's geometric-centre mode."""
+    X, P, Y0, st = gauss
+    with make_ctx(px, L=L, centre_mode=1) as ctx:
+        ctx.set_P(P.row_ptr, P.col, P.val.astype(np.float32))
+        ctx.init(Y0)
+        ctx.step(30)
+        z, s, _, _, _ = ctx.get_state()
+        cnt_o = oracle.pyramid(z, L)[0]
+        for lev in range(L + 1):
+            cnt, _, _, _ = ctx.get_tree(lev)
+            off = oracle.level_offset(lev)
+            assert np.array_equal(cnt, cnt_o[off:off + 4 ** lev]), f"level {lev}"
+        with pytest.raises(px.PxsneError) as ei:
+            ctx.get_tree(L, sums=True)
+        assert ei.value.code == -6
+        ctx.set_state(*ctx.get_state())
+        Frep, Zi, _, _ = ctx.get_forces()
+        assert ctx.sync() == 0
+    oF, oZi, _ = oracle.bh_repulsion(z, s, L, 0.5, centre_mode=1)
+    assert rel(Frep, oF) <= FORCE_TOL
+    assert rel(Zi, oZi) <= FORCE_TOL
+
+
 def test_one_step_matches_oracle(px, gauss):
     X, P, Y0, st = gauss
     L = 9
