@@ -36,6 +36,13 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
     return __ffma2_rn(a, b, c);
 }
 __device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+// The kernel value 1 / (1 + d^2) (argument >= 1): the hardware's approximate
+// reciprocal (PTX rcp.approx, relative error within 2^-23), one instruction.
+__device__ __forceinline__ float rcp1(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // Offset z - c of a lane's two points from the cell's centre: of mass (the
 // split record r), or (CENTRE = 1) the geometric centre, passed in r.x / r.z
@@ -170,9 +177,8 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
                     n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
                 }
                 const float2 w1 = add2(bc2(1.0f), d2);
-                const float2 q = make_float2(__fdividef(1.0f, w1.x), __fdividef(1.0f, w1.y));
-                const float2 Nq0 = mul2(Nf, q);
-                const float2 Nq = make_float2(acc0 ? Nq0.x : 0.0f, acc1 ? Nq0.y : 0.0f);
+                const float2 q = make_float2(rcp1(w1.x), rcp1(w1.y));
+                const float2 Nq = mul2(make_float2(acc0 ? Nf.x : 0.0f, acc1 ? Nf.y : 0.0f), q);
                 zs = add2(zs, Nq);
                 const float2 Nq2 = mul2(Nq, q);
                 fx = fma2(Nq2, dx, fx);
@@ -209,9 +215,8 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
                     n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
                 }
                 const float2 w1 = add2(bc2(1.0f), d2);
-                const float2 q = make_float2(__fdividef(1.0f, w1.x), __fdividef(1.0f, w1.y));
-                const float2 Nq0 = mul2(bc2(N), q);
-                const float2 Nq = make_float2(acc0 ? Nq0.x : 0.0f, acc1 ? Nq0.y : 0.0f);
+                const float2 q = make_float2(rcp1(w1.x), rcp1(w1.y));
+                const float2 Nq = mul2(make_float2(acc0 ? N : 0.0f, acc1 ? N : 0.0f), q);
                 zs = add2(zs, Nq);
                 const float2 Nq2 = mul2(Nq, q);
                 fx = fma2(Nq2, dx, fx);
