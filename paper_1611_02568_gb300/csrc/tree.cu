@@ -740,10 +740,12 @@ cudaError_t launch_centre_y(pxsne_ctx *c, float *Ydev, int32_t *pixdev, float *s
     const int n = (int)c->n;
     u64 *sums = reinterpret_cast<u64 *>(scratch);
     cudaError_t e;
-    if ((e = cudaMemsetAsync(sums, 0, 2 * sizeof(u64), st))) return e;
-    const int blocks = (n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184;
-    k_sum_z<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(n, c->z, sums);
-    if ((e = cudaGetLastError())) return e;
+    if (Ydev) {  // the mean, for centred coordinates (pixels alone need none)
+        if ((e = cudaMemsetAsync(sums, 0, 2 * sizeof(u64), st))) return e;
+        const int blocks = (n + 255) / 256 < 1184 ? (n + 255) / 256 : 1184;
+        k_sum_z<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(n, c->z, sums);
+        if ((e = cudaGetLastError())) return e;
+    }
     k_write_y<<<(n + 255) / 256, 256, 0, st>>>(n, c->L, c->z, sums, c->sc,
                                                reinterpret_cast<float2 *>(Ydev),
                                                reinterpret_cast<int2 *>(pixdev));

@@ -295,7 +295,10 @@ def test_get_Y_and_pixels(px, gauss):
     with make_ctx(px, L=9) as ctx:
         inject(ctx, P, st)
         Y, pix = ctx.get_Y()
+        pix_only = np.empty_like(pix)
+        ctx.get_Y(None, pix_only)          # pixels alone (no centring pass)
     assert np.array_equal(pix, (st.z >> (32 - 9)).astype(np.int32))
+    assert np.array_equal(pix_only, pix)
     y = st.y()
     np.testing.assert_allclose(Y, y - y.mean(0), rtol=0, atol=1e-6 * np.abs(y).max())
 
