@@ -32,6 +32,7 @@ constexpr int kH = 256;          // hidden width
 constexpr int kMaxBatch = 8192;  // rows per training step
 constexpr int kGemmThreads = 128;
 constexpr int kGemmPolls = 1 << 24;
+constexpr int kSplitK = 512;     // batch rows per CTA in the weight-gradient GEMMs
 
 typedef __nv_bfloat16 bf16;
 
@@ -124,33 +125,66 @@ __global__ void __launch_bounds__(kGemmThreads)
                         tc::mbar_wait(&mbar[last & 1], (uint32_t)((last >> 1) & 1), kGemmPolls));
     }
     if (!ok && lane == 0 && chunks > 0) atomicOr(ep.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
+    if (!ok && lane == 0) s_abort = 1;
     tc::fence_after();
+    // Epilogue, 32 columns at a time: each thread holds one row of the block
+    // (TMEM lane = row); values pass through shared memory (the operand
+    // stages are free now) so that row-major stores, loads and atomics are
+    // made by a warp along a row, coalesced.  Transposed stores go straight
+    // from the row's thread (consecutive rows, coalesced as well).
+    __syncthreads();
+    ok = !s_abort;  // the same in every warp (the barriers below need it)
     if (ok) {
-        const int row = m0 + 32 * warp + lane;
+        constexpr int SP = 33;  // padded row pitch: conflict-free both ways
+        float *sZ = reinterpret_cast<float *>(smem);
+        float *sH = sZ + 128 * SP;
+        const int rl = 32 * warp + lane, row = m0 + rl;
         const bool rv = row < ep.rows;
 #pragma unroll 1
         for (int cb = 0; cb < NT; cb += 32) {
+            const int colb = n0 + cb;
+            if (EPI == EPI_DGELU) {
+                // the pre-activations of this block, loaded along rows
+                for (int r = warp; r < 128; r += kGemmThreads / 32) {
+                    const int gr = m0 + r, gc = colb + lane;
+                    sZ[r * SP + lane] = (gr < ep.rows && gc < N) ? ep.Z[(size_t)gr * ep.ld + gc] : 0.f;
+                }
+                __syncthreads();
+            }
             float v[32];
             tc::tmem_ld32(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)cb, v);
-#pragma unroll 4
-            for (int j = 0; j < 32 && rv; j++) {
-                const int col = n0 + cb + j;
-                if (col >= N) break;
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
+                const int col = colb + j;
                 if (EPI == EPI_Z_GELU) {
-                    const float z = v[j] + ep.bias[col];
-                    ep.Z[(size_t)row * ep.ld + col] = z;
-                    const bf16 h = __float2bfloat16_rn(gelu_f(z));
-                    if (ep.H) ep.H[(size_t)row * ep.ld + col] = h;
-                    if (ep.HT) ep.HT[(size_t)col * ep.ldT + row] = h;
+                    const float z = v[j] + (col < N ? ep.bias[col] : 0.f);
+                    const float h = gelu_f(z);
+                    sZ[rl * SP + j] = z;
+                    sH[rl * SP + j] = h;
+                    if (ep.HT && rv && col < N) ep.HT[(size_t)col * ep.ldT + row] = __float2bfloat16_rn(h);
                 } else if (EPI == EPI_DGELU) {
-                    const float g = v[j] * gelu_df(ep.Z[(size_t)row * ep.ld + col]);
-                    const bf16 h = __float2bfloat16_rn(g);
-                    if (ep.H) ep.H[(size_t)row * ep.ld + col] = h;
-                    if (ep.HT) ep.HT[(size_t)col * ep.ldT + row] = h;
+                    const float g = v[j] * gelu_df(sZ[rl * SP + j]);
+                    sH[rl * SP + j] = g;
+                    if (ep.HT && rv && col < N) ep.HT[(size_t)col * ep.ldT + row] = __float2bfloat16_rn(g);
                 } else {
-                    atomicAdd(ep.acc + (size_t)row * ep.ld + col, v[j]);
+                    sZ[rl * SP + j] = v[j];
                 }
             }
+            __syncthreads();
+            for (int r = warp; r < 128; r += kGemmThreads / 32) {
+                const int gr = m0 + r, gc = colb + lane;
+                if (gr >= ep.rows || gc >= N) continue;
+                const size_t o = (size_t)gr * ep.ld + gc;
+                if (EPI == EPI_Z_GELU) {
+                    ep.Z[o] = sZ[r * SP + lane];
+                    if (ep.H) ep.H[o] = __float2bfloat16_rn(sH[r * SP + lane]);
+                } else if (EPI == EPI_DGELU) {
+                    if (ep.H) ep.H[o] = __float2bfloat16_rn(sH[r * SP + lane]);
+                } else {
+                    atomicAdd(ep.acc + o, sZ[r * SP + lane]);
+                }
+            }
+            __syncthreads();
         }
     }
     tc::fence_before();
@@ -170,18 +204,23 @@ cudaError_t gemm(cudaStream_t st, int M, int N, int K, int k_split, const bf16 *
     return cudaGetLastError();
 }
 
-// Output layer, one warp per row (lane owns 8 of the 256 hidden units).
+// Output layer: a CTA takes 32 consecutive rows of the batch, a warp 4 of
+// them, a lane 8 of the 256 hidden units of a row (16-byte loads and stores).
 // With targets: loss (sum of squared errors / m), dy = 2 (y - t) / m,
-// dz2 = (W3^T dy) * GELU'(z2) (row-major and transposed), dL/dW3 and dL/db3
-// accumulated per warp and added atomically.
+// dz2 = (W3^T dy) * GELU'(z2), row-major and transposed (the transposed copy
+// is staged in shared memory and written 8 rows per 16-byte store), and
+// dL/dW3, dL/db3 accumulated per warp and added atomically.
+constexpr int kOutRows = 32;
 __global__ void __launch_bounds__(256)
     k_out_layer(int m, int rows_pad, const bf16 *__restrict__ H2, const float *__restrict__ Z2,
                 const bf16 *__restrict__ W3, const float *__restrict__ b3,
                 const float *__restrict__ T, float *__restrict__ Y, bf16 *__restrict__ dZ2,
                 bf16 *__restrict__ dZ2T, float *__restrict__ gW3, float *__restrict__ gb3,
                 double *__restrict__ loss) {
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
+    constexpr int SP = kH + 8;  // row pitch of the staged gradient (bf16)
+    __shared__ __align__(16) bf16 sG[kOutRows * SP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r0 = blockIdx.x * kOutRows;
     float aW3[2][8];
 #pragma unroll
     for (int o = 0; o < 2; o++)
@@ -195,56 +234,71 @@ __global__ void __launch_bounds__(256)
         w3[0][u] = __bfloat162float(W3[lane * 8 + u]);
         w3[1][u] = __bfloat162float(W3[kH + lane * 8 + u]);
     }
-    for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows_pad; r += warps) {
-        if (r >= m) {  // padding rows of the batch: exact zero gradients
+    for (int i = 0; i < kOutRows / 8; i++) {
+        const int rl = warp * (kOutRows / 8) + i, r = r0 + rl;
+        uint4 gq = make_uint4(0u, 0u, 0u, 0u);  // the row's 8 gradients (bf16), 0 if padding
+        if (r < m) {
+            const uint4 hq = *reinterpret_cast<const uint4 *>(H2 + (size_t)r * kH + lane * 8);
+            const bf16 *hb = reinterpret_cast<const bf16 *>(&hq);
+            float h[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) h[u] = __bfloat162float(hb[u]);
+            float y0 = 0.f, y1 = 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                y0 = fmaf(w3[0][u], h[u], y0);
+                y1 = fmaf(w3[1][u], h[u], y1);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                y0 += __shfl_xor_sync(0xffffffffu, y0, o);
+                y1 += __shfl_xor_sync(0xffffffffu, y1, o);
+            }
+            y0 += b3[0];
+            y1 += b3[1];
+            if (lane == 0 && Y) {
+                Y[2 * r] = y0;
+                Y[2 * r + 1] = y1;
+            }
             if (T) {
+                const float e0 = y0 - T[2 * r], e1 = y1 - T[2 * r + 1];
+                if (lane == 0) aloss += (double)e0 * e0 + (double)e1 * e1;
+                const float d0 = 2.0f * e0 / (float)m, d1 = 2.0f * e1 / (float)m;
+                ab3[0] += d0;
+                ab3[1] += d1;
+                const float4 za = *reinterpret_cast<const float4 *>(Z2 + (size_t)r * kH + lane * 8);
+                const float4 zb = *reinterpret_cast<const float4 *>(Z2 + (size_t)r * kH + lane * 8 + 4);
+                const float z[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+                bf16 *gb = reinterpret_cast<bf16 *>(&gq);
 #pragma unroll
                 for (int u = 0; u < 8; u++) {
-                    const int c = lane * 8 + u;
-                    dZ2[(size_t)r * kH + c] = __float2bfloat16_rn(0.f);
-                    dZ2T[(size_t)c * rows_pad + r] = __float2bfloat16_rn(0.f);
+                    aW3[0][u] = fmaf(d0, h[u], aW3[0][u]);
+                    aW3[1][u] = fmaf(d1, h[u], aW3[1][u]);
+                    gb[u] = __float2bfloat16_rn((d0 * w3[0][u] + d1 * w3[1][u]) * gelu_df(z[u]));
                 }
             }
-            continue;
         }
-        float h[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++) h[u] = __bfloat162float(H2[(size_t)r * kH + lane * 8 + u]);
-        float y0 = 0.f, y1 = 0.f;
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            y0 = fmaf(w3[0][u], h[u], y0);
-            y1 = fmaf(w3[1][u], h[u], y1);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            y0 += __shfl_xor_sync(0xffffffffu, y0, o);
-            y1 += __shfl_xor_sync(0xffffffffu, y1, o);
-        }
-        y0 += b3[0];
-        y1 += b3[1];
-        if (lane == 0 && Y) {
-            Y[2 * r] = y0;
-            Y[2 * r + 1] = y1;
-        }
-        if (!T) continue;
-        const float e0 = y0 - T[2 * r], e1 = y1 - T[2 * r + 1];
-        if (lane == 0) aloss += (double)e0 * e0 + (double)e1 * e1;
-        const float d0 = 2.0f * e0 / (float)m, d1 = 2.0f * e1 / (float)m;
-        ab3[0] += d0;
-        ab3[1] += d1;
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            const int c = lane * 8 + u;
-            aW3[0][u] = fmaf(d0, h[u], aW3[0][u]);
-            aW3[1][u] = fmaf(d1, h[u], aW3[1][u]);
-            const float g = (d0 * w3[0][u] + d1 * w3[1][u]) * gelu_df(Z2[(size_t)r * kH + c]);
-            const bf16 gb = __float2bfloat16_rn(g);
-            dZ2[(size_t)r * kH + c] = gb;
-            dZ2T[(size_t)c * rows_pad + r] = gb;
+        if (T && r < rows_pad) {
+            *reinterpret_cast<uint4 *>(dZ2 + (size_t)r * kH + lane * 8) = gq;
+            *reinterpret_cast<uint4 *>(sG + rl * SP + lane * 8) = gq;
         }
     }
     if (!T) return;
+    __syncthreads();
+    // transposed copy: thread c writes unit c of the CTA's 32 rows, 8 rows per
+    // 16-byte store
+    {
+        const int c = threadIdx.x;
+#pragma unroll
+        for (int q = 0; q < kOutRows; q += 8) {
+            if (r0 + q >= rows_pad) break;
+            uint4 v;
+            bf16 *vb = reinterpret_cast<bf16 *>(&v);
+#pragma unroll
+            for (int k = 0; k < 8; k++) vb[k] = sG[(q + k) * SP + c];
+            *reinterpret_cast<uint4 *>(dZ2T + (size_t)c * rows_pad + r0 + q) = v;
+        }
+    }
 #pragma unroll
     for (int o = 0; o < 2; o++)
 #pragma unroll
@@ -423,15 +477,15 @@ int forward_backward(pxsne_mlp *M, int m, bool train) {
     e.Z = M->Z1;
     e.H = M->H1;
     e.HT = train ? M->H1T : nullptr;
-    MCK(M, (gemm<256, EPI_Z_GELU>(st, rp, kH, M->dp, M->dp, M->Xb, M->dp, M->W1b, M->dp, e)));
+    MCK(M, (gemm<64, EPI_Z_GELU>(st, rp, kH, M->dp, M->dp, M->Xb, M->dp, M->W1b, M->dp, e)));
     // layer 2
     e.bias = M->w + L.b2;
     e.Z = M->Z2;
     e.H = M->H2;
     e.HT = nullptr;
-    MCK(M, (gemm<256, EPI_Z_GELU>(st, rp, kH, kH, kH, M->H1, kH, M->W2b, kH, e)));
+    MCK(M, (gemm<64, EPI_Z_GELU>(st, rp, kH, kH, kH, M->H1, kH, M->W2b, kH, e)));
     // output layer (+ loss, dW3, db3, dZ2)
-    const int ob = (rp + 7) / 8 < 1184 ? (rp + 7) / 8 : 1184;
+    const int ob = (rp + kOutRows - 1) / kOutRows;
     k_out_layer<<<ob, 256, 0, st>>>(m, rp, M->H2, M->Z2, M->W3b, M->w + L.b3,
                                     train ? M->Tb : nullptr, M->Yb, M->dZ2, M->dZ2T,
                                     M->g + L.W3, M->g + L.b3, M->loss);
@@ -443,7 +497,7 @@ int forward_backward(pxsne_mlp *M, int m, bool train) {
     a.ld = kH;
     a.rows = kH;
     a.acc = M->g + L.W2;
-    MCK(M, (gemm<256, EPI_ATOMIC>(st, kH, kH, rp, 1024, M->dZ2T, rp, M->H1T, rp, a)));
+    MCK(M, (gemm<64, EPI_ATOMIC>(st, kH, kH, rp, kSplitK, M->dZ2T, rp, M->H1T, rp, a)));
     k_colsum<<<128, kH, 0, st>>>(m, M->dZ2, M->g + L.b2);
     MCK(M, cudaGetLastError());
     // dZ1 = (dZ2 W2) * GELU'(Z1)
@@ -455,15 +509,11 @@ int forward_backward(pxsne_mlp *M, int m, bool train) {
     b.Z = M->Z1;
     b.H = M->dZ1;
     b.HT = M->dZ1T;
-    MCK(M, (gemm<256, EPI_DGELU>(st, rp, kH, kH, kH, M->dZ2, kH, M->W2Tb, kH, b)));
+    MCK(M, (gemm<64, EPI_DGELU>(st, rp, kH, kH, kH, M->dZ2, kH, M->W2Tb, kH, b)));
     // dW1 = dZ1^T X
     a.ld = M->d;
     a.acc = M->g + L.W1;
-    if (M->d <= 128) {
-        MCK(M, (gemm<128, EPI_ATOMIC>(st, kH, M->d, rp, 1024, M->dZ1T, rp, M->XT, rp, a)));
-    } else {
-        MCK(M, (gemm<256, EPI_ATOMIC>(st, kH, M->d, rp, 1024, M->dZ1T, rp, M->XT, rp, a)));
-    }
+    MCK(M, (gemm<64, EPI_ATOMIC>(st, kH, M->d, rp, kSplitK, M->dZ1T, rp, M->XT, rp, a)));
     k_colsum<<<128, kH, 0, st>>>(m, M->dZ1, M->g + L.b1);
     MCK(M, cudaGetLastError());
     return PXSNE_OK;
