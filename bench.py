@@ -535,17 +535,27 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    ctx.step(args.steps)
-    e1.record(stream)
-    e1.synchronize()
+    # events every 100 iterations as well (recorded on the same stream between
+    # graph launches): the cost of an iteration along the schedule
+    chunk = 100
+    marks = [torch.cuda.Event(enable_timing=True)]
+    marks[0].record(stream)
+    done = 0
+    while done < args.steps:
+        c = min(chunk, args.steps - done)
+        ctx.step(c)
+        done += c
+        marks.append(torch.cuda.Event(enable_timing=True))
+        marks[-1].record(stream)
+    marks[-1].synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     ck = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    ms = marks[0].elapsed_time(marks[-1])
+    along = [{"t": f"{chunk * q}..{min(chunk * (q + 1), args.steps) - 1}",
+              "ms_per_iteration": marks[q].elapsed_time(marks[q + 1]) /
+              (min(chunk * (q + 1), args.steps) - chunk * q)} for q in range(len(marks) - 1)]
     ctx.sync()
     ms = max_over_ranks(ms, dist, "cuda")
     value = job_rate(args.steps, ms / 1000.0, ws)
@@ -685,6 +695,7 @@ def run_gpu(args):
                           "warp_steps": wsteps, "nodes": nodes,
                           "lanes_per_step": tst / wsteps if wsteps else None},
             "profiled_total_ms": prof_total, "p_construction_s": p_seconds, "knn": knn,
+            "along_schedule": along,
             "kl_after_timed": kl_after,
             "clocks": ck, "e2e": e2e, "cpu_baseline": cpu, "warmstart": warm,
             "studies": studies,
