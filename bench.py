@@ -310,6 +310,47 @@ def screen_sweep(px, X, Y0, params_kw, levels, iters, stream, torch):
     return out
 
 
+# The survey's smaller workloads: (generator, n, screen, iterations, PCA dims)
+SMALL_CONFIGS = {"gauss10": ("gauss10", 2000, 9, 500, None),
+                 "protos784": ("protos784", 70000, 10, 1000, 50)}
+
+
+def small_configs_study(px, stream, torch):
+    """The whole method on the smaller workloads through the public calls: the
+    10-Gaussian mixture (n = 2000, 512^2, 500 iterations) and the 784-D
+    prototype data (n = 70,000, PCA to 50 on the GPU, 1024^2, 1000
+    iterations): P construction time, iterations/s of the full schedule
+    (CUDA events), final KL."""
+    import datagen
+    out = {}
+    for name, (gen, n, L, iters, dpca) in SMALL_CONFIGS.items():
+        X, _ = getattr(datagen, gen)(0, n=n)
+        Y0 = datagen.init_y0(0, n)
+        p = px.Params(log2_r=L, theta=0.5, k=90, perplexity=30.0)
+        with px.Context(p, stream=stream.cuda_stream) as c:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Xin = px.pca(X, dpca)[0] if dpca else X
+            c.affinities(Xin)
+            t_p = time.perf_counter() - t0
+            c.init(Y0)
+            c.step(3)
+            c.sync()
+            c.init(Y0)
+            c.sync()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.step(iters)
+            e1.record(stream)
+            e1.synchronize()
+            c.sync()
+            out[name] = {"n": n, "screen": f"{1 << L}^2", "iterations": iters,
+                         "pca": dpca, "p_construction_s": t_p,
+                         "it_per_s": iters / (e0.elapsed_time(e1) / 1e3), "kl": c.kl()}
+    return out
+
+
 def geometric_centre_study(px, X, Y0, params_kw, steps, com, stream, torch):
     """The paper's own approximation of a cell by its geometric centre (Sec.
     4.1; the tree keeps counts only) on the same data, start and schedule as
@@ -649,6 +690,19 @@ def run_gpu(args):
             v1, det1, w1, reps1 = repeat(max(1000, args.cpu_rows // 16), 8.0)
         finally:
             oracle.set_num_threads(cores)
+        # the oracle on the smaller workloads: the whole first iteration from Y0
+        # (tree, BH and attraction of every row, update, rescale)
+        import datagen
+        cpu["small_configs"] = {}
+        for name, (gen, nn, LL, _, _) in SMALL_CONFIGS.items():
+            Ys = datagen.init_y0(0, nn)
+            vals, wall = [], 0.0
+            while wall < 3.0 and len(vals) < 20:
+                vv, _, ww = oracle_sample(None, Ys, nn, LL, W["theta"], seed=len(vals))
+                vals.append(vv)
+                wall += ww
+            cpu["small_configs"][name] = {"value": float(np.mean(vals)), "unit": "it/s",
+                                          "cores": cores, "n": nn, "samples": len(vals)}
         cpu["one_thread"] = {"value": v1, "unit": "it/s", "cores": 1,
                              "sample": f"{det1['rows']} of {n} rows scaled by "
                                        f"{det1['scale']:.1f}, {reps1} samples ({w1:.1f} s of "
@@ -664,6 +718,7 @@ def run_gpu(args):
                 {"it_per_s": value, "kl": kl_after, "precision_k10": prec_after,
                  "tree_ms_per_iteration": {g: avg_ms[g] for g in ("k_snap_hist", "k_pyr_pass")}},
                 stream, torch) if n <= 2_000_000 else None,
+            "small_configs": small_configs_study(px, stream, torch),
             # (P is rebuilt for every screen: skipped for the 10M scale workload)
             "screen_sweep": screen_sweep(
                 px, X, Y0, dict(theta=W["theta"], k=W["k"], perplexity=W["perplexity"]),
