@@ -179,8 +179,8 @@ def group_bytes(n, nnz, L):
 # DRAM bytes per launch from one ncu capture of the current kernels at full size
 # (dram__bytes_read.sum + dram__bytes_write.sum, profiles/traffic_gmm128_n1M.md);
 # to be set to None whenever the kernel changes
-TRAFFIC_BYTES = {"k_bh_traverse": 47.33e6, "k_attract": 1.2946e9, "k_snap_hist": 49.51e6,
-                 "k_pyr_pass": 153.47e6}
+TRAFFIC_BYTES = {"k_bh_traverse": 47.31e6, "k_attract": 1.2945e9, "k_snap_hist": 49.50e6,
+                 "k_pyr_pass": 153.13e6}
 
 FLOP_TEST = 10    # offset, d^2 and criterion of one tested cell
 FLOP_ACCEPT = 10  # kernel value, N w, N w^2 and the three accumulations
