@@ -156,7 +156,7 @@ def measured_peaks():
 
 # Algorithmic bytes (HBM) per launch of each kernel group, and FLOPs of the
 # traversal per tested / accepted (point, cell) pair.
-RELABEL_EVERY = 25  # the library refreshes the attraction's relabelled P this often
+RELABEL_EVERY = 100  # the library refreshes the attraction's relabelled P this often
 
 
 def group_bytes(n, nnz, L):

@@ -213,7 +213,7 @@ cudaError_t launch_attract(pxsne_ctx *c, cudaStream_t st);
 cudaError_t launch_count_traversal(pxsne_ctx *c);
 // Renumber P's rows and columns in the Morton order of the last tree (perm)
 // into rp2/col2/val2 and refresh aperm, ainv and zp.
-constexpr int kRelabelEvery = 25;
+constexpr int kRelabelEvery = 100;
 cudaError_t launch_relabel(pxsne_ctx *c, cudaStream_t st);
 // out[0..m] = exclusive scan of in[0..m) with out[m] = the total
 cudaError_t scan_u32_to_i64(const uint32_t *in, int64_t m, int64_t *out, cudaStream_t st);

@@ -105,10 +105,10 @@ def test_tree_and_forces_at_init(run):
     check_state(ctx, P, sample_rows(3, 512))
 
 
-def test_tree_and_forces_after_100_iterations(run):
-    # the attraction's relabelled copy of P is refreshed four times on the way
+def test_tree_and_forces_after_250_iterations(run):
+    # the attraction's relabelled copy of P is refreshed twice on the way
     _, ctx, P = run
-    ctx.step(100)
+    ctx.step(250)
     check_state(ctx, P, sample_rows(4, 512))
 
 
