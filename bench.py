@@ -310,7 +310,7 @@ def screen_sweep(px, X, Y0, params_kw, levels, iters, stream, torch):
     return out
 
 
-# The survey's smaller workloads: (generator, n, screen, iterations, PCA dims)
+# The smaller workloads: (generator, n, screen, iterations, PCA dims)
 SMALL_CONFIGS = {"gauss10": ("gauss10", 2000, 9, 500, None),
                  "protos784": ("protos784", 70000, 10, 1000, 50)}
 
@@ -380,7 +380,7 @@ def geometric_centre_study(px, X, Y0, params_kw, steps, com, stream, torch):
 
 
 def warmstart_experiment(px, ctx, X, Y0, args, torch):
-    """Learned warm start (survey config 4), on ctx's P (the bench workload).
+    """Learned warm start, on ctx's P (the bench workload).
 
     Training data: embeddings the method produced for independent draws of the
     same mixture (args.warm_seeds draws of args.warm_n rows).  The first is the

@@ -651,8 +651,8 @@ double orc_nbr_precision(const int32_t *knn_hd, int32_t kh, int32_t k, int64_t n
 }
 
 /* ------------------------------------------------------------------------ */
-/* Learned warm start (not in the paper; the initialiser of the north-star
- * "learned part"): y = W3 g(W2 g(W1 x + b1) + b2) + b3 with g the exact GELU
+/* Learned warm start (not in the paper; a learned initialiser that
+ * warm-starts the method): y = W3 g(W2 g(W1 x + b1) + b2) + b3 with g the exact GELU
  * g(z) = z Phi(z) = 0.5 z (1 + erf(z / sqrt 2)), dimensions d -> H -> H -> 2.
  * Weights row-major: W1[H x d], W2[H x H], W3[2 x H].  Loss over a batch of m
  * rows: L = (1/m) sum_r ||y_r - t_r||^2.  Returns L; when grad != NULL writes

@@ -31,7 +31,7 @@ def px():
 
 @pytest.fixture(scope="module")
 def gauss():
-    """Config-1 workload: oracle P and an oracle state after 60 iterations
+    """The 2000-point mixture (10 Gaussians in D = 50): oracle P and an oracle state after 60 iterations
     (clustered under exaggeration)."""
     X, lab = datagen.gauss10(0)
     P, idx, d2, bad = oracle.affinities(X, 30.0, 90)
@@ -171,7 +171,7 @@ def test_one_step_matches_oracle(px, gauss):
 
 
 def test_full_run_kl_within_one_percent(px, gauss):
-    """Config 1 (n=2000, 512^2, 500 iterations): injected oracle P, same Y0."""
+    """The 2000-point mixture (512^2, 500 iterations): injected oracle P, same Y0."""
     X, P, Y0, _ = gauss
     params = oracle.Params(L=9)
     st = oracle.State.from_y0(Y0)
