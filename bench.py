@@ -557,14 +557,22 @@ def run_gpu(args):
     # bf16 share the tensor rate)
     knn_ms = ctx.knn_time_ms()
     kx, ki, kpath = ctx.knn_counters()
-    knn_flop = 2.0 * n * n * X.shape[1]
+    kskip, kpairs = ctx.knn_pruning()
+    # the products the tensor cores actually formed: the (query tile,
+    # candidate tile) pairs of 128 x 128 rows not skipped by the tile bound,
+    # 2 * 128 * 128 * Dp FLOP each (rows padded to the tiles, D to Dp)
+    Dp = (X.shape[1] + 63) // 64 * 64
+    knn_dense = 2.0 * n * n * X.shape[1]
+    knn_flop = (kpairs - kskip) * 2.0 * 128 * 128 * Dp if kpairs else knn_dense
     pk, pk_kind = measured_peaks()
     knn = {"kernel": "k_knn_tc" if kpath == 1 else "k_knn_tile", "ms": knn_ms,
            "bound": "tensor", "achieved": knn_flop / (knn_ms / 1e3) / 1e12,
            "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
            "frac": knn_flop / (knn_ms / 1e3) / 1e12 / pk["bf16_tflops"],
+           "dense_equivalent_tflops": knn_dense / (knn_ms / 1e3) / 1e12,
            "peak_source": f"bf16_tflops of MEASURED_PEAKS.json ({pk_kind})",
-           "exact_rerank_per_row": kx / n, "insertions_per_row": ki / n}
+           "exact_rerank_per_row": kx / n, "insertions_per_row": ki / n,
+           "tile_pairs_skipped": kskip / kpairs if kpairs else None}
     ctx.init(Y0)
     ctx.step(max(args.warmup, 3) if args.warmup >= 0 else 3)  # graph capture + warm-up
     ctx.sync()

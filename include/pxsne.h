@@ -236,6 +236,13 @@ int pxsne_get_counters(pxsne_ctx *ctx, uint64_t *n_accept, uint64_t *n_test,
  * Synchronises. */
 int pxsne_get_knn_counters(pxsne_ctx *ctx, uint64_t *exact, uint64_t *inserted, int32_t *path);
 
+/* Tile pruning of the last tensor-core neighbour search: (query tile,
+ * candidate tile) pairs of 128 x 128 rows it skipped because the triangle
+ * inequality on the tiles' centroids and radii put every candidate beyond the
+ * query rows' current k-th distances, and the number of pairs (T^2).  Both 0
+ * after the FP32 search.  Any pointer may be NULL.  Synchronises. */
+int pxsne_get_knn_pruning(pxsne_ctx *ctx, uint64_t *skipped_pairs, uint64_t *pairs);
+
 /* Device time in milliseconds of the last neighbour-search kernel (the brute
  * force of Sec. 3.3's kNN pattern; CUDA events around its launch on the
  * context's stream).  PXSNE_E_STATE if no search has run.  Synchronises. */

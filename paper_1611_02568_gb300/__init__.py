@@ -108,6 +108,7 @@ def load(path: str | None = None):
                                      C.POINTER(u64)]
     L.pxsne_get_knn_counters.argtypes = [vp, C.POINTER(u64), C.POINTER(u64), C.POINTER(i32)]
     L.pxsne_get_knn_time.argtypes = [vp, C.POINTER(C.c_double)]
+    L.pxsne_get_knn_pruning.argtypes = [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]
     L.pxsne_test_bounded_wait.argtypes = [vp, i32, C.POINTER(C.c_uint32)]
     L.pxsne_set_schedule.argtypes = [vp, C.POINTER(_CParams)]
     L.pxsne_nbr_precision.argtypes = [vp, i32, vp, i32, C.c_int, C.POINTER(C.c_double), vp]
@@ -359,6 +360,13 @@ class Context:
         rc = self.L.pxsne_test_bounded_wait(self.h, int(polls), C.byref(f))
         return rc, f.value
 
+    def knn_pruning(self):
+        """(skipped (query tile, candidate tile) pairs, all pairs) of the last
+        tensor-core neighbour search."""
+        a, b = C.c_uint64(), C.c_uint64()
+        self._ck(self.L.pxsne_get_knn_pruning(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
     def knn_time_ms(self):
         """Device time of the last neighbour-search kernel (ms)."""
         ms = C.c_double()
@@ -479,7 +487,7 @@ EXPORTED = ["pxsne_default_params", "pxsne_create", "pxsne_destroy", "pxsne_last
             "pxsne_sync", "pxsne_get_sizes", "pxsne_get_P", "pxsne_set_P", "pxsne_get_knn",
             "pxsne_set_state", "pxsne_get_state", "pxsne_get_tree", "pxsne_get_forces",
             "pxsne_device_bytes", "pxsne_step_profiled", "pxsne_kernel_group_name",
-            "pxsne_get_knn_time", "pxsne_test_bounded_wait",
+            "pxsne_get_knn_time", "pxsne_test_bounded_wait", "pxsne_get_knn_pruning",
             "pxsne_get_counters", "pxsne_kl_noalloc", "pxsne_kl_noalloc_max_rows",
             "pxsne_get_knn_counters", "pxsne_set_schedule", "pxsne_mlp_create",
             "pxsne_mlp_destroy", "pxsne_mlp_last_error", "pxsne_mlp_num_params",

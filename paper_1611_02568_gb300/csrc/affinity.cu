@@ -258,6 +258,9 @@ constexpr int kTcAcc = 4;        // TMEM accumulators (4 x 128 columns)
 constexpr int kTcThreads = 192;  // warps 0-3 filter, 4 loads, 5 issues MMAs
 constexpr int kTcPolls = 1 << 22;
 constexpr uint32_t kTcSleepNs = 2000u;  // suspend hint of the pipeline waits
+// per candidate tile: h_j (128), g_j (128), then per 32-column chunk min h and
+// max g (4 + 4): 264 floats, 1056 bytes (a multiple of 16 for the bulk copy)
+constexpr int kHG = 2 * kTcCols + 8;
 
 __global__ void k_absmax(int64_t m, const float *__restrict__ X, unsigned *out) {
     unsigned v = 0u;
@@ -292,17 +295,69 @@ __global__ void k_to_half_img(int64_t n, int D, int Dp, int64_t T, float scale,
         *reinterpret_cast<const uint4 *>(h);
 }
 
-// Per candidate tile t: h_j = (1-eps)|c_j|^2 (+inf past n) at HG[256 t + j]
-// and |c_j| at HG[256 t + 128 + j].
+// Per candidate tile t (kHG floats from HG + kHG t): h_j = (1-eps)|c_j|^2
+// (+inf past n), then g_j = |c_j|, then for each 32-column chunk the min of its
+// h_j and the max of its g_j (a warp covers one chunk).
 __global__ void k_tile_norms(int64_t n, int64_t T, float eps_abs, const float *__restrict__ nrm,
                              float *__restrict__ HG) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= T * kTcCols) return;
+    if (i >= T * kTcCols) return;  // whole warps (T * 128 is a multiple of 32)
     const int64_t t = i / kTcCols;
     const int j = (int)(i % kTcCols);
     const float c2 = i < n ? nrm[i] : 0.f;
-    HG[t * 2 * kTcCols + j] = i < n ? (1.0f - eps_abs) * c2 : INFINITY;
-    HG[t * 2 * kTcCols + kTcCols + j] = sqrtf(c2);
+    const float h = i < n ? (1.0f - eps_abs) * c2 : INFINITY, g = sqrtf(c2);
+    float *hg = HG + t * kHG;
+    hg[j] = h;
+    hg[kTcCols + j] = g;
+    float hmin = h, gmax = g;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        hmin = fminf(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
+        gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+    }
+    if ((j & 31) == 0) {
+        hg[2 * kTcCols + (j >> 5)] = hmin;
+        hg[2 * kTcCols + 4 + (j >> 5)] = gmax;
+    }
+}
+
+// Per tile t of the ordered rows: centroid (thread d sums dimension d over
+// the tile's rows) and radius = max over its rows of |x - centroid|, raised by
+// 1e-4 relative so that FP32 rounding cannot make it too small.  The
+// triangle inequality then bounds every distance between two tiles from below
+// by |c_a - c_b| - r_a - r_b (any centroid would do).
+__global__ void __launch_bounds__(128)
+    k_tile_bounds(int64_t n, int D, int Dp, const float *__restrict__ X, float *__restrict__ cent,
+                  float *__restrict__ rad) {
+    __shared__ float s_c[256];
+    __shared__ float s_r[4];
+    const int64_t t = blockIdx.x;
+    const int64_t r0 = t * kTcRows;
+    const int cnt = (int)(n - r0 < kTcRows ? n - r0 : kTcRows);
+    const int tid = threadIdx.x;
+    for (int d = tid; d < Dp; d += blockDim.x) {
+        float sum = 0.f;
+        if (d < D)
+            for (int r = 0; r < cnt; r++) sum += X[(r0 + r) * D + d];
+        const float c = d < D ? sum / (float)cnt : 0.f;
+        s_c[d] = c;
+        cent[t * Dp + d] = c;
+    }
+    __syncthreads();
+    float m = 0.f;
+    if (tid < cnt) {
+        float acc = 0.f;
+        for (int d = 0; d < D; d++) {
+            const float df = X[(r0 + tid) * D + d] - s_c[d];
+            acc = fmaf(df, df, acc);
+        }
+        m = sqrtf(acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0) s_r[tid >> 5] = m;
+    __syncthreads();
+    if (tid == 0) rad[t] = fmaxf(fmaxf(s_r[0], s_r[1]), fmaxf(s_r[2], s_r[3])) * 1.0001f + 1e-30f;
 }
 
 // Exact FP32 squared distance between rows a and b by one thread, summed in
@@ -424,12 +479,14 @@ struct KnnTcArgs {
     const float *X;       // FP32 rows (exact distances)
     const uint8_t *img;   // FP16 tile images
     const float *nrm;     // |x|^2
-    const float *HG;      // per tile: h_j then |c_j|
+    const float *HG;      // per tile: h_j, |c_j|, chunk bounds (kHG floats)
     const uint32_t *order;  // sorted position -> row of X (the locality order)
     int32_t *out_idx;
     float *out_d2;
     unsigned *err;
     u64 *stats;
+    const float *cent;    // per tile: centroid of its rows (Dp floats, FP32)
+    const float *rad;     // per tile: an upper bound of |x - centroid| over its rows
 };
 
 // The i-th candidate tile a CTA visits: its own, then alternately the next
@@ -446,6 +503,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
         bar_te[kTcAcc], bar_hf[kTcAcc], bar_he[kTcAcc];
     __shared__ uint32_t tslot;
     __shared__ volatile int s_abort;
+    // pruning: per filter warp the largest current k-th distance of its rows
+    // (only decreases), and the candidate tile of each kept slot (-1: end)
+    __shared__ volatile float s_taumax[4];
+    __shared__ volatile int s_tile[8];
+    __shared__ float s_cq[128];  // the query tile's centroid (loader warp)
     // 1024-byte aligned base for the swizzled operand tiles
     uint8_t *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     const int64_t n = a.n, T = a.T;
@@ -454,11 +516,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
     uint8_t *sA = smem;
     uint8_t *sB = smem + tile_bytes;
     // per accumulator: h_j (128) then g_j (128) of its tile
-    float *hbuf = reinterpret_cast<float *>(sB + (size_t)kTcStages * tile_bytes);  // [4][256]
+    float *hbuf = reinterpret_cast<float *>(sB + (size_t)kTcStages * tile_bytes);  // [4][kHG]
     // per row: its k best (d2, index) so far as a max-heap on (d2, index),
     // rows at an odd stride (no bank conflicts between the rows)
     const int ks = k | 1;
-    KnnEntry *lst = reinterpret_cast<KnnEntry *>(hbuf + kTcAcc * 2 * kTcCols);
+    KnnEntry *lst = reinterpret_cast<KnnEntry *>(hbuf + kTcAcc * kHG);
     // per filter warp: queued survivors (row lane << 24 | candidate index),
     // their exact d2 and, per entry, the previous entry of the same row
     uint32_t *qc_all = reinterpret_cast<uint32_t *>(lst + kTcRows * ks);
@@ -484,6 +546,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             tc::mbar_init(&bar_he[b], 4);
         }
         s_abort = 0;
+        for (int w = 0; w < 4; w++) s_taumax[w] = INFINITY;
     }
     tc::fence_before();
     __syncthreads();
@@ -491,40 +554,118 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
     const uint32_t tbase = tslot;
 
     if (warp == 4) {
-        // ---- producer: candidate tiles and their h values
+        // ---- producer: candidate tiles and their h values.  A tile whose
+        // rows are all farther from every query row than that row's current
+        // k-th distance (triangle inequality on the tiles' centroids and
+        // radii, against the largest current k-th distance of the CTA) is
+        // skipped.  The kept tiles form a sequence j = 0, 1, ... that the
+        // MMA issuer and the filter warps follow through s_tile; the entry
+        // after the last kept tile is -1 (barriers completed without data).
+        // the query tile's centroid, for every lane
+        for (int d = lane; d < a.Dp; d += 32) s_cq[d] = a.cent[qt * a.Dp + d];
+        __syncwarp();
+        const float rq = a.rad[qt];
         if (lane == 0) {
             tc::mbar_expect_tx(&bar_a, tile_bytes);
             tc::bulk_g2s(sA, a.img + qt * tile_bytes, tile_bytes, &bar_a);
-            int64_t i = 0;
-            for (; i < T && !s_abort; i++) {
-                const int64_t t = knn_tile_at(qt, i, T);
-                const int s = (int)(i % kTcStages), b = (int)(i % kTcAcc);
-                if (i >= kTcStages &&
-                    !tc::mbar_wait_sleep(&bar_se[s], (uint32_t)((i / kTcStages - 1) & 1), kTcPolls, kTcSleepNs)) {
-                    s_abort = 1;
-                    atomicOr(a.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
-                    break;
+        }
+        int64_t j = 0;  // kept tiles so far
+        u64 n_skip = 0u;
+        bool fail = false;
+        int64_t n_sf = 0, n_hf = 0;  // stage and h copies issued (kept tiles 0 ..)
+        // the tiles are judged 32 at a time, one per lane; the kept ones are
+        // then issued in order
+        for (int64_t i0 = 0; i0 <= T && !fail; i0 += 32) {
+            // (one reading of the abort flag for the whole warp)
+            if (__shfl_sync(0xffffffffu, s_abort, 0)) break;
+            const int64_t il = i0 + lane;
+            const bool in = il < T;
+            const int64_t tl = in ? knn_tile_at(qt, il, T) : 0;
+            float dd = 0.f;
+            if (in) {
+                const float4 *ct = reinterpret_cast<const float4 *>(a.cent + tl * a.Dp);
+                for (int d4 = 0; d4 < a.Dp / 4; d4++) {
+                    const float4 c = __ldg(ct + d4);
+                    const float e0 = s_cq[4 * d4] - c.x, e1 = s_cq[4 * d4 + 1] - c.y;
+                    const float e2 = s_cq[4 * d4 + 2] - c.z, e3 = s_cq[4 * d4 + 3] - c.w;
+                    dd = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, dd))));
                 }
-                tc::mbar_expect_tx(&bar_sf[s], tile_bytes);
-                tc::bulk_g2s(sB + (size_t)s * tile_bytes, a.img + t * tile_bytes, tile_bytes,
-                             &bar_sf[s]);
-                if (i >= kTcAcc &&
-                    !tc::mbar_wait_sleep(&bar_he[b], (uint32_t)((i / kTcAcc - 1) & 1), kTcPolls, kTcSleepNs)) {
-                    s_abort = 1;
-                    atomicOr(a.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
-                    i++;  // the stage copy above is in flight
-                    break;
-                }
-                tc::mbar_expect_tx(&bar_hf[b], 2 * kTcCols * 4);
-                tc::bulk_g2s(hbuf + b * 2 * kTcCols, a.HG + t * 2 * kTcCols, 2 * kTcCols * 4,
-                             &bar_hf[b]);
             }
-            // copies still in flight complete before the CTA exits
+            const float taum = fmaxf(fmaxf(s_taumax[0], s_taumax[1]), fmaxf(s_taumax[2], s_taumax[3]));
+            const float lbd = sqrtf(dd) * 0.9999f - rq - (in ? a.rad[tl] : 0.f);
+            const bool skip = in && il > 0 && lbd > 0.f && lbd * lbd > taum * 1.0001f;
+            n_skip += (u64)__popc(__ballot_sync(0xffffffffu, skip));
+            // kept tiles of this block, and the end mark after the last block
+            unsigned keep = __ballot_sync(0xffffffffu, in && !skip);
+            const bool last_block = i0 + 32 > T;
+            while (keep || last_block) {
+                const bool end = keep == 0u;  // (only in the last block)
+                int64_t t = -1;
+                if (!end) {
+                    const int src = __ffs(keep) - 1;
+                    keep &= keep - 1u;
+                    t = __shfl_sync(0xffffffffu, tl, src);
+                }
+            const int s = (int)(j % kTcStages), b = (int)(j % kTcAcc);
+            // every lane waits (a converged warp is suspended and woken as
+            // one); lane 0 writes the slot and issues the copies
+            bool ok = j < kTcStages ||
+                      tc::mbar_wait_sleep(&bar_se[s], (uint32_t)((j / kTcStages - 1) & 1), kTcPolls, kTcSleepNs);
+            ok = __all_sync(0xffffffffu, ok);
+            if (ok) {
+                if (lane == 0) {
+                    s_tile[j & 7] = (int)t;
+                    if (end) {
+                        tc::mbar_arrive(&bar_sf[s]);
+                    } else {
+                        tc::mbar_expect_tx(&bar_sf[s], tile_bytes);
+                        tc::bulk_g2s(sB + (size_t)s * tile_bytes, a.img + t * tile_bytes, tile_bytes,
+                                     &bar_sf[s]);
+                    }
+                }
+                if (!end) n_sf++;
+                __syncwarp();
+                ok = j < kTcAcc ||
+                     tc::mbar_wait_sleep(&bar_he[b], (uint32_t)((j / kTcAcc - 1) & 1), kTcPolls, kTcSleepNs);
+                ok = __all_sync(0xffffffffu, ok);
+                if (ok) {
+                    if (lane == 0) {
+                        if (end) {
+                            tc::mbar_arrive(&bar_hf[b]);
+                        } else {
+                            tc::mbar_expect_tx(&bar_hf[b], kHG * 4);
+                            tc::bulk_g2s(hbuf + b * kHG, a.HG + t * kHG, kHG * 4, &bar_hf[b]);
+                        }
+                    }
+                    if (!end) n_hf++;
+                }
+            }
+            if (!ok) {
+                fail = true;
+                if (lane == 0) {
+                    s_abort = 1;
+                    atomicOr(a.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
+                }
+            }
+            __syncwarp();
+            if (fail) break;
+            if (end) break;
+            j++;
+            }
+        }
+        if (lane == 0) {
+            atomicAdd(&a.stats[2], n_skip);
+            // copies still in flight complete before the CTA exits: those of
+            // the last kept tiles (kept tile q used stage q % 2 and h slot
+            // q % 4).  After the end mark the copies into the slots it reused
+            // are known complete (their consumers released them first), and
+            // waiting on them by phase parity would be ambiguous.
+            const int64_t ws = fail ? kTcStages : kTcStages - 1, wh = fail ? kTcAcc : kTcAcc - 1;
             tc::mbar_wait(&bar_a, 0u, kTcPolls);
-            for (int64_t j = (i > kTcStages ? i - kTcStages : 0); j < i; j++)
-                tc::mbar_wait(&bar_sf[j % kTcStages], (uint32_t)((j / kTcStages) & 1), kTcPolls);
-            for (int64_t j = (i > kTcAcc ? i - kTcAcc : 0); j < i; j++)
-                tc::mbar_wait(&bar_hf[j % kTcAcc], (uint32_t)((j / kTcAcc) & 1), kTcPolls);
+            for (int64_t q = (n_sf > ws ? n_sf - ws : 0); q < n_sf; q++)
+                tc::mbar_wait(&bar_sf[q % kTcStages], (uint32_t)((q / kTcStages) & 1), kTcPolls);
+            for (int64_t q = (n_hf > wh ? n_hf - wh : 0); q < n_hf; q++)
+                tc::mbar_wait(&bar_hf[q % kTcAcc], (uint32_t)((q / kTcAcc) & 1), kTcPolls);
         }
     } else if (warp == 5) {
         // ---- MMA issuer
@@ -532,14 +673,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             const uint32_t idesc = tc::idesc_f16(kTcRows, kTcCols, 0);
             const uint32_t a0 = tc::smem_u32(sA);
             bool ok = tc::mbar_wait(&bar_a, 0u, kTcPolls);
-            int64_t i = 0;
-            for (; ok && i < T && !s_abort; i++) {
+            int64_t i = 0;  // kept tiles multiplied
+            bool ended = false;
+            for (; ok && i <= T && !s_abort; i++) {
                 const int s = (int)(i % kTcStages), b = (int)(i % kTcAcc);
                 ok = tc::mbar_wait_sleep(&bar_sf[s], (uint32_t)((i / kTcStages) & 1), kTcPolls, kTcSleepNs);
                 if (ok && i >= kTcAcc)
                     ok = tc::mbar_wait_sleep(&bar_te[b], (uint32_t)((i / kTcAcc - 1) & 1), kTcPolls, kTcSleepNs);
                 if (!ok) break;
                 tc::fence_after();
+                if (s_tile[i & 7] < 0) {
+                    // the end: the filter warps learn it through an
+                    // accumulator completed without data
+                    tc::mbar_arrive(&bar_tf[b]);
+                    ended = true;
+                    break;
+                }
                 const uint32_t b0 = tc::smem_u32(sB + (size_t)s * tile_bytes);
                 for (int kk = 0; kk < a.Dp / 16; kk++) {
                     const uint32_t off =
@@ -554,8 +703,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                 s_abort = 1;
                 atomicOr(a.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
             }
-            // MMAs still in flight finish before TMEM is freed
-            for (int64_t j = (i > kTcAcc ? i - kTcAcc : 0); j < i; j++)
+            // MMAs still in flight finish before TMEM is freed.  After the end
+            // mark, the MMA into the accumulator it reused is known complete
+            // (the filter warps released it first), and waiting on it by
+            // phase parity would be ambiguous.
+            const int64_t wa = ended ? kTcAcc - 1 : kTcAcc;
+            for (int64_t j = (i > wa ? i - wa : 0); j < i; j++)
                 tc::mbar_wait(&bar_tf[j % kTcAcc], (uint32_t)((j / kTcAcc) & 1), kTcPolls);
         }
     } else {
@@ -622,9 +775,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             __syncwarp();
             head = kNil;
             qn = 0u;
+            // the largest current k-th distance of the warp's rows, for the
+            // loader's pruning (rows past n do not count)
+            float tm = qvalid ? tau : -INFINITY;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tm = fmaxf(tm, __shfl_xor_sync(0xffffffffu, tm, o));
+            if (lane == 0) s_taumax[warp] = tm;
         };
-        for (int64_t i = 0; i < T; i++) {
-            const int64_t t = knn_tile_at(qt, i, T);
+        for (int64_t i = 0; i <= T; i++) {  // the kept tiles, then the end mark
             const int b = (int)(i % kTcAcc);
             const uint32_t par = (uint32_t)((i / kTcAcc) & 1);
             // warp-uniform: every lane takes the same path into the aligned
@@ -638,8 +796,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                 break;
             }
             tc::fence_after();
+            const int tt = s_tile[i & 7];
+            if (tt < 0) break;  // no more kept tiles
+            const int64_t t = tt;
             const int64_t c0 = t * kTcCols;
-            const float *hb = hbuf + b * 2 * kTcCols;
+            const float *hb = hbuf + b * kHG;
             // all 128 columns of the warp's rows in one round trip; the
             // accumulator is released right after, h and g after the filter
             uint32_t raw[4][32];
@@ -658,22 +819,40 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                 float v[32];
 #pragma unroll
                 for (int j = 0; j < 32; j++) v[j] = __uint_as_float(raw[ci][j]);
-                // e_j = (1-eps)|c|^2 - kappa|q||c| - 2 q.c (in place of v)
-                float mn[8];
+                // Chunk bound: e_j >= min h - kappa|q| max g - 2 max_j q.c
+                // (-2 < 0, kappa|q| >= 0).  A chunk whose bound exceeds the
+                // threshold by more than the FP32 roundings of both sides
+                // (margin 2^-19 of the terms' sizes, eight times their bound)
+                // has no survivor, and its per-candidate values are not formed.
+                float mx[8];
 #pragma unroll
-                for (int j4 = 0; j4 < 8; j4++) {
-                    const float4 h4 = *reinterpret_cast<const float4 *>(hb + cb + 4 * j4);
-                    const float4 g4 = *reinterpret_cast<const float4 *>(hb + kTcCols + cb + 4 * j4);
-                    v[4 * j4] = fmaf(-Bq, g4.x, fmaf(cneg, v[4 * j4], h4.x));
-                    v[4 * j4 + 1] = fmaf(-Bq, g4.y, fmaf(cneg, v[4 * j4 + 1], h4.y));
-                    v[4 * j4 + 2] = fmaf(-Bq, g4.z, fmaf(cneg, v[4 * j4 + 2], h4.z));
-                    v[4 * j4 + 3] = fmaf(-Bq, g4.w, fmaf(cneg, v[4 * j4 + 3], h4.w));
-                    mn[j4] = fminf(fminf(v[4 * j4], v[4 * j4 + 1]), fminf(v[4 * j4 + 2], v[4 * j4 + 3]));
+                for (int j4 = 0; j4 < 8; j4++)
+                    mx[j4] = fmaxf(fmaxf(v[4 * j4], v[4 * j4 + 1]), fmaxf(v[4 * j4 + 2], v[4 * j4 + 3]));
+                const float vmax = fmaxf(fmaxf(fmaxf(mx[0], mx[1]), fmaxf(mx[2], mx[3])),
+                                         fmaxf(fmaxf(mx[4], mx[5]), fmaxf(mx[6], mx[7])));
+                const float hmin = hb[2 * kTcCols + ci], gmax = hb[2 * kTcCols + 4 + ci];
+                const float lb = fmaf(cneg, vmax, fmaf(-Bq, gmax, hmin));
+                const float margin = (fabsf(hmin) + Bq * gmax + fabsf(cneg * vmax)) * 1.9073486e-6f;
+                const bool near = qvalid && !(lb > tauA + margin);
+                float m = INFINITY;
+                if (near) {
+                    // e_j = (1-eps)|c|^2 - kappa|q||c| - 2 q.c (in place of v)
+                    float mn[8];
+#pragma unroll
+                    for (int j4 = 0; j4 < 8; j4++) {
+                        const float4 h4 = *reinterpret_cast<const float4 *>(hb + cb + 4 * j4);
+                        const float4 g4 = *reinterpret_cast<const float4 *>(hb + kTcCols + cb + 4 * j4);
+                        v[4 * j4] = fmaf(-Bq, g4.x, fmaf(cneg, v[4 * j4], h4.x));
+                        v[4 * j4 + 1] = fmaf(-Bq, g4.y, fmaf(cneg, v[4 * j4 + 1], h4.y));
+                        v[4 * j4 + 2] = fmaf(-Bq, g4.z, fmaf(cneg, v[4 * j4 + 2], h4.z));
+                        v[4 * j4 + 3] = fmaf(-Bq, g4.w, fmaf(cneg, v[4 * j4 + 3], h4.w));
+                        mn[j4] = fminf(fminf(v[4 * j4], v[4 * j4 + 1]), fminf(v[4 * j4 + 2], v[4 * j4 + 3]));
+                    }
+                    m = fminf(fminf(fminf(mn[0], mn[1]), fminf(mn[2], mn[3])),
+                              fminf(fminf(mn[4], mn[5]), fminf(mn[6], mn[7])));
                 }
-                const float m = fminf(fminf(fminf(mn[0], mn[1]), fminf(mn[2], mn[3])),
-                                      fminf(fminf(mn[4], mn[5]), fminf(mn[6], mn[7])));
                 uint32_t sm = 0u;
-                if (qvalid && m <= tauA) {
+                if (near && m <= tauA) {
                     // survivors:
                     //   (1-eps)|c|^2 - kappa|q||c| - 2 q.c <= tau - (1-eps)|q|^2
 #pragma unroll
@@ -763,7 +942,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
 }
 
 static size_t knn_tc_smem(int Dp, int k) {
-    return (size_t)(1 + kTcStages) * kTcRows * Dp * 2 + (size_t)kTcAcc * 2 * kTcCols * 4 +
+    return (size_t)(1 + kTcStages) * kTcRows * Dp * 2 + (size_t)kTcAcc * kHG * 4 +
            (size_t)kTcRows * (k | 1) * 8 + (size_t)4 * kTcQueue * (4 + 4 + 2) + 1024;
 }
 
@@ -808,7 +987,7 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         c->knn_path = 1;
         unsigned *amax = nullptr;
         unsigned *err = &c->sc->err;
-        if ((e = cudaMemsetAsync(&c->sc->knn_exact, 0, 2 * sizeof(u64), st))) return e;
+        if ((e = cudaMemsetAsync(&c->sc->knn_exact, 0, 3 * sizeof(u64), st))) return e;
         if ((e = cudaMallocAsync(&amax, sizeof(unsigned), st))) return e;
         if ((e = cudaMemsetAsync(amax, 0, sizeof(unsigned), st))) return e;
         k_absmax<<<1184, 256, 0, st>>>(n * D, Xdev, amax);
@@ -921,12 +1100,19 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         uint8_t *img = nullptr;
         float *HG = nullptr;
         if ((e = cudaMallocAsync(&img, img_bytes, st))) return e;
-        if ((e = cudaMallocAsync(&HG, (size_t)T * 2 * kTcCols * sizeof(float), st))) return e;
+        if ((e = cudaMallocAsync(&HG, (size_t)T * kHG * sizeof(float), st))) return e;
         const int64_t nchunks = T * kTcRows * (Dp / 8);
         k_to_half_img<<<(unsigned)((nchunks + 255) / 256), 256, 0, st>>>(n, D, Dp, T, scale, Xo,
                                                                           img);
         k_tile_norms<<<(unsigned)((T * kTcCols + 255) / 256), 256, 0, st>>>(n, T, eps_abs, ns, HG);
         if ((e = cudaGetLastError())) return e;
+        // tile centroids and radii (the loader's pruning bound)
+        float *cent = nullptr, *rad = nullptr;
+        if ((e = cudaMallocAsync(&cent, (size_t)T * Dp * sizeof(float), st))) return e;
+        if ((e = cudaMallocAsync(&rad, (size_t)T * sizeof(float), st))) return e;
+        k_tile_bounds<<<(unsigned)T, 128, 0, st>>>(n, D, Dp, Xo, cent, rad);
+        if ((e = cudaGetLastError())) return e;
+        c->knn_tiles = T;
         if ((e = cudaFuncSetAttribute(k_knn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem_tc)))
             return e;
@@ -948,12 +1134,16 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         ka.out_d2 = d2;
         ka.err = err;
         ka.stats = &c->sc->knn_exact;
+        ka.cent = cent;
+        ka.rad = rad;
         if ((e = knn_mark(c, 0, st))) return e;
         k_knn_tc<<<(unsigned)T, kTcThreads, smem_tc, st>>>(ka);
         if ((e = cudaGetLastError())) return e;
         if ((e = knn_mark(c, 1, st))) return e;
         cudaFreeAsync(img, st);
         cudaFreeAsync(HG, st);
+        cudaFreeAsync(cent, st);
+        cudaFreeAsync(rad, st);
         cudaFreeAsync(amax, st);
         cudaFreeAsync(piv, st);
         cudaFreeAsync(cell, st);

@@ -790,6 +790,18 @@ int pxsne_get_counters(pxsne_ctx *c, uint64_t *n_accept, uint64_t *n_test,
     return PXSNE_OK;
 }
 
+int pxsne_get_knn_pruning(pxsne_ctx *c, uint64_t *skipped_pairs, uint64_t *pairs) {
+    if (!c) return PXSNE_E_ARG;
+    DevScalars h;
+    CK(c, cudaMemcpyAsync(&h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    int rc = check_device(c, nullptr);
+    if (rc) return rc;
+    const bool tc_path = c->knn_path == 1;
+    if (skipped_pairs) *skipped_pairs = tc_path ? h.knn_skip : 0u;
+    if (pairs) *pairs = tc_path ? (uint64_t)c->knn_tiles * (uint64_t)c->knn_tiles : 0u;
+    return PXSNE_OK;
+}
+
 int pxsne_get_knn_counters(pxsne_ctx *c, uint64_t *exact, uint64_t *inserted, int32_t *path) {
     if (!c) return PXSNE_E_ARG;
     DevScalars h;

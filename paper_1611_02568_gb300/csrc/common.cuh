@@ -43,6 +43,7 @@ struct DevScalars {
     u64 n_nodes;         // stack entries popped by the last traversal
     u64 knn_exact;       // exact distances computed by the last neighbour search
     u64 knn_insert;      // list insertions of the last neighbour search
+    u64 knn_skip;        // (query tile, candidate tile) pairs it skipped by the tile bound
 };
 
 // The pyramid of cell records.  Cell (l, m) (level l, Morton index m) is at
@@ -138,6 +139,7 @@ struct pxsne_ctx {
     float *beta = nullptr;
     int32_t knn_k = 0;
     int knn_path = -1;  // 1: tensor-core kNN, 0: FP32 CUDA-core kNN
+    int64_t knn_tiles = 0;  // row tiles of the last tensor-core search
     cudaEvent_t knn_ev[2] = {nullptr, nullptr};  // around the last search kernel
     bool knn_timed = false;
 
