@@ -400,7 +400,8 @@ template <int DP>
 __global__ void __launch_bounds__(256)
     k_assign_cells(int64_t n, int D, int m, const float *__restrict__ X,
                    const float *__restrict__ piv, const float *__restrict__ pn,
-                   uint32_t *__restrict__ cell) {
+                   const float *__restrict__ nrm, uint32_t *__restrict__ cell,
+                   float *__restrict__ dpiv) {
     extern __shared__ float s_piv[];  // kPivChunk x DP
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     float xr[DP];
@@ -434,7 +435,30 @@ __global__ void __launch_bounds__(256)
             }
         }
     }
-    if (i < n) cell[i] = bi;
+    if (i < n) {
+        cell[i] = bi;
+        dpiv[i] = best + nrm[i];  // squared distance to the nearest pivot
+    }
+}
+
+// Sum of v[0..n) into *out (FP64, atomics per block).
+__global__ void k_sum_f64(int64_t n, const float *__restrict__ v, double *out) {
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)v[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+// Rows far from their nearest pivot (outliers, and rows of small clusters
+// that drew no pivot) go to a cell of their own after the others, so that
+// they do not share tiles with a cluster's rows.
+__global__ void k_far_rows(int64_t n, const float *__restrict__ dpiv, float thr, uint32_t far_cell,
+                           uint32_t *__restrict__ cell) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n && dpiv[i] > thr) cell[i] = far_cell;
 }
 
 __global__ void k_cell_count(int64_t n, const uint32_t *__restrict__ cell, uint32_t *cnt) {
@@ -1050,7 +1074,11 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         if ((e = cudaMallocAsync(&piv, (size_t)m * (D + 1) * sizeof(float), st))) return e;
         if ((e = cudaMallocAsync(&cell, (size_t)n * sizeof(uint32_t), st))) return e;
         if ((e = cudaMallocAsync(&order, (size_t)n * sizeof(uint32_t), st))) return e;
-        if ((e = cudaMallocAsync(&ccnt, (size_t)m * sizeof(uint32_t), st))) return e;
+        if ((e = cudaMallocAsync(&ccnt, (size_t)(m + 1) * sizeof(uint32_t), st))) return e;
+        float *dpiv = nullptr;
+        double *dsum = nullptr;
+        if ((e = cudaMallocAsync(&dpiv, (size_t)n * sizeof(float), st))) return e;
+        if ((e = cudaMallocAsync(&dsum, sizeof(double), st))) return e;
         if ((e = cudaMallocAsync(&Xs, (size_t)n * D * sizeof(float), st))) return e;
         if ((e = cudaMallocAsync(&ns, (size_t)n * sizeof(float), st))) return e;
         float *pn = piv + (size_t)m * D;
@@ -1066,27 +1094,38 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
             if ((e = cudaFuncSetAttribute(k_assign_cells<64>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a)))
                 return e;
-            k_assign_cells<64><<<ablocks, 256, smem_a, st>>>(n, D, m, Xdev, piv, pn, cell);
+            k_assign_cells<64><<<ablocks, 256, smem_a, st>>>(n, D, m, Xdev, piv, pn, nrm, cell, dpiv);
         } else {
             if ((e = cudaFuncSetAttribute(k_assign_cells<128>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a)))
                 return e;
-            k_assign_cells<128><<<ablocks, 256, smem_a, st>>>(n, D, m, Xdev, piv, pn, cell);
+            k_assign_cells<128><<<ablocks, 256, smem_a, st>>>(n, D, m, Xdev, piv, pn, nrm, cell, dpiv);
         }
-        if ((e = cudaMemsetAsync(ccnt, 0, (size_t)m * sizeof(uint32_t), st))) return e;
+        // far rows: squared distance to the nearest pivot above 3x the mean
+        // (within a cluster that holds a pivot the distances concentrate near
+        // the mean; an outlier or a row of a cluster without a pivot is
+        // several times farther)
+        if ((e = cudaMemsetAsync(dsum, 0, sizeof(double), st))) return e;
+        k_sum_f64<<<ablocks < 1184 ? ablocks : 1184, 256, 0, st>>>(n, dpiv, dsum);
+        double hsum = 0.0;
+        if ((e = cudaMemcpyAsync(&hsum, dsum, sizeof(double), cudaMemcpyDeviceToHost, st))) return e;
+        if ((e = cudaStreamSynchronize(st))) return e;
+        k_far_rows<<<ablocks, 256, 0, st>>>(n, dpiv, (float)(3.0 * hsum / (double)n), (uint32_t)m,
+                                            cell);
+        if ((e = cudaMemsetAsync(ccnt, 0, (size_t)(m + 1) * sizeof(uint32_t), st))) return e;
         k_cell_count<<<ablocks, 256, 0, st>>>(n, cell, ccnt);
-        std::vector<uint32_t> hc((size_t)m);
-        if ((e = cudaMemcpyAsync(hc.data(), ccnt, (size_t)m * sizeof(uint32_t),
+        std::vector<uint32_t> hc((size_t)m + 1);
+        if ((e = cudaMemcpyAsync(hc.data(), ccnt, (size_t)(m + 1) * sizeof(uint32_t),
                                  cudaMemcpyDeviceToHost, st)))
             return e;
         if ((e = cudaStreamSynchronize(st))) return e;
         uint32_t run = 0u;
-        for (int q = 0; q < m; q++) {
+        for (int q = 0; q <= m; q++) {
             const uint32_t v = hc[(size_t)q];
             hc[(size_t)q] = run;
             run += v;
         }
-        if ((e = cudaMemcpyAsync(ccnt, hc.data(), (size_t)m * sizeof(uint32_t),
+        if ((e = cudaMemcpyAsync(ccnt, hc.data(), (size_t)(m + 1) * sizeof(uint32_t),
                                  cudaMemcpyHostToDevice, st)))
             return e;
         k_cell_scatter<<<ablocks, 256, 0, st>>>(n, cell, ccnt, order);
@@ -1149,6 +1188,8 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         cudaFreeAsync(cell, st);
         cudaFreeAsync(order, st);
         cudaFreeAsync(ccnt, st);
+        cudaFreeAsync(dpiv, st);
+        cudaFreeAsync(dsum, st);
         cudaFreeAsync(Xs, st);
         cudaFreeAsync(ns, st);
         return cudaFreeAsync(nrm, st);
