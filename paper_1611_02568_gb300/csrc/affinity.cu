@@ -236,13 +236,18 @@ __global__ void __launch_bounds__(kKnnThreads)
 // distance plus that bound; only those get their exact FP32 distance
 // (sum of squared differences) and enter the row's sorted list.
 //
-// One CTA owns 128 query rows and sweeps every candidate tile (all CTAs in the
-// same order, so that concurrent CTAs share each tile through L2).  Warp roles: warp 4 streams candidate tiles (pre-swizzled FP16
-// images, one bulk copy each) into a ring of shared-memory stages; warp 5
-// issues the MMAs into four TMEM accumulators; warps 0-3 (one query row per
-// thread, TMEM lanes 32w..32w+31) filter.  With h_j = (1-eps)|c_j|^2 and
-// g_j = |c_j| (staged with the tile), each (row, candidate) costs two FMAs and
-// a min: a 32-column chunk is skipped when
+// One CTA owns 128 query rows and sweeps the candidate tiles outward from its
+// own in the locality order (neighbouring CTAs read the same tiles at about
+// the same time, so each tile is shared through L2).  Warp roles: warp 4
+// judges the candidate tiles (a tile whose rows all lie beyond the query rows'
+// current k-th distances, by the triangle inequality on tile centroids and
+// radii, is skipped) and streams the kept ones (pre-swizzled FP16 images, one
+// bulk copy each) into a ring of shared-memory stages; warp 5 issues the MMAs
+// into four TMEM accumulators; warps 0-3 (one query row per thread, TMEM lanes
+// 32w..32w+31) filter.  With h_j = (1-eps)|c_j|^2 and g_j = |c_j| (staged with
+// the tile), a 32-column chunk is skipped when a bound from its min h, max g
+// and max q.c already exceeds the threshold; otherwise each (row, candidate)
+// costs two FMAs and a min: the chunk is skipped when
 //   min_j (h_j - kappa |q| g_j - 2 q.c_j) > tau - (1-eps)|q|^2,
 // and otherwise the same per-column values pick the survivors.  A warp queues the
 // survivors of its 32 rows (a chain per row through the queue) over as many
