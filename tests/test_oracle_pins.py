@@ -378,6 +378,42 @@ def test_bh_theta0_equals_pixel_bruteforce():
     np.testing.assert_allclose(Zb, Zr, rtol=1e-12)
 
 
+def test_bh_theta0_geometric_equals_pixel_midpoint_bruteforce():
+    # Sec. 4.1's geometric-centre approximation at theta = 0: every leaf is
+    # reached, and each stands for its points at the pixel's midpoint; the
+    # own pixel counts its other points, still at the midpoint
+    L = 5
+    F = 32 - L
+    rng = np.random.default_rng(25)
+    n = 300
+    pix = rng.integers(0, 2 ** L, (n, 2))
+    pix[:40] = pix[40:80]       # shared pixels
+    z = ((pix.astype(np.int64) << F) + rng.integers(0, 2 ** F, (n, 2))).astype(np.uint32)
+    s = np.array([0.9e-9, 1.3e-9])
+    Fb, Zb, _ = oracle.bh_repulsion(z, s, L, 0.0, centre_mode=1)
+    groups = {}
+    for i in range(n):
+        groups.setdefault((int(pix[i, 0]), int(pix[i, 1])), []).append(i)
+    Fr = np.zeros((n, 2))
+    Zr = np.zeros(n)
+    half = 2.0 ** (F - 1)
+    for i in range(n):
+        for (px, py), members in groups.items():
+            N = sum(1 for j in members if j != i)
+            if N == 0:
+                continue
+            dx = s[0] * (int(z[i, 0]) - (px * 2.0 ** F + half))
+            dy = s[1] * (int(z[i, 1]) - (py * 2.0 ** F + half))
+            w = 1.0 / (1.0 + dx * dx + dy * dy)
+            Zr[i] += N * w
+            Fr[i] += N * w * w * np.array([dx, dy])
+    np.testing.assert_allclose(Fb, Fr, rtol=1e-9, atol=1e-12 * np.abs(Fr).max())
+    np.testing.assert_allclose(Zb, Zr, rtol=1e-12)
+    # and it differs from the centre-of-mass tree (the two modes are distinct)
+    Fc, _, _ = oracle.bh_repulsion(z, s, L, 0.0)
+    assert np.abs(Fc - Fb).max() > 1e-3 * np.abs(Fb).max()
+
+
 def test_bh_theta_half_close_to_exact():
     rng = np.random.default_rng(16)
     L = 9
