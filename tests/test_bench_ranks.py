@@ -1,6 +1,7 @@
-"""The multi-replica timing of bench.py on CPU ranks (gloo, world size 2): every
-rank sees the slowest replica's time, and the job rate counts all replicas'
-units over it."""
+"""Host logic of bench.py on the CPU: the multi-replica timing on gloo ranks
+(world size 2: every rank sees the slowest replica's time, and the job rate
+counts all replicas' units over it), the reference arm's JSON line, and the
+parsing of the clocks sampled during the timed region."""
 import os
 import socket
 import sys
@@ -75,3 +76,39 @@ def test_reference_arm_line_on_cpu():
     env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
     out1 = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
     assert out1.returncode == 0 and out1.stdout.strip() == ""
+
+
+def test_clock_sampler_parses_a_fake_nvidia_smi(tmp_path, monkeypatch):
+    """The clocks record of the bench line: median SM clock, the highest
+    maximum, and every throttle reason seen Active, read from nvidia-smi's CSV
+    (a stand-in script on PATH; unparsable lines are skipped)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    lines = [
+        "0, 1900, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1950, 2070, 1100.4, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2010, 2070, 1200.0, 0x8, Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+    ]
+    (tmp_path / "out.csv").write_text("\n".join(lines) + "\n")
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text(f"#!/bin/sh\ncat '{tmp_path / 'out.csv'}'\nexec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}{os.pathsep}{os.environ['PATH']}")
+    cs = bench.ClockSampler(0)
+    cs.start()
+    import time
+    time.sleep(0.5)
+    rec = cs.stop()
+    assert rec == {"sm_mhz": 1950.0, "sm_max_mhz": 2070.0,
+                   "reasons": ["hw_slowdown", "sw_power_cap"], "samples": 3}
+
+
+def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("PATH", str(tmp_path))
+    cs = bench.ClockSampler(0)
+    cs.start()
+    assert cs.stop() is None
