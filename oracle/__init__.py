@@ -7,8 +7,8 @@ library: it neither imports nor links anything from it.
 
 Parity pins: every function here is pinned in ``tests/test_oracle_pins.py``
 against closed forms, invariants, finite differences or brute force; see the
-header of that file for the mapping.  ``nbr_precision`` is pinned by its
-identity cases only.
+header of that file for the mapping.  ``tests/test_oracle_mutants.py`` checks
+that planted mistakes in this package fail those pins.
 """
 from __future__ import annotations
 

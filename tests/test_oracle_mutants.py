@@ -1,0 +1,175 @@
+"""Planted mistakes in the oracle are caught by its pins.
+
+Each case below plants one plausible mistake in a scratch copy of the oracle:
+a dropped term, a wrong sign, index or operand, a swapped axis, a missing
+normalisation.  The copy is built, and ``tests/test_oracle_pins.py`` is run
+against it in a child process.  At least one pin must fail, as a reported
+test failure and not as a crash.  An unmodified copy must pass the same run.
+The oracle in the repository is never modified.
+"""
+import os
+import shutil
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+C_SRC = "oracle/pxsne_oracle.c"
+PY_SRC = "oracle/__init__.py"
+
+# (what the mistake is, file, text in the oracle, text planted instead)
+MUTANTS = [
+    # kNN (Sec. 3.3)
+    ("knn: ties broken towards the higher index", C_SRC,
+     "da < db || (da == db && ja < jb)", "da < db || (da == db && ja > jb)"),
+    ("knn: the point itself not excluded", C_SRC,
+     "if (j == i) continue;\n            const float *xj", "const float *xj"),
+    ("knn: first coordinate dropped from the distance", C_SRC,
+     "for (int32_t d = 0; d < D; d++) {", "for (int32_t d = 1; d < D; d++) {"),
+    # perplexity bisection (Sec. 3.2)
+    ("perplexity: entropy with the wrong sign on the mean term", C_SRC,
+     "H = log(sum) + beta * hs / sum;", "H = log(sum) - beta * hs / sum;"),
+    ("perplexity: target entropy in bits", C_SRC,
+     "const double target = log(perplexity);", "const double target = log2(perplexity);"),
+    ("perplexity: bracket moved the wrong way", C_SRC,
+     "if (H > target) { /* too flat: sharpen */", "if (H < target) { /* too flat: sharpen */"),
+    ("perplexity: rows not normalised", C_SRC,
+     "for (int32_t j = 0; j < k; j++) p[j] /= sum;", ""),
+    # symmetrisation (Sec. 3.3)
+    ("symmetrize: divided by n instead of 2n", C_SRC,
+     "val[nnz] = v / (2.0 * (double)n);", "val[nnz] = v / (double)n;"),
+    ("symmetrize: transposed entry not added", C_SRC,
+     "t[o].r = j; t[o].c = (int32_t)i;", "t[o].r = i; t[o].c = j;"),
+    # screen map (Eq. z1/z2)
+    ("init: extremes taken over the other axis", C_SRC,
+     "double v = Y0[2 * i + d];", "double v = Y0[2 * i + (1 - d)];"),
+    # tree (Sec. 4.1)
+    ("morton: x and y bits swapped", C_SRC,
+     "m |= ((px >> b) & 1u) << (2 * b);\n        m |= ((py >> b) & 1u) << (2 * b + 1);",
+     "m |= ((py >> b) & 1u) << (2 * b);\n        m |= ((px >> b) & 1u) << (2 * b + 1);"),
+    ("pyramid: y sums accumulate x", C_SRC, "sy[c] += z[2 * i + 1];", "sy[c] += z[2 * i];"),
+    ("pyramid: leaves one level too coarse", C_SRC,
+     "uint32_t m = orc_morton(z[2 * i] >> F, z[2 * i + 1] >> F);",
+     "uint32_t m = orc_morton(z[2 * i] >> (F + 1), z[2 * i + 1] >> (F + 1));"),
+    # Barnes-Hut repulsion (Sec. 3.3, Eq. bh_criteria)
+    ("bh: centre-of-mass remainder added, not subtracted", C_SRC,
+     "- (double)r / (double)N;", "+ (double)r / (double)N;"),
+    ("bh: own point left in the x sum of its leaf", C_SRC, "Sx -= zx;", ""),
+    ("bh: own point counted in its leaf", C_SRC,
+     "N -= 1;\n                if (N == 0) continue;", "if (N == 0) continue;"),
+    ("bh: force missing one kernel factor", C_SRC, "fx += Nw * w * dx;", "fx += Nw * dx;"),
+    ("bh: acceptance test reversed", C_SRC, "(rc2 < th2 * dd)", "(rc2 > th2 * dd)"),
+    ("bh: cell size of the child level", C_SRC,
+     "double rc2 = (s0 * W) * (s0 * W) + (s1 * W) * (s1 * W);",
+     "double rc2 = 0.25 * ((s0 * W) * (s0 * W) + (s1 * W) * (s1 * W));"),
+    ("bh: cell width along x instead of the diagonal", C_SRC,
+     "double rc2 = (s0 * W) * (s0 * W) + (s1 * W) * (s1 * W);",
+     "double rc2 = (s0 * W) * (s0 * W);"),
+    ("bh geometric: centre at the cell's corner", C_SRC,
+     "((double)cx * W + 0.5 * W)", "((double)cx * W)"),
+    ("bh geometric: x and y cell bits swapped", C_SRC,
+     "cx |= ((mc >> (2 * b)) & 1u) << b;\n                    cy |= ((mc >> (2 * b + 1)) & 1u) << b;",
+     "cy |= ((mc >> (2 * b)) & 1u) << b;\n                    cx |= ((mc >> (2 * b + 1)) & 1u) << b;"),
+    # exact repulsion and attraction (Eq. grad)
+    ("exact repulsion: w instead of w^2", C_SRC, "fx += w * w * dx;", "fx += w * dx;"),
+    ("attraction: wrong sign", C_SRC, "fx += val[e] * w * dx;", "fx -= val[e] * w * dx;"),
+    ("attraction: kernel squared", C_SRC,
+     "fx += val[e] * w * dx;\n            fy += val[e] * w * dy;",
+     "fx += val[e] * w * w * dx;\n            fy += val[e] * w * w * dy;"),
+    # optimiser step (Eq. grad, BH-SNE's gains and momentum)
+    ("update: exaggeration applied to repulsion too", C_SRC,
+     "double g = 4.0 * (alpha * Fattr[k] - Frep[k] / Z);",
+     "double g = 4.0 * alpha * (Fattr[k] - Frep[k] / Z);"),
+    ("update: repulsion not normalised by Z", C_SRC,
+     "double g = 4.0 * (alpha * Fattr[k] - Frep[k] / Z);",
+     "double g = 4.0 * (alpha * Fattr[k] - Frep[k]);"),
+    ("update: gains rule inverted", C_SRC, "(sgn(g) != sgn(u[k]))", "(sgn(g) == sgn(u[k]))"),
+    ("update: minimum gain not applied", C_SRC, "if (gn < min_gain) gn = min_gain;", ""),
+    ("update: momentum with the wrong sign", C_SRC,
+     "u[k] = mu * u[k] - eta * gn * g;", "u[k] = -mu * u[k] - eta * gn * g;"),
+    # screen rescale (Sec. 4.2, Eq. beta_scaling)
+    ("rescale: compensation of s not applied", C_SRC,
+     "s[d] = s[d] * ldexp((double)gamma, -32);", ""),
+    ("rescale: offset from the maximum", C_SRC,
+     "(uint64_t)(zhat[2 * i + d] - mn) << 32", "(uint64_t)(mx - zhat[2 * i + d]) << 32"),
+    # KL (Eq. cost_func)
+    ("kl: q not normalised by Z", C_SRC,
+     "double q = 1.0 / ((1.0 + dx * dx + dy * dy) * Z);",
+     "double q = 1.0 / (1.0 + dx * dx + dy * dy);"),
+    ("kl: ratio inverted", C_SRC, "c += p * log(p / q);", "c += p * log(q / p);"),
+    # neighbourhood precision (Eq. nei_prec)
+    ("nbr_precision: distance along x only", C_SRC,
+     "double dd = dx * dx + dy * dy;\n            int32_t p;",
+     "double dd = dx * dx;\n            int32_t p;"),
+    ("nbr_precision: not divided by k", C_SRC,
+     "return (double)hits / ((double)k * (double)m);", "return (double)hits / (double)m;"),
+    # warm-start MLP
+    ("gelu': missing factor z", C_SRC,
+     "+ z * exp(-0.5 * z * z) / sqrt(2.0 * M_PI);", "+ exp(-0.5 * z * z) / sqrt(2.0 * M_PI);"),
+    ("mlp: first layer's derivative taken at the second layer's input", C_SRC,
+     "dz1[c] = dh * gelu_d(z1[c]);", "dz1[c] = dh * gelu_d(z2[c]);"),
+    ("mlp: W2 not transposed in the backward pass", C_SRC,
+     "dh += dz2[a] * W2[(size_t)a * H + c];", "dh += dz2[a] * W2[(size_t)c * H + a];"),
+    ("mlp: loss gradient without the factor 2", C_SRC,
+     "dy[o] = 2.0 * e / (double)m;", "dy[o] = e / (double)m;"),
+    ("mlp: bias b2 left out", C_SRC, "double s = b2[a];", "double s = 0.0;"),
+    # PCA (Sec. 5.1.1 pre-processing)
+    ("pca: data not centred", PY_SRC, "Xc = Xd - mu\n", "Xc = Xd\n"),
+    ("pca: smallest eigenvalues kept", PY_SRC,
+     'order = np.argsort(-lam, kind="stable")[:dout]',
+     'order = np.argsort(lam, kind="stable")[:dout]'),
+]
+
+COPY = ["oracle/__init__.py", C_SRC, "tests/conftest.py", "tests/test_oracle_pins.py",
+        "tests/golden", "datagen"]
+
+
+def _scratch(base, name):
+    d = os.path.join(base, name)
+    for rel in COPY:
+        src, dst = os.path.join(ROOT, rel), os.path.join(d, rel)
+        os.makedirs(os.path.dirname(dst), exist_ok=True)
+        if os.path.isdir(src):
+            shutil.copytree(src, dst, ignore=shutil.ignore_patterns("__pycache__", "_build"))
+        else:
+            shutil.copy(src, dst)
+    return d
+
+
+def _run_pins(d):
+    env = dict(os.environ, OMP_NUM_THREADS="2", PYTHONDONTWRITEBYTECODE="1")
+    env.pop("PYTHONPATH", None)
+    p = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "tests/test_oracle_pins.py"], cwd=d, env=env, capture_output=True,
+                       text=True, timeout=900)
+    return p.returncode, p.stdout[-3000:] + p.stderr[-2000:]
+
+
+def test_pins_catch_planted_mistakes(tmp_path):
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc is needed to build the oracle")
+    pytest.importorskip("sklearn")
+    jobs = [("control", None)]
+    for i, (what, rel, old, new) in enumerate(MUTANTS):
+        with open(os.path.join(ROOT, rel)) as f:
+            text = f.read()
+        assert text.count(old) == 1, f"{what}: the planted text must occur once in {rel}"
+        jobs.append((what, (rel, text.replace(old, new))))
+    dirs = []
+    for i, (what, edit) in enumerate(jobs):
+        d = _scratch(str(tmp_path), f"m{i:02d}")
+        if edit is not None:
+            rel, text = edit
+            with open(os.path.join(d, rel), "w") as f:
+                f.write(text)
+        dirs.append(d)
+    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    with ThreadPoolExecutor(workers) as ex:
+        results = list(ex.map(_run_pins, dirs))
+    rc0, out0 = results[0]
+    assert rc0 == 0, "the unmodified copy must pass its pins:\n" + out0
+    missed = [(what, rc, out) for (what, _), (rc, out) in zip(jobs[1:], results[1:])
+              if rc != 1 or "failed" not in out]
+    assert not missed, "\n\n".join(f"{w} (exit {rc}):\n{o[-1500:]}" for w, rc, o in missed)

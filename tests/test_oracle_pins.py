@@ -17,13 +17,26 @@ fails at least one test:
                  differences of the KL; net force zero
   bh_repulsion   theta = 0 with <= 1 point per pixel equals the exact sum;
                  theta = 0 in general equals a tree-free brute force over pixels
+                 (centres of mass; pixel midpoints in geometric-centre mode);
+                 the acceptance threshold on a hand-built tree sits at
+                 r_c / d = theta (r_c the cell diagonal, d the distance to the
+                 centre of mass; r_c / d^2 in the printed form); error falls
+                 with theta
   rescale        Python big-integer arithmetic; pixel range exactly 0..r-1
+  update         hand cases of the gains rule
   run            the fixed-point + rescale + beta run equals plain y-space
                  t-SNE (scikit-learn gradient) up to translation (Sec. 4.2's
                  claimed equivalence)
-  kl             scikit-learn, closed forms, KL >= 0
-  nbr_precision  identity cases (precision 1 for the same geometry, ~k/n for
-                 an unrelated one)
+  kl             scikit-learn, closed forms, KL >= 0, a stored value written
+                 by tests/golden/make_kl_target.py
+  nbr_precision  per-row brute force by a full stable argsort; identity cases
+                 (precision 1 for the same geometry, ~k/n for an unrelated one)
+  gelu, mlp      the erf definition and central differences; a closed-form
+                 forward pass; finite differences of the loss
+  pca            SVD of the centred matrix
+
+tests/test_oracle_mutants.py plants one such mistake at a time in a copy of
+the oracle and checks that these pins fail.
 """
 import json
 import math
@@ -412,6 +425,37 @@ def test_bh_theta0_geometric_equals_pixel_midpoint_bruteforce():
     # and it differs from the centre-of-mass tree (the two modes are distinct)
     Fc, _, _ = oracle.bh_repulsion(z, s, L, 0.0)
     assert np.abs(Fc - Fb).max() > 1e-3 * np.abs(Fb).max()
+
+
+@pytest.mark.parametrize("crit_mode", [0, 1])
+def test_bh_acceptance_threshold_is_the_cell_diagonal(crit_mode):
+    # Eq. bh_criteria on a hand-built tree (L = 3): point i alone in pixel
+    # (0, 0), three points in the level-1 cell x, y in [4, 8), one per
+    # level-2 child.  That cell is summarised by one interaction when
+    # r_c / d (crit_mode 0; r_c / d^2, the printed form, in crit_mode 1) is
+    # below theta, with r_c the diagonal of a level-1 cell and d the distance
+    # to its centre of mass; otherwise it is opened and its three points come
+    # back as three interactions.  Theta one part in 1e9 either side of the
+    # threshold must land on either side.
+    L = 3
+    F = 32 - L
+    s = np.array([1.3e-9, 0.8e-9])
+    pix = [(0, 0), (4, 4), (6, 5), (5, 7)]
+    sub = [(12345, 777), (2 ** 28, 3), (99, 2 ** 27), (5, 6)]
+    z = np.array([[(px << F) + a, (py << F) + b] for (px, py), (a, b) in zip(pix, sub)],
+                 dtype=np.uint32)
+    Wc = 2.0 ** 31            # width of a level-1 cell in ulps
+    rc = math.hypot(s[0] * Wc, s[1] * Wc)
+    cx = sum(int(v) for v in z[1:, 0]) / 3
+    cy = sum(int(v) for v in z[1:, 1]) / 3
+    d = math.hypot(s[0] * (int(z[0, 0]) - cx), s[1] * (int(z[0, 1]) - cy))
+    th_star = rc / d if crit_mode == 0 else rc / d ** 2
+    _, _, acc_hi = oracle.bh_repulsion(z, s, L, th_star * (1 + 1e-9), rows=[0],
+                                       crit_mode=crit_mode)
+    _, _, acc_lo = oracle.bh_repulsion(z, s, L, th_star * (1 - 1e-9), rows=[0],
+                                       crit_mode=crit_mode)
+    assert acc_hi[0] == 1
+    assert acc_lo[0] == 3
 
 
 def test_bh_theta_half_close_to_exact():
