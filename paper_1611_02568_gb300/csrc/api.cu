@@ -297,6 +297,10 @@ int pxsne_create(pxsne_ctx **out, const pxsne_params *p, void *stream) {
         cudaGetLastError();
         fail(nullptr, e == cudaErrorMemoryAllocation ? PXSNE_E_OOM : PXSNE_E_CUDA,
              "pxsne_create: %s", cudaGetErrorString(e));
+        if (c->sc) cudaFree(c->sc);
+        if (c->ev_join) cudaEventDestroy(c->ev_join);
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        if (c->side) cudaStreamDestroy(c->side);
         if (c->own_stream) cudaStreamDestroy(c->stream);
         delete c;
         return e == cudaErrorMemoryAllocation ? PXSNE_E_OOM : PXSNE_E_CUDA;
@@ -521,7 +525,16 @@ int pxsne_step_profiled(pxsne_ctx *c, int32_t iters, double *group_ms, int32_t n
     if (rc) return rc;
     if (iters < 1 || !group_ms || n_groups < KG_COUNT)
         return fail(c, PXSNE_E_ARG, "need iters >= 1 and %d group slots", (int)KG_COUNT);
-    std::vector<cudaEvent_t> ev((size_t)iters * (KG_COUNT + 1) + 2, nullptr);
+    // destroyed on every return path, the early ones included
+    struct Events {
+        std::vector<cudaEvent_t> v;
+        ~Events() {
+            for (auto e : v)
+                if (e) cudaEventDestroy(e);
+        }
+    } evs;
+    evs.v.assign((size_t)iters * (KG_COUNT + 1) + 2, nullptr);
+    std::vector<cudaEvent_t> &ev = evs.v;
     for (auto &e : ev) CK(c, cudaEventCreate(&e));
     cudaEvent_t *t0 = &ev[ev.size() - 2], *t1 = &ev[ev.size() - 1];
     CK(c, cudaEventRecord(*t0, c->stream));
@@ -553,7 +566,6 @@ int pxsne_step_profiled(pxsne_ctx *c, int32_t iters, double *group_ms, int32_t n
             *total_ms = ms;
         }
     }
-    for (auto &e : ev) cudaEventDestroy(e);
     if (rc) return rc;
     return check_device(c, nullptr);
 }
