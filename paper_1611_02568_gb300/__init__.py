@@ -30,7 +30,7 @@ _lib = None
 PXSNE_OK = 0
 ERRORS = {-1: "E_ARG", -2: "E_OOM", -3: "E_CUDA", -4: "E_STATE", -5: "E_DEVICE",
           -6: "E_UNSUPPORTED"}
-DEVERR = {1: "NONFINITE", 2: "STACK", 4: "BISECT", 8: "RANGE"}
+DEVERR = {1: "NONFINITE", 2: "STACK", 4: "BISECT", 8: "RANGE", 16: "TIMEOUT"}
 
 
 class PxsneError(RuntimeError):
@@ -133,24 +133,47 @@ def load(path: str | None = None):
     return L
 
 
-def _ptr(a):
-    """(pointer, on_device) of a numpy array or torch tensor (or None)."""
+def _buf(a, dtype, shape, name):
+    """(pointer, on_device) of a C-contiguous numpy array or torch tensor (or
+    None) of exactly this element type and shape; a None entry in ``shape``
+    matches any extent.  Raises instead of handing the library a buffer it
+    would read or write past.  A CUDA tensor's current stream is synchronised
+    first (the library works on its own stream)."""
     if a is None:
         return None, 0
+    dt = np.dtype(dtype)
     if isinstance(a, np.ndarray):
-        assert a.flags.c_contiguous
-        return a.ctypes.data, 0
-    try:
+        got, contiguous, ptr, dev = a.dtype, a.flags.c_contiguous, a.ctypes.data, 0
+    else:
+        try:
+            import torch
+        except ImportError:
+            torch = None
+        if torch is None or not isinstance(a, torch.Tensor):
+            raise TypeError(f"{name}: unsupported buffer type {type(a).__name__}")
+        try:
+            got = np.dtype(str(a.dtype).replace("torch.", ""))
+        except TypeError:
+            got = None
+        contiguous, ptr, dev = a.is_contiguous(), a.data_ptr(), int(a.is_cuda)
+    if got is None or got != dt:
+        raise TypeError(f"{name}: element type {got if got is not None else a.dtype}, "
+                        f"expected {dt}")
+    if len(a.shape) != len(shape) or any(w is not None and g != w
+                                         for g, w in zip(a.shape, shape)):
+        want = "(" + ", ".join("*" if w is None else str(w) for w in shape) + ")"
+        raise ValueError(f"{name}: shape {tuple(a.shape)}, expected {want}")
+    if not contiguous:
+        raise ValueError(f"{name}: not C-contiguous")
+    if dev:
         import torch
-        if isinstance(a, torch.Tensor):
-            assert a.is_contiguous()
-            if a.is_cuda:
-                torch.cuda.current_stream(a.device).synchronize()
-                return a.data_ptr(), 1
-            return a.data_ptr(), 0
-    except ImportError:
-        pass
-    raise TypeError(f"unsupported buffer type {type(a)}")
+        torch.cuda.current_stream(a.device).synchronize()
+    return ptr, dev
+
+
+def _f32(a):
+    """numpy input as C-contiguous float32 (tensors pass through unchanged)."""
+    return np.ascontiguousarray(a, np.float32) if isinstance(a, np.ndarray) else a
 
 
 class Context:
@@ -189,16 +212,15 @@ class Context:
 
     # ---------------------------------------------------------------- the method
     def affinities(self, X, perplexity: float = 0.0):
-        if isinstance(X, np.ndarray):
-            X = np.ascontiguousarray(X, dtype=np.float32)
+        X = _f32(X)
+        p, dev = _buf(X, np.float32, (None, None), "X")
         n, D = X.shape
-        p, dev = _ptr(X)
         self._ck(self.L.pxsne_affinities(self.h, p, n, D, float(perplexity), dev))
 
     def init(self, Y0=None, seed: int = 0):
-        if isinstance(Y0, np.ndarray):
-            Y0 = np.ascontiguousarray(Y0, dtype=np.float32)
-        p, dev = _ptr(Y0)
+        Y0 = _f32(Y0)
+        n = self.sizes()[0] or None   # without P the library reports the order error
+        p, dev = _buf(Y0, np.float32, (n, 2), "Y0")
         self._ck(self.L.pxsne_init(self.h, p, dev, int(seed)))
 
     def step(self, iters: int = 1):
@@ -216,8 +238,10 @@ class Context:
         if Y is None and pix is None:
             Y = np.empty((n, 2), np.float32)
             pix = np.empty((n, 2), np.int32) if want_pix else None
-        py, dy = _ptr(Y)
-        pp, dp = _ptr(pix)
+        py, dy = _buf(Y, np.float32, (n, 2), "Y")
+        pp, dp = _buf(pix, np.int32, (n, 2), "pix")
+        if Y is not None and pix is not None and dy != dp:
+            raise ValueError("Y and pix must both be host or both be device buffers")
         dev = dy or dp
         self._ck(self.L.pxsne_get_Y(self.h, py, pp, dev))
         return Y, pix
@@ -246,6 +270,11 @@ class Context:
         row_ptr = np.ascontiguousarray(row_ptr, np.int64)
         col = np.ascontiguousarray(col, np.int32)
         val = np.ascontiguousarray(val, np.float32)
+        if row_ptr.ndim != 1 or row_ptr.shape[0] < 1:
+            raise ValueError("row_ptr: expected a 1-D array of n + 1 offsets")
+        nnz = int(row_ptr[-1])
+        _buf(col, np.int32, (nnz,), "col")
+        _buf(val, np.float32, (nnz,), "val")
         self._ck(self.L.pxsne_set_P(self.h, row_ptr.shape[0] - 1, row_ptr.ctypes.data,
                                     col.ctypes.data, val.ctypes.data))
 
@@ -259,13 +288,16 @@ class Context:
         return idx, d2, beta
 
     def set_state(self, z, s, u=None, gains=None, t=0):
+        n = self.sizes()[0] or None   # without P the library reports the order error
         z = np.ascontiguousarray(z, np.uint32)
         s = np.ascontiguousarray(s, np.float64)
         u = None if u is None else np.ascontiguousarray(u, np.float32)
         gains = None if gains is None else np.ascontiguousarray(gains, np.float32)
-        self._ck(self.L.pxsne_set_state(self.h, z.ctypes.data, s.ctypes.data,
-                                        None if u is None else u.ctypes.data,
-                                        None if gains is None else gains.ctypes.data, int(t)))
+        pz, _ = _buf(z, np.uint32, (n, 2), "z")
+        ps, _ = _buf(s, np.float64, (2,), "s")
+        pu, _ = _buf(u, np.float32, (n, 2), "u")
+        pg, _ = _buf(gains, np.float32, (n, 2), "gains")
+        self._ck(self.L.pxsne_set_state(self.h, pz, ps, pu, pg, int(t)))
 
     def get_state(self):
         n, _ = self.sizes()
@@ -334,6 +366,7 @@ class Context:
                                             None if hits is None else hits.ctypes.data)
         else:
             kd = np.ascontiguousarray(knn_hd, np.int32)
+            _buf(kd, np.int32, (n, None), "knn_hd")
             rc = self.L.pxsne_nbr_precision(self.h, int(k), kd.ctypes.data, kd.shape[1], 0,
                                             C.byref(prec),
                                             None if hits is None else hits.ctypes.data)
@@ -417,13 +450,15 @@ class MLP:
         return w
 
     def set_params(self, w):
-        w = np.ascontiguousarray(w, np.float32)
-        assert w.size == self.np
+        w = np.ascontiguousarray(w, np.float32).reshape(-1)
+        _buf(w, np.float32, (self.np,), "w")
         self._ck(self.L.pxsne_mlp_set_params(self.h, w.ctypes.data))
 
     def loss_grad(self, X, T):
         X = np.ascontiguousarray(X, np.float32)
         T = np.ascontiguousarray(T, np.float32)
+        _buf(X, np.float32, (None, self.d), "X")
+        _buf(T, np.float32, (X.shape[0], 2), "T")
         g = np.empty(self.np, np.float32)
         loss = C.c_double()
         self._ck(self.L.pxsne_mlp_loss_grad(self.h, X.ctypes.data, T.ctypes.data, X.shape[0],
@@ -431,24 +466,26 @@ class MLP:
         return loss.value, g
 
     def train(self, X, T, epochs=10, batch=4096, lr=1e-3, seed=0):
-        Xp, dx = _ptr(np.ascontiguousarray(X, np.float32) if isinstance(X, np.ndarray) else X)
-        Tp, dt = _ptr(np.ascontiguousarray(T, np.float32) if isinstance(T, np.ndarray) else T)
-        assert dx == dt
+        X, T = _f32(X), _f32(T)
+        Xp, dx = _buf(X, np.float32, (None, self.d), "X")
         n = X.shape[0]
+        Tp, dt = _buf(T, np.float32, (n, 2), "T")
+        if dx != dt:
+            raise ValueError("X and T must both be host or both be device buffers")
         loss = C.c_double()
         self._ck(self.L.pxsne_mlp_train(self.h, Xp, Tp, n, int(epochs), int(batch), float(lr),
                                         int(seed), C.byref(loss), dx))
         return loss.value
 
     def predict(self, X, Y=None):
-        if isinstance(X, np.ndarray):
-            X = np.ascontiguousarray(X, np.float32)
+        X = _f32(X)
+        Xp, dx = _buf(X, np.float32, (None, self.d), "X")
         n = X.shape[0]
         if Y is None:
             Y = np.empty((n, 2), np.float32)
-        Xp, dx = _ptr(X)
-        Yp, dy = _ptr(Y)
-        assert dx == dy
+        Yp, dy = _buf(Y, np.float32, (n, 2), "Y")
+        if dx != dy:
+            raise ValueError("X and Y must both be host or both be device buffers")
         self._ck(self.L.pxsne_mlp_predict(self.h, Xp, n, Yp, dx))
         return Y
 
@@ -459,7 +496,9 @@ def embed_align(Y, Yref=None):
     L = load()
     Y = np.ascontiguousarray(Y, np.float32)
     out = np.empty_like(Y)
+    _buf(Y, np.float32, (None, 2), "Y")
     R = None if Yref is None else np.ascontiguousarray(Yref, np.float32)
+    _buf(R, np.float32, Y.shape, "Yref")
     rc = L.pxsne_embed_align(Y.ctypes.data, None if R is None else R.ctypes.data, Y.shape[0],
                              out.ctypes.data, 0)
     if rc != PXSNE_OK:
@@ -471,6 +510,7 @@ def pca(X, dout=50, seed=0):
     """(projection [n, dout], components [D, dout], eigenvalues [dout])."""
     L = load()
     X = np.ascontiguousarray(X, np.float32)
+    _buf(X, np.float32, (None, None), "X")
     n, D = X.shape
     out = np.empty((n, dout), np.float32)
     V = np.empty((D, dout), np.float32)
