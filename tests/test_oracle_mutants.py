@@ -28,6 +28,8 @@ MUTANTS = [
      "if (j == i) continue;\n            const float *xj", "const float *xj"),
     ("knn: first coordinate dropped from the distance", C_SRC,
      "for (int32_t d = 0; d < D; d++) {", "for (int32_t d = 1; d < D; d++) {"),
+    ("knn: sampled rows ignored", C_SRC,
+     "int64_t i = rows ? rows[q] : q;\n        if (i < 0", "int64_t i = q;\n        if (i < 0"),
     # perplexity bisection (Sec. 3.2)
     ("perplexity: entropy with the wrong sign on the mean term", C_SRC,
      "H = log(sum) + beta * hs / sum;", "H = log(sum) - beta * hs / sum;"),
@@ -35,6 +37,8 @@ MUTANTS = [
      "const double target = log(perplexity);", "const double target = log2(perplexity);"),
     ("perplexity: bracket moved the wrong way", C_SRC,
      "if (H > target) { /* too flat: sharpen */", "if (H < target) { /* too flat: sharpen */"),
+    ("perplexity: row minimum left in the mean term", C_SRC,
+     "hs += (d[j] - dmin) * e;", "hs += d[j] * e;"),
     ("perplexity: rows not normalised", C_SRC,
      "for (int32_t j = 0; j < k; j++) p[j] /= sum;", ""),
     # symmetrisation (Sec. 3.3)
@@ -45,6 +49,9 @@ MUTANTS = [
     # screen map (Eq. z1/z2)
     ("init: extremes taken over the other axis", C_SRC,
      "double v = Y0[2 * i + d];", "double v = Y0[2 * i + (1 - d)];"),
+    ("init: zero-extent axis off the origin", C_SRC,
+     "for (int64_t i = 0; i < n; i++) z[2 * i + d] = 0u;",
+     "for (int64_t i = 0; i < n; i++) z[2 * i + d] = 1u;"),
     # tree (Sec. 4.1)
     ("morton: x and y bits swapped", C_SRC,
      "m |= ((px >> b) & 1u) << (2 * b);\n        m |= ((py >> b) & 1u) << (2 * b + 1);",
@@ -67,6 +74,9 @@ MUTANTS = [
     ("bh: cell width along x instead of the diagonal", C_SRC,
      "double rc2 = (s0 * W) * (s0 * W) + (s1 * W) * (s1 * W);",
      "double rc2 = (s0 * W) * (s0 * W);"),
+    ("bh: sampled rows ignored", C_SRC,
+     "int64_t i = rows ? rows[q] : q;\n        const uint32_t zx",
+     "int64_t i = q;\n        const uint32_t zx"),
     ("bh geometric: centre at the cell's corner", C_SRC,
      "((double)cx * W + 0.5 * W)", "((double)cx * W)"),
     ("bh geometric: x and y cell bits swapped", C_SRC,
@@ -74,6 +84,12 @@ MUTANTS = [
      "cy |= ((mc >> (2 * b)) & 1u) << b;\n                    cx |= ((mc >> (2 * b + 1)) & 1u) << b;"),
     # exact repulsion and attraction (Eq. grad)
     ("exact repulsion: w instead of w^2", C_SRC, "fx += w * w * dx;", "fx += w * dx;"),
+    ("exact repulsion: sampled rows ignored", C_SRC,
+     "int64_t i = rows ? rows[q] : q;\n        double fx = 0.0, fy = 0.0, zs = 0.0;",
+     "int64_t i = q;\n        double fx = 0.0, fy = 0.0, zs = 0.0;"),
+    ("attraction: sampled rows ignored", C_SRC,
+     "int64_t i = rows ? rows[q] : q;\n        double fx = 0.0, fy = 0.0;\n",
+     "int64_t i = q;\n        double fx = 0.0, fy = 0.0;\n"),
     ("attraction: wrong sign", C_SRC, "fx += val[e] * w * dx;", "fx -= val[e] * w * dx;"),
     ("attraction: kernel squared", C_SRC,
      "fx += val[e] * w * dx;\n            fy += val[e] * w * dy;",
@@ -89,6 +105,14 @@ MUTANTS = [
     ("update: minimum gain not applied", C_SRC, "if (gn < min_gain) gn = min_gain;", ""),
     ("update: momentum with the wrong sign", C_SRC,
      "u[k] = mu * u[k] - eta * gn * g;", "u[k] = -mu * u[k] - eta * gn * g;"),
+    # the run's schedule (exaggeration and momentum phases)
+    ("run: exaggeration one iteration too long", C_SRC,
+     "double alpha = t < p->exag_iters ? p->exag : 1.0;",
+     "double alpha = t <= p->exag_iters ? p->exag : 1.0;"),
+    ("run: momentum phases swapped", C_SRC,
+     "double mu = t < p->mom_switch ? p->mom0 : p->mom1;",
+     "double mu = t < p->mom_switch ? p->mom1 : p->mom0;"),
+    ("run: screen rescale skipped", C_SRC, "        orc_rescale(n, zhat, z, s);\n    }", "    }"),
     # screen rescale (Sec. 4.2, Eq. beta_scaling)
     ("rescale: compensation of s not applied", C_SRC,
      "s[d] = s[d] * ldexp((double)gamma, -32);", ""),
@@ -99,10 +123,17 @@ MUTANTS = [
      "double q = 1.0 / ((1.0 + dx * dx + dy * dy) * Z);",
      "double q = 1.0 / (1.0 + dx * dx + dy * dy);"),
     ("kl: ratio inverted", C_SRC, "c += p * log(p / q);", "c += p * log(q / p);"),
+    ("kl: stored zeros of P not skipped", C_SRC,
+     "if (p <= 0.0) continue;", "if (p < 0.0) continue;"),
+    ("kl: Z of the tree replaced by the exact sum", C_SRC,
+     "    if (p->exact) {\n        orc_exact_repulsion(z, s, n, NULL, n, Frep, Zi);\n    } else {",
+     "    if (1) {\n        orc_exact_repulsion(z, s, n, NULL, n, Frep, Zi);\n    } else {"),
     # neighbourhood precision (Eq. nei_prec)
     ("nbr_precision: distance along x only", C_SRC,
      "double dd = dx * dx + dy * dy;\n            int32_t p;",
      "double dd = dx * dx;\n            int32_t p;"),
+    ("nbr_precision: sampled rows ignored", C_SRC,
+     "int64_t i = rows ? rows[q] : q;\n        int32_t *I", "int64_t i = q;\n        int32_t *I"),
     ("nbr_precision: not divided by k", C_SRC,
      "return (double)hits / ((double)k * (double)m);", "return (double)hits / (double)m;"),
     # warm-start MLP

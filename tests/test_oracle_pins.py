@@ -14,7 +14,8 @@ fails at least one test:
   pyramid        per-level bincount of the shifted pixel pairs; sums
   exact forces   scikit-learn's exact t-SNE KL and gradient; hand-derived
                  closed forms (tests/golden/kl_closed_forms.txt); finite
-                 differences of the KL; net force zero
+                 differences of the KL; net force zero; stored zeros of P
+                 add nothing to the KL; sampled rows equal the full rows
   bh_repulsion   theta = 0 with <= 1 point per pixel equals the exact sum;
                  theta = 0 in general equals a tree-free brute force over pixels
                  (centres of mass; pixel midpoints in geometric-centre mode);
@@ -332,6 +333,61 @@ def test_net_forces_vanish():
     Fattr = oracle.attraction(P, z, s)
     assert np.abs(Fattr.sum(0)).max() < 1e-12 * np.abs(Fattr).sum()
     assert np.abs(Frep.sum(0)).max() < 1e-12 * np.abs(Frep).sum()
+
+
+def test_sampled_rows_equal_the_full_rows():
+    # the row-sampled forms (used at full sizes, where only a sample of rows
+    # is affordable) give row rows[q] of the full result, in the listed order,
+    # repeats included
+    n, L = 300, 6
+    rng = np.random.default_rng(26)
+    A = (rng.random((n, n)) < 0.05) * rng.random((n, n))
+    A = A + A.T
+    np.fill_diagonal(A, 0)
+    P = _dense_csr(A / A.sum())
+    z, s = _random_state(n, 27)
+    rows = np.array([299, 0, 17, 17, 150, 3])
+    Fe, Ze = oracle.exact_repulsion(z, s)
+    Fr, Zr = oracle.exact_repulsion(z, s, rows=rows)
+    assert np.array_equal(Fr, Fe[rows]) and np.array_equal(Zr, Ze[rows])
+    Fa = oracle.attraction(P, z, s)
+    assert np.array_equal(oracle.attraction(P, z, s, rows=rows), Fa[rows])
+    for cm in (0, 1):
+        Fb, Zb, ab = oracle.bh_repulsion(z, s, L, 0.5, centre_mode=cm)
+        Fq, Zq, aq = oracle.bh_repulsion(z, s, L, 0.5, rows=rows, centre_mode=cm)
+        assert np.array_equal(Fq, Fb[rows]) and np.array_equal(Zq, Zb[rows])
+        assert np.array_equal(aq, ab[rows])
+    idx, _ = oracle.knn(rng.standard_normal((n, 3)).astype(np.float32), 8)
+    _, hits = oracle.nbr_precision(idx, 8, z, s, per_row=True)
+    p_r, hits_r = oracle.nbr_precision(idx[rows], 8, z, s, rows=rows, per_row=True)
+    assert np.array_equal(hits_r, hits[rows])
+    assert p_r == hits[rows].sum() / (8 * len(rows))
+
+
+def test_kl_ignores_explicit_zeros():
+    # a stored zero of P (0 ln 0 = 0) adds nothing to Eq. cost_func
+    n = 30
+    rng = np.random.default_rng(28)
+    A = (rng.random((n, n)) < 0.3) * rng.random((n, n))
+    A = A + A.T
+    np.fill_diagonal(A, 0)
+    Pd = A / A.sum()
+    P = _dense_csr(Pd)
+    z, s = _random_state(n, 29)
+    _, Zi = oracle.exact_repulsion(z, s)
+    Z = Zi.sum()
+    # the same P with every absent off-diagonal pair of row 0 stored as 0
+    rp, col, val = [0], [], []
+    for i in range(n):
+        for j in range(n):
+            if j != i and (Pd[i, j] > 0 or i == 0):
+                col.append(j)
+                val.append(Pd[i, j])
+        rp.append(len(col))
+    P0 = oracle.CSR(np.array(rp, np.int64), np.array(col, np.int32), np.array(val))
+    assert P0.nnz > P.nnz
+    # (equal up to the order in which the threads' partial sums are added)
+    assert oracle.kl(P0, z, s, Z) == pytest.approx(oracle.kl(P, z, s, Z), rel=1e-13)
 
 
 def _unique_pixel_state(n, L, seed):
