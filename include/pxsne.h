@@ -49,7 +49,8 @@ extern "C" {
 #define PXSNE_E_DEVICE (-5)      /* error flagged by a kernel */
 #define PXSNE_E_UNSUPPORTED (-6) /* valid request this build does not support */
 
-/* Device error flags (pxsne_device_errors). */
+/* Device error flags, read back by pxsne_sync (and by every synchronising
+ * call, which then returns PXSNE_E_DEVICE and clears them). */
 #define PXSNE_DEVERR_NONFINITE 1u   /* non-finite gradient or step */
 #define PXSNE_DEVERR_STACK 2u       /* BH traversal stack overflow */
 #define PXSNE_DEVERR_BISECT 4u      /* a perplexity row did not converge */
@@ -150,7 +151,8 @@ int pxsne_get_Y(pxsne_ctx *ctx, float *Y, int32_t *pix, int on_device);
  * i of knn_hd (n x kh int32, host or device per on_device, neighbours in
  * ascending distance; NULL = the lists of the last pxsne_affinities).
  * N_d^k(i) = the exact k nearest points of i in the 2-D embedding by squared
- * y-space distance (FP64), ties to the lower index.  1 <= k <= min(32, kh).
+ * y-space distance (FP64), ties to the lower index.  1 <= k <= min(32, kh)
+ * and k < n.
  * hits (host, n int32, may be NULL) gets |N_D^k(i) ∩ N_d^k(i)| per point.
  * Synchronises. */
 int pxsne_nbr_precision(pxsne_ctx *ctx, int32_t k, const int32_t *knn_hd, int32_t kh,
@@ -169,12 +171,16 @@ int pxsne_sync(pxsne_ctx *ctx, uint32_t *dev_errors);
 /* Number of points and non-zeros of P (0 before affinities). */
 int pxsne_get_sizes(pxsne_ctx *ctx, int64_t *n, int64_t *nnz);
 
-/* P as CSR with columns ascending per row: row_ptr[n+1] int64, col[nnz]
- * int32, val[nnz] float32.  Any pointer may be NULL. */
+/* P as CSR: row_ptr[n+1] int64, col[nnz] int32, val[nnz] float32, with nnz
+ * from pxsne_get_sizes.  Rows are as built by pxsne_affinities (columns
+ * ascending) or as given to pxsne_set_P.  Any pointer may be NULL. */
 int pxsne_get_P(pxsne_ctx *ctx, int64_t *row_ptr, int32_t *col, float *val);
 
-/* Replace P by a caller CSR (2 <= n <= 2^24; row_ptr[n+1] int64, col int32 in
- * [0, n), no self entries; val float32 >= 0).  Clears the embedding state. */
+/* Replace P by a caller CSR (2 <= n <= 2^24; row_ptr[n+1] int64 with
+ * row_ptr[0] = 0 and non-decreasing, col int32 in [0, n) with no self
+ * entries, val float32 finite and >= 0).  P is used as given: it is neither
+ * symmetrised nor normalised.  Arguments are checked on the host
+ * (PXSNE_E_ARG names the first bad row).  Clears the embedding state. */
 int pxsne_set_P(pxsne_ctx *ctx, int64_t n, const int64_t *row_ptr, const int32_t *col,
                 const float *val);
 
