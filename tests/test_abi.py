@@ -63,3 +63,37 @@ def test_null_context_is_rejected(lib):
 
 def test_sources_target_sm103a_only():
     assert pxbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_product_and_oracle_share_nothing():
+    """The CUDA path and the oracle are independent: no source of either names
+    the other, the library is built from the package's own sources and
+    headers only and exports none of the oracle's symbols, and importing the
+    package loads no oracle module."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_1611_02568_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"\boracle\b|orc_", text), f
+    for f in os.listdir(os.path.join(root, "include")):
+        assert "orc_" not in open(os.path.join(root, "include", f)).read()
+    src = open(os.path.join(root, "oracle", "pxsne_oracle.c")).read()
+    assert "pxsne.h" not in src and "common.cuh" not in src
+    assert not re.search(r"\bpxsne_[a-z]", src)
+    flags = pxbuild._flags()
+    incs = [flags[i + 1] for i, f in enumerate(flags) if f == "-I"]
+    assert sorted(incs) == sorted([pxbuild.INCLUDE, pxbuild.CSRC])
+    assert os.path.dirname(pxbuild.CSRC) == pkg
+    lib = ctypes.CDLL(px.LIB_PATH)
+    for sym in ("orc_run", "orc_bh_repulsion", "orc_knn", "orc_kl"):
+        assert not hasattr(lib, sym)
+    code = ("import sys, paper_1611_02568_gb300 as p; p.load(); "
+            "print(sorted(m for m in sys.modules if m.split('.')[0] == 'oracle'))")
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True,
+                         text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == "[]"
