@@ -168,9 +168,9 @@ def group_bytes(n, nnz, L):
         "k_relabel": (nnz * 16 + n * (4 + 8 + 4 + 4 + 4 + 8 + 8 + 8 + 8)) / RELABEL_EVERY,
         "k_update": n * (8 + 8 + 8 + 8 + 8 + 8 + 8 + 16),      # z,Frep,Fattr,u,gains r; u,gains w; zhat w
         "k_snap_hist": leaves * 20 + n * (4 + 16 + 8 + 4 + 4 + 8),  # memset; perm,zhat,ainv r; z,rank,zp w
-        "k_pyr_pass": leaves * (20 + 4) + cells * 16,          # leaf sums r, leaf_start w, records w
+        "k_pyr_pass": leaves * (20 + 4) + cells * 20,          # leaf sums r, leaf_start w, rec + recn w
         "k_perm_scatter": n * (8 + 4 + 4 + 4),
-        "k_bh_traverse": n * (4 + 8 + 8 + 4) + cells * 16,
+        "k_bh_traverse": n * (4 + 8 + 8 + 4) + cells * 20,    # perm, z r; Frep, Zi w; rec + recn r
         "k_attract": nnz * 8 + (n + 1) * 8 + n * (8 + 4 + 8),
         "k_zsum": n * 4,
     }

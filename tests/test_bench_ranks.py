@@ -112,3 +112,21 @@ def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
     cs = bench.ClockSampler(0)
     cs.start()
     assert cs.stop() is None
+
+
+def test_algorithmic_bytes_per_unit():
+    """The bytes each kernel group must move, per the units it processes:
+    per point, per leaf, per cell of the pyramid and per non-zero of P."""
+    sys.path.insert(0, ROOT)
+    import bench
+    n, nnz, L = 1000, 90_000, 4
+    leaves, cells = 4 ** L, sum(4 ** l for l in range(L + 1))
+    b = bench.group_bytes(n, nnz, L)
+    assert b["k_update"] == 72 * n
+    assert b["k_snap_hist"] == 44 * n + 20 * leaves
+    assert b["k_pyr_pass"] == 24 * leaves + 20 * cells
+    assert b["k_perm_scatter"] == 20 * n
+    assert b["k_bh_traverse"] == 24 * n + 20 * cells
+    assert b["k_attract"] == 8 * nnz + 8 * (n + 1) + 20 * n
+    assert b["k_zsum"] == 4 * n
+    assert b["k_relabel"] == (16 * nnz + 56 * n) / bench.RELABEL_EVERY
