@@ -400,6 +400,56 @@ def nbr_precision(knn_hd, k, z, s, rows=None, per_row=False):
     return (v, hits) if per_row else v
 
 
+# ---------------------------------------------------------------- seeded start
+# The random initial embedding drawn when the caller gives none (t-SNE starts
+# from a random layout, Sec. 3.2; Sec. 4.2 draws it from an isotropic
+# Gaussian, here of a chosen scale sigma).  The draw is not part of the
+# method's arithmetic, so both sides implement the same
+# published counter-based generator: Philox4x32-10 (Salmon, Moraes, Dror and
+# Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC 2011), followed by
+# the Box-Muller transform (Box and Muller, 1958).
+_PHILOX_M = (0xD2511F53, 0xCD9E8D57)   # round multipliers
+_PHILOX_W = (0x9E3779B9, 0xBB67AE85)   # key schedule (Weyl) increments
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32 with 10 rounds: ctr uint32 [m, 4], key (k0, k1) -> uint32
+    [m, 4].  Each round multiplies words 0 and 2 by the round multipliers
+    into 64-bit products; the new words are (hi(w2 M1) ^ w1 ^ k0, lo(w2 M1),
+    hi(w0 M0) ^ w3 ^ k1, lo(w0 M0)); the key advances by the Weyl increments
+    between rounds."""
+    c = np.array(ctr, dtype=np.uint64).reshape(-1, 4)
+    k0, k1 = np.uint64(key[0]), np.uint64(key[1])
+    mask = np.uint64(0xFFFFFFFF)
+    for r in range(10):
+        if r:
+            k0 = (k0 + np.uint64(_PHILOX_W[0])) & mask
+            k1 = (k1 + np.uint64(_PHILOX_W[1])) & mask
+        p0 = c[:, 0] * np.uint64(_PHILOX_M[0])
+        p1 = c[:, 2] * np.uint64(_PHILOX_M[1])
+        c = np.stack([((p1 >> np.uint64(32)) ^ c[:, 1] ^ k0) & mask, p1 & mask,
+                      ((p0 >> np.uint64(32)) ^ c[:, 3] ^ k1) & mask, p0 & mask], 1)
+    return c.astype(np.uint32)
+
+
+def philox_y0(seed, n, sigma=1e-4):
+    """Y0 [n, 2] float32 ~ N(0, sigma^2 I): point i takes counter (i, 0, 0, 0)
+    and key (low, high 32 bits of seed); its first two output words give the
+    uniforms u = (w + 1/2) 2^-32, and Box-Muller gives
+    (sigma r cos a, sigma r sin a) with r = sqrt(-2 ln u1), a = 2 pi u2, in
+    FP64, rounded to float32 (sigma is taken as a float32 value)."""
+    ctr = np.zeros((n, 4), np.uint64)
+    ctr[:, 0] = np.arange(n, dtype=np.uint64)
+    seed = int(seed)
+    w = philox4x32_10(ctr, (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)).astype(np.float64)
+    u1 = (w[:, 0] + 0.5) * 2.0 ** -32
+    u2 = (w[:, 1] + 0.5) * 2.0 ** -32
+    rad = np.sqrt(-2.0 * np.log(u1))
+    ang = 6.283185307179586 * u2
+    sg = float(np.float32(sigma))
+    return np.stack([sg * rad * np.cos(ang), sg * rad * np.sin(ang)], 1).astype(np.float32)
+
+
 # ---------------------------------------------------------------- MLP warm start
 @dataclass
 class MLP:

@@ -146,6 +146,17 @@ MUTANTS = [
     ("mlp: loss gradient without the factor 2", C_SRC,
      "dy[o] = 2.0 * e / (double)m;", "dy[o] = e / (double)m;"),
     ("mlp: bias b2 left out", C_SRC, "double s = b2[a];", "double s = 0.0;"),
+    # seeded start (Philox4x32-10 and Box-Muller)
+    ("philox: key increments swapped", PY_SRC,
+     "_PHILOX_W = (0x9E3779B9, 0xBB67AE85)", "_PHILOX_W = (0xBB67AE85, 0x9E3779B9)"),
+    ("philox: high word of a product where the low one belongs", PY_SRC,
+     "p1 & mask,", "(p1 >> np.uint64(32)) & mask,"),
+    ("philox_y0: both uniforms from the first word", PY_SRC,
+     "u2 = (w[:, 1] + 0.5)", "u2 = (w[:, 0] + 0.5)"),
+    ("philox_y0: radius without its factor 2", PY_SRC,
+     "rad = np.sqrt(-2.0 * np.log(u1))", "rad = np.sqrt(-np.log(u1))"),
+    ("philox_y0: high half of the seed ignored", PY_SRC,
+     "(seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)", "(seed & 0xFFFFFFFF, 0)"),
     # PCA (Sec. 5.1.1 pre-processing)
     ("pca: data not centred", PY_SRC, "Xc = Xd - mu\n", "Xc = Xd\n"),
     ("pca: smallest eigenvalues kept", PY_SRC,

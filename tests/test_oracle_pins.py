@@ -35,6 +35,8 @@ fails at least one test:
   gelu, mlp      the erf definition and central differences; a closed-form
                  forward pass; finite differences of the loss
   pca            SVD of the centred matrix
+  philox_y0      the generator's published known-answer vectors; the draw's
+                 mean, scale, one-sigma mass and independence
 
 tests/test_oracle_mutants.py plants one such mistake at a time in a copy of
 the oracle and checks that these pins fail.
@@ -642,6 +644,37 @@ def test_nbr_precision_identity_cases():
     # unrelated geometry: precision ~ k / n
     z2, s2 = oracle.init_fx(rng.standard_normal((n, 2)))
     assert oracle.nbr_precision(idx, k, z2, s2) < 0.15
+
+
+# ------------------------------------------------------------------ seeded start
+def test_philox_known_answers():
+    # the generator's published known-answer vectors
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        rows = [[int(w, 16) for w in line.split()] for line in f
+                if line.strip() and not line.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        out = oracle.philox4x32_10([r[0:4]], (r[4], r[5]))[0]
+        assert [int(v) for v in out] == r[6:10]
+
+
+def test_philox_y0_is_a_gaussian_draw():
+    sigma = 1e-4
+    Y = oracle.philox_y0(7, 400_000, sigma).astype(np.float64)
+    assert np.array_equal(Y, oracle.philox_y0(7, 400_000, sigma))
+    # N(0, sigma^2 I): mean, scale, the one-sigma mass, no correlation
+    assert np.abs(Y.mean(0)).max() < 5 * sigma / math.sqrt(400_000)
+    assert np.abs(Y.std(0) / sigma - 1).max() < 0.005
+    assert abs((np.abs(Y) < sigma).mean() - math.erf(1 / math.sqrt(2))) < 0.003
+    assert abs(np.corrcoef(Y[:, 0], Y[:, 1])[0, 1]) < 0.005
+    # Box-Muller: the angle is uniform and independent of the radius
+    r = np.hypot(Y[:, 0], Y[:, 1])
+    a = np.arctan2(Y[:, 1], Y[:, 0])
+    assert abs(np.corrcoef(r, a)[0, 1]) < 0.005
+    assert abs(np.corrcoef(r, np.abs(a))[0, 1]) < 0.005
+    # both halves of the 64-bit seed matter; the draw is a prefix of a longer one
+    assert not np.array_equal(oracle.philox_y0(1, 10), oracle.philox_y0(1 + 2 ** 32, 10))
+    assert np.array_equal(oracle.philox_y0(3, 10), oracle.philox_y0(3, 1000)[:10])
 
 
 # ------------------------------------------------------------------ MLP warm start
