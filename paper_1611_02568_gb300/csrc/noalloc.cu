@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(kNoallocThreads)
 extern "C" int pxsne_kl_noalloc(const int64_t *row_ptr, const int32_t *col, const float *val,
                                 int64_t n, const uint32_t *z, double s0, double s1, double Z,
                                 double *out, void *stream) {
-    if (!row_ptr || !z || !out || n < 1) return PXSNE_E_ARG;
+    if (!row_ptr || !col || !val || !z || !out || n < 1) return PXSNE_E_ARG;
     if (n > kNoallocMaxRows) return PXSNE_E_ARG;
     if (!(s0 > 0.0) || !(s1 > 0.0) || !(Z > 0.0)) return PXSNE_E_ARG;
     NoallocScratch *scr = nullptr;

@@ -61,6 +61,24 @@ def test_null_context_is_rejected(lib):
     L.pxsne_destroy(None)
 
 
+def test_kl_noalloc_rejects_bad_arguments_before_any_device_work(lib):
+    vp = ctypes.c_void_p
+    f = lib.pxsne_kl_noalloc
+    f.argtypes = [vp, vp, vp, ctypes.c_int64, vp, ctypes.c_double, ctypes.c_double,
+                  ctypes.c_double, vp, vp]
+    f.restype = ctypes.c_int
+    lib.pxsne_kl_noalloc_max_rows.restype = ctypes.c_int64
+    big = lib.pxsne_kl_noalloc_max_rows()
+    assert big == 2 ** 24
+    ok = dict(rp=1, col=1, val=1, n=10, z=1, s0=1.0, s1=1.0, Z=1.0, out=1)
+    for bad in (dict(rp=None), dict(col=None), dict(val=None), dict(z=None), dict(out=None),
+                dict(n=0), dict(n=big + 1), dict(s0=0.0), dict(s1=-1.0), dict(Z=0.0),
+                dict(Z=float("nan"))):
+        a = ok | bad
+        assert f(a["rp"], a["col"], a["val"], a["n"], a["z"], a["s0"], a["s1"], a["Z"],
+                 a["out"], None) == -1, bad
+
+
 def test_sources_target_sm103a_only():
     assert pxbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
