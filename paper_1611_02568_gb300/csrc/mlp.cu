@@ -556,8 +556,9 @@ int check_dev(pxsne_mlp *M) {
 extern "C" {
 
 int pxsne_mlp_create(pxsne_mlp **out, int32_t d_in, uint64_t seed, void *stream) {
-    if (!out || d_in < 1 || d_in > 1024) return PXSNE_E_ARG;
+    if (!out) return PXSNE_E_ARG;
     *out = nullptr;
+    if (d_in < 1 || d_in > 1024) return PXSNE_E_ARG;
     pxsne_mlp *M = new (std::nothrow) pxsne_mlp();
     if (!M) return PXSNE_E_OOM;
     M->d = d_in;

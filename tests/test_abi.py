@@ -79,6 +79,38 @@ def test_kl_noalloc_rejects_bad_arguments_before_any_device_work(lib):
                  a["out"], None) == -1, bad
 
 
+def test_stateless_calls_reject_bad_arguments_before_any_device_work(lib):
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    lib.pxsne_pca.argtypes = [vp, i64, i32, i32, vp, vp, vp, ctypes.c_int, ctypes.c_uint64]
+    lib.pxsne_embed_align.argtypes = [vp, vp, i64, vp, ctypes.c_int]
+    lib.pxsne_mlp_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_uint64, vp]
+    lib.pxsne_mlp_train.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.c_float, ctypes.c_uint64,
+                                    vp, ctypes.c_int]
+    lib.pxsne_mlp_predict.argtypes = [vp, vp, i64, vp, ctypes.c_int]
+    lib.pxsne_mlp_num_params.argtypes = [vp]
+    lib.pxsne_mlp_num_params.restype = i64
+    lib.pxsne_mlp_destroy.argtypes = [vp]
+    # PCA: 2 <= n, 1 <= dout <= D, X and Xout given
+    for args in [(None, 10, 4, 2), (1, 1, 4, 2), (1, 10, 4, 5), (1, 10, 4, 0), (1, 10, 0, 0)]:
+        X, n, D, dout = args
+        assert lib.pxsne_pca(X, n, D, dout, 1, None, None, 0, 0) == -1, args
+    assert lib.pxsne_pca(1, 10, 4, 2, None, None, None, 0, 0) == -1
+    # alignment: 2 <= n, Y and Yout given
+    assert lib.pxsne_embed_align(None, None, 10, 1, 0) == -1
+    assert lib.pxsne_embed_align(1, None, 1, 1, 0) == -1
+    assert lib.pxsne_embed_align(1, None, 10, None, 0) == -1
+    # MLP: 1 <= d <= 1024; *out is NULL after a failure; NULL models are rejected
+    h = vp(12345)
+    assert lib.pxsne_mlp_create(ctypes.byref(h), 0, 0, None) == -1 and not h.value
+    h = vp(12345)
+    assert lib.pxsne_mlp_create(ctypes.byref(h), 1025, 0, None) == -1 and not h.value
+    assert lib.pxsne_mlp_create(None, 8, 0, None) == -1
+    assert lib.pxsne_mlp_train(None, 1, 1, 10, 1, 8, 1e-3, 0, None, 0) == -1
+    assert lib.pxsne_mlp_predict(None, 1, 10, 1, 0) == -1
+    assert lib.pxsne_mlp_num_params(None) == 0
+    lib.pxsne_mlp_destroy(None)
+
+
 def test_sources_target_sm103a_only():
     assert pxbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
