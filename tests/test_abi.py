@@ -111,6 +111,22 @@ def test_stateless_calls_reject_bad_arguments_before_any_device_work(lib):
     lib.pxsne_mlp_destroy(None)
 
 
+def test_kernel_group_names(lib):
+    # the tracing groups of one iteration, in launch order, as the bench's
+    # roofline and byte model name them
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    lib.pxsne_kernel_group_name.argtypes = [ctypes.c_int32]
+    lib.pxsne_kernel_group_name.restype = ctypes.c_char_p
+    names = [lib.pxsne_kernel_group_name(g) for g in range(8)]
+    assert [x.decode() for x in names] == [
+        "k_relabel", "k_update", "k_snap_hist", "k_pyr_pass", "k_perm_scatter",
+        "k_bh_traverse", "k_attract", "k_zsum"]
+    assert lib.pxsne_kernel_group_name(8) is None and lib.pxsne_kernel_group_name(-1) is None
+    assert set(bench.group_bytes(100, 1000, 3)) == {x.decode() for x in names}
+
+
 def test_sources_target_sm103a_only():
     assert pxbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
