@@ -127,6 +127,27 @@ def test_kernel_group_names(lib):
     assert set(bench.group_bytes(100, 1000, 3)) == {x.decode() for x in names}
 
 
+def test_missing_library_fails_loudly():
+    """Without the compiled library every entry point raises: there is no
+    CPU fallback."""
+    import subprocess
+    import sys
+    code = ("import paper_1611_02568_gb300 as p\n"
+            "p.LIB_PATH = p.LIB_PATH + '.absent'\n"
+            "for f in (lambda: p.Context(), lambda: p.MLP(8), lambda: p.pca([[0.0]], 1),\n"
+            "          lambda: p.embed_align([[0.0, 0.0]])):\n"
+            "    try:\n"
+            "        f()\n"
+            "    except RuntimeError as e:\n"
+            "        assert 'missing' in str(e)\n"
+            "    else:\n"
+            "        raise SystemExit('no error')\n"
+            "print('ok')\n")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
+
+
 def test_sources_target_sm103a_only():
     assert pxbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
