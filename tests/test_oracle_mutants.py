@@ -39,16 +39,24 @@ MUTANTS = [
      "if (H > target) { /* too flat: sharpen */", "if (H < target) { /* too flat: sharpen */"),
     ("perplexity: row minimum left in the mean term", C_SRC,
      "hs += (d[j] - dmin) * e;", "hs += d[j] * e;"),
+    ("perplexity: stop test a hundred times too loose", C_SRC,
+     "if (fabs(H - target) < tol) { ok = 1; break; }",
+     "if (fabs(H - target) < 100 * tol) { ok = 1; break; }"),
     ("perplexity: rows not normalised", C_SRC,
      "for (int32_t j = 0; j < k; j++) p[j] /= sum;", ""),
     # symmetrisation (Sec. 3.3)
     ("symmetrize: divided by n instead of 2n", C_SRC,
      "val[nnz] = v / (2.0 * (double)n);", "val[nnz] = v / (double)n;"),
+    ("symmetrize: columns left unsorted within a row", C_SRC,
+     "    if (x->c != y->c) return x->c < y->c ? -1 : 1;\n", ""),
     ("symmetrize: transposed entry not added", C_SRC,
      "t[o].r = j; t[o].c = (int32_t)i;", "t[o].r = i; t[o].c = j;"),
     # screen map (Eq. z1/z2)
     ("init: extremes taken over the other axis", C_SRC,
      "double v = Y0[2 * i + d];", "double v = Y0[2 * i + (1 - d)];"),
+    ("init: ceiling in place of the floor", C_SRC,
+     "double q = floor((Y0[2 * i + d] - mn) * ORC_R / range);",
+     "double q = ceil((Y0[2 * i + d] - mn) * ORC_R / range);"),
     ("init: zero-extent axis off the origin", C_SRC,
      "for (int64_t i = 0; i < n; i++) z[2 * i + d] = 0u;",
      "for (int64_t i = 0; i < n; i++) z[2 * i + d] = 1u;"),
@@ -56,6 +64,14 @@ MUTANTS = [
     ("morton: x and y bits swapped", C_SRC,
      "m |= ((px >> b) & 1u) << (2 * b);\n        m |= ((py >> b) & 1u) << (2 * b + 1);",
      "m |= ((py >> b) & 1u) << (2 * b);\n        m |= ((px >> b) & 1u) << (2 * b + 1);"),
+    ("leaf keys: x and y pixels swapped", C_SRC,
+     "uint32_t x = z[2 * i] >> F, y = z[2 * i + 1] >> F;",
+     "uint32_t y = z[2 * i] >> F, x = z[2 * i + 1] >> F;"),
+    ("level offsets shifted by one", C_SRC,
+     "return (((int64_t)1 << (2 * l)) - 1) / 3;", "return (((int64_t)1 << (2 * l)) + 2) / 3;"),
+    ("pyramid: root level left empty", C_SRC,
+     "for (int32_t l = 0; l <= L; l++) {\n            int64_t c = orc_level_offset(l)",
+     "for (int32_t l = 1; l <= L; l++) {\n            int64_t c = orc_level_offset(l)"),
     ("pyramid: y sums accumulate x", C_SRC, "sy[c] += z[2 * i + 1];", "sy[c] += z[2 * i];"),
     ("pyramid: leaves one level too coarse", C_SRC,
      "uint32_t m = orc_morton(z[2 * i] >> F, z[2 * i + 1] >> F);",
@@ -103,6 +119,9 @@ MUTANTS = [
      "double g = 4.0 * (alpha * Fattr[k] - Frep[k]);"),
     ("update: gains rule inverted", C_SRC, "(sgn(g) != sgn(u[k]))", "(sgn(g) == sgn(u[k]))"),
     ("update: minimum gain not applied", C_SRC, "if (gn < min_gain) gn = min_gain;", ""),
+    ("update: step truncated, not rounded", C_SRC,
+     "zhat[k] = (int64_t)z[k] + llrint(u[k] / s[d]);",
+     "zhat[k] = (int64_t)z[k] + (int64_t)(u[k] / s[d]);"),
     ("update: momentum with the wrong sign", C_SRC,
      "u[k] = mu * u[k] - eta * gn * g;", "u[k] = -mu * u[k] - eta * gn * g;"),
     # the run's schedule (exaggeration and momentum phases)
@@ -137,6 +156,10 @@ MUTANTS = [
     ("nbr_precision: not divided by k", C_SRC,
      "return (double)hits / ((double)k * (double)m);", "return (double)hits / (double)m;"),
     # warm-start MLP
+    ("gelu: Phi with the wrong scale", C_SRC,
+     "return 0.5 * z * (1.0 + erf(z / sqrt(2.0))); }", "return 0.5 * z * (1.0 + erf(z / 2.0)); }"),
+    ("mlp: bias b1 left out", C_SRC, "double s = b1[a];", "double s = 0.0;"),
+    ("mlp: gradient of b3 missing", C_SRC, "gb3[o] += dy[o];", ""),
     ("gelu': missing factor z", C_SRC,
      "+ z * exp(-0.5 * z * z) / sqrt(2.0 * M_PI);", "+ exp(-0.5 * z * z) / sqrt(2.0 * M_PI);"),
     ("mlp: first layer's derivative taken at the second layer's input", C_SRC,

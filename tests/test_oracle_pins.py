@@ -9,7 +9,8 @@ fails at least one test:
                  row = ln u, p proportional to exp(-beta d2), rows sum to 1),
                  closed form for equal distances, scale invariance
   symmetrize     dense (P_cond + P_cond^T) / 2n construction, sum 1, symmetry
-  init_fx        extremes map to 0 and R-1, affine within one ulp
+  init_fx        extremes map to 0 and R-1, affine within one ulp; the floor
+                 of the exact rational map
   morton         recursive quadtree child numbering (child = 2*ybit + xbit)
   pyramid        per-level bincount of the shifted pixel pairs; sums
   exact forces   scikit-learn's exact t-SNE KL and gradient; hand-derived
@@ -24,7 +25,7 @@ fails at least one test:
                  centre of mass; r_c / d^2 in the printed form); error falls
                  with theta
   rescale        Python big-integer arithmetic; pixel range exactly 0..r-1
-  update         hand cases of the gains rule
+  update         hand cases of the gains rule; the step rounded half to even
   run            the fixed-point + rescale + beta run equals plain y-space
                  t-SNE (scikit-learn gradient) up to translation (Sec. 4.2's
                  claimed equivalence)
@@ -573,6 +574,43 @@ def test_update_rule_cases():
     oracle.update(z[:1], s, np.array([[1.0, 1.0]]), np.zeros((1, 2)), 1.0, 1.0, 0.5, 1.0,
                   u2, gains2, min_gain=0.01)
     np.testing.assert_allclose(gains2, [[0.01, 0.01]])
+
+
+def test_update_rounds_the_step_half_to_even():
+    # zhat = z + rint(u / s): nearest ulp, ties to even (2.5 -> 2, 3.5 -> 4,
+    # -2.5 -> -2), not truncation (2.7 -> 3, -2.7 -> -3)
+    want = np.array([2.5, 3.5, -2.5, 2.7, -2.7, 0.49])
+    m = want.shape[0]
+    z = np.full((m, 2), 1000, np.uint32)
+    s = np.array([1.0, 1.0])
+    # u = 0, gains 0.8 -> 1.0 (the signs differ), mu = 0, eta = 1: u' = -g = -4 Fattr
+    Fattr = np.stack([-want / 4, -want / 4], 1)
+    u = np.zeros((m, 2))
+    gains = np.full((m, 2), 0.8)
+    zhat, _ = oracle.update(z, s, Fattr, np.zeros((m, 2)), 1.0, 1.0, 0.0, 1.0, u, gains)
+    np.testing.assert_allclose(u[:, 0], want, rtol=1e-15)
+    assert list(zhat[:, 0] - 1000) == [2, 4, -2, 3, -3, 0]
+
+
+def test_init_fx_is_the_floor_of_the_exact_map():
+    # Eq. z1: z = floor((y - min) 2^32 / (max - min)); against exact rational
+    # arithmetic on the same float64 inputs (the FP64 evaluation may differ
+    # only where the exact value lies within a few 2^-20 of an integer)
+    from fractions import Fraction
+    rng = np.random.default_rng(30)
+    Y = rng.standard_normal((3000, 2)) * 3.0 + 1.0
+    z, _ = oracle.init_fx(Y)
+    for d in range(2):
+        mn, mx = Fraction(Y[:, d].min()), Fraction(Y[:, d].max())
+        off = 0
+        for i in range(Y.shape[0]):
+            t = (Fraction(Y[i, d]) - mn) * 2 ** 32 / (mx - mn)
+            exact = min(2 ** 32 - 1, t.numerator // t.denominator)
+            if int(z[i, d]) != exact:
+                frac = t - (t.numerator // t.denominator)
+                assert min(frac, 1 - frac) < Fraction(1, 2 ** 18), (i, d)
+                off += 1
+        assert off <= 3
 
 
 def test_fixed_point_run_equals_y_space_tsne():
