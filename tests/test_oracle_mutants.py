@@ -82,6 +82,9 @@ MUTANTS = [
     ("bh: own point left in the x sum of its leaf", C_SRC, "Sx -= zx;", ""),
     ("bh: own point counted in its leaf", C_SRC,
      "N -= 1;\n                if (N == 0) continue;", "if (N == 0) continue;"),
+    ("bh: own cells above the leaves left to the criterion", C_SRC,
+     "int contains = ((mi >> (2 * (L - l))) == mc);",
+     "int contains = leaf && ((mi >> (2 * (L - l))) == mc);"),
     ("bh: force missing one kernel factor", C_SRC, "fx += Nw * w * dx;", "fx += Nw * dx;"),
     ("bh: acceptance test reversed", C_SRC, "(rc2 < th2 * dd)", "(rc2 > th2 * dd)"),
     ("bh: cell size of the child level", C_SRC,

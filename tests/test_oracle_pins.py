@@ -22,8 +22,9 @@ fails at least one test:
                  (centres of mass; pixel midpoints in geometric-centre mode);
                  the acceptance threshold on a hand-built tree sits at
                  r_c / d = theta (r_c the cell diagonal, d the distance to the
-                 centre of mass; r_c / d^2 in the printed form); error falls
-                 with theta
+                 centre of mass; r_c / d^2 in the printed form); at a huge
+                 theta exactly the siblings of a point's own cells; error
+                 falls with theta
   rescale        Python big-integer arithmetic; pixel range exactly 0..r-1
   update         hand cases of the gains rule; the step rounded half to even
   run            the fixed-point + rescale + beta run equals plain y-space
@@ -515,6 +516,49 @@ def test_bh_acceptance_threshold_is_the_cell_diagonal(crit_mode):
                                        crit_mode=crit_mode)
     assert acc_hi[0] == 1
     assert acc_lo[0] == 3
+
+
+def test_bh_own_cells_are_always_opened():
+    # with theta so large that every other cell is accepted at its first test,
+    # point i interacts exactly with the non-empty siblings of each of its
+    # ancestors (one level at a time) and with the others of its own pixel:
+    # a tree-free count and sum over pixel coordinates
+    L = 4
+    F = 32 - L
+    rng = np.random.default_rng(31)
+    n = 200
+    pix = rng.integers(0, 2 ** L, (n, 2))
+    pix[:30] = pix[30:60]
+    z = ((pix.astype(np.int64) << F) + rng.integers(0, 2 ** F, (n, 2))).astype(np.uint32)
+    s = np.array([1.0e-9, 1.5e-9])
+    Fb, Zb, acc = oracle.bh_repulsion(z, s, L, 1e6)
+    zi64 = z.astype(np.int64)
+    for i in range(n):
+        cnt, fx, fy, zs = 0, 0.0, 0.0, 0.0
+        for l in range(1, L + 1):
+            cell = pix >> (L - l)
+            mine = cell[i]
+            sib = np.all((cell >> 1) == (mine >> 1), axis=1) & ~np.all(cell == mine, axis=1)
+            groups = {}
+            for j in np.nonzero(sib)[0]:
+                groups.setdefault((int(cell[j, 0]), int(cell[j, 1])), []).append(j)
+            if l == L:
+                others = [j for j in np.nonzero(np.all(cell == mine, axis=1))[0] if j != i]
+                if others:
+                    groups["own"] = others
+            for mem in groups.values():
+                N = len(mem)
+                dx = s[0] * (int(zi64[i, 0]) - zi64[mem, 0].sum() / N)
+                dy = s[1] * (int(zi64[i, 1]) - zi64[mem, 1].sum() / N)
+                w = 1.0 / (1.0 + dx * dx + dy * dy)
+                cnt += 1
+                zs += N * w
+                fx += N * w * w * dx
+                fy += N * w * w * dy
+        assert acc[i] == cnt, i
+        assert Zb[i] == pytest.approx(zs, rel=1e-12)
+        assert Fb[i, 0] == pytest.approx(fx, rel=1e-9, abs=1e-12 * abs(Fb).max())
+        assert Fb[i, 1] == pytest.approx(fy, rel=1e-9, abs=1e-12 * abs(Fb).max())
 
 
 def test_bh_theta_half_close_to_exact():
