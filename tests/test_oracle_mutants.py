@@ -77,6 +77,10 @@ MUTANTS = [
      "uint32_t m = orc_morton(z[2 * i] >> F, z[2 * i + 1] >> F);",
      "uint32_t m = orc_morton(z[2 * i] >> (F + 1), z[2 * i + 1] >> (F + 1));"),
     # Barnes-Hut repulsion (Sec. 3.3, Eq. bh_criteria)
+    ("bh: centre of mass without its remainder", C_SRC,
+     "uint64_t q = S / N, r = S % N;", "uint64_t q = S / N, r = 0;"),
+    ("bh: distance along x only", C_SRC,
+     "double dd = dx * dx + dy * dy;\n            if (!leaf", "double dd = dx * dx;\n            if (!leaf"),
     ("bh: centre-of-mass remainder added, not subtracted", C_SRC,
      "- (double)r / (double)N;", "+ (double)r / (double)N;"),
     ("bh: own point left in the x sum of its leaf", C_SRC, "Sx -= zx;", ""),
@@ -109,6 +113,12 @@ MUTANTS = [
     ("attraction: sampled rows ignored", C_SRC,
      "int64_t i = rows ? rows[q] : q;\n        double fx = 0.0, fy = 0.0;\n",
      "int64_t i = q;\n        double fx = 0.0, fy = 0.0;\n"),
+    ("attraction: kernel without the y offset", C_SRC,
+     "double w = 1.0 / (1.0 + dx * dx + dy * dy);\n            fx += val[e]",
+     "double w = 1.0 / (1.0 + dx * dx);\n            fx += val[e]"),
+    ("exact repulsion: kernel without the y offset", C_SRC,
+     "double w = 1.0 / (1.0 + dx * dx + dy * dy);\n            zs += w;",
+     "double w = 1.0 / (1.0 + dx * dx);\n            zs += w;"),
     ("attraction: wrong sign", C_SRC, "fx += val[e] * w * dx;", "fx -= val[e] * w * dx;"),
     ("attraction: kernel squared", C_SRC,
      "fx += val[e] * w * dx;\n            fy += val[e] * w * dy;",
@@ -138,12 +148,16 @@ MUTANTS = [
     # screen rescale (Sec. 4.2, Eq. beta_scaling)
     ("rescale: compensation of s not applied", C_SRC,
      "s[d] = s[d] * ldexp((double)gamma, -32);", ""),
+    ("rescale: both axes' extremes from x", C_SRC,
+     "int64_t mn = zhat[d], mx = zhat[d];", "int64_t mn = zhat[0], mx = zhat[0];"),
     ("rescale: offset from the maximum", C_SRC,
      "(uint64_t)(zhat[2 * i + d] - mn) << 32", "(uint64_t)(mx - zhat[2 * i + d]) << 32"),
     # KL (Eq. cost_func)
     ("kl: q not normalised by Z", C_SRC,
      "double q = 1.0 / ((1.0 + dx * dx + dy * dy) * Z);",
      "double q = 1.0 / (1.0 + dx * dx + dy * dy);"),
+    ("kl: distance along x only", C_SRC,
+     "double q = 1.0 / ((1.0 + dx * dx + dy * dy) * Z);", "double q = 1.0 / ((1.0 + dx * dx) * Z);"),
     ("kl: ratio inverted", C_SRC, "c += p * log(p / q);", "c += p * log(q / p);"),
     ("kl: stored zeros of P not skipped", C_SRC,
      "if (p <= 0.0) continue;", "if (p < 0.0) continue;"),
