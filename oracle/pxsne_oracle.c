@@ -693,11 +693,10 @@ double orc_mlp(int32_t d, int32_t H, const double *W1, const double *b1, const d
             z2[a] = s;
             h2[a] = gelu(s);
         }
-        double y[2], dy[2];
+        double dy[2];
         for (int o = 0; o < 2; o++) {
             double s = b3[o];
             for (int32_t c = 0; c < H; c++) s += W3[(size_t)o * H + c] * h2[c];
-            y[o] = s;
             if (Y) Y[2 * r + o] = s;
             double e = T ? s - (double)T[2 * r + o] : 0.0;
             L += e * e;
