@@ -368,6 +368,22 @@ def test_sampled_rows_equal_the_full_rows():
     assert p_r == hits[rows].sum() / (8 * len(rows))
 
 
+def test_Z_of_the_run_is_the_sum_of_its_repulsion():
+    # the KL's normalisation: Z = sum_i Z_i of the run's own repulsion, the
+    # tree's at the run's theta and centre mode, the exact sum when exact
+    n, L = 400, 7
+    z, s = _random_state(n, 32)
+    st = oracle.State(z, s, np.zeros((n, 2)), np.ones((n, 2)))
+    for theta, cm in ((0.5, 0), (0.8, 1), (0.0, 0)):
+        _, Zi, _ = oracle.bh_repulsion(z, s, L, theta, centre_mode=cm)
+        Z = oracle.Z_of(st, oracle.Params(L=L, theta=theta, centre_mode=cm))
+        assert Z == pytest.approx(Zi.sum(), rel=1e-12)
+    _, Ze = oracle.exact_repulsion(z, s)
+    assert oracle.Z_of(st, oracle.Params(L=L, exact=1)) == pytest.approx(Ze.sum(), rel=1e-12)
+    _, Zb, _ = oracle.bh_repulsion(z, s, L, 0.5)
+    assert abs(Zb.sum() - Ze.sum()) > 1e-9 * Ze.sum()     # the two differ here
+
+
 def test_kl_ignores_explicit_zeros():
     # a stored zero of P (0 ln 0 = 0) adds nothing to Eq. cost_func
     n = 30
