@@ -148,6 +148,43 @@ def test_missing_library_fails_loudly():
     assert out.returncode == 0 and out.stdout.strip() == "ok", out.stdout + out.stderr
 
 
+C_CLIENT = r"""
+#include "pxsne.h"
+#include <stdio.h>
+int main(void) {
+    pxsne_params p;
+    pxsne_ctx *c = 0;
+    int rc;
+    pxsne_default_params(&p);
+    rc = pxsne_create(&c, 0, 0);
+    printf("%d %d %d\n", p.log2_r, p.k, rc);
+    return !(p.log2_r == 11 && p.k == 90 && rc == PXSNE_E_ARG && c == 0 &&
+             pxsne_last_error(0)[0] != 0);
+}
+"""
+
+
+def test_header_serves_a_plain_c_client(tmp_path):
+    """include/pxsne.h is plain C (C99, pedantic, no warnings) and C++; a C
+    program links against the library and calls it (no device work)."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None or shutil.which("g++") is None:
+        pytest.skip("gcc/g++ needed")
+    pxbuild.build()
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(pxbuild.LIB)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                    "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lpxsne",
+                    f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout.split() == ["11", "90", "-1"], out
+    subprocess.run(["g++", "-std=c++17", "-Wall", "-Wextra", "-Werror", "-fsyntax-only",
+                    "-x", "c++", HEADER], check=True)
+
+
 def test_sources_target_sm103a_only():
     assert pxbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
 
