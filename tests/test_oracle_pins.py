@@ -612,6 +612,15 @@ def test_rescale_big_integer_arithmetic():
         F = 32 - L
         for d in range(2):
             assert (z[:, d] >> F).min() == 0 and (z[:, d] >> F).max() == 2 ** L - 1
+    # the widest range a step can produce (steps are clamped to 2^58 ulps):
+    # (zhat - min) 2^32 overflows 64 bits and must still be exact
+    zw = np.array([[-(2 ** 58), 0], [2 ** 32 - 1 + 2 ** 58, 1], [12345, 2 ** 58],
+                   [2 ** 57 + 3, 7]], np.int64)
+    z, _ = oracle.rescale(zw, s)
+    for d in range(2):
+        mn, mx = int(zw[:, d].min()), int(zw[:, d].max())
+        gamma = mx - mn + 1
+        assert [int(v) for v in z[:, d]] == [((int(v) - mn) << 32) // gamma for v in zw[:, d]]
 
 
 def test_update_rule_cases():
