@@ -144,6 +144,12 @@ MUTANTS = [
     ("run: momentum phases swapped", C_SRC,
      "double mu = t < p->mom_switch ? p->mom0 : p->mom1;",
      "double mu = t < p->mom_switch ? p->mom1 : p->mom0;"),
+    ("run: centre mode not passed to the repulsion", C_SRC,
+     "p->theta, p->crit_mode, p->centre_mode,\n                             cnt, sx, sy",
+     "p->theta, p->crit_mode, 0,\n                             cnt, sx, sy"),
+    ("run: criterion form not passed to the repulsion", C_SRC,
+     "p->theta, p->crit_mode, p->centre_mode,\n                             cnt, sx, sy",
+     "p->theta, 0, p->centre_mode,\n                             cnt, sx, sy"),
     ("run: screen rescale skipped", C_SRC, "        orc_rescale(n, zhat, z, s);\n    }", "    }"),
     # screen rescale (Sec. 4.2, Eq. beta_scaling)
     ("rescale: compensation of s not applied", C_SRC,

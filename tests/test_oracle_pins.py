@@ -27,7 +27,8 @@ fails at least one test:
                  falls with theta
   rescale        Python big-integer arithmetic; pixel range exactly 0..r-1
   update         hand cases of the gains rule; the step rounded half to even
-  run            the fixed-point + rescale + beta run equals plain y-space
+  run            one step is the composition of the pinned parts, bit for
+                 bit; the fixed-point + rescale + beta run equals plain y-space
                  t-SNE (scikit-learn gradient) up to translation (Sec. 4.2's
                  claimed equivalence)
   kl             scikit-learn, closed forms, KL >= 0, a stored value written
@@ -621,6 +622,42 @@ def test_rescale_big_integer_arithmetic():
         mn, mx = int(zw[:, d].min()), int(zw[:, d].max())
         gamma = mx - mn + 1
         assert [int(v) for v in z[:, d]] == [((int(v) - mn) << 32) // gamma for v in zw[:, d]]
+
+
+@pytest.mark.parametrize("mode", [dict(), dict(centre_mode=1), dict(crit_mode=1, theta=2.0),
+                                  dict(exact=1)])
+def test_run_step_is_the_composition_of_its_parts(mode):
+    # one iteration of the run = tree, repulsion (the run's theta, criterion
+    # and centre mode, or the exact sum), attraction, update with Z = sum Z_i
+    # and the schedule's alpha and mu, then the rescale: each part pinned above
+    n = 300
+    rng = np.random.default_rng(33)
+    A = (rng.random((n, n)) < 0.05) * rng.random((n, n))
+    A = A + A.T
+    np.fill_diagonal(A, 0)
+    P = _dense_csr(A / A.sum())
+    z, s = _random_state(n, 34)
+    prm = oracle.Params(L=7, **mode)
+    for t0 in (0, prm.exag_iters):
+        st = oracle.State(z.copy(), s.copy(), rng.standard_normal((n, 2)) * 1e-3,
+                          rng.uniform(0.5, 2.0, (n, 2)), t0)
+        ref = st.copy()
+        oracle.run(P, st, prm, 1)
+        if prm.exact:
+            Fr, Zi = oracle.exact_repulsion(ref.z, ref.s)
+        else:
+            Fr, Zi, _ = oracle.bh_repulsion(ref.z, ref.s, prm.L, prm.theta,
+                                            crit_mode=prm.crit_mode, centre_mode=prm.centre_mode)
+        Fa = oracle.attraction(P, ref.z, ref.s)
+        alpha = prm.exag if t0 < prm.exag_iters else 1.0
+        mu = prm.mom0 if t0 < prm.mom_switch else prm.mom1
+        Z = float(np.cumsum(Zi)[-1])     # summed in point order, as the run does
+        zhat, _ = oracle.update(ref.z, ref.s, Fa, Fr, Z, alpha, mu, prm.eta, ref.u,
+                                ref.gains, min_gain=prm.min_gain)
+        zr, sr = oracle.rescale(zhat, ref.s)
+        assert np.array_equal(st.z, zr) and np.array_equal(st.s, sr)
+        assert np.array_equal(st.u, ref.u) and np.array_equal(st.gains, ref.gains)
+        assert st.t == t0 + 1
 
 
 def test_update_rule_cases():
