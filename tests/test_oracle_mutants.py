@@ -28,6 +28,8 @@ MUTANTS = [
      "if (j == i) continue;\n            const float *xj", "const float *xj"),
     ("knn: first coordinate dropped from the distance", C_SRC,
      "for (int32_t d = 0; d < D; d++) {", "for (int32_t d = 1; d < D; d++) {"),
+    ("knn: absolute differences summed, not squares", C_SRC,
+     "s += t * t;", "s += fabs(t);"),
     ("knn: sampled rows ignored", C_SRC,
      "int64_t i = rows ? rows[q] : q;\n        if (i < 0", "int64_t i = q;\n        if (i < 0"),
     # perplexity bisection (Sec. 3.2)
@@ -37,6 +39,8 @@ MUTANTS = [
      "const double target = log(perplexity);", "const double target = log2(perplexity);"),
     ("perplexity: bracket moved the wrong way", C_SRC,
      "if (H > target) { /* too flat: sharpen */", "if (H < target) { /* too flat: sharpen */"),
+    ("perplexity: bisection started at beta = 0", C_SRC,
+     "double beta = 1.0, lo = 0.0, hi = 0.0;", "double beta = 0.0, lo = 0.0, hi = 0.0;"),
     ("perplexity: row minimum left in the mean term", C_SRC,
      "hs += (d[j] - dmin) * e;", "hs += d[j] * e;"),
     ("perplexity: stop test a hundred times too loose", C_SRC,
@@ -107,6 +111,13 @@ MUTANTS = [
      "cy |= ((mc >> (2 * b)) & 1u) << b;\n                    cx |= ((mc >> (2 * b + 1)) & 1u) << b;"),
     # exact repulsion and attraction (Eq. grad)
     ("exact repulsion: w instead of w^2", C_SRC, "fx += w * w * dx;", "fx += w * dx;"),
+    ("exact repulsion: a point counted against itself", C_SRC,
+     "if (j == i) continue;\n            double dx = s0 * (double)((int64_t)z[2 * i] - (int64_t)z[2 * j]);\n"
+     "            double dy = s1 * (double)((int64_t)z[2 * i + 1] - (int64_t)z[2 * j + 1]);\n"
+     "            double w = 1.0 / (1.0 + dx * dx + dy * dy);\n            zs += w;",
+     "double dx = s0 * (double)((int64_t)z[2 * i] - (int64_t)z[2 * j]);\n"
+     "            double dy = s1 * (double)((int64_t)z[2 * i + 1] - (int64_t)z[2 * j + 1]);\n"
+     "            double w = 1.0 / (1.0 + dx * dx + dy * dy);\n            zs += w;"),
     ("exact repulsion: sampled rows ignored", C_SRC,
      "int64_t i = rows ? rows[q] : q;\n        double fx = 0.0, fy = 0.0, zs = 0.0;",
      "int64_t i = q;\n        double fx = 0.0, fy = 0.0, zs = 0.0;"),
@@ -176,6 +187,9 @@ MUTANTS = [
      "double dd = dx * dx;\n            int32_t p;"),
     ("nbr_precision: sampled rows ignored", C_SRC,
      "int64_t i = rows ? rows[q] : q;\n        int32_t *I", "int64_t i = q;\n        int32_t *I"),
+    ("nbr_precision: all kh listed neighbours used, not the first k", C_SRC,
+     "for (int32_t b = 0; b < k; b++)\n                if (knn_hd",
+     "for (int32_t b = 0; b < kh; b++)\n                if (knn_hd"),
     ("nbr_precision: not divided by k", C_SRC,
      "return (double)hits / ((double)k * (double)m);", "return (double)hits / (double)m;"),
     # warm-start MLP
