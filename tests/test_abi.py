@@ -73,7 +73,8 @@ def test_kl_noalloc_rejects_bad_arguments_before_any_device_work(lib):
     ok = dict(rp=1, col=1, val=1, n=10, z=1, s0=1.0, s1=1.0, Z=1.0, out=1)
     for bad in (dict(rp=None), dict(col=None), dict(val=None), dict(z=None), dict(out=None),
                 dict(n=0), dict(n=big + 1), dict(s0=0.0), dict(s1=-1.0), dict(Z=0.0),
-                dict(Z=float("nan"))):
+                dict(Z=float("nan")), dict(Z=float("inf")), dict(s0=float("inf")),
+                dict(s1=float("inf"))):
         a = ok | bad
         assert f(a["rp"], a["col"], a["val"], a["n"], a["z"], a["s0"], a["s1"], a["Z"],
                  a["out"], None) == -1, bad
