@@ -52,8 +52,6 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="points (debug only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-rows", type=int, default=200000,
-                    help="rows of the oracle sample (CPU baseline)")
     ap.add_argument("--no-studies", action="store_true",
                     help="skip the time-to-KL-target and screen-size studies")
     ap.add_argument("--no-warmstart", action="store_true",
@@ -176,56 +174,48 @@ def group_bytes(n, nnz, L):
     }
 
 
-# DRAM bytes per launch from one ncu capture of the current kernels at full size
-# (dram__bytes_read.sum + dram__bytes_write.sum, profiles/traffic_gmm128_n1M.md);
-# to be set to None whenever the kernel changes
-TRAFFIC_BYTES = {"k_bh_traverse": 47.31e6, "k_attract": 1.2945e9, "k_snap_hist": 49.50e6,
-                 "k_pyr_pass": 153.13e6}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an
+# ncu capture of the current kernels, by (workload, n); emptied whenever a
+# kernel changes, until the capture is taken again
+TRAFFIC_BYTES = {}
+TRAFFIC_SOURCE = ""
 
 FLOP_TEST = 10    # offset, d^2 and criterion of one tested cell
 FLOP_ACCEPT = 10  # kernel value, N w, N w^2 and the three accumulations
+RECORD_BYTES = 20  # a cell's record: centre of mass (16 B) + count (4 B)
 
 
-def oracle_sample(_unused, Y0, rows, L, theta, seed=0):
-    """Time the oracle's iteration on a bounded sample: the full tree, the BH
-    repulsion and attraction of `rows` sampled points, the full update and
-    rescale; scaled to one full iteration.  Returns (it/s, details)."""
+def synthetic_P(n, seed=0, per=135):
+    """A P of the workload's shape for timing the oracle: `per` entries per row
+    (90 neighbours + about 45 reverse edges at k = 90), uniform columns other
+    than the row, values 1/(2 n 90).  The workload's exact P would need the
+    oracle's O(n^2 D) neighbour search (hours at n = 1M)."""
     import oracle
-    n = Y0.shape[0]
     rng = np.random.default_rng(seed + 99)
+    rp = np.arange(n + 1, dtype=np.int64) * per
+    rows = np.repeat(np.arange(n, dtype=np.int64), per)
+    col = ((rows + 1 + rng.integers(0, n - 1, size=n * per)) % n).astype(np.int32)
+    val = np.full(n * per, 1.0 / (2 * n * 90))
+    return oracle.CSR(rp, col, val)
+
+
+def oracle_iterations(P, Y0, L, theta, min_seconds, max_iters, warmup=0):
+    """Whole iterations of the oracle (tree, Barnes-Hut repulsion and
+    attraction of every row, Z, update, rescale) from Y0, one at a time until
+    min_seconds of CPU work or max_iters are done (after `warmup` untimed
+    ones).  Returns (it/s, iterations, seconds)."""
+    import oracle
     st = oracle.State.from_y0(Y0)
-    sample = np.sort(rng.choice(n, size=min(rows, n), replace=False)).astype(np.int64)
-    m = sample.shape[0]
-    # a P of the workload's shape for the sampled rows only: 90 neighbours + 45
-    # reverse edges per row, uniform columns, values 1/(2 n 90)
-    per = 135
-    rp = np.zeros(n + 1, np.int64)
-    cnt = np.zeros(n, np.int64)
-    cnt[sample] = per
-    rp[1:] = np.cumsum(cnt)
-    col = rng.integers(0, n, size=m * per).astype(np.int32)
-    val = np.full(m * per, 1.0 / (2 * n * 90))
-    P = oracle.CSR(rp, col, val)
-    t0 = time.perf_counter()
-    tree = oracle.pyramid(st.z, L)
-    t1 = time.perf_counter()
-    Frep, Zi, _ = oracle.bh_repulsion(st.z, st.s, L, theta, rows=sample, tree=tree)
-    t2 = time.perf_counter()
-    Fattr = oracle.attraction(P, st.z, st.s, rows=sample)
-    t3 = time.perf_counter()
-    Fr = np.zeros((n, 2))
-    Fa = np.zeros((n, 2))
-    Fr[sample] = Frep
-    Fa[sample] = Fattr
-    zhat, _ = oracle.update(st.z, st.s, Fa, Fr, max(Zi.sum() * n / m, 1.0), 12.0, 0.5, 200.0,
-                            st.u, st.gains)
-    oracle.rescale(zhat, st.s)
-    t4 = time.perf_counter()
-    scale = n / m
-    per_iter = (t1 - t0) + (t2 - t1) * scale + (t3 - t2) * scale + (t4 - t3)
-    det = {"tree_s": t1 - t0, "bh_sample_s": t2 - t1, "attr_sample_s": t3 - t2,
-           "update_rescale_s": t4 - t3, "rows": m, "scale": scale}
-    return 1.0 / per_iter, det, (t4 - t0)
+    params = oracle.Params(L=L, theta=theta)
+    for _ in range(warmup):
+        oracle.run(P, st, params, 1)
+    wall, its = 0.0, 0
+    while its < max(max_iters, 1) and (its == 0 or wall < min_seconds):
+        t0 = time.perf_counter()
+        oracle.run(P, st, params, 1)
+        wall += time.perf_counter() - t0
+        its += 1
+    return its / wall, its, wall
 
 
 def iterate_to_kl(ctx, target, chunk, max_iters, stream, torch):
@@ -484,7 +474,9 @@ def warmstart_experiment(px, ctx, X, Y0, args, torch):
 
 
 def run_reference(args):
-    """The oracle (plain FP64 C, OpenMP) as the reference arm."""
+    """The oracle (plain FP64 C, OpenMP) as the reference arm: each step is one
+    whole iteration of the workload on the host cores, on a synthetic P of the
+    workload's shape."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
@@ -494,24 +486,23 @@ def run_reference(args):
     n = args.n
     Y0 = datagen.init_y0(0, n)
     L = WORKLOAD["log2_r"]
-    vals = []
+    P = synthetic_P(n)
+    st = oracle.State.from_y0(Y0)
+    params = oracle.Params(L=L, theta=WORKLOAD["theta"])
     for _ in range(max(args.warmup, 0)):
-        oracle_sample(None, Y0, max(1000, args.cpu_rows // 8), L, WORKLOAD["theta"])
-    wall = 0.0
-    for k in range(max(args.steps, 1)):
-        v, det, w = oracle_sample(None, Y0, max(1000, args.cpu_rows // 8), L,
-                                  WORKLOAD["theta"], seed=k)
-        vals.append(v)
-        wall += w
-        if wall > 120.0:
-            break
-    value = float(np.mean(vals))
+        oracle.run(P, st, params, 1)
+    steps = max(args.steps, 1)
+    t0 = time.perf_counter()
+    oracle.run(P, st, params, steps)
+    wall = time.perf_counter() - t0
+    value = steps / wall
     cores = oracle.num_threads()
-    sample = (f"first iteration from Y0 at n={n}: full tree + BH/attraction of "
-              f"{det['rows']} sampled rows scaled by {det['scale']:.1f} + full update/rescale, "
-              f"{len(vals)} repetitions")
+    sample = (f"{steps} whole iterations at n={n} from Y0 after {max(args.warmup, 0)} "
+              f"untimed ones (tree, Barnes-Hut and attraction of every row, Z, update, "
+              f"rescale), on a synthetic P of the workload's shape (135 uniform columns "
+              f"per row)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "it/s",
-            "n_gpus": args.gpus, "steps": len(vals), "warmup": args.warmup,
+            "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {k: WORKLOAD[k] for k in WORKLOAD} | {"n": n},
@@ -544,6 +535,8 @@ def run_gpu(args):
     W = WORKLOAD
     X, Y0 = make_inputs(n, seed=rank)
     stream = torch.cuda.Stream()
+    # the L2 and FP32 peaks of this GPU, measured before anything else runs
+    mpeaks = px.measure_peaks(stream.cuda_stream)
     params = px.Params(log2_r=W["log2_r"], theta=W["theta"], k=W["k"],
                        perplexity=W["perplexity"])
     ctx = px.Context(params, stream=stream.cuda_stream)
@@ -615,32 +608,46 @@ def run_gpu(args):
     # events around each kernel group on the library's stream
     ctx.init(Y0)
     groups, prof_total = ctx.step_profiled(args.steps)
+    # (the traversal's work counters: sums over the K profiled iterations)
     acc, tst, wsteps, nodes = ctx.counters()
     peaks, peak_kind = measured_peaks()
     gb = group_bytes(n, nnz, W["log2_r"])
-    # the recorded DRAM traffic holds for the headline workload at full size only
-    traffic = TRAFFIC_BYTES if (W["workload"] == "gmm128" and n == 1_000_000) else {}
+    traffic = TRAFFIC_BYTES.get((W["workload"], n), {})
     top = max(groups, key=groups.get)
     avg_ms = {g: v / args.steps for g, v in groups.items()}
-    sm_mhz = ck["sm_mhz"] if ck else 1477.0
-    alu_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     if top == "k_bh_traverse":
-        # work of the last traversal (final state) as the per-launch estimate
+        # FLOPs of the tested and accepted (point, cell) pairs of all K
+        # iterations over the traversal's summed time, against the FP32 rate
+        # measured in this process (packed pairs, the traversal's form)
         flops = FLOP_TEST * tst + FLOP_ACCEPT * acc
-        achieved = flops / (avg_ms[top] / 1e3) / 1e12
-        roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": alu_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / alu_peak_tflops,
+        sec = groups[top] / 1e3
+        achieved = flops / sec / 1e12
+        fp32 = max(mpeaks["fp32_tflops"], mpeaks["fp32_packed_tflops"])
+        l2_alg = RECORD_BYTES * tst / sec / 1e9
+        roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": fp32,
+                "unit": "TFLOP/s", "frac": achieved / fp32,
                 "traffic": traffic.get(top),
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median "
-                               "SM clock of this run)"}
+                "peak_source": "measured in this run by pxsne_measure_peaks (FP32 FMA "
+                               "chains, packed pairs; see measured_peaks)",
+                "work": f"{FLOP_TEST} FLOP per tested + {FLOP_ACCEPT} per accepted "
+                        f"(point, cell) pair, summed over the {args.steps} profiled "
+                        f"iterations",
+                "l2": {"achieved": l2_alg, "peak": mpeaks["l2_read_gbs"], "unit": "GB/s",
+                       "frac": l2_alg / mpeaks["l2_read_gbs"],
+                       "work": f"{RECORD_BYTES} B of cell record per tested (point, cell) "
+                               f"pair"}}
     else:
         achieved = gb[top] / (avg_ms[top] / 1e3) / 1e9
         roof = {"kernel": top, "bound": "hbm", "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic.get(top),
                 "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_kind})"}
+    roof["traffic_source"] = (TRAFFIC_SOURCE if roof["traffic"] is not None else
+                              "no ncu capture of the current kernel at this size")
     kernels = {g: {"ms_per_launch": avg_ms[g], "share": groups[g] / sum(groups.values()),
-                   "alg_GBps": gb[g] / (avg_ms[g] / 1e3) / 1e9 if avg_ms[g] > 0 else None}
+                   "alg_GBps": gb[g] / (avg_ms[g] / 1e3) / 1e9 if avg_ms[g] > 0 else None,
+                   "hbm_frac": gb[g] / (avg_ms[g] / 1e3) / 1e9 / peaks["hbm_gbs"]
+                   if avg_ms[g] > 0 else None}
                for g in groups}
 
     # end to end through the public API with host buffers: P from pinned host
@@ -676,45 +683,32 @@ def run_gpu(args):
         oracle.build()
         cores = oracle.num_threads()
 
-        def repeat(rows, min_s):
-            # the sampled iteration again (other samples) until min_s seconds of
-            # CPU work are done
-            vals, wall, det = [], 0.0, None
-            while wall < min_s and len(vals) < 50:
-                v, det, w = oracle_sample(X.shape, Y0, rows, W["log2_r"], W["theta"],
-                                          seed=len(vals))
-                vals.append(v)
-                wall += w
-            return float(np.mean(vals)), det, wall, len(vals)
-
-        v, det, w, reps = repeat(args.cpu_rows, 10.0)
+        Pc = synthetic_P(n)
+        # whole iterations from Y0 until about 10 s of CPU work (at least one)
+        v, its, w = oracle_iterations(Pc, Y0, W["log2_r"], W["theta"], 10.0, 50)
         cpu = {"value": v, "unit": "it/s", "cores": cores, "kind": "oracle",
-               "sample": (f"first iteration from Y0: full tree + BH/attraction of "
-                          f"{det['rows']} of {n} rows scaled by {det['scale']:.1f} + full "
-                          f"update/rescale, {reps} samples ({w:.1f} s of CPU work)")}
+               "sample": (f"{its} whole iterations from Y0 at n={n} (tree, Barnes-Hut and "
+                          f"attraction of every row, Z, update, rescale; {w:.1f} s of CPU "
+                          f"work) on a synthetic P of the workload's shape (135 uniform "
+                          f"columns per row)")}
         # the same on one thread (the paper times its CPU code single-threaded)
         oracle.set_num_threads(1)
         try:
-            v1, det1, w1, reps1 = repeat(max(1000, args.cpu_rows // 16), 8.0)
+            v1, its1, w1 = oracle_iterations(Pc, Y0, W["log2_r"], W["theta"], 8.0, 50)
         finally:
             oracle.set_num_threads(cores)
-        # the oracle on the smaller workloads: the whole first iteration from Y0
-        # (tree, BH and attraction of every row, update, rescale)
+        del Pc
+        # the oracle on the smaller workloads, whole iterations the same way
         import datagen
         cpu["small_configs"] = {}
         for name, (gen, nn, LL, _, _) in SMALL_CONFIGS.items():
             Ys = datagen.init_y0(0, nn)
-            vals, wall = [], 0.0
-            while wall < 3.0 and len(vals) < 20:
-                vv, _, ww = oracle_sample(None, Ys, nn, LL, W["theta"], seed=len(vals))
-                vals.append(vv)
-                wall += ww
-            cpu["small_configs"][name] = {"value": float(np.mean(vals)), "unit": "it/s",
-                                          "cores": cores, "n": nn, "samples": len(vals)}
+            vv, itv, _ = oracle_iterations(synthetic_P(nn), Ys, LL, W["theta"], 3.0, 200)
+            cpu["small_configs"][name] = {"value": vv, "unit": "it/s", "cores": cores,
+                                          "n": nn, "iterations": itv}
         cpu["one_thread"] = {"value": v1, "unit": "it/s", "cores": 1,
-                             "sample": f"{det1['rows']} of {n} rows scaled by "
-                                       f"{det1['scale']:.1f}, {reps1} samples ({w1:.1f} s of "
-                                       f"CPU work)"}
+                             "sample": f"{its1} whole iterations from Y0 at n={n} ({w1:.1f} s "
+                                       f"of CPU work), same synthetic P"}
 
     studies = None
     if rank == 0 and not args.no_studies:
@@ -752,7 +746,7 @@ def run_gpu(args):
                                               "l2": f"inputs larger than L2 (P "
                                                     f"{nnz * 8 / 1e9:.1f} GB read per iteration)",
                                               "timed_iterations": f"t = 0..{args.steps - 1}"},
-            "roofline": roof, "kernels": kernels,
+            "roofline": roof, "kernels": kernels, "measured_peaks": mpeaks,
             "traversal": {"accepted_pairs": acc, "tested_pairs": tst,
                           "accepted_per_point": acc / n, "tested_per_point": tst / n,
                           "warp_steps": wsteps, "nodes": nodes,

@@ -227,8 +227,9 @@ int pxsne_step_profiled(pxsne_ctx *ctx, int32_t iters, double *group_ms, int32_t
 const char *pxsne_kernel_group_name(int32_t g);
 
 /* Work counters of the Barnes-Hut traversal of the state set by pxsne_init or
- * pxsne_set_state, or of the final state of pxsne_step_profiled (counted by
- * one extra traversal after its timed groups): n_accept =
+ * pxsne_set_state, or, after pxsne_step_profiled, their sums over the states
+ * of all its iterations (each counted by one extra traversal after that
+ * iteration's timed groups): n_accept =
  * accepted (point, cell) pairs (the interactions of Eq. bh_criteria), n_test =
  * tested pairs (accepted + opened + own-pixel), n_warp_steps = warp-level
  * (node, non-empty child) steps, n_nodes = stack entries popped.  Any pointer
@@ -263,6 +264,22 @@ int pxsne_get_knn_time(pxsne_ctx *ctx, double *search_ms);
  * did not, PXSNE_E_ARG on a bad polls.  The context stays usable.
  * Synchronises. */
 int pxsne_test_bounded_wait(pxsne_ctx *ctx, int32_t polls, uint32_t *flags);
+
+/* Measurement (no counterpart in the paper): the peaks that the iteration's
+ * rooflines are taken against, measured on the current device by plain
+ * kernels timed with CUDA events on `stream` (a cudaStream_t, NULL = the
+ * legacy default stream), best of five launches after one warm-up:
+ *   - l2_read_gbs: read bandwidth of 16-byte loads that bypass L1 from a
+ *     buffer of the largest power of two within a quarter of L2 (resident),
+ *     64 passes;
+ *   - fp32_tflops / fp32_packed_tflops: 16 independent chains of FP32 FMAs
+ *     per thread as scalar FMAs / as packed pairs (2 FLOP per FMA);
+ *   - sm_count and l2_bytes: from the device properties.
+ * Any pointer may be NULL (that measurement is skipped).  Allocates and frees
+ * a buffer of at most a quarter of L2.  Synchronises the stream.  Returns
+ * PXSNE_E_CUDA / PXSNE_E_OOM on failure. */
+int pxsne_measure_peaks(void *stream, double *l2_read_gbs, double *fp32_tflops,
+                        double *fp32_packed_tflops, int32_t *sm_count, int64_t *l2_bytes);
 
 /* Total bytes of device memory the context holds. */
 int64_t pxsne_device_bytes(const pxsne_ctx *ctx);
@@ -338,17 +355,21 @@ int pxsne_embed_align(const float *Y, const float *Yref, int64_t n, float *Yout,
  * C = sum_ij p_ij ln(p_ij Z / w_ij), w_ij = 1 / (1 + s0^2 dz_x^2 + s1^2 dz_y^2),
  * enqueued on `stream` (a cudaStream_t; NULL = the legacy default stream) of
  * the current device.  All pointers are device pointers owned by the caller:
- * row_ptr[n+1] int64 and col[nnz] int32 (values in [0, n)) and val[nnz]
- * float32 of P, z[n*2] u32 fixed-point positions; s0, s1 > 0 are the y-units
- * per ulp and Z > 0 the normalisation (e.g. from pxsne_get_forces).  The result
- * is written to out[0] (device) when the stream reaches it.
+ * row_ptr[n+1] int64 (non-decreasing, within col/val: not checked) and
+ * col[nnz] int32 and val[nnz] float32 of P, z[n*2] u32 fixed-point positions;
+ * s0, s1 are the y-units per ulp and Z the normalisation (e.g. from
+ * pxsne_get_forces), each finite and > 0.  The result is written to out[0]
+ * (device) when the stream reaches it.  An entry whose column lies outside
+ * [0, n) is skipped without reading z, and the result is then NaN.
  *
  * No memory is allocated: the reduction's scratch is one file-scope device
  * array of 128 KiB (8192 block partials) that every GPU which loads the
  * library holds until the process exits, so n is limited to
  * pxsne_kl_noalloc_max_rows() = 16,777,216 rows (larger n returns
  * PXSNE_E_ARG).  The first call on a device looks the array's address up on
- * that device (make that first call before any stream capture).  All calls
+ * that device and keeps it (make that first call before any stream capture;
+ * after a cudaDeviceReset of that device the kept address is stale, so do not
+ * call this entry point on that device again in the process).  All calls
  * share the array: calls whose executions overlap on the GPU (other streams,
  * other threads) race and must be serialised by the caller.  Returns
  * PXSNE_E_ARG for bad arguments and PXSNE_E_CUDA if the launch fails; there is

@@ -129,6 +129,8 @@ def load(path: str | None = None):
     L.pxsne_pca.argtypes = [vp, i64, i32, i32, vp, vp, vp, C.c_int, u64]
     L.pxsne_device_bytes.argtypes = [vp]
     L.pxsne_device_bytes.restype = i64
+    L.pxsne_measure_peaks.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.POINTER(i32), C.POINTER(i64)]
     _lib = L
     return L
 
@@ -522,6 +524,21 @@ def pca(X, dout=50, seed=0):
     return out, V, lam
 
 
+def measure_peaks(stream=None):
+    """Measured L2 read bandwidth (GB/s), FP32 FMA rate scalar and packed
+    (TFLOP/s), SM count and L2 size of the current device
+    (``pxsne_measure_peaks``)."""
+    L = load()
+    l2, f1, f2 = C.c_double(), C.c_double(), C.c_double()
+    sms, l2b = C.c_int32(), C.c_int64()
+    rc = L.pxsne_measure_peaks(stream, C.byref(l2), C.byref(f1), C.byref(f2), C.byref(sms),
+                               C.byref(l2b))
+    if rc != PXSNE_OK:
+        raise PxsneError(rc, "pxsne_measure_peaks")
+    return {"l2_read_gbs": l2.value, "fp32_tflops": f1.value, "fp32_packed_tflops": f2.value,
+            "sm_count": sms.value, "l2_bytes": l2b.value}
+
+
 EXPORTED = ["pxsne_default_params", "pxsne_create", "pxsne_destroy", "pxsne_last_error",
             "pxsne_affinities", "pxsne_init", "pxsne_step", "pxsne_kl", "pxsne_get_Y",
             "pxsne_sync", "pxsne_get_sizes", "pxsne_get_P", "pxsne_set_P", "pxsne_get_knn",
@@ -533,4 +550,4 @@ EXPORTED = ["pxsne_default_params", "pxsne_create", "pxsne_destroy", "pxsne_last
             "pxsne_mlp_destroy", "pxsne_mlp_last_error", "pxsne_mlp_num_params",
             "pxsne_mlp_set_params", "pxsne_mlp_get_params", "pxsne_mlp_loss_grad",
             "pxsne_mlp_train", "pxsne_mlp_predict", "pxsne_embed_align",
-            "pxsne_nbr_precision", "pxsne_pca"]
+            "pxsne_nbr_precision", "pxsne_pca", "pxsne_measure_peaks"]

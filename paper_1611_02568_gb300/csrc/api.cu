@@ -537,6 +537,7 @@ int pxsne_step_profiled(pxsne_ctx *c, int32_t iters, double *group_ms, int32_t n
     std::vector<cudaEvent_t> &ev = evs.v;
     for (auto &e : ev) CK(c, cudaEventCreate(&e));
     cudaEvent_t *t0 = &ev[ev.size() - 2], *t1 = &ev[ev.size() - 1];
+    CK(c, cudaMemsetAsync(c->sc->tot, 0, sizeof(c->sc->tot), c->stream));
     CK(c, cudaEventRecord(*t0, c->stream));
     for (int32_t k = 0; k < iters; k++) {
         cudaEvent_t *m = &ev[(size_t)k * (KG_COUNT + 1)];
@@ -545,11 +546,16 @@ int pxsne_step_profiled(pxsne_ctx *c, int32_t iters, double *group_ms, int32_t n
         rc = one_iteration(c, m);
         if (rc) break;
         c->since_relabel++;
+        // work counters of this iteration's state: one more traversal after
+        // the iteration's last mark, outside the timed groups
+        CK(c, launch_count_traversal(c));
+        CK(c, launch_accumulate_counters(c));
     }
     if (!rc) {
         CK(c, cudaEventRecord(*t1, c->stream));
-        // work counters of the final state, outside the timed groups
-        CK(c, launch_count_traversal(c));
+        // the sums over the run replace the last state's counters
+        CK(c, cudaMemcpyAsync(&c->sc->n_accept, c->sc->tot, sizeof(c->sc->tot),
+                              cudaMemcpyDeviceToDevice, c->stream));
         CK(c, cudaEventSynchronize(*t1));
         for (int g = 0; g < KG_COUNT; g++) group_ms[g] = 0.0;
         for (int32_t k = 0; k < iters; k++) {

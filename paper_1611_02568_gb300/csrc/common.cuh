@@ -41,6 +41,7 @@ struct DevScalars {
     u64 n_test;          // (point, cell) pairs tested by the last traversal
     u64 n_steps;         // warp-level (node, non-empty child) steps of the last traversal
     u64 n_nodes;         // stack entries popped by the last traversal
+    u64 tot[4];          // sums of the four counters above over a profiled run
     u64 knn_exact;       // exact distances computed by the last neighbour search
     u64 knn_insert;      // list insertions of the last neighbour search
     u64 knn_skip;        // (query tile, candidate tile) pairs it skipped by the tile bound
@@ -213,6 +214,8 @@ cudaError_t launch_snap(pxsne_ctx *c, bool rescale, cudaEvent_t *marks = nullptr
 cudaError_t launch_pyramid(pxsne_ctx *c, bool rescale, cudaEvent_t *marks = nullptr);
 cudaError_t launch_attract(pxsne_ctx *c, cudaStream_t st);
 cudaError_t launch_count_traversal(pxsne_ctx *c);
+// tot[] += the counters of the last counting traversal (one thread)
+cudaError_t launch_accumulate_counters(pxsne_ctx *c);
 // Renumber P's rows and columns in the Morton order of the last tree (perm)
 // into rp2/col2/val2 and refresh aperm, ainv and zp.
 constexpr int kRelabelEvery = 100;

@@ -465,6 +465,18 @@ cudaError_t launch_relabel(pxsne_ctx *c, cudaStream_t st) {
 // values.
 cudaError_t launch_count_traversal(pxsne_ctx *c) { return traverse(c, c->stream, true); }
 
+__global__ void k_accumulate_counters(DevScalars *sc) {
+    sc->tot[0] += sc->n_accept;
+    sc->tot[1] += sc->n_test;
+    sc->tot[2] += sc->n_steps;
+    sc->tot[3] += sc->n_nodes;
+}
+
+cudaError_t launch_accumulate_counters(pxsne_ctx *c) {
+    k_accumulate_counters<<<1, 1, 0, c->stream>>>(c->sc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_traverse_zsum(pxsne_ctx *c) {
     cudaError_t e = traverse(c, c->stream, false);
     if (e) return e;

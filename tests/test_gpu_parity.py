@@ -198,6 +198,7 @@ def check_knn_rows(X, rows, idx_o, d2_o, idx, d2, tol=2e-5):
         dk = d2_o[q, -1]
         must = set(idx_o[q][d2_o[q] < dk * (1 - tol)])
         got = set(idx[i])
+        assert len(got) == idx.shape[1], i       # k distinct neighbours
         assert must <= got, i
         dd = ((X[idx[i]].astype(np.float64) - X[i].astype(np.float64)) ** 2).sum(1)
         assert np.all(dd <= dk * (1 + tol)), i
@@ -387,12 +388,19 @@ def test_pca_matches_oracle(px):
 
 
 def test_profiled_run_and_work_counters(px, gauss):
-    """pxsne_step_profiled times the iteration's own kernels and counts the
-    final state's traversal afterwards: its counters equal those of the same
-    state set again, and the accepted pairs equal the oracle's count."""
+    """pxsne_step_profiled times the iteration's own kernels and counts each
+    iteration's state by one more traversal afterwards: its counters are the
+    sums over those states, equal to the counters of the same states set
+    again one by one, and the accepted pairs equal the oracle's count."""
     X, P, Y0, _ = gauss
-    with make_ctx(px, L=9) as ctx:
+    with make_ctx(px, L=9) as ctx, make_ctx(px, L=9) as ref:
         ctx.set_P(P.row_ptr, P.col, P.val.astype(np.float32))
+        ref.set_P(P.row_ptr, P.col, P.val.astype(np.float32))
+        ctx.init(Y0)
+        states = []
+        for _ in range(7):
+            ctx.step(1)
+            states.append(ctx.get_state())
         ctx.init(Y0)
         groups, total = ctx.step_profiled(7)
         assert list(groups) == ["k_relabel", "k_update", "k_snap_hist", "k_pyr_pass",
@@ -402,16 +410,23 @@ def test_profiled_run_and_work_counters(px, gauss):
         c1 = ctx.counters()
         F1 = ctx.get_forces()
         z, s, u, g, t = ctx.get_state()
-        ctx.set_state(z, s, u, g, t)
-        c2 = ctx.counters()
+        for a, b in zip((z, s, u, g, t), states[-1]):
+            assert np.array_equal(a, b)
+        sums = np.zeros(4, np.int64)
+        acc_oracle = 0
+        for st in states:
+            ref.set_state(*st)
+            sums += np.array(ref.counters(), np.int64)
+            _, _, acc = oracle.bh_repulsion(st[0], st[1], 9, 0.5)
+            acc_oracle += int(acc.sum())
         # per-point counts are the same; warp steps and nodes depend on how
         # points within a pixel are grouped into warps, which follows the
         # order of the previous tree (identity order after set_state)
-        assert c2[:2] == c1[:2]
-        assert c2[2] == pytest.approx(c1[2], rel=0.01) and c2[3] == pytest.approx(c1[3], rel=0.01)
-        F2 = ctx.get_forces()
+        assert tuple(sums[:2]) == c1[:2]
+        assert c1[2] == pytest.approx(sums[2], rel=0.01)
+        assert c1[3] == pytest.approx(sums[3], rel=0.01)
+        F2 = ref.get_forces()
         for a, b in zip(F1[:3], F2[:3]):
             assert np.array_equal(a, b)
-    _, _, acc = oracle.bh_repulsion(z, s, 9, 0.5)
-    assert c1[0] == pytest.approx(int(acc.sum()), rel=1e-4)
+    assert c1[0] == pytest.approx(acc_oracle, rel=1e-4)
     assert c1[1] >= c1[0] and c1[2] > 0 and c1[3] > 0
