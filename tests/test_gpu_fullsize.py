@@ -59,6 +59,7 @@ def test_knn_sampled_rows(run):
         assert np.all(ex <= tau * (1 + 2e-5)), r
         # every true neighbour clearly inside the k-th distance is returned
         must = set(idx_o[a][d2_o[a] < tau * (1 - 2e-5)].tolist())
+        assert len(set(idx[r].tolist())) == K, r      # k distinct neighbours
         assert must <= set(idx[r].tolist()), r
         assert r not in set(idx[r].tolist())
         np.testing.assert_allclose(d2[r], ex, rtol=1e-5)
@@ -79,6 +80,55 @@ def test_P_properties(run):
             p = np.searchsorted(cj, r)
             assert p < cj.size and cj[p] == r
             assert val[rp[j] + p] == pytest.approx(v, rel=1e-6)
+
+
+def test_P_values_and_entropy_sampled_rows(run):
+    """P of sampled rows against the oracle's (Sec. 3.2-3.3): each GPU row's
+    entropy at ln u from its own beta and distances, beta within the
+    bisection's tolerance of the oracle's, and every symmetric value
+    p_ij = (p_j|i + p_i|j) / 2n of a clear neighbour j within 2e-3 of the
+    oracle's, with p_i|j from the oracle's own lists of the rows j."""
+    X, ctx, P = run
+    u, tol = 30.0, 2e-5
+    rows = sample_rows(5, 12)
+    idx_o, d2_o = oracle.knn(X, K, rows=rows)
+    pc_o, beta_o, _, bad = oracle.perplexity(d2_o, u)
+    assert bad == 0
+    idx, d2, beta = ctx.get_knn()
+    d2r = d2[rows].astype(np.float64)
+    e = np.exp(-beta[rows, None].astype(np.float64) * (d2r - d2r[:, :1]))
+    p = e / e.sum(1, keepdims=True)
+    H = -(p * np.log(p)).sum(1)
+    assert np.abs(H - np.log(u)).max() < 1e-4
+    np.testing.assert_allclose(beta[rows], beta_o, rtol=2e-3)
+    # the rows j of the sampled rows' clear neighbours, exactly
+    clear = [idx_o[a][d2_o[a] < d2_o[a, K - 1] * (1 - tol)] for a in range(len(rows))]
+    J = np.unique(np.concatenate(clear))
+    idx_j, d2_j = oracle.knn(X, K, rows=J)
+    pc_j, _, _, bad_j = oracle.perplexity(d2_j, u)
+    assert bad_j == 0
+    where = {int(j): q for q, j in enumerate(J)}
+    rp, col, val = P.row_ptr, P.col, P.val
+    checked = 0
+    for a, i in enumerate(rows):
+        cs, vs = col[rp[i]:rp[i + 1]], val[rp[i]:rp[i + 1]]
+        for b, j in enumerate(idx_o[a]):
+            if d2_o[a, b] >= d2_o[a, K - 1] * (1 - tol):
+                continue
+            q = where[int(j)]
+            dj = d2_j[q]
+            dij = d2_o[a, b]
+            if abs(dij - dj[K - 1]) <= tol * dj[K - 1]:
+                continue                      # i on the edge of j's list: either is right
+            pij = pc_o[a, b]
+            hit = np.nonzero(idx_j[q] == i)[0]
+            pji = pc_j[q, hit[0]] if hit.size else 0.0
+            ref = (pij + pji) / (2 * N)
+            at = np.searchsorted(cs, j)
+            assert at < cs.size and cs[at] == j, (i, j)
+            assert vs[at] == pytest.approx(ref, rel=2e-3), (i, j)
+            checked += 1
+    assert checked > 0.9 * len(rows) * K
 
 
 def check_state(ctx, P, rows, L=L, theta=THETA):
@@ -131,6 +181,7 @@ def test_scale_workload_shape_at_2M():
             ex = ((x[idx[r]] - x[r]) ** 2).sum(1)
             assert np.all(ex <= tau * (1 + 2e-5)), r
             must = set(idx_o[a][d2_o[a] < tau * (1 - 2e-5)].tolist())
+            assert len(set(idx[r].tolist())) == K, r
             assert must <= set(idx[r].tolist()), r
         ctx.init(datagen.init_y0(0, n))
         ctx.step(60)

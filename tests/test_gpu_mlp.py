@@ -3,7 +3,7 @@
 The GPU uses BF16 weights and activations as tensor-core operands with FP32
 accumulation; the oracle runs the same network in FP64 on the same (BF16-
 representable) weights and inputs.  Bars: loss within 1 %, each gradient
-tensor within 3 % relative L2, outputs within 1 % relative L2."""
+tensor within 1 % relative L2, outputs within 1 % relative L2."""
 import numpy as np
 import pytest
 
@@ -54,8 +54,11 @@ def test_mlp_loss_and_gradient_match_oracle(px):
     assert abs(loss - loss_o) <= 1e-2 * loss_o
     go = oracle.MLP.from_flat(g_o, d, H)
     gg = oracle.MLP.from_flat(g.astype(np.float64), d, H)
-    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
-        assert rel(getattr(gg, name), getattr(go, name)) <= 3e-2, name
+    errs = {name: rel(getattr(gg, name), getattr(go, name))
+            for name in ("W1", "b1", "W2", "b2", "W3", "b3")}
+    print("MLP gradient relative L2 errors", errs, "loss", loss, loss_o)
+    for name, e in errs.items():
+        assert e <= 1e-2, name
 
 
 def test_mlp_predict_multibatch_and_padded_width(px):

@@ -910,3 +910,24 @@ def test_stored_kl_target_matches_the_oracle():
     assert stored["kl"] == pytest.approx(fresh["kl"], rel=1e-9)
     assert {k: v for k, v in stored.items() if k != "kl"} == \
         {k: v for k, v in fresh.items() if k != "kl"}
+
+
+def test_stored_large_kl_targets_describe_their_workloads():
+    """The stored oracle KL of the larger workloads (hours of CPU to recompute
+    at n = 1M, minutes at 70k and 200k) carry the workload the script names,
+    a KL that falls along the schedule, and a P whose size fits k = 90."""
+    sys.path.insert(0, GOLDEN)
+    import make_kl_target
+    for name, (gen, n, L, iters, dpca) in make_kl_target.WORKLOADS.items():
+        path = os.path.join(GOLDEN, f"kl_target_{name}.json")
+        if name == "gauss10" or not os.path.exists(path):
+            continue
+        with open(path) as f:
+            g = json.load(f)
+        assert (g["workload"], g["n"], g["log2_r"], g["iterations"], g["pca"]) == \
+            (gen, n, L, iters, dpca)
+        assert g["k"] == 90 and g["perplexity"] == 30.0 and g["theta"] == 0.5
+        assert g["unconverged_rows"] == 0
+        q = g["kl_quarters"]
+        assert len(q) == 4 and q[-1] == g["kl"] and all(a > b > 0 for a, b in zip(q, q[1:]))
+        assert 90 * n <= g["nnz"] <= 2 * 90 * n
