@@ -157,16 +157,21 @@ def measured_peaks():
 RELABEL_EVERY = 100  # the library refreshes the attraction's relabelled P this often
 
 
-def group_bytes(n, nnz, L):
+def group_bytes(n, nnz, L, nonempty=None):
+    """Bytes each kernel group must move per launch.  `nonempty`: cells of
+    the tree holding at least one point (only their 16-byte records are
+    written; every cell's count is), all cells when not given."""
     leaves = 4 ** L
     cells = (4 ** (L + 1) - 1) // 3
+    nonempty = cells if nonempty is None else nonempty
     return {
         # per iteration on average: P read and written once per relabel, plus
         # the maps, row lengths, scan and positions
         "k_relabel": (nnz * 16 + n * (4 + 8 + 4 + 4 + 4 + 8 + 8 + 8 + 8)) / RELABEL_EVERY,
         "k_update": n * (8 + 8 + 8 + 8 + 8 + 8 + 8 + 16),      # z,Frep,Fattr,u,gains r; u,gains w; zhat w
         "k_snap_hist": leaves * 20 + n * (4 + 16 + 8 + 4 + 4 + 8),  # memset; perm,zhat,ainv r; z,rank,zp w
-        "k_pyr_pass": leaves * (20 + 4) + cells * 20,          # leaf sums r, leaf_start w, rec + recn w
+        "k_pyr_pass": leaves * (20 + 4) + cells * 4 + nonempty * 16,  # leaf sums r, leaf_start w,
+                                                               # recn w, rec of non-empty cells w
         "k_perm_scatter": n * (8 + 4 + 4 + 4),
         "k_bh_traverse": n * (4 + 8 + 8 + 4) + cells * 20,    # perm, z r; Frep, Zi w; rec + recn r
         "k_attract": nnz * 8 + (n + 1) * 8 + n * (8 + 4 + 8),
@@ -610,8 +615,11 @@ def run_gpu(args):
     groups, prof_total = ctx.step_profiled(args.steps)
     # (the traversal's work counters: sums over the K profiled iterations)
     acc, tst, wsteps, nodes = ctx.counters()
+    lvc = ctx.level_counters()
     peaks, peak_kind = measured_peaks()
-    gb = group_bytes(n, nnz, W["log2_r"])
+    # non-empty cells of the final state (only their records are written)
+    nonempty = sum(int(np.count_nonzero(ctx.get_tree(l)[0])) for l in range(W["log2_r"] + 1))
+    gb = group_bytes(n, nnz, W["log2_r"], nonempty)
     traffic = TRAFFIC_BYTES.get((W["workload"], n), {})
     top = max(groups, key=groups.get)
     avg_ms = {g: v / args.steps for g, v in groups.items()}
@@ -748,9 +756,15 @@ def run_gpu(args):
                                               "timed_iterations": f"t = 0..{args.steps - 1}"},
             "roofline": roof, "kernels": kernels, "measured_peaks": mpeaks,
             "traversal": {"accepted_pairs": acc, "tested_pairs": tst,
-                          "accepted_per_point": acc / n, "tested_per_point": tst / n,
+                          "accepted_per_point": acc / n / args.steps,
+                          "tested_per_point": tst / n / args.steps,
                           "warp_steps": wsteps, "nodes": nodes,
-                          "lanes_per_step": tst / wsteps if wsteps else None},
+                          "lanes_per_step": tst / wsteps if wsteps else None,
+                          "iterations": args.steps,
+                          "by_level": {str(l): {"tested_per_point": int(lvc[l, 0]) / n / args.steps,
+                                                "accepted_per_point": int(lvc[l, 1]) / n / args.steps,
+                                                "lanes_per_step": int(lvc[l, 0]) / int(lvc[l, 2])}
+                                       for l in range(1, lvc.shape[0]) if lvc[l, 2]}},
             "profiled_total_ms": prof_total, "p_construction_s": p_seconds, "knn": knn,
             "along_schedule": along,
             "kl_after_timed": kl_after,

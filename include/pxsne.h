@@ -237,6 +237,15 @@ const char *pxsne_kernel_group_name(int32_t g);
 int pxsne_get_counters(pxsne_ctx *ctx, uint64_t *n_accept, uint64_t *n_test,
                        uint64_t *n_warp_steps, uint64_t *n_nodes);
 
+/* The traversal's work counters by level l of the tested cell (1 = the
+ * root's children .. L = pixels): counts[3 l + 0] tested and counts[3 l + 1]
+ * accepted (point, cell) pairs, counts[3 l + 2] warp-level steps, over the
+ * same states as pxsne_get_counters (the state of the last pxsne_init /
+ * pxsne_set_state, or the sum over the iterations of the last
+ * pxsne_step_profiled).  levels >= L + 1 entries of three; the rest are
+ * zeroed.  Synchronises. */
+int pxsne_get_level_counters(pxsne_ctx *ctx, uint64_t *counts, int32_t levels);
+
 /* Work counters of the last neighbour search: exact FP32 distances computed
  * and list insertions over all rows (tensor-core search only; 0 otherwise),
  * and the search used (1 tensor cores, 0 FP32 CUDA cores, -1 none).

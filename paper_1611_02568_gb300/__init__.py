@@ -129,6 +129,7 @@ def load(path: str | None = None):
     L.pxsne_pca.argtypes = [vp, i64, i32, i32, vp, vp, vp, C.c_int, u64]
     L.pxsne_device_bytes.argtypes = [vp]
     L.pxsne_device_bytes.restype = i64
+    L.pxsne_get_level_counters.argtypes = [vp, C.POINTER(u64), i32]
     L.pxsne_measure_peaks.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.POINTER(i32), C.POINTER(i64)]
     _lib = L
@@ -357,6 +358,14 @@ class Context:
                                            C.byref(nd)))
         return a.value, t.value, w.value, nd.value
 
+    def level_counters(self):
+        """(tested, accepted, warp steps) by level of the tested cell, rows
+        0 .. L (``pxsne_get_level_counters``)."""
+        lv = self.params.log2_r + 1
+        buf = (C.c_uint64 * (3 * lv))()
+        self._ck(self.L.pxsne_get_level_counters(self.h, buf, lv))
+        return np.array(buf[:], dtype=np.int64).reshape(lv, 3)
+
     def nbr_precision(self, k=10, knn_hd=None, per_point=False):
         """Eq. nei_prec of the current embedding (high-D lists from the last
         affinities call unless knn_hd [n x kh] is given)."""
@@ -550,4 +559,5 @@ EXPORTED = ["pxsne_default_params", "pxsne_create", "pxsne_destroy", "pxsne_last
             "pxsne_mlp_destroy", "pxsne_mlp_last_error", "pxsne_mlp_num_params",
             "pxsne_mlp_set_params", "pxsne_mlp_get_params", "pxsne_mlp_loss_grad",
             "pxsne_mlp_train", "pxsne_mlp_predict", "pxsne_embed_align",
-            "pxsne_nbr_precision", "pxsne_pca", "pxsne_measure_peaks"]
+            "pxsne_nbr_precision", "pxsne_pca", "pxsne_measure_peaks",
+            "pxsne_get_level_counters"]

@@ -130,6 +130,9 @@ int ensure_state(pxsne_ctx *c) {
     CK(c, dalloc(c, &c->leaf_sy, leaves));
     CK(c, dalloc(c, &c->rec, cells));
     CK(c, dalloc(c, &c->recn, cells));
+    // records of empty cells are never written by the pyramid (nor read by
+    // the traversal): they start as zeros
+    CK(c, cudaMemsetAsync(c->rec, 0, (size_t)cells * sizeof(float4), c->stream));
     CK(c, dalloc(c, &c->leaf_start, leaves));
     CK(c, dalloc(c, &c->blk_off, lvl));
     for (int k = 0; k < 2; k++) {
@@ -538,6 +541,7 @@ int pxsne_step_profiled(pxsne_ctx *c, int32_t iters, double *group_ms, int32_t n
     for (auto &e : ev) CK(c, cudaEventCreate(&e));
     cudaEvent_t *t0 = &ev[ev.size() - 2], *t1 = &ev[ev.size() - 1];
     CK(c, cudaMemsetAsync(c->sc->tot, 0, sizeof(c->sc->tot), c->stream));
+    CK(c, cudaMemsetAsync(c->sc->lvl, 0, sizeof(c->sc->lvl), c->stream));
     CK(c, cudaEventRecord(*t0, c->stream));
     for (int32_t k = 0; k < iters; k++) {
         cudaEvent_t *m = &ev[(size_t)k * (KG_COUNT + 1)];
@@ -805,6 +809,20 @@ int pxsne_get_counters(pxsne_ctx *c, uint64_t *n_accept, uint64_t *n_test,
     if (n_test) *n_test = h.n_test;
     if (n_warp_steps) *n_warp_steps = h.n_steps;
     if (n_nodes) *n_nodes = h.n_nodes;
+    return PXSNE_OK;
+}
+
+int pxsne_get_level_counters(pxsne_ctx *c, uint64_t *counts, int32_t levels) {
+    int rc = need_state(c);
+    if (rc) return rc;
+    if (!counts || levels < c->L + 1)
+        return fail(c, PXSNE_E_ARG, "need room for %d levels", c->L + 1);
+    DevScalars h;
+    CK(c, cudaMemcpyAsync(&h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
+    rc = check_device(c, nullptr);
+    if (rc) return rc;
+    for (int l = 0; l < levels; l++)
+        for (int q = 0; q < 3; q++) counts[3 * l + q] = l <= c->L ? h.lvl[l][q] : 0ull;
     return PXSNE_OK;
 }
 

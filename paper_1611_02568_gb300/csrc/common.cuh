@@ -42,6 +42,8 @@ struct DevScalars {
     u64 n_steps;         // warp-level (node, non-empty child) steps of the last traversal
     u64 n_nodes;         // stack entries popped by the last traversal
     u64 tot[4];          // sums of the four counters above over a profiled run
+    u64 lvl[kMaxL + 2][3];  // (tested, accepted, warp steps) by child level, summed
+                            // over the counting traversals since the last reset
     u64 knn_exact;       // exact distances computed by the last neighbour search
     u64 knn_insert;      // list insertions of the last neighbour search
     u64 knn_skip;        // (query tile, candidate tile) pairs it skipped by the tile bound
@@ -56,6 +58,8 @@ struct DevScalars {
 //        so that a point's offset z - com is (z_hi - c_hi) + (z_lo - c_lo)
 //        with one rounding;
 //   recn float N_c (exact below 2^24).
+// The record of an empty cell (N_c = 0) is not written each iteration; it
+// keeps an earlier value and is never read.
 // rec_offset pads level 0 to four slots so that every group of four siblings
 // starts on a 16-byte boundary.
 __host__ __device__ inline int64_t rec_offset(int l) {

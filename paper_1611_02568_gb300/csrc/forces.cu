@@ -60,6 +60,21 @@ __device__ __forceinline__ void cell_offset2(float4 r, float2 zhx, float2 zlx, f
     }
 }
 
+// COUNT: one warp step's (tested, accepted) pairs and the step itself, added
+// to the CTA's counters of the child's level by lane 0.
+__device__ __forceinline__ void count_level(u64 *lv, bool me0, bool me1, bool acc0, bool acc1,
+                                            int lane) {
+    const unsigned t = __popc(__ballot_sync(0xffffffffu, me0)) +
+                       __popc(__ballot_sync(0xffffffffu, me1));
+    const unsigned a = __popc(__ballot_sync(0xffffffffu, acc0)) +
+                       __popc(__ballot_sync(0xffffffffu, acc1));
+    if (lane == 0) {
+        atomicAdd(&lv[0], (u64)t);
+        atomicAdd(&lv[1], (u64)a);
+        atomicAdd(&lv[2], 1ull);
+    }
+}
+
 struct __align__(16) TravEntry {
     uint32_t node, m0, m1, pad;
 };
@@ -74,9 +89,12 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
     __shared__ TravEntry s_stk[kTravWarps][kTravStack];
     __shared__ float s_T[kMaxL + 2];
     __shared__ int s_off[kMaxL + 2];
+    // COUNT: (tested, accepted, warp steps) by level of the child
+    __shared__ u64 s_lv[COUNT ? kMaxL + 2 : 1][3];
     if (threadIdx.x < kMaxL + 2) {
         s_T[threadIdx.x] = sc->T[threadIdx.x];
         s_off[threadIdx.x] = threadIdx.x <= L ? (int)rec_offset(threadIdx.x) : 0;
+        if (COUNT) s_lv[threadIdx.x][0] = s_lv[threadIdx.x][1] = s_lv[threadIdx.x][2] = 0ull;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -86,7 +104,8 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
     const bool valid0 = idx0 < n, valid1 = idx1 < n;
     const unsigned act0 = __ballot_sync(0xffffffffu, valid0);
     const unsigned act1 = __ballot_sync(0xffffffffu, valid1);
-    if (act0 == 0u) return;
+    // (a counting traversal keeps every warp to the CTA's final barrier)
+    if (!COUNT && act0 == 0u) return;
     const uint32_t i0 = valid0 ? perm[idx0] : 0u, i1 = valid1 ? perm[idx1] : 0u;
     const uint2 z0 = z[i0], z1 = z[i1];
     const uint32_t mi0 = morton2(z0.x >> F, z0.y >> F), mi1 = morton2(z1.x >> F, z1.y >> F);
@@ -102,13 +121,18 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
     TravEntry *stk = s_stk[w];
     // The root contains every point: start with its four children.
     if (lane == 0) stk[0] = TravEntry{0u, act0, act1, 0u};  // (level 0 << 28) | morton 0
-    int sp = 1;
+    int sp = act0 != 0u ? 1 : 0;
     __syncwarp();
     bool overflow = false;
     while (sp > 0) {
         sp--;
-        const TravEntry top = stk[sp];
+        TravEntry top = stk[sp];
         __syncwarp();
+        // the entry is the same for every lane: taken from lane 0, so that
+        // the node, its level and addresses are known to be warp-uniform
+        top.node = __shfl_sync(0xffffffffu, top.node, 0);
+        top.m0 = __shfl_sync(0xffffffffu, top.m0, 0);
+        top.m1 = __shfl_sync(0xffffffffu, top.m1, 0);
         const uint32_t node = top.node;
         const int lc = (int)(node >> 28) + 1;  // level of the children
         const uint32_t m0 = (node & 0x0fffffffu) << 2;
@@ -175,6 +199,7 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
                 if (COUNT) {
                     n_tst += (me0 ? 1u : 0u) + (me1 ? 1u : 0u);
                     n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
+                    count_level(s_lv[lc], me0, me1, acc0, acc1, lane);
                 }
                 const float2 w1 = add2(bc2(1.0f), d2);
                 const float2 q = make_float2(rcp1(w1.x), rcp1(w1.y));
@@ -213,6 +238,7 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
                 if (COUNT) {
                     n_tst += (me0 ? 1u : 0u) + (me1 ? 1u : 0u);
                     n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
+                    count_level(s_lv[lc], me0, me1, acc0, acc1, lane);
                 }
                 const float2 w1 = add2(bc2(1.0f), d2);
                 const float2 q = make_float2(rcp1(w1.x), rcp1(w1.y));
@@ -241,6 +267,11 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
     }
     if (overflow && lane == 0) atomicOr(&sc->err, (unsigned)PXSNE_DEVERR_STACK);
     if (COUNT) {
+        __syncthreads();
+        if (threadIdx.x < (L + 1) * 3) {
+            const int l = threadIdx.x / 3, q = threadIdx.x % 3;
+            if (s_lv[l][q]) atomicAdd(&sc->lvl[l][q], s_lv[l][q]);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             n_acc += __shfl_xor_sync(0xffffffffu, n_acc, o);
@@ -488,8 +519,10 @@ cudaError_t launch_forces(pxsne_ctx *c, cudaEvent_t *marks) {
     cudaStream_t st = c->stream;
     cudaError_t e;
     if (marks && (e = cudaEventRecord(marks[KG_TRAVERSE], st))) return e;
-    // the initial state's traversal keeps the work counters; a timed one is
-    // the kernel of the iteration itself
+    // the initial state's traversal keeps the work counters (the level
+    // counters restart with it); a timed one is the kernel of the iteration
+    // itself
+    if (!marks && (e = cudaMemsetAsync(c->sc->lvl, 0, sizeof(c->sc->lvl), st))) return e;
     if ((e = traverse(c, st, marks == nullptr))) return e;
     if (marks && (e = cudaEventRecord(marks[KG_ATTRACT], st))) return e;
     if ((e = launch_attract(c, st))) return e;

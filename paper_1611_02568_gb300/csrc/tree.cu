@@ -285,7 +285,8 @@ __device__ __forceinline__ u64 shfl_xor_u64(u64 v, int o) {
 
 __device__ __forceinline__ void put_record(float4 *rec, float *recn, int l, uint32_t m,
                                            uint32_t N, u64 X, u64 Y) {
-    if (rec != nullptr) rec[rec_offset(l) + m] = make_record(N, X, Y, l, m);  // NULL: counts only
+    // NULL: counts only; an empty cell's record is never read, so not written
+    if (rec != nullptr && N != 0u) rec[rec_offset(l) + m] = make_record(N, X, Y, l, m);
     recn[rec_offset(l) + m] = (float)N;
 }
 
@@ -388,10 +389,11 @@ __global__ void __launch_bounds__(256)
         y01 = reinterpret_cast<const ulonglong2 *>(in_sy)[cell0 >> 1];
         y23 = reinterpret_cast<const ulonglong2 *>(in_sy)[(cell0 >> 1) + 1];
         float4 *rl = rec + rec_offset(h) + cell0;
-        rl[0] = make_record(c4.x, x01.x, y01.x, h, cell0);
-        rl[1] = make_record(c4.y, x01.y, y01.y, h, cell0 + 1u);
-        rl[2] = make_record(c4.z, x23.x, y23.x, h, cell0 + 2u);
-        rl[3] = make_record(c4.w, x23.y, y23.y, h, cell0 + 3u);
+        // (an empty cell's record is never read: not written)
+        if (c4.x) rl[0] = make_record(c4.x, x01.x, y01.x, h, cell0);
+        if (c4.y) rl[1] = make_record(c4.y, x01.y, y01.y, h, cell0 + 1u);
+        if (c4.z) rl[2] = make_record(c4.z, x23.x, y23.x, h, cell0 + 2u);
+        if (c4.w) rl[3] = make_record(c4.w, x23.y, y23.y, h, cell0 + 3u);
     }
     reinterpret_cast<float4 *>(recn + rec_offset(h))[cell0 >> 2] =
         make_float4((float)c4.x, (float)c4.y, (float)c4.z, (float)c4.w);

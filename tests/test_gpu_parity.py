@@ -408,6 +408,10 @@ def test_profiled_run_and_work_counters(px, gauss):
         assert all(v >= 0.0 for v in groups.values()) and groups["k_bh_traverse"] > 0.0
         assert sum(groups.values()) <= total * 1.001 + 1e-3
         c1 = ctx.counters()
+        lv = ctx.level_counters()
+        # by level of the tested cell: they add up to the totals
+        assert (int(lv[:, 1].sum()), int(lv[:, 0].sum()), int(lv[:, 2].sum())) == c1[:3]
+        assert lv[0].sum() == 0 and lv[9, 0] > 0
         F1 = ctx.get_forces()
         z, s, u, g, t = ctx.get_state()
         for a, b in zip((z, s, u, g, t), states[-1]):
