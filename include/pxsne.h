@@ -129,6 +129,38 @@ int pxsne_init(pxsne_ctx *ctx, const float *Y0, int y_on_device, uint64_t seed);
  * Returns enqueue errors only. */
 int pxsne_step(pxsne_ctx *ctx, int32_t iters);
 
+/* Checkpoint and resume (Sec. 5 runs the method for a fixed number of
+ * iterations; a long run can be stopped and continued).  pxsne_save writes P
+ * (as CSR), the state (z, s, u, gains, t) and the parameters and schedule of
+ * ctx to one file at `path` (written under path + ".tmp", then renamed over
+ * path); the iteration needs nothing else, so a run continued from the file
+ * reproduces the one that wrote it bit for bit.  The neighbour lists of the
+ * last pxsne_affinities are not kept (pxsne_nbr_precision of a loaded context
+ * needs the caller's lists).  Synchronises.  Returns PXSNE_E_STATE before
+ * pxsne_init, PXSNE_E_ARG if the file cannot be written.
+ *
+ * File layout (byte order of the writing host, little-endian on every
+ * supported one): a 128-byte header {char magic[8] = "PXSNECK\0"; uint32
+ * version = 1; uint32 header bytes = 128; pxsne_params (52 bytes); uint32 0;
+ * int64 n, nnz; int32 t, 0; double s[2]; uint64 payload bytes; uint64
+ * checksum}, then row_ptr[n+1] int64, col[nnz] int32, val[nnz] float32,
+ * z[2n] uint32, u[2n] float32, gains[2n] float32.  The checksum is FNV-1a
+ * (64-bit offset basis and prime) over the payload taken as little-endian
+ * 64-bit words, the last one zero-padded. */
+int pxsne_save(pxsne_ctx *ctx, const char *path);
+
+/* Create a context from a file written by pxsne_save, on the current device
+ * (stream as in pxsne_create), with the file's parameters, P and state.  The
+ * header, sizes and checksum are checked before any device work: a bad or
+ * truncated file returns PXSNE_E_ARG (PXSNE_E_UNSUPPORTED for another
+ * version) with the reason in pxsne_last_error(NULL); *out stays NULL on
+ * every failure. */
+int pxsne_load(pxsne_ctx **out, const char *path, void *stream);
+
+/* The parameters and schedule ctx runs with (after pxsne_set_schedule or
+ * pxsne_load). */
+int pxsne_get_params(const pxsne_ctx *ctx, pxsne_params *p);
+
 /* Change the optimiser schedule of an existing context (learning rate,
  * exaggeration and its length, momenta and switch, minimum gain) without
  * rebuilding P; e.g. refining a warm start without exaggeration.  Takes effect
@@ -289,6 +321,15 @@ int pxsne_test_bounded_wait(pxsne_ctx *ctx, int32_t polls, uint32_t *flags);
  * PXSNE_E_CUDA / PXSNE_E_OOM on failure. */
 int pxsne_measure_peaks(void *stream, double *l2_read_gbs, double *fp32_tflops,
                         double *fp32_packed_tflops, int32_t *sm_count, int64_t *l2_bytes);
+
+/* Test hook of the traversal's stack guard (no counterpart in the paper):
+ * the Barnes-Hut traversal keeps at most `entries` (4 <= entries <= 48) nodes
+ * on a warp's stack, the room a screen of depth L needs being 3 L - 2
+ * entries; 0 restores the full stack.  With too little room a warp stops
+ * its walk, sets PXSNE_DEVERR_STACK and writes the forces gathered so far,
+ * and the next synchronising call returns PXSNE_E_DEVICE; the context stays
+ * usable.  Takes effect from the next traversal.  Synchronises. */
+int pxsne_test_stack_limit(pxsne_ctx *ctx, int32_t entries);
 
 /* Total bytes of device memory the context holds. */
 int64_t pxsne_device_bytes(const pxsne_ctx *ctx);

@@ -130,6 +130,10 @@ def load(path: str | None = None):
     L.pxsne_device_bytes.argtypes = [vp]
     L.pxsne_device_bytes.restype = i64
     L.pxsne_get_level_counters.argtypes = [vp, C.POINTER(u64), i32]
+    L.pxsne_save.argtypes = [vp, C.c_char_p]
+    L.pxsne_test_stack_limit.argtypes = [vp, i32]
+    L.pxsne_load.argtypes = [C.POINTER(vp), C.c_char_p, vp]
+    L.pxsne_get_params.argtypes = [vp, C.POINTER(_CParams)]
     L.pxsne_measure_peaks.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.POINTER(i32), C.POINTER(i64)]
     _lib = L
@@ -195,6 +199,27 @@ class Context:
     def _ck(self, rc):
         if rc != PXSNE_OK:
             raise PxsneError(rc, self.L.pxsne_last_error(self.h).decode())
+
+    @classmethod
+    def load(cls, path, stream=None):
+        """A context resumed from a checkpoint file (``pxsne_load``)."""
+        L = load()
+        h = C.c_void_p()
+        rc = L.pxsne_load(C.byref(h), os.fsencode(path), stream)
+        if rc != PXSNE_OK:
+            raise PxsneError(rc, L.pxsne_last_error(None).decode())
+        self = cls.__new__(cls)
+        self.L, self.h = L, h
+        cp = _CParams()
+        self._ck(L.pxsne_get_params(h, C.byref(cp)))
+        self.params = Params(**{f: getattr(cp, f) for f, _ in _CParams._fields_})
+        self._p = self.params.c()
+        return self
+
+    def save(self, path):
+        """Write P, the state and the schedule to a checkpoint file
+        (``pxsne_save``)."""
+        self._ck(self.L.pxsne_save(self.h, os.fsencode(path)))
 
     def close(self):
         if getattr(self, "h", None):
@@ -404,6 +429,10 @@ class Context:
         rc = self.L.pxsne_test_bounded_wait(self.h, int(polls), C.byref(f))
         return rc, f.value
 
+    def test_stack_limit(self, entries):
+        """Lower the traversal's stack room (test hook; 0 restores it)."""
+        self._ck(self.L.pxsne_test_stack_limit(self.h, int(entries)))
+
     def knn_pruning(self):
         """(skipped (query tile, candidate tile) pairs, all pairs) of the last
         tensor-core neighbour search."""
@@ -560,4 +589,5 @@ EXPORTED = ["pxsne_default_params", "pxsne_create", "pxsne_destroy", "pxsne_last
             "pxsne_mlp_set_params", "pxsne_mlp_get_params", "pxsne_mlp_loss_grad",
             "pxsne_mlp_train", "pxsne_mlp_predict", "pxsne_embed_align",
             "pxsne_nbr_precision", "pxsne_pca", "pxsne_measure_peaks",
-            "pxsne_get_level_counters"]
+            "pxsne_get_level_counters", "pxsne_save", "pxsne_load", "pxsne_get_params",
+            "pxsne_test_stack_limit"]

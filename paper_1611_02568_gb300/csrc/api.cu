@@ -887,3 +887,196 @@ int64_t pxsne_device_bytes(const pxsne_ctx *c) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- checkpoints
+// A checkpoint is one flat file: a 128-byte header, then the payload
+//   row_ptr[n+1] int64, col[nnz] int32, val[nnz] float32   (P as CSR)
+//   z[2n] uint32, u[2n] float32, gains[2n] float32           (the state)
+// in the byte order of the machine that wrote it (little-endian on every
+// supported host).  The header's checksum is FNV-1a (64-bit offset basis and
+// prime) applied to the payload taken as consecutive little-endian 64-bit
+// words, the last one zero-padded.
+namespace {
+
+struct CheckpointHeader {
+    char magic[8];          // "PXSNECK" + NUL
+    uint32_t version;       // 1
+    uint32_t header_bytes;  // sizeof(CheckpointHeader)
+    pxsne_params params;    // the context's parameters and schedule
+    uint32_t pad0;
+    int64_t n, nnz;
+    int32_t t, pad1;
+    double s[2];
+    uint64_t payload_bytes;
+    uint64_t checksum;
+};
+static_assert(sizeof(pxsne_params) == 52, "pxsne_params layout");
+static_assert(sizeof(CheckpointHeader) == 128, "checkpoint header layout");
+constexpr char kMagic[8] = {'P', 'X', 'S', 'N', 'E', 'C', 'K', 0};
+
+struct Fnv64Words {
+    uint64_t h = 14695981039346656037ull;
+    unsigned char carry[8];
+    int nc = 0;
+    void word(uint64_t w) {
+        h ^= w;
+        h *= 1099511628211ull;
+    }
+    void add(const void *p, size_t bytes) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        while (bytes && nc) {
+            carry[nc++] = *b++;
+            bytes--;
+            if (nc == 8) {
+                uint64_t w;
+                memcpy(&w, carry, 8);
+                word(w);
+                nc = 0;
+            }
+        }
+        for (; bytes >= 8; b += 8, bytes -= 8) {
+            uint64_t w;
+            memcpy(&w, b, 8);
+            word(w);
+        }
+        while (bytes--) carry[nc++] = *b++;
+    }
+    uint64_t done() {
+        if (nc) {
+            memset(carry + nc, 0, 8 - nc);
+            uint64_t w;
+            memcpy(&w, carry, 8);
+            word(w);
+            nc = 0;
+        }
+        return h;
+    }
+};
+
+uint64_t payload_bytes_of(int64_t n, int64_t nnz) {
+    return 8ull * (uint64_t)(n + 1) + 8ull * (uint64_t)nnz + 24ull * (uint64_t)n;
+}
+
+}  // namespace
+
+int pxsne_save(pxsne_ctx *c, const char *path) {
+    int rc = need_state(c);
+    if (rc) return rc;
+    if (!path) return fail(c, PXSNE_E_ARG, "path is NULL");
+    const int64_t n = c->n, nnz = c->nnz;
+    std::vector<int64_t> rp(n + 1);
+    std::vector<int32_t> col(nnz > 0 ? nnz : 1);
+    std::vector<float> val(nnz > 0 ? nnz : 1);
+    if ((rc = pxsne_get_P(c, rp.data(), col.data(), val.data()))) return rc;
+    std::vector<uint32_t> z(2 * n);
+    std::vector<float> u(2 * n), g(2 * n);
+    CheckpointHeader h;
+    memset(&h, 0, sizeof(h));
+    if ((rc = pxsne_get_state(c, z.data(), h.s, u.data(), g.data(), &h.t))) return rc;
+    memcpy(h.magic, kMagic, 8);
+    h.version = 1;
+    h.header_bytes = sizeof(CheckpointHeader);
+    h.params = c->p;
+    h.n = n;
+    h.nnz = nnz;
+    h.payload_bytes = payload_bytes_of(n, nnz);
+    Fnv64Words f;
+    f.add(rp.data(), 8 * (size_t)(n + 1));
+    f.add(col.data(), 4 * (size_t)nnz);
+    f.add(val.data(), 4 * (size_t)nnz);
+    f.add(z.data(), 8 * (size_t)n);
+    f.add(u.data(), 8 * (size_t)n);
+    f.add(g.data(), 8 * (size_t)n);
+    h.checksum = f.done();
+    // written to a temporary name, then renamed over the target
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *fp = fopen(tmp.c_str(), "wb");
+    if (!fp) return fail(c, PXSNE_E_ARG, "cannot open %s for writing", tmp.c_str());
+    bool ok = fwrite(&h, sizeof(h), 1, fp) == 1;
+    ok = ok && fwrite(rp.data(), 8, (size_t)(n + 1), fp) == (size_t)(n + 1);
+    ok = ok && (nnz == 0 || fwrite(col.data(), 4, (size_t)nnz, fp) == (size_t)nnz);
+    ok = ok && (nnz == 0 || fwrite(val.data(), 4, (size_t)nnz, fp) == (size_t)nnz);
+    ok = ok && fwrite(z.data(), 8, (size_t)n, fp) == (size_t)n;
+    ok = ok && fwrite(u.data(), 8, (size_t)n, fp) == (size_t)n;
+    ok = ok && fwrite(g.data(), 8, (size_t)n, fp) == (size_t)n;
+    ok = (fclose(fp) == 0) && ok;
+    if (!ok || rename(tmp.c_str(), path) != 0) {
+        remove(tmp.c_str());
+        return fail(c, PXSNE_E_ARG, "writing %s failed", path);
+    }
+    return PXSNE_OK;
+}
+
+int pxsne_load(pxsne_ctx **out, const char *path, void *stream) {
+    if (!out) return fail(nullptr, PXSNE_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!path) return fail(nullptr, PXSNE_E_ARG, "path is NULL");
+    FILE *fp = fopen(path, "rb");
+    if (!fp) return fail(nullptr, PXSNE_E_ARG, "cannot open %s", path);
+    struct Closer {
+        FILE *f;
+        ~Closer() { fclose(f); }
+    } closer{fp};
+    CheckpointHeader h;
+    if (fread(&h, sizeof(h), 1, fp) != 1) return fail(nullptr, PXSNE_E_ARG, "%s: short header", path);
+    if (memcmp(h.magic, kMagic, 8) != 0) return fail(nullptr, PXSNE_E_ARG, "%s: not a checkpoint", path);
+    if (h.version != 1 || h.header_bytes != sizeof(CheckpointHeader))
+        return fail(nullptr, PXSNE_E_UNSUPPORTED, "%s: version %u", path, h.version);
+    if (h.n < 2 || h.n > kMaxN || h.nnz < 0 || h.nnz > (int64_t(1) << 40) || h.t < 0 ||
+        !(std::isfinite(h.s[0]) && h.s[0] > 0.0) || !(std::isfinite(h.s[1]) && h.s[1] > 0.0) ||
+        h.payload_bytes != payload_bytes_of(h.n, h.nnz))
+        return fail(nullptr, PXSNE_E_ARG, "%s: bad sizes in the header", path);
+    int rc = check_params(&h.params);
+    if (rc) return rc;
+    const int64_t n = h.n, nnz = h.nnz;
+    std::vector<int64_t> rp(n + 1);
+    std::vector<int32_t> col(nnz > 0 ? nnz : 1);
+    std::vector<float> val(nnz > 0 ? nnz : 1);
+    std::vector<uint32_t> z(2 * n);
+    std::vector<float> u(2 * n), g(2 * n);
+    bool ok = fread(rp.data(), 8, (size_t)(n + 1), fp) == (size_t)(n + 1);
+    ok = ok && (nnz == 0 || fread(col.data(), 4, (size_t)nnz, fp) == (size_t)nnz);
+    ok = ok && (nnz == 0 || fread(val.data(), 4, (size_t)nnz, fp) == (size_t)nnz);
+    ok = ok && fread(z.data(), 8, (size_t)n, fp) == (size_t)n;
+    ok = ok && fread(u.data(), 8, (size_t)n, fp) == (size_t)n;
+    ok = ok && fread(g.data(), 8, (size_t)n, fp) == (size_t)n;
+    if (!ok) return fail(nullptr, PXSNE_E_ARG, "%s: truncated", path);
+    unsigned char extra;
+    if (fread(&extra, 1, 1, fp) != 0) return fail(nullptr, PXSNE_E_ARG, "%s: trailing bytes", path);
+    Fnv64Words f;
+    f.add(rp.data(), 8 * (size_t)(n + 1));
+    f.add(col.data(), 4 * (size_t)nnz);
+    f.add(val.data(), 4 * (size_t)nnz);
+    f.add(z.data(), 8 * (size_t)n);
+    f.add(u.data(), 8 * (size_t)n);
+    f.add(g.data(), 8 * (size_t)n);
+    if (f.done() != h.checksum) return fail(nullptr, PXSNE_E_ARG, "%s: checksum mismatch", path);
+    pxsne_ctx *c = nullptr;
+    if ((rc = pxsne_create(&c, &h.params, stream))) return rc;
+    rc = pxsne_set_P(c, n, rp.data(), col.data(), val.data());
+    if (!rc) rc = pxsne_set_state(c, z.data(), h.s, u.data(), g.data(), h.t);
+    if (rc) {
+        fail(nullptr, rc, "%s: %s", path, c->err.c_str());
+        pxsne_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return PXSNE_OK;
+}
+
+int pxsne_get_params(const pxsne_ctx *c, pxsne_params *p) {
+    if (!c || !p) return PXSNE_E_ARG;
+    *p = c->p;
+    return PXSNE_OK;
+}
+
+int pxsne_test_stack_limit(pxsne_ctx *c, int32_t entries) {
+    if (!c) return PXSNE_E_ARG;
+    if (entries != 0 && (entries < 4 || entries > kTravStack))
+        return fail(c, PXSNE_E_ARG, "entries must be 0 or in [4, %d]", kTravStack);
+    const int lim = entries;  // 0: the full stack
+    CK(c, cudaMemcpyAsync(&c->sc->stack_limit, &lim, sizeof(int), cudaMemcpyHostToDevice,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return PXSNE_OK;
+}

@@ -37,6 +37,8 @@ struct DevScalars {
     unsigned ticket;     // last-block-done counter of the Z reduction
     unsigned ticket2;    // same for the KL reduction
     unsigned pyr_ticket; // last-block-done counter of the pyramid's first pass
+    int stack_limit;     // entries of a traversal warp's stack in use (0: all
+                         // kTravStack; lowered only by pxsne_test_stack_limit)
     u64 n_accept;        // accepted (point, cell) pairs of the last traversal
     u64 n_test;          // (point, cell) pairs tested by the last traversal
     u64 n_steps;         // warp-level (node, non-empty child) steps of the last traversal

@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
     __shared__ TravEntry s_stk[kTravWarps][kTravStack];
     __shared__ float s_T[kMaxL + 2];
     __shared__ int s_off[kMaxL + 2];
+    const int stk_lim = sc->stack_limit > 0 ? min(max(sc->stack_limit, 4), kTravStack) : kTravStack;
     // COUNT: (tested, accepted, warp steps) by level of the child
     __shared__ u64 s_lv[COUNT ? kMaxL + 2 : 1][3];
     if (threadIdx.x < kMaxL + 2) {
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
             const int sh = 2 * (L - lc);
             const uint32_t mine0 = OWN ? mi0 >> sh : 0xffffffffu, mine1 = OWN ? mi1 >> sh : 0xffffffffu;
             // room for the (at most four) entries this node may push
-            if (sp + 4 > kTravStack) {
+            if (sp + 4 > stk_lim) {
                 overflow = true;
                 break;
             }

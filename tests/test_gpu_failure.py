@@ -16,7 +16,7 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 E_ARG, E_DEVICE = -1, -5
-NONFINITE, BISECT, RANGE, TIMEOUT = 1, 4, 8, 16
+NONFINITE, STACK, BISECT, RANGE, TIMEOUT = 1, 2, 4, 8, 16
 
 
 @pytest.fixture(scope="module")
@@ -121,3 +121,61 @@ def test_unreachable_perplexity_flagged(px, monkeypatch):
             ctx.init(datagen.init_y0(0, X.shape[0]))
             ctx.step(10)
             assert ctx.sync() == 0
+
+
+def test_stack_overflow_flagged(px):
+    """The traversal's stack guard: with room for 4 entries (a 512^2 screen
+    needs 3 L - 2 = 25) a warp stops its walk, sets the flag and skips the
+    push; the next synchronising call reports it, and with the full stack
+    back the same state gives the oracle's forces."""
+    X, _ = datagen.gauss10(5, n=1800)
+    with px.Context(px.Params(log2_r=9)) as ctx:
+        ctx.affinities(X)
+        ctx.init(datagen.init_y0(3, X.shape[0]))
+        ctx.step(30)
+        assert ctx.sync() == 0
+        z, s, u, g, t = ctx.get_state()
+        assert ctx.L.pxsne_test_stack_limit(ctx.h, 3) == E_ARG
+        ctx.test_stack_limit(4)
+        ctx.step(1)
+        with pytest.raises(px.PxsneError) as ei:
+            ctx.sync()
+        assert ei.value.code == E_DEVICE and "stack" in str(ei.value)
+        assert ctx.sync() == 0                 # read and cleared
+        ctx.test_stack_limit(0)
+        ctx.set_state(z, s, u, g, t)
+        Frep, Zi, _, _ = ctx.get_forces()
+        oF, oZi, _ = oracle.bh_repulsion(z, s, 9, 0.5)
+        assert np.linalg.norm(Frep - oF) / np.linalg.norm(oF) < 1e-4
+        ctx.step(10)
+        assert ctx.sync() == 0
+
+
+def test_clamped_step_rescales_exactly(px):
+    """A step clamped to 2^58 ulps makes the rescale's range gamma about 2^59
+    (Sec. 4.2's gamma_d at its widest): the GPU's new z and s equal the
+    oracle's exact-integer rescale of the same zhat, bit for bit.  zhat is
+    rebuilt on the host from the GPU's own new velocities, exactly as the
+    step forms it: z + rint(u / s) in FP64, clamped to +-2^58."""
+    X, _ = datagen.gauss10(6, n=1300)
+    with px.Context(px.Params(log2_r=9)) as ctx:
+        ctx.affinities(X)
+        ctx.init(datagen.init_y0(4, X.shape[0]))
+        ctx.step(12)
+        z, s, u, g, t = ctx.get_state()
+        u[5, 0] = 1e30
+        u[77, 1] = -3e29
+        ctx.set_state(z, s, u, g, t)
+        ctx.step(1)
+        with pytest.raises(px.PxsneError):
+            ctx.sync()                         # RANGE, as expected
+        z2, s2, u2, _, _ = ctx.get_state()
+    lim = 2.0 ** 58
+    st = np.rint(u2.astype(np.float64) * (1.0 / s)[None, :])
+    assert abs(st[5, 0]) > lim and abs(st[77, 1]) > lim
+    st = np.clip(st, -lim, lim)
+    zhat = z.astype(np.int64) + st.astype(np.int64)
+    assert zhat[:, 0].max() - zhat[:, 0].min() > 2 ** 58
+    zo, so = oracle.rescale(zhat, s)
+    assert np.array_equal(z2, zo)
+    assert np.array_equal(s2, so)
