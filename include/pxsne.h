@@ -27,7 +27,8 @@
  *  - One context may be used by one host thread at a time.
  *
  * Positions.  The state holds each point as unsigned 32-bit fixed point per
- * axis: z_d in [0, 2^32) ulps, pixel = z_d >> (32 - L) for a 2^L x 2^L screen.
+ * axis: z_d in [0, R_d) ulps, pixel = z_d >> (32 - L) in [0, r_d) for an
+ * r_1 x r_2 screen (R_d = r_d 2^(32 - L); 2^32 for a 2^L x 2^L screen).
  * t-SNE's own coordinates are y_d = s_d * z_d (+ an arbitrary offset), where the
  * per-axis scale s_d (y-units per ulp) carries the compensation of
  * Eq. beta_scaling (s_d^2 = beta_d).
@@ -62,7 +63,13 @@ typedef struct pxsne_ctx pxsne_ctx;
 /* Parameters of one embedding.  Defaults (pxsne_default_params): L = 11,
  * theta = 0.5, eta = 200, exaggeration 12 for 250 iterations, momentum 0.5
  * then 0.8 from iteration 250, min_gain 0.01, k = 90, perplexity 30,
- * init_sigma 1e-4, centre of mass. */
+ * init_sigma 1e-4, centre of mass, a square 2^L x 2^L screen.
+ *
+ * Screens of r_1 x r_2 pixels (Sec. 4.2's per-axis r_d; e.g. 1024 x 768 with
+ * L = 10) keep the quadtree's root at the padded 2^L x 2^L square, so the
+ * tree's depth is L on both axes; axis d then spans R_d = r_d 2^(32 - L) ulps,
+ * z_d in [0, R_d) and its pixel z_d >> (32 - L) in [0, r_d).  The init map
+ * and the rescale use R_d in place of 2^32 (pxsne_init, pxsne_step). */
 typedef struct pxsne_params {
     int32_t log2_r;          /* L: screen is 2^L x 2^L pixels, 1 <= L <= 14 (Sec. 4.1 depth) */
     float theta;             /* Barnes-Hut threshold, >= 0 (Eq. bh_criteria) */
@@ -77,6 +84,8 @@ typedef struct pxsne_params {
     float perplexity;        /* target perplexity u of each row, 0 < u <= k */
     float init_sigma;        /* std-dev of the random initial embedding */
     int32_t centre_mode;     /* 0: cell centre of mass; 1: geometric cell centre (Sec. 4.1) */
+    int32_t screen_x;        /* screen width r_1 in pixels, 1 <= r_1 <= 2^L; 0: 2^L */
+    int32_t screen_y;        /* screen height r_2 in pixels, 1 <= r_2 <= 2^L; 0: 2^L */
 } pxsne_params;
 
 void pxsne_default_params(pxsne_params *p);
@@ -111,9 +120,10 @@ int pxsne_affinities(pxsne_ctx *ctx, const float *X, int64_t n, int32_t D,
 
 /* Start an embedding (Sec. 3.1, Eq. z1/z2): Y0 (host or device, n x 2 float32,
  * y-units) is mapped per axis onto the fixed-point screen,
- *   z_d = min(2^32 - 1, floor((y_d - min_d) * 2^32 / (max_d - min_d))),
- *   s_d = (max_d - min_d) / 2^32,
- * in FP64 (an axis with zero extent maps to z_d = 0, s_d = 2^-32).  Y0 == NULL
+ *   z_d = min(R_d - 1, floor((y_d - min_d) * R_d / (max_d - min_d))),
+ *   s_d = (max_d - min_d) / R_d,
+ * in FP64, R_d the axis' extent in ulps (2^32 on a square 2^L screen; an axis
+ * with zero extent maps to z_d = 0, s_d = 1 / R_d).  Y0 == NULL
  * draws Y0 ~ N(0, init_sigma^2 I) from `seed` with Philox4x32-10 (Salmon et al.
  * 2011) and the Box-Muller transform.  Velocities are zeroed, gains set to 1,
  * the iteration counter to 0, and the forces of the initial state computed.
@@ -123,8 +133,9 @@ int pxsne_init(pxsne_ctx *ctx, const float *Y0, int y_on_device, uint64_t seed);
 /* Run `iters` >= 0 gradient iterations, asynchronously on the context's
  * stream.  Iteration t: g = 4 (alpha_t Fattr - Frep / Z) (Eq. grad), the
  * gains/momentum step u = mu_t u - eta gain g, zhat = z + rint(u / s), then the
- * screen-driven rescale z_d = floor((zhat_d - min_d) 2^32 / (max_d - min_d + 1)),
- * s_d <- s_d (max_d - min_d + 1) / 2^32 (Sec. 4.2), then the pixel-aligned tree
+ * screen-driven rescale z_d = floor((zhat_d - min_d) R_d / (max_d - min_d + 1)),
+ * s_d <- (s_d (max_d - min_d + 1)) / R_d (Sec. 4.2; R_d = 2^32 on a square
+ * 2^L screen, r_d 2^(32 - L) in general), then the pixel-aligned tree
  * and forces of the new state (Sec. 4.1, Eq. bh_criteria, Eq. grad).
  * Returns enqueue errors only. */
 int pxsne_step(pxsne_ctx *ctx, int32_t iters);
@@ -140,8 +151,8 @@ int pxsne_step(pxsne_ctx *ctx, int32_t iters);
  * pxsne_init, PXSNE_E_ARG if the file cannot be written.
  *
  * File layout (byte order of the writing host, little-endian on every
- * supported one): a 128-byte header {char magic[8] = "PXSNECK\0"; uint32
- * version = 1; uint32 header bytes = 128; pxsne_params (52 bytes); uint32 0;
+ * supported one): a 136-byte header {char magic[8] = "PXSNECK\0"; uint32
+ * version = 1; uint32 header bytes = 136; pxsne_params (60 bytes); uint32 0;
  * int64 n, nnz; int32 t, 0; double s[2]; uint64 payload bytes; uint64
  * checksum}, then row_ptr[n+1] int64, col[nnz] int32, val[nnz] float32,
  * z[2n] uint32, u[2n] float32, gains[2n] float32.  The checksum is FNV-1a

@@ -64,6 +64,7 @@ def lib():
         L.orc_symmetrize.argtypes = [pi32, pd, i64, i32, pi64, pi32, pd]
         L.orc_symmetrize.restype = i64
         L.orc_init_fx.argtypes = [pd, i64, pu32, pd]
+        L.orc_init_fx_screen.argtypes = [pd, i64, pd, pu32, pd]
         L.orc_morton.argtypes = [u32, u32]
         L.orc_morton.restype = u32
         L.orc_level_offset.argtypes = [i32]
@@ -77,6 +78,7 @@ def lib():
         L.orc_update.argtypes = [i64, pu32, pd, pd, pd, dbl, dbl, dbl, dbl, dbl, pd, pd,
                                  pd, pi64]
         L.orc_rescale.argtypes = [i64, pi64, pu32, pd]
+        L.orc_rescale_screen.argtypes = [i64, pi64, pd, pu32, pd]
         L.orc_kl.argtypes = [pi64, pi32, pd, i64, pu32, pd, dbl]
         L.orc_kl.restype = dbl
         L.orc_run.argtypes = [C.c_void_p, pi64, pi32, pd, i64, pu32, pd, pd, pd, i32, i32,
@@ -190,12 +192,24 @@ def affinities(X, perplexity_u, k):
 
 
 # ---------------------------------------------------------------- tree / forces
-def init_fx(Y0):
+def screen_R(L, rx=0, ry=0):
+    """Per-axis extent R_d = r_d 2^(32 - L) in ulps of an r_x x r_y screen
+    (0: 2^L pixels) whose quadtree root is the padded 2^L x 2^L square."""
+    return np.array([float(r) * 2.0 ** (32 - L) if r else 2.0 ** 32 for r in (rx, ry)])
+
+
+def init_fx(Y0, R=None):
+    """Eq. z1/z2 onto [0, R_d) ulps per axis (R: screen_R; None: 2^32)."""
     Y0 = np.ascontiguousarray(Y0, dtype=np.float64)
     n = Y0.shape[0]
     z = np.empty((n, 2), dtype=np.uint32)
     s = np.empty(2)
-    lib().orc_init_fx(_P(Y0, C.c_double), n, _P(z, C.c_uint32), _P(s, C.c_double))
+    if R is None:
+        lib().orc_init_fx(_P(Y0, C.c_double), n, _P(z, C.c_uint32), _P(s, C.c_double))
+    else:
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        lib().orc_init_fx_screen(_P(Y0, C.c_double), n, _P(R, C.c_double), _P(z, C.c_uint32),
+                                 _P(s, C.c_double))
     return z, s
 
 
@@ -290,13 +304,18 @@ def update(z, s, Fattr, Frep, Z, alpha, mu, eta, u, gains, min_gain=0.01):
     return zhat, g
 
 
-def rescale(zhat, s):
-    """Returns (z u32 [n,2], s_new)."""
+def rescale(zhat, s, R=None):
+    """Returns (z u32 [n,2], s_new); R: per-axis screen extent (None: 2^32)."""
     zhat = np.ascontiguousarray(zhat, dtype=np.int64)
     s2 = np.array(s, dtype=np.float64)
     n = zhat.shape[0]
     z = np.empty((n, 2), dtype=np.uint32)
-    lib().orc_rescale(n, _P(zhat, C.c_int64), _P(z, C.c_uint32), _P(s2, C.c_double))
+    if R is None:
+        lib().orc_rescale(n, _P(zhat, C.c_int64), _P(z, C.c_uint32), _P(s2, C.c_double))
+    else:
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        lib().orc_rescale_screen(n, _P(zhat, C.c_int64), _P(R, C.c_double), _P(z, C.c_uint32),
+                                 _P(s2, C.c_double))
     return z, s2
 
 
@@ -313,7 +332,8 @@ class _Params(C.Structure):
                 ("exag", C.c_double), ("exag_iters", C.c_int32), ("mom0", C.c_double),
                 ("mom1", C.c_double), ("mom_switch", C.c_int32),
                 ("min_gain", C.c_double), ("crit_mode", C.c_int32),
-                ("centre_mode", C.c_int32), ("exact", C.c_int32)]
+                ("centre_mode", C.c_int32), ("exact", C.c_int32), ("rx", C.c_int32),
+                ("ry", C.c_int32)]
 
 
 @dataclass
@@ -331,11 +351,16 @@ class Params:
     crit_mode: int = 0
     centre_mode: int = 0
     exact: int = 0
+    rx: int = 0        # screen pixels per axis (0: 2^L)
+    ry: int = 0
 
     def c(self):
         return _Params(self.L, self.theta, self.eta, self.exag, self.exag_iters, self.mom0,
                        self.mom1, self.mom_switch, self.min_gain, self.crit_mode,
-                       self.centre_mode, self.exact)
+                       self.centre_mode, self.exact, self.rx, self.ry)
+
+    def R(self):
+        return screen_R(self.L, self.rx, self.ry)
 
 
 @dataclass
@@ -347,8 +372,8 @@ class State:
     t: int = 0
 
     @classmethod
-    def from_y0(cls, Y0):
-        z, s = init_fx(Y0)
+    def from_y0(cls, Y0, R=None):
+        z, s = init_fx(Y0, R)
         n = z.shape[0]
         return cls(z, s, np.zeros((n, 2)), np.ones((n, 2)), 0)
 

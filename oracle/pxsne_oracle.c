@@ -11,8 +11,11 @@
  * Embedding", arXiv 1611.02568) and cites the passage it follows.
  *
  * Conventions (the readings of the paper that this oracle implements):
- *  - Screen r x r with r = 2^L.  Positions are fixed point: z_d is a u32 in
- *    [0, 2^32) ulps; the pixel is z_d >> F with F = 32 - L (Eq. z1/z2).
+ *  - Screen r_1 x r_2 pixels with r_d <= 2^L (Sec. 4.2's per-axis r_d): the
+ *    quadtree's root is the padded square of 2^L x 2^L pixels.  Positions are
+ *    fixed point: z_d is a u32 in [0, R_d) ulps with R_d = r_d 2^F, F = 32 - L,
+ *    and the pixel is z_d >> F (Eq. z1/z2); a square 2^L screen has
+ *    R_d = 2^32.
  *  - y-space (t-SNE's own coordinates) is y_d = s_d * z_d (+ an offset that no
  *    quantity depends on).  s_d is the product of the per-iteration rescale
  *    factors, i.e. sqrt(beta_d) of Eq. beta_scaling, carried directly.
@@ -208,12 +211,13 @@ int64_t orc_symmetrize(const int32_t *idx, const double *pcond, int64_t n, int32
 }
 
 /* Eq. z1/z2: map an initial embedding Y0 (n x 2, y-units) onto the fixed-point
- * screen: z_d = min(R-1, floor((y_d - min_d) * R / (max_d - min_d))),
- * s_d = (max_d - min_d) / R, with R = 2^32.  An axis with zero extent maps to
- * z_d = 0 and s_d = 1/R. */
-void orc_init_fx(const double *Y0, int64_t n, uint32_t *z, double *s)
+ * screen: z_d = min(R_d-1, floor((y_d - min_d) * R_d / (max_d - min_d))),
+ * s_d = (max_d - min_d) / R_d, with R_d = r_d 2^F the axis' extent in ulps
+ * (R[d]).  An axis with zero extent maps to z_d = 0 and s_d = 1/R_d. */
+void orc_init_fx_screen(const double *Y0, int64_t n, const double *R, uint32_t *z, double *s)
 {
     for (int d = 0; d < 2; d++) {
+        const double Rd = R[d];
         double mn = Y0[d], mx = Y0[d];
         for (int64_t i = 1; i < n; i++) {
             double v = Y0[2 * i + d];
@@ -223,15 +227,22 @@ void orc_init_fx(const double *Y0, int64_t n, uint32_t *z, double *s)
         double range = mx - mn;
         if (!(range > 0.0)) {
             for (int64_t i = 0; i < n; i++) z[2 * i + d] = 0u;
-            s[d] = 1.0 / ORC_R;
+            s[d] = 1.0 / Rd;
             continue;
         }
         for (int64_t i = 0; i < n; i++) {
-            double q = floor((Y0[2 * i + d] - mn) * ORC_R / range);
-            z[2 * i + d] = q >= ORC_R - 1.0 ? 0xFFFFFFFFu : (uint32_t)q;
+            double q = floor((Y0[2 * i + d] - mn) * Rd / range);
+            z[2 * i + d] = q >= Rd - 1.0 ? (uint32_t)(Rd - 1.0) : (uint32_t)q;
         }
-        s[d] = range / ORC_R;
+        s[d] = range / Rd;
     }
+}
+
+/* The square 2^L screen: R_d = 2^32 on both axes. */
+void orc_init_fx(const double *Y0, int64_t n, uint32_t *z, double *s)
+{
+    const double R[2] = {ORC_R, ORC_R};
+    orc_init_fx_screen(Y0, n, R, z, s);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -471,13 +482,16 @@ void orc_update(int64_t n, const uint32_t *z, const double *s, const double *Fat
         }
 }
 
-/* Sec. 4.2 screen-driven scaling, in exact integer arithmetic:
- *   z_d = floor((zhat_d - min_d) * R / gamma_d),  gamma_d = (max_d - min_d) + 1
- * (the "+ epsilon" of gamma is one ulp), and the compensation of Eq.
- * beta_scaling carried as s_d <- s_d * gamma_d / R. */
-void orc_rescale(int64_t n, const int64_t *zhat, uint32_t *z, double *s)
+/* Sec. 4.2 screen-driven scaling to the r_d pixels of axis d, in exact
+ * integer arithmetic:
+ *   z_d = floor((zhat_d - min_d) * R_d / gamma_d),  gamma_d = (max_d - min_d) + 1
+ * (the "+ epsilon" of gamma is one ulp; R_d = r_d 2^F, R[d]), and the
+ * compensation of Eq. beta_scaling carried as s_d <- (s_d * gamma_d) / R_d
+ * (two FP64 roundings; one when R_d = 2^32). */
+void orc_rescale_screen(int64_t n, const int64_t *zhat, const double *R, uint32_t *z, double *s)
 {
     for (int d = 0; d < 2; d++) {
+        const uint64_t Rd = (uint64_t)R[d];
         int64_t mn = zhat[d], mx = zhat[d];
         for (int64_t i = 1; i < n; i++) {
             int64_t v = zhat[2 * i + d];
@@ -486,11 +500,18 @@ void orc_rescale(int64_t n, const int64_t *zhat, uint32_t *z, double *s)
         }
         uint64_t gamma = (uint64_t)(mx - mn) + 1u;
         for (int64_t i = 0; i < n; i++) {
-            unsigned __int128 num = (unsigned __int128)(uint64_t)(zhat[2 * i + d] - mn) << 32;
+            unsigned __int128 num = (unsigned __int128)(uint64_t)(zhat[2 * i + d] - mn) * Rd;
             z[2 * i + d] = (uint32_t)(num / gamma);
         }
-        s[d] = s[d] * ldexp((double)gamma, -32);
+        s[d] = (s[d] * (double)gamma) / R[d];
     }
+}
+
+/* The square 2^L screen. */
+void orc_rescale(int64_t n, const int64_t *zhat, uint32_t *z, double *s)
+{
+    const double R[2] = {ORC_R, ORC_R};
+    orc_rescale_screen(n, zhat, R, z, s);
 }
 
 /* Eq. cost_func: C = sum_ij p_ij ln(p_ij / q_ij) with q_ij = w_ij / Z, over the
@@ -536,7 +557,16 @@ typedef struct {
     int32_t crit_mode;
     int32_t centre_mode;
     int32_t exact;
+    int32_t rx, ry;  /* screen pixels per axis (0: 2^L) */
 } orc_params;
+
+/* R_d = r_d 2^(32 - L) of a run's screen. */
+static void screen_extent(const orc_params *p, double *R)
+{
+    const int32_t r[2] = {p->rx, p->ry};
+    for (int d = 0; d < 2; d++)
+        R[d] = r[d] > 0 ? ldexp((double)r[d], 32 - p->L) : ORC_R;
+}
 
 int orc_run(const orc_params *p, const int64_t *row_ptr, const int32_t *col,
             const double *val, int64_t n, uint32_t *z, double *s, double *u,
@@ -558,6 +588,8 @@ int orc_run(const orc_params *p, const int64_t *row_ptr, const int32_t *col,
         free(cnt); free(sx); free(sy); free(Frep); free(Fattr); free(Zi); free(zhat);
         return -1;
     }
+    double R[2];
+    screen_extent(p, R);
     for (int32_t t = t0; t < t0 + iters; t++) {
         if (p->exact) {
             orc_exact_repulsion(z, s, n, NULL, n, Frep, Zi);
@@ -574,7 +606,7 @@ int orc_run(const orc_params *p, const int64_t *row_ptr, const int32_t *col,
         double mu = t < p->mom_switch ? p->mom0 : p->mom1;
         orc_update(n, z, s, Fattr, Frep, Z, alpha, mu, p->eta, p->min_gain, u, gains,
                    NULL, zhat);
-        orc_rescale(n, zhat, z, s);
+        orc_rescale_screen(n, zhat, R, z, s);
     }
     free(cnt); free(sx); free(sy); free(Frep); free(Fattr); free(Zi); free(zhat);
     return 0;

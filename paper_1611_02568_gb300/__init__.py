@@ -45,7 +45,7 @@ class _CParams(C.Structure):
                 ("momentum0", C.c_float), ("momentum1", C.c_float),
                 ("momentum_switch", C.c_int32), ("min_gain", C.c_float), ("k", C.c_int32),
                 ("perplexity", C.c_float), ("init_sigma", C.c_float),
-                ("centre_mode", C.c_int32)]
+                ("centre_mode", C.c_int32), ("screen_x", C.c_int32), ("screen_y", C.c_int32)]
 
 
 @dataclass
@@ -64,6 +64,8 @@ class Params:
     perplexity: float = 30.0
     init_sigma: float = 1e-4
     centre_mode: int = 0
+    screen_x: int = 0      # pixels of the screen's width (0: 2^log2_r)
+    screen_y: int = 0      # pixels of its height (0: 2^log2_r)
 
     def c(self):
         return _CParams(*[getattr(self, f.name) for f in fields(self)])

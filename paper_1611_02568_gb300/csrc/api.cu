@@ -95,6 +95,10 @@ int check_params(const pxsne_params *p) {
     if (!(p->init_sigma > 0.f)) return fail(nullptr, PXSNE_E_ARG, "init_sigma must be > 0");
     if (p->centre_mode != 0 && p->centre_mode != 1)
         return fail(nullptr, PXSNE_E_ARG, "centre_mode must be 0 or 1");
+    const int32_t side = 1 << p->log2_r;
+    if (p->screen_x < 0 || p->screen_x > side || p->screen_y < 0 || p->screen_y > side)
+        return fail(nullptr, PXSNE_E_ARG, "screen %d x %d outside [1, %d] (0: %d)", p->screen_x,
+                    p->screen_y, side, side);
     return PXSNE_OK;
 }
 
@@ -266,6 +270,8 @@ void pxsne_default_params(pxsne_params *p) {
     p->perplexity = 30.f;
     p->init_sigma = 1e-4f;
     p->centre_mode = 0;
+    p->screen_x = 0;
+    p->screen_y = 0;
 }
 
 int pxsne_create(pxsne_ctx **out, const pxsne_params *p, void *stream) {
@@ -889,7 +895,7 @@ int64_t pxsne_device_bytes(const pxsne_ctx *c) {
 }  // extern "C"
 
 // ---------------------------------------------------------------- checkpoints
-// A checkpoint is one flat file: a 128-byte header, then the payload
+// A checkpoint is one flat file: a 136-byte header, then the payload
 //   row_ptr[n+1] int64, col[nnz] int32, val[nnz] float32   (P as CSR)
 //   z[2n] uint32, u[2n] float32, gains[2n] float32           (the state)
 // in the byte order of the machine that wrote it (little-endian on every
@@ -910,8 +916,8 @@ struct CheckpointHeader {
     uint64_t payload_bytes;
     uint64_t checksum;
 };
-static_assert(sizeof(pxsne_params) == 52, "pxsne_params layout");
-static_assert(sizeof(CheckpointHeader) == 128, "checkpoint header layout");
+static_assert(sizeof(pxsne_params) == 60, "pxsne_params layout");
+static_assert(sizeof(CheckpointHeader) == 136, "checkpoint header layout");
 constexpr char kMagic[8] = {'P', 'X', 'S', 'N', 'E', 'C', 'K', 0};
 
 struct Fnv64Words {

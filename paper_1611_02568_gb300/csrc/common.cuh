@@ -20,7 +20,6 @@ constexpr int64_t kMaxN = 1 << 24;  // cell counts are exact floats below 2^24
 constexpr int kTravWarps = 8;       // warps per CTA in the traversal
 constexpr int kTravStack = 48;      // entries per warp; depth <= 3L - 2 <= 40
 constexpr int kPyrK = 5;            // pyramid levels reduced per CTA pass
-constexpr double kR = 4294967296.0; // 2^32 ulps per axis
 
 // Scalars of the iteration that live on the device so that a captured graph
 // can replay iterations without host involvement.
@@ -93,6 +92,12 @@ __device__ __forceinline__ uint32_t gather_bits16(uint32_t x) {
 // Morton key of pixel (px, py): x bits at even positions, y bits at odd ones.
 __device__ __forceinline__ uint32_t morton2(uint32_t px, uint32_t py) {
     return spread_bits16(px) | (spread_bits16(py) << 1);
+}
+
+// Extent R_d of screen axis d in ulps: r_d 2^(32 - L) (2^32 when r_d = 0,
+// the square 2^L screen).
+__host__ __device__ inline u64 screen_extent(int32_t r, int L) {
+    return r > 0 ? (u64)r << (32 - L) : (u64(1) << 32);
 }
 
 // Derived per-iteration scalars from s (called by one thread).

@@ -14,13 +14,14 @@
 
 namespace pxsne {
 
-// floor(a * 2^32 / gamma) for 0 <= a < gamma < 2^61, exactly: a double
-// estimate within one of the quotient, then a remainder correction in
-// wrapping 64-bit arithmetic (the true remainder is within +-3 gamma).
-__device__ __forceinline__ uint32_t rescale_exact(u64 a, u64 gamma, double q) {
+// floor(a * R / gamma) for 0 <= a < gamma < 2^61 and R <= 2^32, exactly: a
+// double estimate (q = R / gamma) within one of the quotient, then a
+// remainder correction in wrapping 64-bit arithmetic (the true remainder is
+// within +-3 gamma).
+__device__ __forceinline__ uint32_t rescale_exact(u64 a, u64 gamma, double q, u64 R) {
     u64 q0 = (u64)((double)a * q);
-    if (q0 > 0xffffffffull) q0 = 0xffffffffull;
-    i64 r = (i64)((a << 32) - q0 * gamma);
+    if (q0 > R - 1ull) q0 = R - 1ull;
+    i64 r = (i64)(a * R - q0 * gamma);
 #pragma unroll 1
     for (int k = 0; k < 4 && r < 0; k++) { q0--; r += (i64)gamma; }
 #pragma unroll 1
@@ -28,7 +29,7 @@ __device__ __forceinline__ uint32_t rescale_exact(u64 a, u64 gamma, double q) {
     return (uint32_t)q0;
 }
 
-__global__ void k_snap_hist(int n, int L, int rescale, float theta,
+__global__ void k_snap_hist(int n, int L, int rescale, float theta, u64 Rx, u64 Ry,
                             const longlong2 *__restrict__ zhat, uint2 *__restrict__ z,
                             const uint32_t *__restrict__ perm, uint32_t *__restrict__ rank,
                             uint32_t *__restrict__ cnt, u64 *__restrict__ sx,
@@ -45,16 +46,16 @@ __global__ void k_snap_hist(int n, int L, int rescale, float theta,
         mny = sc->mm[par][1];
         gx = (u64)(sc->mm[par][2] - mnx) + 1ull;
         gy = (u64)(sc->mm[par][3] - mny) + 1ull;
-        qx = kR / (double)gx;
-        qy = kR / (double)gy;
+        qx = (double)Rx / (double)gx;
+        qy = (double)Ry / (double)gy;
         if (tid == 0) {
             sc->n_accept = 0ull;
             sc->n_test = 0ull;
             sc->n_steps = 0ull;
             sc->n_nodes = 0ull;
-            // Eq. beta_scaling carried as s_d <- s_d * gamma_d / 2^32
-            sc->s[0] = sc->s[0] * ldexp((double)gx, -32);
-            sc->s[1] = sc->s[1] * ldexp((double)gy, -32);
+            // Eq. beta_scaling carried as s_d <- (s_d * gamma_d) / R_d
+            sc->s[0] = (sc->s[0] * (double)gx) / (double)Rx;
+            sc->s[1] = (sc->s[1] * (double)gy) / (double)Ry;
             derive_scalars(sc, theta, L);
             sc->mm[par ^ 1][0] = 0x7fffffffffffffffll;
             sc->mm[par ^ 1][1] = 0x7fffffffffffffffll;
@@ -79,8 +80,8 @@ __global__ void k_snap_hist(int n, int L, int rescale, float theta,
         i = perm[tid];
         if (rescale) {
             const longlong2 h = zhat[i];
-            zx = rescale_exact((u64)(h.x - mnx), gx, qx);
-            zy = rescale_exact((u64)(h.y - mny), gy, qy);
+            zx = rescale_exact((u64)(h.x - mnx), gx, qx, Rx);
+            zy = rescale_exact((u64)(h.y - mny), gy, qy, Ry);
             z[i] = make_uint2(zx, zy);
             zp[ainv[i]] = make_uint2(zx, zy);  // the attraction's copy
         } else {
@@ -548,7 +549,9 @@ cudaError_t launch_snap(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
         if ((e = cudaMemsetAsync(c->leaf_sy, 0, leaves * sizeof(u64), st))) return e;
     }
     const int n = (int)c->n;
-    k_snap_hist<<<(n + 255) / 256, 256, 0, st>>>(n, L, rescale ? 1 : 0, c->p.theta, c->zhat,
+    k_snap_hist<<<(n + 255) / 256, 256, 0, st>>>(n, L, rescale ? 1 : 0, c->p.theta,
+                                                 screen_extent(c->p.screen_x, L),
+                                                 screen_extent(c->p.screen_y, L), c->zhat,
                                                  c->z, c->perm, c->rank, c->leaf_cnt,
                                                  sums ? c->leaf_sx : nullptr,
                                                  sums ? c->leaf_sy : nullptr, c->sc, c->ainv,
@@ -653,15 +656,16 @@ __global__ void k_minmax_y0(int n, const float2 *__restrict__ Y, uint32_t *mm,
 }
 
 // Eq. z1/z2 mapping of the initial embedding onto the fixed-point screen (FP64).
-__global__ void k_map_y0(int n, int L, float theta, const float2 *__restrict__ Y,
+__global__ void k_map_y0(int n, int L, float theta, double Rx, double Ry,
+                         const float2 *__restrict__ Y,
                          const uint32_t *__restrict__ mm, uint2 *__restrict__ z,
                          float2 *__restrict__ u, float2 *__restrict__ gains, DevScalars *sc) {
     const double mnx = (double)key2f(mm[0]), mny = (double)key2f(mm[1]);
     const double rx = (double)key2f(mm[2]) - mnx, ry = (double)key2f(mm[3]) - mny;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) {
-        sc->s[0] = rx > 0.0 ? rx / kR : 1.0 / kR;
-        sc->s[1] = ry > 0.0 ? ry / kR : 1.0 / kR;
+        sc->s[0] = rx > 0.0 ? rx / Rx : 1.0 / Rx;
+        sc->s[1] = ry > 0.0 ? ry / Ry : 1.0 / Ry;
         derive_scalars(sc, theta, L);
         sc->t = 0;
         sc->Z = 0.0;
@@ -676,12 +680,12 @@ __global__ void k_map_y0(int n, int L, float theta, const float2 *__restrict__ Y
     const float2 y = Y[i];
     uint32_t zx = 0u, zy = 0u;
     if (rx > 0.0) {
-        const double q = floor(((double)y.x - mnx) * kR / rx);
-        zx = q >= kR - 1.0 ? 0xffffffffu : (uint32_t)q;
+        const double q = floor(((double)y.x - mnx) * Rx / rx);
+        zx = q >= Rx - 1.0 ? (uint32_t)(Rx - 1.0) : (uint32_t)q;
     }
     if (ry > 0.0) {
-        const double q = floor(((double)y.y - mny) * kR / ry);
-        zy = q >= kR - 1.0 ? 0xffffffffu : (uint32_t)q;
+        const double q = floor(((double)y.y - mny) * Ry / ry);
+        zy = q >= Ry - 1.0 ? (uint32_t)(Ry - 1.0) : (uint32_t)q;
     }
     z[i] = make_uint2(zx, zy);
     u[i] = make_float2(0.f, 0.f);
@@ -700,6 +704,8 @@ cudaError_t launch_init_map(pxsne_ctx *c, const float *Y0dev, uint32_t *mm_scrat
         n, reinterpret_cast<const float2 *>(Y0dev), mm_scratch, c->sc);
     if ((e = cudaGetLastError())) return e;
     k_map_y0<<<(n + 255) / 256, 256, 0, st>>>(n, c->L, c->p.theta,
+                                              (double)screen_extent(c->p.screen_x, c->L),
+                                              (double)screen_extent(c->p.screen_y, c->L),
                                               reinterpret_cast<const float2 *>(Y0dev),
                                               mm_scratch, c->z, c->u, c->gains, c->sc);
     return cudaGetLastError();

@@ -59,8 +59,10 @@ MUTANTS = [
     ("init: extremes taken over the other axis", C_SRC,
      "double v = Y0[2 * i + d];", "double v = Y0[2 * i + (1 - d)];"),
     ("init: ceiling in place of the floor", C_SRC,
-     "double q = floor((Y0[2 * i + d] - mn) * ORC_R / range);",
-     "double q = ceil((Y0[2 * i + d] - mn) * ORC_R / range);"),
+     "double q = floor((Y0[2 * i + d] - mn) * Rd / range);",
+     "double q = ceil((Y0[2 * i + d] - mn) * Rd / range);"),
+    ("init: extent of the other axis", C_SRC,
+     "const double Rd = R[d];", "const double Rd = R[1 - d];"),
     ("init: zero-extent axis off the origin", C_SRC,
      "for (int64_t i = 0; i < n; i++) z[2 * i + d] = 0u;",
      "for (int64_t i = 0; i < n; i++) z[2 * i + d] = 1u;"),
@@ -161,14 +163,23 @@ MUTANTS = [
     ("run: criterion form not passed to the repulsion", C_SRC,
      "p->theta, p->crit_mode, p->centre_mode,\n                             cnt, sx, sy",
      "p->theta, 0, p->centre_mode,\n                             cnt, sx, sy"),
-    ("run: screen rescale skipped", C_SRC, "        orc_rescale(n, zhat, z, s);\n    }", "    }"),
+    ("run: screen rescale skipped", C_SRC, "        orc_rescale_screen(n, zhat, R, z, s);\n    }",
+     "    }"),
+    ("run: screen extent of y used for both axes", C_SRC,
+     "const int32_t r[2] = {p->rx, p->ry};", "const int32_t r[2] = {p->ry, p->ry};"),
+    ("run: screen extent a level too fine", C_SRC,
+     "ldexp((double)r[d], 32 - p->L)", "ldexp((double)r[d], 31 - p->L)"),
     # screen rescale (Sec. 4.2, Eq. beta_scaling)
     ("rescale: compensation of s not applied", C_SRC,
-     "s[d] = s[d] * ldexp((double)gamma, -32);", ""),
+     "s[d] = (s[d] * (double)gamma) / R[d];", ""),
+    ("rescale: compensation by 2^32 whatever the screen", C_SRC,
+     "s[d] = (s[d] * (double)gamma) / R[d];", "s[d] = (s[d] * (double)gamma) / 4294967296.0;"),
+    ("rescale: extent of the other axis", C_SRC,
+     "const uint64_t Rd = (uint64_t)R[d];", "const uint64_t Rd = (uint64_t)R[1 - d];"),
     ("rescale: both axes' extremes from x", C_SRC,
      "int64_t mn = zhat[d], mx = zhat[d];", "int64_t mn = zhat[0], mx = zhat[0];"),
     ("rescale: offset from the maximum", C_SRC,
-     "(uint64_t)(zhat[2 * i + d] - mn) << 32", "(uint64_t)(mx - zhat[2 * i + d]) << 32"),
+     "(uint64_t)(zhat[2 * i + d] - mn) * Rd", "(uint64_t)(mx - zhat[2 * i + d]) * Rd"),
     # KL (Eq. cost_func)
     ("kl: q not normalised by Z", C_SRC,
      "double q = 1.0 / ((1.0 + dx * dx + dy * dy) * Z);",

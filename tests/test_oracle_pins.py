@@ -931,3 +931,95 @@ def test_stored_large_kl_targets_describe_their_workloads():
         q = g["kl_quarters"]
         assert len(q) == 4 and q[-1] == g["kl"] and all(a > b > 0 for a, b in zip(q, q[1:]))
         assert 90 * n <= g["nnz"] <= 2 * 90 * n
+
+
+SCREENS = [(10, 768, 1024), (9, 300, 512), (7, 128, 96), (11, 2048, 2048)]
+
+
+@pytest.mark.parametrize("L,rx,ry", SCREENS)
+def test_screen_rescale_big_integer_arithmetic(L, rx, ry):
+    """Sec. 4.2 on an r_x x r_y screen (per-axis r_d, the padded 2^L root):
+    z_d = floor((zhat_d - min) R_d / gamma_d), R_d = r_d 2^(32-L), exactly;
+    s_d <- (s_d gamma_d) / R_d; pixels span exactly 0 .. r_d - 1."""
+    rng = np.random.default_rng(L + rx)
+    n = 400
+    zhat = np.stack([rng.integers(-2 ** 40, 2 ** 41, n), rng.integers(-9, 2 ** 26, n)], 1)
+    zhat[0] = (-(2 ** 58), 2 ** 58)            # the widest range a clamped step makes
+    R = oracle.screen_R(L, rx, ry)
+    assert list(R) == [rx * 2 ** (32 - L), ry * 2 ** (32 - L)]
+    s = np.array([1e-9, 3e-8])
+    z, s2 = oracle.rescale(zhat, s, R)
+    F = 32 - L
+    for d, r in enumerate((rx, ry)):
+        Rd = r << F
+        mn, mx = int(zhat[:, d].min()), int(zhat[:, d].max())
+        gamma = mx - mn + 1
+        assert [int(v) for v in z[:, d]] == [(int(v) - mn) * Rd // gamma for v in zhat[:, d]]
+        assert s2[d] == (s[d] * float(gamma)) / float(Rd)
+        assert (z[:, d] >> F).min() == 0 and (z[:, d] >> F).max() == r - 1
+        assert int(z[:, d].max()) < Rd
+
+
+@pytest.mark.parametrize("L,rx,ry", SCREENS[:3])
+def test_screen_init_is_the_floor_of_the_exact_map(L, rx, ry):
+    # Eq. z1 with R_d = r_d 2^(32-L): extremes at 0 and R_d - 1, pixels 0 .. r_d - 1
+    from fractions import Fraction
+    rng = np.random.default_rng(31)
+    Y = rng.standard_normal((1500, 2)) * 2.0 - 0.5
+    R = oracle.screen_R(L, rx, ry)
+    z, s = oracle.init_fx(Y, R)
+    F = 32 - L
+    for d, r in enumerate((rx, ry)):
+        Rd = r << F
+        mn, mx = Fraction(Y[:, d].min()), Fraction(Y[:, d].max())
+        assert s[d] == (Y[:, d].max() - Y[:, d].min()) / Rd
+        assert int(z[:, d].min()) == 0 and int(z[:, d].max()) == Rd - 1
+        assert (z[:, d] >> F).max() == r - 1
+        off = 0
+        for i in range(0, Y.shape[0], 3):
+            t = (Fraction(Y[i, d]) - mn) * Rd / (mx - mn)
+            exact = min(Rd - 1, t.numerator // t.denominator)
+            if int(z[i, d]) != exact:
+                frac = t - (t.numerator // t.denominator)
+                assert min(frac, 1 - frac) < Fraction(1, 2 ** 18), (i, d)
+                off += 1
+        assert off <= 3
+
+
+def test_square_screen_is_the_default_extent():
+    rng = np.random.default_rng(32)
+    Y = rng.standard_normal((300, 2))
+    zhat = rng.integers(-2 ** 33, 2 ** 33, (300, 2))
+    for L in (5, 11):
+        R = oracle.screen_R(L)
+        assert list(R) == [2.0 ** 32, 2.0 ** 32]
+        for a, b in zip(oracle.init_fx(Y), oracle.init_fx(Y, R)):
+            assert np.array_equal(a, b)
+        for a, b in zip(oracle.rescale(zhat, [1e-3, 2e-3]), oracle.rescale(zhat, [1e-3, 2e-3], R)):
+            assert np.array_equal(a, b)
+
+
+def test_screen_run_step_is_the_composition_of_its_parts():
+    # the run on a 100 x 128 screen of the padded 2^7 root: one step = the
+    # pinned parts with the screen's per-axis extents in the rescale
+    n = 300
+    rng = np.random.default_rng(35)
+    A = (rng.random((n, n)) < 0.05) * rng.random((n, n))
+    A = A + A.T
+    np.fill_diagonal(A, 0)
+    P = _dense_csr(A / A.sum())
+    prm = oracle.Params(L=7, rx=100, ry=128)
+    Y = rng.standard_normal((n, 2))
+    st = oracle.State.from_y0(Y, prm.R())
+    ref = st.copy()
+    oracle.run(P, st, prm, 1)
+    Fr, Zi, _ = oracle.bh_repulsion(ref.z, ref.s, prm.L, prm.theta)
+    Fa = oracle.attraction(P, ref.z, ref.s)
+    zhat, _ = oracle.update(ref.z, ref.s, Fa, Fr, float(np.cumsum(Zi)[-1]), prm.exag, prm.mom0,
+                            prm.eta, ref.u, ref.gains, min_gain=prm.min_gain)
+    zr, sr = oracle.rescale(zhat, ref.s, prm.R())
+    assert np.array_equal(st.z, zr) and np.array_equal(st.s, sr)
+    # and a longer run keeps every point on the 100 x 128 pixels, spanning them
+    oracle.run(P, st, prm, 40)
+    px, py = st.z[:, 0] >> 25, st.z[:, 1] >> 25
+    assert px.min() == 0 and px.max() == 99 and py.min() == 0 and py.max() == 127
