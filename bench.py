@@ -374,6 +374,32 @@ def geometric_centre_study(px, X, Y0, params_kw, steps, com, stream, torch):
     return out
 
 
+def approx_knn_study(px, ctx, X, params, n, probes=(256, 1024), sample=20000):
+    """P construction with the approximate neighbour search (knn_probe = W
+    candidate tiles per query tile) beside the exact one of ctx: P time, search
+    time and the recall of the exact lists on a row sample."""
+    import dataclasses
+    rows = np.random.default_rng(5).choice(n, min(sample, n), replace=False)
+    idx_e, _, _ = ctx.get_knn()
+    exact = idx_e[rows]
+    out = {"exact": {"knn_ms": ctx.knn_time_ms()}}
+    for W in probes:
+        p = dataclasses.replace(params, knn_probe=W)
+        with px.Context(p) as c:
+            import torch
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c.affinities(X)
+            tp = time.perf_counter() - t0
+            idx, _, _ = c.get_knn()
+            got = idx[rows]
+            hits = sum(len(np.intersect1d(a, b, assume_unique=True)) for a, b in zip(got, exact))
+            out[str(W)] = {"p_construction_s": tp, "knn_ms": c.knn_time_ms(),
+                           "recall_vs_exact": hits / exact.size}
+    out["sample_rows"] = int(len(rows))
+    return out
+
+
 def warmstart_experiment(px, ctx, X, Y0, args, torch):
     """Learned warm start, on ctx's P (the bench workload).
 
@@ -571,6 +597,9 @@ def run_gpu(args):
            "peak_source": f"bf16_tflops of MEASURED_PEAKS.json ({pk_kind})",
            "exact_rerank_per_row": kx / n, "insertions_per_row": ki / n,
            "tile_pairs_skipped": kskip / kpairs if kpairs else None}
+    knn_approx = None
+    if rank == 0 and not args.no_studies:
+        knn_approx = approx_knn_study(px, ctx, X, params, n)
     ctx.init(Y0)
     ctx.step(max(args.warmup, 3) if args.warmup >= 0 else 3)  # graph capture + warm-up
     ctx.sync()
@@ -766,6 +795,7 @@ def run_gpu(args):
                                                 "lanes_per_step": int(lvc[l, 0]) / int(lvc[l, 2])}
                                        for l in range(1, lvc.shape[0]) if lvc[l, 2]}},
             "profiled_total_ms": prof_total, "p_construction_s": p_seconds, "knn": knn,
+            "knn_approx": knn_approx,
             "along_schedule": along,
             "kl_after_timed": kl_after,
             "clocks": ck, "e2e": e2e, "cpu_baseline": cpu, "warmstart": warm,

@@ -86,6 +86,8 @@ typedef struct pxsne_params {
     int32_t centre_mode;     /* 0: cell centre of mass; 1: geometric cell centre (Sec. 4.1) */
     int32_t screen_x;        /* screen width r_1 in pixels, 1 <= r_1 <= 2^L; 0: 2^L */
     int32_t screen_y;        /* screen height r_2 in pixels, 1 <= r_2 <= 2^L; 0: 2^L */
+    int32_t knn_probe;       /* 0: exact neighbour search; W in [1, 1792]: approximate
+                                (see pxsne_affinities) */
 } pxsne_params;
 
 void pxsne_default_params(pxsne_params *p);
@@ -109,6 +111,15 @@ const char *pxsne_last_error(const pxsne_ctx *ctx);
  *   - p_{j|i} proportional to exp(-beta_i d2_ij) with beta_i set by bisection
  *     so that each row's entropy is ln(perplexity);
  *   - p_ij = (p_{j|i} + p_{i|j}) / (2n) on the union pattern, stored as CSR.
+ * With knn_probe = W > 0 the neighbour search is approximate (the role of
+ * Sec. 4.3's random-projection trees): each pivot cell of the search's
+ * locality order is split further by random-projection hyperplanes (each
+ * bisecting two of the segment's rows) into tiles of 128 nearby rows, and the
+ * rows of a tile are searched only against the W tiles with the smallest
+ * triangle-inequality bound |c_q - c_t| - r_t (centroids c, radii r), their
+ * own tile first, with exact FP32 distances; the neighbour lists are then the
+ * k nearest within those tiles (tensor-core search only; the FP32 check path
+ * stays exact).  The lists may differ between runs.
  * X: host or device, row-major n x D float32, 2 <= n <= 2^24, 1 <= D <= 256
  * (the shared-memory tiles of the search bound D further for large k; an
  * unsupported size returns an error).  perplexity <= 0 uses the
@@ -152,7 +163,7 @@ int pxsne_step(pxsne_ctx *ctx, int32_t iters);
  *
  * File layout (byte order of the writing host, little-endian on every
  * supported one): a 136-byte header {char magic[8] = "PXSNECK\0"; uint32
- * version = 1; uint32 header bytes = 136; pxsne_params (60 bytes); uint32 0;
+ * version = 1; uint32 header bytes = 136; pxsne_params (64 bytes);
  * int64 n, nnz; int32 t, 0; double s[2]; uint64 payload bytes; uint64
  * checksum}, then row_ptr[n+1] int64, col[nnz] int32, val[nnz] float32,
  * z[2n] uint32, u[2n] float32, gains[2n] float32.  The checksum is FNV-1a

@@ -45,7 +45,8 @@ class _CParams(C.Structure):
                 ("momentum0", C.c_float), ("momentum1", C.c_float),
                 ("momentum_switch", C.c_int32), ("min_gain", C.c_float), ("k", C.c_int32),
                 ("perplexity", C.c_float), ("init_sigma", C.c_float),
-                ("centre_mode", C.c_int32), ("screen_x", C.c_int32), ("screen_y", C.c_int32)]
+                ("centre_mode", C.c_int32), ("screen_x", C.c_int32), ("screen_y", C.c_int32),
+                ("knn_probe", C.c_int32)]
 
 
 @dataclass
@@ -66,6 +67,7 @@ class Params:
     centre_mode: int = 0
     screen_x: int = 0      # pixels of the screen's width (0: 2^log2_r)
     screen_y: int = 0      # pixels of its height (0: 2^log2_r)
+    knn_probe: int = 0     # 0: exact neighbour search; W: approximate, W tiles per tile
 
     def c(self):
         return _CParams(*[getattr(self, f.name) for f in fields(self)])

@@ -492,6 +492,182 @@ __global__ void k_gather_rows(int64_t n, int D, const uint32_t *__restrict__ ord
     if (d == 0) ns[r] = nrm[i];
 }
 
+// ---- random-projection refinement of the locality order, and the
+// approximate search's per-tile candidate lists.
+//
+// Every segment of the order (at first a pivot cell) is split in two by the
+// hyperplane that bisects two of its rows, picked by a hash of the segment and
+// the level (the random-projection trees of Sec. 4.3, with the bisecting
+// splits of LargeVis and Annoy); the rows on the first one's side go first.
+// Segments of at most kTcRows rows stay as they are, so the tiles of 128
+// consecutive rows end up spatially compact, their radii small and the tile
+// bound of the search tight.  The order inside a pivot cell comes from
+// atomics, so the splits may differ between runs: the exact search's lists do
+// not depend on them, the approximate search's may.
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// seg[r] = [start, end) of the pivot cell of the row at position r
+__global__ void k_seg_init(int64_t n, const uint32_t *__restrict__ order,
+                           const uint32_t *__restrict__ cell, const uint32_t *__restrict__ cstart,
+                           int2 *__restrict__ seg) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const uint32_t c = cell[order[r]];
+    seg[r] = make_int2((int)cstart[c], (int)cstart[c + 1]);
+}
+
+// flag[r] = 1 if the row at position r lies on the side of its segment's
+// first split row (or its segment is not split), else 0
+__global__ void k_rp_side(int64_t n, int D, const float *__restrict__ X,
+                          const uint32_t *__restrict__ order, const int2 *__restrict__ seg,
+                          int level, uint32_t *__restrict__ flag) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int2 sg = seg[r];
+    const int size = sg.y - sg.x;
+    if (size <= kTcRows) {
+        flag[r] = 1u;
+        return;
+    }
+    const uint32_t h = mix32((uint32_t)sg.x * 0x9e3779b9u ^ (uint32_t)(level * 0x632be5abu));
+    const int oa = (int)(h % (uint32_t)size);
+    const int ob = (oa + 1 + (int)(mix32(h + 1u) % (uint32_t)(size - 1))) % size;
+    const float *xa = X + (int64_t)order[sg.x + oa] * D;
+    const float *xb = X + (int64_t)order[sg.x + ob] * D;
+    const float *xi = X + (int64_t)order[r] * D;
+    float p = 0.f;
+    for (int d = 0; d < D; d++) {
+        const float u = __ldg(xa + d), v = __ldg(xb + d);
+        p = fmaf(__ldg(xi + d) - 0.5f * (u + v), u - v, p);
+    }
+    flag[r] = p >= 0.f ? 1u : 0u;
+}
+
+// Stable partition of every split segment by flag (pref = exclusive scan of
+// flag over all positions): first-side rows first; each half becomes a
+// segment.  A segment that every row (or none) fell on one side of is kept
+// whole and split again at the next level with other rows.
+__global__ void k_rp_scatter(int64_t n, const uint32_t *__restrict__ order,
+                             const int2 *__restrict__ seg, const uint32_t *__restrict__ flag,
+                             const int64_t *__restrict__ pref, uint32_t *__restrict__ order2,
+                             int2 *__restrict__ seg2) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int2 sg = seg[r];
+    const int64_t size = sg.y - sg.x;
+    const int64_t ps = pref[sg.x];
+    const int64_t lc = pref[sg.y] - ps;
+    if (size <= kTcRows || lc == 0 || lc == size) {
+        order2[r] = order[r];
+        seg2[r] = sg;
+        return;
+    }
+    const int64_t before = pref[r] - ps;  // first-side rows before r in its segment
+    int64_t pos;
+    int2 ns;
+    if (flag[r]) {
+        pos = sg.x + before;
+        ns = make_int2(sg.x, sg.x + (int)lc);
+    } else {
+        pos = sg.x + lc + (r - sg.x - before);
+        ns = make_int2(sg.x + (int)lc, sg.y);
+    }
+    order2[pos] = order[r];
+    seg2[pos] = ns;
+}
+
+// cand[q W .. q W + W): the W tiles of smallest bound |c_q - c_t| - r_t (the
+// query tile's own radius is common to all), the own tile first, ascending by
+// (bound, tile).  One CTA per query tile keeps the best in shared memory,
+// sorting (bitonic) whenever the buffer may not hold another chunk.
+constexpr int kCandThreads = 256;
+constexpr int kCandCap = 2048;  // buffer entries; W <= kCandCap - kCandThreads
+
+__device__ void cand_sort(float *b, int *t, int cnt) {
+    for (int i = cnt + threadIdx.x; i < kCandCap; i += kCandThreads) {
+        b[i] = INFINITY;
+        t[i] = 0x7fffffff;
+    }
+    __syncthreads();
+    for (int k = 2; k <= kCandCap; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < kCandCap; i += kCandThreads) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const bool gt = b[i] > b[l] || (b[i] == b[l] && t[i] > t[l]);
+                    if (gt == up) {
+                        const float fb = b[i];
+                        b[i] = b[l];
+                        b[l] = fb;
+                        const int ft = t[i];
+                        t[i] = t[l];
+                        t[l] = ft;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kCandThreads)
+    k_tile_cands(int64_t T, int Dp, const float *__restrict__ cent, const float *__restrict__ rad,
+                 int W, int32_t *__restrict__ cand) {
+    __shared__ float s_b[kCandCap];
+    __shared__ int s_t[kCandCap];
+    __shared__ float s_cq[128];
+    __shared__ int s_cnt;
+    __shared__ float s_thr;
+    const int64_t qt = blockIdx.x;
+    for (int d = threadIdx.x; d < Dp; d += kCandThreads) s_cq[d] = cent[qt * Dp + d];
+    if (threadIdx.x == 0) {
+        s_cnt = 0;
+        s_thr = INFINITY;
+    }
+    __syncthreads();
+    for (int64_t t0 = 0; t0 < T; t0 += kCandThreads) {
+        const int64_t t = t0 + threadIdx.x;
+        if (t < T) {
+            float b = -INFINITY;
+            if (t != qt) {
+                const float4 *ct = reinterpret_cast<const float4 *>(cent + t * Dp);
+                float dd = 0.f;
+                for (int d4 = 0; d4 < Dp / 4; d4++) {
+                    const float4 c = __ldg(ct + d4);
+                    const float e0 = s_cq[4 * d4] - c.x, e1 = s_cq[4 * d4 + 1] - c.y;
+                    const float e2 = s_cq[4 * d4 + 2] - c.z, e3 = s_cq[4 * d4 + 3] - c.w;
+                    dd = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, dd))));
+                }
+                b = sqrtf(dd) - __ldg(rad + t);
+            }
+            if (b < s_thr) {
+                const int slot = atomicAdd(&s_cnt, 1);
+                s_b[slot] = b;
+                s_t[slot] = (int)t;
+            }
+        }
+        __syncthreads();
+        if (s_cnt > kCandCap - kCandThreads) {
+            cand_sort(s_b, s_t, s_cnt);
+            if (threadIdx.x == 0) {
+                s_cnt = W;
+                s_thr = s_b[W - 1];
+            }
+            __syncthreads();
+        }
+    }
+    cand_sort(s_b, s_t, s_cnt);
+    for (int i = threadIdx.x; i < W; i += kCandThreads) cand[qt * W + i] = s_t[i];
+}
+
 // A neighbour-list entry; (d, j) orders by distance, then by index.
 struct __align__(8) KnnEntry {
     float d;
@@ -516,6 +692,8 @@ struct KnnTcArgs {
     u64 *stats;
     const float *cent;    // per tile: centroid of its rows (Dp floats, FP32)
     const float *rad;     // per tile: an upper bound of |x - centroid| over its rows
+    const int32_t *cand;  // approximate search: per query tile its W candidate tiles
+    int W;                //   (own tile first); NULL: every tile (the exact search)
 };
 
 // The i-th candidate tile a CTA visits: its own, then alternately the next
@@ -604,12 +782,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
         int64_t n_sf = 0, n_hf = 0;  // stage and h copies issued (kept tiles 0 ..)
         // the tiles are judged 32 at a time, one per lane; the kept ones are
         // then issued in order
-        for (int64_t i0 = 0; i0 <= T && !fail; i0 += 32) {
+        // candidate tiles: every tile outward from the own one, or (the
+        // approximate search) the W listed for this query tile
+        const int64_t NT = a.cand ? (int64_t)a.W : T;
+        for (int64_t i0 = 0; i0 <= NT && !fail; i0 += 32) {
             // (one reading of the abort flag for the whole warp)
             if (__shfl_sync(0xffffffffu, s_abort, 0)) break;
             const int64_t il = i0 + lane;
-            const bool in = il < T;
-            const int64_t tl = in ? knn_tile_at(qt, il, T) : 0;
+            const bool in = il < NT;
+            const int64_t tl =
+                in ? (a.cand ? (int64_t)__ldg(a.cand + qt * a.W + il) : knn_tile_at(qt, il, T)) : 0;
             float dd = 0.f;
             if (in) {
                 const float4 *ct = reinterpret_cast<const float4 *>(a.cent + tl * a.Dp);
@@ -626,7 +808,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             n_skip += (u64)__popc(__ballot_sync(0xffffffffu, skip));
             // kept tiles of this block, and the end mark after the last block
             unsigned keep = __ballot_sync(0xffffffffu, in && !skip);
-            const bool last_block = i0 + 32 > T;
+            const bool last_block = i0 + 32 > NT;
             while (keep || last_block) {
                 const bool end = keep == 0u;  // (only in the last block)
                 int64_t t = -1;
@@ -1134,6 +1316,50 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
                                  cudaMemcpyHostToDevice, st)))
             return e;
         k_cell_scatter<<<ablocks, 256, 0, st>>>(n, cell, ccnt, order);
+        const int probe = c->p.knn_probe;
+        {
+            // split every cell by random projections until segments hold at
+            // most one tile's rows: compact tiles, tighter tile bounds (and,
+            // for the approximate search, a meaningful nearest-tile order)
+            uint32_t biggest = 0u;
+            for (int q = 0; q <= m; q++) {
+                const uint32_t end = q < m ? hc[(size_t)q + 1] : (uint32_t)n;
+                biggest = std::max(biggest, end - hc[(size_t)q]);
+            }
+            int levels = 4;
+            while (((uint64_t)kTcRows << (levels - 4)) < biggest) levels++;
+            uint32_t *cst = nullptr, *order2 = nullptr, *flag = nullptr;
+            int2 *seg = nullptr, *seg2 = nullptr;
+            int64_t *pref = nullptr;
+            if ((e = cudaMallocAsync(&cst, (size_t)(m + 2) * sizeof(uint32_t), st))) return e;
+            if ((e = cudaMallocAsync(&order2, (size_t)n * sizeof(uint32_t), st))) return e;
+            if ((e = cudaMallocAsync(&flag, (size_t)n * sizeof(uint32_t), st))) return e;
+            if ((e = cudaMallocAsync(&seg, (size_t)n * sizeof(int2), st))) return e;
+            if ((e = cudaMallocAsync(&seg2, (size_t)n * sizeof(int2), st))) return e;
+            if ((e = cudaMallocAsync(&pref, (size_t)(n + 1) * sizeof(int64_t), st))) return e;
+            std::vector<uint32_t> hs((size_t)m + 2);
+            for (int q = 0; q <= m; q++) hs[(size_t)q] = hc[(size_t)q];
+            hs[(size_t)m + 1] = (uint32_t)n;
+            if ((e = cudaMemcpyAsync(cst, hs.data(), hs.size() * sizeof(uint32_t),
+                                     cudaMemcpyHostToDevice, st)))
+                return e;
+            k_seg_init<<<ablocks, 256, 0, st>>>(n, order, cell, cst, seg);
+            for (int lv = 0; lv < levels; lv++) {
+                k_rp_side<<<ablocks, 256, 0, st>>>(n, D, Xdev, order, seg, lv, flag);
+                if ((e = cudaGetLastError())) return e;
+                if ((e = scan_u32_to_i64(flag, n, pref, st))) return e;
+                k_rp_scatter<<<ablocks, 256, 0, st>>>(n, order, seg, flag, pref, order2, seg2);
+                if ((e = cudaGetLastError())) return e;
+                std::swap(order, order2);
+                std::swap(seg, seg2);
+            }
+            cudaFreeAsync(cst, st);
+            cudaFreeAsync(order2, st);
+            cudaFreeAsync(flag, st);
+            cudaFreeAsync(seg, st);
+            cudaFreeAsync(seg2, st);
+            cudaFreeAsync(pref, st);
+        }
         k_gather_rows<<<(unsigned)((n * D + 255) / 256), 256, 0, st>>>(n, D, order, Xdev, nrm, Xs,
                                                                        ns);
         if ((e = cudaGetLastError())) return e;
@@ -1180,10 +1406,22 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         ka.stats = &c->sc->knn_exact;
         ka.cent = cent;
         ka.rad = rad;
+        ka.cand = nullptr;
+        ka.W = 0;
+        int32_t *cand = nullptr;
+        if (probe > 0) {
+            const int W = (int)std::min<int64_t>(probe, T);
+            if ((e = cudaMallocAsync(&cand, (size_t)T * W * sizeof(int32_t), st))) return e;
+            k_tile_cands<<<(unsigned)T, kCandThreads, 0, st>>>(T, Dp, cent, rad, W, cand);
+            if ((e = cudaGetLastError())) return e;
+            ka.cand = cand;
+            ka.W = W;
+        }
         if ((e = knn_mark(c, 0, st))) return e;
         k_knn_tc<<<(unsigned)T, kTcThreads, smem_tc, st>>>(ka);
         if ((e = cudaGetLastError())) return e;
         if ((e = knn_mark(c, 1, st))) return e;
+        if (cand) cudaFreeAsync(cand, st);
         cudaFreeAsync(img, st);
         cudaFreeAsync(HG, st);
         cudaFreeAsync(cent, st);

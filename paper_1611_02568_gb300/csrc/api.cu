@@ -99,6 +99,8 @@ int check_params(const pxsne_params *p) {
     if (p->screen_x < 0 || p->screen_x > side || p->screen_y < 0 || p->screen_y > side)
         return fail(nullptr, PXSNE_E_ARG, "screen %d x %d outside [1, %d] (0: %d)", p->screen_x,
                     p->screen_y, side, side);
+    if (p->knn_probe < 0 || p->knn_probe > 1792)
+        return fail(nullptr, PXSNE_E_ARG, "knn_probe = %d outside [0, 1792]", p->knn_probe);
     return PXSNE_OK;
 }
 
@@ -272,6 +274,7 @@ void pxsne_default_params(pxsne_params *p) {
     p->centre_mode = 0;
     p->screen_x = 0;
     p->screen_y = 0;
+    p->knn_probe = 0;
 }
 
 int pxsne_create(pxsne_ctx **out, const pxsne_params *p, void *stream) {
@@ -909,14 +912,13 @@ struct CheckpointHeader {
     uint32_t version;       // 1
     uint32_t header_bytes;  // sizeof(CheckpointHeader)
     pxsne_params params;    // the context's parameters and schedule
-    uint32_t pad0;
     int64_t n, nnz;
     int32_t t, pad1;
     double s[2];
     uint64_t payload_bytes;
     uint64_t checksum;
 };
-static_assert(sizeof(pxsne_params) == 60, "pxsne_params layout");
+static_assert(sizeof(pxsne_params) == 64, "pxsne_params layout");
 static_assert(sizeof(CheckpointHeader) == 136, "checkpoint header layout");
 constexpr char kMagic[8] = {'P', 'X', 'S', 'N', 'E', 'C', 'K', 0};
 

@@ -1,0 +1,58 @@
+"""The approximate neighbour search (knn_probe = W: each tile of 128 query rows
+is searched against only its W candidate tiles of smallest bound), on the
+bench workload's recipe (gmm128, D = 128) at n = 1,000,000.  Bars: every
+returned neighbour is a distinct other row, its distance is the exact FP32
+one, rows are sorted; the recall of the oracle's exact neighbour sets of
+sampled rows (FP64 brute force; neighbours within 2e-5 of the k-th distance
+may go either way) grows with W and is at least 0.9 at W = 1024.  (On these
+full-rank Gaussian mixtures a point's nearest neighbours spread over its whole
+cluster, so no small set of tiles holds them: the exact search, with the same
+random-projection tiles and the tile bound, is the default.)"""
+import numpy as np
+import pytest
+
+import datagen
+import oracle
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+K = 90
+
+
+def recall(X, idx, d2, rows, idx_o, d2_o):
+    x = X.astype(np.float64)
+    hit = tot = 0
+    for a, r in enumerate(rows):
+        got = idx[r]
+        assert len(set(got.tolist())) == K and r not in set(got.tolist())
+        ex = ((x[got] - x[r]) ** 2).sum(1)
+        np.testing.assert_allclose(d2[r], ex, rtol=1e-5, atol=1e-30)
+        assert np.all(np.diff(d2[r]) >= 0)
+        tau = d2_o[a, K - 1]
+        must = set(idx_o[a][d2_o[a] < tau * (1 - 2e-5)].tolist())
+        hit += len(must & set(got.tolist()))
+        tot += len(must)
+    return hit / tot
+
+
+def test_approximate_search_recall_grows_with_the_probe():
+    import paper_1611_02568_gb300 as px
+    from paper_1611_02568_gb300 import build
+    build.build()
+    n, L = 1_000_000, 11
+    X, _ = datagen.gmm128(seed=0, n=n)
+    rows = np.unique(np.concatenate([np.random.default_rng(11).choice(n, 40, replace=False),
+                                     [0, n - 1]]))
+    idx_o, d2_o = oracle.knn(X, K, rows=rows)
+    rec = {}
+    for W in (256, 1024):
+        with px.Context(px.Params(log2_r=L, k=K, knn_probe=W)) as ctx:
+            ctx.affinities(X)
+            ms = ctx.knn_time_ms()
+            idx, d2, _ = ctx.get_knn()
+            rec[W] = recall(X, idx, d2, rows, idx_o, d2_o)
+            _, _, val = ctx.get_P()
+        print(f"probe {W}: search {ms:.1f} ms, recall {rec[W]:.4f}")
+        # P from the approximate lists is still a distribution
+        assert abs(val.astype(np.float64).sum() - 1.0) < 1e-5
+    assert rec[1024] > rec[256] and rec[1024] >= 0.9, rec
