@@ -115,9 +115,9 @@ const char *pxsne_last_error(const pxsne_ctx *ctx);
  * Sec. 4.3's random-projection trees): each pivot cell of the search's
  * locality order is split further by random-projection hyperplanes (each
  * bisecting two of the segment's rows) into tiles of 128 nearby rows, and the
- * rows of a tile are searched only against the W tiles with the smallest
- * triangle-inequality bound |c_q - c_t| - r_t (centroids c, radii r), their
- * own tile first, with exact FP32 distances; the neighbour lists are then the
+ * rows of a tile are searched only against the W tiles whose centroids are
+ * nearest to their tile's (their own tile first), with exact FP32 distances
+ * and the exact search's tile bound; the neighbour lists are then the
  * k nearest within those tiles (tensor-core search only; the FP32 check path
  * stays exact).  The lists may differ between runs.
  * X: host or device, row-major n x D float32, 2 <= n <= 2^24, 1 <= D <= 256

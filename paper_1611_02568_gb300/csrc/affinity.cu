@@ -583,9 +583,11 @@ __global__ void k_rp_scatter(int64_t n, const uint32_t *__restrict__ order,
     seg2[pos] = ns;
 }
 
-// cand[q W .. q W + W): the W tiles of smallest bound |c_q - c_t| - r_t (the
-// query tile's own radius is common to all), the own tile first, ascending by
-// (bound, tile).  One CTA per query tile keeps the best in shared memory,
+// cand[q W .. q W + W): the W tiles whose centroids are nearest to the query
+// tile's, the own tile first, ascending by (distance, tile).  (Ranking by the
+// triangle-inequality bound |c_q - c_t| - r_t instead would put the few tiles
+// of wide radius -- outliers spread over the whole space -- ahead of the
+// query's own cluster.)  One CTA per query tile keeps the best in shared memory,
 // sorting (bitonic) whenever the buffer may not hold another chunk.
 constexpr int kCandThreads = 256;
 constexpr int kCandCap = 2048;  // buffer entries; W <= kCandCap - kCandThreads
@@ -619,8 +621,8 @@ __device__ void cand_sort(float *b, int *t, int cnt) {
 }
 
 __global__ void __launch_bounds__(kCandThreads)
-    k_tile_cands(int64_t T, int Dp, const float *__restrict__ cent, const float *__restrict__ rad,
-                 int W, int32_t *__restrict__ cand) {
+    k_tile_cands(int64_t T, int Dp, const float *__restrict__ cent, int W,
+                 int32_t *__restrict__ cand) {
     __shared__ float s_b[kCandCap];
     __shared__ int s_t[kCandCap];
     __shared__ float s_cq[128];
@@ -646,7 +648,7 @@ __global__ void __launch_bounds__(kCandThreads)
                     const float e2 = s_cq[4 * d4 + 2] - c.z, e3 = s_cq[4 * d4 + 3] - c.w;
                     dd = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, dd))));
                 }
-                b = sqrtf(dd) - __ldg(rad + t);
+                b = dd;
             }
             if (b < s_thr) {
                 const int slot = atomicAdd(&s_cnt, 1);
@@ -1412,7 +1414,7 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         if (probe > 0) {
             const int W = (int)std::min<int64_t>(probe, T);
             if ((e = cudaMallocAsync(&cand, (size_t)T * W * sizeof(int32_t), st))) return e;
-            k_tile_cands<<<(unsigned)T, kCandThreads, 0, st>>>(T, Dp, cent, rad, W, cand);
+            k_tile_cands<<<(unsigned)T, kCandThreads, 0, st>>>(T, Dp, cent, W, cand);
             if ((e = cudaGetLastError())) return e;
             ka.cand = cand;
             ka.W = W;

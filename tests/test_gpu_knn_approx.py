@@ -1,5 +1,5 @@
 """The approximate neighbour search (knn_probe = W: each tile of 128 query rows
-is searched against only its W candidate tiles of smallest bound), on the
+is searched against only the W tiles nearest by centroid), on the
 bench workload's recipe (gmm128, D = 128) at n = 1,000,000.  Bars: every
 returned neighbour is a distinct other row, its distance is the exact FP32
 one, rows are sorted; the recall of the oracle's exact neighbour sets of
