@@ -182,8 +182,9 @@ def group_bytes(n, nnz, L, nonempty=None):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from an
 # ncu capture of the current kernels, by (workload, n); emptied whenever a
 # kernel changes, until the capture is taken again
-TRAFFIC_BYTES = {}
-TRAFFIC_SOURCE = ""
+TRAFFIC_BYTES = {("gmm128", 1_000_000): {"k_bh_traverse": 45.48e6 + 1.96e6}}
+TRAFFIC_SOURCE = ("profiles/traversal_gmm128_n1M_dram.md (one-pass ncu capture of the "
+                  "9th launch, t about 2)")
 
 FLOP_TEST = 10    # offset, d^2 and criterion of one tested cell
 FLOP_ACCEPT = 10  # kernel value, N w, N w^2 and the three accumulations
@@ -686,7 +687,12 @@ def run_gpu(args):
                 "l2": {"achieved": l2_alg, "peak": mpeaks["l2_read_gbs"], "unit": "GB/s",
                        "frac": l2_alg / mpeaks["l2_read_gbs"],
                        "work": f"{RECORD_BYTES} B of cell record per tested (point, cell) "
-                               f"pair"}}
+                               f"pair (the survey's per-pair model; a warp loads each "
+                               f"record once for all its points, so the loads it issues "
+                               f"are the warp steps' records, below)",
+                       "warp_loads_GBps": nodes * 80 / sec / 1e9,
+                       "warp_loads_work": "80 B per node popped (the four children's "
+                                          "records and counts, one load each per warp)"}}
     else:
         achieved = gb[top] / (avg_ms[top] / 1e3) / 1e9
         roof = {"kernel": top, "bound": "hbm", "achieved": achieved,

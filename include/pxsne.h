@@ -331,12 +331,14 @@ int pxsne_test_bounded_wait(pxsne_ctx *ctx, int32_t polls, uint32_t *flags);
 /* Measurement (no counterpart in the paper): the peaks that the iteration's
  * rooflines are taken against, measured on the current device by plain
  * kernels timed with CUDA events on `stream` (a cudaStream_t, NULL = the
- * legacy default stream), best of five launches after one warm-up:
- *   - l2_read_gbs: read bandwidth of 16-byte loads that bypass L1 from a
- *     buffer of the largest power of two within a quarter of L2 (resident),
- *     64 passes;
+ * legacy default stream), best of five launches after one warm-up, and the
+ * best over a few launch shapes:
+ *   - l2_read_gbs: read bandwidth of 16-byte loads that bypass L1 from
+ *     buffers (resident in L2) of 1/4, 1/2 and all of the largest power of
+ *     two within a quarter of L2, 2, 4 or 8 CTAs of 512 threads per SM;
  *   - fp32_tflops / fp32_packed_tflops: 16 independent chains of FP32 FMAs
- *     per thread as scalar FMAs / as packed pairs (2 FLOP per FMA);
+ *     per thread as scalar FMAs / as packed pairs (2 FLOP per FMA), 4, 8 or
+ *     16 CTAs of 256 threads per SM;
  *   - sm_count and l2_bytes: from the device properties.
  * Any pointer may be NULL (that measurement is skipped).  Allocates and frees
  * a buffer of at most a quarter of L2.  Synchronises the stream.  Returns

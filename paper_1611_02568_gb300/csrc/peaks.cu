@@ -100,42 +100,59 @@ extern "C" int pxsne_measure_peaks(void *stream, double *l2_read_gbs, double *fp
     if (cudaMalloc(&sink, 64)) return PXSNE_E_OOM;
     int rc = PXSNE_OK;
     if (l2_read_gbs) {
-        // the largest power of two within a quarter of L2: resident after the
-        // first pass, and within one die's half of the cache
-        int64_t bytes = 1 << 20;
-        while (bytes * 2 <= (int64_t)prop.l2CacheSize / 4) bytes *= 2;
+        // buffers of 1/16, 1/8 and 1/4 of L2 (powers of two, resident after the
+        // first pass), 2, 4 or 8 CTAs of 512 threads per SM: the best of all
+        int64_t top = 1 << 20;
+        while (top * 2 <= (int64_t)prop.l2CacheSize / 4) top *= 2;
         uint4 *buf = nullptr;
-        if (cudaMalloc(&buf, bytes)) {
+        double best = 0.0;
+        if (cudaMalloc(&buf, top)) {
             rc = PXSNE_E_OOM;
         } else {
-            cudaMemsetAsync(buf, 1, bytes, st);
-            const int64_t n16 = bytes / 16;
-            const int64_t total = n16 * 64;  // 64 passes over the buffer
-            const int blocks = sms * 4;
-            double ms = 0.0;
-            auto go = [&] {
-                k_l2_read<<<blocks, 512, 0, st>>>(buf, (uint32_t)(n16 - 1), total, sink);
-            };
-            if (time_ms(st, go, 1, &ms) || time_ms(st, go, 5, &ms)) rc = PXSNE_E_CUDA;
-            else *l2_read_gbs = (double)total * 16.0 / (ms * 1e-3) / 1e9;
+            cudaMemsetAsync(buf, 1, top, st);
+            for (int64_t bytes = top / 4; bytes <= top && rc == PXSNE_OK; bytes *= 2) {
+                const int64_t n16 = bytes / 16;
+                const int64_t total = (top / 16) * 64;  // 64 passes over the largest buffer
+                for (int per_sm = 2; per_sm <= 8 && rc == PXSNE_OK; per_sm *= 2) {
+                    double ms = 0.0;
+                    auto go = [&] {
+                        k_l2_read<<<sms * per_sm, 512, 0, st>>>(buf, (uint32_t)(n16 - 1), total,
+                                                                sink);
+                    };
+                    if (time_ms(st, go, 1, &ms) || time_ms(st, go, 5, &ms)) rc = PXSNE_E_CUDA;
+                    else best = fmax(best, (double)total * 16.0 / (ms * 1e-3) / 1e9);
+                }
+            }
             cudaFree(buf);
+            if (rc == PXSNE_OK) *l2_read_gbs = best;
         }
     }
     const int iters = 4096;
-    const int blocks = sms * 8;
-    // flops per launch: threads x iterations x 8 chains x 2 lanes x 2 (FMA)
-    const double flops = (double)blocks * 256 * iters * 8 * 2 * 2;
+    // flops per launch: threads x iterations x 8 chains x 2 lanes x 2 (FMA);
+    // 4, 8 or 16 CTAs of 256 threads per SM, the best
     if (rc == PXSNE_OK && fp32_tflops) {
-        double ms = 0.0;
-        auto go = [&] { k_ffma<false><<<blocks, 256, 0, st>>>(iters, 1.0f, (float *)sink); };
-        if (time_ms(st, go, 1, &ms) || time_ms(st, go, 5, &ms)) rc = PXSNE_E_CUDA;
-        else *fp32_tflops = flops / (ms * 1e-3) / 1e12;
+        double best = 0.0;
+        for (int per_sm = 4; per_sm <= 16 && rc == PXSNE_OK; per_sm *= 2) {
+            const int blocks = sms * per_sm;
+            const double flops = (double)blocks * 256 * iters * 8 * 2 * 2;
+            double ms = 0.0;
+            auto go = [&] { k_ffma<false><<<blocks, 256, 0, st>>>(iters, 1.0f, (float *)sink); };
+            if (time_ms(st, go, 1, &ms) || time_ms(st, go, 5, &ms)) rc = PXSNE_E_CUDA;
+            else best = fmax(best, flops / (ms * 1e-3) / 1e12);
+        }
+        if (rc == PXSNE_OK) *fp32_tflops = best;
     }
     if (rc == PXSNE_OK && fp32_packed_tflops) {
-        double ms = 0.0;
-        auto go = [&] { k_ffma<true><<<blocks, 256, 0, st>>>(iters, 1.0f, (float *)sink); };
-        if (time_ms(st, go, 1, &ms) || time_ms(st, go, 5, &ms)) rc = PXSNE_E_CUDA;
-        else *fp32_packed_tflops = flops / (ms * 1e-3) / 1e12;
+        double best = 0.0;
+        for (int per_sm = 4; per_sm <= 16 && rc == PXSNE_OK; per_sm *= 2) {
+            const int blocks = sms * per_sm;
+            const double flops = (double)blocks * 256 * iters * 8 * 2 * 2;
+            double ms = 0.0;
+            auto go = [&] { k_ffma<true><<<blocks, 256, 0, st>>>(iters, 1.0f, (float *)sink); };
+            if (time_ms(st, go, 1, &ms) || time_ms(st, go, 5, &ms)) rc = PXSNE_E_CUDA;
+            else best = fmax(best, flops / (ms * 1e-3) / 1e12);
+        }
+        if (rc == PXSNE_OK) *fp32_packed_tflops = best;
     }
     cudaFree(sink);
     return rc;
