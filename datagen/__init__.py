@@ -140,11 +140,11 @@ def gmm64out(seed: int = 0, n: int = 10_000_000):
     return gmm(seed, n, 64, 256, 1.2, outlier_frac=0.01)
 
 
-def init_y0(seed: int, n: int, sigma: float = 1e-4) -> np.ndarray:
-    """The random initial embedding Y0 ~ N(0, sigma^2 I), shape (n, 2),
+def init_y0(seed: int, n: int, sigma: float = 1e-4, dim: int = 2) -> np.ndarray:
+    """The random initial embedding Y0 ~ N(0, sigma^2 I), shape (n, dim),
     float32 (the random draw that t-SNE starts from; passed to both sides)."""
     rng = np.random.default_rng([seed, 7])
-    return (rng.standard_normal((n, 2)) * sigma).astype(np.float32)
+    return (rng.standard_normal((n, dim)) * sigma).astype(np.float32)
 
 
 # name -> (generator, default n, screen log2 resolution L, iterations T)

@@ -69,7 +69,19 @@ typedef struct pxsne_ctx pxsne_ctx;
  * L = 10) keep the quadtree's root at the padded 2^L x 2^L square, so the
  * tree's depth is L on both axes; axis d then spans R_d = r_d 2^(32 - L) ulps,
  * z_d in [0, R_d) and its pixel z_d >> (32 - L) in [0, r_d).  The init map
- * and the rescale use R_d in place of 2^32 (pxsne_init, pxsne_step). */
+ * and the rescale use R_d in place of 2^32 (pxsne_init, pxsne_step).
+ *
+ * dim = 3 embeds in 3-D (the extension of the paper's introduction): a voxel
+ * grid of 2^L per axis (1 <= L <= 9, no screen_x / screen_y), each point z_d
+ * in [0, 2^32) ulps on three axes, the quadtree an octree of eight children
+ * per cell (Morton bits x, y, z from the least significant), the cell
+ * diagonal of Eq. bh_criteria W sqrt(s_0^2 + s_1^2 + s_2^2); every other step
+ * is the 2-D method with a third coordinate.  With dim = 3 the buffers of
+ * pxsne_init (Y0, which must be given), pxsne_get_Y, pxsne_get_state,
+ * pxsne_set_state and pxsne_get_forces hold three values per point and s
+ * three; pxsne_get_tree3 reads the octree; the geometric-centre tree,
+ * pxsne_step_profiled, the counters, pxsne_nbr_precision, checkpoints and
+ * pxsne_kl_noalloc are 2-D only (PXSNE_E_UNSUPPORTED). */
 typedef struct pxsne_params {
     int32_t log2_r;          /* L: screen is 2^L x 2^L pixels, 1 <= L <= 14 (Sec. 4.1 depth) */
     float theta;             /* Barnes-Hut threshold, >= 0 (Eq. bh_criteria) */
@@ -88,6 +100,7 @@ typedef struct pxsne_params {
     int32_t screen_y;        /* screen height r_2 in pixels, 1 <= r_2 <= 2^L; 0: 2^L */
     int32_t knn_probe;       /* 0: exact neighbour search; W in [1, 1792]: approximate
                                 (see pxsne_affinities) */
+    int32_t dim;             /* embedding dimension: 2 (0 means 2) or 3 (see below) */
 } pxsne_params;
 
 void pxsne_default_params(pxsne_params *p);
@@ -162,8 +175,8 @@ int pxsne_step(pxsne_ctx *ctx, int32_t iters);
  * pxsne_init, PXSNE_E_ARG if the file cannot be written.
  *
  * File layout (byte order of the writing host, little-endian on every
- * supported one): a 136-byte header {char magic[8] = "PXSNECK\0"; uint32
- * version = 1; uint32 header bytes = 136; pxsne_params (64 bytes);
+ * supported one): a 144-byte header {char magic[8] = "PXSNECK\0"; uint32
+ * version = 1; uint32 header bytes = 144; pxsne_params (68 bytes); uint32 0;
  * int64 n, nnz; int32 t, 0; double s[2]; uint64 payload bytes; uint64
  * checksum}, then row_ptr[n+1] int64, col[nnz] int32, val[nnz] float32,
  * z[2n] uint32, u[2n] float32, gains[2n] float32.  The checksum is FNV-1a
@@ -261,6 +274,13 @@ int pxsne_get_state(pxsne_ctx *ctx, uint32_t *z, double *s, float *u, float *gai
  * asking for sx or sy fails with PXSNE_E_UNSUPPORTED. */
 int pxsne_get_tree(pxsne_ctx *ctx, int32_t level, uint32_t *cnt, uint64_t *sx,
                    uint64_t *sy, uint32_t *morton);
+
+/* The octree of a 3-D state (dim = 3) at one level l (0 = root .. L =
+ * voxels), in Morton order: cnt[8^l] cell counts and, for l = L only,
+ * sx/sy/sz[8^l] exact sums of the fixed-point coordinates (NULL to skip);
+ * voxel Morton keys per point to morton[n] when non-NULL.  Synchronises. */
+int pxsne_get_tree3(pxsne_ctx *ctx, int32_t level, uint32_t *cnt, uint64_t *sx, uint64_t *sy,
+                    uint64_t *sz, uint32_t *morton);
 
 /* Forces of the current state: Frep[n*2] = sum over accepted cells of
  * N w^2 (y_i - y_c) (un-normalised), Zi[n] = sum of N w, Fattr[n*2] =

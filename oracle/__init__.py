@@ -79,6 +79,25 @@ def lib():
                                  pd, pi64]
         L.orc_rescale.argtypes = [i64, pi64, pu32, pd]
         L.orc_rescale_screen.argtypes = [i64, pi64, pd, pu32, pd]
+        L.orc_init_fx_dim.argtypes = [pd, i64, i32, pd, pu32, pd]
+        L.orc_update_dim.argtypes = [i64, i32, pu32, pd, pd, pd, dbl, dbl, dbl, dbl, dbl, pd, pd,
+                                     pd, pi64]
+        L.orc_rescale_dim.argtypes = [i64, i32, pi64, pd, pu32, pd]
+        L.orc_morton3.argtypes = [u32, u32, u32]
+        L.orc_morton3.restype = u32
+        L.orc_level_offset3.argtypes = [i32]
+        L.orc_level_offset3.restype = i64
+        L.orc_pyramid3.argtypes = [pu32, i64, i32, pu32, pu64, pu64, pu64]
+        L.orc_bh_repulsion3.argtypes = [pu32, pd, i64, i32, dbl, pu32, pu64, pu64, pu64, pi64,
+                                        i64, pd, pd, pi64]
+        L.orc_exact_repulsion3.argtypes = [pu32, pd, i64, pi64, i64, pd, pd]
+        L.orc_attraction3.argtypes = [pi64, pi32, pd, pu32, pd, pi64, i64, pd]
+        L.orc_kl3.argtypes = [pi64, pi32, pd, i64, pu32, pd, dbl]
+        L.orc_kl3.restype = dbl
+        L.orc_run3.argtypes = [C.c_void_p, pi64, pi32, pd, i64, pu32, pd, pd, pd, i32, i32]
+        L.orc_run3.restype = C.c_int
+        L.orc_Z3.argtypes = [C.c_void_p, i64, pu32, pd]
+        L.orc_Z3.restype = dbl
         L.orc_kl.argtypes = [pi64, pi32, pd, i64, pu32, pd, dbl]
         L.orc_kl.restype = dbl
         L.orc_run.argtypes = [C.c_void_p, pi64, pi32, pd, i64, pu32, pd, pd, pd, i32, i32,
@@ -544,3 +563,153 @@ def pca(X, dout):
     sg = np.sign(V[np.argmax(np.abs(V), axis=0), np.arange(dout)])
     V = V * sg
     return Xc @ V, V, lam
+
+
+# ---------------------------------------------------------------- 3-D embedding
+# Sec. 1's footnote: the method on a voxel grid of 2^L per axis, the octree of
+# eight children per cell (Morton bits x, y, z from the least significant).
+def init_fx3(Y0):
+    """Eq. z1/z2 per axis of a 3-D start (n x 3) onto [0, 2^32) ulps."""
+    Y0 = np.ascontiguousarray(Y0, dtype=np.float64)
+    n = Y0.shape[0]
+    z = np.empty((n, 3), dtype=np.uint32)
+    s = np.empty(3)
+    R = np.full(3, 2.0 ** 32)
+    lib().orc_init_fx_dim(_P(Y0, C.c_double), n, 3, _P(R, C.c_double), _P(z, C.c_uint32),
+                          _P(s, C.c_double))
+    return z, s
+
+
+def morton3(px, py, pz):
+    return int(lib().orc_morton3(int(px), int(py), int(pz)))
+
+
+def level_offset3(l):
+    return int(lib().orc_level_offset3(int(l)))
+
+
+def pyramid3(z, L):
+    z = np.ascontiguousarray(z, dtype=np.uint32)
+    cells = level_offset3(L + 1)
+    cnt = np.empty(cells, np.uint32)
+    sx, sy, sz = (np.empty(cells, np.uint64) for _ in range(3))
+    lib().orc_pyramid3(_P(z, C.c_uint32), z.shape[0], L, _P(cnt, C.c_uint32),
+                       _P(sx, C.c_uint64), _P(sy, C.c_uint64), _P(sz, C.c_uint64))
+    return cnt, sx, sy, sz
+
+
+def bh_repulsion3(z, s, L, theta, rows=None, tree=None):
+    z = np.ascontiguousarray(z, dtype=np.uint32)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    n = z.shape[0]
+    cnt, sx, sy, sz = tree if tree is not None else pyramid3(z, L)
+    r, m = _rows(rows, n)
+    F = np.empty((m, 3))
+    Zi = np.empty(m)
+    acc = np.empty(m, np.int64)
+    lib().orc_bh_repulsion3(_P(z, C.c_uint32), _P(s, C.c_double), n, L, float(theta),
+                            _P(cnt, C.c_uint32), _P(sx, C.c_uint64), _P(sy, C.c_uint64),
+                            _P(sz, C.c_uint64), _ptr_or_null(r, C.c_int64), m, _P(F, C.c_double),
+                            _P(Zi, C.c_double), _P(acc, C.c_int64))
+    return F, Zi, acc
+
+
+def exact_repulsion3(z, s, rows=None):
+    z = np.ascontiguousarray(z, dtype=np.uint32)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    n = z.shape[0]
+    r, m = _rows(rows, n)
+    F = np.empty((m, 3))
+    Zi = np.empty(m)
+    lib().orc_exact_repulsion3(_P(z, C.c_uint32), _P(s, C.c_double), n,
+                               _ptr_or_null(r, C.c_int64), m, _P(F, C.c_double),
+                               _P(Zi, C.c_double))
+    return F, Zi
+
+
+def attraction3(P: CSR, z, s, rows=None):
+    z = np.ascontiguousarray(z, dtype=np.uint32)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    r, m = _rows(rows, P.n)
+    F = np.empty((m, 3))
+    lib().orc_attraction3(_P(P.row_ptr, C.c_int64), _P(P.col, C.c_int32), _P(P.val, C.c_double),
+                          _P(z, C.c_uint32), _P(s, C.c_double), _ptr_or_null(r, C.c_int64), m,
+                          _P(F, C.c_double))
+    return F
+
+
+def update3(z, s, Fattr, Frep, Z, alpha, mu, eta, u, gains, min_gain=0.01):
+    """One optimiser step of a 3-D state; u and gains updated in place."""
+    z = np.ascontiguousarray(z, dtype=np.uint32)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    Fattr = np.ascontiguousarray(Fattr, dtype=np.float64)
+    Frep = np.ascontiguousarray(Frep, dtype=np.float64)
+    assert u.dtype == np.float64 and u.flags.c_contiguous
+    assert gains.dtype == np.float64 and gains.flags.c_contiguous
+    n = z.shape[0]
+    zhat = np.empty((n, 3), dtype=np.int64)
+    g = np.empty((n, 3))
+    lib().orc_update_dim(n, 3, _P(z, C.c_uint32), _P(s, C.c_double), _P(Fattr, C.c_double),
+                         _P(Frep, C.c_double), float(Z), float(alpha), float(mu), float(eta),
+                         float(min_gain), _P(u, C.c_double), _P(gains, C.c_double),
+                         _P(g, C.c_double), _P(zhat, C.c_int64))
+    return zhat, g
+
+
+def rescale3(zhat, s):
+    zhat = np.ascontiguousarray(zhat, dtype=np.int64)
+    s2 = np.array(s, dtype=np.float64)
+    n = zhat.shape[0]
+    z = np.empty((n, 3), dtype=np.uint32)
+    R = np.full(3, 2.0 ** 32)
+    lib().orc_rescale_dim(n, 3, _P(zhat, C.c_int64), _P(R, C.c_double), _P(z, C.c_uint32),
+                          _P(s2, C.c_double))
+    return z, s2
+
+
+def kl3(P: CSR, z, s, Z):
+    z = np.ascontiguousarray(z, dtype=np.uint32)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    return float(lib().orc_kl3(_P(P.row_ptr, C.c_int64), _P(P.col, C.c_int32),
+                               _P(P.val, C.c_double), P.n, _P(z, C.c_uint32),
+                               _P(s, C.c_double), float(Z)))
+
+
+@dataclass
+class State3:
+    z: np.ndarray       # uint32 [n,3]
+    s: np.ndarray       # float64 [3]
+    u: np.ndarray       # float64 [n,3]
+    gains: np.ndarray   # float64 [n,3]
+    t: int = 0
+
+    @classmethod
+    def from_y0(cls, Y0):
+        z, s = init_fx3(Y0)
+        n = z.shape[0]
+        return cls(z, s, np.zeros((n, 3)), np.ones((n, 3)), 0)
+
+    def copy(self):
+        return State3(self.z.copy(), self.s.copy(), self.u.copy(), self.gains.copy(), self.t)
+
+
+def run3(P: CSR, state: State3, params: Params, iters: int):
+    """Advance a 3-D state in place by ``iters`` iterations (L <= 10)."""
+    pc = params.c()
+    rc = lib().orc_run3(C.byref(pc), _P(P.row_ptr, C.c_int64), _P(P.col, C.c_int32),
+                        _P(P.val, C.c_double), P.n, _P(state.z, C.c_uint32),
+                        _P(state.s, C.c_double), _P(state.u, C.c_double),
+                        _P(state.gains, C.c_double), state.t, iters)
+    if rc != 0:
+        raise MemoryError("orc_run3")
+    state.t += iters
+
+
+def Z_of3(state: State3, params: Params):
+    pc = params.c()
+    return float(lib().orc_Z3(C.byref(pc), state.z.shape[0], _P(state.z, C.c_uint32),
+                              _P(state.s, C.c_double)))
+
+
+def kl_of3(P: CSR, state: State3, params: Params):
+    return kl3(P, state.z, state.s, Z_of3(state, params))

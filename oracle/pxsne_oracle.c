@@ -214,28 +214,35 @@ int64_t orc_symmetrize(const int32_t *idx, const double *pcond, int64_t n, int32
  * screen: z_d = min(R_d-1, floor((y_d - min_d) * R_d / (max_d - min_d))),
  * s_d = (max_d - min_d) / R_d, with R_d = r_d 2^F the axis' extent in ulps
  * (R[d]).  An axis with zero extent maps to z_d = 0 and s_d = 1/R_d. */
-void orc_init_fx_screen(const double *Y0, int64_t n, const double *R, uint32_t *z, double *s)
+void orc_init_fx_dim(const double *Y0, int64_t n, int32_t dim, const double *R, uint32_t *z,
+                     double *s)
 {
-    for (int d = 0; d < 2; d++) {
+    for (int d = 0; d < dim; d++) {
         const double Rd = R[d];
         double mn = Y0[d], mx = Y0[d];
         for (int64_t i = 1; i < n; i++) {
-            double v = Y0[2 * i + d];
+            double v = Y0[dim * i + d];
             if (v < mn) mn = v;
             if (v > mx) mx = v;
         }
         double range = mx - mn;
         if (!(range > 0.0)) {
-            for (int64_t i = 0; i < n; i++) z[2 * i + d] = 0u;
+            for (int64_t i = 0; i < n; i++) z[dim * i + d] = 0u;
             s[d] = 1.0 / Rd;
             continue;
         }
         for (int64_t i = 0; i < n; i++) {
-            double q = floor((Y0[2 * i + d] - mn) * Rd / range);
-            z[2 * i + d] = q >= Rd - 1.0 ? (uint32_t)(Rd - 1.0) : (uint32_t)q;
+            double q = floor((Y0[dim * i + d] - mn) * Rd / range);
+            z[dim * i + d] = q >= Rd - 1.0 ? (uint32_t)(Rd - 1.0) : (uint32_t)q;
         }
         s[d] = range / Rd;
     }
+}
+
+/* The 2-D screen of r_1 x r_2 pixels. */
+void orc_init_fx_screen(const double *Y0, int64_t n, const double *R, uint32_t *z, double *s)
+{
+    orc_init_fx_dim(Y0, n, 2, R, z, s);
 }
 
 /* The square 2^L screen: R_d = 2^32 on both axes. */
@@ -465,13 +472,14 @@ void orc_attraction(const int64_t *row_ptr, const int32_t *col, const double *va
  * zhat is the un-normalised update of Sec. 4.2, before screen rescaling. */
 static int sgn(double x) { return x > 0.0 ? 1 : (x < 0.0 ? -1 : 0); }
 
-void orc_update(int64_t n, const uint32_t *z, const double *s, const double *Fattr,
-                const double *Frep, double Z, double alpha, double mu, double eta,
-                double min_gain, double *u, double *gains, double *grad, int64_t *zhat)
+void orc_update_dim(int64_t n, int32_t dim, const uint32_t *z, const double *s,
+                    const double *Fattr, const double *Frep, double Z, double alpha, double mu,
+                    double eta, double min_gain, double *u, double *gains, double *grad,
+                    int64_t *zhat)
 {
     for (int64_t i = 0; i < n; i++)
-        for (int d = 0; d < 2; d++) {
-            int64_t k = 2 * i + d;
+        for (int d = 0; d < dim; d++) {
+            int64_t k = dim * i + d;
             double g = 4.0 * (alpha * Fattr[k] - Frep[k] / Z);
             if (grad) grad[k] = g;
             double gn = (sgn(g) != sgn(u[k])) ? gains[k] + 0.2 : gains[k] * 0.8;
@@ -482,29 +490,43 @@ void orc_update(int64_t n, const uint32_t *z, const double *s, const double *Fat
         }
 }
 
+void orc_update(int64_t n, const uint32_t *z, const double *s, const double *Fattr,
+                const double *Frep, double Z, double alpha, double mu, double eta,
+                double min_gain, double *u, double *gains, double *grad, int64_t *zhat)
+{
+    orc_update_dim(n, 2, z, s, Fattr, Frep, Z, alpha, mu, eta, min_gain, u, gains, grad, zhat);
+}
+
 /* Sec. 4.2 screen-driven scaling to the r_d pixels of axis d, in exact
  * integer arithmetic:
  *   z_d = floor((zhat_d - min_d) * R_d / gamma_d),  gamma_d = (max_d - min_d) + 1
  * (the "+ epsilon" of gamma is one ulp; R_d = r_d 2^F, R[d]), and the
  * compensation of Eq. beta_scaling carried as s_d <- (s_d * gamma_d) / R_d
  * (two FP64 roundings; one when R_d = 2^32). */
-void orc_rescale_screen(int64_t n, const int64_t *zhat, const double *R, uint32_t *z, double *s)
+void orc_rescale_dim(int64_t n, int32_t dim, const int64_t *zhat, const double *R, uint32_t *z,
+                     double *s)
 {
-    for (int d = 0; d < 2; d++) {
+    for (int d = 0; d < dim; d++) {
         const uint64_t Rd = (uint64_t)R[d];
         int64_t mn = zhat[d], mx = zhat[d];
         for (int64_t i = 1; i < n; i++) {
-            int64_t v = zhat[2 * i + d];
+            int64_t v = zhat[dim * i + d];
             if (v < mn) mn = v;
             if (v > mx) mx = v;
         }
         uint64_t gamma = (uint64_t)(mx - mn) + 1u;
         for (int64_t i = 0; i < n; i++) {
-            unsigned __int128 num = (unsigned __int128)(uint64_t)(zhat[2 * i + d] - mn) * Rd;
-            z[2 * i + d] = (uint32_t)(num / gamma);
+            unsigned __int128 num = (unsigned __int128)(uint64_t)(zhat[dim * i + d] - mn) * Rd;
+            z[dim * i + d] = (uint32_t)(num / gamma);
         }
         s[d] = (s[d] * (double)gamma) / R[d];
     }
+}
+
+/* The 2-D screen of r_1 x r_2 pixels. */
+void orc_rescale_screen(int64_t n, const int64_t *zhat, const double *R, uint32_t *z, double *s)
+{
+    orc_rescale_dim(n, 2, zhat, R, z, s);
 }
 
 /* The square 2^L screen. */
@@ -763,3 +785,279 @@ double orc_mlp(int32_t d, int32_t H, const double *W1, const double *b1, const d
 
 double orc_gelu(double z) { return gelu(z); }
 double orc_gelu_d(double z) { return gelu_d(z); }
+
+/* ------------------------------------------------------------------------ */
+/* The 3-D embedding (Sec. 1's footnote: the same method on a voxel grid).
+ * The screen is 2^L voxels per axis; z_d in [0, 2^32) ulps per axis and the
+ * voxel is z_d >> (32 - L).  The quadtree becomes an octree: cell (l, m) of
+ * level l holds the voxels whose top l bits of x, y and z give m, with the
+ * bits interleaved x, y, z from the least significant (so a cell's child
+ * c = 4 zbit + 2 ybit + xbit); level offsets in a flattened pyramid are
+ * (8^l - 1) / 7.  Everything else is the 2-D method with a third axis. */
+uint32_t orc_morton3(uint32_t px, uint32_t py, uint32_t pz)
+{
+    uint32_t m = 0;
+    for (int b = 0; b < 10; b++) {
+        m |= ((px >> b) & 1u) << (3 * b);
+        m |= ((py >> b) & 1u) << (3 * b + 1);
+        m |= ((pz >> b) & 1u) << (3 * b + 2);
+    }
+    return m;
+}
+
+int64_t orc_level_offset3(int32_t l)
+{
+    int64_t o = 0, p = 1;
+    for (int32_t k = 0; k < l; k++) { o += p; p *= 8; }
+    return o;
+}
+
+/* Sec. 4.1's tree in 3-D: counts and exact coordinate sums of every cell,
+ * each point added to its cell at every level. */
+void orc_pyramid3(const uint32_t *z, int64_t n, int32_t L, uint32_t *cnt, uint64_t *sx,
+                  uint64_t *sy, uint64_t *sz)
+{
+    int64_t cells = orc_level_offset3(L + 1);
+    memset(cnt, 0, (size_t)cells * sizeof(uint32_t));
+    memset(sx, 0, (size_t)cells * sizeof(uint64_t));
+    memset(sy, 0, (size_t)cells * sizeof(uint64_t));
+    memset(sz, 0, (size_t)cells * sizeof(uint64_t));
+    int F = 32 - L;
+    for (int64_t i = 0; i < n; i++) {
+        uint32_t m = orc_morton3(z[3 * i] >> F, z[3 * i + 1] >> F, z[3 * i + 2] >> F);
+        for (int32_t l = 0; l <= L; l++) {
+            int64_t c = orc_level_offset3(l) + (m >> (3 * (L - l)));
+            cnt[c] += 1u;
+            sx[c] += z[3 * i];
+            sy[c] += z[3 * i + 1];
+            sz[c] += z[3 * i + 2];
+        }
+    }
+}
+
+/* Eq. grad's second term with Eq. bh_criteria on the voxel-aligned octree:
+ * the 2-D traversal with eight children and the cell diagonal
+ * r_c^2 = W^2 (s_0^2 + s_1^2 + s_2^2); the cell holding i is opened and i is
+ * taken out of its own voxel. */
+void orc_bh_repulsion3(const uint32_t *z, const double *s, int64_t n, int32_t L, double theta,
+                       const uint32_t *cnt, const uint64_t *sx, const uint64_t *sy,
+                       const uint64_t *sz, const int64_t *rows, int64_t m, double *Frep,
+                       double *Zi, int64_t *n_inter)
+{
+    const int F = 32 - L;
+    const double th2 = theta * theta;
+    const double s0 = s[0], s1 = s[1], s2 = s[2];
+    (void)n;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < m; q++) {
+        int64_t i = rows ? rows[q] : q;
+        const uint32_t zx = z[3 * i], zy = z[3 * i + 1], zz = z[3 * i + 2];
+        const uint32_t mi = orc_morton3(zx >> F, zy >> F, zz >> F);
+        int32_t stk_l[16 * 8];
+        uint32_t stk_m[16 * 8];
+        int sp = 0;
+        double fx = 0.0, fy = 0.0, fz = 0.0, zsum = 0.0;
+        int64_t acc = 0;
+        stk_l[sp] = 0; stk_m[sp] = 0; sp++;
+        while (sp > 0) {
+            sp--;
+            int32_t l = stk_l[sp];
+            uint32_t mc = stk_m[sp];
+            int64_t c = orc_level_offset3(l) + mc;
+            uint64_t N = cnt[c];
+            if (N == 0) continue;
+            int leaf = (l == L);
+            int contains = ((mi >> (3 * (L - l))) == mc);
+            uint64_t Sx = sx[c], Sy = sy[c], Sz = sz[c];
+            if (contains) {
+                if (!leaf) {
+                    for (uint32_t ch = 0; ch < 8; ch++) {
+                        stk_l[sp] = l + 1; stk_m[sp] = 8 * mc + ch; sp++;
+                    }
+                    continue;
+                }
+                N -= 1;
+                if (N == 0) continue;
+                Sx -= zx;
+                Sy -= zy;
+                Sz -= zz;
+            }
+            double dx = s0 * com_offset(zx, Sx, N);
+            double dy = s1 * com_offset(zy, Sy, N);
+            double dz = s2 * com_offset(zz, Sz, N);
+            double dd = dx * dx + dy * dy + dz * dz;
+            if (!leaf && !contains) {
+                double W = ldexp(1.0, 32 - l);
+                double rc2 = (s0 * W) * (s0 * W) + (s1 * W) * (s1 * W) + (s2 * W) * (s2 * W);
+                if (!(rc2 < th2 * dd)) {
+                    for (uint32_t ch = 0; ch < 8; ch++) {
+                        stk_l[sp] = l + 1; stk_m[sp] = 8 * mc + ch; sp++;
+                    }
+                    continue;
+                }
+            }
+            double w = 1.0 / (1.0 + dd);
+            double Nw = (double)N * w;
+            zsum += Nw;
+            fx += Nw * w * dx;
+            fy += Nw * w * dy;
+            fz += Nw * w * dz;
+            acc++;
+        }
+        Frep[3 * q] = fx;
+        Frep[3 * q + 1] = fy;
+        Frep[3 * q + 2] = fz;
+        Zi[q] = zsum;
+        if (n_inter) n_inter[q] = acc;
+    }
+}
+
+/* Eq. q and Eq. grad's second term without approximation, in 3-D. */
+void orc_exact_repulsion3(const uint32_t *z, const double *s, int64_t n, const int64_t *rows,
+                          int64_t m, double *Frep, double *Zi)
+{
+    const double s0 = s[0], s1 = s[1], s2 = s[2];
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t q = 0; q < m; q++) {
+        int64_t i = rows ? rows[q] : q;
+        double fx = 0.0, fy = 0.0, fz = 0.0, zs = 0.0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double dx = s0 * (double)((int64_t)z[3 * i] - (int64_t)z[3 * j]);
+            double dy = s1 * (double)((int64_t)z[3 * i + 1] - (int64_t)z[3 * j + 1]);
+            double dz = s2 * (double)((int64_t)z[3 * i + 2] - (int64_t)z[3 * j + 2]);
+            double w = 1.0 / (1.0 + dx * dx + dy * dy + dz * dz);
+            zs += w;
+            fx += w * w * dx;
+            fy += w * w * dy;
+            fz += w * w * dz;
+        }
+        Frep[3 * q] = fx;
+        Frep[3 * q + 1] = fy;
+        Frep[3 * q + 2] = fz;
+        Zi[q] = zs;
+    }
+}
+
+/* Eq. grad's first term over the sparse P, in 3-D (un-exaggerated). */
+void orc_attraction3(const int64_t *row_ptr, const int32_t *col, const double *val,
+                     const uint32_t *z, const double *s, const int64_t *rows, int64_t m,
+                     double *Fattr)
+{
+    const double s0 = s[0], s1 = s[1], s2 = s[2];
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t q = 0; q < m; q++) {
+        int64_t i = rows ? rows[q] : q;
+        double fx = 0.0, fy = 0.0, fz = 0.0;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; e++) {
+            int64_t j = col[e];
+            double dx = s0 * (double)((int64_t)z[3 * i] - (int64_t)z[3 * j]);
+            double dy = s1 * (double)((int64_t)z[3 * i + 1] - (int64_t)z[3 * j + 1]);
+            double dz = s2 * (double)((int64_t)z[3 * i + 2] - (int64_t)z[3 * j + 2]);
+            double w = 1.0 / (1.0 + dx * dx + dy * dy + dz * dz);
+            fx += val[e] * w * dx;
+            fy += val[e] * w * dy;
+            fz += val[e] * w * dz;
+        }
+        Fattr[3 * q] = fx;
+        Fattr[3 * q + 1] = fy;
+        Fattr[3 * q + 2] = fz;
+    }
+}
+
+/* Eq. cost_func in 3-D. */
+double orc_kl3(const int64_t *row_ptr, const int32_t *col, const double *val, int64_t n,
+               const uint32_t *z, const double *s, double Z)
+{
+    const double s0 = s[0], s1 = s[1], s2 = s[2];
+    double C = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : C)
+    for (int64_t i = 0; i < n; i++) {
+        double c = 0.0;
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; e++) {
+            double p = val[e];
+            if (p <= 0.0) continue;
+            int64_t j = col[e];
+            double dx = s0 * (double)((int64_t)z[3 * i] - (int64_t)z[3 * j]);
+            double dy = s1 * (double)((int64_t)z[3 * i + 1] - (int64_t)z[3 * j + 1]);
+            double dz = s2 * (double)((int64_t)z[3 * i + 2] - (int64_t)z[3 * j + 2]);
+            double q = 1.0 / ((1.0 + dx * dx + dy * dy + dz * dz) * Z);
+            c += p * log(p / q);
+        }
+        C += c;
+    }
+    return C;
+}
+
+/* One 3-D run: for t = t0 .. t0+iters-1 the octree, its Barnes-Hut repulsion
+ * (or the exact sum), the attraction, Z, the gradient step and the screen
+ * rescale of all three axes (R = 2^32).  Schedule as orc_run. */
+int orc_run3(const orc_params *p, const int64_t *row_ptr, const int32_t *col, const double *val,
+             int64_t n, uint32_t *z, double *s, double *u, double *gains, int32_t t0,
+             int32_t iters)
+{
+    int64_t cells = orc_level_offset3(p->L + 1);
+    uint32_t *cnt = NULL;
+    uint64_t *sx = NULL, *sy = NULL, *sz = NULL;
+    if (!p->exact) {
+        cnt = (uint32_t *)malloc((size_t)cells * sizeof(uint32_t));
+        sx = (uint64_t *)malloc((size_t)cells * sizeof(uint64_t));
+        sy = (uint64_t *)malloc((size_t)cells * sizeof(uint64_t));
+        sz = (uint64_t *)malloc((size_t)cells * sizeof(uint64_t));
+    }
+    double *Frep = (double *)malloc((size_t)n * 3 * sizeof(double));
+    double *Fattr = (double *)malloc((size_t)n * 3 * sizeof(double));
+    double *Zi = (double *)malloc((size_t)n * sizeof(double));
+    int64_t *zhat = (int64_t *)malloc((size_t)n * 3 * sizeof(int64_t));
+    if ((!p->exact && (!cnt || !sx || !sy || !sz)) || !Frep || !Fattr || !Zi || !zhat) {
+        free(cnt); free(sx); free(sy); free(sz); free(Frep); free(Fattr); free(Zi); free(zhat);
+        return -1;
+    }
+    const double R[3] = {ORC_R, ORC_R, ORC_R};
+    for (int32_t t = t0; t < t0 + iters; t++) {
+        if (p->exact) {
+            orc_exact_repulsion3(z, s, n, NULL, n, Frep, Zi);
+        } else {
+            orc_pyramid3(z, n, p->L, cnt, sx, sy, sz);
+            orc_bh_repulsion3(z, s, n, p->L, p->theta, cnt, sx, sy, sz, NULL, n, Frep, Zi, NULL);
+        }
+        double Z = 0.0;
+        for (int64_t i = 0; i < n; i++) Z += Zi[i];
+        orc_attraction3(row_ptr, col, val, z, s, NULL, n, Fattr);
+        double alpha = t < p->exag_iters ? p->exag : 1.0;
+        double mu = t < p->mom_switch ? p->mom0 : p->mom1;
+        orc_update_dim(n, 3, z, s, Fattr, Frep, Z, alpha, mu, p->eta, p->min_gain, u, gains,
+                       NULL, zhat);
+        orc_rescale_dim(n, 3, zhat, R, z, s);
+    }
+    free(cnt); free(sx); free(sy); free(sz); free(Frep); free(Fattr); free(Zi); free(zhat);
+    return 0;
+}
+
+/* Z of a 3-D state (Barnes-Hut with the run's theta, or exact), for the KL. */
+double orc_Z3(const orc_params *p, int64_t n, const uint32_t *z, const double *s)
+{
+    double *Zi = (double *)malloc((size_t)n * sizeof(double));
+    double *Frep = (double *)malloc((size_t)n * 3 * sizeof(double));
+    double Z = -1.0;
+    if (!Zi || !Frep) goto out;
+    if (p->exact) {
+        orc_exact_repulsion3(z, s, n, NULL, n, Frep, Zi);
+    } else {
+        int64_t cells = orc_level_offset3(p->L + 1);
+        uint32_t *cnt = (uint32_t *)malloc((size_t)cells * sizeof(uint32_t));
+        uint64_t *sx = (uint64_t *)malloc((size_t)cells * sizeof(uint64_t));
+        uint64_t *sy = (uint64_t *)malloc((size_t)cells * sizeof(uint64_t));
+        uint64_t *sz = (uint64_t *)malloc((size_t)cells * sizeof(uint64_t));
+        if (!cnt || !sx || !sy || !sz) { free(cnt); free(sx); free(sy); free(sz); goto out; }
+        orc_pyramid3(z, n, p->L, cnt, sx, sy, sz);
+        orc_bh_repulsion3(z, s, n, p->L, p->theta, cnt, sx, sy, sz, NULL, n, Frep, Zi, NULL);
+        free(cnt); free(sx); free(sy); free(sz);
+    }
+    Z = 0.0;
+    for (int64_t i = 0; i < n; i++) Z += Zi[i];
+out:
+    free(Zi);
+    free(Frep);
+    return Z;
+}

@@ -46,7 +46,7 @@ class _CParams(C.Structure):
                 ("momentum_switch", C.c_int32), ("min_gain", C.c_float), ("k", C.c_int32),
                 ("perplexity", C.c_float), ("init_sigma", C.c_float),
                 ("centre_mode", C.c_int32), ("screen_x", C.c_int32), ("screen_y", C.c_int32),
-                ("knn_probe", C.c_int32)]
+                ("knn_probe", C.c_int32), ("dim", C.c_int32)]
 
 
 @dataclass
@@ -68,6 +68,7 @@ class Params:
     screen_x: int = 0      # pixels of the screen's width (0: 2^log2_r)
     screen_y: int = 0      # pixels of its height (0: 2^log2_r)
     knn_probe: int = 0     # 0: exact neighbour search; W: approximate, W tiles per tile
+    dim: int = 2           # embedding dimension: 2, or 3 (voxel grid and octree)
 
     def c(self):
         return _CParams(*[getattr(self, f.name) for f in fields(self)])
@@ -138,6 +139,7 @@ def load(path: str | None = None):
     L.pxsne_test_stack_limit.argtypes = [vp, i32]
     L.pxsne_load.argtypes = [C.POINTER(vp), C.c_char_p, vp]
     L.pxsne_get_params.argtypes = [vp, C.POINTER(_CParams)]
+    L.pxsne_get_tree3.argtypes = [vp, i32, vp, vp, vp, vp, vp]
     L.pxsne_measure_peaks.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.POINTER(i32), C.POINTER(i64)]
     _lib = L
@@ -252,7 +254,7 @@ class Context:
     def init(self, Y0=None, seed: int = 0):
         Y0 = _f32(Y0)
         n = self.sizes()[0] or None   # without P the library reports the order error
-        p, dev = _buf(Y0, np.float32, (n, 2), "Y0")
+        p, dev = _buf(Y0, np.float32, (n, self.dim), "Y0")
         self._ck(self.L.pxsne_init(self.h, p, dev, int(seed)))
 
     def step(self, iters: int = 1):
@@ -266,12 +268,12 @@ class Context:
     def get_Y(self, Y=None, pix=None, want_pix=True):
         """Centred y-space coordinates and pixels; fills Y/pix if given
         (numpy, or CUDA tensors), else returns new numpy arrays."""
-        n = self.sizes()[0]
+        n, d = self.sizes()[0], self.dim
         if Y is None and pix is None:
-            Y = np.empty((n, 2), np.float32)
-            pix = np.empty((n, 2), np.int32) if want_pix else None
-        py, dy = _buf(Y, np.float32, (n, 2), "Y")
-        pp, dp = _buf(pix, np.int32, (n, 2), "pix")
+            Y = np.empty((n, d), np.float32)
+            pix = np.empty((n, d), np.int32) if want_pix else None
+        py, dy = _buf(Y, np.float32, (n, d), "Y")
+        pp, dp = _buf(pix, np.int32, (n, d), "pix")
         if Y is not None and pix is not None and dy != dp:
             raise ValueError("Y and pix must both be host or both be device buffers")
         dev = dy or dp
@@ -325,18 +327,20 @@ class Context:
         s = np.ascontiguousarray(s, np.float64)
         u = None if u is None else np.ascontiguousarray(u, np.float32)
         gains = None if gains is None else np.ascontiguousarray(gains, np.float32)
-        pz, _ = _buf(z, np.uint32, (n, 2), "z")
-        ps, _ = _buf(s, np.float64, (2,), "s")
-        pu, _ = _buf(u, np.float32, (n, 2), "u")
-        pg, _ = _buf(gains, np.float32, (n, 2), "gains")
+        d = self.dim
+        pz, _ = _buf(z, np.uint32, (n, d), "z")
+        ps, _ = _buf(s, np.float64, (d,), "s")
+        pu, _ = _buf(u, np.float32, (n, d), "u")
+        pg, _ = _buf(gains, np.float32, (n, d), "gains")
         self._ck(self.L.pxsne_set_state(self.h, pz, ps, pu, pg, int(t)))
 
     def get_state(self):
         n, _ = self.sizes()
-        z = np.empty((n, 2), np.uint32)
-        s = np.empty(2, np.float64)
-        u = np.empty((n, 2), np.float32)
-        g = np.empty((n, 2), np.float32)
+        d = self.dim
+        z = np.empty((n, d), np.uint32)
+        s = np.empty(d, np.float64)
+        u = np.empty((n, d), np.float32)
+        g = np.empty((n, d), np.float32)
         t = C.c_int32()
         self._ck(self.L.pxsne_get_state(self.h, z.ctypes.data, s.ctypes.data, u.ctypes.data,
                                         g.ctypes.data, C.byref(t)))
@@ -355,11 +359,26 @@ class Context:
                                        None if mk is None else mk.ctypes.data))
         return cnt, sx, sy, mk
 
+    def get_tree3(self, level, sums=False, morton=False):
+        """The octree of a 3-D state at one level (``pxsne_get_tree3``)."""
+        n, _ = self.sizes()
+        cells = 8 ** level
+        cnt = np.empty(cells, np.uint32)
+        sx, sy, sz = ((np.empty(cells, np.uint64) if sums else None) for _ in range(3))
+        mk = np.empty(n, np.uint32) if morton else None
+        ptr = [None if a is None else a.ctypes.data for a in (sx, sy, sz, mk)]
+        self._ck(self.L.pxsne_get_tree3(self.h, int(level), cnt.ctypes.data, *ptr))
+        return cnt, sx, sy, sz, mk
+
+    @property
+    def dim(self):
+        return 3 if self.params.dim == 3 else 2
+
     def get_forces(self):
         n, _ = self.sizes()
-        Frep = np.empty((n, 2), np.float32)
+        Frep = np.empty((n, self.dim), np.float32)
         Zi = np.empty(n, np.float32)
-        Fattr = np.empty((n, 2), np.float32)
+        Fattr = np.empty((n, self.dim), np.float32)
         Z = C.c_double()
         self._ck(self.L.pxsne_get_forces(self.h, Frep.ctypes.data, Zi.ctypes.data,
                                          Fattr.ctypes.data, C.byref(Z)))
@@ -594,4 +613,4 @@ EXPORTED = ["pxsne_default_params", "pxsne_create", "pxsne_destroy", "pxsne_last
             "pxsne_mlp_train", "pxsne_mlp_predict", "pxsne_embed_align",
             "pxsne_nbr_precision", "pxsne_pca", "pxsne_measure_peaks",
             "pxsne_get_level_counters", "pxsne_save", "pxsne_load", "pxsne_get_params",
-            "pxsne_test_stack_limit"]
+            "pxsne_test_stack_limit", "pxsne_get_tree3"]

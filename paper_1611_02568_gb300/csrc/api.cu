@@ -75,6 +75,7 @@ void free_state(pxsne_ctx *c) {
     dfree(c->leaf_start); dfree(c->blk_off); dfree(c->zpart); dfree(c->klpart);
     dfree(c->rp2); dfree(c->col2); dfree(c->val2);
     dfree(c->aperm); dfree(c->ainv); dfree(c->rl2); dfree(c->zp);
+    free3(c);
     c->state_ready = false;
 }
 
@@ -101,15 +102,38 @@ int check_params(const pxsne_params *p) {
                     p->screen_y, side, side);
     if (p->knn_probe < 0 || p->knn_probe > 1792)
         return fail(nullptr, PXSNE_E_ARG, "knn_probe = %d outside [0, 1792]", p->knn_probe);
+    if (p->dim != 0 && p->dim != 2 && p->dim != 3)
+        return fail(nullptr, PXSNE_E_ARG, "dim = %d: 2 or 3", p->dim);
+    if (p->dim == 3 && (p->log2_r > kMaxL3 || p->screen_x || p->screen_y || p->centre_mode))
+        return fail(nullptr, PXSNE_E_ARG,
+                    "dim 3: log2_r <= %d, a cube of 2^L voxels, centres of mass", kMaxL3);
     return PXSNE_OK;
+}
+
+bool is3(const pxsne_ctx *c) { return c->p.dim == 3; }
+
+int unsupported3(pxsne_ctx *c, const char *what) {
+    return fail(c, PXSNE_E_UNSUPPORTED, "%s: 2-D embeddings only", what);
 }
 
 // Allocate the per-point and tree buffers for the current n and L.
 int ensure_state(pxsne_ctx *c) {
-    if (c->z && c->L == c->p.log2_r) return PXSNE_OK;
+    if ((c->z || c->z3) && c->L == c->p.log2_r) return PXSNE_OK;
     free_state(c);
     const int64_t n = c->n;
     c->L = c->p.log2_r;
+    if (is3(c)) {
+        // the 3-D state: the shared per-point buffers and the octree's
+        CK(c, dalloc(c, &c->Zi, n));
+        CK(c, dalloc(c, &c->perm, n));
+        CK(c, dalloc(c, &c->rank, n));
+        CK(c, alloc3(c));
+        c->zblocks = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (n + 4095) / 4096));
+        CK(c, dalloc(c, &c->zpart, c->zblocks));
+        c->klblocks = 304;
+        CK(c, dalloc(c, &c->klpart, 2 * c->klblocks));
+        return PXSNE_OK;
+    }
     const int L = c->L;
     const int64_t leaves = int64_t(1) << (2 * L);
     const int64_t cells = rec_offset(L + 1);
@@ -182,6 +206,11 @@ __global__ void k_fill_f2(int n, float2 *p, float v) {
 // Tree and forces of the state just written (no rescale).
 int prime(pxsne_ctx *c) {
     const int n = (int)c->n;
+    if (is3(c)) {
+        CK(c, launch_prime3(c, false));
+        c->state_ready = true;
+        return PXSNE_OK;
+    }
     k_iota<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->perm);
     CK(c, cudaGetLastError());
     CK(c, launch_tree(c, false));
@@ -197,7 +226,7 @@ int prime(pxsne_ctx *c) {
 // The attraction's relabelled copy of P follows the Morton order of the last
 // tree; it is refreshed every kRelabelEvery iterations (before the update).
 cudaError_t relabel_if_due(pxsne_ctx *c) {
-    if (c->since_relabel < kRelabelEvery) return cudaSuccess;
+    if (is3(c) || c->since_relabel < kRelabelEvery) return cudaSuccess;
     c->since_relabel = 0;
     return launch_relabel(c, c->stream);
 }
@@ -209,6 +238,10 @@ cudaError_t relabel_if_due(pxsne_ctx *c) {
 // the attraction's blocks fill the SMs as the traversal's drain.  The two
 // join before the next update.
 int one_iteration(pxsne_ctx *c, cudaEvent_t *marks = nullptr) {
+    if (is3(c)) {
+        CK(c, launch_iteration3(c));
+        return PXSNE_OK;
+    }
     CK(c, launch_update(c, marks));
     if (marks || !c->side) {
         CK(c, launch_tree(c, true, marks));
@@ -216,6 +249,10 @@ int one_iteration(pxsne_ctx *c, cudaEvent_t *marks = nullptr) {
         return PXSNE_OK;
     }
     CK(c, launch_tree(c, true));
+    if (c->fused) {
+        CK(c, launch_traverse_zsum(c));
+        return PXSNE_OK;
+    }
     CK(c, cudaEventRecord(c->ev_fork, c->stream));
     CK(c, launch_traverse_zsum(c));
     CK(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
@@ -275,6 +312,7 @@ void pxsne_default_params(pxsne_params *p) {
     p->screen_x = 0;
     p->screen_y = 0;
     p->knn_probe = 0;
+    p->dim = 2;
 }
 
 int pxsne_create(pxsne_ctx **out, const pxsne_params *p, void *stream) {
@@ -302,6 +340,10 @@ int pxsne_create(pxsne_ctx **out, const pxsne_params *p, void *stream) {
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, lo);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    }
+    {
+        const char *f = getenv("PXSNE_FORCES");
+        c->fused = f && f[0] == 'f';
     }
     if (e == cudaSuccess) e = dalloc(c, &c->sc, 1);
     if (e == cudaSuccess) e = cudaMemset(c->sc, 0, sizeof(DevScalars));
@@ -449,6 +491,28 @@ int pxsne_init(pxsne_ctx *c, const float *Y0, int y_on_device, uint64_t seed) {
     if (rc) return rc;
     cudaStream_t st = c->stream;
     const int64_t n = c->n;
+    if (is3(c)) {
+        if (!Y0) return fail(c, PXSNE_E_UNSUPPORTED, "dim 3: the start Y0 must be given");
+        float *Yd3 = nullptr;
+        double *scr = nullptr;
+        CK(c, cudaMallocAsync(&scr, 8 * sizeof(double), st));
+        const float *Y3 = Y0;
+        if (!y_on_device) {
+            CK(c, cudaMallocAsync(&Yd3, (size_t)n * 12, st));
+            CK(c, cudaMemcpyAsync(Yd3, Y0, (size_t)n * 12, cudaMemcpyHostToDevice, st));
+            Y3 = Yd3;
+        }
+        const unsigned zero3 = 0;
+        CK(c, cudaMemcpyAsync(&c->sc->err, &zero3, sizeof(unsigned), cudaMemcpyHostToDevice, st));
+        CK(c, launch_init3(c, Y3, scr));
+        rc = prime(c);
+        if (rc) return rc;
+        if (Yd3) CK(c, cudaFreeAsync(Yd3, st));
+        CK(c, cudaFreeAsync(scr, st));
+        rc = check_device(c, nullptr);
+        if (rc) c->state_ready = false;
+        return rc;
+    }
     float *Yd = nullptr;
     uint32_t *mm = nullptr;
     CK(c, cudaMallocAsync(&mm, 4 * sizeof(uint32_t), st));
@@ -487,6 +551,21 @@ int pxsne_set_state(pxsne_ctx *c, const uint32_t *z, const double *s, const floa
     if (rc) return rc;
     const int n = (int)c->n;
     cudaStream_t st = c->stream;
+    if (is3(c)) {
+        if (!(s[2] > 0.0)) return fail(c, PXSNE_E_ARG, "bad s");
+        // host rows of three values into the 4-wide device vectors
+        CK(c, cudaMemcpy2DAsync(c->z3, 16, z, 12, 12, (size_t)n, cudaMemcpyHostToDevice, st));
+        CK(c, launch_fill3(c, c->u3, 0.f, 0.f, 0.f));
+        CK(c, launch_fill3(c, c->gains3, 1.f, 1.f, 1.f));
+        if (u) CK(c, cudaMemcpy2DAsync(c->u3, 16, u, 12, 12, (size_t)n, cudaMemcpyHostToDevice, st));
+        if (gains)
+            CK(c, cudaMemcpy2DAsync(c->gains3, 16, gains, 12, 12, (size_t)n,
+                                    cudaMemcpyHostToDevice, st));
+        CK(c, launch_set_scalars3(c, s, t));
+        rc = prime(c);
+        if (rc) return rc;
+        return check_device(c, nullptr);
+    }
     CK(c, cudaMemcpyAsync(c->z, z, (size_t)n * 8, cudaMemcpyHostToDevice, st));
     if (u) CK(c, cudaMemcpyAsync(c->u, u, (size_t)n * 8, cudaMemcpyHostToDevice, st));
     else k_fill_f2<<<(n + 255) / 256, 256, 0, st>>>(n, c->u, 0.f);
@@ -535,6 +614,7 @@ int pxsne_step_profiled(pxsne_ctx *c, int32_t iters, double *group_ms, int32_t n
                         double *total_ms) {
     int rc = need_state(c);
     if (rc) return rc;
+    if (is3(c)) return unsupported3(c, "pxsne_step_profiled");
     if (iters < 1 || !group_ms || n_groups < KG_COUNT)
         return fail(c, PXSNE_E_ARG, "need iters >= 1 and %d group slots", (int)KG_COUNT);
     // destroyed on every return path, the early ones included
@@ -616,7 +696,8 @@ int pxsne_kl(pxsne_ctx *c, double *out) {
     if (!out) return fail(c, PXSNE_E_ARG, "out is NULL");
     double *d = nullptr;
     CK(c, cudaMallocAsync(&d, sizeof(double), c->stream));
-    CK(c, launch_kl(c, d));
+    if (is3(c)) CK(c, launch_kl3(c, d));
+    else CK(c, launch_kl(c, d));
     CK(c, cudaMemcpyAsync(out, d, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaFreeAsync(d, c->stream));
     return check_device(c, nullptr);
@@ -627,24 +708,26 @@ int pxsne_get_Y(pxsne_ctx *c, float *Y, int32_t *pix, int on_device) {
     if (rc) return rc;
     cudaStream_t st = c->stream;
     const int64_t n = c->n;
+    const size_t row = is3(c) ? 12 : 8;  // bytes of one point's values
     float *scratch = nullptr;
-    CK(c, cudaMallocAsync(&scratch, 16, st));
+    CK(c, cudaMallocAsync(&scratch, 32, st));
     float *Yd = Y;
     int32_t *Pd = pix;
     if (!on_device) {
         Yd = nullptr;
         Pd = nullptr;
-        if (Y) CK(c, cudaMallocAsync(&Yd, (size_t)n * 8, st));
-        if (pix) CK(c, cudaMallocAsync(&Pd, (size_t)n * 8, st));
+        if (Y) CK(c, cudaMallocAsync(&Yd, (size_t)n * row, st));
+        if (pix) CK(c, cudaMallocAsync(&Pd, (size_t)n * row, st));
     }
-    CK(c, launch_centre_y(c, Yd, Pd, scratch));
+    if (is3(c)) CK(c, launch_centre_y3(c, Yd, Pd, reinterpret_cast<double *>(scratch)));
+    else CK(c, launch_centre_y(c, Yd, Pd, scratch));
     if (!on_device) {
         if (Y) {
-            CK(c, cudaMemcpyAsync(Y, Yd, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+            CK(c, cudaMemcpyAsync(Y, Yd, (size_t)n * row, cudaMemcpyDeviceToHost, st));
             CK(c, cudaFreeAsync(Yd, st));
         }
         if (pix) {
-            CK(c, cudaMemcpyAsync(pix, Pd, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+            CK(c, cudaMemcpyAsync(pix, Pd, (size_t)n * row, cudaMemcpyDeviceToHost, st));
             CK(c, cudaFreeAsync(Pd, st));
         }
     }
@@ -656,6 +739,7 @@ int pxsne_nbr_precision(pxsne_ctx *c, int32_t k, const int32_t *knn_hd, int32_t 
                         int on_device, double *precision, int32_t *hits) {
     int rc = need_state(c);
     if (rc) return rc;
+    if (is3(c)) return unsupported3(c, "pxsne_nbr_precision");
     if (!knn_hd) {
         if (!c->knn_idx) return fail(c, PXSNE_E_STATE, "no neighbour lists: pass knn_hd");
         knn_hd = c->knn_idx;
@@ -749,16 +833,27 @@ int pxsne_get_state(pxsne_ctx *c, uint32_t *z, double *s, float *u, float *gains
     if (rc) return rc;
     cudaStream_t st = c->stream;
     const size_t n = (size_t)c->n;
-    if (z) CK(c, cudaMemcpyAsync(z, c->z, n * 8, cudaMemcpyDeviceToHost, st));
-    if (u) CK(c, cudaMemcpyAsync(u, c->u, n * 8, cudaMemcpyDeviceToHost, st));
-    if (gains) CK(c, cudaMemcpyAsync(gains, c->gains, n * 8, cudaMemcpyDeviceToHost, st));
+    if (is3(c)) {
+        if (z) CK(c, cudaMemcpy2DAsync(z, 12, c->z3, 16, 12, n, cudaMemcpyDeviceToHost, st));
+        if (u) CK(c, cudaMemcpy2DAsync(u, 12, c->u3, 16, 12, n, cudaMemcpyDeviceToHost, st));
+        if (gains)
+            CK(c, cudaMemcpy2DAsync(gains, 12, c->gains3, 16, 12, n, cudaMemcpyDeviceToHost, st));
+    } else {
+        if (z) CK(c, cudaMemcpyAsync(z, c->z, n * 8, cudaMemcpyDeviceToHost, st));
+        if (u) CK(c, cudaMemcpyAsync(u, c->u, n * 8, cudaMemcpyDeviceToHost, st));
+        if (gains) CK(c, cudaMemcpyAsync(gains, c->gains, n * 8, cudaMemcpyDeviceToHost, st));
+    }
     DevScalars h;
     CK(c, cudaMemcpyAsync(&h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
     rc = check_device(c, nullptr);
     if (rc) return rc;
     if (s) {
-        s[0] = h.s[0];
-        s[1] = h.s[1];
+        if (is3(c)) {
+            for (int d = 0; d < 3; d++) s[d] = h.s3[d];
+        } else {
+            s[0] = h.s[0];
+            s[1] = h.s[1];
+        }
     }
     if (t) *t = h.t;
     return PXSNE_OK;
@@ -768,6 +863,7 @@ int pxsne_get_tree(pxsne_ctx *c, int32_t level, uint32_t *cnt, uint64_t *sx, uin
                    uint32_t *morton) {
     int rc = need_state(c);
     if (rc) return rc;
+    if (is3(c)) return unsupported3(c, "pxsne_get_tree (use pxsne_get_tree3)");
     if (level < 0 || level > c->L) return fail(c, PXSNE_E_ARG, "level out of range");
     if (level == c->L && (sx || sy) && c->p.centre_mode != 0)
         return fail(c, PXSNE_E_UNSUPPORTED, "the geometric-centre tree keeps no coordinate sums");
@@ -799,9 +895,16 @@ int pxsne_get_forces(pxsne_ctx *c, float *Frep, float *Zi, float *Fattr, double 
     if (rc) return rc;
     cudaStream_t st = c->stream;
     const size_t n = (size_t)c->n;
-    if (Frep) CK(c, cudaMemcpyAsync(Frep, c->Frep, n * 8, cudaMemcpyDeviceToHost, st));
+    if (is3(c)) {
+        if (Frep)
+            CK(c, cudaMemcpy2DAsync(Frep, 12, c->Frep3, 16, 12, n, cudaMemcpyDeviceToHost, st));
+        if (Fattr)
+            CK(c, cudaMemcpy2DAsync(Fattr, 12, c->Fattr3, 16, 12, n, cudaMemcpyDeviceToHost, st));
+    } else {
+        if (Frep) CK(c, cudaMemcpyAsync(Frep, c->Frep, n * 8, cudaMemcpyDeviceToHost, st));
+        if (Fattr) CK(c, cudaMemcpyAsync(Fattr, c->Fattr, n * 8, cudaMemcpyDeviceToHost, st));
+    }
     if (Zi) CK(c, cudaMemcpyAsync(Zi, c->Zi, n * 4, cudaMemcpyDeviceToHost, st));
-    if (Fattr) CK(c, cudaMemcpyAsync(Fattr, c->Fattr, n * 8, cudaMemcpyDeviceToHost, st));
     if (Z) CK(c, cudaMemcpyAsync(Z, &c->sc->Z, sizeof(double), cudaMemcpyDeviceToHost, st));
     return check_device(c, nullptr);
 }
@@ -810,6 +913,7 @@ int pxsne_get_counters(pxsne_ctx *c, uint64_t *n_accept, uint64_t *n_test,
                        uint64_t *n_warp_steps, uint64_t *n_nodes) {
     int rc = need_state(c);
     if (rc) return rc;
+    if (is3(c)) return unsupported3(c, "pxsne_get_counters");
     DevScalars h;
     CK(c, cudaMemcpyAsync(&h, c->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, c->stream));
     rc = check_device(c, nullptr);
@@ -824,6 +928,7 @@ int pxsne_get_counters(pxsne_ctx *c, uint64_t *n_accept, uint64_t *n_test,
 int pxsne_get_level_counters(pxsne_ctx *c, uint64_t *counts, int32_t levels) {
     int rc = need_state(c);
     if (rc) return rc;
+    if (is3(c)) return unsupported3(c, "pxsne_get_level_counters");
     if (!counts || levels < c->L + 1)
         return fail(c, PXSNE_E_ARG, "need room for %d levels", c->L + 1);
     DevScalars h;
@@ -898,7 +1003,7 @@ int64_t pxsne_device_bytes(const pxsne_ctx *c) {
 }  // extern "C"
 
 // ---------------------------------------------------------------- checkpoints
-// A checkpoint is one flat file: a 136-byte header, then the payload
+// A checkpoint is one flat file: a 144-byte header, then the payload
 //   row_ptr[n+1] int64, col[nnz] int32, val[nnz] float32   (P as CSR)
 //   z[2n] uint32, u[2n] float32, gains[2n] float32           (the state)
 // in the byte order of the machine that wrote it (little-endian on every
@@ -912,14 +1017,15 @@ struct CheckpointHeader {
     uint32_t version;       // 1
     uint32_t header_bytes;  // sizeof(CheckpointHeader)
     pxsne_params params;    // the context's parameters and schedule
+    uint32_t pad0;
     int64_t n, nnz;
     int32_t t, pad1;
     double s[2];
     uint64_t payload_bytes;
     uint64_t checksum;
 };
-static_assert(sizeof(pxsne_params) == 64, "pxsne_params layout");
-static_assert(sizeof(CheckpointHeader) == 136, "checkpoint header layout");
+static_assert(sizeof(pxsne_params) == 68, "pxsne_params layout");
+static_assert(sizeof(CheckpointHeader) == 144, "checkpoint header layout");
 constexpr char kMagic[8] = {'P', 'X', 'S', 'N', 'E', 'C', 'K', 0};
 
 struct Fnv64Words {
@@ -970,6 +1076,7 @@ uint64_t payload_bytes_of(int64_t n, int64_t nnz) {
 int pxsne_save(pxsne_ctx *c, const char *path) {
     int rc = need_state(c);
     if (rc) return rc;
+    if (is3(c)) return unsupported3(c, "pxsne_save");
     if (!path) return fail(c, PXSNE_E_ARG, "path is NULL");
     const int64_t n = c->n, nnz = c->nnz;
     std::vector<int64_t> rp(n + 1);
@@ -1087,4 +1194,31 @@ int pxsne_test_stack_limit(pxsne_ctx *c, int32_t entries) {
                           c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return PXSNE_OK;
+}
+
+int pxsne_get_tree3(pxsne_ctx *c, int32_t level, uint32_t *cnt, uint64_t *sx, uint64_t *sy,
+                    uint64_t *sz, uint32_t *morton) {
+    int rc = need_state(c);
+    if (rc) return rc;
+    if (!is3(c)) return fail(c, PXSNE_E_UNSUPPORTED, "pxsne_get_tree3: 3-D embeddings only");
+    if (level < 0 || level > c->L) return fail(c, PXSNE_E_ARG, "level out of range");
+    cudaStream_t st = c->stream;
+    const size_t cells = size_t(1) << (3 * level);
+    const int64_t all = cells3(c->L), at = level_offset3(level);
+    if (cnt) CK(c, cudaMemcpyAsync(cnt, c->cnt3 + at, cells * 4, cudaMemcpyDeviceToHost, st));
+    if (level == c->L) {
+        uint64_t *out[3] = {sx, sy, sz};
+        for (int d = 0; d < 3; d++)
+            if (out[d])
+                CK(c, cudaMemcpyAsync(out[d], c->sum3 + d * all + at, cells * 8,
+                                      cudaMemcpyDeviceToHost, st));
+    }
+    if (morton) {
+        uint32_t *d = nullptr;
+        CK(c, cudaMallocAsync(&d, (size_t)c->n * 4, st));
+        CK(c, launch_morton3(c, d));
+        CK(c, cudaMemcpyAsync(morton, d, (size_t)c->n * 4, cudaMemcpyDeviceToHost, st));
+        CK(c, cudaFreeAsync(d, st));
+    }
+    return check_device(c, nullptr);
 }

@@ -48,6 +48,11 @@ struct DevScalars {
     u64 knn_exact;       // exact distances computed by the last neighbour search
     u64 knn_insert;      // list insertions of the last neighbour search
     u64 knn_skip;        // (query tile, candidate tile) pairs it skipped by the tile bound
+    // the 3-D embedding (dim = 3): the same scalars for three axes
+    double s3[3], inv_s3[3];
+    float sf3[3];
+    float T3[kMaxL + 2];
+    i64 mm3[2][6];       // [t & 1] = {min_x, min_y, min_z, max_x, max_y, max_z} of zhat
 };
 
 // The pyramid of cell records.  Cell (l, m) (level l, Morton index m) is at
@@ -94,6 +99,70 @@ __device__ __forceinline__ uint32_t morton2(uint32_t px, uint32_t py) {
     return spread_bits16(px) | (spread_bits16(py) << 1);
 }
 
+// floor(a * R / gamma) for 0 <= a < gamma < 2^61 and R <= 2^32, exactly: a
+// double estimate (q = R / gamma) within one of the quotient, then a
+// remainder correction in wrapping 64-bit arithmetic (the true remainder is
+// within +-3 gamma).
+__device__ __forceinline__ uint32_t rescale_exact(u64 a, u64 gamma, double q, u64 R) {
+    u64 q0 = (u64)((double)a * q);
+    if (q0 > R - 1ull) q0 = R - 1ull;
+    i64 r = (i64)(a * R - q0 * gamma);
+#pragma unroll 1
+    for (int k = 0; k < 4 && r < 0; k++) { q0--; r += (i64)gamma; }
+#pragma unroll 1
+    for (int k = 0; k < 4 && (u64)r >= gamma; k++) { q0++; r -= (i64)gamma; }
+    return (uint32_t)q0;
+}
+
+// One axis of a centre-of-mass record: the centre base + S_off / N of a cell
+// whose lower corner is `base` (S_off = S - N base, the sum of the points'
+// offsets in the cell, exact), split at bit 16 as the layout in common.cuh
+// asks.  The offset is one FP32 quotient (relative error about 2^-23 of the
+// cell width, a fraction of an ulp at the leaves).
+__device__ __forceinline__ void record_axis(uint32_t N, u64 S, uint32_t base, int sh,
+                                            float &hi, float &lo) {
+    const u64 soff = S - (u64)N * base;
+    float c = (float)soff / (float)N;  // in [0, 2^sh]
+    c = fminf(c, 4294967040.0f);
+    uint32_t q = (uint32_t)c;
+    float fr = c - (float)q;
+    const uint32_t wmax = sh >= 32 ? 0xffffffffu : ((1u << sh) - 1u);
+    if (q > wmax) {  // rounding at the cell's far edge
+        q = wmax;
+        fr = 1.0f;
+    }
+    hi = (float)(base + (q & 0xffff0000u));
+    lo = (float)(q & 0xffffu) + fr;
+}
+
+// Optimiser parameters of the update kernels (Eq. grad and BH-SNE's gains and
+// momentum).
+struct UpdateParams {
+    float eta, exag, mom0, mom1, min_gain;
+    int exag_iters, mom_switch;
+};
+
+__device__ __forceinline__ int sgnf(float x) { return (x > 0.f) - (x < 0.f); }
+
+// Step of one coordinate; returns zhat.
+__device__ __forceinline__ i64 step1(float fa, float fr, float alpha, float invZ, float mu,
+                                     const UpdateParams &p, float &u, float &gain,
+                                     uint32_t z, double inv_s, unsigned &err) {
+    const float g = 4.0f * (alpha * fa - fr * invZ);
+    float gn = (sgnf(g) != sgnf(u)) ? gain + 0.2f : gain * 0.8f;
+    gn = fmaxf(gn, p.min_gain);
+    gain = gn;
+    u = mu * u - p.eta * gn * g;
+    double st = (double)u * inv_s;
+    const double lim = 288230376151711744.0;  // 2^58 ulps
+    if (!(fabs(st) <= lim)) {
+        err |= isfinite(st) ? (unsigned)PXSNE_DEVERR_RANGE : (unsigned)PXSNE_DEVERR_NONFINITE;
+        st = isfinite(st) ? copysign(lim, st) : 0.0;
+        if (!isfinite(u)) u = 0.f;
+    }
+    return (i64)z + __double2ll_rn(st);
+}
+
 // Extent R_d of screen axis d in ulps: r_d 2^(32 - L) (2^32 when r_d = 0,
 // the square 2^L screen).
 __host__ __device__ inline u64 screen_extent(int32_t r, int L) {
@@ -127,6 +196,9 @@ struct pxsne_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t side = nullptr;          // stream of the attraction (overlaps the traversal)
+    // the attraction inside the traversal kernel (k_bh_traverse<..., ATT>,
+    // environment PXSNE_FORCES=fused); else two kernels on two streams
+    bool fused = false;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     std::string err;
@@ -193,6 +265,19 @@ struct pxsne_ctx {
     double *klpart = nullptr;
     int klblocks = 0;
 
+    // the 3-D embedding (dim = 3): positions, velocities, gains and forces
+    // per point as 4-wide vectors (the fourth lane unused), zhat as three
+    // int64 per point, and the octree's per-level counts and exact sums, its
+    // records {c_hi x, y, z, N} and {c_lo x, y, z, 0} per cell
+    int dim = 2;
+    uint4 *z3 = nullptr;
+    long long *zhat3 = nullptr;
+    float4 *u3 = nullptr, *gains3 = nullptr, *Frep3 = nullptr, *Fattr3 = nullptr;
+    uint32_t *cnt3 = nullptr;
+    unsigned long long *sum3 = nullptr;  // [3][cells]
+    float4 *rec3a = nullptr, *rec3b = nullptr;
+    int64_t *vstart3 = nullptr;          // exclusive scan of the voxel counts
+
     pxsne::DevScalars *sc = nullptr;
     bool state_ready = false;
     cudaGraphExec_t graph = nullptr;
@@ -233,6 +318,7 @@ constexpr int kRelabelEvery = 100;
 cudaError_t launch_relabel(pxsne_ctx *c, cudaStream_t st);
 // out[0..m] = exclusive scan of in[0..m) with out[m] = the total
 cudaError_t scan_u32_to_i64(const uint32_t *in, int64_t m, int64_t *out, cudaStream_t st);
+// traversal (with the attraction when c->fused) and Z
 cudaError_t launch_traverse_zsum(pxsne_ctx *c);
 cudaError_t launch_update(pxsne_ctx *c, cudaEvent_t *marks = nullptr);
 cudaError_t launch_kl(pxsne_ctx *c, double *out_dev);
@@ -251,4 +337,21 @@ cudaError_t launch_morton_keys(pxsne_ctx *c, uint32_t *keys);
 void launch_wait_probe(pxsne_ctx *c, int polls);
 cudaError_t launch_nbr_precision(pxsne_ctx *c, int k, const int32_t *knn_hd, int kh,
                                  int32_t *hits, unsigned long long *total);
+// Z = sum_i Z_i (FP64, fixed order) on the main stream.
+cudaError_t launch_zsum(pxsne_ctx *c);
+// The 3-D embedding (dim3.cu): buffers, the start, one iteration, the tree
+// and forces of the current state, KL, and the state's output.
+constexpr int kMaxL3 = 9;   // voxel screen up to 2^9 per axis (Morton keys < 2^27)
+int64_t cells3(int L);      // (8^(L+1) - 1) / 7
+int64_t level_offset3(int l);  // (8^l - 1) / 7
+cudaError_t launch_morton3(pxsne_ctx *c, uint32_t *out);
+cudaError_t launch_fill3(pxsne_ctx *c, float4 *p, float x, float y, float z);
+cudaError_t alloc3(pxsne_ctx *c);
+void free3(pxsne_ctx *c);
+cudaError_t launch_init3(pxsne_ctx *c, const float *Y0dev, double *scratch);
+cudaError_t launch_iteration3(pxsne_ctx *c);
+cudaError_t launch_prime3(pxsne_ctx *c, bool rescale);
+cudaError_t launch_kl3(pxsne_ctx *c, double *out_dev);
+cudaError_t launch_centre_y3(pxsne_ctx *c, float *Ydev, int32_t *pixdev, double *scratch);
+cudaError_t launch_set_scalars3(pxsne_ctx *c, const double *s, int t);
 }  // namespace pxsne

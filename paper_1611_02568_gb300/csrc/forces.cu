@@ -75,15 +75,97 @@ __device__ __forceinline__ void count_level(u64 *lv, bool me0, bool me1, bool ac
     }
 }
 
+// Eq. grad, first term: Fattr_i = sum_j p_ij w_ij (y_i - y_j), one warp per
+// row (row lengths vary with the in-degree of the kNN graph; a warp per row
+// keeps long rows from stalling short ones).  It runs over the relabelled copy
+// of P (rows and columns in the Morton order of a recent state), so a row's
+// gathered positions zp[j] lie close together in memory, and writes each row's
+// force back under the point's own index.  Each lane keeps four entries in
+// flight; P is streamed with evict-first loads so that the positions stay in
+// L2.  z_i - z_j is formed exactly in float from the 16-bit halves of the
+// fixed-point coordinates (both differences are exact; one final rounding).
+// Entry order within a row is that of P, so the sums equal those over P.
+struct AttractArgs {
+    const int64_t *rp;
+    const int32_t *col;
+    const float *val;
+    const uint2 *z;         // positions under the relabelled labels
+    const uint32_t *aperm;  // relabelled row -> point
+    float2 *Fattr;
+};
+
+__device__ __forceinline__ void attract_row(int row, int lane, const AttractArgs &a, float sf0,
+                                            float sf1) {
+    constexpr int U = 4;
+    const int64_t *__restrict__ rp = a.rp;
+    const int32_t *__restrict__ col = a.col;
+    const float *__restrict__ val = a.val;
+    const uint2 *__restrict__ z = a.z;
+    const uint2 zi = z[row];
+    const float xh = (float)(zi.x & 0xffff0000u), xl = (float)(zi.x & 0xffffu);
+    const float yh = (float)(zi.y & 0xffff0000u), yl = (float)(zi.y & 0xffffu);
+    const int64_t e0 = rp[row], e1 = rp[row + 1];
+    float fx = 0.f, fy = 0.f;
+    // software pipeline: the next batch of P is requested while the current
+    // batch's positions are being gathered
+    int32_t jn[U];
+    float pn[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int64_t q = e0 + lane + 32 * u;
+        jn[u] = q < e1 ? __ldcs(col + q) : row;
+        pn[u] = q < e1 ? __ldcs(val + q) : 0.f;
+    }
+    for (int64_t e = e0 + lane; e < e1; e += 32 * U) {
+        int32_t j[U];
+        float p[U];
+        uint2 zj[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            j[u] = jn[u];
+            p[u] = pn[u];
+            zj[u] = z[j[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int64_t q = e + 32 * (U + u);
+            jn[u] = q < e1 ? __ldcs(col + q) : row;
+            pn[u] = q < e1 ? __ldcs(val + q) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const float dx =
+                ((xh - (float)(zj[u].x & 0xffff0000u)) + (xl - (float)(zj[u].x & 0xffffu))) * sf0;
+            const float dy =
+                ((yh - (float)(zj[u].y & 0xffff0000u)) + (yl - (float)(zj[u].y & 0xffffu))) * sf1;
+            const float w = __fdividef(1.0f, 1.0f + fmaf(dx, dx, dy * dy));
+            const float pw = p[u] * w;
+            fx = fmaf(pw, dx, fx);
+            fy = fmaf(pw, dy, fy);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+    }
+    if (lane == 0) a.Fattr[a.aperm[row]] = make_float2(fx, fy);
+}
+
 struct __align__(16) TravEntry {
     uint32_t node, m0, m1, pad;
 };
 
-template <int CENTRE, int COUNT, bool OWN>
+// ATT: after its 64 points, the warp also computes the attraction of the 64
+// rows of the relabelled P with the same positions in the order (the same
+// per-row sums as k_attract).  The rows' position gathers then wait on memory
+// while other warps of the SM traverse, instead of in a kernel of their own.
+template <int CENTRE, int COUNT, bool OWN, bool ATT>
 __global__ void __launch_bounds__(kTravWarps * 32, 4)
     k_bh_traverse(int n, int L, const uint2 *__restrict__ z, const uint32_t *__restrict__ perm,
                   const float4 *__restrict__ rec, const float *__restrict__ recn,
-                  DevScalars *sc, float2 *__restrict__ Frep, float *__restrict__ Zi) {
+                  DevScalars *sc, float2 *__restrict__ Frep, float *__restrict__ Zi,
+                  AttractArgs att) {
     // stack entry: (level << 28) | Morton index of a node, and for each half of
     // the warp's points the mask of the lanes whose point opens it
     __shared__ TravEntry s_stk[kTravWarps][kTravStack];
@@ -267,6 +349,11 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
         Zi[i1] = zs.y;
     }
     if (overflow && lane == 0) atomicOr(&sc->err, (unsigned)PXSNE_DEVERR_STACK);
+    if (ATT) {
+        const float a0 = sc->sf[0], a1 = sc->sf[1];
+        const int rend = min(n, base + 64);
+        for (int row = base; row < rend; row++) attract_row(row, lane, att, a0, a1);
+    }
     if (COUNT) {
         __syncthreads();
         if (threadIdx.x < (L + 1) * 3) {
@@ -287,75 +374,13 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
     }
 }
 
-// Eq. grad, first term: Fattr_i = sum_j p_ij w_ij (y_i - y_j), one warp per
-// row (row lengths vary with the in-degree of the kNN graph; a warp per row
-// keeps long rows from stalling short ones).  It runs over the relabelled copy
-// of P (rows and columns in the Morton order of a recent state), so a row's
-// gathered positions zp[j] lie close together in memory, and writes each row's
-// force back under the point's own index.  Each lane keeps four entries in
-// flight; P is streamed with evict-first loads so that the positions stay in
-// L2.  z_i - z_j is formed exactly in float from the 16-bit halves of the
-// fixed-point coordinates (both differences are exact; one final rounding).
-// Entry order within a row is that of P, so the sums equal those over P.
+// The attraction as its own kernel: one warp per row.
 __global__ void __launch_bounds__(256)
-    k_attract(int n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-              const float *__restrict__ val, const uint2 *__restrict__ z,
-              const uint32_t *__restrict__ aperm, const DevScalars *__restrict__ sc,
-              float2 *__restrict__ Fattr) {
-    constexpr int U = 4;
+    k_attract(int n, AttractArgs a, const DevScalars *__restrict__ sc) {
     const int lane = threadIdx.x & 31;
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (row >= n) return;
-    const float sf0 = sc->sf[0], sf1 = sc->sf[1];
-    const uint2 zi = z[row];
-    const float xh = (float)(zi.x & 0xffff0000u), xl = (float)(zi.x & 0xffffu);
-    const float yh = (float)(zi.y & 0xffff0000u), yl = (float)(zi.y & 0xffffu);
-    const int64_t e0 = rp[row], e1 = rp[row + 1];
-    float fx = 0.f, fy = 0.f;
-    // software pipeline: the next batch of P is requested while the current
-    // batch's positions are being gathered
-    int32_t jn[U];
-    float pn[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-        const int64_t q = e0 + lane + 32 * u;
-        jn[u] = q < e1 ? __ldcs(col + q) : row;
-        pn[u] = q < e1 ? __ldcs(val + q) : 0.f;
-    }
-    for (int64_t e = e0 + lane; e < e1; e += 32 * U) {
-        int32_t j[U];
-        float p[U];
-        uint2 zj[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            j[u] = jn[u];
-            p[u] = pn[u];
-            zj[u] = z[j[u]];
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int64_t q = e + 32 * (U + u);
-            jn[u] = q < e1 ? __ldcs(col + q) : row;
-            pn[u] = q < e1 ? __ldcs(val + q) : 0.f;
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const float dx =
-                ((xh - (float)(zj[u].x & 0xffff0000u)) + (xl - (float)(zj[u].x & 0xffffu))) * sf0;
-            const float dy =
-                ((yh - (float)(zj[u].y & 0xffff0000u)) + (yl - (float)(zj[u].y & 0xffffu))) * sf1;
-            const float w = __fdividef(1.0f, 1.0f + fmaf(dx, dx, dy * dy));
-            const float pw = p[u] * w;
-            fx = fmaf(pw, dx, fx);
-            fy = fmaf(pw, dy, fy);
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        fx += __shfl_xor_sync(0xffffffffu, fx, o);
-        fy += __shfl_xor_sync(0xffffffffu, fy, o);
-    }
-    if (lane == 0) Fattr[aperm[row]] = make_float2(fx, fy);
+    attract_row(row, lane, a, sc->sf[0], sc->sf[1]);
 }
 
 // Relabelling: new label r is the point perm[r] (Morton order of the last
@@ -441,33 +466,43 @@ __global__ void __launch_bounds__(512)
     }
 }
 
-template <int CENTRE, int COUNT, bool OWN>
+static AttractArgs attract_args(const pxsne_ctx *c) {
+    return AttractArgs{c->rp2, c->col2, c->val2, c->zp, c->aperm, c->Fattr};
+}
+
+template <int CENTRE, int COUNT, bool OWN, bool ATT>
 static void traverse_as(pxsne_ctx *c, cudaStream_t st) {
     const int n = (int)c->n;
     const int per_block = kTravWarps * 64;
-    k_bh_traverse<CENTRE, COUNT, OWN><<<(n + per_block - 1) / per_block, kTravWarps * 32, 0, st>>>(
-        n, c->L, c->z, c->perm, c->rec, c->recn, c->sc, c->Frep, c->Zi);
+    k_bh_traverse<CENTRE, COUNT, OWN, ATT>
+        <<<(n + per_block - 1) / per_block, kTravWarps * 32, 0, st>>>(
+            n, c->L, c->z, c->perm, c->rec, c->recn, c->sc, c->Frep, c->Zi, attract_args(c));
 }
 
-static cudaError_t traverse(pxsne_ctx *c, cudaStream_t st, bool count) {
+template <int CENTRE>
+static void traverse_centre(pxsne_ctx *c, cudaStream_t st, bool count, bool own, bool fused) {
+    if (fused)  // (a fused traversal never counts)
+        own ? traverse_as<CENTRE, 0, true, true>(c, st) : traverse_as<CENTRE, 0, false, true>(c, st);
+    else if (count)
+        own ? traverse_as<CENTRE, 1, true, false>(c, st) : traverse_as<CENTRE, 1, false, false>(c, st);
+    else
+        own ? traverse_as<CENTRE, 0, true, false>(c, st) : traverse_as<CENTRE, 0, false, false>(c, st);
+}
+
+// The traversal, and with fused = true the attraction inside the same kernel.
+static cudaError_t traverse(pxsne_ctx *c, cudaStream_t st, bool count, bool fused = false) {
     // the own-cell test is redundant below theta = 1 (with a margin for the
     // rounding of d^2)
     const bool own = c->p.theta >= 0.999f;
-    if (c->p.centre_mode == 0) {
-        if (count) own ? traverse_as<0, 1, true>(c, st) : traverse_as<0, 1, false>(c, st);
-        else own ? traverse_as<0, 0, true>(c, st) : traverse_as<0, 0, false>(c, st);
-    } else {
-        if (count) own ? traverse_as<1, 1, true>(c, st) : traverse_as<1, 1, false>(c, st);
-        else own ? traverse_as<1, 0, true>(c, st) : traverse_as<1, 0, false>(c, st);
-    }
+    if (c->p.centre_mode == 0) traverse_centre<0>(c, st, count && !fused, own, fused);
+    else traverse_centre<1>(c, st, count && !fused, own, fused);
     return cudaGetLastError();
 }
 
 cudaError_t launch_attract(pxsne_ctx *c, cudaStream_t st) {
     const int n = (int)c->n;
     const int att_blocks = (int)((int64_t(n) * 32 + 255) / 256);
-    k_attract<<<att_blocks, 256, 0, st>>>(n, c->rp2, c->col2, c->val2, c->zp, c->aperm, c->sc,
-                                          c->Fattr);
+    k_attract<<<att_blocks, 256, 0, st>>>(n, attract_args(c), c->sc);
     return cudaGetLastError();
 }
 
@@ -475,6 +510,8 @@ static cudaError_t zsum(pxsne_ctx *c, cudaStream_t st) {
     k_zsum<<<c->zblocks, 512, 0, st>>>((int)c->n, c->Zi, c->zpart, c->sc);
     return cudaGetLastError();
 }
+
+cudaError_t launch_zsum(pxsne_ctx *c) { return zsum(c, c->stream); }
 
 cudaError_t launch_relabel(pxsne_ctx *c, cudaStream_t st) {
     const int n = (int)c->n;
@@ -510,15 +547,25 @@ cudaError_t launch_accumulate_counters(pxsne_ctx *c) {
 }
 
 cudaError_t launch_traverse_zsum(pxsne_ctx *c) {
-    cudaError_t e = traverse(c, c->stream, false);
+    cudaError_t e = traverse(c, c->stream, false, c->fused);
     if (e) return e;
     return zsum(c, c->stream);
 }
 
 // Sequential forces (traversal, attraction, Z) with optional timing marks.
+// Timed (marks) and fused, the one kernel is the traversal group and the
+// attraction group is empty.
 cudaError_t launch_forces(pxsne_ctx *c, cudaEvent_t *marks) {
     cudaStream_t st = c->stream;
     cudaError_t e;
+    if (marks && c->fused) {
+        if ((e = cudaEventRecord(marks[KG_TRAVERSE], st))) return e;
+        if ((e = traverse(c, st, false, true))) return e;
+        if ((e = cudaEventRecord(marks[KG_ATTRACT], st))) return e;
+        if ((e = cudaEventRecord(marks[KG_ZSUM], st))) return e;
+        if ((e = zsum(c, st))) return e;
+        return cudaEventRecord(marks[KG_COUNT], st);
+    }
     if (marks && (e = cudaEventRecord(marks[KG_TRAVERSE], st))) return e;
     // the initial state's traversal keeps the work counters (the level
     // counters restart with it); a timed one is the kernel of the iteration

@@ -14,21 +14,6 @@
 
 namespace pxsne {
 
-// floor(a * R / gamma) for 0 <= a < gamma < 2^61 and R <= 2^32, exactly: a
-// double estimate (q = R / gamma) within one of the quotient, then a
-// remainder correction in wrapping 64-bit arithmetic (the true remainder is
-// within +-3 gamma).
-__device__ __forceinline__ uint32_t rescale_exact(u64 a, u64 gamma, double q, u64 R) {
-    u64 q0 = (u64)((double)a * q);
-    if (q0 > R - 1ull) q0 = R - 1ull;
-    i64 r = (i64)(a * R - q0 * gamma);
-#pragma unroll 1
-    for (int k = 0; k < 4 && r < 0; k++) { q0--; r += (i64)gamma; }
-#pragma unroll 1
-    for (int k = 0; k < 4 && (u64)r >= gamma; k++) { q0++; r -= (i64)gamma; }
-    return (uint32_t)q0;
-}
-
 __global__ void k_snap_hist(int n, int L, int rescale, float theta, u64 Rx, u64 Ry,
                             const longlong2 *__restrict__ zhat, uint2 *__restrict__ z,
                             const uint32_t *__restrict__ perm, uint32_t *__restrict__ rank,
@@ -123,27 +108,6 @@ __global__ void k_snap_hist(int n, int L, int rescale, float theta, u64 Rx, u64 
     }
     base = __shfl_sync(0xffffffffu, base, end);
     if (valid) rank[i] = base + (uint32_t)(lane - start);
-}
-
-// One axis of a centre-of-mass record: the centre base + S_off / N of a cell
-// whose lower corner is `base` (S_off = S - N base, the sum of the points'
-// offsets in the cell, exact), split at bit 16 as the layout in common.cuh
-// asks.  The offset is one FP32 quotient (relative error about 2^-23 of the
-// cell width, a fraction of an ulp at the leaves).
-__device__ __forceinline__ void record_axis(uint32_t N, u64 S, uint32_t base, int sh,
-                                            float &hi, float &lo) {
-    const u64 soff = S - (u64)N * base;
-    float c = (float)soff / (float)N;  // in [0, 2^sh]
-    c = fminf(c, 4294967040.0f);
-    uint32_t q = (uint32_t)c;
-    float fr = c - (float)q;
-    const uint32_t wmax = sh >= 32 ? 0xffffffffu : ((1u << sh) - 1u);
-    if (q > wmax) {  // rounding at the cell's far edge
-        q = wmax;
-        fr = 1.0f;
-    }
-    hi = (float)(base + (q & 0xffff0000u));
-    lo = (float)(q & 0xffffu) + fr;
 }
 
 // Centre-of-mass record of cell m of level l (layout in common.cuh).

@@ -11,32 +11,6 @@
 
 namespace pxsne {
 
-struct UpdateParams {
-    float eta, exag, mom0, mom1, min_gain;
-    int exag_iters, mom_switch;
-};
-
-__device__ __forceinline__ int sgnf(float x) { return (x > 0.f) - (x < 0.f); }
-
-// Step of one coordinate; returns zhat.
-__device__ __forceinline__ i64 step1(float fa, float fr, float alpha, float invZ, float mu,
-                                     const UpdateParams &p, float &u, float &gain,
-                                     uint32_t z, double inv_s, unsigned &err) {
-    const float g = 4.0f * (alpha * fa - fr * invZ);
-    float gn = (sgnf(g) != sgnf(u)) ? gain + 0.2f : gain * 0.8f;
-    gn = fmaxf(gn, p.min_gain);
-    gain = gn;
-    u = mu * u - p.eta * gn * g;
-    double st = (double)u * inv_s;
-    const double lim = 288230376151711744.0;  // 2^58 ulps
-    if (!(fabs(st) <= lim)) {
-        err |= isfinite(st) ? (unsigned)PXSNE_DEVERR_RANGE : (unsigned)PXSNE_DEVERR_NONFINITE;
-        st = isfinite(st) ? copysign(lim, st) : 0.0;
-        if (!isfinite(u)) u = 0.f;
-    }
-    return (i64)z + __double2ll_rn(st);
-}
-
 __global__ void __launch_bounds__(256)
     k_update(int n, UpdateParams p, const uint2 *__restrict__ z,
              const float2 *__restrict__ Frep, const float2 *__restrict__ Fattr,

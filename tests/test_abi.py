@@ -46,7 +46,10 @@ def test_default_params_and_binding_mirror(lib):
 def test_create_rejects_bad_params(lib):
     L = px.load()
     for bad in (dict(log2_r=0), dict(log2_r=15), dict(theta=-1.0), dict(k=0),
-                dict(perplexity=200.0), dict(momentum1=1.0), dict(centre_mode=2)):
+                dict(perplexity=200.0), dict(momentum1=1.0), dict(centre_mode=2),
+                dict(screen_x=3000, log2_r=11), dict(knn_probe=5000), dict(dim=4),
+                dict(dim=1), dict(dim=3, log2_r=10), dict(dim=3, screen_x=100),
+                dict(dim=3, centre_mode=1)):
         p = px.Params(**bad).c()
         h = ctypes.c_void_p()
         rc = L.pxsne_create(ctypes.byref(h), ctypes.byref(p), None)

@@ -57,15 +57,15 @@ MUTANTS = [
      "t[o].r = j; t[o].c = (int32_t)i;", "t[o].r = i; t[o].c = j;"),
     # screen map (Eq. z1/z2)
     ("init: extremes taken over the other axis", C_SRC,
-     "double v = Y0[2 * i + d];", "double v = Y0[2 * i + (1 - d)];"),
+     "double v = Y0[dim * i + d];", "double v = Y0[dim * i + (1 - d)];"),
     ("init: ceiling in place of the floor", C_SRC,
-     "double q = floor((Y0[2 * i + d] - mn) * Rd / range);",
-     "double q = ceil((Y0[2 * i + d] - mn) * Rd / range);"),
+     "double q = floor((Y0[dim * i + d] - mn) * Rd / range);",
+     "double q = ceil((Y0[dim * i + d] - mn) * Rd / range);"),
     ("init: extent of the other axis", C_SRC,
      "const double Rd = R[d];", "const double Rd = R[1 - d];"),
     ("init: zero-extent axis off the origin", C_SRC,
-     "for (int64_t i = 0; i < n; i++) z[2 * i + d] = 0u;",
-     "for (int64_t i = 0; i < n; i++) z[2 * i + d] = 1u;"),
+     "for (int64_t i = 0; i < n; i++) z[dim * i + d] = 0u;",
+     "for (int64_t i = 0; i < n; i++) z[dim * i + d] = 1u;"),
     # tree (Sec. 4.1)
     ("morton: x and y bits swapped", C_SRC,
      "m |= ((px >> b) & 1u) << (2 * b);\n        m |= ((py >> b) & 1u) << (2 * b + 1);",
@@ -89,14 +89,19 @@ MUTANTS = [
      "double dd = dx * dx + dy * dy;\n            if (!leaf", "double dd = dx * dx;\n            if (!leaf"),
     ("bh: centre-of-mass remainder added, not subtracted", C_SRC,
      "- (double)r / (double)N;", "+ (double)r / (double)N;"),
-    ("bh: own point left in the x sum of its leaf", C_SRC, "Sx -= zx;", ""),
+    ("bh: own point left in the x sum of its leaf", C_SRC,
+     "Sx -= zx;\n                Sy -= zy;\n            }", "Sy -= zy;\n            }"),
     ("bh: own point counted in its leaf", C_SRC,
-     "N -= 1;\n                if (N == 0) continue;", "if (N == 0) continue;"),
+     "N -= 1;\n                if (N == 0) continue;\n                Sx -= zx;\n                Sy -= zy;\n            }",
+     "if (N == 0) continue;\n                Sx -= zx;\n                Sy -= zy;\n            }"),
     ("bh: own cells above the leaves left to the criterion", C_SRC,
      "int contains = ((mi >> (2 * (L - l))) == mc);",
      "int contains = leaf && ((mi >> (2 * (L - l))) == mc);"),
-    ("bh: force missing one kernel factor", C_SRC, "fx += Nw * w * dx;", "fx += Nw * dx;"),
-    ("bh: acceptance test reversed", C_SRC, "(rc2 < th2 * dd)", "(rc2 > th2 * dd)"),
+    ("bh: force missing one kernel factor", C_SRC,
+     "fx += Nw * w * dx;\n            fy += Nw * w * dy;\n            acc++;",
+     "fx += Nw * dx;\n            fy += Nw * w * dy;\n            acc++;"),
+    ("bh: acceptance test reversed", C_SRC, "crit_mode == 0 ? (rc2 < th2 * dd)",
+     "crit_mode == 0 ? (rc2 > th2 * dd)"),
     ("bh: cell size of the child level", C_SRC,
      "double rc2 = (s0 * W) * (s0 * W) + (s1 * W) * (s1 * W);",
      "double rc2 = 0.25 * ((s0 * W) * (s0 * W) + (s1 * W) * (s1 * W));"),
@@ -104,15 +109,17 @@ MUTANTS = [
      "double rc2 = (s0 * W) * (s0 * W) + (s1 * W) * (s1 * W);",
      "double rc2 = (s0 * W) * (s0 * W);"),
     ("bh: sampled rows ignored", C_SRC,
-     "int64_t i = rows ? rows[q] : q;\n        const uint32_t zx",
-     "int64_t i = q;\n        const uint32_t zx"),
+     "int64_t i = rows ? rows[q] : q;\n        const uint32_t zx = z[2 * i]",
+     "int64_t i = q;\n        const uint32_t zx = z[2 * i]"),
     ("bh geometric: centre at the cell's corner", C_SRC,
      "((double)cx * W + 0.5 * W)", "((double)cx * W)"),
     ("bh geometric: x and y cell bits swapped", C_SRC,
      "cx |= ((mc >> (2 * b)) & 1u) << b;\n                    cy |= ((mc >> (2 * b + 1)) & 1u) << b;",
      "cy |= ((mc >> (2 * b)) & 1u) << b;\n                    cx |= ((mc >> (2 * b + 1)) & 1u) << b;"),
     # exact repulsion and attraction (Eq. grad)
-    ("exact repulsion: w instead of w^2", C_SRC, "fx += w * w * dx;", "fx += w * dx;"),
+    ("exact repulsion: w instead of w^2", C_SRC,
+     "fx += w * w * dx;\n            fy += w * w * dy;\n        }",
+     "fx += w * dx;\n            fy += w * w * dy;\n        }"),
     ("exact repulsion: a point counted against itself", C_SRC,
      "if (j == i) continue;\n            double dx = s0 * (double)((int64_t)z[2 * i] - (int64_t)z[2 * j]);\n"
      "            double dy = s1 * (double)((int64_t)z[2 * i + 1] - (int64_t)z[2 * j + 1]);\n"
@@ -132,10 +139,12 @@ MUTANTS = [
     ("exact repulsion: kernel without the y offset", C_SRC,
      "double w = 1.0 / (1.0 + dx * dx + dy * dy);\n            zs += w;",
      "double w = 1.0 / (1.0 + dx * dx);\n            zs += w;"),
-    ("attraction: wrong sign", C_SRC, "fx += val[e] * w * dx;", "fx -= val[e] * w * dx;"),
+    ("attraction: wrong sign", C_SRC,
+     "fx += val[e] * w * dx;\n            fy += val[e] * w * dy;\n        }",
+     "fx -= val[e] * w * dx;\n            fy += val[e] * w * dy;\n        }"),
     ("attraction: kernel squared", C_SRC,
-     "fx += val[e] * w * dx;\n            fy += val[e] * w * dy;",
-     "fx += val[e] * w * w * dx;\n            fy += val[e] * w * w * dy;"),
+     "fx += val[e] * w * dx;\n            fy += val[e] * w * dy;\n        }",
+     "fx += val[e] * w * w * dx;\n            fy += val[e] * w * w * dy;\n        }"),
     # optimiser step (Eq. grad, BH-SNE's gains and momentum)
     ("update: exaggeration applied to repulsion too", C_SRC,
      "double g = 4.0 * (alpha * Fattr[k] - Frep[k] / Z);",
@@ -152,11 +161,11 @@ MUTANTS = [
      "u[k] = mu * u[k] - eta * gn * g;", "u[k] = -mu * u[k] - eta * gn * g;"),
     # the run's schedule (exaggeration and momentum phases)
     ("run: exaggeration one iteration too long", C_SRC,
-     "double alpha = t < p->exag_iters ? p->exag : 1.0;",
-     "double alpha = t <= p->exag_iters ? p->exag : 1.0;"),
+     "orc_attraction(row_ptr, col, val, z, s, NULL, n, Fattr);\n        double alpha = t < p->exag_iters",
+     "orc_attraction(row_ptr, col, val, z, s, NULL, n, Fattr);\n        double alpha = t <= p->exag_iters"),
     ("run: momentum phases swapped", C_SRC,
-     "double mu = t < p->mom_switch ? p->mom0 : p->mom1;",
-     "double mu = t < p->mom_switch ? p->mom1 : p->mom0;"),
+     "double mu = t < p->mom_switch ? p->mom0 : p->mom1;\n        orc_update(",
+     "double mu = t < p->mom_switch ? p->mom1 : p->mom0;\n        orc_update("),
     ("run: centre mode not passed to the repulsion", C_SRC,
      "p->theta, p->crit_mode, p->centre_mode,\n                             cnt, sx, sy",
      "p->theta, p->crit_mode, 0,\n                             cnt, sx, sy"),
@@ -179,16 +188,39 @@ MUTANTS = [
     ("rescale: both axes' extremes from x", C_SRC,
      "int64_t mn = zhat[d], mx = zhat[d];", "int64_t mn = zhat[0], mx = zhat[0];"),
     ("rescale: offset from the maximum", C_SRC,
-     "(uint64_t)(zhat[2 * i + d] - mn) * Rd", "(uint64_t)(mx - zhat[2 * i + d]) * Rd"),
+     "(uint64_t)(zhat[dim * i + d] - mn) * Rd", "(uint64_t)(mx - zhat[dim * i + d]) * Rd"),
+    # the 3-D embedding (octree)
+    ("morton3: x bits taken from z", C_SRC,
+     "m |= ((px >> b) & 1u) << (3 * b);", "m |= ((pz >> b) & 1u) << (3 * b);"),
+    ("level_offset3: levels of four cells", C_SRC, "o += p; p *= 8; }", "o += p; p *= 4; }"),
+    ("pyramid3: z sums accumulate y", C_SRC, "sz[c] += z[3 * i + 2];", "sz[c] += z[3 * i + 1];"),
+    ("bh3: cell diagonal without the z axis", C_SRC,
+     "double rc2 = (s0 * W) * (s0 * W) + (s1 * W) * (s1 * W) + (s2 * W) * (s2 * W);",
+     "double rc2 = (s0 * W) * (s0 * W) + (s1 * W) * (s1 * W);"),
+    ("bh3: distance along x and y only", C_SRC,
+     "double dd = dx * dx + dy * dy + dz * dz;", "double dd = dx * dx + dy * dy;"),
+    ("bh3: own voxel keeps the point's z", C_SRC, "                Sz -= zz;\n", ""),
+    ("attraction3: z force from the y difference", C_SRC,
+     "            fz += val[e] * w * dz;", "            fz += val[e] * w * dy;"),
+    ("kl3: distance along x and y only", C_SRC,
+     "double q = 1.0 / ((1.0 + dx * dx + dy * dy + dz * dz) * Z);",
+     "double q = 1.0 / ((1.0 + dx * dx + dy * dy) * Z);"),
+    ("update: coordinates strided by two whatever the dimension", C_SRC,
+     "int64_t k = dim * i + d;", "int64_t k = 2 * i + d;"),
+    ("rescale: extremes strided by two whatever the dimension", C_SRC,
+     "int64_t v = zhat[dim * i + d];", "int64_t v = zhat[2 * i + d];"),
     # KL (Eq. cost_func)
     ("kl: q not normalised by Z", C_SRC,
      "double q = 1.0 / ((1.0 + dx * dx + dy * dy) * Z);",
      "double q = 1.0 / (1.0 + dx * dx + dy * dy);"),
     ("kl: distance along x only", C_SRC,
      "double q = 1.0 / ((1.0 + dx * dx + dy * dy) * Z);", "double q = 1.0 / ((1.0 + dx * dx) * Z);"),
-    ("kl: ratio inverted", C_SRC, "c += p * log(p / q);", "c += p * log(q / p);"),
+    ("kl: ratio inverted", C_SRC,
+     "double q = 1.0 / ((1.0 + dx * dx + dy * dy) * Z);\n            c += p * log(p / q);",
+     "double q = 1.0 / ((1.0 + dx * dx + dy * dy) * Z);\n            c += p * log(q / p);"),
     ("kl: stored zeros of P not skipped", C_SRC,
-     "if (p <= 0.0) continue;", "if (p < 0.0) continue;"),
+     "if (p <= 0.0) continue;\n            int64_t j = col[e];\n            double dx = s0 * (double)((int64_t)z[2 * i]",
+     "if (p < 0.0) continue;\n            int64_t j = col[e];\n            double dx = s0 * (double)((int64_t)z[2 * i]"),
     ("kl: Z of the tree replaced by the exact sum", C_SRC,
      "    if (p->exact) {\n        orc_exact_repulsion(z, s, n, NULL, n, Frep, Zi);\n    } else {",
      "    if (1) {\n        orc_exact_repulsion(z, s, n, NULL, n, Frep, Zi);\n    } else {"),

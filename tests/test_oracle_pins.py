@@ -1023,3 +1023,203 @@ def test_screen_run_step_is_the_composition_of_its_parts():
     oracle.run(P, st, prm, 40)
     px, py = st.z[:, 0] >> 25, st.z[:, 1] >> 25
     assert px.min() == 0 and px.max() == 99 and py.min() == 0 and py.max() == 127
+
+
+# ---------------------------------------------------------------- 3-D embedding
+def _kl3_y(Pd, Y):
+    """Eq. cost_func from its definition on a dense P and 3-D y (numpy)."""
+    D2 = ((Y[:, None, :] - Y[None, :, :]) ** 2).sum(-1)
+    W = 1.0 / (1.0 + D2)
+    np.fill_diagonal(W, 0.0)
+    Q = W / W.sum()
+    m = Pd > 0
+    return float((Pd[m] * np.log(Pd[m] / Q[m])).sum())
+
+
+def test_morton3_is_the_octree_child_numbering():
+    rng = np.random.default_rng(40)
+    L = 7
+    for _ in range(200):
+        px, py, pz = (int(v) for v in rng.integers(0, 2 ** L, 3))
+        m = 0
+        for b in range(L - 1, -1, -1):       # root to leaf: child = 4 z + 2 y + x
+            m = 8 * m + 4 * ((pz >> b) & 1) + 2 * ((py >> b) & 1) + ((px >> b) & 1)
+        assert oracle.morton3(px, py, pz) == m
+    assert [oracle.level_offset3(l) for l in range(4)] == [0, 1, 9, 73]
+
+
+def test_pyramid3_counts_and_sums():
+    rng = np.random.default_rng(41)
+    L = 4
+    z = rng.integers(0, 2 ** 32, (500, 3), dtype=np.uint64).astype(np.uint32)
+    z[:50] = z[50]                            # one crowded voxel
+    cnt, sx, sy, sz = oracle.pyramid3(z, L)
+    vox = z >> (32 - L)
+    for l in range(L + 1):
+        key = [oracle.morton3(*(v >> (L - l))) for v in vox]
+        off = oracle.level_offset3(l)
+        ref = np.bincount(key, minlength=8 ** l)
+        assert np.array_equal(cnt[off:off + 8 ** l], ref)
+        for ax, S in enumerate((sx, sy, sz)):
+            acc = {}
+            for k, v in zip(key, z[:, ax]):
+                acc[k] = acc.get(k, 0) + int(v)
+            for k, v in acc.items():
+                assert int(S[off + k]) == v
+
+
+def test_bh3_theta0_and_the_exact_sum():
+    rng = np.random.default_rng(42)
+    z, s = oracle.init_fx3(rng.standard_normal((300, 3)))
+    Fe, Ze = oracle.exact_repulsion3(z, s)
+    # one point per voxel (L = 8, checked): theta = 0 is the exact sum
+    assert len({tuple(v) for v in (z >> 24)}) == len(z)
+    F, Zi, _ = oracle.bh_repulsion3(z, s, 8, 0.0)
+    assert np.abs(F - Fe).max() <= 1e-12 * np.abs(Fe).max()
+    assert np.abs(Zi - Ze).max() <= 1e-12 * Ze.max()
+    # Newton's third law on the exact sum
+    assert np.abs(Fe.sum(0)).max() <= 1e-10 * np.abs(Fe).sum()
+    # the error falls with theta
+    errs = [np.linalg.norm(oracle.bh_repulsion3(z, s, 8, th)[0] - Fe) / np.linalg.norm(Fe)
+            for th in (0.25, 0.5, 1.0)]
+    assert errs[0] < errs[1] < errs[2] < 0.05
+
+
+def test_bh3_theta0_is_the_voxel_bruteforce():
+    # with several points per voxel, theta = 0 sums every other voxel's centre
+    # of mass (weight N) and the own voxel without the point itself
+    rng = np.random.default_rng(43)
+    L = 4
+    z, s = oracle.init_fx3(rng.standard_normal((400, 3)))
+    F, Zi, _ = oracle.bh_repulsion3(z, s, L, 0.0)
+    vox = [tuple(v) for v in (z >> (32 - L))]
+    groups = {}
+    for i, v in enumerate(vox):
+        groups.setdefault(v, []).append(i)
+    zz = z.astype(np.float64)
+    for i in range(0, 400, 37):
+        f = np.zeros(3)
+        zs = 0.0
+        for v, mem in groups.items():
+            mem = [j for j in mem if j != i]
+            if not mem:
+                continue
+            c = zz[mem].mean(0)
+            d = s * (zz[i] - c)
+            w = 1.0 / (1.0 + d @ d)
+            zs += len(mem) * w
+            f += len(mem) * w * w * d
+        np.testing.assert_allclose(F[i], f, rtol=1e-9, atol=1e-14)
+        assert Zi[i] == pytest.approx(zs, rel=1e-10)
+
+
+def test_gradient3_is_the_derivative_of_the_kl():
+    # 4 (Fattr - Frep / Z) (exact repulsion) against central differences of
+    # the KL written from its definition in y-space
+    rng = np.random.default_rng(44)
+    n = 40
+    A = rng.random((n, n)) * (rng.random((n, n)) < 0.3)
+    A = A + A.T
+    np.fill_diagonal(A, 0)
+    Pd = A / A.sum()
+    P = _dense_csr(Pd)
+    z, s = oracle.init_fx3(rng.standard_normal((n, 3)))
+    Y = z.astype(np.float64) * s
+    Fa = oracle.attraction3(P, z, s)
+    Fr, Zi = oracle.exact_repulsion3(z, s)
+    g = 4.0 * (Fa - Fr / Zi.sum())
+    h = 1e-5
+    for i in range(0, n, 7):
+        for d in range(3):
+            Yp, Ym = Y.copy(), Y.copy()
+            Yp[i, d] += h
+            Ym[i, d] -= h
+            fd = (_kl3_y(Pd, Yp) - _kl3_y(Pd, Ym)) / (2 * h)
+            assert g[i, d] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+    assert oracle.kl3(P, z, s, Zi.sum()) == pytest.approx(_kl3_y(Pd, Y), rel=1e-10)
+
+
+def test_update3_and_rescale3_per_coordinate():
+    # the optimiser acts per coordinate: a 3-D step equals the 2-D one on the
+    # same coordinates; the rescale is exact per axis (big integers)
+    rng = np.random.default_rng(45)
+    n = 300
+    z = rng.integers(0, 2 ** 32, (n, 3), dtype=np.uint64).astype(np.uint32)
+    s = np.array([1e-6, 2e-6, 3e-7])
+    Fa, Fr = rng.standard_normal((n, 3)), rng.standard_normal((n, 3))
+    u, g = rng.standard_normal((n, 3)) * 1e-3, rng.uniform(0.5, 2, (n, 3))
+    u3, g3 = u.copy(), g.copy()
+    zh3, gr3 = oracle.update3(z, s, Fa, Fr, 3.5, 12.0, 0.5, 200.0, u3, g3)
+    for cols in ((0, 1), (2, 2)):
+        c = list(cols)
+        u2, g2 = np.ascontiguousarray(u[:, c]), np.ascontiguousarray(g[:, c])
+        zh2, gr2 = oracle.update(np.ascontiguousarray(z[:, c]), s[c], Fa[:, c], Fr[:, c], 3.5,
+                                 12.0, 0.5, 200.0, u2, g2)
+        assert np.array_equal(zh3[:, c], zh2) and np.array_equal(u3[:, c], u2)
+        assert np.array_equal(g3[:, c], g2) and np.array_equal(gr3[:, c], gr2)
+    zhat = np.stack([rng.integers(-2 ** 40, 2 ** 40, n), rng.integers(5, 2 ** 20, n),
+                     rng.integers(-(2 ** 58), 2 ** 58, n)], 1)
+    zr, sr = oracle.rescale3(zhat, s)
+    for d in range(3):
+        mn, mx = int(zhat[:, d].min()), int(zhat[:, d].max())
+        gamma = mx - mn + 1
+        assert [int(v) for v in zr[:, d]] == [((int(v) - mn) << 32) // gamma for v in zhat[:, d]]
+        assert sr[d] == (s[d] * float(gamma)) / 2.0 ** 32
+
+
+def test_run3_step_is_the_composition_of_its_parts():
+    n = 250
+    rng = np.random.default_rng(46)
+    A = (rng.random((n, n)) < 0.05) * rng.random((n, n))
+    A = A + A.T
+    np.fill_diagonal(A, 0)
+    P = _dense_csr(A / A.sum())
+    prm = oracle.Params(L=5)
+    st = oracle.State3.from_y0(rng.standard_normal((n, 3)))
+    ref = st.copy()
+    oracle.run3(P, st, prm, 1)
+    Fr, Zi, _ = oracle.bh_repulsion3(ref.z, ref.s, prm.L, prm.theta)
+    Fa = oracle.attraction3(P, ref.z, ref.s)
+    zhat, _ = oracle.update3(ref.z, ref.s, Fa, Fr, float(np.cumsum(Zi)[-1]), prm.exag, prm.mom0,
+                             prm.eta, ref.u, ref.gains, min_gain=prm.min_gain)
+    zr, sr = oracle.rescale3(zhat, ref.s)
+    assert np.array_equal(st.z, zr) and np.array_equal(st.s, sr)
+    assert np.array_equal(st.u, ref.u) and np.array_equal(st.gains, ref.gains)
+    # without exaggeration a run lowers the KL from its start, and keeps every
+    # voxel axis spanned
+    plain = oracle.Params(L=5, exag=1.0)
+    kl0 = oracle.kl_of3(P, st, plain)
+    oracle.run3(P, st, plain, 60)
+    assert oracle.kl_of3(P, st, plain) < kl0
+    vox = st.z >> (32 - prm.L)
+    assert vox.min() == 0 and vox.max() == 2 ** prm.L - 1
+
+
+def test_bh3_acceptance_threshold_is_the_cell_diagonal():
+    # Eq. bh_criteria in 3-D on a hand-built tree: A near the origin, B1 and B2
+    # in the far octant (level 1) but in different level-2 cells.  Just above
+    # theta* = r_c / d (r_c = W sqrt(s0^2 + s1^2 + s2^2), W = 2^31, d from A to
+    # the octant's centre of mass) the octant is accepted as one body; just
+    # below it is opened and A meets B1 and B2 one by one.
+    L = 5
+    z = np.array([[1 << 27, 3 << 26, 5 << 25],
+                  [(3 << 30) + 12345, (3 << 30) + 777, (3 << 30) + 99],
+                  [(2 << 30) + 4321, (2 << 30) + 55, (2 << 30) + 8]], np.uint32)
+    s = np.array([1.3e-9, 0.7e-9, 2.1e-9])
+    zz = z.astype(np.float64)
+    com = zz[1:].mean(0)
+    dA = s * (zz[0] - com)
+    rc = 2.0 ** 31 * np.sqrt((s ** 2).sum())
+    th = rc / np.sqrt(dA @ dA)
+    w = 1.0 / (1.0 + dA @ dA)
+    one_body = 2.0 * w * w * dA
+    each = np.zeros(3)
+    for j in (1, 2):
+        d = s * (zz[0] - zz[j])
+        wj = 1.0 / (1.0 + d @ d)
+        each += wj * wj * d
+    assert np.abs(one_body - each).max() > 1e-6 * np.abs(each).max()
+    F_hi, _, _ = oracle.bh_repulsion3(z, s, L, th * (1 + 1e-9), rows=[0])
+    F_lo, _, _ = oracle.bh_repulsion3(z, s, L, th * (1 - 1e-9), rows=[0])
+    np.testing.assert_allclose(F_hi[0], one_body, rtol=1e-10)
+    np.testing.assert_allclose(F_lo[0], each, rtol=1e-10)
