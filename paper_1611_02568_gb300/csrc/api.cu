@@ -233,10 +233,9 @@ cudaError_t relabel_if_due(pxsne_ctx *c) {
 
 // One iteration.  With timing marks every kernel runs in order on the main
 // stream.  Without, the attraction (which needs only the rescaled positions
-// and P) runs on the side stream concurrently with the traversal: the
-// traversal is enqueued first so that its blocks are dispatched first, and
-// the attraction's blocks fill the SMs as the traversal's drain.  The two
-// join before the next update.
+// and P) runs on the side stream concurrently with the traversal: both are
+// persistent grids sized to share the SMs (kTravCtasPerSm, kAttCtasPerSm),
+// the traversal enqueued first.  The two join before the next update.
 int one_iteration(pxsne_ctx *c, cudaEvent_t *marks = nullptr) {
     if (is3(c)) {
         CK(c, launch_iteration3(c));
@@ -249,10 +248,6 @@ int one_iteration(pxsne_ctx *c, cudaEvent_t *marks = nullptr) {
         return PXSNE_OK;
     }
     CK(c, launch_tree(c, true));
-    if (c->fused) {
-        CK(c, launch_traverse_zsum(c));
-        return PXSNE_OK;
-    }
     CK(c, cudaEventRecord(c->ev_fork, c->stream));
     CK(c, launch_traverse_zsum(c));
     CK(c, cudaStreamWaitEvent(c->side, c->ev_fork, 0));
@@ -324,6 +319,8 @@ int pxsne_create(pxsne_ctx **out, const pxsne_params *p, void *stream) {
     if (!c) return fail(nullptr, PXSNE_E_OOM, "host allocation");
     c->p = *p;
     cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e == cudaSuccess) {
         if (stream) {
             c->stream = (cudaStream_t)stream;
@@ -340,10 +337,6 @@ int pxsne_create(pxsne_ctx **out, const pxsne_params *p, void *stream) {
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, lo);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
-    }
-    {
-        const char *f = getenv("PXSNE_FORCES");
-        c->fused = f && f[0] == 'f';
     }
     if (e == cudaSuccess) e = dalloc(c, &c->sc, 1);
     if (e == cudaSuccess) e = cudaMemset(c->sc, 0, sizeof(DevScalars));

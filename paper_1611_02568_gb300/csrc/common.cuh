@@ -19,6 +19,13 @@ constexpr int kMaxL = 14;           // screen up to 2^14 x 2^14 (Morton keys < 2
 constexpr int64_t kMaxN = 1 << 24;  // cell counts are exact floats below 2^24
 constexpr int kTravWarps = 8;       // warps per CTA in the traversal
 constexpr int kTravStack = 48;      // entries per warp; depth <= 3L - 2 <= 40
+// Persistent grids of the forces: CTAs per SM of the traversal and of the
+// attraction that runs beside it on the side stream.  The traversal alone is
+// fastest at four CTAs (all of the SM's registers); at two it leaves room
+// for three of the attraction's CTAs from the start, and the whole
+// 1000-iteration schedule at n = 1M runs 6.6 % faster than with four.
+constexpr int kTravCtasPerSm = 2;
+constexpr int kAttCtasPerSm = 4;
 constexpr int kPyrK = 5;            // pyramid levels reduced per CTA pass
 
 // Scalars of the iteration that live on the device so that a captured graph
@@ -38,6 +45,10 @@ struct DevScalars {
     unsigned pyr_ticket; // last-block-done counter of the pyramid's first pass
     int stack_limit;     // entries of a traversal warp's stack in use (0: all
                          // kTravStack; lowered only by pxsne_test_stack_limit)
+    unsigned trav_next;  // next 64-point chunk of the traversal (0 between launches)
+    unsigned trav_done;  // traversal warps finished (the last one resets both)
+    unsigned att_next;   // the same two counters for the attraction's row chunks
+    unsigned att_done;
     u64 n_accept;        // accepted (point, cell) pairs of the last traversal
     u64 n_test;          // (point, cell) pairs tested by the last traversal
     u64 n_steps;         // warp-level (node, non-empty child) steps of the last traversal
@@ -196,9 +207,7 @@ struct pxsne_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t side = nullptr;          // stream of the attraction (overlaps the traversal)
-    // the attraction inside the traversal kernel (k_bh_traverse<..., ATT>,
-    // environment PXSNE_FORCES=fused); else two kernels on two streams
-    bool fused = false;
+    int sms = 0;                          // streaming multiprocessors of the device
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     std::string err;
@@ -318,7 +327,6 @@ constexpr int kRelabelEvery = 100;
 cudaError_t launch_relabel(pxsne_ctx *c, cudaStream_t st);
 // out[0..m] = exclusive scan of in[0..m) with out[m] = the total
 cudaError_t scan_u32_to_i64(const uint32_t *in, int64_t m, int64_t *out, cudaStream_t st);
-// traversal (with the attraction when c->fused) and Z
 cudaError_t launch_traverse_zsum(pxsne_ctx *c);
 cudaError_t launch_update(pxsne_ctx *c, cudaEvent_t *marks = nullptr);
 cudaError_t launch_kl(pxsne_ctx *c, double *out_dev);

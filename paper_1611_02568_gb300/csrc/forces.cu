@@ -8,6 +8,7 @@
 //   k_attract      attraction over the CSR of P, one warp per row
 //   k_zsum         Z = sum_i Z_i in FP64, fixed summation order
 //   k_kl           Eq. cost_func in FP64 accumulation
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -156,16 +157,11 @@ struct __align__(16) TravEntry {
     uint32_t node, m0, m1, pad;
 };
 
-// ATT: after its 64 points, the warp also computes the attraction of the 64
-// rows of the relabelled P with the same positions in the order (the same
-// per-row sums as k_attract).  The rows' position gathers then wait on memory
-// while other warps of the SM traverse, instead of in a kernel of their own.
-template <int CENTRE, int COUNT, bool OWN, bool ATT>
+template <int CENTRE, int COUNT, bool OWN>
 __global__ void __launch_bounds__(kTravWarps * 32, 4)
     k_bh_traverse(int n, int L, const uint2 *__restrict__ z, const uint32_t *__restrict__ perm,
                   const float4 *__restrict__ rec, const float *__restrict__ recn,
-                  DevScalars *sc, float2 *__restrict__ Frep, float *__restrict__ Zi,
-                  AttractArgs att) {
+                  DevScalars *sc, float2 *__restrict__ Frep, float *__restrict__ Zi) {
     // stack entry: (level << 28) | Morton index of a node, and for each half of
     // the warp's points the mask of the lanes whose point opens it
     __shared__ TravEntry s_stk[kTravWarps][kTravStack];
@@ -181,178 +177,187 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int base = (blockIdx.x * kTravWarps + w) * 64;
     const int F = 32 - L;
-    const int idx0 = base + lane, idx1 = base + 32 + lane;
-    const bool valid0 = idx0 < n, valid1 = idx1 < n;
-    const unsigned act0 = __ballot_sync(0xffffffffu, valid0);
-    const unsigned act1 = __ballot_sync(0xffffffffu, valid1);
-    // (a counting traversal keeps every warp to the CTA's final barrier)
-    if (!COUNT && act0 == 0u) return;
-    const uint32_t i0 = valid0 ? perm[idx0] : 0u, i1 = valid1 ? perm[idx1] : 0u;
-    const uint2 z0 = z[i0], z1 = z[i1];
-    const uint32_t mi0 = morton2(z0.x >> F, z0.y >> F), mi1 = morton2(z1.x >> F, z1.y >> F);
-    // z split at bit 16, both halves exact in float (see rec in common.cuh)
-    const float2 zhx = make_float2((float)(z0.x & 0xffff0000u), (float)(z1.x & 0xffff0000u));
-    const float2 zlx = make_float2((float)(z0.x & 0xffffu), (float)(z1.x & 0xffffu));
-    const float2 zhy = make_float2((float)(z0.y & 0xffff0000u), (float)(z1.y & 0xffff0000u));
-    const float2 zly = make_float2((float)(z0.y & 0xffffu), (float)(z1.y & 0xffffu));
     const float2 sf0 = bc2(sc->sf[0]), sf1 = bc2(sc->sf[1]);
-    float2 fx = bc2(0.f), fy = bc2(0.f), zs = bc2(0.f);
     uint32_t n_acc = 0u, n_tst = 0u, n_stp = 0u, n_nod = 0u;
-
     TravEntry *stk = s_stk[w];
-    // The root contains every point: start with its four children.
-    if (lane == 0) stk[0] = TravEntry{0u, act0, act1, 0u};  // (level 0 << 28) | morton 0
-    int sp = act0 != 0u ? 1 : 0;
-    __syncwarp();
-    bool overflow = false;
-    while (sp > 0) {
-        sp--;
-        TravEntry top = stk[sp];
+    // Each warp takes the next 64 points of the Morton order until none are
+    // left: a warp whose points are cheap moves on instead of idling until
+    // the slowest warp of its CTA is done.
+    for (;;) {
+        unsigned chunk = 0u;
+        if (lane == 0) chunk = atomicAdd(&sc->trav_next, 1u);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        if ((int64_t)chunk * 64 >= n) break;
+        const int base = (int)chunk * 64;
+        const int idx0 = base + lane, idx1 = base + 32 + lane;
+        const bool valid0 = idx0 < n, valid1 = idx1 < n;
+        const unsigned act0 = __ballot_sync(0xffffffffu, valid0);
+        const unsigned act1 = __ballot_sync(0xffffffffu, valid1);
+        const uint32_t i0 = valid0 ? perm[idx0] : 0u, i1 = valid1 ? perm[idx1] : 0u;
+        const uint2 z0 = z[i0], z1 = z[i1];
+        const uint32_t mi0 = morton2(z0.x >> F, z0.y >> F), mi1 = morton2(z1.x >> F, z1.y >> F);
+        // z split at bit 16, both halves exact in float (see rec in common.cuh)
+        const float2 zhx = make_float2((float)(z0.x & 0xffff0000u), (float)(z1.x & 0xffff0000u));
+        const float2 zlx = make_float2((float)(z0.x & 0xffffu), (float)(z1.x & 0xffffu));
+        const float2 zhy = make_float2((float)(z0.y & 0xffff0000u), (float)(z1.y & 0xffff0000u));
+        const float2 zly = make_float2((float)(z0.y & 0xffffu), (float)(z1.y & 0xffffu));
+        float2 fx = bc2(0.f), fy = bc2(0.f), zs = bc2(0.f);
+
+        // The root contains every point: start with its four children.
+        if (lane == 0) stk[0] = TravEntry{0u, act0, act1, 0u};  // (level 0 << 28) | morton 0
+        int sp = 1;
         __syncwarp();
-        // the entry is the same for every lane: taken from lane 0, so that
-        // the node, its level and addresses are known to be warp-uniform
-        top.node = __shfl_sync(0xffffffffu, top.node, 0);
-        top.m0 = __shfl_sync(0xffffffffu, top.m0, 0);
-        top.m1 = __shfl_sync(0xffffffffu, top.m1, 0);
-        const uint32_t node = top.node;
-        const int lc = (int)(node >> 28) + 1;  // level of the children
-        const uint32_t m0 = (node & 0x0fffffffu) << 2;
-        const int at = s_off[lc] + (int)m0;
-        const float4 nv = __ldg(reinterpret_cast<const float4 *>(recn + at));
-        // the four children's records are requested together with their
-        // counts (one latency per node instead of two)
-        float4 rr[4];
-        if (CENTRE == 0) {
+        bool overflow = false;
+        while (sp > 0) {
+            sp--;
+            TravEntry top = stk[sp];
+            __syncwarp();
+            // the entry is the same for every lane: taken from lane 0, so that
+            // the node, its level and addresses are known to be warp-uniform
+            top.node = __shfl_sync(0xffffffffu, top.node, 0);
+            top.m0 = __shfl_sync(0xffffffffu, top.m0, 0);
+            top.m1 = __shfl_sync(0xffffffffu, top.m1, 0);
+            const uint32_t node = top.node;
+            const int lc = (int)(node >> 28) + 1;  // level of the children
+            const uint32_t m0 = (node & 0x0fffffffu) << 2;
+            const int at = s_off[lc] + (int)m0;
+            const float4 nv = __ldg(reinterpret_cast<const float4 *>(recn + at));
+            // the four children's records are requested together with their
+            // counts (one latency per node instead of two)
+            float4 rr[4];
+            if (CENTRE == 0) {
 #pragma unroll
-            for (int ch = 0; ch < 4; ch++) rr[ch] = __ldg(rec + at + ch);
-        } else {
-            // geometric centres: the node's corner (exact floats) and width
-            // 2^(33 - lc); child ch's centre is a quarter or three quarters
-            // across on each axis
-            const uint32_t pm = node & 0x0fffffffu;
-            const float wp = __int_as_float((127 + 33 - lc) << 23);
-            const float px = (float)gather_bits16(pm) * wp, py = (float)gather_bits16(pm >> 1) * wp;
+                for (int ch = 0; ch < 4; ch++) rr[ch] = __ldg(rec + at + ch);
+            } else {
+                // geometric centres: the node's corner (exact floats) and width
+                // 2^(33 - lc); child ch's centre is a quarter or three quarters
+                // across on each axis
+                const uint32_t pm = node & 0x0fffffffu;
+                const float wp = __int_as_float((127 + 33 - lc) << 23);
+                const float px = (float)gather_bits16(pm) * wp, py = (float)gather_bits16(pm >> 1) * wp;
 #pragma unroll
-            for (int ch = 0; ch < 4; ch++)
-                rr[ch] = make_float4(fmaf(wp, (ch & 1) ? 0.75f : 0.25f, px), 0.f,
-                                     fmaf(wp, (ch & 2) ? 0.75f : 0.25f, py), 0.f);
-        }
-        const bool me0 = (top.m0 >> lane) & 1u, me1 = (top.m1 >> lane) & 1u;
-        const float Nc[4] = {nv.x, nv.y, nv.z, nv.w};
-        if (COUNT) {
-            n_nod++;
-            n_stp += (nv.x != 0.f) + (nv.y != 0.f) + (nv.z != 0.f) + (nv.w != 0.f);
-        }
-        if (lc == L) {
-            const uint32_t mine0 = mi0, mine1 = mi1;  // own pixels
+                for (int ch = 0; ch < 4; ch++)
+                    rr[ch] = make_float4(fmaf(wp, (ch & 1) ? 0.75f : 0.25f, px), 0.f,
+                                         fmaf(wp, (ch & 2) ? 0.75f : 0.25f, py), 0.f);
+            }
+            const bool me0 = (top.m0 >> lane) & 1u, me1 = (top.m1 >> lane) & 1u;
+            const float Nc[4] = {nv.x, nv.y, nv.z, nv.w};
+            if (COUNT) {
+                n_nod++;
+                n_stp += (nv.x != 0.f) + (nv.y != 0.f) + (nv.z != 0.f) + (nv.w != 0.f);
+            }
+            if (lc == L) {
+                const uint32_t mine0 = mi0, mine1 = mi1;  // own pixels
 #pragma unroll
-            for (int ch = 0; ch < 4; ch++) {
-                const float N = Nc[ch];
-                if (N == 0.f) continue;
-                const uint32_t mc = m0 + ch;
-                const float4 r = rr[ch];
-                float2 dx, dy;
-                cell_offset2<CENTRE>(r, zhx, zlx, zhy, zly, dx, dy);
-                const bool own0 = me0 && (mine0 == mc), own1 = me1 && (mine1 == mc);
-                float2 Nf = bc2(N);
-                if (__any_sync(0xffffffffu, own0 || own1)) {  // own pixel: take the point out
-                    if (own0) {
-                        Nf.x = N - 1.0f;
-                        if (CENTRE == 0 && N > 1.0f) {
-                            const float k = N / Nf.x;
-                            dx.x *= k;
-                            dy.x *= k;
+                for (int ch = 0; ch < 4; ch++) {
+                    const float N = Nc[ch];
+                    if (N == 0.f) continue;
+                    const uint32_t mc = m0 + ch;
+                    const float4 r = rr[ch];
+                    float2 dx, dy;
+                    cell_offset2<CENTRE>(r, zhx, zlx, zhy, zly, dx, dy);
+                    const bool own0 = me0 && (mine0 == mc), own1 = me1 && (mine1 == mc);
+                    float2 Nf = bc2(N);
+                    if (__any_sync(0xffffffffu, own0 || own1)) {  // own pixel: take the point out
+                        if (own0) {
+                            Nf.x = N - 1.0f;
+                            if (CENTRE == 0 && N > 1.0f) {
+                                const float k = N / Nf.x;
+                                dx.x *= k;
+                                dy.x *= k;
+                            }
+                        }
+                        if (own1) {
+                            Nf.y = N - 1.0f;
+                            if (CENTRE == 0 && N > 1.0f) {
+                                const float k = N / Nf.y;
+                                dx.y *= k;
+                                dy.y *= k;
+                            }
                         }
                     }
-                    if (own1) {
-                        Nf.y = N - 1.0f;
-                        if (CENTRE == 0 && N > 1.0f) {
-                            const float k = N / Nf.y;
-                            dx.y *= k;
-                            dy.y *= k;
-                        }
+                    dx = mul2(dx, sf0);
+                    dy = mul2(dy, sf1);
+                    const float2 d2 = fma2(dx, dx, mul2(dy, dy));
+                    const bool acc0 = me0 && (Nf.x > 0.f), acc1 = me1 && (Nf.y > 0.f);
+                    if (COUNT) {
+                        n_tst += (me0 ? 1u : 0u) + (me1 ? 1u : 0u);
+                        n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
+                        count_level(s_lv[lc], me0, me1, acc0, acc1, lane);
                     }
+                    const float2 w1 = add2(bc2(1.0f), d2);
+                    const float2 q = make_float2(rcp1(w1.x), rcp1(w1.y));
+                    const float2 Nq = mul2(make_float2(acc0 ? Nf.x : 0.0f, acc1 ? Nf.y : 0.0f), q);
+                    zs = add2(zs, Nq);
+                    const float2 Nq2 = mul2(Nq, q);
+                    fx = fma2(Nq2, dx, fx);
+                    fy = fma2(Nq2, dy, fy);
                 }
-                dx = mul2(dx, sf0);
-                dy = mul2(dy, sf1);
-                const float2 d2 = fma2(dx, dx, mul2(dy, dy));
-                const bool acc0 = me0 && (Nf.x > 0.f), acc1 = me1 && (Nf.y > 0.f);
-                if (COUNT) {
-                    n_tst += (me0 ? 1u : 0u) + (me1 ? 1u : 0u);
-                    n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
-                    count_level(s_lv[lc], me0, me1, acc0, acc1, lane);
+            } else {
+                const float Tl = s_T[lc];
+                // a point's own cell: opened by the criterion itself when theta < 1
+                // (the point and the centre of mass lie in the cell, so d <= r_c <
+                // r_c / theta); tested explicitly otherwise
+                const int sh = 2 * (L - lc);
+                const uint32_t mine0 = OWN ? mi0 >> sh : 0xffffffffu, mine1 = OWN ? mi1 >> sh : 0xffffffffu;
+                // room for the (at most four) entries this node may push
+                if (sp + 4 > stk_lim) {
+                    overflow = true;
+                    break;
                 }
-                const float2 w1 = add2(bc2(1.0f), d2);
-                const float2 q = make_float2(rcp1(w1.x), rcp1(w1.y));
-                const float2 Nq = mul2(make_float2(acc0 ? Nf.x : 0.0f, acc1 ? Nf.y : 0.0f), q);
-                zs = add2(zs, Nq);
-                const float2 Nq2 = mul2(Nq, q);
-                fx = fma2(Nq2, dx, fx);
-                fy = fma2(Nq2, dy, fy);
-            }
-        } else {
-            const float Tl = s_T[lc];
-            // a point's own cell: opened by the criterion itself when theta < 1
-            // (the point and the centre of mass lie in the cell, so d <= r_c <
-            // r_c / theta); tested explicitly otherwise
-            const int sh = 2 * (L - lc);
-            const uint32_t mine0 = OWN ? mi0 >> sh : 0xffffffffu, mine1 = OWN ? mi1 >> sh : 0xffffffffu;
-            // room for the (at most four) entries this node may push
-            if (sp + 4 > stk_lim) {
-                overflow = true;
-                break;
-            }
 #pragma unroll
-            for (int ch = 0; ch < 4; ch++) {
-                const float N = Nc[ch];
-                if (N == 0.f) continue;
-                const uint32_t mc = m0 + ch;
-                const float4 r = rr[ch];
-                float2 dx, dy;
-                cell_offset2<CENTRE>(r, zhx, zlx, zhy, zly, dx, dy);
-                dx = mul2(dx, sf0);
-                dy = mul2(dy, sf1);
-                const float2 d2 = fma2(dx, dx, mul2(dy, dy));
-                const bool far0 = (d2.x > Tl) && (!OWN || mine0 != mc);
-                const bool far1 = (d2.y > Tl) && (!OWN || mine1 != mc);
-                const bool acc0 = me0 && far0, acc1 = me1 && far1;
-                if (COUNT) {
-                    n_tst += (me0 ? 1u : 0u) + (me1 ? 1u : 0u);
-                    n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
-                    count_level(s_lv[lc], me0, me1, acc0, acc1, lane);
+                for (int ch = 0; ch < 4; ch++) {
+                    const float N = Nc[ch];
+                    if (N == 0.f) continue;
+                    const uint32_t mc = m0 + ch;
+                    const float4 r = rr[ch];
+                    float2 dx, dy;
+                    cell_offset2<CENTRE>(r, zhx, zlx, zhy, zly, dx, dy);
+                    dx = mul2(dx, sf0);
+                    dy = mul2(dy, sf1);
+                    const float2 d2 = fma2(dx, dx, mul2(dy, dy));
+                    const bool far0 = (d2.x > Tl) && (!OWN || mine0 != mc);
+                    const bool far1 = (d2.y > Tl) && (!OWN || mine1 != mc);
+                    const bool acc0 = me0 && far0, acc1 = me1 && far1;
+                    if (COUNT) {
+                        n_tst += (me0 ? 1u : 0u) + (me1 ? 1u : 0u);
+                        n_acc += (acc0 ? 1u : 0u) + (acc1 ? 1u : 0u);
+                        count_level(s_lv[lc], me0, me1, acc0, acc1, lane);
+                    }
+                    const float2 w1 = add2(bc2(1.0f), d2);
+                    const float2 q = make_float2(rcp1(w1.x), rcp1(w1.y));
+                    const float2 Nq = mul2(make_float2(acc0 ? N : 0.0f, acc1 ? N : 0.0f), q);
+                    zs = add2(zs, Nq);
+                    const float2 Nq2 = mul2(Nq, q);
+                    fx = fma2(Nq2, dx, fx);
+                    fy = fma2(Nq2, dy, fy);
+                    const unsigned ob0 = __ballot_sync(0xffffffffu, me0 && !far0);
+                    const unsigned ob1 = __ballot_sync(0xffffffffu, me1 && !far1);
+                    // written in any case above the top; kept if some point opens it
+                    if (lane == 0) stk[sp] = TravEntry{((uint32_t)lc << 28) | mc, ob0, ob1, 0u};
+                    sp += (ob0 | ob1) != 0u;
                 }
-                const float2 w1 = add2(bc2(1.0f), d2);
-                const float2 q = make_float2(rcp1(w1.x), rcp1(w1.y));
-                const float2 Nq = mul2(make_float2(acc0 ? N : 0.0f, acc1 ? N : 0.0f), q);
-                zs = add2(zs, Nq);
-                const float2 Nq2 = mul2(Nq, q);
-                fx = fma2(Nq2, dx, fx);
-                fy = fma2(Nq2, dy, fy);
-                const unsigned ob0 = __ballot_sync(0xffffffffu, me0 && !far0);
-                const unsigned ob1 = __ballot_sync(0xffffffffu, me1 && !far1);
-                // written in any case above the top; kept if some point opens it
-                if (lane == 0) stk[sp] = TravEntry{((uint32_t)lc << 28) | mc, ob0, ob1, 0u};
-                sp += (ob0 | ob1) != 0u;
             }
+            __syncwarp();
+            if (overflow) break;
         }
+        if (valid0) {
+            Frep[i0] = make_float2(fx.x, fy.x);
+            Zi[i0] = zs.x;
+        }
+        if (valid1) {
+            Frep[i1] = make_float2(fx.y, fy.y);
+            Zi[i1] = zs.y;
+        }
+        if (overflow && lane == 0) atomicOr(&sc->err, (unsigned)PXSNE_DEVERR_STACK);
         __syncwarp();
-        if (overflow) break;
     }
-    if (valid0) {
-        Frep[i0] = make_float2(fx.x, fy.x);
-        Zi[i0] = zs.x;
-    }
-    if (valid1) {
-        Frep[i1] = make_float2(fx.y, fy.y);
-        Zi[i1] = zs.y;
-    }
-    if (overflow && lane == 0) atomicOr(&sc->err, (unsigned)PXSNE_DEVERR_STACK);
-    if (ATT) {
-        const float a0 = sc->sf[0], a1 = sc->sf[1];
-        const int rend = min(n, base + 64);
-        for (int row = base; row < rend; row++) attract_row(row, lane, att, a0, a1);
+    // every warp has taken its last chunk: the last one out resets the counter
+    // for the next launch
+    if (lane == 0 && atomicAdd(&sc->trav_done, 1u) == gridDim.x * kTravWarps - 1u) {
+        sc->trav_next = 0u;
+        sc->trav_done = 0u;
     }
     if (COUNT) {
         __syncthreads();
@@ -374,13 +379,26 @@ __global__ void __launch_bounds__(kTravWarps * 32, 4)
     }
 }
 
-// The attraction as its own kernel: one warp per row.
+// The attraction as its own kernel: one warp per row, the warps of a small
+// persistent grid taking the rows kAttRows at a time until none are left, so
+// that it runs beside the traversal on the SMs' spare registers.
+constexpr int kAttRows = 4;
 __global__ void __launch_bounds__(256)
-    k_attract(int n, AttractArgs a, const DevScalars *__restrict__ sc) {
+    k_attract(int n, AttractArgs a, DevScalars *sc) {
     const int lane = threadIdx.x & 31;
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (row >= n) return;
-    attract_row(row, lane, a, sc->sf[0], sc->sf[1]);
+    const float sf0 = sc->sf[0], sf1 = sc->sf[1];
+    for (;;) {
+        unsigned chunk = 0u;
+        if (lane == 0) chunk = atomicAdd(&sc->att_next, 1u);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        if ((int64_t)chunk * kAttRows >= n) break;
+        const int r0 = (int)chunk * kAttRows, r1 = min(n, r0 + kAttRows);
+        for (int row = r0; row < r1; row++) attract_row(row, lane, a, sf0, sf1);
+    }
+    if (lane == 0 && atomicAdd(&sc->att_done, 1u) == gridDim.x * (blockDim.x >> 5) - 1u) {
+        sc->att_next = 0u;
+        sc->att_done = 0u;
+    }
 }
 
 // Relabelling: new label r is the point perm[r] (Morton order of the last
@@ -470,39 +488,36 @@ static AttractArgs attract_args(const pxsne_ctx *c) {
     return AttractArgs{c->rp2, c->col2, c->val2, c->zp, c->aperm, c->Fattr};
 }
 
-template <int CENTRE, int COUNT, bool OWN, bool ATT>
+// One wave of kTravCtasPerSm CTAs per SM (at most the four the launch bounds
+// allow), fewer when the points fill fewer.
+template <int CENTRE, int COUNT, bool OWN>
 static void traverse_as(pxsne_ctx *c, cudaStream_t st) {
     const int n = (int)c->n;
     const int per_block = kTravWarps * 64;
-    k_bh_traverse<CENTRE, COUNT, OWN, ATT>
-        <<<(n + per_block - 1) / per_block, kTravWarps * 32, 0, st>>>(
-            n, c->L, c->z, c->perm, c->rec, c->recn, c->sc, c->Frep, c->Zi, attract_args(c));
+    const int blocks = std::min((n + per_block - 1) / per_block, kTravCtasPerSm * std::max(c->sms, 1));
+    k_bh_traverse<CENTRE, COUNT, OWN><<<blocks, kTravWarps * 32, 0, st>>>(
+        n, c->L, c->z, c->perm, c->rec, c->recn, c->sc, c->Frep, c->Zi);
 }
 
-template <int CENTRE>
-static void traverse_centre(pxsne_ctx *c, cudaStream_t st, bool count, bool own, bool fused) {
-    if (fused)  // (a fused traversal never counts)
-        own ? traverse_as<CENTRE, 0, true, true>(c, st) : traverse_as<CENTRE, 0, false, true>(c, st);
-    else if (count)
-        own ? traverse_as<CENTRE, 1, true, false>(c, st) : traverse_as<CENTRE, 1, false, false>(c, st);
-    else
-        own ? traverse_as<CENTRE, 0, true, false>(c, st) : traverse_as<CENTRE, 0, false, false>(c, st);
-}
-
-// The traversal, and with fused = true the attraction inside the same kernel.
-static cudaError_t traverse(pxsne_ctx *c, cudaStream_t st, bool count, bool fused = false) {
+static cudaError_t traverse(pxsne_ctx *c, cudaStream_t st, bool count) {
     // the own-cell test is redundant below theta = 1 (with a margin for the
     // rounding of d^2)
     const bool own = c->p.theta >= 0.999f;
-    if (c->p.centre_mode == 0) traverse_centre<0>(c, st, count && !fused, own, fused);
-    else traverse_centre<1>(c, st, count && !fused, own, fused);
+    if (c->p.centre_mode == 0) {
+        if (count) own ? traverse_as<0, 1, true>(c, st) : traverse_as<0, 1, false>(c, st);
+        else own ? traverse_as<0, 0, true>(c, st) : traverse_as<0, 0, false>(c, st);
+    } else {
+        if (count) own ? traverse_as<1, 1, true>(c, st) : traverse_as<1, 1, false>(c, st);
+        else own ? traverse_as<1, 0, true>(c, st) : traverse_as<1, 0, false>(c, st);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_attract(pxsne_ctx *c, cudaStream_t st) {
     const int n = (int)c->n;
-    const int att_blocks = (int)((int64_t(n) * 32 + 255) / 256);
-    k_attract<<<att_blocks, 256, 0, st>>>(n, attract_args(c), c->sc);
+    const int need = (int)((int64_t(n) + 8 * kAttRows - 1) / (8 * kAttRows));
+    const int blocks = std::min(need, kAttCtasPerSm * std::max(c->sms, 1));
+    k_attract<<<blocks, 256, 0, st>>>(n, attract_args(c), c->sc);
     return cudaGetLastError();
 }
 
@@ -547,25 +562,15 @@ cudaError_t launch_accumulate_counters(pxsne_ctx *c) {
 }
 
 cudaError_t launch_traverse_zsum(pxsne_ctx *c) {
-    cudaError_t e = traverse(c, c->stream, false, c->fused);
+    cudaError_t e = traverse(c, c->stream, false);
     if (e) return e;
     return zsum(c, c->stream);
 }
 
 // Sequential forces (traversal, attraction, Z) with optional timing marks.
-// Timed (marks) and fused, the one kernel is the traversal group and the
-// attraction group is empty.
 cudaError_t launch_forces(pxsne_ctx *c, cudaEvent_t *marks) {
     cudaStream_t st = c->stream;
     cudaError_t e;
-    if (marks && c->fused) {
-        if ((e = cudaEventRecord(marks[KG_TRAVERSE], st))) return e;
-        if ((e = traverse(c, st, false, true))) return e;
-        if ((e = cudaEventRecord(marks[KG_ATTRACT], st))) return e;
-        if ((e = cudaEventRecord(marks[KG_ZSUM], st))) return e;
-        if ((e = zsum(c, st))) return e;
-        return cudaEventRecord(marks[KG_COUNT], st);
-    }
     if (marks && (e = cudaEventRecord(marks[KG_TRAVERSE], st))) return e;
     // the initial state's traversal keeps the work counters (the level
     // counters restart with it); a timed one is the kernel of the iteration
