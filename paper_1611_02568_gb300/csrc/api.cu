@@ -158,6 +158,10 @@ int ensure_state(pxsne_ctx *c) {
     CK(c, dalloc(c, &c->leaf_cnt, leaves));
     CK(c, dalloc(c, &c->leaf_sx, leaves));
     CK(c, dalloc(c, &c->leaf_sy, leaves));
+    // the leaf histogram starts from zeros; the pyramid clears what it read
+    CK(c, cudaMemsetAsync(c->leaf_cnt, 0, (size_t)leaves * sizeof(uint32_t), c->stream));
+    CK(c, cudaMemsetAsync(c->leaf_sx, 0, (size_t)leaves * sizeof(u64), c->stream));
+    CK(c, cudaMemsetAsync(c->leaf_sy, 0, (size_t)leaves * sizeof(u64), c->stream));
     CK(c, dalloc(c, &c->rec, cells));
     CK(c, dalloc(c, &c->recn, cells));
     // records of empty cells are never written by the pyramid (nor read by
@@ -869,9 +873,13 @@ int pxsne_get_tree(pxsne_ctx *c, int32_t level, uint32_t *cnt, uint64_t *sx, uin
         CK(c, cudaMemcpyAsync(cnt, d, cells * 4, cudaMemcpyDeviceToHost, st));
         CK(c, cudaFreeAsync(d, st));
     }
-    if (level == c->L) {
-        if (sx) CK(c, cudaMemcpyAsync(sx, c->leaf_sx, cells * 8, cudaMemcpyDeviceToHost, st));
-        if (sy) CK(c, cudaMemcpyAsync(sy, c->leaf_sy, cells * 8, cudaMemcpyDeviceToHost, st));
+    if (level == c->L && (sx || sy)) {
+        u64 *d = nullptr;
+        CK(c, cudaMallocAsync(&d, cells * 16, st));
+        CK(c, launch_leaf_hist(c, nullptr, d, d + cells));
+        if (sx) CK(c, cudaMemcpyAsync(sx, d, cells * 8, cudaMemcpyDeviceToHost, st));
+        if (sy) CK(c, cudaMemcpyAsync(sy, d + cells, cells * 8, cudaMemcpyDeviceToHost, st));
+        CK(c, cudaFreeAsync(d, st));
     }
     if (morton) {
         uint32_t *d = nullptr;

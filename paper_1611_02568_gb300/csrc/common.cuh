@@ -339,6 +339,8 @@ cudaError_t launch_perplexity(pxsne_ctx *c, const float *d2, int64_t n, int32_t 
 cudaError_t build_symmetric_csr(pxsne_ctx *c, const int32_t *idx, const float *pcond,
                                 int64_t n, int32_t k, std::string &err);
 cudaError_t launch_level_counts(pxsne_ctx *c, int level, uint32_t *cnt);
+// counts and exact coordinate sums of the leaves of the current state (any may be NULL)
+cudaError_t launch_leaf_hist(pxsne_ctx *c, uint32_t *cnt, u64 *sx, u64 *sy);
 cudaError_t launch_morton_keys(pxsne_ctx *c, uint32_t *keys);
 // One CTA waiting on an mbarrier that nothing arrives at (bounded; sets
 // PXSNE_DEVERR_TIMEOUT when the polls run out).

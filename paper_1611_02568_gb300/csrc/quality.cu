@@ -21,7 +21,7 @@ __device__ __forceinline__ double d2_fp64(uint2 a, uint2 b, double s0, double s1
 
 __global__ void __launch_bounds__(128)
     k_nbr_precision(int n, int L, int K1, int k, const uint2 *__restrict__ z,
-                    const uint32_t *__restrict__ perm, const uint32_t *__restrict__ leaf_cnt,
+                    const uint32_t *__restrict__ perm, const float *__restrict__ leaf_n,
                     const uint32_t *__restrict__ leaf_start,
                     const uint32_t *__restrict__ blk_off, const int32_t *__restrict__ knn_hd,
                     int kh, const DevScalars *__restrict__ sc, int32_t *__restrict__ hits,
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(128)
             }
             if (x < 0 || y < 0 || x >= R || y >= R) continue;
             const uint32_t m = morton2((uint32_t)x, (uint32_t)y);
-            const uint32_t c = leaf_cnt[m];
+            const uint32_t c = (uint32_t)leaf_n[m];  // the pixel's count (exact float)
             if (c == 0u) continue;
             const uint32_t st = blk_off[m >> (2 * K1)] + leaf_start[m];
             for (uint32_t u = 0; u < c; u++) {
@@ -108,7 +108,8 @@ cudaError_t launch_nbr_precision(pxsne_ctx *c, int k, const int32_t *knn_hd, int
     const int n = (int)c->n;
     const int K1 = c->L < kPyrK ? c->L : kPyrK;
     k_nbr_precision<<<(n + 127) / 128, 128, 0, c->stream>>>(n, c->L, K1, k, c->z, c->perm,
-                                                           c->leaf_cnt, c->leaf_start, c->blk_off,
+                                                           c->recn + rec_offset(c->L),
+                                                           c->leaf_start, c->blk_off,
                                                            knn_hd, kh, c->sc, hits, total);
     return cudaGetLastError();
 }

@@ -151,6 +151,22 @@ __device__ uint32_t block_excl_scan(uint32_t v, int nt, uint32_t *s_warp) {
     return before + x - v;
 }
 
+// The leaf histogram is consumed by the first pass of the pyramid, which sets
+// the groups of four leaves it read back to zero where any was occupied, so
+// the next iteration's histogram starts from zero without a memset of every
+// leaf (sx == NULL: counts only).
+__device__ __forceinline__ void clear_leaves(uint32_t cell0, uint4 c4, uint32_t *cnt, u64 *sx,
+                                             u64 *sy) {
+    if ((c4.x | c4.y | c4.z | c4.w) == 0u) return;
+    reinterpret_cast<uint4 *>(cnt)[cell0 >> 2] = make_uint4(0u, 0u, 0u, 0u);
+    if (sx == nullptr) return;
+    const ulonglong2 z2{0ull, 0ull};
+    reinterpret_cast<ulonglong2 *>(sx)[cell0 >> 1] = z2;
+    reinterpret_cast<ulonglong2 *>(sx)[(cell0 >> 1) + 1] = z2;
+    reinterpret_cast<ulonglong2 *>(sy)[cell0 >> 1] = z2;
+    reinterpret_cast<ulonglong2 *>(sy)[(cell0 >> 1) + 1] = z2;
+}
+
 // One bottom-up pass: reads the sums of level h for 4^K consecutive cells per
 // CTA (an aligned 2^K x 2^K block), writes the records of levels h .. h-K+1
 // (and of level h-K when `top`), and the sums of level h-K (one cell per CTA).
@@ -163,7 +179,7 @@ __global__ void __launch_bounds__(1 << (2 * (K - 1)))
                float4 *__restrict__ rec, float *__restrict__ recn,
                uint32_t *__restrict__ out_cnt,
                u64 *__restrict__ out_sx, u64 *__restrict__ out_sy,
-               uint32_t *__restrict__ leaf_start, DevScalars *sc, int bump_t) {
+               uint32_t *__restrict__ leaf_start, DevScalars *sc, int bump_t, int clear) {
     constexpr int NT = 1 << (2 * (K - 1));
     __shared__ uint32_t s_c[NT];
     __shared__ u64 s_x[NT], s_y[NT];
@@ -187,6 +203,8 @@ __global__ void __launch_bounds__(1 << (2 * (K - 1)))
     }
     reinterpret_cast<float4 *>(recn + rec_offset(h))[cell0 >> 2] =
         make_float4((float)c4.x, (float)c4.y, (float)c4.z, (float)c4.w);
+    if (clear) clear_leaves(cell0, c4, const_cast<uint32_t *>(in_cnt), const_cast<u64 *>(in_sx),
+                            const_cast<u64 *>(in_sy));
     uint32_t N = c4.x + c4.y + c4.z + c4.w;
     u64 X = x01.x + x01.y + x23.x + x23.y;
     u64 Y = y01.x + y01.y + y23.x + y23.y;
@@ -332,8 +350,8 @@ __device__ void pyr_top(int h0, uint32_t *c0, u64 *x0, u64 *y0, uint32_t *c1, u6
 }
 
 __global__ void __launch_bounds__(256)
-    k_pyr_bottom(int h, const uint32_t *__restrict__ in_cnt, const u64 *__restrict__ in_sx,
-                 const u64 *__restrict__ in_sy, float4 *__restrict__ rec, float *__restrict__ recn,
+    k_pyr_bottom(int h, uint32_t *__restrict__ in_cnt, u64 *__restrict__ in_sx,
+                 u64 *__restrict__ in_sy, float4 *__restrict__ rec, float *__restrict__ recn,
                  uint32_t *out_cnt, u64 *out_sx, u64 *out_sy, uint32_t *scr_cnt, u64 *scr_sx,
                  u64 *scr_sy, uint32_t *__restrict__ leaf_start, uint32_t *blk_off,
                  DevScalars *sc, int bump_t) {
@@ -362,6 +380,7 @@ __global__ void __launch_bounds__(256)
     }
     reinterpret_cast<float4 *>(recn + rec_offset(h))[cell0 >> 2] =
         make_float4((float)c4.x, (float)c4.y, (float)c4.z, (float)c4.w);
+    clear_leaves(cell0, c4, in_cnt, in_sx, in_sy);
     uint32_t N = c4.x + c4.y + c4.z + c4.w;
     u64 X = x01.x + x01.y + x23.x + x23.y;
     u64 Y = y01.x + y01.y + y23.x + y23.y;
@@ -484,14 +503,14 @@ static cudaError_t pyr_pass(int K, int64_t blocks, cudaStream_t st, int h, int t
                             const uint32_t *ic, const u64 *ix, const u64 *iy, float4 *rec,
                             float *recn,
                             uint32_t *oc, u64 *ox, u64 *oy, uint32_t *ls, DevScalars *sc,
-                            int bump) {
+                            int bump, int clear) {
     const dim3 g((unsigned)blocks);
     switch (K) {
-    case 1: k_pyr_pass<1><<<g, 1, 0, st>>>(h, top, ic, ix, iy, rec, recn, oc, ox, oy, ls, sc, bump); break;
-    case 2: k_pyr_pass<2><<<g, 4, 0, st>>>(h, top, ic, ix, iy, rec, recn, oc, ox, oy, ls, sc, bump); break;
-    case 3: k_pyr_pass<3><<<g, 16, 0, st>>>(h, top, ic, ix, iy, rec, recn, oc, ox, oy, ls, sc, bump); break;
-    case 4: k_pyr_pass<4><<<g, 64, 0, st>>>(h, top, ic, ix, iy, rec, recn, oc, ox, oy, ls, sc, bump); break;
-    default: k_pyr_pass<5><<<g, 256, 0, st>>>(h, top, ic, ix, iy, rec, recn, oc, ox, oy, ls, sc, bump); break;
+    case 1: k_pyr_pass<1><<<g, 1, 0, st>>>(h, top, ic, ix, iy, rec, recn, oc, ox, oy, ls, sc, bump, clear); break;
+    case 2: k_pyr_pass<2><<<g, 4, 0, st>>>(h, top, ic, ix, iy, rec, recn, oc, ox, oy, ls, sc, bump, clear); break;
+    case 3: k_pyr_pass<3><<<g, 16, 0, st>>>(h, top, ic, ix, iy, rec, recn, oc, ox, oy, ls, sc, bump, clear); break;
+    case 4: k_pyr_pass<4><<<g, 64, 0, st>>>(h, top, ic, ix, iy, rec, recn, oc, ox, oy, ls, sc, bump, clear); break;
+    default: k_pyr_pass<5><<<g, 256, 0, st>>>(h, top, ic, ix, iy, rec, recn, oc, ox, oy, ls, sc, bump, clear); break;
     }
     return cudaGetLastError();
 }
@@ -502,16 +521,12 @@ static cudaError_t pyr_pass(int K, int64_t blocks, cudaStream_t st, int h, int t
 cudaError_t launch_snap(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
     cudaStream_t st = c->stream;
     const int L = c->L;
-    const int64_t leaves = int64_t(1) << (2 * L);
     cudaError_t e;
     if (marks && (e = cudaEventRecord(marks[KG_SNAP], st))) return e;
-    // geometric centres (Sec. 4.1's approximation) need the counts only
+    // geometric centres (Sec. 4.1's approximation) need the counts only; the
+    // leaves are zero here (set at allocation, cleared by the pyramid's first
+    // pass after each histogram)
     const bool sums = c->p.centre_mode == 0;
-    if ((e = cudaMemsetAsync(c->leaf_cnt, 0, leaves * sizeof(uint32_t), st))) return e;
-    if (sums) {
-        if ((e = cudaMemsetAsync(c->leaf_sx, 0, leaves * sizeof(u64), st))) return e;
-        if ((e = cudaMemsetAsync(c->leaf_sy, 0, leaves * sizeof(u64), st))) return e;
-    }
     const int n = (int)c->n;
     k_snap_hist<<<(n + 255) / 256, 256, 0, st>>>(n, L, rescale ? 1 : 0, c->p.theta,
                                                  screen_extent(c->p.screen_x, L),
@@ -535,7 +550,8 @@ cudaError_t launch_pyramid(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
     if (L >= kPyrK && L - kPyrK <= 7) {
         // one pass: shuffle-reduced bottom levels, the top by the last CTA
         k_pyr_bottom<<<(unsigned)(leaves >> 10), 256, 0, st>>>(
-            L, c->leaf_cnt, c->leaf_sx, c->leaf_sy, sums ? c->rec : nullptr, c->recn, c->lvl_cnt[0],
+            L, c->leaf_cnt, sums ? c->leaf_sx : nullptr, sums ? c->leaf_sy : nullptr,
+            sums ? c->rec : nullptr, c->recn, c->lvl_cnt[0],
             c->lvl_sx[0], c->lvl_sy[0], c->lvl_cnt[1], c->lvl_sx[1], c->lvl_sy[1],
             c->leaf_start, c->blk_off, c->sc, rescale ? 1 : 0);
         if ((e = cudaGetLastError())) return e;
@@ -549,7 +565,7 @@ cudaError_t launch_pyramid(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
             if ((e = pyr_pass(K1, blocks, st, h, top, c->leaf_cnt, sums ? c->leaf_sx : nullptr,
                               c->leaf_sy,
                               c->rec, c->recn, c->lvl_cnt[0], c->lvl_sx[0], c->lvl_sy[0],
-                              c->leaf_start, c->sc, (rescale && top) ? 1 : 0)))
+                              c->leaf_start, c->sc, (rescale && top) ? 1 : 0, 1)))
                 return e;
             h -= K1;
         }
@@ -564,7 +580,7 @@ cudaError_t launch_pyramid(pxsne_ctx *c, bool rescale, cudaEvent_t *marks) {
                               sums ? c->lvl_sx[cur] : nullptr, c->lvl_sy[cur], c->rec, c->recn,
                               c->lvl_cnt[cur ^ 1],
                               c->lvl_sx[cur ^ 1], c->lvl_sy[cur ^ 1], nullptr, c->sc,
-                              (rescale && top) ? 1 : 0)))
+                              (rescale && top) ? 1 : 0, 0)))
                 return e;
             cur ^= 1;
             h -= K;
@@ -733,6 +749,30 @@ cudaError_t launch_level_counts(pxsne_ctx *c, int level, uint32_t *cnt) {
     const int64_t cells = int64_t(1) << (2 * level);
     k_level_counts<<<(unsigned)((cells + 255) / 256), 256, 0, c->stream>>>(
         cells, c->recn + rec_offset(level), cnt);
+    return cudaGetLastError();
+}
+
+// The leaf histogram of the current state, for inspection (the iteration's
+// own is cleared by the pyramid once read): counts and exact coordinate sums.
+__global__ void k_leaf_hist(int n, int L, const uint2 *__restrict__ z, uint32_t *cnt, u64 *sx,
+                            u64 *sy) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint2 v = z[i];
+    const uint32_t m = morton2(v.x >> (32 - L), v.y >> (32 - L));
+    if (cnt) atomicAdd(&cnt[m], 1u);
+    if (sx) atomicAdd(&sx[m], (u64)v.x);
+    if (sy) atomicAdd(&sy[m], (u64)v.y);
+}
+
+cudaError_t launch_leaf_hist(pxsne_ctx *c, uint32_t *cnt, u64 *sx, u64 *sy) {
+    const int n = (int)c->n;
+    const size_t leaves = size_t(1) << (2 * c->L);
+    cudaError_t e;
+    if (cnt && (e = cudaMemsetAsync(cnt, 0, leaves * 4, c->stream))) return e;
+    if (sx && (e = cudaMemsetAsync(sx, 0, leaves * 8, c->stream))) return e;
+    if (sy && (e = cudaMemsetAsync(sy, 0, leaves * 8, c->stream))) return e;
+    k_leaf_hist<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->L, c->z, cnt, sx, sy);
     return cudaGetLastError();
 }
 
