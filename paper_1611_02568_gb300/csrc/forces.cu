@@ -76,6 +76,21 @@ __device__ __forceinline__ void count_level(u64 *lv, bool me0, bool me1, bool ac
     }
 }
 
+// A coordinate's two 16-bit halves as floats, each offset by a power of two
+// that leaves the half's bits as the mantissa: hi_bits(v) = 2^39 + (v >> 16)
+// 2^16 (ulp 2^16 at 2^39) and lo_bits(v) = 2^23 + (v & 0xffff) (ulp 1 at
+// 2^23), both exact and built by bit operations instead of integer-to-float
+// conversions.  The difference of two such values cancels the offset
+// exactly, so (hi_bits(a) - hi_bits(b)) + (lo_bits(a) - lo_bits(b)) is the
+// exact difference of the halves with one final rounding, as when the halves
+// are converted and subtracted directly.
+__device__ __forceinline__ float hi_bits(uint32_t v) {
+    return __uint_as_float(0x53000000u | (v >> 16));
+}
+__device__ __forceinline__ float lo_bits(uint32_t v) {
+    return __uint_as_float(0x4B000000u | (v & 0xffffu));
+}
+
 // Eq. grad, first term: Fattr_i = sum_j p_ij w_ij (y_i - y_j), one warp per
 // row (row lengths vary with the in-degree of the kNN graph; a warp per row
 // keeps long rows from stalling short ones).  It runs over the relabelled copy
@@ -103,8 +118,9 @@ __device__ __forceinline__ void attract_row(int row, int lane, const AttractArgs
     const float *__restrict__ val = a.val;
     const uint2 *__restrict__ z = a.z;
     const uint2 zi = z[row];
-    const float xh = (float)(zi.x & 0xffff0000u), xl = (float)(zi.x & 0xffffu);
-    const float yh = (float)(zi.y & 0xffff0000u), yl = (float)(zi.y & 0xffffu);
+    // the row's halves offset by the same constants as hi_bits / lo_bits
+    const float xh = hi_bits(zi.x), xl = lo_bits(zi.x);
+    const float yh = hi_bits(zi.y), yl = lo_bits(zi.y);
     const int64_t e0 = rp[row], e1 = rp[row + 1];
     float fx = 0.f, fy = 0.f;
     // software pipeline: the next batch of P is requested while the current
@@ -135,10 +151,8 @@ __device__ __forceinline__ void attract_row(int row, int lane, const AttractArgs
         }
 #pragma unroll
         for (int u = 0; u < U; u++) {
-            const float dx =
-                ((xh - (float)(zj[u].x & 0xffff0000u)) + (xl - (float)(zj[u].x & 0xffffu))) * sf0;
-            const float dy =
-                ((yh - (float)(zj[u].y & 0xffff0000u)) + (yl - (float)(zj[u].y & 0xffffu))) * sf1;
+            const float dx = ((xh - hi_bits(zj[u].x)) + (xl - lo_bits(zj[u].x))) * sf0;
+            const float dy = ((yh - hi_bits(zj[u].y)) + (yl - lo_bits(zj[u].y))) * sf1;
             const float w = __fdividef(1.0f, 1.0f + fmaf(dx, dx, dy * dy));
             const float pw = p[u] * w;
             fx = fmaf(pw, dx, fx);
