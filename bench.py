@@ -389,9 +389,10 @@ def geometric_centre_study(px, X, Y0, params_kw, steps, com, stream, torch):
     return out
 
 
-def approx_knn_study(px, ctx, X, params, n, probes=(256, 1024), sample=20000):
+def approx_knn_study(px, ctx, X, params, n, probes=(256, 1024, (256, 2)), sample=20000):
     """P construction with the approximate neighbour search (knn_probe = W
-    candidate tiles per query tile) beside the exact one of ctx: P time, search
+    candidate tiles per query tile, optionally followed by R rounds of
+    neighbour exploring, (W, R)) beside the exact one of ctx: P time, search
     time and the recall of the exact lists on a row sample."""
     import dataclasses
     rows = np.random.default_rng(5).choice(n, min(sample, n), replace=False)
@@ -399,7 +400,8 @@ def approx_knn_study(px, ctx, X, params, n, probes=(256, 1024), sample=20000):
     exact = idx_e[rows]
     out = {"exact": {"knn_ms": ctx.knn_time_ms()}}
     for W in probes:
-        p = dataclasses.replace(params, knn_probe=W)
+        W, R = W if isinstance(W, tuple) else (W, 0)
+        p = dataclasses.replace(params, knn_probe=W, knn_explore=R)
         with px.Context(p) as c:
             import torch
             torch.cuda.synchronize()
@@ -409,8 +411,9 @@ def approx_knn_study(px, ctx, X, params, n, probes=(256, 1024), sample=20000):
             idx, _, _ = c.get_knn()
             got = idx[rows]
             hits = sum(len(np.intersect1d(a, b, assume_unique=True)) for a, b in zip(got, exact))
-            out[str(W)] = {"p_construction_s": tp, "knn_ms": c.knn_time_ms(),
-                           "recall_vs_exact": hits / exact.size}
+            out[str(W) if R == 0 else f"{W}+explore{R}"] = {
+                "p_construction_s": tp, "knn_ms": c.knn_time_ms(),
+                "recall_vs_exact": hits / exact.size}
     out["sample_rows"] = int(len(rows))
     return out
 

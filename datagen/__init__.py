@@ -140,6 +140,21 @@ def gmm64out(seed: int = 0, n: int = 10_000_000):
     return gmm(seed, n, 64, 256, 1.2, outlier_frac=0.01)
 
 
+def lowdim(seed: int = 0, n: int = 1_000_000, d_latent: int = 4, D: int = 64,
+           noise: float = 1e-3):
+    """Points near a d_latent-dimensional linear manifold of R^D: latent
+    coordinates uniform in the unit cube, mapped by a fixed Gaussian D x
+    d_latent matrix, plus isotropic noise of std ``noise``.  The stand-in for
+    data of low intrinsic dimension, where a neighbour's neighbours are likely
+    neighbours (the premise of Sec. 4.3's neighbour exploring); the Gaussian
+    mixtures above are full-rank and have none of that structure."""
+    wrng = np.random.default_rng([12345, d_latent, D])
+    A = wrng.standard_normal((d_latent, D))
+    rng = np.random.default_rng([seed, 5, d_latent, D])
+    Z = rng.random((n, d_latent))
+    return (Z @ A + noise * rng.standard_normal((n, D))).astype(np.float32)
+
+
 def init_y0(seed: int, n: int, sigma: float = 1e-4, dim: int = 2) -> np.ndarray:
     """The random initial embedding Y0 ~ N(0, sigma^2 I), shape (n, dim),
     float32 (the random draw that t-SNE starts from; passed to both sides)."""

@@ -101,6 +101,9 @@ typedef struct pxsne_params {
     int32_t knn_probe;       /* 0: exact neighbour search; W in [1, 1792]: approximate
                                 (see pxsne_affinities) */
     int32_t dim;             /* embedding dimension: 2 (0 means 2) or 3 (see below) */
+    int32_t knn_explore;     /* rounds of neighbour exploring after an approximate
+                                search, 0 .. 8 (needs knn_probe > 0; see
+                                pxsne_affinities) */
 } pxsne_params;
 
 void pxsne_default_params(pxsne_params *p);
@@ -132,7 +135,13 @@ const char *pxsne_last_error(const pxsne_ctx *ctx);
  * nearest to their tile's (their own tile first), with exact FP32 distances
  * and the exact search's tile bound; the neighbour lists are then the
  * k nearest within those tiles (tensor-core search only; the FP32 check path
- * stays exact).  The lists may differ between runs.
+ * stays exact).  The lists may differ between runs.  knn_explore = R > 0 then
+ * refines them by R rounds of Sec. 4.3's neighbour exploring (LargeVis'
+ * "a neighbour of my neighbour is likely my neighbour"): in each round every
+ * row tests, with the same exact FP32 distance, every entry of the lists of
+ * its first min(k, 16) neighbours, and keeps the k nearest of its list and
+ * those (each round reads the previous round's lists only, so a round's
+ * result does not depend on the order of the rows).
  * X: host or device, row-major n x D float32, 2 <= n <= 2^24, 1 <= D <= 256
  * (the shared-memory tiles of the search bound D further for large k; an
  * unsupported size returns an error).  perplexity <= 0 uses the
@@ -176,7 +185,7 @@ int pxsne_step(pxsne_ctx *ctx, int32_t iters);
  *
  * File layout (byte order of the writing host, little-endian on every
  * supported one): a 144-byte header {char magic[8] = "PXSNECK\0"; uint32
- * version = 1; uint32 header bytes = 144; pxsne_params (68 bytes); uint32 0;
+ * version = 1; uint32 header bytes = 144; pxsne_params (72 bytes);
  * int64 n, nnz; int32 t, 0; double s[2]; uint64 payload bytes; uint64
  * checksum}, then row_ptr[n+1] int64, col[nnz] int32, val[nnz] float32,
  * z[2n] uint32, u[2n] float32, gains[2n] float32.  The checksum is FNV-1a

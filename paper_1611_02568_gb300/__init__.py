@@ -46,7 +46,7 @@ class _CParams(C.Structure):
                 ("momentum_switch", C.c_int32), ("min_gain", C.c_float), ("k", C.c_int32),
                 ("perplexity", C.c_float), ("init_sigma", C.c_float),
                 ("centre_mode", C.c_int32), ("screen_x", C.c_int32), ("screen_y", C.c_int32),
-                ("knn_probe", C.c_int32), ("dim", C.c_int32)]
+                ("knn_probe", C.c_int32), ("dim", C.c_int32), ("knn_explore", C.c_int32)]
 
 
 @dataclass
@@ -69,6 +69,7 @@ class Params:
     screen_y: int = 0      # pixels of its height (0: 2^log2_r)
     knn_probe: int = 0     # 0: exact neighbour search; W: approximate, W tiles per tile
     dim: int = 2           # embedding dimension: 2, or 3 (voxel grid and octree)
+    knn_explore: int = 0   # rounds of neighbour exploring after an approximate search
 
     def c(self):
         return _CParams(*[getattr(self, f.name) for f in fields(self)])

@@ -1174,6 +1174,107 @@ void launch_wait_probe(pxsne_ctx *c, int polls) {
 }
 
 // Timing events around the search kernel (created on first use).
+// ---------------------------------------------------------------- neighbour exploring
+// Sec. 4.3's refinement of approximate neighbour lists (LargeVis' neighbour
+// exploring): a row's new list is the k nearest among its old list and the
+// old lists of its first ke neighbours.  One warp per row, the rows taken in
+// the search's locality order so that neighbouring warps gather neighbouring
+// rows of Xs; the list lives in shared memory sorted by (d2, index) (the
+// search's order and tie rule), and each candidate that beats the current
+// k-th entry and is not listed yet is inserted by a warp-wide shift.  The
+// distance is the search's exact FP32 one (thread_exact_d2 on the same
+// rows), so an entry found by both has the same d2.  Lists are read from
+// (idx_in, d2_in) and written to (idx_out, d2_out): the result does not
+// depend on the order in which rows are processed.
+constexpr int kExploreNbrs = 16;
+constexpr int kExploreWarps = 8;
+__global__ void __launch_bounds__(kExploreWarps * 32)
+    k_knn_explore(int64_t n, int k, int ke, int D, int vec4, const float *__restrict__ Xs,
+                  const uint32_t *__restrict__ order, const uint32_t *__restrict__ rank,
+                  const int32_t *__restrict__ idx_in, const float *__restrict__ d2_in,
+                  int32_t *__restrict__ idx_out, float *__restrict__ d2_out) {
+    __shared__ float s_d[kExploreWarps][256];
+    __shared__ int32_t s_j[kExploreWarps][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t p = (int64_t)blockIdx.x * kExploreWarps + warp;
+    if (p >= n) return;
+    const int64_t i = order[p];
+    float *ld = s_d[warp];
+    int32_t *lj = s_j[warp];
+    for (int e = lane; e < k; e += 32) {
+        ld[e] = d2_in[i * k + e];
+        lj[e] = idx_in[i * k + e];
+    }
+    __syncwarp();
+    float tau = ld[k - 1];
+    int32_t jl = lj[k - 1];
+    for (int e = 0; e < ke; e++) {
+        const int64_t j = __ldg(idx_in + i * k + e);
+        for (int f0 = 0; f0 < k; f0 += 32) {
+            const int f = f0 + lane;
+            int32_t l = -1;
+            float d = INFINITY;
+            if (f < k) {
+                l = __ldg(idx_in + j * k + f);
+                if (l != (int32_t)i) d = thread_exact_d2(Xs, D, p, (int64_t)__ldg(rank + l), vec4 != 0);
+            }
+            const bool pass = l >= 0 && l != (int32_t)i && (d < tau || (d == tau && l < jl));
+            unsigned m = __ballot_sync(0xffffffffu, pass);
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1u;
+                const float dc = __shfl_sync(0xffffffffu, d, src);
+                const int32_t lc = __shfl_sync(0xffffffffu, l, src);
+                if (!(dc < tau || (dc == tau && lc < jl))) continue;  // the list moved on
+                bool dup = false;
+                int before = 0;
+                for (int q = lane; q < k; q += 32) {
+                    dup |= lj[q] == lc;
+                    before += (ld[q] < dc || (ld[q] == dc && lj[q] < lc)) ? 1 : 0;
+                }
+                if (__any_sync(0xffffffffu, dup)) continue;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+                // entries before .. k - 2 move down one place, the last drops
+                float vd[8];
+                int32_t vj[8];
+#pragma unroll
+                for (int t = 0; t < 8; t++) {
+                    const int q = lane + 32 * t;
+                    if (q < k && q > before) {
+                        vd[t] = ld[q - 1];
+                        vj[t] = lj[q - 1];
+                    }
+                }
+                __syncwarp();
+#pragma unroll
+                for (int t = 0; t < 8; t++) {
+                    const int q = lane + 32 * t;
+                    if (q < k && q > before) {
+                        ld[q] = vd[t];
+                        lj[q] = vj[t];
+                    } else if (q == before) {
+                        ld[q] = dc;
+                        lj[q] = lc;
+                    }
+                }
+                __syncwarp();
+                tau = ld[k - 1];
+                jl = lj[k - 1];
+            }
+        }
+    }
+    for (int e = lane; e < k; e += 32) {
+        d2_out[i * k + e] = ld[e];
+        idx_out[i * k + e] = lj[e];
+    }
+}
+
+__global__ void k_rank_of(int64_t n, const uint32_t *__restrict__ order, uint32_t *__restrict__ rank) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < n) rank[order[p]] = (uint32_t)p;
+}
+
 static cudaError_t knn_mark(pxsne_ctx *c, int which, cudaStream_t st) {
     cudaError_t e;
     if (!c->knn_ev[which] && (e = cudaEventCreate(&c->knn_ev[which]))) return e;
@@ -1422,6 +1523,43 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         if ((e = knn_mark(c, 0, st))) return e;
         k_knn_tc<<<(unsigned)T, kTcThreads, smem_tc, st>>>(ka);
         if ((e = cudaGetLastError())) return e;
+        if (probe > 0 && c->p.knn_explore > 0) {
+            // rounds of neighbour exploring, ping-ponging with a second pair
+            // of lists; the last round writes into idx / d2
+            uint32_t *rank = nullptr;
+            int32_t *idx2 = nullptr;
+            float *d22 = nullptr;
+            if ((e = cudaMallocAsync(&rank, (size_t)n * sizeof(uint32_t), st))) return e;
+            if ((e = cudaMallocAsync(&idx2, (size_t)n * k * sizeof(int32_t), st))) return e;
+            if ((e = cudaMallocAsync(&d22, (size_t)n * k * sizeof(float), st))) return e;
+            k_rank_of<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, order, rank);
+            const int R = c->p.knn_explore;
+            const int ke = std::min(k, kExploreNbrs);
+            const int v4 = ((D & 3) == 0) && ((reinterpret_cast<uintptr_t>(Xo) & 15) == 0);
+            const unsigned eb = (unsigned)((n + kExploreWarps - 1) / kExploreWarps);
+            // with R odd the first round reads a copy of the search's lists
+            if ((R & 1) &&
+                (e = cudaMemcpyAsync(idx2, idx, (size_t)n * k * sizeof(int32_t),
+                                     cudaMemcpyDeviceToDevice, st)))
+                return e;
+            if ((R & 1) && (e = cudaMemcpyAsync(d22, d2, (size_t)n * k * sizeof(float),
+                                                cudaMemcpyDeviceToDevice, st)))
+                return e;
+            for (int r = 0; r < R; r++) {
+                // round r writes the pair that the last round must end in
+                const bool into_main = ((R - 1 - r) & 1) == 0;
+                const int32_t *ii = into_main ? idx2 : idx;
+                const float *di = into_main ? d22 : d2;
+                int32_t *io = into_main ? idx : idx2;
+                float *dout = into_main ? d2 : d22;
+                k_knn_explore<<<eb, kExploreWarps * 32, 0, st>>>(n, k, ke, D, v4, Xo, order, rank,
+                                                                ii, di, io, dout);
+                if ((e = cudaGetLastError())) return e;
+            }
+            cudaFreeAsync(rank, st);
+            cudaFreeAsync(idx2, st);
+            cudaFreeAsync(d22, st);
+        }
         if ((e = knn_mark(c, 1, st))) return e;
         if (cand) cudaFreeAsync(cand, st);
         cudaFreeAsync(img, st);

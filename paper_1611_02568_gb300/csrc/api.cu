@@ -102,6 +102,10 @@ int check_params(const pxsne_params *p) {
                     p->screen_y, side, side);
     if (p->knn_probe < 0 || p->knn_probe > 1792)
         return fail(nullptr, PXSNE_E_ARG, "knn_probe = %d outside [0, 1792]", p->knn_probe);
+    if (p->knn_explore < 0 || p->knn_explore > 8)
+        return fail(nullptr, PXSNE_E_ARG, "knn_explore = %d outside [0, 8]", p->knn_explore);
+    if (p->knn_explore > 0 && p->knn_probe == 0)
+        return fail(nullptr, PXSNE_E_ARG, "knn_explore refines an approximate search (knn_probe > 0)");
     if (p->dim != 0 && p->dim != 2 && p->dim != 3)
         return fail(nullptr, PXSNE_E_ARG, "dim = %d: 2 or 3", p->dim);
     if (p->dim == 3 && (p->log2_r > kMaxL3 || p->screen_x || p->screen_y || p->centre_mode))
@@ -312,6 +316,7 @@ void pxsne_default_params(pxsne_params *p) {
     p->screen_y = 0;
     p->knn_probe = 0;
     p->dim = 2;
+    p->knn_explore = 0;
 }
 
 int pxsne_create(pxsne_ctx **out, const pxsne_params *p, void *stream) {
@@ -1018,14 +1023,13 @@ struct CheckpointHeader {
     uint32_t version;       // 1
     uint32_t header_bytes;  // sizeof(CheckpointHeader)
     pxsne_params params;    // the context's parameters and schedule
-    uint32_t pad0;
     int64_t n, nnz;
     int32_t t, pad1;
     double s[2];
     uint64_t payload_bytes;
     uint64_t checksum;
 };
-static_assert(sizeof(pxsne_params) == 68, "pxsne_params layout");
+static_assert(sizeof(pxsne_params) == 72, "pxsne_params layout");
 static_assert(sizeof(CheckpointHeader) == 144, "checkpoint header layout");
 constexpr char kMagic[8] = {'P', 'X', 'S', 'N', 'E', 'C', 'K', 0};
 

@@ -26,7 +26,7 @@ def fnv_words(payload: bytes) -> int:
 def make_file(n=4, version=1, magic=b"PXSNECK\0", corrupt=None, trailing=b"", short=0):
     p = px.Params(log2_r=4, k=1, perplexity=1.0)
     cp = bytes(p.c())
-    assert len(cp) == 68
+    assert len(cp) == 72
     rp = np.array([0, 1, 2, 3, 4], np.int64)[: n + 1]
     col = np.array([1, 0, 3, 2], np.int32)
     val = np.full(4, 0.25, np.float32)
@@ -39,7 +39,7 @@ def make_file(n=4, version=1, magic=b"PXSNECK\0", corrupt=None, trailing=b"", sh
         payload = bytearray(payload)
         payload[corrupt] ^= 1
         payload = bytes(payload)
-    head = magic + struct.pack("<II", version, 144) + cp + struct.pack("<I", 0)
+    head = magic + struct.pack("<II", version, 144) + cp
     head += struct.pack("<qqii", n, 4, 7, 0) + struct.pack("<dd", 2.0 ** -30, 2.0 ** -31)
     head += struct.pack("<QQ", len(rp) * 8 + 8 * 4 + 24 * n, ck)
     assert len(head) == 144

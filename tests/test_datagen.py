@@ -79,3 +79,14 @@ def test_gmm_recipes():
 def test_workload_table(name):
     gen, n0, L, T = datagen.WORKLOADS[name]
     assert callable(gen) and n0 >= 2000 and 9 <= L <= 12 and T in (500, 1000)
+
+
+def test_lowdim_recipe():
+    # rank d_latent up to the noise: the centred data's singular values drop
+    # by orders of magnitude after the d_latent-th
+    X = datagen.lowdim(seed=1, n=3000, d_latent=4, D=32)
+    assert X.shape == (3000, 32) and X.dtype == np.float32
+    assert np.array_equal(X, datagen.lowdim(seed=1, n=3000, d_latent=4, D=32))
+    assert not np.array_equal(X, datagen.lowdim(seed=2, n=3000, d_latent=4, D=32))
+    sv = np.linalg.svd(X - X.mean(0), compute_uv=False)
+    assert sv[3] > 100 * sv[4]

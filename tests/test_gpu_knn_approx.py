@@ -7,7 +7,14 @@ sampled rows (FP64 brute force; neighbours within 2e-5 of the k-th distance
 may go either way) grows with W and is at least 0.9 at W = 1024.  (On these
 full-rank Gaussian mixtures a point's nearest neighbours spread over its whole
 cluster, so no small set of tiles holds them: the exact search, with the same
-random-projection tiles and the tile bound, is the default.)"""
+random-projection tiles and the tile bound, is the default.)
+
+Neighbour exploring (knn_explore = R rounds after the approximate search,
+Sec. 4.3) is checked where its premise holds, on points near a 4-dimensional
+manifold of R^64 (datagen.lowdim): the recall rises with every round and
+reaches 0.99 after two rounds at W = 64; on the bench workload's mixture one
+round still raises it.  The lists stay valid (distinct other rows, exact
+distances, sorted)."""
 import numpy as np
 import pytest
 
@@ -56,3 +63,36 @@ def test_approximate_search_recall_grows_with_the_probe():
         # P from the approximate lists is still a distribution
         assert abs(val.astype(np.float64).sum() - 1.0) < 1e-5
     assert rec[1024] > rec[256] and rec[1024] >= 0.9, rec
+
+
+def test_neighbour_exploring_raises_recall():
+    import paper_1611_02568_gb300 as px
+    from paper_1611_02568_gb300 import build
+    build.build()
+    n, L = 1_000_000, 11
+    X = datagen.lowdim(seed=0, n=n, d_latent=4, D=64)
+    rows = np.unique(np.concatenate([np.random.default_rng(12).choice(n, 60, replace=False),
+                                     [0, n - 1]]))
+    idx_o, d2_o = oracle.knn(X, K, rows=rows)
+    rec = {}
+    for R in (0, 1, 2):
+        with px.Context(px.Params(log2_r=L, k=K, knn_probe=64, knn_explore=R)) as ctx:
+            ctx.affinities(X)
+            idx, d2, _ = ctx.get_knn()
+            rec[R] = recall(X, idx, d2, rows, idx_o, d2_o)
+            assert ctx.sync() == 0
+        print(f"low-dimensional data, probe 64, {R} exploring rounds: recall {rec[R]:.4f}")
+    assert rec[0] < rec[1] < rec[2] and rec[2] >= 0.99, rec
+    # the bench workload's full-rank mixture: one round still helps
+    n = 200_000
+    X, _ = datagen.gmm128(seed=0, n=n)
+    rows = np.unique(np.random.default_rng(13).choice(n, 40, replace=False))
+    idx_o, d2_o = oracle.knn(X, K, rows=rows)
+    rec = {}
+    for R in (0, 1):
+        with px.Context(px.Params(log2_r=10, k=K, knn_probe=64, knn_explore=R)) as ctx:
+            ctx.affinities(X)
+            idx, d2, _ = ctx.get_knn()
+            rec[R] = recall(X, idx, d2, rows, idx_o, d2_o)
+    print(f"gmm128 at n = 200k, probe 64: recall {rec[0]:.4f} -> {rec[1]:.4f} after one round")
+    assert rec[1] > rec[0], rec
