@@ -98,8 +98,8 @@ typedef struct pxsne_params {
     int32_t centre_mode;     /* 0: cell centre of mass; 1: geometric cell centre (Sec. 4.1) */
     int32_t screen_x;        /* screen width r_1 in pixels, 1 <= r_1 <= 2^L; 0: 2^L */
     int32_t screen_y;        /* screen height r_2 in pixels, 1 <= r_2 <= 2^L; 0: 2^L */
-    int32_t knn_probe;       /* 0: exact neighbour search; W in [1, 1792]: approximate
-                                (see pxsne_affinities) */
+    int32_t knn_probe;       /* 0: exact neighbour search; W in [ceil(k / 128) + 1,
+                                1792]: approximate (see pxsne_affinities) */
     int32_t dim;             /* embedding dimension: 2 (0 means 2) or 3 (see below) */
     int32_t knn_explore;     /* rounds of neighbour exploring after an approximate
                                 search, 0 .. 8 (needs knn_probe > 0; see
@@ -132,10 +132,11 @@ const char *pxsne_last_error(const pxsne_ctx *ctx);
  * locality order is split further by random-projection hyperplanes (each
  * bisecting two of the segment's rows) into tiles of 128 nearby rows, and the
  * rows of a tile are searched only against the W tiles whose centroids are
- * nearest to their tile's (their own tile first), with exact FP32 distances
- * and the exact search's tile bound; the neighbour lists are then the
- * k nearest within those tiles (tensor-core search only; the FP32 check path
- * stays exact).  The lists may differ between runs.  knn_explore = R > 0 then
+ * nearest to their tile's (their own tile first), with exact FP32 distances;
+ * the neighbour lists are then the k nearest within those tiles, the same on
+ * every run (tensor-core search only; the FP32 check path stays exact).  W
+ * must be at least ceil(k / 128) + 1, so that W tiles hold k other rows even
+ * when the own tile is the last, partial one.  knn_explore = R > 0 then
  * refines them by R rounds of Sec. 4.3's neighbour exploring (LargeVis'
  * "a neighbour of my neighbour is likely my neighbour"): in each round every
  * row tests, with the same exact FP32 distance, every entry of the lists of

@@ -473,10 +473,41 @@ __global__ void k_cell_count(int64_t n, const uint32_t *__restrict__ cell, uint3
 
 // order[r]: the row at sorted position r (rows of one cell contiguous, cells
 // in chain order; the order inside a cell is immaterial to the result)
-__global__ void k_cell_scatter(int64_t n, const uint32_t *__restrict__ cell, uint32_t *cursor,
-                               uint32_t *__restrict__ order) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) order[atomicAdd(&cursor[cell[i]], 1u)] = (uint32_t)i;
+// Stable counting sort of the rows by pivot cell: the rows of a cell keep
+// their index order, so the locality order, its random-projection splits and
+// the tiles are the same on every run.  Blocks of kCsRows rows; a row's place
+// is the offset of (its cell, its block) in the cell-major scan of the
+// per-block counts, plus the rows of its cell in earlier warps of the block,
+// plus those in earlier lanes of its warp.  off == NULL: write the block's
+// counts hist[c * nb + b]; else scatter the rows into order.
+constexpr int kCsRows = 512;
+__global__ void __launch_bounds__(kCsRows)
+    k_cell_rank(int64_t n, int nc, const uint32_t *__restrict__ cell, uint32_t *__restrict__ hist,
+                int64_t nb, const int64_t *__restrict__ off, uint32_t *__restrict__ order) {
+    __shared__ uint32_t s_cnt[kCsRows / 32][kCells + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t b = blockIdx.x;
+    const int64_t i = b * kCsRows + threadIdx.x;
+    for (int q = threadIdx.x; q < (kCsRows / 32) * nc; q += blockDim.x) s_cnt[q / nc][q % nc] = 0u;
+    __syncthreads();
+    const bool valid = i < n;
+    const uint32_t c = valid ? cell[i] : 0xffffffffu;
+    const unsigned same = __match_any_sync(0xffffffffu, c);
+    const int rw = __popc(same & ((1u << lane) - 1u));
+    if (valid && rw == 0) s_cnt[warp][c] = (uint32_t)__popc(same);
+    __syncthreads();
+    if (off == nullptr) {
+        for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+            uint32_t t = 0u;
+            for (int w = 0; w < kCsRows / 32; w++) t += s_cnt[w][q];
+            hist[(int64_t)q * nb + b] = t;
+        }
+        return;
+    }
+    if (!valid) return;
+    uint32_t before = 0u;
+    for (int w = 0; w < warp; w++) before += s_cnt[w][c];
+    order[off[(int64_t)c * nb + b] + before + (uint32_t)rw] = (uint32_t)i;
 }
 
 // Xs[r] = X[order[r]], ns[r] = nrm[order[r]]
@@ -806,7 +837,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             }
             const float taum = fmaxf(fmaxf(s_taumax[0], s_taumax[1]), fmaxf(s_taumax[2], s_taumax[3]));
             const float lbd = sqrtf(dd) * 0.9999f - rq - (in ? a.rad[tl] : 0.f);
-            const bool skip = in && il > 0 && lbd > 0.f && lbd * lbd > taum * 1.0001f;
+            // (the approximate search takes its W tiles whole: with the bound,
+            // which tiles pass would depend on how far the filter warps have
+            // got, and the lists would differ between runs)
+            const bool skip =
+                in && il > 0 && !a.cand && lbd > 0.f && lbd * lbd > taum * 1.0001f;
             n_skip += (u64)__popc(__ballot_sync(0xffffffffu, skip));
             // kept tiles of this block, and the end mark after the last block
             unsigned keep = __ballot_sync(0xffffffffu, in && !skip);
@@ -1199,6 +1234,7 @@ __global__ void __launch_bounds__(kExploreWarps * 32)
     const int64_t p = (int64_t)blockIdx.x * kExploreWarps + warp;
     if (p >= n) return;
     const int64_t i = order[p];
+    // (an entry outside [0, n), which a full list never holds, is not followed)
     float *ld = s_d[warp];
     int32_t *lj = s_j[warp];
     for (int e = lane; e < k; e += 32) {
@@ -1210,13 +1246,16 @@ __global__ void __launch_bounds__(kExploreWarps * 32)
     int32_t jl = lj[k - 1];
     for (int e = 0; e < ke; e++) {
         const int64_t j = __ldg(idx_in + i * k + e);
+        if (j < 0 || j >= n) continue;
         for (int f0 = 0; f0 < k; f0 += 32) {
             const int f = f0 + lane;
             int32_t l = -1;
             float d = INFINITY;
             if (f < k) {
                 l = __ldg(idx_in + j * k + f);
-                if (l != (int32_t)i) d = thread_exact_d2(Xs, D, p, (int64_t)__ldg(rank + l), vec4 != 0);
+                if (l < 0 || (int64_t)l >= n) l = -1;
+                else if (l != (int32_t)i)
+                    d = thread_exact_d2(Xs, D, p, (int64_t)__ldg(rank + l), vec4 != 0);
             }
             const bool pass = l >= 0 && l != (int32_t)i && (d < tau || (d == tau && l < jl));
             unsigned m = __ballot_sync(0xffffffffu, pass);
@@ -1418,7 +1457,21 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         if ((e = cudaMemcpyAsync(ccnt, hc.data(), (size_t)(m + 1) * sizeof(uint32_t),
                                  cudaMemcpyHostToDevice, st)))
             return e;
-        k_cell_scatter<<<ablocks, 256, 0, st>>>(n, cell, ccnt, order);
+        {
+            const int nc = m + 1;  // the pivots' cells and the far rows' one
+            const int64_t nb = (n + kCsRows - 1) / kCsRows;
+            uint32_t *hist = nullptr;
+            int64_t *off = nullptr;
+            if ((e = cudaMallocAsync(&hist, (size_t)(nc * nb) * sizeof(uint32_t), st))) return e;
+            if ((e = cudaMallocAsync(&off, (size_t)(nc * nb + 1) * sizeof(int64_t), st))) return e;
+            k_cell_rank<<<(unsigned)nb, kCsRows, 0, st>>>(n, nc, cell, hist, nb, nullptr, nullptr);
+            if ((e = cudaGetLastError())) return e;
+            if ((e = scan_u32_to_i64(hist, (int64_t)nc * nb, off, st))) return e;
+            k_cell_rank<<<(unsigned)nb, kCsRows, 0, st>>>(n, nc, cell, hist, nb, off, order);
+            if ((e = cudaGetLastError())) return e;
+            cudaFreeAsync(hist, st);
+            cudaFreeAsync(off, st);
+        }
         const int probe = c->p.knn_probe;
         {
             // split every cell by random projections until segments hold at

@@ -102,6 +102,10 @@ int check_params(const pxsne_params *p) {
                     p->screen_y, side, side);
     if (p->knn_probe < 0 || p->knn_probe > 1792)
         return fail(nullptr, PXSNE_E_ARG, "knn_probe = %d outside [0, 1792]", p->knn_probe);
+    if (p->knn_probe > 0 && p->knn_probe < (p->k + 127) / 128 + 1)
+        return fail(nullptr, PXSNE_E_ARG,
+                    "knn_probe = %d: at least ceil(k / 128) + 1 = %d tiles hold k other rows",
+                    p->knn_probe, (p->k + 127) / 128 + 1);
     if (p->knn_explore < 0 || p->knn_explore > 8)
         return fail(nullptr, PXSNE_E_ARG, "knn_explore = %d outside [0, 8]", p->knn_explore);
     if (p->knn_explore > 0 && p->knn_probe == 0)

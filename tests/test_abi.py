@@ -50,7 +50,7 @@ def test_create_rejects_bad_params(lib):
                 dict(screen_x=3000, log2_r=11), dict(knn_probe=5000), dict(dim=4),
                 dict(dim=1), dict(dim=3, log2_r=10), dict(dim=3, screen_x=100),
                 dict(dim=3, centre_mode=1), dict(knn_explore=2), dict(knn_probe=64, knn_explore=9),
-                dict(knn_probe=64, knn_explore=-1)):
+                dict(knn_probe=64, knn_explore=-1), dict(knn_probe=1), dict(knn_probe=2, k=200)):
         p = px.Params(**bad).c()
         h = ctypes.c_void_p()
         rc = L.pxsne_create(ctypes.byref(h), ctypes.byref(p), None)

@@ -52,7 +52,8 @@ def test_approximate_search_recall_grows_with_the_probe():
                                      [0, n - 1]]))
     idx_o, d2_o = oracle.knn(X, K, rows=rows)
     rec = {}
-    for W in (256, 1024):
+    lists = {}
+    for W in (256, 1024, 256):
         with px.Context(px.Params(log2_r=L, k=K, knn_probe=W)) as ctx:
             ctx.affinities(X)
             ms = ctx.knn_time_ms()
@@ -62,6 +63,10 @@ def test_approximate_search_recall_grows_with_the_probe():
         print(f"probe {W}: search {ms:.1f} ms, recall {rec[W]:.4f}")
         # P from the approximate lists is still a distribution
         assert abs(val.astype(np.float64).sum() - 1.0) < 1e-5
+        # the same lists on every run
+        if W in lists:
+            assert np.array_equal(idx, lists[W][0]) and np.array_equal(d2, lists[W][1])
+        lists[W] = (idx, d2)
     assert rec[1024] > rec[256] and rec[1024] >= 0.9, rec
 
 
@@ -96,3 +101,27 @@ def test_neighbour_exploring_raises_recall():
             rec[R] = recall(X, idx, d2, rows, idx_o, d2_o)
     print(f"gmm128 at n = 200k, probe 64: recall {rec[0]:.4f} -> {rec[1]:.4f} after one round")
     assert rec[1] > rec[0], rec
+
+
+def test_probe_covering_every_tile_is_the_exact_search():
+    # n = 3000 rows make 24 tiles: W = 64 probes all of them, so the lists
+    # are the exact ones; the smallest W allowed for k = 90 (two tiles) still
+    # fills every list with distinct valid rows
+    import paper_1611_02568_gb300 as px
+    from paper_1611_02568_gb300 import build
+    build.build()
+    X, _ = datagen.gauss10(5, n=3000)
+    with px.Context(px.Params(log2_r=9, k=K)) as ctx:
+        ctx.affinities(X)
+        idx_e, d2_e, _ = ctx.get_knn()
+    with px.Context(px.Params(log2_r=9, k=K, knn_probe=64, knn_explore=1)) as ctx:
+        ctx.affinities(X)
+        idx, d2, _ = ctx.get_knn()
+    assert np.array_equal(idx, idx_e) and np.array_equal(d2, d2_e)
+    with px.Context(px.Params(log2_r=9, k=K, knn_probe=2, knn_explore=2)) as ctx:
+        ctx.affinities(X)
+        idx, d2, _ = ctx.get_knn()
+        assert ctx.sync() == 0
+    assert idx.min() >= 0 and idx.max() < 3000 and np.isfinite(d2).all()
+    for r in range(0, 3000, 97):
+        assert len(set(idx[r].tolist())) == K and r not in set(idx[r].tolist())
