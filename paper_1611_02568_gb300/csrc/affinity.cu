@@ -1564,6 +1564,8 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         ka.rad = rad;
         ka.cand = nullptr;
         ka.W = 0;
+        // (the search's time includes its candidate lists)
+        if ((e = knn_mark(c, 0, st))) return e;
         int32_t *cand = nullptr;
         if (probe > 0) {
             const int W = (int)std::min<int64_t>(probe, T);
@@ -1573,7 +1575,6 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
             ka.cand = cand;
             ka.W = W;
         }
-        if ((e = knn_mark(c, 0, st))) return e;
         k_knn_tc<<<(unsigned)T, kTcThreads, smem_tc, st>>>(ka);
         if ((e = cudaGetLastError())) return e;
         if (probe > 0 && c->p.knn_explore > 0) {
