@@ -389,6 +389,28 @@ def geometric_centre_study(px, X, Y0, params_kw, steps, com, stream, torch):
     return out
 
 
+def variant_study(px, P3, Y0, params, steps, stream, torch):
+    """The bench workload's P (row_ptr, col, val from the timed context) under
+    other parameters: the same start, the same schedule length; iterations/s
+    by CUDA events and the final KL."""
+    with px.Context(params, stream=stream.cuda_stream) as c:
+        c.set_P(*P3)
+        c.init(Y0)
+        c.step(3)
+        c.sync()
+        c.init(Y0)
+        c.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.step(steps)
+        e1.record(stream)
+        e1.synchronize()
+        assert c.sync() == 0
+        return {"it_per_s": steps / (e0.elapsed_time(e1) / 1e3), "kl": c.kl(),
+                "iterations": steps}
+
+
 def approx_knn_study(px, ctx, X, params, n, probes=(256, 1024, (256, 2)), sample=20000):
     """P construction with the approximate neighbour search (knn_probe = W
     candidate tiles per query tile, optionally followed by R rounds of
@@ -786,6 +808,22 @@ def run_gpu(args):
                 px, X, Y0, dict(theta=W["theta"], k=W["k"], perplexity=W["perplexity"]),
                 [W["log2_r"] - 2, W["log2_r"] - 1, W["log2_r"], W["log2_r"] + 1,
                  W["log2_r"] + 2], 300, stream, torch) if n <= 2_000_000 else None}
+        if n <= 2_000_000:
+            import datagen
+            P3 = ctx.get_P()
+            kw = dict(theta=W["theta"], k=W["k"], perplexity=W["perplexity"])
+            L = W["log2_r"]
+            # an r_1 x r_2 screen of 4:3 on the same 2^L root (Sec. 4.2's r_d)
+            rx, ry = 1 << L, 3 << (L - 2)
+            studies["nonsquare_screen"] = dict(
+                screen=f"{rx}x{ry}", square_it_per_s=value, square_kl=kl_after,
+                **variant_study(px, P3, Y0, px.Params(log2_r=L, screen_x=rx, screen_y=ry, **kw),
+                                args.steps, stream, torch))
+            # the 3-D embedding on a 256^3 voxel grid (octree), its own 3-D start
+            studies["dim3"] = dict(
+                grid="256^3", kl_2d=kl_after,
+                **variant_study(px, P3, datagen.init_y0(0, n, dim=3),
+                                px.Params(log2_r=8, dim=3, **kw), args.steps, stream, torch))
 
     warm = None
     if rank == 0 and not args.no_warmstart:
