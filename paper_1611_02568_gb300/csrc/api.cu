@@ -1213,14 +1213,24 @@ int pxsne_get_tree3(pxsne_ctx *c, int32_t level, uint32_t *cnt, uint64_t *sx, ui
     if (level < 0 || level > c->L) return fail(c, PXSNE_E_ARG, "level out of range");
     cudaStream_t st = c->stream;
     const size_t cells = size_t(1) << (3 * level);
-    const int64_t all = cells3(c->L), at = level_offset3(level);
-    if (cnt) CK(c, cudaMemcpyAsync(cnt, c->cnt3 + at, cells * 4, cudaMemcpyDeviceToHost, st));
-    if (level == c->L) {
+    const int64_t at = level_offset3(level);
+    if (level < c->L) {
+        if (cnt) CK(c, cudaMemcpyAsync(cnt, c->cnt3 + at, cells * 4, cudaMemcpyDeviceToHost, st));
+    } else {
+        // the leaves: rebuilt from z (the iteration clears its own once read)
+        uint32_t *dc = nullptr;
+        u64 *ds = nullptr;
+        CK(c, cudaMallocAsync(&dc, cells * 4, st));
+        CK(c, cudaMallocAsync(&ds, cells * 24, st));
+        CK(c, launch_leaf_hist3(c, dc, ds));
+        if (cnt) CK(c, cudaMemcpyAsync(cnt, dc, cells * 4, cudaMemcpyDeviceToHost, st));
         uint64_t *out[3] = {sx, sy, sz};
         for (int d = 0; d < 3; d++)
             if (out[d])
-                CK(c, cudaMemcpyAsync(out[d], c->sum3 + d * all + at, cells * 8,
-                                      cudaMemcpyDeviceToHost, st));
+                CK(c, cudaMemcpyAsync(out[d], ds + d * cells, cells * 8, cudaMemcpyDeviceToHost,
+                                      st));
+        CK(c, cudaFreeAsync(dc, st));
+        CK(c, cudaFreeAsync(ds, st));
     }
     if (morton) {
         uint32_t *d = nullptr;

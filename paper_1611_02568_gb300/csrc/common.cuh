@@ -354,6 +354,8 @@ cudaError_t launch_zsum(pxsne_ctx *c);
 constexpr int kMaxL3 = 9;   // voxel screen up to 2^9 per axis (Morton keys < 2^27)
 int64_t cells3(int L);      // (8^(L+1) - 1) / 7
 int64_t level_offset3(int l);  // (8^l - 1) / 7
+// counts and exact coordinate sums (three arrays of 8^L) of the current voxels
+cudaError_t launch_leaf_hist3(pxsne_ctx *c, uint32_t *cnt, u64 *sums);
 cudaError_t launch_morton3(pxsne_ctx *c, uint32_t *out);
 cudaError_t launch_fill3(pxsne_ctx *c, float4 *p, float x, float y, float z);
 cudaError_t alloc3(pxsne_ctx *c);

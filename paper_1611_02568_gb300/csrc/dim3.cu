@@ -9,8 +9,8 @@
 //   k3_update           Eq. grad and the gains/momentum step per coordinate
 //   k3_snap             the exact-integer rescale of Sec. 4.2 per axis, the
 //                       voxel snap and the leaf histogram (counts, exact sums)
-//   k3_reduce, k3_records, k3_perm   the octree's upper levels, its cell
-//                       records, the counting sort of the points by voxel
+//   k3_perm, k3_reduce  the counting sort of the points by voxel; the
+//                       octree's upper levels with their cells' records
 //   k3_traverse         Barnes-Hut (Eq. bh_criteria) on the octree, one point
 //                       per lane, 32 points of consecutive voxels per warp
 //   k3_attract          Eq. grad's first term over P, one warp per row
@@ -266,35 +266,12 @@ __global__ void k3_snap(int n, int L, int rescale, float theta, const long long 
     atomicAdd(&sz[m], (u64)zv[2]);
 }
 
-// cells of level l from their eight children at level l + 1
-__global__ void k3_reduce(int l, uint32_t *cnt, u64 *sx, u64 *sy, u64 *sz) {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= (int64_t(1) << (3 * l))) return;
-    const int64_t ch = off3(l + 1) + 8 * c, me = off3(l) + c;
-    uint32_t N = 0u;
-    u64 X = 0ull, Y = 0ull, Zs = 0ull;
-#pragma unroll
-    for (int k = 0; k < 8; k++) {
-        N += cnt[ch + k];
-        X += sx[ch + k];
-        Y += sy[ch + k];
-        Zs += sz[ch + k];
-    }
-    cnt[me] = N;
-    sx[me] = X;
-    sy[me] = Y;
-    sz[me] = Zs;
-}
-
-// records of the cells of level l: {c_hi x, y, z, N} and {c_lo x, y, z, 0},
-// the centre of mass split at bit 16 as in 2-D (record_axis)
-__global__ void k3_records(int l, const uint32_t *__restrict__ cnt, const u64 *__restrict__ sx,
-                           const u64 *__restrict__ sy, const u64 *__restrict__ sz,
-                           float4 *__restrict__ ra, float4 *__restrict__ rb) {
-    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (c >= (int64_t(1) << (3 * l))) return;
-    const int64_t at = off3(l) + c;
-    const uint32_t N = cnt[at];
+// Record of cell at (level l, Morton c): {c_hi x, y, z, N} and {c_lo x, y,
+// z, 0}, the centre of mass split at bit 16 as in 2-D (record_axis); zeros
+// for an empty cell.
+__device__ __forceinline__ void put_record3(int l, int64_t c, int64_t at, uint32_t N, u64 X, u64 Y,
+                                            u64 Zs, float4 *__restrict__ ra,
+                                            float4 *__restrict__ rb) {
     if (N == 0u) {
         ra[at] = make_float4(0.f, 0.f, 0.f, 0.f);
         rb[at] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -305,11 +282,54 @@ __global__ void k3_records(int l, const uint32_t *__restrict__ cnt, const u64 *_
     const uint32_t bx = l > 0 ? demorton3((uint32_t)c, 0) << sh : 0u;
     const uint32_t by = l > 0 ? demorton3((uint32_t)c, 1) << sh : 0u;
     const uint32_t bz = l > 0 ? demorton3((uint32_t)c, 2) << sh : 0u;
-    record_axis(N, sx[at], bx, sh, hx, lx);
-    record_axis(N, sy[at], by, sh, hy, ly);
-    record_axis(N, sz[at], bz, sh, hz, lz);
+    record_axis(N, X, bx, sh, hx, lx);
+    record_axis(N, Y, by, sh, hy, ly);
+    record_axis(N, Zs, bz, sh, hz, lz);
     ra[at] = make_float4(hx, hy, hz, (float)N);
     rb[at] = make_float4(lx, ly, lz, 0.f);
+}
+
+// Cells of level l from their eight children at level l + 1: one thread per
+// child (coalesced), which writes the child's record (and, clear = the
+// children are the leaves, sets an occupied leaf back to zero once read, so
+// the next histogram starts from zeros without a memset of every leaf); the
+// eight threads of a parent add up by shuffles.  At l = 0 the root's own
+// record is written too.
+__global__ void k3_reduce(int l, int clear, uint32_t *cnt, u64 *sx, u64 *sy, u64 *sz,
+                          float4 *__restrict__ ra, float4 *__restrict__ rb) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // child at level l + 1
+    const bool in = k < (int64_t(1) << (3 * (l + 1)));
+    const int64_t at = off3(l + 1) + k;
+    uint32_t N = 0u;
+    u64 X = 0ull, Y = 0ull, Zs = 0ull;
+    if (in) {
+        N = cnt[at];
+        X = sx[at];
+        Y = sy[at];
+        Zs = sz[at];
+        put_record3(l + 1, k, at, N, X, Y, Zs, ra, rb);
+        if (clear && N != 0u) {
+            cnt[at] = 0u;
+            sx[at] = 0ull;
+            sy[at] = 0ull;
+            sz[at] = 0ull;
+        }
+    }
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+        N += __shfl_xor_sync(0xffffffffu, N, o);
+        X += __shfl_xor_sync(0xffffffffu, X, o);
+        Y += __shfl_xor_sync(0xffffffffu, Y, o);
+        Zs += __shfl_xor_sync(0xffffffffu, Zs, o);
+    }
+    if (in && (k & 7) == 0) {
+        const int64_t c = k >> 3, me = off3(l) + c;
+        cnt[me] = N;
+        sx[me] = X;
+        sy[me] = Y;
+        sz[me] = Zs;
+        if (l == 0) put_record3(0, 0, me, N, X, Y, Zs, ra, rb);
+    }
 }
 
 // the counting sort by voxel: perm[start of the voxel + rank] = i; the
@@ -381,11 +401,14 @@ __global__ void __launch_bounds__(kT3Warps * 32)
         const int64_t at = s_off[lc] + m0;
         const bool me = (top.mask >> lane) & 1u;
         if (lc == L) {
+#pragma unroll
             for (int ch = 0; ch < 8; ch++) {
+                // both halves of the record requested together (an empty
+                // cell's second half is read and not used)
                 const float4 r = __ldg(ra + at + ch);
+                const float4 q4 = __ldg(rb + at + ch);
                 const float N = r.w;
                 if (N == 0.f) continue;
-                const float4 q4 = __ldg(rb + at + ch);
                 float dx = (hx - r.x) + (lx - q4.x);
                 float dy = (hy - r.y) + (ly - q4.y);
                 float dz = (hz - r.z) + (lz - q4.z);
@@ -420,11 +443,12 @@ __global__ void __launch_bounds__(kT3Warps * 32)
                 overflow = true;
                 break;
             }
+#pragma unroll
             for (int ch = 0; ch < 8; ch++) {
                 const float4 r = __ldg(ra + at + ch);
+                const float4 q4 = __ldg(rb + at + ch);
                 const float N = r.w;
                 if (N == 0.f) continue;
-                const float4 q4 = __ldg(rb + at + ch);
                 const uint32_t mc = m0 + (uint32_t)ch;
                 const float dx = ((hx - r.x) + (lx - q4.x)) * s0;
                 const float dy = ((hy - r.y) + (ly - q4.y)) * s1;
@@ -586,6 +610,21 @@ __global__ void k3_write_y(int n, int L, const uint4 *__restrict__ z, const DevS
     }
 }
 
+// The leaf histogram of the current state, for inspection (the iteration's
+// own is cleared by the first reduction once read).
+__global__ void k3_leaf_hist(int n, int L, const uint4 *__restrict__ z, uint32_t *cnt, u64 *sx,
+                             u64 *sy, u64 *sz) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int F = 32 - L;
+    const uint4 v = z[i];
+    const uint32_t m = morton3(v.x >> F, v.y >> F, v.z >> F);
+    atomicAdd(&cnt[m], 1u);
+    atomicAdd(&sx[m], (u64)v.x);
+    atomicAdd(&sy[m], (u64)v.y);
+    atomicAdd(&sz[m], (u64)v.z);
+}
+
 __global__ void k3_morton(int n, int L, const uint4 *__restrict__ z, uint32_t *__restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -608,6 +647,17 @@ cudaError_t launch_fill3(pxsne_ctx *c, float4 *p, float x, float y, float z) {
 
 int64_t cells3(int L) { return off3(L + 1); }
 int64_t level_offset3(int l) { return off3(l); }
+
+cudaError_t launch_leaf_hist3(pxsne_ctx *c, uint32_t *cnt, u64 *sums) {
+    const int n = (int)c->n;
+    const size_t leaves = size_t(1) << (3 * c->L);
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(cnt, 0, leaves * 4, c->stream))) return e;
+    if ((e = cudaMemsetAsync(sums, 0, 3 * leaves * 8, c->stream))) return e;
+    k3_leaf_hist<<<(n + 255) / 256, 256, 0, c->stream>>>(n, c->L, c->z3, cnt, sums, sums + leaves,
+                                                         sums + 2 * leaves);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_morton3(pxsne_ctx *c, uint32_t *out) {
     const int n = (int)c->n;
@@ -645,6 +695,9 @@ cudaError_t alloc3(pxsne_ctx *c) {
     if ((e = alloc_n(&c->rec3a, (size_t)cells))) return e;
     if ((e = alloc_n(&c->rec3b, (size_t)cells))) return e;
     if ((e = alloc_n(&c->vstart3, (size_t)(int64_t(1) << (3 * c->L)) + 1))) return e;
+    // the leaf histogram starts from zeros; the first reduction clears what it read
+    if ((e = cudaMemsetAsync(c->cnt3, 0, (size_t)cells * sizeof(uint32_t), c->stream))) return e;
+    if ((e = cudaMemsetAsync(c->sum3, 0, 3 * (size_t)cells * sizeof(u64), c->stream))) return e;
     c->dev_bytes += (int64_t)n * (16 + 24 + 16 * 4) + cells * (4 + 24 + 32) +
                     ((int64_t(1) << (3 * c->L)) + 1) * 8;
     return cudaSuccess;
@@ -692,25 +745,21 @@ static cudaError_t tree3(pxsne_ctx *c, bool rescale) {
     uint32_t *cnt = c->cnt3;
     u64 *sx = c->sum3, *sy = c->sum3 + cells, *sz = c->sum3 + 2 * cells;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(cnt + lo, 0, (size_t)leaves * sizeof(uint32_t), st))) return e;
-    for (u64 *p : {sx, sy, sz})
-        if ((e = cudaMemsetAsync(p + lo, 0, (size_t)leaves * sizeof(u64), st))) return e;
+    // the leaves are zero here (set at allocation, cleared by the first
+    // reduction after each histogram)
     k3_snap<<<(n + 255) / 256, 256, 0, st>>>(n, L, rescale ? 1 : 0, c->p.theta, c->zhat3, c->z3,
                                               c->rank, cnt + lo, sx + lo, sy + lo, sz + lo, c->sc);
     if ((e = cudaGetLastError())) return e;
-    for (int l = L - 1; l >= 0; l--) {
-        const int64_t m = int64_t(1) << (3 * l);
-        k3_reduce<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(l, cnt, sx, sy, sz);
-    }
-    for (int l = 0; l <= L; l++) {
-        const int64_t m = int64_t(1) << (3 * l);
-        k3_records<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(l, cnt, sx, sy, sz, c->rec3a,
-                                                                 c->rec3b);
-    }
-    if ((e = cudaGetLastError())) return e;
+    // the voxel order (before the leaves are cleared)
     if ((e = scan_u32_to_i64(cnt + lo, leaves, c->vstart3, st))) return e;
     k3_perm<<<(n + 255) / 256, 256, 0, st>>>(n, L, c->z3, c->rank, c->vstart3, c->perm, c->sc,
                                               rescale ? 1 : 0);
+    if ((e = cudaGetLastError())) return e;
+    for (int l = L - 1; l >= 0; l--) {
+        const int64_t m = int64_t(1) << (3 * (l + 1));  // the children
+        k3_reduce<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(l, l == L - 1 ? 1 : 0, cnt, sx, sy,
+                                                               sz, c->rec3a, c->rec3b);
+    }
     return cudaGetLastError();
 }
 
