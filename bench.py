@@ -712,7 +712,7 @@ def run_gpu(args):
                 "l2": {"achieved": l2_alg, "peak": mpeaks["l2_read_gbs"], "unit": "GB/s",
                        "frac": l2_alg / mpeaks["l2_read_gbs"],
                        "work": f"{RECORD_BYTES} B of cell record per tested (point, cell) "
-                               f"pair (the survey's per-pair model; a warp loads each "
+                               f"pair (the per-pair record model, n I x 20 B; a warp loads each "
                                f"record once for all its points, so the loads it issues "
                                f"are the warp steps' records, below)",
                        "warp_loads_GBps": nodes * 80 / sec / 1e9,

@@ -48,7 +48,7 @@ extern "C" {
 #define PXSNE_E_CUDA (-3)        /* a CUDA runtime call failed */
 #define PXSNE_E_STATE (-4)       /* call out of order (e.g. step before init) */
 #define PXSNE_E_DEVICE (-5)      /* error flagged by a kernel */
-#define PXSNE_E_UNSUPPORTED (-6) /* valid request this build does not support */
+#define PXSNE_E_UNSUPPORTED (-6) /* a valid request this library does not support */
 
 /* Device error flags, read back by pxsne_sync (and by every synchronising
  * call, which then returns PXSNE_E_DEVICE and clears them). */
