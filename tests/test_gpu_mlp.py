@@ -116,7 +116,8 @@ def test_warm_start_beats_random_init(px):
     mixture places a fresh draw ahead of the plain method: its start alone has
     a lower KL than 250 plain iterations, refinement (no exaggeration) stays
     ahead at equal iteration counts, and after 1,000 iterations it is within 1 %
-    of the plain run.
+    of the plain run; its neighbourhood precision is ahead at the start and at
+    equal iteration counts.
 
     Training layouts: the first from the plain method; the others refined from
     the prediction of a network fitted to the first (so they share its
@@ -158,19 +159,28 @@ def test_warm_start_beats_random_init(px):
     with px.Context(px.Params(log2_r=L)) as ctx:
         ctx.affinities(Xf)
         ctx.init(datagen.init_y0(21, n))
-        plain = []
+        plain, plain_prec = [], []
         for _ in range(4):
             ctx.step(250)
             plain.append(ctx.kl())
+            plain_prec.append(ctx.nbr_precision(k=10))
         ctx.set_schedule(exag_iters=0, momentum_switch=0)
         ctx.init(Y0w.astype(np.float32))
-        warm = [ctx.kl()]
+        warm, warm_prec = [ctx.kl()], [ctx.nbr_precision(k=10)]
         for _ in range(4):
             ctx.step(250)
             warm.append(ctx.kl())
+            warm_prec.append(ctx.nbr_precision(k=10))
     print("plain KL at 250..1000:", np.round(plain, 4), "warm KL at 0..1000:", np.round(warm, 4))
+    print("plain precision (k = 10) at 250..1000:", np.round(plain_prec, 4),
+          "warm at 0..1000:", np.round(warm_prec, 4))
     # the network's start alone is ahead of 250 plain iterations, and the warm
     # run stays ahead at equal iteration counts
     assert warm[0] < plain[0], (warm[0], plain[0])
     assert warm[1] < plain[0] and warm[2] < plain[1], (warm, plain)
     assert warm[4] <= plain[3] * 1.01, (warm, plain)
+    # and the neighbourhood precision (Eq. nei_prec, k = 10) is ahead too, at
+    # the start and at equal iteration counts
+    assert warm_prec[0] > plain_prec[0], (warm_prec, plain_prec)
+    for i in range(1, 5):
+        assert warm_prec[i] >= plain_prec[i - 1], (warm_prec, plain_prec)
