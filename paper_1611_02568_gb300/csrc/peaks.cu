@@ -102,13 +102,18 @@ extern "C" int pxsne_measure_peaks(void *stream, double *l2_read_gbs, double *fp
     if (l2_read_gbs) {
         // buffers of 1/16, 1/8 and 1/4 of L2 (powers of two, resident after the
         // first pass), 2, 4 or 8 CTAs of 512 threads per SM: the best of all
+        // on three allocations held at once (the rate depends on where in the
+        // two dies' L2 halves a buffer's lines fall)
         int64_t top = 1 << 20;
         while (top * 2 <= (int64_t)prop.l2CacheSize / 4) top *= 2;
-        uint4 *buf = nullptr;
+        uint4 *bufs[3] = {nullptr, nullptr, nullptr};
         double best = 0.0;
-        if (cudaMalloc(&buf, top)) {
-            rc = PXSNE_E_OOM;
-        } else {
+        for (int a = 0; a < 3 && rc == PXSNE_OK; a++) {
+            if (cudaMalloc(&bufs[a], top)) {
+                rc = PXSNE_E_OOM;
+                break;
+            }
+            uint4 *buf = bufs[a];
             cudaMemsetAsync(buf, 1, top, st);
             for (int64_t bytes = top / 4; bytes <= top && rc == PXSNE_OK; bytes *= 2) {
                 const int64_t n16 = bytes / 16;
@@ -123,9 +128,10 @@ extern "C" int pxsne_measure_peaks(void *stream, double *l2_read_gbs, double *fp
                     else best = fmax(best, (double)total * 16.0 / (ms * 1e-3) / 1e9);
                 }
             }
-            cudaFree(buf);
-            if (rc == PXSNE_OK) *l2_read_gbs = best;
         }
+        for (uint4 *b : bufs)
+            if (b) cudaFree(b);
+        if (rc == PXSNE_OK) *l2_read_gbs = best;
     }
     const int iters = 4096;
     // flops per launch: threads x iterations x 8 chains x 2 lanes x 2 (FMA);
