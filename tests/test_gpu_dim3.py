@@ -146,3 +146,21 @@ def test_calls_without_a_3d_form_are_refused(px, gauss3):
                 call()
         ctx.step(2)
         assert ctx.sync() == 0
+
+
+def test_octree_rebuilt_from_cleared_leaves(px, gauss3):
+    # the first reduction clears the leaves it read: a second state's octree
+    # has no trace of the first's
+    X, P, Y0, st = gauss3
+    L = 6
+    rng = np.random.default_rng(47)
+    z2 = rng.integers(0, 2 ** 32, st.z.shape, dtype=np.uint64).astype(np.uint32)
+    with px.Context(px.Params(log2_r=L, dim=3)) as ctx:
+        ctx.set_P(P.row_ptr, P.col, P.val.astype(np.float32))
+        for z in (st.z, z2, st.z):
+            ctx.set_state(z, st.s)
+            check_tree(ctx, z, L)
+            Frep, Zi, _, _ = ctx.get_forces()
+            oF, oZi, _ = oracle.bh_repulsion3(z, st.s, L, 0.5)
+            assert rel(Frep, oF) <= FORCE_TOL and rel(Zi, oZi) <= FORCE_TOL
+        assert ctx.sync() == 0

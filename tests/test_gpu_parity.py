@@ -95,6 +95,30 @@ def test_tree_bit_exact(px, gauss, L):
         check_tree(ctx, z, L)
 
 
+@pytest.mark.parametrize("L,cm", [(4, 0), (11, 0), (13, 0), (11, 1)])
+def test_tree_rebuilt_from_cleared_leaves(px, gauss, L, cm):
+    # the pyramid clears the leaves it read: a second state's tree (both
+    # pyramid kernels, and the count-only tree) has no trace of the first's
+    X, P, Y0, st = gauss
+    rng = np.random.default_rng(100 + L)
+    z1 = st.z.copy()
+    z2 = rng.integers(0, 2 ** 32, st.z.shape, dtype=np.uint64).astype(np.uint32)
+    z2[:50] = z2[0]
+    with make_ctx(px, L=L, centre_mode=cm) as ctx:
+        ctx.set_P(P.row_ptr, P.col, P.val.astype(np.float32))
+        for z in (z1, z2, z1):
+            ctx.set_state(z, st.s)
+            if cm == 0:
+                check_tree(ctx, z, L)
+            else:
+                cnt_o, _, _ = oracle.pyramid(z, L)
+                for l in range(L + 1):
+                    cnt, _, _, _ = ctx.get_tree(l)
+                    off = oracle.level_offset(l)
+                    assert np.array_equal(cnt, cnt_o[off:off + 4 ** l]), l
+        assert ctx.sync() == 0
+
+
 @pytest.mark.parametrize("theta", [0.5, 0.0, 0.25, 1.0])
 def test_forces_match_oracle(px, gauss, theta):
     X, P, Y0, st = gauss
