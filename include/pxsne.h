@@ -220,7 +220,12 @@ int pxsne_kl(pxsne_ctx *ctx, double *out);
 /* Current embedding.  Y (host or device, n x 2 float32, may be NULL) gets
  * y = s * z minus the per-axis mean (t-SNE coordinates, centred); pix (host or
  * device, n x 2 int32, may be NULL) gets the pixel coordinates z >> (32 - L).
- * Synchronises. */
+ * on_device: 0 host buffers, 1 device buffers; both synchronise.  2: device
+ * buffers, enqueued on the context's stream without synchronising (the
+ * buffers hold the frame once the stream reaches this point; a device error
+ * flag raised meanwhile is reported by the next synchronising call), so a
+ * caller can copy frame t to the host on a stream of its own while step t + 1
+ * runs. */
 int pxsne_get_Y(pxsne_ctx *ctx, float *Y, int32_t *pix, int on_device);
 
 /* Neighbourhood precision of the current embedding (Eq. nei_prec):

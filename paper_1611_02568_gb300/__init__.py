@@ -266,9 +266,11 @@ class Context:
         self._ck(self.L.pxsne_kl(self.h, C.byref(out)))
         return out.value
 
-    def get_Y(self, Y=None, pix=None, want_pix=True):
+    def get_Y(self, Y=None, pix=None, want_pix=True, blocking=True):
         """Centred y-space coordinates and pixels; fills Y/pix if given
-        (numpy, or CUDA tensors), else returns new numpy arrays."""
+        (numpy, or CUDA tensors), else returns new numpy arrays.  With
+        blocking=False (CUDA tensors only) the frame is enqueued on the
+        context's stream and the call returns at once."""
         n, d = self.sizes()[0], self.dim
         if Y is None and pix is None:
             Y = np.empty((n, d), np.float32)
@@ -278,7 +280,9 @@ class Context:
         if Y is not None and pix is not None and dy != dp:
             raise ValueError("Y and pix must both be host or both be device buffers")
         dev = dy or dp
-        self._ck(self.L.pxsne_get_Y(self.h, py, pp, dev))
+        if not blocking and not dev:
+            raise ValueError("blocking=False needs device buffers")
+        self._ck(self.L.pxsne_get_Y(self.h, py, pp, dev if blocking else 2))
         return Y, pix
 
     def sync(self):

@@ -712,6 +712,8 @@ int pxsne_kl(pxsne_ctx *c, double *out) {
 int pxsne_get_Y(pxsne_ctx *c, float *Y, int32_t *pix, int on_device) {
     int rc = need_state(c);
     if (rc) return rc;
+    if (on_device < 0 || on_device > 2) return fail(c, PXSNE_E_ARG, "on_device = %d", on_device);
+    const bool async = on_device == 2;
     cudaStream_t st = c->stream;
     const int64_t n = c->n;
     const size_t row = is3(c) ? 12 : 8;  // bytes of one point's values
@@ -738,6 +740,10 @@ int pxsne_get_Y(pxsne_ctx *c, float *Y, int32_t *pix, int on_device) {
         }
     }
     CK(c, cudaFreeAsync(scratch, st));
+    if (async) {
+        CK(c, cudaGetLastError());
+        return PXSNE_OK;
+    }
     return check_device(c, nullptr);
 }
 

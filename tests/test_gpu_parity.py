@@ -328,6 +328,33 @@ def test_get_Y_and_pixels(px, gauss):
     np.testing.assert_allclose(Y, y - y.mean(0), rtol=0, atol=1e-6 * np.abs(y).max())
 
 
+def test_get_Y_without_synchronising(px, gauss):
+    # the frame enqueued on the context's stream (device buffers, no host
+    # wait) equals the synchronised one once the stream has reached it, also
+    # with steps enqueued behind it
+    import torch
+    X, P, Y0, st = gauss
+    s = torch.cuda.Stream()
+    n = P.n
+    with px.Context(px.Params(log2_r=9), stream=s.cuda_stream) as ctx:
+        inject(ctx, P, st)
+        Yd = torch.empty((n, 2), dtype=torch.float32, device="cuda")
+        Pd = torch.empty((n, 2), dtype=torch.int32, device="cuda")
+        ctx.get_Y(Yd, Pd, blocking=False)
+        ctx.step(3)
+        s.synchronize()
+        Y2, pix2 = ctx.get_Y()            # after the three steps
+        z2 = ctx.get_state()[0]
+        assert np.array_equal(Pd.cpu().numpy(), (st.z >> (32 - 9)).astype(np.int32))
+        y = st.y()
+        np.testing.assert_allclose(Yd.cpu().numpy(), y - y.mean(0), rtol=0,
+                                   atol=1e-6 * np.abs(y).max())
+        assert np.array_equal(pix2, (z2 >> (32 - 9)).astype(np.int32))
+        with pytest.raises(ValueError):
+            ctx.get_Y(np.empty((n, 2), np.float32), None, blocking=False)
+        assert ctx.sync() == 0
+
+
 def test_edge_cases(px):
     # two points (k = 1), both in one pixel, then apart
     P = oracle.CSR(np.array([0, 1, 2]), np.array([1, 0], np.int32), np.array([0.5, 0.5]))
