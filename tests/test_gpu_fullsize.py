@@ -188,3 +188,21 @@ def test_scale_workload_shape_at_2M():
         rp, col, val = ctx.get_P()
         P = oracle.CSR(rp, col, val.astype(np.float64))
         check_state(ctx, P, np.random.default_rng(8).choice(n, 512, replace=False), L=Ls)
+
+
+def test_largest_n():
+    """n = 2^24, the largest the library takes (the scale workload's recipe on
+    its 4096^2 screen): P and 20 iterations run without a device error flag,
+    and the tree, Z and the sampled forces match the oracle."""
+    import paper_1611_02568_gb300 as px
+    n, Ls = 1 << 24, 12
+    X, _ = datagen.gmm64out(seed=1, n=n)
+    with px.Context(px.Params(log2_r=Ls, theta=THETA, k=K, perplexity=30.0)) as ctx:
+        ctx.affinities(X)
+        assert ctx.sizes()[0] == n
+        ctx.init(datagen.init_y0(1, n))
+        ctx.step(20)
+        assert ctx.sync() == 0
+        rp, col, val = ctx.get_P()
+        P = oracle.CSR(rp, col, val.astype(np.float64))
+        check_state(ctx, P, np.random.default_rng(9).choice(n, 256, replace=False), L=Ls)
