@@ -95,6 +95,29 @@ def test_tree_bit_exact(px, gauss, L):
         check_tree(ctx, z, L)
 
 
+@pytest.mark.slow
+def test_largest_screen(px, gauss):
+    # L = 14 (a 16384^2 screen, the largest; 268M pixels, about 12 GB of
+    # tree): counts at the root, the middle and the two deepest levels, the
+    # leaf sums, and the forces of every point
+    X, P, Y0, st = gauss
+    L = 14
+    with make_ctx(px, L=L) as ctx:
+        inject(ctx, P, st)
+        cnt_o, sx_o, sy_o = oracle.pyramid(st.z, L)
+        for l in (0, 1, 7, 13, 14):
+            cnt, sx, sy, _ = ctx.get_tree(l, sums=(l == L))
+            off = oracle.level_offset(l)
+            assert np.array_equal(cnt, cnt_o[off:off + 4 ** l]), l
+        assert np.array_equal(sx, sx_o[off:off + 4 ** L])
+        assert np.array_equal(sy, sy_o[off:off + 4 ** L])
+        del cnt_o, sx_o, sy_o
+        Frep, Zi, Fattr, Z = ctx.get_forces()
+        assert ctx.sync() == 0
+    oF, oZi, _ = oracle.bh_repulsion(st.z, st.s, L, 0.5)
+    assert rel(Frep, oF) <= FORCE_TOL and rel(Zi, oZi) <= FORCE_TOL
+
+
 @pytest.mark.parametrize("L,cm", [(4, 0), (11, 0), (13, 0), (11, 1)])
 def test_tree_rebuilt_from_cleared_leaves(px, gauss, L, cm):
     # the pyramid clears the leaves it read: a second state's tree (both
