@@ -400,12 +400,16 @@ __global__ void __launch_bounds__(kT3Warps * 32)
         const uint32_t m0 = (top.node & 0x07ffffffu) << 3;
         const int64_t at = s_off[lc] + m0;
         const bool me = (top.mask >> lane) & 1u;
+        // the eight children's first record halves (with the counts) are
+        // requested together, one latency per node; the second halves are
+        // read per child (an empty cell's is read and not used)
+        float4 rpre[8];
+#pragma unroll
+        for (int ch = 0; ch < 8; ch++) rpre[ch] = __ldg(ra + at + ch);
         if (lc == L) {
 #pragma unroll
             for (int ch = 0; ch < 8; ch++) {
-                // both halves of the record requested together (an empty
-                // cell's second half is read and not used)
-                const float4 r = __ldg(ra + at + ch);
+                const float4 r = rpre[ch];
                 const float4 q4 = __ldg(rb + at + ch);
                 const float N = r.w;
                 if (N == 0.f) continue;
@@ -445,7 +449,7 @@ __global__ void __launch_bounds__(kT3Warps * 32)
             }
 #pragma unroll
             for (int ch = 0; ch < 8; ch++) {
-                const float4 r = __ldg(ra + at + ch);
+                const float4 r = rpre[ch];
                 const float4 q4 = __ldg(rb + at + ch);
                 const float N = r.w;
                 if (N == 0.f) continue;
