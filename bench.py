@@ -157,21 +157,27 @@ def measured_peaks():
 RELABEL_EVERY = 100  # the library refreshes the attraction's relabelled P this often
 
 
-def group_bytes(n, nnz, L, nonempty=None):
+def group_bytes(n, nnz, L, nonempty=None, occupied=None):
     """Bytes each kernel group must move per launch.  `nonempty`: cells of
     the tree holding at least one point (only their 16-byte records are
-    written; every cell's count is), all cells when not given."""
+    written; every cell's count is), all cells when not given.  `occupied`:
+    leaves holding at least one point (the histogram writes their count and
+    sums, 20 B, and the pyramid clears them again), min(n, 4^L) when not
+    given."""
     leaves = 4 ** L
     cells = (4 ** (L + 1) - 1) // 3
     nonempty = cells if nonempty is None else nonempty
+    occupied = min(n, leaves) if occupied is None else occupied
     return {
         # per iteration on average: P read and written once per relabel, plus
         # the maps, row lengths, scan and positions
         "k_relabel": (nnz * 16 + n * (4 + 8 + 4 + 4 + 4 + 8 + 8 + 8 + 8)) / RELABEL_EVERY,
         "k_update": n * (8 + 8 + 8 + 8 + 8 + 8 + 8 + 16),      # z,Frep,Fattr,u,gains r; u,gains w; zhat w
-        "k_snap_hist": leaves * 20 + n * (4 + 16 + 8 + 4 + 4 + 8),  # memset; perm,zhat,ainv r; z,rank,zp w
-        "k_pyr_pass": leaves * (20 + 4) + cells * 4 + nonempty * 16,  # leaf sums r, leaf_start w,
-                                                               # recn w, rec of non-empty cells w
+        # perm, zhat, ainv r; z, rank, zp w; the occupied leaves' count and sums w
+        "k_snap_hist": n * (4 + 16 + 8 + 4 + 4 + 8) + occupied * 20,
+        # every leaf's count and sums r, leaf_start w, recn w, records of the
+        # non-empty cells w, the occupied leaves cleared
+        "k_pyr_pass": leaves * (20 + 4) + cells * 4 + nonempty * 16 + occupied * 20,
         "k_perm_scatter": n * (8 + 4 + 4 + 4),
         "k_bh_traverse": n * (4 + 8 + 8 + 4) + cells * 20,    # perm, z r; Frep, Zi w; rec + recn r
         "k_attract": nnz * 8 + (n + 1) * 8 + n * (8 + 4 + 8),
@@ -717,8 +723,8 @@ def run_gpu(args):
     lvc = ctx.level_counters()
     peaks, peak_kind = measured_peaks()
     # non-empty cells of the final state (only their records are written)
-    nonempty = sum(int(np.count_nonzero(ctx.get_tree(l)[0])) for l in range(W["log2_r"] + 1))
-    gb = group_bytes(n, nnz, W["log2_r"], nonempty)
+    occ = [int(np.count_nonzero(ctx.get_tree(l)[0])) for l in range(W["log2_r"] + 1)]
+    gb = group_bytes(n, nnz, W["log2_r"], sum(occ), occ[-1])
     traffic = TRAFFIC_BYTES.get((W["workload"], n), {})
     top = max(groups, key=groups.get)
     avg_ms = {g: v / args.steps for g, v in groups.items()}

@@ -123,9 +123,11 @@ def test_algorithmic_bytes_per_unit():
     leaves, cells = 4 ** L, sum(4 ** l for l in range(L + 1))
     b = bench.group_bytes(n, nnz, L)
     assert b["k_update"] == 72 * n
-    assert b["k_snap_hist"] == 44 * n + 20 * leaves
-    assert b["k_pyr_pass"] == 24 * leaves + 20 * cells
-    assert bench.group_bytes(n, nnz, L, 100)["k_pyr_pass"] == 24 * leaves + 4 * cells + 16 * 100
+    assert b["k_snap_hist"] == 44 * n + 20 * min(n, leaves)
+    assert b["k_pyr_pass"] == 24 * leaves + 20 * cells + 20 * min(n, leaves)
+    b2 = bench.group_bytes(n, nnz, L, 100, 60)
+    assert b2["k_pyr_pass"] == 24 * leaves + 4 * cells + 16 * 100 + 20 * 60
+    assert b2["k_snap_hist"] == 44 * n + 20 * 60
     assert b["k_perm_scatter"] == 20 * n
     assert b["k_bh_traverse"] == 24 * n + 20 * cells
     assert b["k_attract"] == 8 * nnz + 8 * (n + 1) + 20 * n
