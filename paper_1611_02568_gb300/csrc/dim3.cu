@@ -170,8 +170,14 @@ __global__ void __launch_bounds__(256)
     const int t = sc->t;
     const float alpha = t < p.exag_iters ? p.exag : 1.0f;
     const float mu = t < p.mom_switch ? p.mom0 : p.mom1;
-    const double Z = sc->Z;
-    const float invZ = Z > 0.0 ? (float)(1.0 / Z) : 0.0f;
+    // 1 / Z once per CTA (an FP64 division)
+    __shared__ float s_invZ;
+    if (threadIdx.x == 0) {
+        const double Z = sc->Z;
+        s_invZ = Z > 0.0 ? (float)(1.0 / Z) : 0.0f;
+    }
+    __syncthreads();
+    const float invZ = s_invZ;
     const double is0 = sc->inv_s3[0], is1 = sc->inv_s3[1], is2 = sc->inv_s3[2];
     i64 lo[3], hi[3];
     for (int d = 0; d < 3; d++) {
@@ -236,11 +242,15 @@ __global__ void k3_snap(int n, int L, int rescale, float theta, const long long 
         i64 mn[3];
         u64 g[3];
         double q[3];
+        __shared__ double s_q[3];
         for (int d = 0; d < 3; d++) {
             mn[d] = sc->mm3[par][d];
             g[d] = (u64)(sc->mm3[par][3 + d] - mn[d]) + 1ull;
-            q[d] = kR3 / (double)g[d];
         }
+        // one FP64 division per axis and CTA (the same for every point)
+        if (threadIdx.x < 3) s_q[threadIdx.x] = kR3 / (double)g[threadIdx.x];
+        __syncthreads();
+        for (int d = 0; d < 3; d++) q[d] = s_q[d];
         if (i == 0) {
             // Eq. beta_scaling carried as s_d <- (s_d * gamma_d) / 2^32
             for (int d = 0; d < 3; d++) sc->s3[d] = (sc->s3[d] * (double)g[d]) / kR3;

@@ -26,13 +26,21 @@ __global__ void k_snap_hist(int n, int L, int rescale, float theta, u64 Rx, u64 
     i64 mnx = 0, mny = 0;
     u64 gx = 1, gy = 1;
     double qx = 0.0, qy = 0.0;
+    __shared__ double s_q[2];
     if (rescale) {
         mnx = sc->mm[par][0];
         mny = sc->mm[par][1];
         gx = (u64)(sc->mm[par][2] - mnx) + 1ull;
         gy = (u64)(sc->mm[par][3] - mny) + 1ull;
-        qx = (double)Rx / (double)gx;
-        qy = (double)Ry / (double)gy;
+        // R_d / gamma_d is the same for every point: one FP64 division per
+        // CTA (FP64 issues at a small fraction of the FP32 rate)
+        if (threadIdx.x == 0) {
+            s_q[0] = (double)Rx / (double)gx;
+            s_q[1] = (double)Ry / (double)gy;
+        }
+        __syncthreads();
+        qx = s_q[0];
+        qy = s_q[1];
         if (tid == 0) {
             sc->n_accept = 0ull;
             sc->n_test = 0ull;

@@ -20,8 +20,14 @@ __global__ void __launch_bounds__(256)
     const int t = sc->t;
     const float alpha = t < p.exag_iters ? p.exag : 1.0f;
     const float mu = t < p.mom_switch ? p.mom0 : p.mom1;
-    const double Z = sc->Z;
-    const float invZ = Z > 0.0 ? (float)(1.0 / Z) : 0.0f;
+    // 1 / Z once per CTA (an FP64 division)
+    __shared__ float s_invZ;
+    if (threadIdx.x == 0) {
+        const double Z = sc->Z;
+        s_invZ = Z > 0.0 ? (float)(1.0 / Z) : 0.0f;
+    }
+    __syncthreads();
+    const float invZ = s_invZ;
     const double is0 = sc->inv_s[0], is1 = sc->inv_s[1];
     i64 mnx = 0x7fffffffffffffffll, mny = 0x7fffffffffffffffll;
     i64 mxx = (i64)0x8000000000000000ull, mxy = (i64)0x8000000000000000ull;
