@@ -147,8 +147,10 @@ const char *pxsne_last_error(const pxsne_ctx *ctx);
  * (the shared-memory tiles of the search bound D further for large k; an
  * unsupported size returns an error).  perplexity <= 0 uses the
  * context's parameter.  Replaces any previous P and clears the embedding
- * state.  Synchronises.  Row convergence failures set PXSNE_DEVERR_BISECT and
- * return PXSNE_E_DEVICE (P is still built from the last bracket). */
+ * state.  Synchronises.  A non-finite entry of X (checked on the device)
+ * returns PXSNE_E_ARG and leaves the context as it was.  Row convergence
+ * failures set PXSNE_DEVERR_BISECT and return PXSNE_E_DEVICE (P is still
+ * built from the last bracket). */
 int pxsne_affinities(pxsne_ctx *ctx, const float *X, int64_t n, int32_t D,
                      float perplexity, int x_on_device);
 

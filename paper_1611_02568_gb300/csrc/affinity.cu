@@ -38,6 +38,24 @@ constexpr int kQR = 64;    // query rows per CTA
 constexpr int kCT = 128;   // candidates per tile
 constexpr int kKnnThreads = 256;
 
+// flag |= 1 if any of the m values of X is not finite (the input check of
+// P construction, on the device where X already is)
+__global__ void k_nonfinite(int64_t m, const float *__restrict__ X, unsigned *flag) {
+    bool bad = false;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < m;
+         q += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(__ldcs(X + q));
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+cudaError_t launch_nonfinite(pxsne_ctx *c, const float *X, int64_t m, unsigned *flag,
+                             cudaStream_t st) {
+    const int64_t need = (m + 255) / 256;
+    const int cap = 8 * std::max(c->sms, 1);
+    k_nonfinite<<<(unsigned)std::min<int64_t>(need, cap), 256, 0, st>>>(m, X, flag);
+    return cudaGetLastError();
+}
+
 __global__ void k_row_norms(int64_t n, int D, const float *__restrict__ X, float *__restrict__ nrm) {
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;

@@ -399,17 +399,7 @@ int pxsne_affinities(pxsne_ctx *c, const float *X, int64_t n, int32_t D, float p
     if (D < 1 || D > 256) return fail(c, PXSNE_E_UNSUPPORTED, "D = %d outside [1, 256]", D);
     if (perplexity <= 0.f) perplexity = c->p.perplexity;
     if (perplexity > (float)k) return fail(c, PXSNE_E_ARG, "perplexity > k");
-    if (!x_on_device) {
-        for (int64_t q = 0; q < n * D; q++)
-            if (!std::isfinite(X[q])) return fail(c, PXSNE_E_ARG, "X has a non-finite entry");
-    }
     cudaStream_t st = c->stream;
-    free_state(c);
-    dfree(c->rp); dfree(c->col); dfree(c->val); dfree(c->rowlen);
-    dfree(c->knn_idx); dfree(c->knn_d2); dfree(c->beta);
-    c->n = n;
-    c->D = D;
-    c->nnz = 0;
     float *Xd = nullptr;
     const float *Xuse = X;
     if (!x_on_device) {
@@ -417,6 +407,28 @@ int pxsne_affinities(pxsne_ctx *c, const float *X, int64_t n, int32_t D, float p
         CK(c, cudaMemcpyAsync(Xd, X, (size_t)n * D * sizeof(float), cudaMemcpyHostToDevice, st));
         Xuse = Xd;
     }
+    {
+        // X is checked for non-finite entries on the device, before any
+        // state is replaced (a host loop over the n D values cost more than
+        // the copy)
+        unsigned *flag = nullptr, bad = 0u;
+        CK(c, cudaMallocAsync(&flag, sizeof(unsigned), st));
+        CK(c, cudaMemsetAsync(flag, 0, sizeof(unsigned), st));
+        CK(c, launch_nonfinite(c, Xuse, n * D, flag, st));
+        CK(c, cudaMemcpyAsync(&bad, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        CK(c, cudaFreeAsync(flag, st));
+        CK(c, cudaStreamSynchronize(st));
+        if (bad) {
+            if (Xd) CK(c, cudaFreeAsync(Xd, st));
+            return fail(c, PXSNE_E_ARG, "X has a non-finite entry");
+        }
+    }
+    free_state(c);
+    dfree(c->rp); dfree(c->col); dfree(c->val); dfree(c->rowlen);
+    dfree(c->knn_idx); dfree(c->knn_d2); dfree(c->beta);
+    c->n = n;
+    c->D = D;
+    c->nnz = 0;
     CK(c, dalloc(c, &c->knn_idx, (size_t)n * k));
     CK(c, dalloc(c, &c->knn_d2, (size_t)n * k));
     CK(c, dalloc(c, &c->beta, (size_t)n));

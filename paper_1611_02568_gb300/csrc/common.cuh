@@ -332,6 +332,8 @@ cudaError_t launch_update(pxsne_ctx *c, cudaEvent_t *marks = nullptr);
 cudaError_t launch_kl(pxsne_ctx *c, double *out_dev);
 cudaError_t launch_centre_y(pxsne_ctx *c, float *Ydev, int32_t *pixdev, float *scratch);
 cudaError_t launch_philox_y0(pxsne_ctx *c, float *Y0dev, uint64_t seed, float sigma);
+cudaError_t launch_nonfinite(pxsne_ctx *c, const float *X, int64_t m, unsigned *flag,
+                             cudaStream_t st);
 cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, int32_t k,
                        int32_t *idx, float *d2);
 cudaError_t launch_perplexity(pxsne_ctx *c, const float *d2, int64_t n, int32_t k,
