@@ -426,6 +426,34 @@ def test_invalid_calls(px):
             ctx.affinities(np.zeros((50, 300), np.float32))   # D > 256
 
 
+def test_nonfinite_X_refused_and_context_kept(px, gauss):
+    # the check runs on the device, for host and device X alike, before any
+    # state is replaced: a refused call leaves P and the embedding as they were
+    import torch
+    X, P, Y0, _ = gauss
+    with make_ctx(px, L=9) as ctx:
+        ctx.affinities(X)
+        ctx.init(Y0)
+        ctx.step(3)
+        before = ctx.get_state()
+        rp, col, val = ctx.get_P()
+        for bad in (np.inf, -np.inf, np.nan):
+            Xb = X.copy()
+            Xb[X.shape[0] - 1, X.shape[1] - 1] = bad   # the last value of X
+            for src in (Xb, torch.from_numpy(Xb).cuda()):
+                with pytest.raises(px.PxsneError):
+                    ctx.affinities(src)
+        for a, b in zip(ctx.get_state(), before):
+            assert np.array_equal(a, b)
+        rp2, col2, val2 = ctx.get_P()
+        assert np.array_equal(rp, rp2) and np.array_equal(col, col2) and np.array_equal(val, val2)
+        ctx.step(2)
+        assert ctx.sync() == 0
+        # a finite X passed on the device is taken
+        ctx.affinities(torch.from_numpy(X).cuda())
+        assert np.array_equal(ctx.get_P()[1], col)
+
+
 @pytest.mark.parametrize("k", [1, 10, 32])
 def test_nbr_precision_matches_oracle(px, gauss, k):
     X, P, Y0, st = gauss
