@@ -426,6 +426,40 @@ def test_invalid_calls(px):
             ctx.affinities(np.zeros((50, 300), np.float32))   # D > 256
 
 
+def test_P_with_empty_rows(px, gauss):
+    # points that nothing attracts: the first, a middle and the last row of P
+    # emptied, and every entry pointing at them removed; checked at the
+    # injected state and after 120 iterations (across the attraction's
+    # relabel at t = 100)
+    X, P, Y0, st = gauss
+    n, L = P.n, 9
+    params = oracle.Params(L=L)
+    gone = np.array([0, 777, n - 1])
+    keep_row = np.ones(n, bool)
+    keep_row[gone] = False
+    rows = np.repeat(np.arange(n), np.diff(P.row_ptr))
+    keep = keep_row[rows] & keep_row[P.col]
+    rp = np.concatenate([[0], np.cumsum(np.bincount(rows[keep], minlength=n))]).astype(np.int64)
+    Pe = oracle.CSR(rp, P.col[keep].astype(np.int32), P.val[keep])
+    assert all(rp[i] == rp[i + 1] for i in gone)
+    with make_ctx(px, L=L) as ctx:
+        ctx.set_P(Pe.row_ptr, Pe.col, Pe.val.astype(np.float32))
+        ctx.set_state(st.z, st.s, st.u.astype(np.float32), st.gains.astype(np.float32), st.t)
+        for it in (0, 120):
+            if it:
+                ctx.step(it)
+            z, s, _, _, t = ctx.get_state()
+            assert t == st.t + it
+            Frep, Zi, Fattr, Z = ctx.get_forces()
+            assert not Fattr[gone].any()
+            assert rel(Fattr, oracle.attraction(Pe, z, s)) <= FORCE_TOL
+            oF, oZi, _ = oracle.bh_repulsion(z, s, L, 0.5)
+            assert rel(Frep, oF) <= FORCE_TOL
+            kl_o = oracle.kl_of(Pe, oracle.State(z, s, None, None), params)
+            assert abs(ctx.kl() - kl_o) <= 1e-4 * kl_o
+        assert ctx.sync() == 0
+
+
 def test_nonfinite_X_refused_and_context_kept(px, gauss):
     # the check runs on the device, for host and device X alike, before any
     # state is replaced: a refused call leaves P and the embedding as they were
