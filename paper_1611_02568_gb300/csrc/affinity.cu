@@ -414,6 +414,28 @@ __device__ __forceinline__ float thread_exact_d2(const float *__restrict__ X, in
 }
 
 // ---- locality order for the search (rows grouped by their nearest pivot)
+// dp[q] = row q n / m of X, the m pivots (m D values)
+__global__ void k_pivot_rows(int64_t n, int m, int D, const float *__restrict__ X,
+                             float *__restrict__ dp) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)m * D) return;
+    const int64_t q = t / D, d = t % D;
+    dp[t] = X[(q * n / m) * D + d];
+}
+
+// dd[q m + r] = |p_q - p_r|^2 in FP64, the dimensions added in order
+__global__ void k_pivot_d2(int m, int D, const float *__restrict__ dp, double *__restrict__ dd) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)m * m) return;
+    const int64_t q = t / m, r = t % m;
+    double s = 0.0;
+    for (int d = 0; d < D; d++) {
+        const double v = (double)dp[q * D + d] - (double)dp[r * D + d];
+        s += v * v;
+    }
+    dd[t] = s;
+}
+
 constexpr int kCells = 512;     // pivots (cells) of the locality order
 constexpr int kPivChunk = 128;  // pivots staged in shared memory at a time
 
@@ -1381,12 +1403,30 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         // i n / m), the pivots chained greedily by nearest neighbour on the host
         const int m = (int)std::min<int64_t>(kCells, std::max<int64_t>(1, n / 256));
         std::vector<float> hp((size_t)m * D), hq((size_t)m * D), hn((size_t)m);
-        for (int q = 0; q < m; q++)
-            if ((e = cudaMemcpyAsync(hp.data() + (size_t)q * D, Xdev + (q * n / m) * D,
-                                     (size_t)D * sizeof(float), cudaMemcpyDeviceToHost, st)))
-                return e;
-        if ((e = cudaStreamSynchronize(st))) return e;
+        std::vector<double> hd((size_t)m * m);
         {
+            // the pivot rows and their squared distances, formed on the device
+            // (a host loop over the m^2 D / 2 terms of the chain took 28 ms)
+            float *dp = nullptr;
+            double *dd = nullptr;
+            if ((e = cudaMallocAsync(&dp, (size_t)m * D * sizeof(float), st))) return e;
+            if ((e = cudaMallocAsync(&dd, (size_t)m * m * sizeof(double), st))) return e;
+            k_pivot_rows<<<(unsigned)(((int64_t)m * D + 255) / 256), 256, 0, st>>>(n, m, D, Xdev,
+                                                                                  dp);
+            k_pivot_d2<<<(unsigned)(((int64_t)m * m + 255) / 256), 256, 0, st>>>(m, D, dp, dd);
+            if ((e = cudaGetLastError())) return e;
+            if ((e = cudaMemcpyAsync(hp.data(), dp, (size_t)m * D * sizeof(float),
+                                     cudaMemcpyDeviceToHost, st)))
+                return e;
+            if ((e = cudaMemcpyAsync(hd.data(), dd, (size_t)m * m * sizeof(double),
+                                     cudaMemcpyDeviceToHost, st)))
+                return e;
+            if ((e = cudaFreeAsync(dp, st))) return e;
+            if ((e = cudaFreeAsync(dd, st))) return e;
+            if ((e = cudaStreamSynchronize(st))) return e;
+        }
+        {
+            // greedy chain: from pivot 0, always on to the nearest unused one
             std::vector<char> used((size_t)m, 0);
             int cur = 0;
             for (int q = 0; q < m; q++) {
@@ -1400,16 +1440,12 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
                 hn[(size_t)q] = (float)pn2;
                 int nxt = -1;
                 double bd = 0.0;
+                const double *row = hd.data() + (size_t)cur * m;
                 for (int r = 0; r < m; r++) {
                     if (used[(size_t)r]) continue;
-                    double dd = 0.0;
-                    for (int d = 0; d < D; d++) {
-                        const double t = (double)hp[(size_t)cur * D + d] - hp[(size_t)r * D + d];
-                        dd += t * t;
-                    }
-                    if (nxt < 0 || dd < bd) {
+                    if (nxt < 0 || row[r] < bd) {
                         nxt = r;
-                        bd = dd;
+                        bd = row[r];
                     }
                 }
                 if (nxt < 0) break;
