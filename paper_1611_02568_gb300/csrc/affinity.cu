@@ -244,14 +244,18 @@ __global__ void __launch_bounds__(kKnnThreads)
 }
 
 // ---------------------------------------------------------------- tensor-core kNN
-// The same search on the tensor cores: the dot products q.c of a 128 x 128
-// tile come from tcgen05 MMAs on FP16 copies of X scaled by 2^e, accumulated
-// in FP32 in TMEM.  An FP16 operand carries a relative rounding error of at
-// most u = 2^-11, so |q~.c~ - 2^2e q.c| <= 2^2e |q||c| (2u + u^2 + D 2^-24) and
-// the approximate d2 = |q|^2 + |c|^2 - 2 q.c is within kappa |q||c| (plus
-// FP32 rounding of the norms) of the exact one.  A candidate can only belong
-// to the k nearest if its approximate d2 is below the row's current k-th exact
-// distance plus that bound; only those get their exact FP32 distance
+// The same search on the tensor cores: the dot products of a 128 x 128 tile
+// come from tcgen05 MMAs on FP16 copies x~ of the rows (X scaled by 2^e),
+// accumulated in FP32 in TMEM.  With the norms |x~|^2 of the rounded rows,
+// |q~|^2 + |c~|^2 - 2 q~.c~ is the squared distance of the rounded rows up to
+// the FP32 accumulation (kappa |q~||c~|, kappa about 2 D 2^-24) and the norms'
+// own rounding (eps).  The triangle inequality gives
+// |q - c| >= |q~ - c~| - |q~ - q| - |c~ - c|, and each row's rounding error
+// E = |x~ - x| is known exactly, so a candidate can only belong to the k
+// nearest if |q~ - c~| <= sqrt(tau) + E_q + E_c, tau the row's current k-th
+// exact distance.  The band this leaves is about 2 sqrt(tau) (E_q + E_c), a
+// multiple of |x| 2^-11 rather than of |x|^2 2^-11 as a bound on the dot
+// product alone would be.  Only the survivors get their exact FP32 distance
 // (sum of squared differences) and enter the row's sorted list.
 //
 // One CTA owns 128 query rows and sweeps the candidate tiles outward from its
@@ -262,11 +266,12 @@ __global__ void __launch_bounds__(kKnnThreads)
 // radii, is skipped) and streams the kept ones (pre-swizzled FP16 images, one
 // bulk copy each) into a ring of shared-memory stages; warp 5 issues the MMAs
 // into four TMEM accumulators; warps 0-3 (one query row per thread, TMEM lanes
-// 32w..32w+31) filter.  With h_j = (1-eps)|c_j|^2 and g_j = |c_j| (staged with
-// the tile), a 32-column chunk is skipped when a bound from its min h, max g
-// and max q.c already exceeds the threshold; otherwise each (row, candidate)
-// costs two FMAs and a min: the chunk is skipped when
-//   min_j (h_j - kappa |q| g_j - 2 q.c_j) > tau - (1-eps)|q|^2,
+// 32w..32w+31) filter.  With h_j = (1-eps)|c~_j|^2 and g_j = |c~_j| (staged
+// with the tile, with each 32-column chunk's largest E_c), a chunk is skipped
+// when a bound from its min h, max g and max q.c already exceeds the
+// threshold; otherwise each (row, candidate) costs two FMAs and a min: the
+// chunk is skipped when
+//   min_j (h_j - kappa |q~| g_j - 2 q~.c~_j) > (sqrt(tau) + E_q + max E_c)^2 - (1-eps)|q~|^2,
 // and otherwise the same per-column values pick the survivors.  A warp queues the
 // survivors of its 32 rows (a chain per row through the queue) over as many
 // tiles as it takes to gather a batch; then the warp computes their exact
@@ -283,7 +288,7 @@ constexpr int kTcPolls = 1 << 22;
 constexpr uint32_t kTcSleepNs = 2000u;  // suspend hint of the pipeline waits
 // per candidate tile: h_j (128), g_j (128), then per 32-column chunk min h and
 // max g (4 + 4): 264 floats, 1056 bytes (a multiple of 16 for the bulk copy)
-constexpr int kHG = 2 * kTcCols + 8;
+constexpr int kHG = 2 * kTcCols + 12;
 
 __global__ void k_absmax(int64_t m, const float *__restrict__ X, unsigned *out) {
     unsigned v = 0u;
@@ -318,11 +323,34 @@ __global__ void k_to_half_img(int64_t n, int D, int Dp, int64_t T, float scale,
         *reinterpret_cast<const uint4 *>(h);
 }
 
-// Per candidate tile t (kHG floats from HG + kHG t): h_j = (1-eps)|c_j|^2
-// (+inf past n), then g_j = |c_j|, then for each 32-column chunk the min of its
-// h_j and the max of its g_j (a warp covers one chunk).
+// Per ordered row r, from the same FP16 conversion as the tile images:
+// n16[r] = |x~|^2 of the rounded row x~ (in X's units) and err[r] >= |x~ - x|,
+// the norm of its rounding error, rounded up, plus the largest error a
+// flushed FP16 subnormal could add in each dimension.
+__global__ void k_round_err(int64_t n, int D, float scale, const float *__restrict__ X,
+                            float *__restrict__ n16, float *__restrict__ err) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const float *x = X + r * D;
+    double s2 = 0.0, e2 = 0.0;
+    for (int d = 0; d < D; d++) {
+        const float xs = x[d] * scale;  // exact (a power of two)
+        const float hs = __half2float(__float2half_rn(xs));
+        const float es = hs - xs;       // exact (the two lie within a factor of two, or hs = 0)
+        s2 += (double)hs * hs;
+        e2 += (double)es * es;
+    }
+    const double inv = 1.0 / (double)scale;
+    n16[r] = (float)(s2 * inv * inv);
+    err[r] = (float)((sqrt(e2) * (1.0 + 1e-6) + sqrt((double)D) * 6.103515625e-05) * inv);
+}
+
+// Per candidate tile t (kHG floats from HG + kHG t): h_j = (1-eps)|c~_j|^2 of
+// the rounded rows (+inf past n), then g_j = |c~_j|, then for each 32-column
+// chunk the min of its h_j, the max of its g_j and the max of its rows'
+// rounding errors (a warp covers one chunk).
 __global__ void k_tile_norms(int64_t n, int64_t T, float eps_abs, const float *__restrict__ nrm,
-                             float *__restrict__ HG) {
+                             const float *__restrict__ rerr, float *__restrict__ HG) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= T * kTcCols) return;  // whole warps (T * 128 is a multiple of 32)
     const int64_t t = i / kTcCols;
@@ -332,15 +360,17 @@ __global__ void k_tile_norms(int64_t n, int64_t T, float eps_abs, const float *_
     float *hg = HG + t * kHG;
     hg[j] = h;
     hg[kTcCols + j] = g;
-    float hmin = h, gmax = g;
+    float hmin = h, gmax = g, emax = i < n ? rerr[i] : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         hmin = fminf(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
         gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+        emax = fmaxf(emax, __shfl_xor_sync(0xffffffffu, emax, o));
     }
     if ((j & 31) == 0) {
         hg[2 * kTcCols + (j >> 5)] = hmin;
         hg[2 * kTcCols + 4 + (j >> 5)] = gmax;
+        hg[2 * kTcCols + 8 + (j >> 5)] = emax;
     }
 }
 
@@ -756,7 +786,8 @@ struct KnnTcArgs {
     float inv_s2, kappa, eps_abs;
     const float *X;       // FP32 rows (exact distances)
     const uint8_t *img;   // FP16 tile images
-    const float *nrm;     // |x|^2
+    const float *nrm;     // |x~|^2 of the rounded rows
+    const float *rerr;    // |x~ - x|, rounded up
     const float *HG;      // per tile: h_j, |c_j|, chunk bounds (kHG floats)
     const uint32_t *order;  // sorted position -> row of X (the locality order)
     int32_t *out_idx;
@@ -1004,6 +1035,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
         const int64_t qi = q0 + tid;
         const bool qvalid = qi < n;
         const float qn2 = qvalid ? a.nrm[qi] : 0.f, qn1 = sqrtf(qn2);
+        const float Eq = qvalid ? a.rerr[qi] : 0.f;
         KnnEntry *heap = lst + (size_t)tid * ks;
         float tau = INFINITY;
         int32_t jlast = 0x7fffffff;
@@ -1012,9 +1044,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
         const float onem = 1.0f - a.eps_abs;
         const float cneg = -2.0f * a.inv_s2;
         const bool vec4 = ((a.D & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.X) & 15) == 0);
-        // tau - (1 - eps)|q|^2; finite while the list fills so that padding
-        // candidates (+inf) never pass
-        float tauA = 3.402823466e38f;
+        // sqrt(tau) + |q~ - q| (+inf while the list fills); a chunk's
+        // threshold adds its rows' largest rounding error
+        float sqE = INFINITY;
         uint32_t *wq = qc_all + warp * kTcQueue;
         float *wd = qd_all + warp * kTcQueue;
         uint16_t *wp = qp_all + warp * kTcQueue;
@@ -1058,7 +1090,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                 const KnnEntry rt = heap[0];
                 tau = rt.d;
                 jlast = rt.j;
-                tauA = fminf(tau - onem * qn2, 3.402823466e38f);
+                sqE = sqrtf(tau) + Eq;
             }
             __syncwarp();
             head = kNil;
@@ -1119,12 +1151,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                 const float vmax = fmaxf(fmaxf(fmaxf(mx[0], mx[1]), fmaxf(mx[2], mx[3])),
                                          fmaxf(fmaxf(mx[4], mx[5]), fmaxf(mx[6], mx[7])));
                 const float hmin = hb[2 * kTcCols + ci], gmax = hb[2 * kTcCols + 4 + ci];
+                // survivors: |q~ - c~| <= sqrt(tau) + |q~ - q| + |c~ - c| (the
+                // true distance is at least the rounded rows' distance less
+                // both rounding errors), squared with a margin of 2^-20 for
+                // its own rounding; tau - (1 - eps)|q~|^2 in the form below,
+                // finite while the list fills so that padding (+inf) never passes
+                const float tE = sqE + hb[2 * kTcCols + 8 + ci];
+                const float tauA =
+                    fminf(fmaf(tE * tE, 9.5367431640625e-07f, tE * tE) - onem * qn2, 3.402823466e38f);
                 const float lb = fmaf(cneg, vmax, fmaf(-Bq, gmax, hmin));
                 const float margin = (fabsf(hmin) + Bq * gmax + fabsf(cneg * vmax)) * 1.9073486e-6f;
                 const bool near = qvalid && !(lb > tauA + margin);
                 float m = INFINITY;
                 if (near) {
-                    // e_j = (1-eps)|c|^2 - kappa|q||c| - 2 q.c (in place of v)
+                    // e_j = (1-eps)|c~|^2 - kappa|q~||c~| - 2 q~.c~ (in place of v)
                     float mn[8];
 #pragma unroll
                     for (int j4 = 0; j4 < 8; j4++) {
@@ -1141,8 +1181,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                 }
                 uint32_t sm = 0u;
                 if (near && m <= tauA) {
-                    // survivors:
-                    //   (1-eps)|c|^2 - kappa|q||c| - 2 q.c <= tau - (1-eps)|q|^2
+                    // survivors: e_j <= (sqrt(tau) + E_q + max E_c)^2 - (1-eps)|q~|^2
 #pragma unroll
                     for (int j = 0; j < 32; j++) sm |= (v[j] <= tauA) ? (1u << j) : 0u;
                     if (qi >= c0 + cb && qi < c0 + cb + 32) sm &= ~(1u << (int)(qi - c0 - cb));
@@ -1397,7 +1436,11 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         const float scale = ldexpf(1.0f, ex);
         const float inv_s2 = ldexpf(1.0f, -2 * ex);
         const float u = 1.0f / 2048.0f;
-        const float kappa = 1.25f * 2.0f * (2.0f * u + u * u + (float)Dp * 5.9604645e-8f * 1.01f);
+        // the MMA's FP32 accumulation of exact FP16 products (the FP16
+        // rounding itself enters through the rows' rounding errors), and
+        // 2^-19 for the filter's own arithmetic
+        const float kappa = 1.25f * 2.0f * ((float)Dp * 5.9604645e-8f * 1.01f) + 1.9073486e-06f;
+        (void)u;
         const float eps_abs = (float)(2 * D + 8) * 5.9604645e-8f;
         // locality order: rows grouped by their nearest of m pivots (rows
         // i n / m), the pivots chained greedily by nearest neighbour on the host
@@ -1584,7 +1627,12 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         const int64_t nchunks = T * kTcRows * (Dp / 8);
         k_to_half_img<<<(unsigned)((nchunks + 255) / 256), 256, 0, st>>>(n, D, Dp, T, scale, Xo,
                                                                           img);
-        k_tile_norms<<<(unsigned)((T * kTcCols + 255) / 256), 256, 0, st>>>(n, T, eps_abs, ns, HG);
+        float *n16 = nullptr, *rerr = nullptr;
+        if ((e = cudaMallocAsync(&n16, (size_t)n * sizeof(float), st))) return e;
+        if ((e = cudaMallocAsync(&rerr, (size_t)n * sizeof(float), st))) return e;
+        k_round_err<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, D, scale, Xo, n16, rerr);
+        k_tile_norms<<<(unsigned)((T * kTcCols + 255) / 256), 256, 0, st>>>(n, T, eps_abs, n16,
+                                                                           rerr, HG);
         if ((e = cudaGetLastError())) return e;
         // tile centroids and radii (the loader's pruning bound)
         float *cent = nullptr, *rad = nullptr;
@@ -1607,7 +1655,8 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         ka.eps_abs = eps_abs;
         ka.X = Xo;
         ka.img = img;
-        ka.nrm = ns;
+        ka.nrm = n16;
+        ka.rerr = rerr;
         ka.HG = HG;
         ka.order = order;
         ka.out_idx = idx;
@@ -1672,6 +1721,8 @@ cudaError_t launch_knn(pxsne_ctx *c, const float *Xdev, int64_t n, int32_t D, in
         if (cand) cudaFreeAsync(cand, st);
         cudaFreeAsync(img, st);
         cudaFreeAsync(HG, st);
+        cudaFreeAsync(n16, st);
+        cudaFreeAsync(rerr, st);
         cudaFreeAsync(cent, st);
         cudaFreeAsync(rad, st);
         cudaFreeAsync(amax, st);
