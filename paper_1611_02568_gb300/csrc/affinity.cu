@@ -1189,18 +1189,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                 if (__any_sync(0xffffffffu, sm != 0u)) {
                     // append the chunk's survivors to the queue, 16 columns at
                     // a time (at most 512 entries; flush first if they might
-                    // not fit)
+                    // not fit); one warp scan gives both halves' positions
+                    // (16-bit fields: a half's total is at most 512)
+                    const uint32_t c2 = (uint32_t)__popc(sm & 0x0000ffffu) |
+                                        ((uint32_t)__popc(sm & 0xffff0000u) << 16);
+                    uint32_t incl2 = c2;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, incl2, o);
+                        if (lane >= o) incl2 += y;
+                    }
+                    const uint32_t tot2 = __shfl_sync(0xffffffffu, incl2, 31);
 #pragma unroll
                     for (int hf = 0; hf < 2; hf++) {
                         const uint32_t hm = hf ? (sm & 0xffff0000u) : (sm & 0x0000ffffu);
                         const uint32_t cnt = (uint32_t)__popc(hm);
-                        uint32_t incl = cnt;
-#pragma unroll
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-                            if (lane >= o) incl += y;
-                        }
-                        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                        const uint32_t incl = hf ? (incl2 >> 16) : (incl2 & 0xffffu);
+                        const uint32_t total = hf ? (tot2 >> 16) : (tot2 & 0xffffu);
                         if (total == 0u) continue;
                         if (qn + total > (uint32_t)kTcQueue) flush();
                         uint32_t mm = hm;
