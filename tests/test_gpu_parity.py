@@ -287,6 +287,22 @@ def test_affinities_match_oracle(px, knn_path):
     assert abs(val.astype(np.float64).sum() - 1.0) < 1e-5
 
 
+def test_knn_far_from_origin(px, knn_path):
+    """Points far from the origin next to their spread (the 10-Gaussian
+    mixture moved by 500 on every axis: |x| about 3,500 against neighbour
+    distances about 10), where the FP16 copies' rounding errors are a
+    sizeable part of the distances: the lists must stay exact."""
+    X, _ = datagen.gauss10(2, n=3000)
+    X = (X.astype(np.float64) + 500.0).astype(np.float32)
+    k = 90
+    rows = np.arange(X.shape[0])
+    idx_o, d2_o = oracle.knn(X, k)
+    with make_ctx(px, L=9, k=k, perplexity=30.0) as ctx:
+        ctx.affinities(X)
+        idx, d2, _ = ctx.get_knn()
+    check_knn_rows(X, rows, idx_o, d2_o, idx, d2)
+
+
 def test_affinities_with_hub_rows(px):
     """Rows of the symmetric P longer than a warp's staging buffer (1,024
     entries): points spread over a shell (radii 8 to 12) around two central
