@@ -260,13 +260,14 @@ __global__ void __launch_bounds__(kKnnThreads)
 //
 // One CTA owns 128 query rows and sweeps the candidate tiles outward from its
 // own in the locality order (neighbouring CTAs read the same tiles at about
-// the same time, so each tile is shared through L2).  Warp roles: warp 4
+// the same time, so each tile is shared through L2).  Warp roles: warp 8
 // judges the candidate tiles (a tile whose rows all lie beyond the query rows'
 // current k-th distances, by the triangle inequality on tile centroids and
 // radii, is skipped) and streams the kept ones (pre-swizzled FP16 images, one
-// bulk copy each) into a ring of shared-memory stages; warp 5 issues the MMAs
-// into four TMEM accumulators; warps 0-3 (one query row per thread, TMEM lanes
-// 32w..32w+31) filter.  With h_j = (1-eps)|c~_j|^2 and g_j = |c~_j| (staged
+// bulk copy each) into a ring of shared-memory stages; warp 9 issues the MMAs
+// into four TMEM accumulators; warps 0-7 filter, warps w and w + 4 on the
+// same 32 query rows (TMEM lanes 32(w % 4) ..), each on 64 of a tile's 128
+// columns, so that two warps per scheduler hide each other's latencies.  With h_j = (1-eps)|c~_j|^2 and g_j = |c~_j| (staged
 // with the tile, with each 32-column chunk's largest E_c), a chunk is skipped
 // when a bound from its min h, max g and max q.c already exceeds the
 // threshold; otherwise each (row, candidate) costs two FMAs and a min: the
@@ -275,15 +276,18 @@ __global__ void __launch_bounds__(kKnnThreads)
 // and otherwise the same per-column values pick the survivors.  A warp queues the
 // survivors of its 32 rows (a chain per row through the queue) over as many
 // tiles as it takes to gather a batch; then the warp computes their exact
-// distances, one survivor per lane, and every lane walks its own row's chain
-// inserting them, all lanes at once.
+// distances, one survivor per lane, and, holding the lock its row quarter
+// shares with the other warp on those rows, every lane walks its own row's
+// chain inserting them, all lanes at once, against the lists' current roots.
 constexpr int kTcRows = 128;     // query rows per CTA (MMA M)
 constexpr int kTcCols = 128;     // candidates per tile (MMA N)
 constexpr int kTcStages = 2;     // candidate-tile stages in shared memory
-constexpr int kTcQueue = 768;    // survivor queue per filter warp (entries)
+constexpr int kTcQueue = 384;    // survivor queue per filter warp (entries)
 constexpr uint32_t kTcFlushAt = 128u;  // queued survivors that trigger a flush
 constexpr int kTcAcc = 4;        // TMEM accumulators (4 x 128 columns)
-constexpr int kTcThreads = 192;  // warps 0-3 filter, 4 loads, 5 issues MMAs
+constexpr int kTcFilterWarps = 8;  // two per TMEM lane quarter, 64 columns each
+constexpr int kTcThreads = 32 * (kTcFilterWarps + 2);  // then the loader, then the MMA issuer
+constexpr int kTcLoadWarp = kTcFilterWarps, kTcMmaWarp = kTcFilterWarps + 1;
 constexpr int kTcPolls = 1 << 22;
 constexpr uint32_t kTcSleepNs = 2000u;  // suspend hint of the pipeline waits
 // per candidate tile: h_j (128), g_j (128), then per 32-column chunk min h and
@@ -816,7 +820,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
     __shared__ volatile int s_abort;
     // pruning: per filter warp the largest current k-th distance of its rows
     // (only decreases), and the candidate tile of each kept slot (-1: end)
-    __shared__ volatile float s_taumax[4];
+    __shared__ volatile float s_taumax[kTcFilterWarps];
+    // the two filter warps of a lane quarter insert into the same rows'
+    // lists, one at a time: a lock per quarter
+    __shared__ int s_lock[4];
     __shared__ volatile int s_tile[8];
     __shared__ float s_cq[128];  // the query tile's centroid (loader warp)
     // 1024-byte aligned base for the swizzled operand tiles
@@ -835,15 +842,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
     // per filter warp: queued survivors (row lane << 24 | candidate index),
     // their exact d2 and, per entry, the previous entry of the same row
     uint32_t *qc_all = reinterpret_cast<uint32_t *>(lst + kTcRows * ks);
-    float *qd_all = reinterpret_cast<float *>(qc_all + 4 * kTcQueue);
-    uint16_t *qp_all = reinterpret_cast<uint16_t *>(qd_all + 4 * kTcQueue);
+    float *qd_all = reinterpret_cast<float *>(qc_all + kTcFilterWarps * kTcQueue);
+    uint16_t *qp_all = reinterpret_cast<uint16_t *>(qd_all + kTcFilterWarps * kTcQueue);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t qt = blockIdx.x;  // query tile
     const int64_t q0 = qt * kTcRows;
 
     for (int e = tid; e < kTcRows * ks; e += kTcThreads) lst[e] = KnnEntry{INFINITY, 0x7fffffff};
-    if (warp == 5) tc::tmem_alloc(&tslot, kTcAcc * kTcCols);
+    if (warp == kTcMmaWarp) tc::tmem_alloc(&tslot, kTcAcc * kTcCols);
     if (tid == 0) {
         tc::mbar_init(&bar_a, 1);
         for (int s = 0; s < kTcStages; s++) {
@@ -852,19 +859,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
         }
         for (int b = 0; b < kTcAcc; b++) {
             tc::mbar_init(&bar_tf[b], 1);
-            tc::mbar_init(&bar_te[b], 4);
+            tc::mbar_init(&bar_te[b], kTcFilterWarps);
             tc::mbar_init(&bar_hf[b], 1);
-            tc::mbar_init(&bar_he[b], 4);
+            tc::mbar_init(&bar_he[b], kTcFilterWarps);
         }
         s_abort = 0;
-        for (int w = 0; w < 4; w++) s_taumax[w] = INFINITY;
+        for (int w = 0; w < kTcFilterWarps; w++) s_taumax[w] = INFINITY;
+        for (int w = 0; w < 4; w++) s_lock[w] = 0;
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tbase = tslot;
 
-    if (warp == 4) {
+    if (warp == kTcLoadWarp) {
         // ---- producer: candidate tiles and their h values.  A tile whose
         // rows are all farther from every query row than that row's current
         // k-th distance (triangle inequality on the tiles' centroids and
@@ -906,7 +914,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                     dd = fmaf(e0, e0, fmaf(e1, e1, fmaf(e2, e2, fmaf(e3, e3, dd))));
                 }
             }
-            const float taum = fmaxf(fmaxf(s_taumax[0], s_taumax[1]), fmaxf(s_taumax[2], s_taumax[3]));
+            float taum = s_taumax[0];
+#pragma unroll
+            for (int w = 1; w < kTcFilterWarps; w++) taum = fmaxf(taum, s_taumax[w]);
             const float lbd = sqrtf(dd) * 0.9999f - rq - (in ? a.rad[tl] : 0.f);
             // (the approximate search takes its W tiles whole: with the bound,
             // which tiles pass would depend on how far the filter warps have
@@ -986,7 +996,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             for (int64_t q = (n_hf > wh ? n_hf - wh : 0); q < n_hf; q++)
                 tc::mbar_wait(&bar_hf[q % kTcAcc], (uint32_t)((q / kTcAcc) & 1), kTcPolls);
         }
-    } else if (warp == 5) {
+    } else if (warp == kTcMmaWarp) {
         // ---- MMA issuer
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_f16(kTcRows, kTcCols, 0);
@@ -1031,12 +1041,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                 tc::mbar_wait(&bar_tf[j % kTcAcc], (uint32_t)((j / kTcAcc) & 1), kTcPolls);
         }
     } else {
-        // ---- filter: thread tid owns query row q0 + tid
-        const int64_t qi = q0 + tid;
+        // ---- filter: warps quarter and quarter + 4 own query rows
+        // q0 + 32 quarter + lane; warp `half` filters columns 64 half .. +63
+        const int quarter = warp & 3, half = warp >> 2;
+        const int64_t qi = q0 + 32 * quarter + lane;
         const bool qvalid = qi < n;
         const float qn2 = qvalid ? a.nrm[qi] : 0.f, qn1 = sqrtf(qn2);
         const float Eq = qvalid ? a.rerr[qi] : 0.f;
-        KnnEntry *heap = lst + (size_t)tid * ks;
+        KnnEntry *heap = lst + (size_t)(32 * quarter + lane) * ks;
         float tau = INFINITY;
         int32_t jlast = 0x7fffffff;
         uint32_t n_exact = 0u, n_ins = 0u;
@@ -1059,9 +1071,35 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             __syncwarp();
             for (uint32_t q = lane; q < qn; q += 32) {
                 const uint32_t e = wq[q];
-                wd[q] = thread_exact_d2(a.X, a.D, q0 + 32 * warp + (e >> 24), e & 0xffffffu, vec4);
+                wd[q] = thread_exact_d2(a.X, a.D, q0 + 32 * quarter + (e >> 24), e & 0xffffffu,
+                                        vec4);
             }
             __syncwarp();
+            // the lists of these rows are shared with the quarter's other
+            // filter warp: insert while holding the quarter's lock (bounded
+            // wait; the holder waits on nothing), from the lists' current roots
+            bool locked = true;
+            if (lane == 0) {
+                int it = 0;
+                while (atomicCAS(&s_lock[quarter], 0, 1) != 0) {
+                    if (++it >= kTcPolls) {
+                        locked = false;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            locked = __shfl_sync(0xffffffffu, locked, 0);
+            __threadfence_block();
+            if (!locked) {
+                s_abort = 1;
+                if (lane == 0) atomicOr(a.err, (unsigned)PXSNE_DEVERR_TIMEOUT);
+                head = kNil;
+            } else {
+                const KnnEntry r0 = heap[0];
+                tau = r0.d;
+                jlast = r0.j;
+            }
             for (uint32_t q = head; q != kNil; q = wp[q]) {
                 const int32_t cand = (int32_t)__ldg(a.order + (wq[q] & 0xffffffu));
                 const float d = wd[q];
@@ -1090,9 +1128,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                 const KnnEntry rt = heap[0];
                 tau = rt.d;
                 jlast = rt.j;
-                sqE = sqrtf(tau) + Eq;
             }
             __syncwarp();
+            __threadfence_block();
+            if (locked && lane == 0) atomicExch(&s_lock[quarter], 0);
+            sqE = sqrtf(tau) + Eq;
             head = kNil;
             qn = 0u;
             // the largest current k-th distance of the warp's rows, for the
@@ -1121,24 +1161,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
             const int64_t t = tt;
             const int64_t c0 = t * kTcCols;
             const float *hb = hbuf + b * kHG;
-            // all 128 columns of the warp's rows in one round trip; the
+            // the other warp of the quarter may have tightened the rows' lists
+            // (a root read while it inserts is the old or the new one, both
+            // at least the final k-th distance)
+            {
+                const float tr = reinterpret_cast<volatile const KnnEntry *>(heap)->d;
+                if (tr < tau) sqE = sqrtf(tr) + Eq;
+            }
+            // the warp's 64 columns of its rows in one round trip; the
             // accumulator is released right after, h and g after the filter
-            uint32_t raw[4][32];
+            uint32_t raw[2][32];
 #pragma unroll
-            for (int ci = 0; ci < 4; ci++)
-                tc::tmem_ld32_async(
-                    tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)(b * kTcCols + 32 * ci),
-                    raw[ci]);
+            for (int cc = 0; cc < 2; cc++)
+                tc::tmem_ld32_async(tbase + ((uint32_t)(32 * quarter) << 16) +
+                                        (uint32_t)(b * kTcCols + 64 * half + 32 * cc),
+                                    raw[cc]);
             tc::tmem_wait_ld();
             tc::fence_before();
             __syncwarp();
             if (lane == 0) tc::mbar_arrive(&bar_te[b]);
 #pragma unroll
-            for (int ci = 0; ci < 4; ci++) {
+            for (int cc = 0; cc < 2; cc++) {
+                const int ci = 2 * half + cc;
                 const int cb = 32 * ci;
                 float v[32];
 #pragma unroll
-                for (int j = 0; j < 32; j++) v[j] = __uint_as_float(raw[ci][j]);
+                for (int j = 0; j < 32; j++) v[j] = __uint_as_float(raw[cc][j]);
                 // Chunk bound: e_j >= min h - kappa|q| max g - 2 max_j q.c
                 // (-2 < 0, kappa|q| >= 0).  A chunk whose bound exceeds the
                 // threshold by more than the FP32 roundings of both sides
@@ -1187,25 +1235,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
                     if (qi >= c0 + cb && qi < c0 + cb + 32) sm &= ~(1u << (int)(qi - c0 - cb));
                 }
                 if (__any_sync(0xffffffffu, sm != 0u)) {
-                    // append the chunk's survivors to the queue, 16 columns at
-                    // a time (at most 512 entries; flush first if they might
-                    // not fit); one warp scan gives both halves' positions
-                    // (16-bit fields: a half's total is at most 512)
-                    const uint32_t c2 = (uint32_t)__popc(sm & 0x0000ffffu) |
-                                        ((uint32_t)__popc(sm & 0xffff0000u) << 16);
-                    uint32_t incl2 = c2;
+                    // append the chunk's survivors to the queue, 8 columns at
+                    // a time (at most 256 entries, which a flushed queue holds;
+                    // flush first if they might not fit); one warp scan gives
+                    // two groups' positions (16-bit fields)
+                    uint32_t incl4[2], tot4[2];
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t y = __shfl_up_sync(0xffffffffu, incl2, o);
-                        if (lane >= o) incl2 += y;
+                    for (int pr = 0; pr < 2; pr++) {
+                        uint32_t x = (uint32_t)__popc(sm & (0xffu << (16 * pr))) |
+                                     ((uint32_t)__popc(sm & (0xff00u << (16 * pr))) << 16);
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                            if (lane >= o) x += y;
+                        }
+                        incl4[pr] = x;
+                        tot4[pr] = __shfl_sync(0xffffffffu, x, 31);
                     }
-                    const uint32_t tot2 = __shfl_sync(0xffffffffu, incl2, 31);
 #pragma unroll
-                    for (int hf = 0; hf < 2; hf++) {
-                        const uint32_t hm = hf ? (sm & 0xffff0000u) : (sm & 0x0000ffffu);
+                    for (int hf = 0; hf < 4; hf++) {
+                        const uint32_t hm = sm & (0xffu << (8 * hf));
                         const uint32_t cnt = (uint32_t)__popc(hm);
-                        const uint32_t incl = hf ? (incl2 >> 16) : (incl2 & 0xffffu);
-                        const uint32_t total = hf ? (tot2 >> 16) : (tot2 & 0xffffu);
+                        const uint32_t incl = (hf & 1) ? (incl4[hf >> 1] >> 16) : (incl4[hf >> 1] & 0xffffu);
+                        const uint32_t total = (hf & 1) ? (tot4[hf >> 1] >> 16) : (tot4[hf >> 1] & 0xffffu);
                         if (total == 0u) continue;
                         if (qn + total > (uint32_t)kTcQueue) flush();
                         uint32_t mm = hm;
@@ -1234,7 +1286,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 5) tc::tmem_dealloc(tbase, kTcAcc * kTcCols);
+    if (warp == kTcMmaWarp) tc::tmem_dealloc(tbase, kTcAcc * kTcCols);
     // heap sort of each row's list (ascending), then out
     if (tid < kTcRows) {
         KnnEntry *heap = lst + (size_t)tid * ks;
@@ -1275,7 +1327,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const KnnTcArgs a) {
 
 static size_t knn_tc_smem(int Dp, int k) {
     return (size_t)(1 + kTcStages) * kTcRows * Dp * 2 + (size_t)kTcAcc * kHG * 4 +
-           (size_t)kTcRows * (k | 1) * 8 + (size_t)4 * kTcQueue * (4 + 4 + 2) + 1024;
+           (size_t)kTcRows * (k | 1) * 8 + (size_t)kTcFilterWarps * kTcQueue * (4 + 4 + 2) + 1024;
 }
 
 // The bounded wait of the pipelines above, on an mbarrier that nothing
