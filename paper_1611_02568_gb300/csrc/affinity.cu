@@ -283,7 +283,7 @@ constexpr int kTcRows = 128;     // query rows per CTA (MMA M)
 constexpr int kTcCols = 128;     // candidates per tile (MMA N)
 constexpr int kTcStages = 2;     // candidate-tile stages in shared memory
 constexpr int kTcQueue = 384;    // survivor queue per filter warp (entries)
-constexpr uint32_t kTcFlushAt = 128u;  // queued survivors that trigger a flush
+constexpr uint32_t kTcFlushAt = 48u;   // queued survivors that trigger a flush
 constexpr int kTcAcc = 4;        // TMEM accumulators (4 x 128 columns)
 constexpr int kTcFilterWarps = 8;  // two per TMEM lane quarter, 64 columns each
 constexpr int kTcThreads = 32 * (kTcFilterWarps + 2);  // then the loader, then the MMA issuer
