@@ -287,6 +287,18 @@ def test_affinities_match_oracle(px, knn_path):
     assert abs(val.astype(np.float64).sum() - 1.0) < 1e-5
 
 
+@pytest.mark.parametrize("n,k", [(130, 5), (129, 90), (200, 90), (257, 33)])
+def test_knn_small_sizes(px, knn_path, n, k):
+    """Small searches: a few tiles, the last one ragged (129 rows: one row in
+    it), k close to n, a small k (short lists, odd row strides)."""
+    X, _ = datagen.gauss10(4, n=n)
+    idx_o, d2_o = oracle.knn(X, k)
+    with make_ctx(px, L=9, k=k, perplexity=min(30.0, k / 3.0)) as ctx:
+        ctx.affinities(X)
+        idx, d2, _ = ctx.get_knn()
+    check_knn_rows(X, np.arange(n), idx_o, d2_o, idx, d2)
+
+
 def test_knn_far_from_origin(px, knn_path):
     """Points far from the origin next to their spread (the 10-Gaussian
     mixture moved by 500 on every axis: |x| about 3,500 against neighbour
