@@ -299,6 +299,28 @@ def test_knn_small_sizes(px, knn_path, n, k):
     check_knn_rows(X, np.arange(n), idx_o, d2_o, idx, d2)
 
 
+def test_knn_many_duplicates(px, knn_path):
+    """300 identical rows: each one's list is decided by the tie rule alone
+    (distance 0, then the lower index), whatever order the survivors are
+    inserted in.  Those rows' k neighbours all lie at distance 0, so no
+    bandwidth gives them perplexity 30: the call reports the bisection flag,
+    as documented, and the lists are still there."""
+    X, _ = datagen.gauss10(5, n=1000)
+    X[100:400] = X[100]
+    k = 90
+    idx_o, d2_o = oracle.knn(X, k)
+    with make_ctx(px, L=9, k=k, perplexity=30.0) as ctx:
+        with pytest.raises(px.PxsneError, match="bisection"):
+            ctx.affinities(X)
+        idx, d2, _ = ctx.get_knn()
+        assert ctx.sync() == 0
+    check_knn_rows(X, np.arange(X.shape[0]), idx_o, d2_o, idx, d2)
+    for i in (100, 150, 399):
+        want = [j for j in range(100, 400) if j != i][:k]
+        assert list(idx[i]) == want, i
+        assert not d2[i].any()
+
+
 def test_knn_far_from_origin(px, knn_path):
     """Points far from the origin next to their spread (the 10-Gaussian
     mixture moved by 500 on every axis: |x| about 3,500 against neighbour
